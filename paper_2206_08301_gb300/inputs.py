@@ -1,0 +1,186 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle harness.
+
+This module holds no MTTKRP or TTMc arithmetic.  It defines one counter-based
+random generator and the synthetic tensors built from it, so that any element
+of any input can be regenerated by index on the host (for sampled oracle
+checks) and on the device (by the CUDA generator kernels, which implement the
+same definitions and are checked bit for bit against this module).
+
+Generator
+---------
+SplitMix64 (S. Vigna, the ``splitmix64.c`` public-domain generator, also
+described by Steele, Lea and Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014): state advances by the golden-ratio increment
+``GAMMA`` and every output is the 64-bit finaliser ``mix64`` of the state.
+
+* ``state0(seed, stream) = mix64(seed + stream * GAMMA)``            (mod 2^64)
+* ``raw(seed, stream, i) = mix64(state0 + (i + 1) * GAMMA)``         (mod 2^64)
+
+i.e. element ``i`` of a stream is the (i+1)-th output of a SplitMix64
+generator seeded with ``state0``.
+
+Derived draws (all exact in the stated precision, so host and device agree
+bit for bit):
+
+* ``uniform_f32``: ``(raw >> 40) * 2^-23 - 1``  in [-1, 1) (24 random bits).
+* ``uniform_f64``: ``(raw >> 11) * 2^-52 - 1``  in [-1, 1) (53 random bits).
+* ``irwin_hall``: ``(sum_{t<12} (raw(12 i + t) >> 40) - 6 * 2^24) * 2^-24``,
+  the classical sum-of-twelve-uniforms approximation of N(0, 1) (mean 0,
+  variance 1), computed in exact integer arithmetic.
+* ``normal_f64`` (host only): Box-Muller on ``raw(2 i)`` and ``raw(2 i + 1)``.
+  It goes through ``log``/``cos``, so it is used only for small operands
+  (factor matrices) that are generated on the host and uploaded.
+
+Synthetic CP tensor
+-------------------
+``X[idx] = f32( sum_s prod_m A_m[i_m, s]  +  sigma * irwin_hall(idx) )``
+evaluated in float64 with the product taken over m = 0..N-1 left to right,
+the sum over s = 0..R-1 left to right, no fused multiply-add, then rounded to
+nearest float32.  numpy evaluates it with separate multiplies and adds, and
+the device kernel uses explicitly rounded double operations in the same order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# Stream identifiers: one independent stream per role of a workload.
+STREAM_X = 1          # the dense input tensor X
+STREAM_NOISE = 2      # additive noise of a CP tensor
+STREAM_FACTOR = 16    # factor matrix m uses STREAM_FACTOR + m
+STREAM_CP = 64        # CP generating factor m uses STREAM_CP + m
+STREAM_INIT = 128     # CP-ALS initial factor m uses STREAM_INIT + m
+STREAM_SAMPLE = 250   # choice of sampled output rows
+STREAM_DRAW = 251     # workload parameters (extents, ranks, modes)
+
+
+def mix64(z):
+    """SplitMix64 output finaliser (Vigna's constants), on uint64 numpy arrays."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def state0(seed: int, stream: int) -> np.uint64:
+    """Initial SplitMix64 state of ``stream`` under ``seed``."""
+    with np.errstate(over="ignore"):
+        s = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + np.uint64(stream) * GAMMA
+    return np.uint64(mix64(np.array([s], dtype=np.uint64))[0])
+
+
+def raw(seed: int, stream: int, idx) -> np.ndarray:
+    """64-bit draws for element indices ``idx`` (array-like of non-negative ints)."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    s0 = state0(seed, stream)
+    with np.errstate(over="ignore"):
+        st = s0 + (idx + np.uint64(1)) * GAMMA
+    return mix64(st)
+
+
+def uniform_f32(seed: int, stream: int, idx) -> np.ndarray:
+    """float32 uniform on [-1, 1) for element indices ``idx`` (exact)."""
+    u = (raw(seed, stream, idx) >> np.uint64(40)).astype(np.float64)
+    return (u * 2.0 ** -23 - 1.0).astype(np.float32)
+
+
+def uniform_f64(seed: int, stream: int, idx) -> np.ndarray:
+    """float64 uniform on [-1, 1) for element indices ``idx`` (exact)."""
+    u = (raw(seed, stream, idx) >> np.uint64(11)).astype(np.float64)
+    return u * 2.0 ** -52 - 1.0
+
+
+def irwin_hall(seed: int, stream: int, idx) -> np.ndarray:
+    """Approximate N(0,1) draw: sum of 12 uniform 24-bit integers, centred and scaled.
+
+    Exact: the integer sum is below 2^28 and the scaling is a power of two.
+    """
+    idx = np.asarray(idx, dtype=np.uint64)
+    acc = np.zeros(idx.shape, dtype=np.uint64)
+    base = idx * np.uint64(12)
+    for t in range(12):
+        acc += raw(seed, stream, base + np.uint64(t)) >> np.uint64(40)
+    return (acc.astype(np.int64) - 6 * (1 << 24)).astype(np.float64) * 2.0 ** -24
+
+
+def normal_f64(seed: int, stream: int, n: int, mu: float = 0.0, sigma: float = 1.0) -> np.ndarray:
+    """Host-only N(mu, sigma^2) draws by Box-Muller (one draw per pair of raws)."""
+    i = np.arange(n, dtype=np.uint64)
+    r1 = raw(seed, stream, i * np.uint64(2))
+    r2 = raw(seed, stream, i * np.uint64(2) + np.uint64(1))
+    u1 = ((r1 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+    u2 = (r2 >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return mu + sigma * (np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2))
+
+
+# ---------------------------------------------------------------------------
+# Whole operands
+# ---------------------------------------------------------------------------
+
+def tensor_uniform_f32(seed: int, dims, stream: int = STREAM_X) -> np.ndarray:
+    """Dense row-major float32 tensor of shape ``dims`` with uniform[-1,1) entries."""
+    n = int(np.prod(dims, dtype=np.int64))
+    return uniform_f32(seed, stream, np.arange(n, dtype=np.uint64)).reshape(dims)
+
+
+def tensor_uniform_f64(seed: int, dims, stream: int = STREAM_X) -> np.ndarray:
+    n = int(np.prod(dims, dtype=np.int64))
+    return uniform_f64(seed, stream, np.arange(n, dtype=np.uint64)).reshape(dims)
+
+
+def factor_normal(seed: int, m: int, rows: int, cols: int, sigma: float = 1.0,
+                  stream_base: int = STREAM_FACTOR) -> np.ndarray:
+    """Factor matrix (rows x cols, row-major) with N(0, sigma^2) entries, float64."""
+    return normal_f64(seed, stream_base + m, rows * cols, 0.0, sigma).reshape(rows, cols)
+
+
+def flat_index(dims, coords) -> np.ndarray:
+    """Row-major flat index of integer coordinate arrays ``coords`` (one per mode)."""
+    flat = np.zeros(np.broadcast(*coords).shape, dtype=np.uint64)
+    for d, c in zip(dims, coords):
+        flat = flat * np.uint64(d) + np.asarray(c, dtype=np.uint64)
+    return flat
+
+
+def cp_values(dims, cp_factors, sigma: float, seed: int, coords) -> np.ndarray:
+    """Entries of the synthetic CP-plus-noise tensor at coordinate arrays ``coords``.
+
+    ``cp_factors[m]`` is the float64 generating factor of mode m (I_m x Rc).
+    Evaluated exactly as the module docstring states.
+    """
+    shape = np.broadcast(*coords).shape
+    rc = cp_factors[0].shape[1]
+    acc = np.zeros(shape, dtype=np.float64)
+    for s in range(rc):
+        term = cp_factors[0][np.asarray(coords[0]), s]
+        for m in range(1, len(dims)):
+            term = term * cp_factors[m][np.asarray(coords[m]), s]
+        acc = acc + term
+    if sigma != 0.0:
+        z = irwin_hall(seed, STREAM_NOISE, flat_index(dims, coords))
+        acc = acc + np.float64(sigma) * z
+    return acc.astype(np.float32)
+
+
+def tensor_cp_f32(seed: int, dims, cp_factors, sigma: float) -> np.ndarray:
+    """Whole CP-plus-noise tensor (small shapes only: it is built on the host)."""
+    coords = np.meshgrid(*[np.arange(d) for d in dims], indexing="ij")
+    return cp_values(dims, cp_factors, sigma, seed, coords)
+
+
+def sample_rows(seed: int, extent: int, count: int, tag: int = 0) -> np.ndarray:
+    """``count`` distinct output rows out of ``extent``, chosen from the seed, sorted."""
+    count = min(count, extent)
+    keys = raw(seed, STREAM_SAMPLE + tag, np.arange(extent, dtype=np.uint64))
+    return np.sort(np.argsort(keys, kind="stable")[:count]).astype(np.int64)
+
+
+def draw_int(seed: int, tag: int, lo: int, hi: int, n: int) -> np.ndarray:
+    """``n`` integers uniform on [lo, hi] (inclusive), from the workload-parameter stream."""
+    r = raw(seed, STREAM_DRAW + tag, np.arange(n, dtype=np.uint64))
+    span = np.uint64(hi - lo + 1)
+    return (r % span).astype(np.int64) + lo
