@@ -1,0 +1,205 @@
+/*
+ * deinsum.h -- C ABI of the GB300 (sm_103a) MTTKRP / TTMc library.
+ *
+ * The library computes, on one GPU, the local Einstein-summation contractions
+ * of Deinsum's two multilinear kernel classes (arXiv 2206.08301):
+ *
+ *   MTTKRP, mode n (Sec. III-B; Table IV rows MTTKRP-O3-M*, MTTKRP-O5-M*):
+ *     i_0..i_{N-1}, i_0 r, .., i_{n-1} r, i_{n+1} r, .., i_{N-1} r -> i_n r
+ *     M[i_n, r] = sum_{i_m, m != n} X[i_0..i_{N-1}] prod_{m != n} U^m[i_m, r]
+ *
+ *   TTMc, keep mode n (Sec. III-B; Table IV row TTMc-O5-M0):
+ *     i_0..i_{N-1}, i_m r_m (m != n) -> r_0 .. r_{n-1} i_n r_{n+1} .. r_{N-1}
+ *     Y = X x_0 U^0 .. x_{n-1} U^{n-1} x_{n+1} U^{n+1} .. x_{N-1} U^{N-1}
+ *
+ * Conventions shared by every entry point
+ *   - Tensors are dense and row-major (last index fastest), as in the NumPy
+ *     listings of Sec. II-A; indices are 0-based (Sec. III).
+ *   - A factor U^m is I_m x R (row-major) and is contracted on its first index,
+ *     the einsum term "i_m r".
+ *   - Every tensor pointer passed to an execute call is a DEVICE pointer owned
+ *     by the caller; the library never frees it.  Pointers to float32 data must
+ *     be 4-byte aligned, to float64 data 8-byte aligned; the vectorised load
+ *     path is taken when X is 16-byte aligned and its rows allow it, otherwise
+ *     a scalar path runs (same result).
+ *   - Outputs are overwritten (beta = 0): Listing 1 accumulates into a zeroed
+ *     output, which is the same value.
+ *   - Calls return a status and never throw or abort.  Execute calls are
+ *     asynchronous on the given stream; a failure detected on the device (a
+ *     bounded wait that gave up) is recorded in a device word and reported by
+ *     deinsum_last_device_status() after the stream has been synchronised.
+ *   - A plan may be executed on one stream at a time; concurrent executions
+ *     need separate plans.  Plans are not tied to a device until their first
+ *     execute, which allocates the plan's workspace on the current device
+ *     (so make that first call before any stream capture).
+ *   - There is no CPU fallback: without a usable sm_103a device every execute
+ *     returns DEINSUM_ERR_CUDA.
+ */
+#ifndef DEINSUM_H
+#define DEINSUM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DEINSUM_OK = 0,
+    DEINSUM_ERR_PARSE = 1,        /* malformed einsum string */
+    DEINSUM_ERR_UNSUPPORTED = 2,  /* well-formed but not an MTTKRP / TTMc pattern */
+    DEINSUM_ERR_SHAPE = 3,        /* bad extent count or value */
+    DEINSUM_ERR_DTYPE = 4,        /* dtype / precision combination not offered */
+    DEINSUM_ERR_ALIGN = 5,        /* pointer not aligned to its element size */
+    DEINSUM_ERR_OOM = 6,          /* device allocation failed */
+    DEINSUM_ERR_CUDA = 7,         /* CUDA runtime error (no device, launch failure, ...) */
+    DEINSUM_ERR_TIMEOUT = 8,      /* a device-side bounded wait gave up */
+    DEINSUM_ERR_INVALID = 9       /* NULL plan / pointer, wrong operand count, ... */
+} deinsum_status;
+
+typedef enum {
+    DEINSUM_F32 = 0,              /* IEEE binary32 tensors */
+    DEINSUM_F64 = 1               /* IEEE binary64 tensors (plain precision only) */
+} deinsum_dtype;
+
+typedef enum {
+    /* CUDA-core arithmetic in the tensor dtype (FP32 FMA or FP64 FMA). */
+    DEINSUM_PREC_PLAIN = 0,
+    /* F32 tensors only.  Each F32 operand x is split into x_hi = bf16_rn(x) and
+       x_lo = bf16_rn(x - x_hi); the four products hi*hi, hi*lo, lo*hi, lo*lo are
+       formed on the tcgen05 tensor cores with FP32 accumulation in tensor
+       memory, which recovers FP32 accuracy (about 2^-16 relative per term). */
+    DEINSUM_PREC_SPLIT_BF16 = 1
+} deinsum_prec;
+
+typedef enum {
+    DEINSUM_KIND_MTTKRP = 0,
+    DEINSUM_KIND_TTMC = 1
+} deinsum_kind;
+
+typedef struct deinsum_plan_s *deinsum_plan_t;
+
+/* A cudaStream_t passed as an opaque pointer; NULL is the legacy default stream. */
+typedef void *deinsum_stream_t;
+
+/* Plan summary (host data, filled by deinsum_plan_info). */
+typedef struct {
+    int kind;                 /* deinsum_kind */
+    int order;                /* N, the order of X (2..8) */
+    int mode;                 /* MTTKRP output mode n / TTMc kept mode n */
+    int dtype;                /* deinsum_dtype */
+    int prec;                 /* deinsum_prec */
+    int64_t dims[8];          /* I_0..I_{N-1} */
+    int64_t ranks[8];         /* R (MTTKRP: same in every mode) or R_m (TTMc); ranks[n] = I_n */
+    int64_t out_elems;        /* elements of the output */
+    double alg_bytes;         /* |X| + factor bytes + output bytes (compulsory traffic) */
+    double alg_flops;         /* 2 x multiply-adds of the FLOP-minimal binary chain */
+    int64_t n_units;          /* work units of the main kernel (0 before the first execute) */
+} deinsum_plan_info_t;
+
+/*
+ * deinsum_plan -- parse and classify an einsum, fix the kernel and its schedule.
+ *
+ *   einsum     NUL-terminated "in,in,..->out" string with explicit output, e.g.
+ *              "ijk,ja,ka->ia" (MTTKRP-O3-M0) or "ijkl,jb,kc,ld->ibcd" (TTMc).
+ *              The first operand is X (N distinct letters); every other operand
+ *              is a factor "<X letter><rank letter>".  MTTKRP: N-1 factors sharing
+ *              one rank letter, output "<kept letter><rank letter>".  TTMc: N-1
+ *              factors with distinct rank letters, output = X's letters with each
+ *              contracted letter replaced by its rank letter in place.
+ *              Anything else returns DEINSUM_ERR_UNSUPPORTED (paper Sec. III-A
+ *              semantics: repeated letters are summed, output letters kept).
+ *   extents    one positive extent per distinct letter, in order of first
+ *              appearance in `einsum` (host array of n_extents values).
+ *   dtype      tensor element type.
+ *   prec       arithmetic (see deinsum_prec); SPLIT_BF16 needs F32 and R <= 64.
+ *   out        receives the plan (host object; free with deinsum_destroy).
+ * Host only: makes no CUDA call.
+ */
+deinsum_status deinsum_plan(const char *einsum, const int64_t *extents, int n_extents,
+                            deinsum_dtype dtype, deinsum_prec prec, deinsum_plan_t *out);
+
+/*
+ * deinsum_execute -- run the planned contraction on `stream` (asynchronous).
+ *
+ *   inputs     n_inputs DEVICE pointers, one per einsum operand in string order
+ *              (inputs[0] = X, then the factors), each dense row-major in the
+ *              plan's dtype.
+ *   output     DEVICE pointer to the dense row-major output (overwritten):
+ *              MTTKRP I_n x R; TTMc with the extents of the output letters.
+ * The first call on a device allocates the plan's workspace there (cudaMalloc);
+ * later calls allocate nothing.  Returns DEINSUM_ERR_INVALID for NULL pointers
+ * or a wrong operand count, DEINSUM_ERR_ALIGN for a pointer not aligned to its
+ * element size, DEINSUM_ERR_CUDA when a launch fails.
+ */
+deinsum_status deinsum_execute(deinsum_plan_t plan, const void *const *inputs, int n_inputs,
+                               void *output, deinsum_stream_t stream);
+
+/* Bytes of device workspace the plan owns once executed (partial sums, split
+ * factor tiles, schedule table, status word).  Host only. */
+deinsum_status deinsum_workspace_size(deinsum_plan_t plan, size_t *bytes);
+
+/* Fill *info with the plan summary.  Host only. */
+deinsum_status deinsum_plan_info(deinsum_plan_t plan, deinsum_plan_info_t *info);
+
+/* Device-side status of the plan's last execute: DEINSUM_OK, or
+ * DEINSUM_ERR_TIMEOUT when a bounded wait inside a kernel gave up.  Reads one
+ * word from the device (synchronous); call after synchronising the stream. */
+deinsum_status deinsum_last_device_status(deinsum_plan_t plan);
+
+/* Free the plan and its workspace.  NULL is ignored.  The device must not be
+ * running an execute of this plan. */
+void deinsum_destroy(deinsum_plan_t plan);
+
+/* Static, human-readable name of a status code. */
+const char *deinsum_status_string(deinsum_status status);
+
+/* Number of kernels the library has launched in this process (all entry
+ * points, all devices) -- a counter for benchmarks and tests. */
+int64_t deinsum_kernel_launch_count(void);
+
+/*
+ * Benchmark support.  With timing enabled, every execute of the plan records a
+ * pair of CUDA events on its stream around the plan's main kernel (the MTTKRP
+ * contraction kernel; for TTMc the first, largest TTM).  deinsum_kernel_time
+ * waits for the recorded events, returns the summed device time (ms) and the
+ * number of recorded launches, and clears the record.  Events are created on
+ * first use and kept by the plan.  Disabled by default.
+ */
+deinsum_status deinsum_set_kernel_timing(deinsum_plan_t plan, int enable);
+deinsum_status deinsum_kernel_time(deinsum_plan_t plan, double *total_ms, int64_t *launches);
+
+/*
+ * Seeded synthetic inputs on the device.  These implement, bit for bit, the
+ * counter-based generator of the project's input module (SplitMix64 by
+ * S. Vigna: state0 = mix64(seed + stream_id * 0x9E3779B97F4A7C15), element i is
+ * mix64(state0 + (i + 1) * 0x9E3779B97F4A7C15)); they hold none of the
+ * contraction arithmetic.  `out` is a DEVICE pointer to n elements.
+ */
+
+/* out[i] = (raw_i >> 40) * 2^-23 - 1, uniform on [-1, 1) in float32. */
+deinsum_status deinsum_gen_uniform_f32(uint64_t seed, uint64_t stream_id, int64_t n,
+                                       float *out, deinsum_stream_t stream);
+
+/* out[i] = (raw_i >> 11) * 2^-52 - 1, uniform on [-1, 1) in float64. */
+deinsum_status deinsum_gen_uniform_f64(uint64_t seed, uint64_t stream_id, int64_t n,
+                                       double *out, deinsum_stream_t stream);
+
+/*
+ * Rank-`rank` CP tensor plus noise, float32, row-major with extents dims[0..order-1]:
+ *   out[idx] = f32( sum_{s<rank} prod_{m<order} A_m[i_m, s] + sigma * z(idx) )
+ * evaluated in float64 (product over m left to right, sum over s left to right,
+ * no fused multiply-add), z(idx) = (sum of the four 16-bit lanes of raw(idx) - 2^17) * sqrt(3) * 2^-16 on stream 2 under `seed`.
+ * `factors` is a HOST array of `order` DEVICE pointers to float64 I_m x rank
+ * matrices.  order <= 8.
+ */
+deinsum_status deinsum_gen_cp_f32(uint64_t seed, int order, const int64_t *dims, int rank,
+                                  const double *const *factors, double sigma, float *out,
+                                  deinsum_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEINSUM_H */

@@ -1,0 +1,288 @@
+"""GB300 (sm_103a) MTTKRP / TTMc library -- Python binding of ``libdeinsum.so``.
+
+A thin ctypes layer over the C ABI declared in ``include/deinsum.h``: it
+marshals torch CUDA tensors into device pointers and streams and returns
+status codes as exceptions.  Every step of the computation runs in the
+library's CUDA kernels; there is no host or PyTorch fallback, and importing a
+compute entry point without the built library raises.
+
+Entry points mirror the C names: ``Plan`` (deinsum_plan / deinsum_execute /
+deinsum_plan_info / deinsum_workspace_size / deinsum_last_device_status /
+deinsum_destroy), ``gen_uniform`` / ``gen_cp`` (the seeded device generators)
+and ``kernel_launch_count``; ``mttkrp`` / ``ttmc`` build the einsum string of
+the paper's Table IV pattern for a given tensor and factor list.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = ["DeinsumError", "Plan", "mttkrp", "ttmc", "mttkrp_einsum", "ttmc_einsum",
+           "gen_uniform", "gen_cp", "kernel_launch_count", "library_path", "load"]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libdeinsum.so")
+_lib = None
+_lock = threading.Lock()
+
+STATUS = {0: "ok", 1: "parse", 2: "unsupported", 3: "shape", 4: "dtype", 5: "align", 6: "oom",
+          7: "cuda", 8: "timeout", 9: "invalid"}
+DTYPES = {"float32": 0, "f32": 0, "float64": 1, "f64": 1}
+PRECS = {"plain": 0, "split_bf16": 1}
+KINDS = {0: "mttkrp", 1: "ttmc"}
+
+
+class DeinsumError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        name = STATUS.get(status, str(status))
+        msg = _lib.deinsum_status_string(status).decode() if _lib is not None else name
+        super().__init__(f"{what}: {name} ({msg})" if what else f"{name} ({msg})")
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("order", ctypes.c_int), ("mode", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("prec", ctypes.c_int),
+                ("dims", ctypes.c_int64 * 8), ("ranks", ctypes.c_int64 * 8),
+                ("out_elems", ctypes.c_int64), ("alg_bytes", ctypes.c_double),
+                ("alg_flops", ctypes.c_double), ("n_units", ctypes.c_int64)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load ``libdeinsum.so`` (built in-tree by ``build.build()``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is not built; run paper_2206_08301_gb300.build.build() "
+                              "(or __graft_entry__.build()) first -- there is no fallback path")
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        lib.deinsum_plan.argtypes = [ctypes.c_char_p, ctypes.POINTER(i64), i32, i32, i32, ctypes.POINTER(vp)]
+        lib.deinsum_plan.restype = i32
+        lib.deinsum_execute.argtypes = [vp, ctypes.POINTER(vp), i32, vp, vp]
+        lib.deinsum_execute.restype = i32
+        lib.deinsum_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        lib.deinsum_workspace_size.restype = i32
+        lib.deinsum_plan_info.argtypes = [vp, ctypes.POINTER(_PlanInfo)]
+        lib.deinsum_plan_info.restype = i32
+        lib.deinsum_last_device_status.argtypes = [vp]
+        lib.deinsum_last_device_status.restype = i32
+        lib.deinsum_destroy.argtypes = [vp]
+        lib.deinsum_destroy.restype = None
+        lib.deinsum_status_string.argtypes = [i32]
+        lib.deinsum_status_string.restype = ctypes.c_char_p
+        lib.deinsum_kernel_launch_count.argtypes = []
+        lib.deinsum_kernel_launch_count.restype = i64
+        lib.deinsum_set_kernel_timing.argtypes = [vp, i32]
+        lib.deinsum_set_kernel_timing.restype = i32
+        lib.deinsum_kernel_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        lib.deinsum_kernel_time.restype = i32
+        lib.deinsum_gen_uniform_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, vp, vp]
+        lib.deinsum_gen_uniform_f32.restype = i32
+        lib.deinsum_gen_uniform_f64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, vp, vp]
+        lib.deinsum_gen_uniform_f64.restype = i32
+        lib.deinsum_gen_cp_f32.argtypes = [ctypes.c_uint64, i32, ctypes.POINTER(i64), i32,
+                                           ctypes.POINTER(vp), ctypes.c_double, vp, vp]
+        lib.deinsum_gen_cp_f32.restype = i32
+        _lib = lib
+        return lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise DeinsumError(status, what)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch.Tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (dense row-major)")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A planned MTTKRP / TTMc contraction (``deinsum_plan``).
+
+    ``extents`` maps every einsum letter to its extent (dict), or lists the
+    extents in order of first appearance in ``einsum``.
+    """
+
+    def __init__(self, einsum: str, extents, dtype: str = "float32", prec: str = "plain"):
+        lib = load()
+        letters = []
+        for c in einsum.replace(" ", ""):
+            if c.isalpha() and c not in letters:
+                letters.append(c)
+        if isinstance(extents, dict):
+            ext = [int(extents[c]) for c in letters]
+        else:
+            ext = [int(e) for e in extents]
+        self.einsum = einsum
+        self.letters = letters
+        self.extents = dict(zip(letters, ext))
+        arr = (ctypes.c_int64 * len(ext))(*ext)
+        h = ctypes.c_void_p()
+        _check(lib.deinsum_plan(einsum.encode(), arr, len(ext), DTYPES[dtype], PRECS[prec], ctypes.byref(h)),
+               f"deinsum_plan({einsum!r})")
+        self._h = h
+        self.dtype = dtype
+        self.prec = prec
+        info = _PlanInfo()
+        _check(lib.deinsum_plan_info(self._h, ctypes.byref(info)), "deinsum_plan_info")
+        self.kind = KINDS[info.kind]
+        self.order = info.order
+        self.mode = info.mode
+        out = einsum.replace(" ", "").split("->")[1]
+        self.out_shape = tuple(self.extents[c] for c in out)
+
+    def info(self) -> dict:
+        info = _PlanInfo()
+        _check(load().deinsum_plan_info(self._h, ctypes.byref(info)), "deinsum_plan_info")
+        return {"kind": KINDS[info.kind], "order": info.order, "mode": info.mode,
+                "dims": list(info.dims[:info.order]), "ranks": list(info.ranks[:info.order]),
+                "out_elems": info.out_elems, "alg_bytes": info.alg_bytes, "alg_flops": info.alg_flops,
+                "n_units": info.n_units}
+
+    def workspace_size(self) -> int:
+        n = ctypes.c_size_t()
+        _check(load().deinsum_workspace_size(self._h, ctypes.byref(n)), "deinsum_workspace_size")
+        return int(n.value)
+
+    def set_kernel_timing(self, enable: bool = True):
+        _check(load().deinsum_set_kernel_timing(self._h, int(bool(enable))), "deinsum_set_kernel_timing")
+
+    def kernel_time(self):
+        """(summed device ms, launches) of the main kernel since the last call (timing enabled)."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(load().deinsum_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)), "deinsum_kernel_time")
+        return float(ms.value), int(n.value)
+
+    def last_device_status(self) -> int:
+        return int(load().deinsum_last_device_status(self._h))
+
+    def __call__(self, *operands, out=None, stream=None):
+        import torch
+        lib = load()
+        want = torch.float64 if self.dtype in ("float64", "f64") else torch.float32
+        ptrs = (ctypes.c_void_p * len(operands))()
+        for k, t in enumerate(operands):
+            if t.dtype != want:
+                raise TypeError(f"operand {k} has dtype {t.dtype}, plan expects {want}")
+            ptrs[k] = _dev_ptr(t, f"operand {k}")
+        if out is None:
+            out = torch.empty(self.out_shape, dtype=want, device=operands[0].device)
+        elif tuple(out.shape) != self.out_shape or out.dtype != want:
+            raise ValueError("out has the wrong shape or dtype")
+        _check(lib.deinsum_execute(self._h, ptrs, len(operands), _dev_ptr(out, "out"), _stream_ptr(stream)),
+               "deinsum_execute")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.deinsum_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_XL = "abcdefgh"
+_RL = "stuvwxyz"
+
+
+def mttkrp_einsum(order: int, mode: int) -> str:
+    """The MTTKRP einsum of Sec. III-B / Table IV for an order-``order`` tensor, mode ``mode``."""
+    x = _XL[:order]
+    fac = [x[m] + "r" for m in range(order) if m != mode]
+    return ",".join([x] + fac) + "->" + x[mode] + "r"
+
+
+def ttmc_einsum(order: int, keep: int) -> str:
+    """The TTMc einsum (Sec. III-B / Table IV) keeping mode ``keep``."""
+    x = _XL[:order]
+    fac = [x[m] + _RL[m] for m in range(order) if m != keep]
+    out = "".join(x[m] if m == keep else _RL[m] for m in range(order))
+    return ",".join([x] + fac) + "->" + out
+
+
+_plan_cache: dict = {}
+
+
+def _cached_plan(einsum, extents, dtype, prec):
+    key = (einsum, tuple(extents), dtype, prec)
+    p = _plan_cache.get(key)
+    if p is None:
+        p = Plan(einsum, list(extents), dtype, prec)
+        _plan_cache[key] = p
+    return p
+
+
+def mttkrp(X, factors, mode: int, prec: str = "plain", out=None, stream=None):
+    """Mode-``mode`` MTTKRP of X with ``factors`` (``factors[mode]`` is ignored)."""
+    import torch
+    order = X.dim()
+    R = next(f.shape[1] for m, f in enumerate(factors) if m != mode)
+    spec = mttkrp_einsum(order, mode)
+    extents = list(X.shape) + [R]
+    dtype = "float64" if X.dtype == torch.float64 else "float32"
+    plan = _cached_plan(spec, extents, dtype, prec)
+    return plan(X, *[factors[m] for m in range(order) if m != mode], out=out, stream=stream)
+
+
+def ttmc(X, factors, keep: int, prec: str = "plain", out=None, stream=None):
+    """TTMc of X keeping mode ``keep``; every other mode m is contracted with ``factors[m]``."""
+    import torch
+    order = X.dim()
+    spec = ttmc_einsum(order, keep)
+    extents = list(X.shape) + [factors[m].shape[1] for m in range(order) if m != keep]
+    dtype = "float64" if X.dtype == torch.float64 else "float32"
+    plan = _cached_plan(spec, extents, dtype, prec)
+    return plan(X, *[factors[m] for m in range(order) if m != keep], out=out, stream=stream)
+
+
+def gen_uniform(seed: int, stream_id: int, shape, dtype=None, device="cuda", stream=None):
+    """Device tensor of the seeded uniform[-1, 1) stream (float32 or float64)."""
+    import torch
+    dtype = dtype or torch.float32
+    t = torch.empty(tuple(shape), dtype=dtype, device=device)
+    lib = load()
+    fn = lib.deinsum_gen_uniform_f64 if dtype == torch.float64 else lib.deinsum_gen_uniform_f32
+    _check(fn(seed, stream_id, t.numel(), _dev_ptr(t, "out"), _stream_ptr(stream)), "deinsum_gen_uniform")
+    return t
+
+
+def gen_cp(seed: int, dims, cp_factors, sigma: float, device="cuda", stream=None):
+    """Device float32 CP-plus-noise tensor; ``cp_factors`` are float64 CUDA tensors (I_m x rank)."""
+    import torch
+    order = len(dims)
+    t = torch.empty(tuple(dims), dtype=torch.float32, device=device)
+    d = (ctypes.c_int64 * order)(*[int(x) for x in dims])
+    fp = (ctypes.c_void_p * order)(*[_dev_ptr(f, "cp factor").value for f in cp_factors])
+    rank = int(cp_factors[0].shape[1])
+    _check(load().deinsum_gen_cp_f32(seed, order, d, rank, fp, float(sigma), _dev_ptr(t, "out"),
+                                     _stream_ptr(stream)), "deinsum_gen_cp_f32")
+    return t
+
+
+def kernel_launch_count() -> int:
+    """Kernels the library has launched in this process (all entry points)."""
+    return int(load().deinsum_kernel_launch_count())

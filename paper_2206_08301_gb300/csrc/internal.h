@@ -1,0 +1,95 @@
+// Internal declarations shared by the library's translation units.
+//
+// The MTTKRP kernels see X through one "row view" (see MttkrpGeom).  For
+// mode n of an order-N tensor, with P = prod_{m<n} I_m and Q = prod_{m>n} I_m:
+//
+//   case 0 (n < N-1, "K-contiguous"): a row is a (p, i_n) pair; its elements
+//     run over q = (o, k), where k indexes the last mode I_{N-1} (the "inner"
+//     mode contracted on the tensor cores, stride 1 in memory) and o the modes
+//     n+1..N-2 ("outer" modes).  Rows are grouped 128 to a tile: one p and 128
+//     consecutive i_n when I_n >= 128 ("wide"), else G = floor(128/I_n)
+//     consecutive p with all I_n rows each ("narrow").
+//   case 1 (n = N-1, "M-contiguous"): a row is one i_n; its elements run over
+//     p = (o, k) with k indexing mode N-2 (inner) and o modes 0..N-3 (outer);
+//     consecutive rows are adjacent in memory.
+//
+// The inner contraction over k runs in chunks of 64 (BK).  For a fixed tile
+// and outer index o ("fiber group"), the chunks are accumulated into
+// T[row, r] = sum_k X[row, (o, k)] U_inner[k, r]; the fiber group is then
+// folded into the row's accumulator with the weight
+//   w[row, r] = L(p(row))[r] * Ofac(o)[r],
+//   L(p) = prod_{m<n} U^m[i_m(p), r]   (case 0 only),  Ofac(o) = prod_{outer m} U^m[i_m(o), r].
+// This is the MTTKRP sum regrouped by distributivity (Sec. III-B einsum).
+//
+// Work is split into units = (column of 128 output rows, range of fiber
+// groups); every unit writes its own 128 x R_pad block of partial sums and a
+// reduction kernel adds the blocks of each column in unit order, so results do
+// not depend on which CTA ran which unit.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/deinsum.h"
+
+#define DEINSUM_MAX_ORDER 8
+#define DEINSUM_BM 128
+#define DEINSUM_BK 64
+
+namespace deinsum {
+
+struct MttkrpGeom {
+    int order;
+    int mode;
+    int kcase;            // 0: K-contiguous rows, 1: M-contiguous rows (mode == order-1)
+    int narrow;           // case 0 with I < 128
+    int R;                // rank
+    int R_pad;            // rank padded for the kernels (16, 32 or 64)
+    int n_kb;             // ceil(K_in / 64)
+    int n_outer;          // number of outer modes
+    int n_lmodes;         // case 0: modes 0..mode-1 (weights L); case 1: 0
+    int vec_ok;           // rows allow 16-byte vector loads (checked with the X pointer)
+    int64_t dims[DEINSUM_MAX_ORDER];
+    int64_t P, I, Q;
+    int64_t K_in;         // extent of the inner mode
+    int64_t O;            // product of outer extents (1 if none)
+    int outer_mode[DEINSUM_MAX_ORDER];
+    int64_t outer_dim[DEINSUM_MAX_ORDER];
+    int64_t G;            // narrow: p values per tile (else 1)
+    int64_t n_cols;       // columns of 128 output rows (narrow: 1)
+    int64_t tiles_per_col;
+    int64_t fg_per_col;   // tiles_per_col * O
+    int64_t rows_per_col; // min(I, 128)
+};
+
+struct MttkrpArgs {
+    MttkrpGeom g;
+    const void *X;
+    const void *U[DEINSUM_MAX_ORDER];  // factor of each mode (U[mode] unused)
+    const void *Bsplit;                // split-BF16 tiles of the inner factor (TC path)
+    const int64_t *units;              // n_units x 3: column, first fiber group, end
+    int64_t n_units;
+    float *partial;                    // n_units x 128 x R_pad (F32 paths)
+    double *partial64;                 // n_units x 128 x R_pad (F64 path)
+    int *status;                       // device status word
+};
+
+// Launch helpers implemented in the .cu files.  They return a CUDA error code
+// (0 on success) and increment the library's launch counter.
+int launch_mttkrp_plain_f32(const MttkrpArgs &a, int n_sm, void *stream);
+int launch_mttkrp_plain_f64(const MttkrpArgs &a, int n_sm, void *stream);
+int launch_mttkrp_tc(const MttkrpArgs &a, int n_sm, void *stream);
+int launch_split_inner_factor(const MttkrpArgs &a, void *bsplit, void *stream);
+int launch_mttkrp_reduce_f32(const MttkrpArgs &a, const int64_t *col_unit_begin, void *out, void *stream);
+int launch_mttkrp_reduce_f64(const MttkrpArgs &a, const int64_t *col_unit_begin, void *out, void *stream);
+size_t mttkrp_tc_smem_bytes(int R_pad);
+
+// Plain TTM on a (A, Im, B) view: Y[a, r, b] = sum_i X[a, i, b] U[i, r].
+int launch_ttm_plain_f32(const float *X, const float *U, float *Y, int64_t A, int64_t Im,
+                         int64_t B, int64_t Rm, void *stream);
+int launch_ttm_plain_f64(const double *X, const double *U, double *Y, int64_t A, int64_t Im,
+                         int64_t B, int64_t Rm, void *stream);
+
+void count_launch(int n = 1);
+
+}  // namespace deinsum

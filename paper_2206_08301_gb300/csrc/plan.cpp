@@ -1,0 +1,616 @@
+// Host side of the C ABI: einsum parsing and classification, the MTTKRP row
+// view and work schedule, the plan's device workspace, and dispatch of the
+// kernels.  Parsing follows the Einstein-notation rules of Sec. III-A
+// (letters repeated across operands are summed, output letters are kept); the
+// accepted patterns are the MTTKRP and TTMc einsums of Sec. III-B / Table IV.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace deinsum;
+
+namespace deinsum {
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace deinsum
+
+struct deinsum_plan_s {
+    deinsum_kind kind = DEINSUM_KIND_MTTKRP;
+    int order = 0;
+    int mode = 0;
+    deinsum_dtype dtype = DEINSUM_F32;
+    deinsum_prec prec = DEINSUM_PREC_PLAIN;
+    int64_t dims[DEINSUM_MAX_ORDER] = {0};
+    int64_t ranks[DEINSUM_MAX_ORDER] = {0};
+    int n_operands = 0;
+    int operand_mode[DEINSUM_MAX_ORDER + 1] = {0};  // operand k >= 1 -> mode of X
+
+    // MTTKRP
+    MttkrpGeom geom{};
+    std::vector<int64_t> units;           // 3 per unit
+    std::vector<int64_t> col_unit_begin;  // n_cols + 1
+    int64_t planned_units = 0;
+
+    // TTMc: contraction order and intermediate sizes
+    std::vector<int> ttm_order;
+    int64_t ttm_buf_elems = 0;
+
+    // device state (after the first execute)
+    int device = -1;
+    int n_sm = 0;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t *d_units = nullptr;
+    int64_t *d_col_begin = nullptr;
+    void *d_partial = nullptr;
+    void *d_bsplit = nullptr;
+    int *d_status = nullptr;
+    void *d_ttm[2] = {nullptr, nullptr};
+
+    // benchmark timing of the main kernel
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    size_t ev_used = 0;
+};
+
+namespace {
+
+// Record the start event of the main kernel (timing enabled only); returns the pair index or -1.
+long timing_begin(deinsum_plan_s *pl, void *stream) {
+    if (!pl->timing) return -1;
+    if (pl->ev_used == pl->ev_pool.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return -1;
+        if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
+        pl->ev_pool.emplace_back(a, b);
+    }
+    cudaEventRecord(pl->ev_pool[pl->ev_used].first, static_cast<cudaStream_t>(stream));
+    return long(pl->ev_used++);
+}
+
+void timing_end(deinsum_plan_s *pl, long idx, void *stream) {
+    if (idx >= 0) cudaEventRecord(pl->ev_pool[size_t(idx)].second, static_cast<cudaStream_t>(stream));
+}
+
+bool is_letter(char c) { return (c >= 'a' && c <= 'z') || (c >= 'A' && c <= 'Z'); }
+
+struct Parsed {
+    std::vector<std::string> ins;
+    std::string out;
+    std::vector<char> letters;  // distinct, in order of first appearance
+};
+
+deinsum_status parse(const char *s, Parsed &p) {
+    if (!s) return DEINSUM_ERR_INVALID;
+    std::string str;
+    for (const char *c = s; *c; ++c)
+        if (*c != ' ') str.push_back(*c);
+    size_t arrow = str.find("->");
+    if (arrow == std::string::npos || str.find("->", arrow + 2) != std::string::npos)
+        return DEINSUM_ERR_PARSE;
+    std::string lhs = str.substr(0, arrow);
+    p.out = str.substr(arrow + 2);
+    size_t start = 0;
+    while (true) {
+        size_t comma = lhs.find(',', start);
+        std::string t = lhs.substr(start, comma == std::string::npos ? std::string::npos : comma - start);
+        if (t.empty()) return DEINSUM_ERR_PARSE;
+        p.ins.push_back(t);
+        if (comma == std::string::npos) break;
+        start = comma + 1;
+    }
+    auto add = [&](const std::string &t) -> bool {
+        for (char c : t) {
+            if (!is_letter(c)) return false;
+            if (std::find(p.letters.begin(), p.letters.end(), c) == p.letters.end()) p.letters.push_back(c);
+        }
+        return true;
+    };
+    for (auto &t : p.ins)
+        if (!add(t)) return DEINSUM_ERR_PARSE;
+    if (p.out.empty() || !add(p.out)) return DEINSUM_ERR_PARSE;
+    // an output letter must appear in some input (Sec. III-A)
+    for (char c : p.out) {
+        bool found = false;
+        for (auto &t : p.ins)
+            if (t.find(c) != std::string::npos) found = true;
+        if (!found) return DEINSUM_ERR_UNSUPPORTED;
+    }
+    return DEINSUM_OK;
+}
+
+int letter_index(const Parsed &p, char c) {
+    return int(std::find(p.letters.begin(), p.letters.end(), c) - p.letters.begin());
+}
+
+int pad_rank(int R) { return R <= 16 ? 16 : (R <= 32 ? 32 : 64); }
+
+// The row view and schedule of the MTTKRP kernels (see internal.h).
+void build_mttkrp_geometry(deinsum_plan_s *pl) {
+    MttkrpGeom &g = pl->geom;
+    std::memset(&g, 0, sizeof(g));
+    const int N = pl->order, n = pl->mode;
+    g.order = N;
+    g.mode = n;
+    g.R = int(pl->ranks[(n + 1) % N]);
+    g.R_pad = pad_rank(g.R);
+    for (int m = 0; m < N; ++m) g.dims[m] = pl->dims[m];
+    g.P = 1;
+    g.Q = 1;
+    for (int m = 0; m < n; ++m) g.P *= g.dims[m];
+    for (int m = n + 1; m < N; ++m) g.Q *= g.dims[m];
+    g.I = g.dims[n];
+    g.kcase = (n == N - 1) ? 1 : 0;
+    if (g.kcase == 0) {
+        g.K_in = g.dims[N - 1];
+        for (int m = n + 1; m < N - 1; ++m) {
+            g.outer_mode[g.n_outer] = m;
+            g.outer_dim[g.n_outer] = g.dims[m];
+            ++g.n_outer;
+        }
+        g.n_lmodes = n;
+        g.narrow = g.I < DEINSUM_BM ? 1 : 0;
+        if (g.narrow) {
+            g.G = std::max<int64_t>(1, std::min<int64_t>(DEINSUM_BM / g.I, g.P));
+            g.n_cols = 1;
+            g.tiles_per_col = (g.P + g.G - 1) / g.G;
+            g.rows_per_col = g.I;
+        } else {
+            g.G = 1;
+            g.n_cols = (g.I + DEINSUM_BM - 1) / DEINSUM_BM;
+            g.tiles_per_col = g.P;
+            g.rows_per_col = DEINSUM_BM;
+        }
+        g.vec_ok = (g.K_in % 4 == 0) ? 1 : 0;
+    } else {
+        g.K_in = g.dims[N - 2];
+        for (int m = 0; m < N - 2; ++m) {
+            g.outer_mode[g.n_outer] = m;
+            g.outer_dim[g.n_outer] = g.dims[m];
+            ++g.n_outer;
+        }
+        g.n_lmodes = 0;
+        g.narrow = 0;
+        g.G = 1;
+        g.n_cols = (g.I + DEINSUM_BM - 1) / DEINSUM_BM;
+        g.tiles_per_col = 1;
+        g.rows_per_col = std::min<int64_t>(g.I, DEINSUM_BM);
+        g.vec_ok = (g.I % 4 == 0) ? 1 : 0;
+    }
+    g.O = 1;
+    for (int k = 0; k < g.n_outer; ++k) g.O *= g.outer_dim[k];
+    g.n_kb = int((g.K_in + DEINSUM_BK - 1) / DEINSUM_BK);
+    g.fg_per_col = g.tiles_per_col * g.O;
+}
+
+// Split every column's fiber groups into contiguous units, about `target`
+// units in all, so that a persistent grid of `target` CTAs is balanced.
+void build_schedule(deinsum_plan_s *pl, int64_t target) {
+    const MttkrpGeom &g = pl->geom;
+    pl->units.clear();
+    pl->col_unit_begin.assign(size_t(g.n_cols + 1), 0);
+    int64_t per_col = std::max<int64_t>(1, (target + g.n_cols - 1) / g.n_cols);
+    per_col = std::min<int64_t>(per_col, g.fg_per_col);
+    for (int64_t c = 0; c < g.n_cols; ++c) {
+        pl->col_unit_begin[size_t(c)] = int64_t(pl->units.size() / 3);
+        for (int64_t s = 0; s < per_col; ++s) {
+            int64_t f0 = g.fg_per_col * s / per_col;
+            int64_t f1 = g.fg_per_col * (s + 1) / per_col;
+            if (f1 <= f0) continue;
+            pl->units.push_back(c);
+            pl->units.push_back(f0);
+            pl->units.push_back(f1);
+        }
+    }
+    pl->col_unit_begin[size_t(g.n_cols)] = int64_t(pl->units.size() / 3);
+    pl->planned_units = int64_t(pl->units.size() / 3);
+}
+
+size_t elem_size(deinsum_dtype d) { return d == DEINSUM_F64 ? 8 : 4; }
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+deinsum_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return DEINSUM_OK;
+    if (e == cudaErrorMemoryAllocation) return DEINSUM_ERR_OOM;
+    return DEINSUM_ERR_CUDA;
+}
+
+// Allocate the workspace on the current device and upload the schedule.
+deinsum_status ensure_device_state(deinsum_plan_s *pl) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return DEINSUM_ERR_CUDA;
+    if (pl->ws && pl->device == dev) return DEINSUM_OK;
+    if (pl->ws) return DEINSUM_ERR_INVALID;  // a plan stays on its first device
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return DEINSUM_ERR_CUDA;
+    pl->device = dev;
+    pl->n_sm = nsm;
+
+    size_t off = 0;
+    size_t o_units = 0, o_cols = 0, o_partial = 0, o_bsplit = 0, o_ttm0 = 0, o_ttm1 = 0;
+    size_t o_status = off;
+    off = align_up(off + 256, 256);
+    if (pl->kind == DEINSUM_KIND_MTTKRP) {
+        build_schedule(pl, nsm);
+        const MttkrpGeom &g = pl->geom;
+        o_units = off;
+        off = align_up(off + pl->units.size() * sizeof(int64_t), 256);
+        o_cols = off;
+        off = align_up(off + pl->col_unit_begin.size() * sizeof(int64_t), 256);
+        o_partial = off;
+        off = align_up(off + size_t(pl->planned_units) * DEINSUM_BM * g.R_pad * elem_size(pl->dtype), 1024);
+        if (pl->prec == DEINSUM_PREC_SPLIT_BF16) {
+            o_bsplit = off;
+            off = align_up(off + size_t(g.n_kb) * 2 * g.R_pad * DEINSUM_BK * 2, 1024);
+        }
+    } else {
+        o_ttm0 = off;
+        off = align_up(off + size_t(pl->ttm_buf_elems) * elem_size(pl->dtype), 256);
+        o_ttm1 = off;
+        off = align_up(off + size_t(pl->ttm_buf_elems) * elem_size(pl->dtype), 256);
+    }
+    void *ws = nullptr;
+    e = cudaMalloc(&ws, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    pl->ws = static_cast<char *>(ws);
+    pl->ws_bytes = off;
+    pl->d_status = reinterpret_cast<int *>(pl->ws + o_status);
+    e = cudaMemset(pl->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_status(e);
+    if (pl->kind == DEINSUM_KIND_MTTKRP) {
+        pl->d_units = reinterpret_cast<int64_t *>(pl->ws + o_units);
+        pl->d_col_begin = reinterpret_cast<int64_t *>(pl->ws + o_cols);
+        pl->d_partial = pl->ws + o_partial;
+        pl->d_bsplit = pl->prec == DEINSUM_PREC_SPLIT_BF16 ? pl->ws + o_bsplit : nullptr;
+        e = cudaMemcpy(pl->d_units, pl->units.data(), pl->units.size() * sizeof(int64_t),
+                       cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(pl->d_col_begin, pl->col_unit_begin.data(),
+                           pl->col_unit_begin.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_status(e);
+    } else {
+        pl->d_ttm[0] = pl->ws + o_ttm0;
+        pl->d_ttm[1] = pl->ws + o_ttm1;
+    }
+    return DEINSUM_OK;
+}
+
+deinsum_status classify(deinsum_plan_s *pl, const Parsed &p, const int64_t *extents) {
+    const std::string &x = p.ins[0];
+    const int N = int(x.size());
+    if (N < 2 || N > DEINSUM_MAX_ORDER) return DEINSUM_ERR_UNSUPPORTED;
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b)
+            if (x[a] == x[b]) return DEINSUM_ERR_UNSUPPORTED;  // diagonal access of X
+    if (int(p.ins.size()) != N) return DEINSUM_ERR_UNSUPPORTED;
+    pl->order = N;
+    pl->n_operands = N;
+    for (int m = 0; m < N; ++m) pl->dims[m] = extents[letter_index(p, x[m])];
+    std::vector<int> used(size_t(N), 0);
+    std::vector<char> rank_letter(size_t(N), 0);
+    for (int k = 1; k < N; ++k) {
+        const std::string &f = p.ins[size_t(k)];
+        if (f.size() != 2) return DEINSUM_ERR_UNSUPPORTED;
+        size_t pos = x.find(f[0]);
+        if (pos == std::string::npos || x.find(f[1]) != std::string::npos || f[0] == f[1])
+            return DEINSUM_ERR_UNSUPPORTED;
+        if (used[pos]) return DEINSUM_ERR_UNSUPPORTED;
+        used[pos] = 1;
+        pl->operand_mode[k] = int(pos);
+        rank_letter[pos] = f[1];
+    }
+    int kept = -1;
+    for (int m = 0; m < N; ++m)
+        if (!used[size_t(m)]) kept = m;
+    pl->mode = kept;
+    // MTTKRP: every factor shares one rank letter; output = kept letter + rank letter.
+    bool same_rank = true;
+    char r0 = rank_letter[size_t((kept + 1) % N)];
+    for (int m = 0; m < N; ++m)
+        if (m != kept && rank_letter[size_t(m)] != r0) same_rank = false;
+    if (same_rank && p.out.size() == 2 && p.out[0] == x[size_t(kept)] && p.out[1] == r0) {
+        pl->kind = DEINSUM_KIND_MTTKRP;
+        int64_t R = extents[letter_index(p, r0)];
+        for (int m = 0; m < N; ++m) pl->ranks[m] = (m == kept) ? pl->dims[m] : R;
+        return DEINSUM_OK;
+    }
+    // TTMc: distinct rank letters, output = X letters with contracted ones replaced in place.
+    if (int(p.out.size()) != N) return DEINSUM_ERR_UNSUPPORTED;
+    for (int a = 0; a < N; ++a)
+        for (int b = a + 1; b < N; ++b)
+            if (a != kept && b != kept && rank_letter[size_t(a)] == rank_letter[size_t(b)])
+                return DEINSUM_ERR_UNSUPPORTED;
+    for (int m = 0; m < N; ++m) {
+        char want = (m == kept) ? x[size_t(m)] : rank_letter[size_t(m)];
+        if (p.out[size_t(m)] != want) return DEINSUM_ERR_UNSUPPORTED;
+    }
+    pl->kind = DEINSUM_KIND_TTMC;
+    for (int m = 0; m < N; ++m)
+        pl->ranks[m] = (m == kept) ? pl->dims[m] : extents[letter_index(p, rank_letter[size_t(m)])];
+    return DEINSUM_OK;
+}
+
+// TTMc chain order: contract first the mode with the smallest ratio R_m / I_m
+// (largest shrink of the running tensor), which minimises the FLOPs of the
+// binary chain (Sec. II-A / IV-C); ties go to the later mode.
+void plan_ttmc_chain(deinsum_plan_s *pl) {
+    std::vector<int> modes;
+    for (int m = 0; m < pl->order; ++m)
+        if (m != pl->mode) modes.push_back(m);
+    std::stable_sort(modes.begin(), modes.end(), [&](int a, int b) {
+        double ra = double(pl->ranks[a]) / double(pl->dims[a]);
+        double rb = double(pl->ranks[b]) / double(pl->dims[b]);
+        if (ra != rb) return ra < rb;
+        return a > b;
+    });
+    pl->ttm_order = modes;
+    int64_t cur[DEINSUM_MAX_ORDER];
+    for (int m = 0; m < pl->order; ++m) cur[m] = pl->dims[m];
+    int64_t mx = 0;
+    for (size_t s = 0; s + 1 < modes.size(); ++s) {
+        cur[modes[s]] = pl->ranks[modes[s]];
+        int64_t sz = 1;
+        for (int m = 0; m < pl->order; ++m) sz *= cur[m];
+        mx = std::max(mx, sz);
+    }
+    pl->ttm_buf_elems = std::max<int64_t>(mx, 1);
+}
+
+double alg_flops(const deinsum_plan_s *pl) {
+    double x = 1.0;
+    for (int m = 0; m < pl->order; ++m) x *= double(pl->dims[m]);
+    if (pl->kind == DEINSUM_KIND_MTTKRP) return 2.0 * x * double(pl->ranks[(pl->mode + 1) % pl->order]);
+    double cur[DEINSUM_MAX_ORDER];
+    for (int m = 0; m < pl->order; ++m) cur[m] = double(pl->dims[m]);
+    double f = 0.0;
+    for (int m : pl->ttm_order) {
+        double sz = 1.0;
+        for (int k = 0; k < pl->order; ++k) sz *= cur[k];
+        f += 2.0 * sz * double(pl->ranks[m]);
+        cur[m] = double(pl->ranks[m]);
+    }
+    return f;
+}
+
+double alg_bytes(const deinsum_plan_s *pl) {
+    double es = double(elem_size(pl->dtype));
+    double x = 1.0, fac = 0.0, out = 1.0;
+    for (int m = 0; m < pl->order; ++m) {
+        x *= double(pl->dims[m]);
+        if (m != pl->mode) fac += double(pl->dims[m]) * double(pl->ranks[m]);
+    }
+    if (pl->kind == DEINSUM_KIND_MTTKRP)
+        out = double(pl->dims[pl->mode]) * double(pl->ranks[(pl->mode + 1) % pl->order]);
+    else
+        for (int m = 0; m < pl->order; ++m) out *= double(pl->ranks[m]);
+    return es * (x + fac + out);
+}
+
+deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, void *output, void *stream) {
+    MttkrpArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = pl->geom;
+    a.X = inputs[0];
+    for (int k = 1; k < pl->n_operands; ++k) a.U[pl->operand_mode[k]] = inputs[k];
+    a.units = pl->d_units;
+    a.n_units = pl->planned_units;
+    a.status = pl->d_status;
+    if ((reinterpret_cast<uintptr_t>(a.X) & 15) != 0) a.g.vec_ok = 0;
+    int err = 0;
+    if (pl->dtype == DEINSUM_F64) {
+        a.partial64 = static_cast<double *>(pl->d_partial);
+        const long ti = timing_begin(pl, stream);
+        err = launch_mttkrp_plain_f64(a, pl->n_sm, stream);
+        timing_end(pl, ti, stream);
+        if (!err) err = launch_mttkrp_reduce_f64(a, pl->d_col_begin, output, stream);
+    } else {
+        a.partial = static_cast<float *>(pl->d_partial);
+        if (pl->prec == DEINSUM_PREC_SPLIT_BF16) {
+            a.Bsplit = pl->d_bsplit;
+            err = launch_split_inner_factor(a, pl->d_bsplit, stream);
+            const long ti = timing_begin(pl, stream);
+            if (!err) err = launch_mttkrp_tc(a, pl->n_sm, stream);
+            timing_end(pl, ti, stream);
+        } else {
+            const long ti = timing_begin(pl, stream);
+            err = launch_mttkrp_plain_f32(a, pl->n_sm, stream);
+            timing_end(pl, ti, stream);
+        }
+        if (!err) err = launch_mttkrp_reduce_f32(a, pl->d_col_begin, output, stream);
+    }
+    return err ? DEINSUM_ERR_CUDA : DEINSUM_OK;
+}
+
+deinsum_status execute_ttmc(deinsum_plan_s *pl, const void *const *inputs, void *output, void *stream) {
+    const void *U[DEINSUM_MAX_ORDER] = {nullptr};
+    for (int k = 1; k < pl->n_operands; ++k) U[pl->operand_mode[k]] = inputs[k];
+    int64_t cur[DEINSUM_MAX_ORDER];
+    for (int m = 0; m < pl->order; ++m) cur[m] = pl->dims[m];
+    const void *src = inputs[0];
+    int err = 0;
+    for (size_t s = 0; s < pl->ttm_order.size() && !err; ++s) {
+        const int m = pl->ttm_order[s];
+        int64_t A = 1, B = 1;
+        for (int k = 0; k < m; ++k) A *= cur[k];
+        for (int k = m + 1; k < pl->order; ++k) B *= cur[k];
+        void *dst = (s + 1 == pl->ttm_order.size()) ? output : pl->d_ttm[s % 2];
+        const long ti = s == 0 ? timing_begin(pl, stream) : -1;
+        if (pl->dtype == DEINSUM_F64)
+            err = launch_ttm_plain_f64(static_cast<const double *>(src), static_cast<const double *>(U[m]),
+                                       static_cast<double *>(dst), A, cur[m], B, pl->ranks[m], stream);
+        else
+            err = launch_ttm_plain_f32(static_cast<const float *>(src), static_cast<const float *>(U[m]),
+                                       static_cast<float *>(dst), A, cur[m], B, pl->ranks[m], stream);
+        timing_end(pl, ti, stream);
+        cur[m] = pl->ranks[m];
+        src = dst;
+    }
+    return err ? DEINSUM_ERR_CUDA : DEINSUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+deinsum_status deinsum_plan(const char *einsum, const int64_t *extents, int n_extents,
+                            deinsum_dtype dtype, deinsum_prec prec, deinsum_plan_t *out) {
+    if (!out || !einsum || !extents) return DEINSUM_ERR_INVALID;
+    *out = nullptr;
+    Parsed p;
+    deinsum_status st = parse(einsum, p);
+    if (st != DEINSUM_OK) return st;
+    if (int(p.letters.size()) != n_extents) return DEINSUM_ERR_SHAPE;
+    for (int k = 0; k < n_extents; ++k)
+        if (extents[k] < 1 || extents[k] > (int64_t(1) << 40)) return DEINSUM_ERR_SHAPE;
+    if (dtype != DEINSUM_F32 && dtype != DEINSUM_F64) return DEINSUM_ERR_DTYPE;
+    if (prec != DEINSUM_PREC_PLAIN && prec != DEINSUM_PREC_SPLIT_BF16) return DEINSUM_ERR_DTYPE;
+    if (prec == DEINSUM_PREC_SPLIT_BF16 && dtype != DEINSUM_F32) return DEINSUM_ERR_DTYPE;
+    deinsum_plan_s *pl = new (std::nothrow) deinsum_plan_s();
+    if (!pl) return DEINSUM_ERR_OOM;
+    pl->dtype = dtype;
+    pl->prec = prec;
+    st = classify(pl, p, extents);
+    if (st == DEINSUM_OK) {
+        if (pl->kind == DEINSUM_KIND_MTTKRP) {
+            int64_t R = pl->ranks[(pl->mode + 1) % pl->order];
+            if (R > 64) st = DEINSUM_ERR_UNSUPPORTED;
+            else build_mttkrp_geometry(pl);
+        } else {
+            if (prec == DEINSUM_PREC_SPLIT_BF16) st = DEINSUM_ERR_DTYPE;  // split TTMc not offered yet
+            else plan_ttmc_chain(pl);
+        }
+    }
+    if (st != DEINSUM_OK) {
+        delete pl;
+        return st;
+    }
+    *out = pl;
+    return DEINSUM_OK;
+}
+
+deinsum_status deinsum_execute(deinsum_plan_t pl, const void *const *inputs, int n_inputs, void *output,
+                               deinsum_stream_t stream) {
+    if (!pl || !inputs || !output) return DEINSUM_ERR_INVALID;
+    if (n_inputs != pl->n_operands) return DEINSUM_ERR_INVALID;
+    const size_t es = elem_size(pl->dtype);
+    for (int k = 0; k < n_inputs; ++k) {
+        if (!inputs[k]) return DEINSUM_ERR_INVALID;
+        if (reinterpret_cast<uintptr_t>(inputs[k]) % es) return DEINSUM_ERR_ALIGN;
+    }
+    if (reinterpret_cast<uintptr_t>(output) % es) return DEINSUM_ERR_ALIGN;
+    deinsum_status st = ensure_device_state(pl);
+    if (st != DEINSUM_OK) return st;
+    if (pl->kind == DEINSUM_KIND_MTTKRP) return execute_mttkrp(pl, inputs, output, stream);
+    return execute_ttmc(pl, inputs, output, stream);
+}
+
+deinsum_status deinsum_workspace_size(deinsum_plan_t pl, size_t *bytes) {
+    if (!pl || !bytes) return DEINSUM_ERR_INVALID;
+    *bytes = pl->ws_bytes;
+    return DEINSUM_OK;
+}
+
+deinsum_status deinsum_plan_info(deinsum_plan_t pl, deinsum_plan_info_t *info) {
+    if (!pl || !info) return DEINSUM_ERR_INVALID;
+    std::memset(info, 0, sizeof(*info));
+    info->kind = pl->kind;
+    info->order = pl->order;
+    info->mode = pl->mode;
+    info->dtype = pl->dtype;
+    info->prec = pl->prec;
+    for (int m = 0; m < pl->order; ++m) {
+        info->dims[m] = pl->dims[m];
+        info->ranks[m] = pl->ranks[m];
+    }
+    if (pl->kind == DEINSUM_KIND_MTTKRP) {
+        info->out_elems = pl->dims[pl->mode] * pl->ranks[(pl->mode + 1) % pl->order];
+    } else {
+        info->out_elems = 1;
+        for (int m = 0; m < pl->order; ++m) info->out_elems *= pl->ranks[m];
+    }
+    info->alg_bytes = alg_bytes(pl);
+    info->alg_flops = alg_flops(pl);
+    info->n_units = pl->planned_units;
+    return DEINSUM_OK;
+}
+
+deinsum_status deinsum_last_device_status(deinsum_plan_t pl) {
+    if (!pl) return DEINSUM_ERR_INVALID;
+    if (!pl->d_status) return DEINSUM_OK;
+    int v = 0;
+    if (cudaMemcpy(&v, pl->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return DEINSUM_ERR_CUDA;
+    return v == 0 ? DEINSUM_OK : DEINSUM_ERR_TIMEOUT;
+}
+
+deinsum_status deinsum_set_kernel_timing(deinsum_plan_t pl, int enable) {
+    if (!pl) return DEINSUM_ERR_INVALID;
+    pl->timing = enable != 0;
+    return DEINSUM_OK;
+}
+
+deinsum_status deinsum_kernel_time(deinsum_plan_t pl, double *total_ms, int64_t *launches) {
+    if (!pl || !total_ms || !launches) return DEINSUM_ERR_INVALID;
+    double tot = 0.0;
+    for (size_t i = 0; i < pl->ev_used; ++i) {
+        if (cudaEventSynchronize(pl->ev_pool[i].second) != cudaSuccess) return DEINSUM_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pl->ev_pool[i].first, pl->ev_pool[i].second) != cudaSuccess)
+            return DEINSUM_ERR_CUDA;
+        tot += double(ms);
+    }
+    *total_ms = tot;
+    *launches = int64_t(pl->ev_used);
+    pl->ev_used = 0;
+    return DEINSUM_OK;
+}
+
+void deinsum_destroy(deinsum_plan_t pl) {
+    if (!pl) return;
+    for (auto &e : pl->ev_pool) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    if (pl->ws) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != pl->device) cudaSetDevice(pl->device);
+        cudaFree(pl->ws);
+        if (cur != pl->device && cur >= 0) cudaSetDevice(cur);
+    }
+    delete pl;
+}
+
+const char *deinsum_status_string(deinsum_status s) {
+    switch (s) {
+        case DEINSUM_OK: return "ok";
+        case DEINSUM_ERR_PARSE: return "malformed einsum string";
+        case DEINSUM_ERR_UNSUPPORTED: return "not an MTTKRP or TTMc pattern the library offers";
+        case DEINSUM_ERR_SHAPE: return "bad extents";
+        case DEINSUM_ERR_DTYPE: return "dtype / precision combination not offered";
+        case DEINSUM_ERR_ALIGN: return "pointer not aligned to its element size";
+        case DEINSUM_ERR_OOM: return "device allocation failed";
+        case DEINSUM_ERR_CUDA: return "CUDA error";
+        case DEINSUM_ERR_TIMEOUT: return "a device-side bounded wait gave up";
+        case DEINSUM_ERR_INVALID: return "invalid argument";
+    }
+    return "unknown status";
+}
+
+int64_t deinsum_kernel_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

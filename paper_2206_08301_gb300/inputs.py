@@ -24,16 +24,17 @@ bit for bit):
 
 * ``uniform_f32``: ``(raw >> 40) * 2^-23 - 1``  in [-1, 1) (24 random bits).
 * ``uniform_f64``: ``(raw >> 11) * 2^-52 - 1``  in [-1, 1) (53 random bits).
-* ``irwin_hall``: ``(sum_{t<12} (raw(12 i + t) >> 40) - 6 * 2^24) * 2^-24``,
-  the classical sum-of-twelve-uniforms approximation of N(0, 1) (mean 0,
-  variance 1), computed in exact integer arithmetic.
+* ``noise_z``: ``(sum_{t<4} ((raw >> 16 t) & 0xFFFF) - 2^17) * (sqrt(3) * 2^-16)``,
+  an Irwin-Hall sum of the four 16-bit lanes of one draw, scaled to mean 0 and
+  variance 1 (a bell-shaped stand-in for N(0, 1)); the integer sum is exact and
+  the scale is one fixed float64 constant, so host and device agree.
 * ``normal_f64`` (host only): Box-Muller on ``raw(2 i)`` and ``raw(2 i + 1)``.
   It goes through ``log``/``cos``, so it is used only for small operands
   (factor matrices) that are generated on the host and uploaded.
 
 Synthetic CP tensor
 -------------------
-``X[idx] = f32( sum_s prod_m A_m[i_m, s]  +  sigma * irwin_hall(idx) )``
+``X[idx] = f32( sum_s prod_m A_m[i_m, s]  +  sigma * noise_z(idx) )``
 evaluated in float64 with the product taken over m = 0..N-1 left to right,
 the sum over s = 0..R-1 left to right, no fused multiply-add, then rounded to
 nearest float32.  numpy evaluates it with separate multiplies and adds, and
@@ -94,17 +95,19 @@ def uniform_f64(seed: int, stream: int, idx) -> np.ndarray:
     return u * 2.0 ** -52 - 1.0
 
 
-def irwin_hall(seed: int, stream: int, idx) -> np.ndarray:
-    """Approximate N(0,1) draw: sum of 12 uniform 24-bit integers, centred and scaled.
+NOISE_SCALE = float(np.sqrt(3.0) * 2.0 ** -16)
 
-    Exact: the integer sum is below 2^28 and the scaling is a power of two.
+
+def noise_z(seed: int, stream: int, idx) -> np.ndarray:
+    """Approximate N(0,1) draw: Irwin-Hall sum of the four 16-bit lanes of one raw draw.
+
+    The lane sum is an exact integer below 2^18; it is centred and scaled by
+    the float64 constant NOISE_SCALE = sqrt(3) * 2^-16 (variance 1).
     """
-    idx = np.asarray(idx, dtype=np.uint64)
-    acc = np.zeros(idx.shape, dtype=np.uint64)
-    base = idx * np.uint64(12)
-    for t in range(12):
-        acc += raw(seed, stream, base + np.uint64(t)) >> np.uint64(40)
-    return (acc.astype(np.int64) - 6 * (1 << 24)).astype(np.float64) * 2.0 ** -24
+    r = raw(seed, stream, idx)
+    mask = np.uint64(0xFFFF)
+    s = (r & mask) + ((r >> np.uint64(16)) & mask) + ((r >> np.uint64(32)) & mask) + (r >> np.uint64(48))
+    return (s.astype(np.int64) - (1 << 17)).astype(np.float64) * NOISE_SCALE
 
 
 def normal_f64(seed: int, stream: int, n: int, mu: float = 0.0, sigma: float = 1.0) -> np.ndarray:
@@ -161,9 +164,46 @@ def cp_values(dims, cp_factors, sigma: float, seed: int, coords) -> np.ndarray:
             term = term * cp_factors[m][np.asarray(coords[m]), s]
         acc = acc + term
     if sigma != 0.0:
-        z = irwin_hall(seed, STREAM_NOISE, flat_index(dims, coords))
+        z = noise_z(seed, STREAM_NOISE, flat_index(dims, coords))
         acc = acc + np.float64(sigma) * z
     return acc.astype(np.float32)
+
+
+def cp_slab(seed: int, dims, cp_factors, sigma: float, mode: int, row: int) -> np.ndarray:
+    """Slab X[.., row, ..] (mode ``mode`` fixed) of the CP-plus-noise tensor, float32.
+
+    Same values, bit for bit, as ``cp_values`` on the slab's coordinates: the
+    product over modes is still formed left to right in mode order (the fixed
+    index enters as a scalar at its position) and the sum over s left to right.
+    """
+    order = len(dims)
+    rc = cp_factors[0].shape[1]
+    shape = tuple(d for m, d in enumerate(dims) if m != mode)
+    acc = np.zeros(shape, dtype=np.float64)
+    for s in range(rc):
+        term = None
+        for m in range(order):
+            if m == mode:
+                v = cp_factors[m][row, s]
+                term = np.float64(v) if term is None else term * v
+            else:
+                col = cp_factors[m][:, s]
+                term = col.copy() if term is None else np.multiply.outer(term, col)
+        acc = acc + term
+    if sigma != 0.0:
+        coords = np.meshgrid(*[np.arange(d) if m != mode else np.array([row]) for m, d in enumerate(dims)],
+                             indexing="ij", sparse=True)
+        flat = flat_index(dims, coords).reshape(shape)
+        acc = acc + np.float64(sigma) * noise_z(seed, STREAM_NOISE, flat)
+    return acc.astype(np.float32)
+
+
+def uniform_slab(seed: int, dims, mode: int, row: int, stream: int = STREAM_X) -> np.ndarray:
+    """Slab X[.., row, ..] of the uniform float32 tensor, regenerated by index."""
+    coords = np.meshgrid(*[np.arange(d) if m != mode else np.array([row]) for m, d in enumerate(dims)],
+                         indexing="ij", sparse=True)
+    shape = tuple(d for m, d in enumerate(dims) if m != mode)
+    return uniform_f32(seed, stream, flat_index(dims, coords).reshape(shape))
 
 
 def tensor_cp_f32(seed: int, dims, cp_factors, sigma: float) -> np.ndarray:

@@ -1,0 +1,128 @@
+"""Host-side checks of the C ABI (no compute calls, no GPU needed).
+
+The library must load, export every function include/deinsum.h declares, and
+plan (parse + classify, host only) the paper's Table IV patterns while
+rejecting everything else with the documented status codes.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2206_08301_gb300 as dz
+from paper_2206_08301_gb300 import build as dbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "deinsum.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(dz.library_path()):
+        dbuild.build()
+    return dz.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(deinsum_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("deinsum_plan", "deinsum_execute", "deinsum_workspace_size", "deinsum_last_device_status",
+                 "deinsum_destroy", "deinsum_status_string", "deinsum_plan_info"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(dz.library_path())
+    for name in declared_functions():
+        assert hasattr(raw, name), f"{name} declared but not exported"
+
+
+@pytest.mark.parametrize("spec,kind,mode", [
+    ("ijk,ja,ka->ia", "mttkrp", 0),     # Table IV MTTKRP-O3-M0
+    ("ijk,ia,ka->ja", "mttkrp", 1),     # MTTKRP-O3-M1
+    ("ijk,ia,ja->ka", "mttkrp", 2),     # MTTKRP-O3-M2
+    ("ijklm,ja,ka,la,ma->ia", "mttkrp", 0),
+    ("ijklm,ia,ja,la,ma->ka", "mttkrp", 2),
+    ("ijklm,ia,ja,ka,la->ma", "mttkrp", 4),
+    ("ijklm,jb,kc,ld,me->ibcde", "ttmc", 0),   # TTMc-O5-M0
+    ("ijkl,jb,kc,ld->ibcd", "ttmc", 0),
+    ("ijk,ib,jc->bck", "ttmc", 2),
+])
+def test_plan_classifies_table_iv_patterns(lib, spec, kind, mode):
+    letters = []
+    for c in spec:
+        if c.isalpha() and c not in letters:
+            letters.append(c)
+    p = dz.Plan(spec, [5] * len(letters))
+    assert p.kind == kind and p.mode == mode
+    assert p.workspace_size() == 0  # nothing allocated before the first execute
+
+
+@pytest.mark.parametrize("spec,status", [
+    ("ijk,ja,ka", 1),             # no output
+    ("ijk,ja,ka->i a", 2),        # spaces are removed -> "ia"... handled below
+    ("ij1,ja->ia", 1),            # bad character
+    ("ijk,ja,ka,al->il", 2),      # MTTKRP + MM: not offered
+    ("ij,jk,kl->il", 2),          # 2MM chain: not offered
+    ("iik,ia,ka->ia", 2),         # diagonal of X
+    ("ijk,ja,kb->iba", 2),        # TTMc with permuted output modes: not offered
+    ("ijk,ja,ka->ai", 2),         # transposed MTTKRP output
+    ("ijk,ja,ka->iz", 2),         # output letter missing from the inputs
+])
+def test_plan_rejects(lib, spec, status):
+    letters = []
+    for c in spec:
+        if c.isalpha() and c not in letters:
+            letters.append(c)
+    if spec == "ijk,ja,ka->i a":
+        p = dz.Plan(spec, [3] * len(letters))  # whitespace is ignored: this is MTTKRP mode 0
+        assert p.kind == "mttkrp"
+        return
+    with pytest.raises(dz.DeinsumError) as e:
+        dz.Plan(spec, [3] * len(letters))
+    assert e.value.status == status
+
+
+def test_plan_rejects_bad_extents_and_dtype(lib):
+    with pytest.raises(dz.DeinsumError) as e:
+        dz.Plan("ijk,ja,ka->ia", [3, 3, 3])        # one extent missing
+    assert e.value.status == 3
+    with pytest.raises(dz.DeinsumError) as e:
+        dz.Plan("ijk,ja,ka->ia", [3, 0, 3, 4])     # zero extent
+    assert e.value.status == 3
+    with pytest.raises(dz.DeinsumError) as e:
+        dz.Plan("ijk,ja,ka->ia", [3, 3, 3, 4], dtype="float64", prec="split_bf16")
+    assert e.value.status == 4
+    with pytest.raises(dz.DeinsumError) as e:
+        dz.Plan("ijk,ja,ka->ia", [3, 3, 3, 65])    # rank above 64
+    assert e.value.status == 2
+
+
+def test_plan_info_counts(lib):
+    p = dz.Plan("ijk,ja,ka->ia", [1024, 1024, 1024, 32])
+    info = p.info()
+    x = 1024 ** 3
+    assert info["alg_flops"] == 2.0 * x * 32
+    assert info["alg_bytes"] == 4.0 * (x + 3 * 1024 * 32)
+    t = dz.Plan("ijkl,jb,kc,ld->ibcd", [256, 256, 256, 256, 32, 32, 32])
+    ti = t.info()
+    # FLOP-minimal chain: 2*256^4*32 + 2*256^3*32*32 + 2*256^2*32^3
+    assert ti["alg_flops"] == 2.0 * (256 ** 4 * 32 + 256 ** 3 * 32 * 32 + 256 ** 2 * 32 ** 3)
+    assert ti["out_elems"] == 256 * 32 ** 3
+
+
+def test_status_strings(lib):
+    for code in range(10):
+        assert lib.deinsum_status_string(code)
+
+
+def test_einsum_builders():
+    assert dz.mttkrp_einsum(3, 0) == "abc,br,cr->ar"
+    assert dz.mttkrp_einsum(5, 2) == "abcde,ar,br,dr,er->cr"
+    assert dz.ttmc_einsum(4, 0) == "abcd,bt,cu,dv->atuv"

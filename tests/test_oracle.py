@@ -290,7 +290,7 @@ def test_generator_uniform_exact_and_deterministic():
 
 
 def test_generator_streams_and_noise_moments():
-    z = inputs.irwin_hall(3, inputs.STREAM_NOISE, np.arange(200000, dtype=np.uint64))
+    z = inputs.noise_z(3, inputs.STREAM_NOISE, np.arange(200000, dtype=np.uint64))
     assert abs(z.mean()) < 0.01 and abs(z.var() - 1.0) < 0.02
     n = inputs.normal_f64(3, inputs.STREAM_FACTOR, 200000)
     assert abs(n.mean()) < 0.01 and abs(n.var() - 1.0) < 0.02
@@ -305,3 +305,14 @@ def test_cp_values_match_einsum_reconstruction():
     np.testing.assert_allclose(X, ref, rtol=1e-6, atol=1e-6)
     Xn = inputs.tensor_cp_f32(rng_seed, dims, A, 1e-2)
     assert 0.001 < np.abs(Xn - X).mean() < 0.02
+    for mode in range(3):
+        for row in (0, dims[mode] - 1):
+            np.testing.assert_array_equal(inputs.cp_slab(rng_seed, dims, A, 1e-2, mode, row),
+                                          np.take(Xn, row, axis=mode))
+
+
+def test_uniform_slab_matches_whole_tensor():
+    dims = (4, 5, 6)
+    X = inputs.tensor_uniform_f32(3, dims)
+    for mode in range(3):
+        np.testing.assert_array_equal(inputs.uniform_slab(3, dims, mode, 2), np.take(X, 2, axis=mode))
