@@ -83,6 +83,7 @@ int launch_split_inner_factor(const MttkrpArgs &a, void *bsplit, void *stream);
 int launch_mttkrp_reduce_f32(const MttkrpArgs &a, const int64_t *col_unit_begin, void *out, void *stream);
 int launch_mttkrp_reduce_f64(const MttkrpArgs &a, const int64_t *col_unit_begin, void *out, void *stream);
 size_t mttkrp_tc_smem_bytes(int R_pad);
+int mttkrp_plain_ctas_per_sm(int f64, int R_pad);  // resident CTAs per SM of the plain kernel
 
 // Plain TTM on a (A, Im, B) view: Y[a, r, b] = sum_i X[a, i, b] U[i, r].
 int launch_ttm_plain_f32(const float *X, const float *U, float *Y, int64_t A, int64_t Im,

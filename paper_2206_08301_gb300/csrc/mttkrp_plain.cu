@@ -323,6 +323,29 @@ int launch_reduce(const MttkrpArgs &a, const T *partial, const int64_t *col_begi
 
 }  // namespace
 
+template <typename T>
+int plain_ctas_per_sm(int RP) {
+    int per_sm = 1;
+    switch (RP) {
+        case 16:
+            cudaFuncSetAttribute(mttkrp_plain_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(plain_smem_bytes<T>(16)));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mttkrp_plain_kernel<T, 16>, kThreads, plain_smem_bytes<T>(16));
+            break;
+        case 32:
+            cudaFuncSetAttribute(mttkrp_plain_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(plain_smem_bytes<T>(32)));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mttkrp_plain_kernel<T, 32>, kThreads, plain_smem_bytes<T>(32));
+            break;
+        default:
+            cudaFuncSetAttribute(mttkrp_plain_kernel<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(plain_smem_bytes<T>(64)));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mttkrp_plain_kernel<T, 64>, kThreads, plain_smem_bytes<T>(64));
+            break;
+    }
+    cudaGetLastError();
+    return per_sm < 1 ? 1 : per_sm;
+}
+
+int mttkrp_plain_ctas_per_sm(int f64, int R_pad) { return f64 ? plain_ctas_per_sm<double>(R_pad) : plain_ctas_per_sm<float>(R_pad); }
+
 int launch_mttkrp_plain_f32(const MttkrpArgs &a, int n_sm, void *stream) { return launch_plain<float>(a, n_sm, stream); }
 int launch_mttkrp_plain_f64(const MttkrpArgs &a, int n_sm, void *stream) { return launch_plain<double>(a, n_sm, stream); }
 int launch_mttkrp_reduce_f32(const MttkrpArgs &a, const int64_t *col_begin, void *out, void *stream) {

@@ -37,6 +37,7 @@ constexpr int BK = DEINSUM_BK;
 constexpr int PRODUCER_WARPS = 8;
 constexpr int EPI_WARPS = 4;
 constexpr int kFoldEvery = 64;  // fiber groups accumulated in registers before a flush to smem
+constexpr int kPrefetchAhead = 4;  // chunks of X bulk-prefetched into L2 ahead of the loads
 
 template <int RP> struct TcCfg {
     static constexpr int N = 2 * RP;                       // MMA N: hi and lo columns of the factor
@@ -102,7 +103,7 @@ __device__ __forceinline__ bool row_valid(const MttkrpGeom &g, int64_t col, int6
 
 // Load the 32 X values one producer thread owns in the chunk `it`.
 //   case 0: rows rsub + 16 j (j < 8), elements k = 4 k4 .. 4 k4 + 3
-//   case 1: rows 4 iq .. 4 iq + 3, elements k = 8 kq + j (j < 8)
+//   case 1: row pt % 128, elements k = 32 (pt / 128) .. + 31
 __device__ __forceinline__ void producer_load(const MttkrpArgs &a, const Iter &it, int pt, float4 (&v)[8]) {
     const MttkrpGeom &g = a.g;
     const float *X = static_cast<const float *>(a.X);
@@ -130,28 +131,49 @@ __device__ __forceinline__ void producer_load(const MttkrpArgs &a, const Iter &i
             }
         }
     } else {
-        const int w = pt >> 5, l = pt & 31;
-        const int kq = l & 7, iq = (l >> 3) + 4 * w;
-        const int64_t row0 = it.col * BM + 4 * iq;
-        const int64_t kbase = k0 + 8 * kq;
-        const float *base = X + (it.o * g.K_in + kbase) * g.I + row0;
-        if (g.vec_ok) {
-            const bool rv = row0 < g.I;
+        // one row per lane: a warp reads 32 consecutive rows (128 contiguous bytes) of one k
+        const int row = pt & (BM - 1), kh = pt >> 7;
+        const bool rv = it.col * BM + row < g.I;
+        const int64_t kbase = k0 + 32 * kh;
+        const float *base = X + (it.o * g.K_in + kbase) * g.I + it.col * BM + row;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float e[4];
             #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                v[j] = rv && (kbase + j < g.K_in) ? ldg_stream4(base + int64_t(j) * g.I)
-                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-            #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float e[4] = {0.f, 0.f, 0.f, 0.f};
-                if (kbase + j < g.K_in)
-                    #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (row0 + q < g.I) e[q] = __ldg(base + int64_t(j) * g.I + q);
-                v[j] = make_float4(e[0], e[1], e[2], e[3]);
+            for (int q = 0; q < 4; ++q) {
+                const int kk = 4 * j + q;
+                e[q] = (rv && kbase + kk < g.K_in) ? ldg_stream1(base + int64_t(kk) * g.I) : 0.f;
             }
+            v[j] = make_float4(e[0], e[1], e[2], e[3]);
         }
+    }
+}
+
+// Bulk-prefetch into L2 the data kPrefetchAhead chunks after chunk `it` on the
+// same rows.  A case-0 row is contiguous over all q = (o, k), and case-1 rows
+// are contiguous over all p = (o, k), so that data sits a fixed distance
+// further along: thread pt < 128 prefetches 64 elements of row pt (case 0);
+// thread pt < 64 prefetches one 128-row slice (case 1).  Only with 16-byte
+// aligned rows (vec_ok); a hint, bounded to the rows' extent.
+__device__ __forceinline__ void producer_prefetch(const MttkrpArgs &a, const Iter &it, int pt) {
+    const MttkrpGeom &g = a.g;
+    if (!g.vec_ok) return;
+    const float *X = static_cast<const float *>(a.X);
+    const int64_t ahead = int64_t(kPrefetchAhead) * BK;
+    if (g.kcase == 0) {
+        if (pt >= BM) return;
+        const int64_t rowbase = tile_rowbase(g, it.col, it.tile);
+        const int64_t q = it.o * g.K_in + int64_t(it.kb) * BK + ahead;
+        if (q >= g.Q || !row_valid(g, it.col, rowbase, pt)) return;
+        const int64_t n = g.Q - q < BK ? g.Q - q : BK;
+        prefetch_l2(X + (rowbase + pt) * g.Q + q, uint32_t(n * 4));
+    } else {
+        if (pt >= BK) return;
+        const int64_t p = it.o * g.K_in + int64_t(it.kb) * BK + pt + ahead;
+        if (p >= g.O * g.K_in) return;
+        const int64_t r0 = it.col * BM;
+        const int64_t n = g.I - r0 < BM ? g.I - r0 : BM;
+        prefetch_l2(X + p * g.I + r0, uint32_t(n * 4));
     }
 }
 
@@ -171,19 +193,18 @@ __device__ __forceinline__ void producer_store(const MttkrpGeom &g, int pt, uint
             sts64(a_lo + off, l0, l1);
         }
     } else {
-        const int w = pt >> 5, l = pt & 31;
-        const int kq = l & 7, iq = (l >> 3) + 4 * w;
+        // row `row`, k = 32 kh .. 32 kh + 31: four 8-element groups; eight consecutive
+        // lanes hold eight consecutive rows, so their 16-byte stores hit distinct banks
+        const int row = pt & (BM - 1), kh = pt >> 7;
         #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            float x[8];
-            #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                x[j] = e == 0 ? v[j].x : (e == 1 ? v[j].y : (e == 2 ? v[j].z : v[j].w));
+        for (int q = 0; q < 4; ++q) {
+            const float4 x0 = v[2 * q], x1 = v[2 * q + 1];
             uint32_t h[4], lo[4];
-            #pragma unroll
-            for (int q = 0; q < 4; ++q) split2(x[2 * q], x[2 * q + 1], h[q], lo[q]);
-            const uint32_t row = uint32_t(4 * iq + e);
-            const uint32_t off = sw128_offset(row, uint32_t(8 * kq));
+            split2(x0.x, x0.y, h[0], lo[0]);
+            split2(x0.z, x0.w, h[1], lo[1]);
+            split2(x1.x, x1.y, h[2], lo[2]);
+            split2(x1.z, x1.w, h[3], lo[3]);
+            const uint32_t off = sw128_offset(uint32_t(row), uint32_t(32 * kh + 8 * q));
             sts128(a_hi + off, h[0], h[1], h[2], h[3]);
             sts128(a_lo + off, lo[0], lo[1], lo[2], lo[3]);
         }
@@ -281,7 +302,10 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         auto body = [&](float4 (&cur)[8], float4 (&nxt)[8]) -> bool {
             Iter nx = it;
             nx.next(a);
-            if (!nx.done) producer_load(a, nx, pt, nxt);
+            if (!nx.done) {
+                producer_load(a, nx, pt, nxt);
+                producer_prefetch(a, nx, pt);
+            }
             const int s = int(chunk % STAGES);
             const uint32_t j = uint32_t(chunk / STAGES);
             // warp-uniform outcome, so that no lane is left behind at a warp barrier

@@ -242,7 +242,12 @@ deinsum_status ensure_device_state(deinsum_plan_s *pl) {
     size_t o_status = off;
     off = align_up(off + 256, 256);
     if (pl->kind == DEINSUM_KIND_MTTKRP) {
-        build_schedule(pl, nsm);
+        // one unit per resident CTA: the tensor-core kernel keeps one CTA per SM,
+        // the plain kernel as many as its occupancy allows
+        int per_sm = 1;
+        if (pl->prec == DEINSUM_PREC_PLAIN)
+            per_sm = mttkrp_plain_ctas_per_sm(pl->dtype == DEINSUM_F64 ? 1 : 0, pl->geom.R_pad);
+        build_schedule(pl, int64_t(nsm) * per_sm);
         const MttkrpGeom &g = pl->geom;
         o_units = off;
         off = align_up(off + pl->units.size() * sizeof(int64_t), 256);
