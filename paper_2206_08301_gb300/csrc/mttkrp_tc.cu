@@ -13,12 +13,15 @@
 // HBM -- schedule P2 of Sec. IV-E; Sec. II-A decomposition).
 //
 // Warp roles (one CTA per SM, persistent over units):
-//   warps 0-7    producers: 128-bit streaming loads of X -> split -> 128B-swizzled
-//                K-major smem tiles; one thread also bulk-copies the B tile.
-//   warps 8..    epilogue: TMEM -> registers, weight, accumulate, write partials.
-//   last warp    TMEM allocation and the single-thread MMA issue.
-// Pipelines: STAGES smem stages (full/empty mbarriers) and two TMEM accumulators
-// (acc-full/acc-empty mbarriers).  Every wait is bounded (mbar_wait).
+//   warps 0-7    converters: raw FP32 tile (smem) -> split -> 128B-swizzled K-major
+//                A tiles; one thread also bulk-copies the split factor tile B.
+//                Without TMA (unaligned rows) they load X from global themselves.
+//   warps 8-11   epilogue: TMEM -> registers, weight, accumulate, write partials.
+//   warp 12      TMEM allocation and the single-thread MMA issue.
+//   warp 13      TMA: tiled tensor loads of raw X tiles into a ring of RS stages.
+// Rings: raw X (RS stages: raw_full / raw_empty), operand tiles (AS stages:
+// a_full / bfull / a_empty), two TMEM accumulators (accf / acce).  Every wait
+// is bounded (mbar_wait) and warp-uniform where a warp barrier follows.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -34,22 +37,26 @@ using namespace sm100;
 
 constexpr int BM = DEINSUM_BM;
 constexpr int BK = DEINSUM_BK;
-constexpr int PRODUCER_WARPS = 8;
+constexpr int CONV_WARPS = 8;
 constexpr int EPI_WARPS = 4;
-constexpr int kFoldEvery = 64;  // fiber groups accumulated in registers before a flush to smem
-constexpr int kPrefetchAhead = 4;  // chunks of X bulk-prefetched into L2 ahead of the loads
+constexpr int kFoldEvery = 64;  // fiber groups accumulated in registers before a flush
 
 template <int RP> struct TcCfg {
     static constexpr int N = 2 * RP;                       // MMA N: hi and lo columns of the factor
-    static constexpr int STAGES = RP <= 32 ? 4 : 3;
-    static constexpr int WARPS = PRODUCER_WARPS + EPI_WARPS + 1;
+    static constexpr int RS = RP <= 32 ? 4 : 3;            // raw X stages
+    static constexpr int AS = 2;                           // operand stages
+    static constexpr int MMA_WARP = CONV_WARPS + EPI_WARPS;
+    static constexpr int TMA_WARP = MMA_WARP + 1;
+    static constexpr int WARPS = TMA_WARP + 1;
     static constexpr int THREADS = WARPS * 32;
+    static constexpr int RAW_BYTES = BM * BK * 4;
     static constexpr int A_BYTES = BM * BK * 2;            // one of hi / lo
     static constexpr int B_BYTES = N * BK * 2;
-    static constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;
+    static constexpr int ASTAGE_BYTES = 2 * A_BYTES + B_BYTES;
+    static constexpr int LROW_BYTES = BM * RP * 4;         // per-row weights of narrow tiles
     static constexpr int TMEM_COLS = 2 * N;                // two accumulators
-    static constexpr int PRIV_BYTES = 2 * BM * RP * 4;     // per-row weights + flushed sums
-    static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + PRIV_BYTES + 1024 + 256;
+    static constexpr int NBARS = 2 * RS + 3 * AS + 4 + 1;
+    static constexpr size_t SMEM = size_t(RS) * RAW_BYTES + size_t(AS) * ASTAGE_BYTES + LROW_BYTES + 1024 + 256;
 };
 
 struct Iter {
@@ -101,10 +108,41 @@ __device__ __forceinline__ bool row_valid(const MttkrpGeom &g, int64_t col, int6
     return col * BM + l < g.I;
 }
 
-// Load the 32 X values one producer thread owns in the chunk `it`.
-//   case 0: rows rsub + 16 j (j < 8), elements k = 4 k4 .. 4 k4 + 3
-//   case 1: row pt % 128, elements k = 32 (pt / 128) .. + 31
-__device__ __forceinline__ void producer_load(const MttkrpArgs &a, const Iter &it, int pt, float4 (&v)[8]) {
+// ---------------------------------------------------------------------------
+// Converter inputs.  Each of the 256 converter threads owns 32 values of a chunk:
+//   case 0: rows rsub + 16 j (j < 8), k = 4 k4 .. 4 k4 + 3   (pt = 16 rsub + k4)
+//   case 1: row pt % 128, k = 32 (pt / 128) .. + 31
+// ---------------------------------------------------------------------------
+
+// From the raw tile the TMA wrote (out-of-bounds rows and k were zero-filled
+// by the TMA; narrow rows beyond G*I_n, which the box does not cover, are zeroed here).
+__device__ __forceinline__ void conv_read_smem(const MttkrpArgs &a, const float *raw, int pt, float4 (&v)[8]) {
+    const MttkrpGeom &g = a.g;
+    if (g.kcase == 0) {
+        const int k4 = pt & 15, rsub = pt >> 4;
+        const int nrows = g.narrow ? int(g.G * g.I) : BM;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int row = rsub + 16 * j;
+            v[j] = row < nrows ? *reinterpret_cast<const float4 *>(raw + row * BK + 4 * k4)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+        const int row = pt & (BM - 1), kh = pt >> 7;
+        const int pitch = a.raw_pitch;
+        const bool rv = row < pitch;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float e[4];
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) e[q] = rv ? raw[(32 * kh + 4 * j + q) * pitch + row] : 0.f;
+            v[j] = make_float4(e[0], e[1], e[2], e[3]);
+        }
+    }
+}
+
+// From global memory with per-element bounds checks (rows not 16-byte aligned).
+__device__ __forceinline__ void conv_read_global(const MttkrpArgs &a, const Iter &it, int pt, float4 (&v)[8]) {
     const MttkrpGeom &g = a.g;
     const float *X = static_cast<const float *>(a.X);
     const int64_t k0 = int64_t(it.kb) * BK;
@@ -114,24 +152,16 @@ __device__ __forceinline__ void producer_load(const MttkrpArgs &a, const Iter &i
         const int64_t kpos = k0 + 4 * k4;
         const float *p0 = X + (rowbase + rsub) * g.Q + it.o * g.K_in + kpos;
         const int64_t rstride = 16 * g.Q;
-        if (g.vec_ok) {
-            #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                v[j] = (kpos < g.K_in && row_valid(g, it.col, rowbase, rsub + 16 * j))
-                           ? ldg_stream4(p0 + j * rstride) : make_float4(0.f, 0.f, 0.f, 0.f);
-        } else {
-            #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float e[4] = {0.f, 0.f, 0.f, 0.f};
-                if (row_valid(g, it.col, rowbase, rsub + 16 * j))
-                    #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (kpos + q < g.K_in) e[q] = __ldg(p0 + j * rstride + q);
-                v[j] = make_float4(e[0], e[1], e[2], e[3]);
-            }
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float e[4] = {0.f, 0.f, 0.f, 0.f};
+            if (row_valid(g, it.col, rowbase, rsub + 16 * j))
+                #pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (kpos + q < g.K_in) e[q] = __ldg(p0 + j * rstride + q);
+            v[j] = make_float4(e[0], e[1], e[2], e[3]);
         }
     } else {
-        // one row per lane: a warp reads 32 consecutive rows (128 contiguous bytes) of one k
         const int row = pt & (BM - 1), kh = pt >> 7;
         const bool rv = it.col * BM + row < g.I;
         const int64_t kbase = k0 + 32 * kh;
@@ -142,45 +172,18 @@ __device__ __forceinline__ void producer_load(const MttkrpArgs &a, const Iter &i
             #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int kk = 4 * j + q;
-                e[q] = (rv && kbase + kk < g.K_in) ? ldg_stream1(base + int64_t(kk) * g.I) : 0.f;
+                e[q] = (rv && kbase + kk < g.K_in) ? __ldg(base + int64_t(kk) * g.I) : 0.f;
             }
             v[j] = make_float4(e[0], e[1], e[2], e[3]);
         }
     }
 }
 
-// Bulk-prefetch into L2 the data kPrefetchAhead chunks after chunk `it` on the
-// same rows.  A case-0 row is contiguous over all q = (o, k), and case-1 rows
-// are contiguous over all p = (o, k), so that data sits a fixed distance
-// further along: thread pt < 128 prefetches 64 elements of row pt (case 0);
-// thread pt < 64 prefetches one 128-row slice (case 1).  Only with 16-byte
-// aligned rows (vec_ok); a hint, bounded to the rows' extent.
-__device__ __forceinline__ void producer_prefetch(const MttkrpArgs &a, const Iter &it, int pt) {
-    const MttkrpGeom &g = a.g;
-    if (!g.vec_ok) return;
-    const float *X = static_cast<const float *>(a.X);
-    const int64_t ahead = int64_t(kPrefetchAhead) * BK;
-    if (g.kcase == 0) {
-        if (pt >= BM) return;
-        const int64_t rowbase = tile_rowbase(g, it.col, it.tile);
-        const int64_t q = it.o * g.K_in + int64_t(it.kb) * BK + ahead;
-        if (q >= g.Q || !row_valid(g, it.col, rowbase, pt)) return;
-        const int64_t n = g.Q - q < BK ? g.Q - q : BK;
-        prefetch_l2(X + (rowbase + pt) * g.Q + q, uint32_t(n * 4));
-    } else {
-        if (pt >= BK) return;
-        const int64_t p = it.o * g.K_in + int64_t(it.kb) * BK + pt + ahead;
-        if (p >= g.O * g.K_in) return;
-        const int64_t r0 = it.col * BM;
-        const int64_t n = g.I - r0 < BM ? g.I - r0 : BM;
-        prefetch_l2(X + p * g.I + r0, uint32_t(n * 4));
-    }
-}
-
 // Split and store the thread's 32 values into the stage's A_hi / A_lo tiles.
-__device__ __forceinline__ void producer_store(const MttkrpGeom &g, int pt, uint32_t a_hi, uint32_t a_lo,
-                                               const float4 (&v)[8]) {
+__device__ __forceinline__ void conv_store(const MttkrpGeom &g, int pt, uint32_t a_hi, uint32_t a_lo,
+                                           const float4 (&v)[8]) {
     if (g.kcase == 0) {
+        // 16 lanes cover one 128-byte swizzled row: conflict-free 8-byte stores
         const int k4 = pt & 15, rsub = pt >> 4;
         #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -193,8 +196,8 @@ __device__ __forceinline__ void producer_store(const MttkrpGeom &g, int pt, uint
             sts64(a_lo + off, l0, l1);
         }
     } else {
-        // row `row`, k = 32 kh .. 32 kh + 31: four 8-element groups; eight consecutive
-        // lanes hold eight consecutive rows, so their 16-byte stores hit distinct banks
+        // eight consecutive lanes hold eight consecutive rows: their 16-byte
+        // stores land in distinct swizzled bank groups
         const int row = pt & (BM - 1), kh = pt >> 7;
         #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -240,34 +243,41 @@ template <int RP>
 __global__ void __launch_bounds__(TcCfg<RP>::THREADS, 1)
 mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     using C = TcCfg<RP>;
-    constexpr int STAGES = C::STAGES;
+    constexpr int RS = C::RS, AS = C::AS;
     const MttkrpGeom &g = a.g;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float *priv = reinterpret_cast<float *>(smem + STAGES * C::STAGE_BYTES);   // [2][RP][BM] thread-private
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE_BYTES + C::PRIV_BYTES);
-    // bars: full[S], bfull[S], empty[S], accf[2], acce[2], drain
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 3 * STAGES + 5);
+    unsigned char *raw_base = smem;
+    unsigned char *a_base = smem + RS * C::RAW_BYTES;
+    float *Lrow = reinterpret_cast<float *>(a_base + AS * C::ASTAGE_BYTES);   // [RP][BM], thread-private columns
+    uint64_t *bars = reinterpret_cast<uint64_t *>(a_base + AS * C::ASTAGE_BYTES + C::LROW_BYTES);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t sbase = smem_u32(smem);
-    auto a_hi = [&](int s) { return sbase + uint32_t(s) * C::STAGE_BYTES; };
-    auto a_lo = [&](int s) { return sbase + uint32_t(s) * C::STAGE_BYTES + C::A_BYTES; };
-    auto b_t = [&](int s) { return sbase + uint32_t(s) * C::STAGE_BYTES + 2 * C::A_BYTES; };
-    auto full = [&](int s) { return smem_u32(bars + s); };
-    auto bfull = [&](int s) { return smem_u32(bars + STAGES + s); };
-    auto empty = [&](int s) { return smem_u32(bars + 2 * STAGES + s); };
-    auto accf = [&](int b) { return smem_u32(bars + 3 * STAGES + b); };
-    auto acce = [&](int b) { return smem_u32(bars + 3 * STAGES + 2 + b); };
-    const uint32_t drain = smem_u32(bars + 3 * STAGES + 4);
+    const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
+    auto raw_addr = [&](int s) { return raw_s + uint32_t(s) * C::RAW_BYTES; };
+    auto a_hi = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES; };
+    auto a_lo = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + C::A_BYTES; };
+    auto b_t = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + 2 * C::A_BYTES; };
+    auto raw_full = [&](int s) { return smem_u32(bars + s); };
+    auto raw_empty = [&](int s) { return smem_u32(bars + RS + s); };
+    auto a_full = [&](int s) { return smem_u32(bars + 2 * RS + s); };
+    auto bfull = [&](int s) { return smem_u32(bars + 2 * RS + AS + s); };
+    auto a_empty = [&](int s) { return smem_u32(bars + 2 * RS + 2 * AS + s); };
+    auto accf = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + b); };
+    auto acce = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + 2 + b); };
+    const uint32_t drain = smem_u32(bars + 2 * RS + 3 * AS + 4);
 
-    const int mma_warp = C::WARPS - 1;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full(s), PRODUCER_WARPS);
+        for (int s = 0; s < RS; ++s) {
+            mbar_init(raw_full(s), 1);
+            mbar_init(raw_empty(s), CONV_WARPS);
+        }
+        for (int s = 0; s < AS; ++s) {
+            mbar_init(a_full(s), CONV_WARPS);
             mbar_init(bfull(s), 1);
-            mbar_init(empty(s), 1);
+            mbar_init(a_empty(s), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf(b), 1);
@@ -277,7 +287,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == mma_warp) {
+    if (warp == C::MMA_WARP) {
         tmem_alloc(smem_u32(tmem_holder), C::TMEM_COLS);
         tmem_relinquish();
     }
@@ -286,58 +296,78 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
-    if (warp < PRODUCER_WARPS) {
-        // ------------------------------------------------------------ producers
+    if (warp < CONV_WARPS) {
+        // ----------------------------------------------------------- converters
         const int pt = threadIdx.x;
         const bool issuer = (pt == 0);
         const char *bsrc = static_cast<const char *>(a.Bsplit);
         Iter it;
         it.init(a);
-        float4 va[8], vb[8];
-        uint32_t bpar_issued = 0;  // bit s: parity of the last copy issued on stage s
-        uint32_t bused = 0;        // bit s: a copy was issued on stage s
-        int64_t chunk = 0;
-        bool ok = true;
-        if (!it.done) producer_load(a, it, pt, va);
-        auto body = [&](float4 (&cur)[8], float4 (&nxt)[8]) -> bool {
-            Iter nx = it;
-            nx.next(a);
-            if (!nx.done) {
-                producer_load(a, nx, pt, nxt);
-                producer_prefetch(a, nx, pt);
+        uint32_t bpar = 0, bused = 0;  // per operand stage: parity of the last B copy, copy issued
+        for (int64_t chunk = 0; !it.done; ++chunk) {
+            float4 v[8];
+            if (a.use_tma) {
+                const int rs = int(chunk % RS);
+                const uint32_t rj = uint32_t(chunk / RS);
+                if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, a.status))) break;
+                conv_read_smem(a, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(raw_empty(rs));
+            } else {
+                conv_read_global(a, it, pt, v);
             }
-            const int s = int(chunk % STAGES);
-            const uint32_t j = uint32_t(chunk / STAGES);
-            // warp-uniform outcome, so that no lane is left behind at a warp barrier
-            if (!__all_sync(0xffffffffu, mbar_wait(empty(s), (j & 1u) ^ 1u, abort_flag, a.status))) return false;
+            const int as = int(chunk % AS);
+            const uint32_t aj = uint32_t(chunk / AS);
+            if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, a.status))) break;
             if (issuer) {
-                mbar_arrive_expect_tx(bfull(s), C::B_BYTES);
-                bulk_g2s(b_t(s), bsrc + size_t(it.kb) * C::B_BYTES, C::B_BYTES, bfull(s));
-                bpar_issued = (bpar_issued & ~(1u << s)) | ((j & 1u) << s);
-                bused |= 1u << s;
+                mbar_arrive_expect_tx(bfull(as), C::B_BYTES);
+                bulk_g2s(b_t(as), bsrc + size_t(it.kb) * C::B_BYTES, C::B_BYTES, bfull(as));
+                bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
+                bused |= 1u << as;
             }
-            producer_store(g, pt, a_hi(s), a_lo(s), cur);
+            conv_store(g, pt, a_hi(as), a_lo(as), v);
             fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(full(s));
-            it = nx;
-            ++chunk;
-            return true;
-        };
-        while (ok && !it.done) {
-            ok = body(va, vb);
-            if (!ok || it.done) break;
-            ok = body(vb, va);
+            if (lane == 0) mbar_arrive(a_full(as));
+            it.next(a);
         }
         if (issuer) {  // every bulk copy into this CTA's smem has landed before exit
-            for (int s = 0; s < STAGES; ++s)
-                if ((bused >> s) & 1u) mbar_wait(bfull(s), (bpar_issued >> s) & 1u, abort_flag, a.status);
+            for (int s = 0; s < AS; ++s)
+                if ((bused >> s) & 1u) mbar_wait(bfull(s), (bpar >> s) & 1u, abort_flag, a.status);
         }
-    } else if (warp == mma_warp) {
+    } else if (warp == C::TMA_WARP) {
+        // ------------------------------------------------------------------ TMA
+        if (lane == 0 && a.use_tma) {
+            Iter it;
+            it.init(a);
+            int last_rs = -1;
+            uint32_t last_par = 0;
+            for (int64_t chunk = 0; !it.done; ++chunk) {
+                const int rs = int(chunk % RS);
+                const uint32_t rj = uint32_t(chunk / RS);
+                if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, a.status)) break;
+                mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
+                const int kc = it.kb * BK;
+                if (g.kcase == 0) {
+                    const int c2 = g.narrow ? 0 : int(it.col * BM);
+                    const int c3 = g.narrow ? int(it.tile * g.G) : int(it.tile);
+                    tma_load_4d(raw_addr(rs), &a.xmap, kc, int(it.o), c2, c3, raw_full(rs));
+                } else {
+                    tma_load_3d(raw_addr(rs), &a.xmap, int(it.col * BM), kc, int(it.o), raw_full(rs));
+                }
+                last_rs = rs;
+                last_par = rj & 1u;
+                it.next(a);
+            }
+            // the last load has landed before exit (the earlier ones were consumed)
+            if (last_rs >= 0) mbar_wait(raw_full(last_rs), last_par, abort_flag, a.status);
+        }
+        __syncwarp();
+    } else if (warp == C::MMA_WARP) {
         // -------------------------------------------------------------- MMA issue
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16_f32(BM, C::N);
-            int64_t chunk = 0, fgi = 0, nfg = 0;
+            int64_t chunk = 0, nfg = 0;
             {   // count the fiber groups of this CTA
                 Iter it;
                 it.init(a);
@@ -348,16 +378,16 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 }
             }
             bool ok = true;
-            for (fgi = 0; ok && fgi < nfg; ++fgi) {
+            for (int64_t fgi = 0; ok && fgi < nfg; ++fgi) {
                 const int b = int(fgi & 1);
                 const uint32_t jb = uint32_t(fgi >> 1);
                 if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, a.status)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dcol = tmem + uint32_t(b * C::N);
                 for (int kb = 0; kb < g.n_kb; ++kb) {
-                    const int s = int(chunk % STAGES);
-                    const uint32_t j = uint32_t(chunk / STAGES);
-                    if (!mbar_wait(full(s), j & 1u, abort_flag, a.status) ||
+                    const int s = int(chunk % AS);
+                    const uint32_t j = uint32_t(chunk / AS);
+                    if (!mbar_wait(a_full(s), j & 1u, abort_flag, a.status) ||
                         !mbar_wait(bfull(s), j & 1u, abort_flag, a.status)) { ok = false; break; }
                     tc_fence_after();
                     const uint64_t dh = desc_kmajor_sw128(a_hi(s));
@@ -369,7 +399,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                         mma_bf16(dcol, dh + adv, db + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
                         mma_bf16(dcol, dl + adv, db + adv, idesc, 1u);
                     }
-                    mma_commit(empty(s));
+                    mma_commit(a_empty(s));
                     ++chunk;
                 }
                 if (!ok) break;
@@ -384,8 +414,6 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         // ------------------------------------------------------------- epilogue
         const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
         const int l = quad * 32 + lane;            // tile row of this thread
-        float *Lrow = priv;                        // [RP][BM]: per-row weights (narrow tiles)
-        float *Sout = priv + RP * BM;              // [RP][BM]: flushed sums
         const bool lane_weights = g.kcase == 0 && g.narrow && g.n_lmodes > 0;
         Iter it;
         it.init(a);
@@ -394,20 +422,36 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         while (ok && !it.done) {
             const int64_t u = it.u;
             const int64_t ucol = it.col;
+            float *part = a.partial + (u * BM + l) * RP;   // this row's partial sums (thread-private)
+            bool first_flush = true;
             float acc[RP];
             #pragma unroll
-            for (int c = 0; c < RP; ++c) { acc[c] = 0.f; Sout[c * BM + l] = 0.f; }
+            for (int c = 0; c < RP; ++c) acc[c] = 0.f;
+            // fold the register accumulator into the unit's partial row
+            auto flush = [&]() {
+                #pragma unroll
+                for (int c = 0; c < RP; c += 4) {
+                    float4 s = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+                    if (!first_flush) {
+                        const float4 p = *reinterpret_cast<const float4 *>(part + c);
+                        s.x += p.x; s.y += p.y; s.z += p.z; s.w += p.w;
+                    }
+                    *reinterpret_cast<float4 *>(part + c) = s;
+                    acc[c] = acc[c + 1] = acc[c + 2] = acc[c + 3] = 0.f;
+                }
+                first_flush = false;
+            };
             int64_t tile = -1;
             int folded = 0;
             float lw_lane0 = 0.f, lw_lane1 = 0.f;  // lane-independent row weights (wide tiles), columns lane, lane+32
             while (!it.done && it.u == u) {
-                const int64_t rowbase = g.kcase == 0 ? tile_rowbase(g, ucol, it.tile) : 0;
                 if (it.tile != tile) {
                     tile = it.tile;
                     if (lane_weights) {
                         // narrow tile: row l belongs to p = tile*G + l / I_n
                         lw_lane0 = 1.f;
                         lw_lane1 = 1.f;
+                        const int64_t rowbase = tile_rowbase(g, ucol, tile);
                         const bool v = row_valid(g, ucol, rowbase, l);
                         const int64_t p = tile * g.G + l / g.I;
                         #pragma unroll 4
@@ -452,24 +496,18 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 ++fgi;
                 if (++folded == kFoldEvery) {
                     folded = 0;
-                    #pragma unroll
-                    for (int c = 0; c < RP; ++c) { Sout[c * BM + l] += acc[c]; acc[c] = 0.f; }
+                    flush();
                 }
                 for (int kb = 0; kb < g.n_kb; ++kb) it.next(a);  // to the next fiber group
             }
             if (!ok) break;
-            float *part = a.partial + (u * BM + l) * RP;
-            #pragma unroll
-            for (int c = 0; c < RP; c += 4)
-                *reinterpret_cast<float4 *>(part + c) =
-                    make_float4(Sout[c * BM + l] + acc[c], Sout[(c + 1) * BM + l] + acc[c + 1],
-                                Sout[(c + 2) * BM + l] + acc[c + 2], Sout[(c + 3) * BM + l] + acc[c + 3]);
+            flush();
         }
     }
 
     tc_fence_before();
     __syncthreads();
-    if (warp == mma_warp) {
+    if (warp == C::MMA_WARP) {
         tc_fence_after();
         tmem_dealloc(tmem, C::TMEM_COLS);
     }
@@ -509,7 +547,7 @@ int launch_tc_rp(const MttkrpArgs &a, int n_sm, void *stream) {
 
 }  // namespace
 
-size_t mttkrp_tc_smem_bytes(int R_pad) {  // NOLINT
+size_t mttkrp_tc_smem_bytes(int R_pad) {
     switch (R_pad) {
         case 16: return TcCfg<16>::SMEM;
         case 32: return TcCfg<32>::SMEM;

@@ -3,6 +3,8 @@
 // kernels.  Parsing follows the Einstein-notation rules of Sec. III-A
 // (letters repeated across operands are summed, output letters are kept); the
 // accepted patterns are the MTTKRP and TTMc einsums of Sec. III-B / Table IV.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,6 +56,13 @@ struct deinsum_plan_s {
     void *d_bsplit = nullptr;
     int *d_status = nullptr;
     void *d_ttm[2] = {nullptr, nullptr};
+
+    // TMA descriptor of X, re-encoded when X moves
+    CUtensorMap xmap{};
+    const void *xmap_ptr = nullptr;
+    int xmap_ok = 0;
+    uint32_t xmap_box_bytes = 0;
+    int xmap_pitch = 0;
 
     // benchmark timing of the main kernel
     bool timing = false;
@@ -405,6 +414,63 @@ double alg_bytes(const deinsum_plan_s *pl) {
     return es * (x + fac + out);
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tiled tensor map of X for the tensor-core kernel (see MttkrpArgs):
+//   case 0: dims {K_in, O, I, P}, box {64, 1, min(I,128), G}
+//   case 1: dims {I, K_in, O},    box {min(I,128), 64, 1}
+// Needs 16-byte aligned X and rows (vec_ok) and coordinates within int32.
+bool encode_x_map(deinsum_plan_s *pl, const void *X) {
+    if (pl->xmap_ptr == X) return pl->xmap_ok != 0;
+    pl->xmap_ptr = X;
+    pl->xmap_ok = 0;
+    const MttkrpGeom &g = pl->geom;
+    auto enc = tensor_map_encoder();
+    if (!enc || !g.vec_ok || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return false;
+    const int64_t lim = int64_t(1) << 31;
+    cuuint64_t dims[4], strides[3];
+    cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
+    cuuint32_t rank;
+    if (g.kcase == 0) {
+        if (g.K_in >= lim || g.O >= lim || g.I >= lim || g.P >= lim) return false;
+        rank = 4;
+        dims[0] = cuuint64_t(g.K_in); dims[1] = cuuint64_t(g.O); dims[2] = cuuint64_t(g.I); dims[3] = cuuint64_t(g.P);
+        strides[0] = cuuint64_t(g.K_in) * 4; strides[1] = cuuint64_t(g.Q) * 4; strides[2] = cuuint64_t(g.I * g.Q) * 4;
+        box[0] = DEINSUM_BK; box[1] = 1;
+        box[2] = cuuint32_t(g.narrow ? g.I : DEINSUM_BM);
+        box[3] = cuuint32_t(g.narrow ? g.G : 1);
+        pl->xmap_pitch = DEINSUM_BK;
+    } else {
+        if (g.K_in >= lim || g.O >= lim || g.I >= lim) return false;
+        rank = 3;
+        dims[0] = cuuint64_t(g.I); dims[1] = cuuint64_t(g.K_in); dims[2] = cuuint64_t(g.O);
+        strides[0] = cuuint64_t(g.I) * 4; strides[1] = cuuint64_t(g.I * g.K_in) * 4;
+        box[0] = cuuint32_t(std::min<int64_t>(g.I, DEINSUM_BM)); box[1] = DEINSUM_BK; box[2] = 1;
+        pl->xmap_pitch = int(box[0]);
+    }
+    uint64_t bytes = 4;
+    for (cuuint32_t d = 0; d < rank; ++d) bytes *= box[d];
+    pl->xmap_box_bytes = uint32_t(bytes);
+    CUresult r = enc(&pl->xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void *>(X), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    pl->xmap_ok = (r == CUDA_SUCCESS) ? 1 : 0;
+    return pl->xmap_ok != 0;
+}
+
 deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, void *output, void *stream) {
     MttkrpArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -426,6 +492,12 @@ deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, voi
         a.partial = static_cast<float *>(pl->d_partial);
         if (pl->prec == DEINSUM_PREC_SPLIT_BF16) {
             a.Bsplit = pl->d_bsplit;
+            if (encode_x_map(pl, a.X)) {
+                a.xmap = pl->xmap;
+                a.use_tma = 1;
+                a.box_bytes = pl->xmap_box_bytes;
+                a.raw_pitch = pl->xmap_pitch;
+            }
             err = launch_split_inner_factor(a, pl->d_bsplit, stream);
             const long ti = timing_begin(pl, stream);
             if (!err) err = launch_mttkrp_tc(a, pl->n_sm, stream);
