@@ -160,6 +160,24 @@ def cpu_oracle_sample(seed, budget_s: float):
     return covered / spent / 1e9, spent, nrows, cores
 
 
+def run_once(args):
+    """One execute per requested mode (for ncu captures of a small case); prints 'ok'."""
+    import torch
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    n = args.n
+    dims = (n, n, n)
+    X = dz.gen_uniform(2024, inputs.STREAM_X, dims)
+    U = [torch.from_numpy(inputs.factor_normal(2024, m, n, RANK_R, sigma=np.sqrt(1.0 / RANK_R))
+                          .astype(np.float32)).cuda() for m in range(3)]
+    for mode in [int(m) for m in args.modes.split(",")]:
+        p = dz.Plan(dz.mttkrp_einsum(3, mode), list(dims) + [RANK_R], "float32", args.prec)
+        p(X, *[U[m] for m in range(3) if m != mode])
+    torch.cuda.synchronize()
+    print("ok")
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -196,7 +214,13 @@ def main():
     ap.add_argument("--prec", default="split_bf16", choices=["split_bf16", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--once", action="store_true",
+                    help="profiling driver: one execute per mode of --modes at extent --n, no timing")
+    ap.add_argument("--n", type=int, default=N_EXT, help="extent of each mode (--once only)")
+    ap.add_argument("--modes", default="0,1,2", help="modes to run (--once only)")
     args = ap.parse_args()
+    if args.once:
+        return run_once(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
