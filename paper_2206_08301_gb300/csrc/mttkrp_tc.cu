@@ -306,13 +306,11 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         uint32_t bpar = 0, bused = 0;  // per operand stage: parity of the last B copy, copy issued
         for (int64_t chunk = 0; !it.done; ++chunk) {
             float4 v[8];
+            const int rs = int(chunk % RS);
             if (a.use_tma) {
-                const int rs = int(chunk % RS);
                 const uint32_t rj = uint32_t(chunk / RS);
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, a.status))) break;
                 conv_read_smem(a, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(raw_empty(rs));
             } else {
                 conv_read_global(a, it, pt, v);
             }
@@ -326,9 +324,15 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 bused |= 1u << as;
             }
             conv_store(g, pt, a_hi(as), a_lo(as), v);
+            // the proxy fence orders this thread's generic smem accesses (the A
+            // stores, and the raw-tile reads whose values were just consumed)
+            // before the tensor-core reads and the next TMA write of the stages
             fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(a_full(as));
+            if (lane == 0) {
+                mbar_arrive(a_full(as));
+                if (a.use_tma) mbar_arrive(raw_empty(rs));
+            }
             it.next(a);
         }
         if (issuer) {  // every bulk copy into this CTA's smem has landed before exit
