@@ -171,6 +171,44 @@ deinsum_status deinsum_set_kernel_timing(deinsum_plan_t plan, int enable);
 deinsum_status deinsum_kernel_time(deinsum_plan_t plan, double *total_ms, int64_t *launches);
 
 /*
+ * deinsum_mttkrp_noalloc -- split-BF16 MTTKRP that allocates no device memory.
+ *
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc: code whose device memory is owned by another
+ * allocator (a framework's caching allocator that has reserved the HBM
+ * budget), or latency-critical loops that cannot accept the implicit device
+ * synchronisation of cudaMalloc / cudaFree.  It computes the same mode-`mode`
+ * MTTKRP as deinsum_plan + deinsum_execute with DEINSUM_PREC_SPLIT_BF16 and
+ * the same kernels, but keeps its scratch (schedule, per-unit partial sums,
+ * split factor tiles, status word) in one fixed device array of about 9 MiB
+ * inside the library, which every GPU that loads the library holds until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   order, dims  N (2..8) and the extents I_0..I_{N-1} of X (host array).
+ *   mode         the output mode n.
+ *   rank         R, 1..64.
+ *   X            DEVICE pointer, dense row-major float32 tensor.
+ *   factors      HOST array of `order` DEVICE pointers; factors[m] is the
+ *                I_m x R row-major float32 factor (factors[mode] is ignored).
+ *   out          DEVICE pointer to the I_n x R row-major float32 output (overwritten).
+ * Limits of the fixed scratch: I_n <= 32768 (at most 256 blocks of 128 output
+ * rows); the mode contracted on the tensor cores (I_{N-1}, or I_{N-2} when
+ * n = N-1) at most 16384 for R <= 16, 8192 for R <= 32, 4096 for R <= 64.
+ * Larger problems return DEINSUM_ERR_SHAPE without launching anything.
+ * Returns DEINSUM_ERR_INVALID for NULL pointers or a bad order / mode,
+ * DEINSUM_ERR_ALIGN for pointers not 4-byte aligned, DEINSUM_ERR_CUDA when a
+ * launch fails.  The first call on a device looks up that device's address of
+ * the scratch array (with the device current); make that first call before
+ * any stream capture.  Every call shares the one array and leaves its
+ * contents behind (each call clears what must start at zero), so calls that
+ * overlap on the GPU -- on different streams, or from different threads --
+ * race; serialise them.
+ */
+deinsum_status deinsum_mttkrp_noalloc(int order, const int64_t *dims, int mode, int rank,
+                                      const float *X, const float *const *factors, float *out,
+                                      deinsum_stream_t stream);
+
+/*
  * Seeded synthetic inputs on the device.  These implement, bit for bit, the
  * counter-based generator of the project's input module (SplitMix64 by
  * S. Vigna: state0 = mix64(seed + stream_id * 0x9E3779B97F4A7C15), element i is

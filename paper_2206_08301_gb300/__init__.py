@@ -84,6 +84,8 @@ def load():
         lib.deinsum_set_kernel_timing.restype = i32
         lib.deinsum_kernel_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         lib.deinsum_kernel_time.restype = i32
+        lib.deinsum_mttkrp_noalloc.argtypes = [i32, ctypes.POINTER(i64), i32, i32, vp, ctypes.POINTER(vp), vp, vp]
+        lib.deinsum_mttkrp_noalloc.restype = i32
         lib.deinsum_gen_uniform_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, vp, vp]
         lib.deinsum_gen_uniform_f32.restype = i32
         lib.deinsum_gen_uniform_f64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, vp, vp]
@@ -257,6 +259,20 @@ def ttmc(X, factors, keep: int, prec: str = "plain", out=None, stream=None):
     dtype = "float64" if X.dtype == torch.float64 else "float32"
     plan = _cached_plan(spec, extents, dtype, prec)
     return plan(X, *[factors[m] for m in range(order) if m != keep], out=out, stream=stream)
+
+
+def mttkrp_noalloc(X, factors, mode: int, out, stream=None):
+    """Split-BF16 MTTKRP through ``deinsum_mttkrp_noalloc``: the library allocates no
+    device memory for it (its scratch is a fixed array inside the library); the
+    caller provides ``out`` (I_mode x R float32).  Concurrent calls race."""
+    order = X.dim()
+    R = next(f.shape[1] for m, f in enumerate(factors) if m != mode)
+    d = (ctypes.c_int64 * order)(*[int(s) for s in X.shape])
+    fp = (ctypes.c_void_p * order)(*[None if m == mode else _dev_ptr(factors[m], "factor").value
+                                     for m in range(order)])
+    _check(load().deinsum_mttkrp_noalloc(order, d, mode, int(R), _dev_ptr(X, "X"), fp, _dev_ptr(out, "out"),
+                                         _stream_ptr(stream)), "deinsum_mttkrp_noalloc")
+    return out
 
 
 def gen_uniform(seed: int, stream_id: int, shape, dtype=None, device="cuda", stream=None):

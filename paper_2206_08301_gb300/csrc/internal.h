@@ -102,4 +102,8 @@ int launch_ttm_plain_f64(const double *X, const double *U, double *Y, int64_t A,
 
 void count_launch(int n = 1);
 
+// Row view (and TMA descriptor of X when possible) of a one-off split-BF16
+// MTTKRP, computed without heap or device allocation.
+bool mttkrp_prepare_oneoff(int order, const int64_t *dims, int mode, int R, const void *X, MttkrpArgs *a);
+
 }  // namespace deinsum

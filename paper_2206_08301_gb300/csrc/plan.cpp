@@ -541,6 +541,37 @@ deinsum_status execute_ttmc(deinsum_plan_s *pl, const void *const *inputs, void 
 
 }  // namespace
 
+namespace deinsum {
+
+// Row view and TMA descriptor of a one-off split-BF16 MTTKRP, for the entry
+// point that allocates nothing: fills a->g and, when X allows it, a->xmap.
+// Uses a plan object on the stack whose containers stay empty (no heap use).
+bool mttkrp_prepare_oneoff(int order, const int64_t *dims, int mode, int R, const void *X, MttkrpArgs *a) {
+    deinsum_plan_s pl;
+    pl.kind = DEINSUM_KIND_MTTKRP;
+    pl.order = order;
+    pl.mode = mode;
+    pl.dtype = DEINSUM_F32;
+    pl.prec = DEINSUM_PREC_SPLIT_BF16;
+    for (int m = 0; m < order; ++m) {
+        pl.dims[m] = dims[m];
+        pl.ranks[m] = (m == mode) ? dims[m] : R;
+    }
+    build_mttkrp_geometry(&pl);
+    a->g = pl.geom;
+    if ((reinterpret_cast<uintptr_t>(X) & 15) != 0) a->g.vec_ok = 0;
+    a->use_tma = 0;
+    if (encode_x_map(&pl, X)) {
+        a->xmap = pl.xmap;
+        a->use_tma = 1;
+        a->box_bytes = pl.xmap_box_bytes;
+        a->raw_pitch = pl.xmap_pitch;
+    }
+    return true;
+}
+
+}  // namespace deinsum
+
 extern "C" {
 
 deinsum_status deinsum_plan(const char *einsum, const int64_t *extents, int n_extents,
