@@ -171,6 +171,41 @@ deinsum_status deinsum_set_kernel_timing(deinsum_plan_t plan, int enable);
 deinsum_status deinsum_kernel_time(deinsum_plan_t plan, double *total_ms, int64_t *launches);
 
 /*
+ * CP-ALS on the device.  The paper names CP decomposition as the computation
+ * MTTKRP serves (Sec. I); the ALS steps follow Kolda & Bader (SIAM Review
+ * 2009, Sec. 3.4).  Per sweep, for n = 0..N-1 (Gauss-Seidel): M = MTTKRP_n
+ * (this library, `prec`), V = Hadamard of the Grams U_m^T U_m (m != n), U_n
+ * solves U_n V = M by Cholesky, columns normalised to unit 2-norm (norms into
+ * lambda; a zero column keeps lambda = 0), G_n = U_n^T U_n; after the sweep
+ * fit = 1 - ||X - [[lambda; U]]|| / ||X|| from ||X||^2 + ||Xhat||^2 - 2<X, Xhat>.
+ * Grams, Hadamard products, Cholesky, solves, norms and the fit are FP64.
+ */
+typedef struct deinsum_cpals_s *deinsum_cpals_t;
+
+/* Host only: plans the N MTTKRPs of an order-`order` tensor with extents
+ * dims[0..order-1] (host array) and rank `rank` (1..64). */
+deinsum_status deinsum_cpals_create(int order, const int64_t *dims, int rank, deinsum_prec prec,
+                                    deinsum_cpals_t *out);
+
+/* Run `sweeps` ALS sweeps on `stream` (asynchronous).
+ *   X        DEVICE float32 tensor (read only).
+ *   factors  HOST array of `order` DEVICE float32 I_m x rank matrices: the
+ *            initial factors on entry, the (column-normalised) result on exit.
+ *   lambda   DEVICE float64[rank]: the column norms after the last update.
+ *   fits     DEVICE float64[sweeps]: the fit after every sweep.
+ * The first call allocates the handle's workspace (one cudaMalloc). */
+deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const *factors, double *lambda,
+                                 int sweeps, double *fits, deinsum_stream_t stream);
+
+/* After synchronising the stream: DEINSUM_OK, DEINSUM_ERR_TIMEOUT if an MTTKRP
+ * wait gave up, DEINSUM_ERR_INVALID if a Gram-Hadamard matrix was not positive
+ * definite to FP64 precision (its pivot was floored). */
+deinsum_status deinsum_cpals_status(deinsum_cpals_t h);
+
+/* Free the handle, its plans and its workspace.  NULL is ignored. */
+void deinsum_cpals_destroy(deinsum_cpals_t h);
+
+/*
  * deinsum_mttkrp_noalloc -- split-BF16 MTTKRP that allocates no device memory.
  *
  * The paper has no counterpart; this entry point exists for callers that

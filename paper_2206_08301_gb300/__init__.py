@@ -84,6 +84,14 @@ def load():
         lib.deinsum_set_kernel_timing.restype = i32
         lib.deinsum_kernel_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         lib.deinsum_kernel_time.restype = i32
+        lib.deinsum_cpals_create.argtypes = [i32, ctypes.POINTER(i64), i32, i32, ctypes.POINTER(vp)]
+        lib.deinsum_cpals_create.restype = i32
+        lib.deinsum_cpals_run.argtypes = [vp, vp, ctypes.POINTER(vp), vp, i32, vp, vp]
+        lib.deinsum_cpals_run.restype = i32
+        lib.deinsum_cpals_status.argtypes = [vp]
+        lib.deinsum_cpals_status.restype = i32
+        lib.deinsum_cpals_destroy.argtypes = [vp]
+        lib.deinsum_cpals_destroy.restype = None
         lib.deinsum_mttkrp_noalloc.argtypes = [i32, ctypes.POINTER(i64), i32, i32, vp, ctypes.POINTER(vp), vp, vp]
         lib.deinsum_mttkrp_noalloc.restype = i32
         lib.deinsum_gen_uniform_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, vp, vp]
@@ -259,6 +267,48 @@ def ttmc(X, factors, keep: int, prec: str = "plain", out=None, stream=None):
     dtype = "float64" if X.dtype == torch.float64 else "float32"
     plan = _cached_plan(spec, extents, dtype, prec)
     return plan(X, *[factors[m] for m in range(order) if m != keep], out=out, stream=stream)
+
+
+class CPALS:
+    """CP-ALS on the device (``deinsum_cpals_create`` / ``_run`` / ``_status`` / ``_destroy``)."""
+
+    def __init__(self, dims, rank: int, prec: str = "split_bf16"):
+        lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.rank = int(rank)
+        d = (ctypes.c_int64 * len(self.dims))(*self.dims)
+        h = ctypes.c_void_p()
+        _check(lib.deinsum_cpals_create(len(self.dims), d, self.rank, PRECS[prec], ctypes.byref(h)),
+               "deinsum_cpals_create")
+        self._h = h
+
+    def run(self, X, factors, sweeps: int, lam=None, fits=None, stream=None):
+        """Run ``sweeps`` sweeps; ``factors`` (CUDA float32, I_m x R) are updated in place.
+        Returns (lambda, fits) as CUDA float64 tensors."""
+        import torch
+        lib = load()
+        if lam is None:
+            lam = torch.zeros(self.rank, dtype=torch.float64, device=X.device)
+        if fits is None:
+            fits = torch.zeros(sweeps, dtype=torch.float64, device=X.device)
+        fp = (ctypes.c_void_p * len(factors))(*[_dev_ptr(f, "factor").value for f in factors])
+        _check(lib.deinsum_cpals_run(self._h, _dev_ptr(X, "X"), fp, _dev_ptr(lam, "lambda"), int(sweeps),
+                                     _dev_ptr(fits, "fits"), _stream_ptr(stream)), "deinsum_cpals_run")
+        return lam, fits
+
+    def status(self) -> int:
+        return int(load().deinsum_cpals_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.deinsum_cpals_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mttkrp_noalloc(X, factors, mode: int, out, stream=None):

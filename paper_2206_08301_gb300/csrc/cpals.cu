@@ -1,0 +1,377 @@
+// CP-ALS on the device: the decomposition whose bottleneck the paper's MTTKRP
+// serves (Sec. I).  The ALS steps follow Kolda & Bader, "Tensor Decompositions
+// and Applications", SIAM Review 2009, Sec. 3.4: for each mode n in turn
+// (Gauss-Seidel),
+//   M   = MTTKRP_n(X, U)                         (split-BF16 tensor-core kernel)
+//   V   = Hadamard_{m != n} G_m,  G_m = U_m^T U_m    (FP64, R x R)
+//   U_n = M V^{-1}                               (Cholesky of V, FP64 solves per row)
+//   lambda_r = ||U_n[:, r]||_2,  U_n[:, r] /= lambda_r   (FP64 norms)
+//   G_n = U_n^T U_n
+// and after the sweep fit = 1 - sqrt(max(0, ||X||^2 + ||Xhat||^2 - 2 <X, Xhat>)) / ||X||
+// with ||Xhat||^2 = lambda^T (Hadamard_m G_m) lambda and
+// <X, Xhat> = sum_r lambda_r sum_i M_last[i, r] U_last[i, r].
+// Only the MTTKRP runs in (split) FP32; every R x R quantity, the solves, the
+// norms and the fit are FP64.  Everything stays on the device; the host only
+// enqueues kernels.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace deinsum {
+namespace {
+
+constexpr int kMaxR = 64;
+
+// G = U^T U in FP64 (U: I x R float, row-major).  One block per row r1 of G;
+// threads stride over the rows of U, block-reduce each column r2.
+__global__ void gram_kernel(const float *__restrict__ U, int64_t I, int R, double *__restrict__ G) {
+    const int r1 = blockIdx.x;
+    __shared__ double red[kMaxR][33];
+    double acc[kMaxR];
+    for (int r2 = 0; r2 < R; ++r2) acc[r2] = 0.0;
+    for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
+        const double a = double(U[i * R + r1]);
+        for (int r2 = 0; r2 < R; ++r2) acc[r2] += a * double(U[i * R + r2]);
+    }
+    // warp reduce then one value per warp
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r2 = 0; r2 < R; ++r2) {
+        double v = acc[r2];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[r2][warp] = v;
+    }
+    __syncthreads();
+    const int nwarps = blockDim.x >> 5;
+    for (int r2 = threadIdx.x; r2 < R; r2 += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < nwarps; ++w) s += red[r2][w];
+        G[r1 * R + r2] = s;
+    }
+}
+
+// Per block: V = Hadamard of the Grams of every mode except `mode`, its
+// Cholesky factor L (V = L L^T), then for the block's rows i of M the two
+// triangular solves L y = M[i]^T, L^T z = y, written as U_n[i] = z (float).
+// A pivot that is not positive (V singular to FP64 precision) is replaced by
+// the smallest positive pivot scale, and the status word records it.
+__global__ void solve_kernel(const float *__restrict__ M, float *__restrict__ Un, int64_t I, int R,
+                             const double *__restrict__ grams, int order, int mode, int *status) {
+    __shared__ double L[kMaxR][kMaxR + 1];
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        const int a = e / R, b = e % R;
+        double v = 1.0;
+        for (int m = 0; m < order; ++m)
+            if (m != mode) v *= grams[(size_t(m) * R + a) * R + b];
+        L[a][b] = v;
+    }
+    __syncthreads();
+    // in-place Cholesky of the lower triangle, right-looking: per column k the
+    // pivot, the scaled column, then the rank-1 update of the trailing block
+    __shared__ double floor_pivot;
+    if (threadIdx.x == 0) {
+        double dmax = 0.0;
+        for (int k = 0; k < R; ++k) dmax = fmax(dmax, fabs(L[k][k]));
+        floor_pivot = dmax > 0.0 ? dmax * 1e-300 : 1e-300;
+    }
+    __syncthreads();
+    for (int k = 0; k < R; ++k) {
+        if (threadIdx.x == 0) {
+            double d = L[k][k];
+            if (!(d > 0.0)) {
+                d = floor_pivot;
+                atomicOr(status, 2);
+            }
+            L[k][k] = sqrt(d);
+        }
+        __syncthreads();
+        for (int i = k + 1 + int(threadIdx.x); i < R; i += blockDim.x) L[i][k] /= L[k][k];
+        __syncthreads();
+        const int rem = R - k - 1;
+        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+            const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+            if (j <= i) L[i][j] -= L[i][k] * L[j][k];
+        }
+        __syncthreads();
+    }
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < I; i += int64_t(gridDim.x) * blockDim.x) {
+        double y[kMaxR];
+        for (int a = 0; a < R; ++a) {
+            double s = double(M[i * R + a]);
+            for (int p = 0; p < a; ++p) s -= L[a][p] * y[p];
+            y[a] = s / L[a][a];
+        }
+        for (int a = R - 1; a >= 0; --a) {
+            double s = y[a];
+            for (int p = a + 1; p < R; ++p) s -= L[p][a] * y[p];
+            y[a] = s / L[a][a];
+        }
+        for (int a = 0; a < R; ++a) Un[i * R + a] = float(y[a]);
+    }
+}
+
+// lambda_r = ||U[:, r]||_2 in FP64, then U[:, r] /= lambda_r (a zero column keeps lambda = 0).
+__global__ void normalize_kernel(float *__restrict__ U, int64_t I, int R, double *__restrict__ lambda) {
+    const int r = blockIdx.x;
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
+        const double v = double(U[i * R + r]);
+        s += v * v;
+    }
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    __shared__ double nrm;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+        nrm = sqrt(t);
+        lambda[r] = nrm;
+    }
+    __syncthreads();
+    if (nrm > 0.0) {
+        const double inv = 1.0 / nrm;
+        for (int64_t i = threadIdx.x; i < I; i += blockDim.x) U[i * R + r] = float(double(U[i * R + r]) * inv);
+    }
+}
+
+// ||X||^2 in FP64: per-block partial sums, then a single-block finish.
+__global__ void sumsq_partial_kernel(const float *__restrict__ X, int64_t n, double *__restrict__ partial) {
+    double s = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const double v = double(X[i]);
+        s += v * v;
+    }
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void sum_kernel(const double *__restrict__ partial, int n, double *__restrict__ out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+        *out = t;
+    }
+}
+
+// fit after a sweep (one block): inner = sum_r lambda_r sum_i M[i, r] U[i, r]
+// over the last mode; normXhat^2 = lambda^T (Hadamard_m G_m) lambda.
+__global__ void fit_kernel(const float *__restrict__ M, const float *__restrict__ U, int64_t I, int R,
+                           const double *__restrict__ lambda, const double *__restrict__ grams, int order,
+                           const double *__restrict__ normx2, double *__restrict__ fit_out) {
+    __shared__ double red[32];
+    __shared__ double colsum[kMaxR];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = int(blockDim.x >> 5);
+    for (int r = 0; r < R; ++r) {
+        double s = 0.0;
+        for (int64_t i = threadIdx.x; i < I; i += blockDim.x) s += double(M[i * R + r]) * double(U[i * R + r]);
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) red[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += red[w];
+            colsum[r] = t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double inner = 0.0;
+        for (int r = 0; r < R; ++r) inner += lambda[r] * colsum[r];
+        double xhat2 = 0.0;
+        for (int a = 0; a < R; ++a)
+            for (int b = 0; b < R; ++b) {
+                double h = 1.0;
+                for (int m = 0; m < order; ++m) h *= grams[(size_t(m) * R + a) * R + b];
+                xhat2 += lambda[a] * h * lambda[b];
+            }
+        const double res2 = fmax(0.0, *normx2 + xhat2 - 2.0 * inner);
+        *fit_out = 1.0 - sqrt(res2) / sqrt(*normx2);
+    }
+}
+
+}  // namespace
+}  // namespace deinsum
+
+using namespace deinsum;
+
+struct deinsum_cpals_s {
+    int order = 0;
+    int R = 0;
+    int64_t dims[DEINSUM_MAX_ORDER] = {0};
+    deinsum_prec prec = DEINSUM_PREC_SPLIT_BF16;
+    deinsum_plan_t plans[DEINSUM_MAX_ORDER] = {nullptr};
+    int device = -1;
+    char *ws = nullptr;
+    float *M = nullptr;          // max_n I_n x R
+    double *grams = nullptr;     // order x R x R
+    double *normx2 = nullptr;    // 1
+    double *partial = nullptr;   // kSumBlocks
+    int *status = nullptr;       // 1
+};
+
+namespace {
+constexpr int kSumBlocks = 1024;
+
+std::string mttkrp_spec(int order, int mode) {
+    const char *x = "abcdefgh";
+    std::string s(x, size_t(order));
+    for (int m = 0; m < order; ++m)
+        if (m != mode) {
+            s += ',';
+            s += x[m];
+            s += 'r';
+        }
+    s += "->";
+    s += x[mode];
+    s += 'r';
+    return s;
+}
+}  // namespace
+
+extern "C" {
+
+deinsum_status deinsum_cpals_create(int order, const int64_t *dims, int rank, deinsum_prec prec,
+                                    deinsum_cpals_t *out) {
+    if (!out || !dims || order < 2 || order > DEINSUM_MAX_ORDER) return DEINSUM_ERR_INVALID;
+    *out = nullptr;
+    if (rank < 1 || rank > kMaxR) return DEINSUM_ERR_SHAPE;
+    if (prec != DEINSUM_PREC_PLAIN && prec != DEINSUM_PREC_SPLIT_BF16) return DEINSUM_ERR_DTYPE;
+    deinsum_cpals_s *h = new (std::nothrow) deinsum_cpals_s();
+    if (!h) return DEINSUM_ERR_OOM;
+    h->order = order;
+    h->R = rank;
+    h->prec = prec;
+    for (int m = 0; m < order; ++m) {
+        if (dims[m] < 1) { delete h; return DEINSUM_ERR_SHAPE; }
+        h->dims[m] = dims[m];
+    }
+    for (int n = 0; n < order; ++n) {
+        std::vector<int64_t> ext(dims, dims + order);
+        ext.push_back(rank);
+        deinsum_status st = deinsum_plan(mttkrp_spec(order, n).c_str(), ext.data(), order + 1, DEINSUM_F32, prec,
+                                         &h->plans[n]);
+        if (st != DEINSUM_OK) {
+            deinsum_cpals_destroy(h);
+            return st;
+        }
+    }
+    *out = h;
+    return DEINSUM_OK;
+}
+
+deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const *factors, double *lambda,
+                                 int sweeps, double *fits, deinsum_stream_t stream) {
+    if (!h || !X || !factors || !lambda || !fits || sweeps < 1) return DEINSUM_ERR_INVALID;
+    for (int m = 0; m < h->order; ++m)
+        if (!factors[m]) return DEINSUM_ERR_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DEINSUM_ERR_CUDA;
+    const int R = h->R;
+    if (!h->ws) {
+        int64_t imax = 0;
+        for (int m = 0; m < h->order; ++m) imax = h->dims[m] > imax ? h->dims[m] : imax;
+        const size_t bM = (size_t(imax) * R * 4 + 255) / 256 * 256;
+        const size_t bG = (size_t(h->order) * R * R * 8 + 255) / 256 * 256;
+        const size_t total = bM + bG + 256 + size_t(kSumBlocks) * 8 + 256;
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? DEINSUM_ERR_OOM : DEINSUM_ERR_CUDA;
+        }
+        h->ws = static_cast<char *>(p);
+        h->device = dev;
+        h->M = reinterpret_cast<float *>(h->ws);
+        h->grams = reinterpret_cast<double *>(h->ws + bM);
+        h->normx2 = reinterpret_cast<double *>(h->ws + bM + bG);
+        h->status = reinterpret_cast<int *>(h->ws + bM + bG + 8);
+        h->partial = reinterpret_cast<double *>(h->ws + bM + bG + 256);
+    } else if (dev != h->device) {
+        return DEINSUM_ERR_INVALID;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t nx = 1;
+    for (int m = 0; m < h->order; ++m) nx *= h->dims[m];
+    // ||X||^2 and the Grams of the initial factors
+    cudaMemsetAsync(h->status, 0, sizeof(int), s);
+    sumsq_partial_kernel<<<kSumBlocks, 256, 0, s>>>(X, nx, h->partial);
+    sum_kernel<<<1, 256, 0, s>>>(h->partial, kSumBlocks, h->normx2);
+    count_launch(2);
+    for (int m = 0; m < h->order; ++m) {
+        gram_kernel<<<R, 256, 0, s>>>(factors[m], h->dims[m], R, h->grams + size_t(m) * R * R);
+        count_launch();
+    }
+    if (cudaGetLastError() != cudaSuccess) return DEINSUM_ERR_CUDA;
+    std::vector<const void *> ins(size_t(h->order));
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int n = 0; n < h->order; ++n) {
+            ins[0] = X;
+            int k = 1;
+            for (int m = 0; m < h->order; ++m)
+                if (m != n) ins[size_t(k++)] = factors[m];
+            deinsum_status st = deinsum_execute(h->plans[n], ins.data(), h->order, h->M, stream);
+            if (st != DEINSUM_OK) return st;
+            const int64_t I = h->dims[n];
+            int blocks = int((I + 127) / 128);
+            solve_kernel<<<blocks, 128, 0, s>>>(h->M, factors[n], I, R, h->grams, h->order, n, h->status);
+            normalize_kernel<<<R, 256, 0, s>>>(factors[n], I, R, lambda);
+            gram_kernel<<<R, 256, 0, s>>>(factors[n], I, R, h->grams + size_t(n) * R * R);
+            count_launch(3);
+        }
+        const int last = h->order - 1;
+        fit_kernel<<<1, 256, 0, s>>>(h->M, factors[last], h->dims[last], R, lambda, h->grams, h->order, h->normx2,
+                                     fits + sw);
+        count_launch();
+        if (cudaGetLastError() != cudaSuccess) return DEINSUM_ERR_CUDA;
+    }
+    return DEINSUM_OK;
+}
+
+deinsum_status deinsum_cpals_status(deinsum_cpals_t h) {
+    if (!h) return DEINSUM_ERR_INVALID;
+    if (!h->status) return DEINSUM_OK;
+    int v = 0;
+    if (cudaMemcpy(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DEINSUM_ERR_CUDA;
+    for (int n = 0; n < h->order; ++n) {
+        deinsum_status st = deinsum_last_device_status(h->plans[n]);
+        if (st != DEINSUM_OK) return st;
+    }
+    return v == 0 ? DEINSUM_OK : DEINSUM_ERR_INVALID;
+}
+
+void deinsum_cpals_destroy(deinsum_cpals_t h) {
+    if (!h) return;
+    for (int n = 0; n < DEINSUM_MAX_ORDER; ++n)
+        if (h->plans[n]) deinsum_destroy(h->plans[n]);
+    if (h->ws) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != h->device) cudaSetDevice(h->device);
+        cudaFree(h->ws);
+        if (cur != h->device && cur >= 0) cudaSetDevice(cur);
+    }
+    delete h;
+}
+
+}  // extern "C"

@@ -68,7 +68,7 @@ struct MttkrpArgs {
     // TMA descriptor of X for the tensor-core kernel (valid when use_tma != 0):
     //   case 0: 4-D {K_in, O, I, P}, box {64, 1, min(I,128), G}
     //   case 1: 3-D {I, K_in, O},    box {min(I,128), 64, 1}
-    alignas(64) CUtensorMap xmap;
+    CUtensorMap xmap;     // (the type carries its own 128-byte alignment)
     int use_tma;
     uint32_t box_bytes;   // bytes one box load writes (out-of-bounds parts are zero-filled)
     int raw_pitch;        // elements per row of the raw tile in shared memory
