@@ -210,6 +210,110 @@ __global__ void fit_kernel(const float *__restrict__ M, const float *__restrict_
     }
 }
 
+// Direct residual ||X - Xhat||^2 with Xhat = [[lambda; U]]: X is viewed as
+// rows (all modes but the last) x K (the last mode).  A block handles tiles of
+// 64 rows x 64 k: W[row, r] = lambda_r prod_{m < N-1} U_m[i_m(row), r] and the
+// last factor's chunk are staged in shared memory (r-major), each thread forms
+// 4 x 4 reconstructed entries in FP32 (R multiply-adds each), squares the
+// residuals, sums them in FP32 over its tile and adds the tile sum to an FP64
+// per-block partial.  Accurate where the expansion of the fit cancels.
+struct ResidualArgs {
+    const float *X;
+    const float *U[DEINSUM_MAX_ORDER];
+    int64_t dims[DEINSUM_MAX_ORDER];
+    int order, R;
+    const double *lambda;
+    double *partial;  // gridDim.x
+};
+
+__global__ void __launch_bounds__(256) residual_kernel(const ResidualArgs a) {
+    __shared__ float Ws[kMaxR][64 + 4];
+    __shared__ float Cs[kMaxR][64 + 4];
+    __shared__ double red[8];
+    const int R = a.R;
+    const int64_t K = a.dims[a.order - 1];
+    int64_t rows = 1;
+    for (int m = 0; m < a.order - 1; ++m) rows *= a.dims[m];
+    const int64_t rtiles = (rows + 63) / 64, ktiles = (K + 63) / 64;
+    const int t = threadIdx.x, tr = t >> 4, tk = t & 15;
+    const float *C = a.U[a.order - 1];
+    double block_sum = 0.0;
+    for (int64_t tile = blockIdx.x; tile < rtiles * ktiles; tile += gridDim.x) {
+        const int64_t r0 = (tile / ktiles) * 64, k0 = (tile % ktiles) * 64;
+        __syncthreads();
+        for (int e = t; e < 64 * R; e += 256) {
+            const int rl = e / R, r = e % R;
+            const int64_t row = r0 + rl;
+            float w = 0.f;
+            if (row < rows) {
+                double v = a.lambda[r];
+                int64_t rem = row;
+                for (int m = a.order - 2; m >= 0; --m) {
+                    const int64_t i = rem % a.dims[m];
+                    rem /= a.dims[m];
+                    v *= double(a.U[m][i * R + r]);
+                }
+                w = float(v);
+            }
+            Ws[r][rl] = w;
+        }
+        for (int e = t; e < 64 * R; e += 256) {
+            const int kl = e / R, r = e % R;
+            Cs[r][kl] = (k0 + kl < K) ? C[(k0 + kl) * R + r] : 0.f;
+        }
+        __syncthreads();
+        float xh[4][4] = {};
+        for (int r = 0; r < R; ++r) {
+            const float4 w4 = *reinterpret_cast<const float4 *>(&Ws[r][4 * tr]);
+            const float4 c4 = *reinterpret_cast<const float4 *>(&Cs[r][4 * tk]);
+            const float wv[4] = {w4.x, w4.y, w4.z, w4.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w};
+            #pragma unroll
+            for (int i = 0; i < 4; ++i)
+                #pragma unroll
+                for (int j = 0; j < 4; ++j) xh[i][j] = fmaf(wv[i], cv[j], xh[i][j]);
+        }
+        float s = 0.f;
+        #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t row = r0 + 4 * tr + i;
+            if (row >= rows) continue;
+            #pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t k = k0 + 4 * tk + j;
+                if (k < K) {
+                    const float d = a.X[row * K + k] - xh[i][j];
+                    s = fmaf(d, d, s);
+                }
+            }
+        }
+        block_sum += double(s);
+    }
+    for (int off = 16; off > 0; off >>= 1) block_sum += __shfl_down_sync(0xffffffffu, block_sum, off);
+    if ((t & 31) == 0) red[t >> 5] = block_sum;
+    __syncthreads();
+    if (t == 0) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[w];
+        a.partial[blockIdx.x] = v;
+    }
+}
+
+// fit = 1 - sqrt(residual^2) / ||X|| from the summed residual partials (one block).
+__global__ void fit_from_residual_kernel(const double *__restrict__ partial, int n, const double *__restrict__ normx2,
+                                         double *__restrict__ fit_out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+        *fit_out = 1.0 - sqrt(t) / sqrt(*normx2);
+    }
+}
+
 }  // namespace
 }  // namespace deinsum
 
@@ -340,9 +444,28 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
             count_launch(3);
         }
         const int last = h->order - 1;
-        fit_kernel<<<1, 256, 0, s>>>(h->M, factors[last], h->dims[last], R, lambda, h->grams, h->order, h->normx2,
-                                     fits + sw);
-        count_launch();
+        if (sw + 1 < sweeps) {
+            // expansion of the residual from quantities the sweep already has
+            fit_kernel<<<1, 256, 0, s>>>(h->M, factors[last], h->dims[last], R, lambda, h->grams, h->order,
+                                         h->normx2, fits + sw);
+            count_launch();
+        } else {
+            // final fit from the residual itself: the expansion cancels near convergence
+            ResidualArgs ra;
+            std::memset(&ra, 0, sizeof(ra));
+            ra.X = X;
+            for (int m = 0; m < h->order; ++m) {
+                ra.U[m] = factors[m];
+                ra.dims[m] = h->dims[m];
+            }
+            ra.order = h->order;
+            ra.R = R;
+            ra.lambda = lambda;
+            ra.partial = h->partial;
+            residual_kernel<<<kSumBlocks, 256, 0, s>>>(ra);
+            fit_from_residual_kernel<<<1, 256, 0, s>>>(h->partial, kSumBlocks, h->normx2, fits + sw);
+            count_launch(2);
+        }
         if (cudaGetLastError() != cudaSuccess) return DEINSUM_ERR_CUDA;
     }
     return DEINSUM_OK;
