@@ -140,6 +140,19 @@ deinsum_status deinsum_execute(deinsum_plan_t plan, const void *const *inputs, i
  * factor tiles, schedule table, status word).  Host only. */
 deinsum_status deinsum_workspace_size(deinsum_plan_t plan, size_t *bytes);
 
+/* Caller-provided workspace (for runtimes that manage device memory
+ * themselves, e.g. the serving loop below).  deinsum_plan_workspace_bytes
+ * fixes the plan's device (the current one) and schedule and returns the
+ * bytes its workspace needs; deinsum_plan_bind_workspace hands it a DEVICE
+ * buffer of at least that size (1024-byte aligned; DEINSUM_ERR_ALIGN
+ * otherwise, DEINSUM_ERR_SHAPE if too small), uploading the schedule on
+ * `stream`.  A bound workspace stays owned by the caller (deinsum_destroy does
+ * not free it) and must outlive the plan's executions.  Binding is refused
+ * (DEINSUM_ERR_INVALID) once the plan has a workspace. */
+deinsum_status deinsum_plan_workspace_bytes(deinsum_plan_t plan, size_t *bytes);
+deinsum_status deinsum_plan_bind_workspace(deinsum_plan_t plan, void *workspace, size_t bytes,
+                                           deinsum_stream_t stream);
+
 /* Fill *info with the plan summary.  Host only. */
 deinsum_status deinsum_plan_info(deinsum_plan_t plan, deinsum_plan_info_t *info);
 
@@ -201,6 +214,12 @@ deinsum_status deinsum_cpals_create(int order, const int64_t *dims, int rank, de
 deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const *factors, double *lambda,
                                  int sweeps, double *fits, deinsum_stream_t stream);
 
+/* Caller-provided workspace for the handle and its plans (same rules as
+ * deinsum_plan_bind_workspace); without it the first run allocates one. */
+deinsum_status deinsum_cpals_workspace_bytes(deinsum_cpals_t h, size_t *bytes);
+deinsum_status deinsum_cpals_bind_workspace(deinsum_cpals_t h, void *workspace, size_t bytes,
+                                            deinsum_stream_t stream);
+
 /* After synchronising the stream: DEINSUM_OK, DEINSUM_ERR_TIMEOUT if an MTTKRP
  * wait gave up, DEINSUM_ERR_INVALID if a Gram-Hadamard matrix was not positive
  * definite to FP64 precision (its pivot was floored). */
@@ -208,6 +227,69 @@ deinsum_status deinsum_cpals_status(deinsum_cpals_t h);
 
 /* Free the handle, its plans and its workspace.  NULL is ignored. */
 void deinsum_cpals_destroy(deinsum_cpals_t h);
+
+/*
+ * Serving: CP-ALS requests with continuous batching under an HBM budget.
+ * The server owns one device arena of `hbm_budget_bytes` (one cudaMalloc at
+ * creation) and `slots` CUDA streams.  A request waits in a FIFO until a slot
+ * is free and the arena can place its footprint (X, factors, generating
+ * factors, lambda, fits, CP-ALS workspace); on admission its X is generated on
+ * the device from its seed (deinsum_gen_cp_f32), its sweeps are enqueued on the
+ * slot's stream and an event marks the end.  Requests admitted while others
+ * run overlap with them on the device.  deinsum_server_poll retires finished
+ * requests and admits waiting ones; it never waits for running work.  Results
+ * depend only on the request (deterministic kernels), not on what else ran.
+ * The server is not thread-safe; use it from one host thread.
+ */
+typedef struct deinsum_server_s *deinsum_server_t;
+
+typedef struct {
+    int order;                          /* 2..8 */
+    int64_t dims[8];                    /* extents of X */
+    int rank;                           /* CP-ALS rank, 1..64 */
+    int sweeps;                         /* ALS sweeps, 1..4096 */
+    uint64_t seed;                      /* seed of the noise of X */
+    int cp_rank;                        /* rank of the generating CP tensor */
+    double noise;                       /* sigma of the additive noise */
+    const float *const *cp_factors;     /* HOST: `order` float32 I_m x cp_rank generating factors */
+    const float *const *init_factors;   /* HOST: `order` float32 I_m x rank initial factors */
+    double arrival_s;                   /* arrival time on deinsum_server_clock() */
+    int want_factors;                   /* keep the final factors for deinsum_server_take */
+} deinsum_request_t;
+
+typedef struct {
+    int64_t id;
+    int status;                         /* deinsum_status of the request */
+    double arrival_s, admit_s, done_s;  /* deinsum_server_clock() times */
+    double gen_ms;                      /* device time of generating X */
+    int sweeps;
+    double fit;                         /* fit after the last sweep */
+} deinsum_result_t;
+
+/* Steady clock (seconds) the server stamps admission and completion with. */
+double deinsum_server_clock(void);
+
+deinsum_status deinsum_server_create(size_t hbm_budget_bytes, int slots, deinsum_prec prec,
+                                     deinsum_server_t *out);
+
+/* Queue a request (host data is copied); *id identifies it.  Shape errors are
+ * refused here; a request larger than the whole budget finishes with
+ * DEINSUM_ERR_OOM when it reaches the head of the queue. */
+deinsum_status deinsum_server_submit(deinsum_server_t s, const deinsum_request_t *req, int64_t *id);
+
+/* Retire finished requests and admit waiting ones; reports the number of
+ * running and waiting requests. */
+deinsum_status deinsum_server_poll(deinsum_server_t s, int *n_active, int *n_waiting);
+
+/* Copy a finished request's result (and, if non-NULL, its fits[sweeps],
+ * lambda[rank] and -- if it asked for them -- the factors concatenated by mode)
+ * into host buffers and forget it.  DEINSUM_ERR_INVALID if it is unknown or
+ * not finished yet. */
+deinsum_status deinsum_server_take(deinsum_server_t s, int64_t id, deinsum_result_t *res, double *fits,
+                                   double *lambda, float *factors);
+
+/* Wait for running work, free the arena, streams and every request. */
+void deinsum_server_destroy(deinsum_server_t s);
 
 /*
  * deinsum_mttkrp_noalloc -- split-BF16 MTTKRP that allocates no device memory.
@@ -265,14 +347,15 @@ deinsum_status deinsum_gen_uniform_f64(uint64_t seed, uint64_t stream_id, int64_
 
 /*
  * Rank-`rank` CP tensor plus noise, float32, row-major with extents dims[0..order-1]:
- *   out[idx] = f32( sum_{s<rank} prod_{m<order} A_m[i_m, s] + sigma * z(idx) )
- * evaluated in float64 (product over m left to right, sum over s left to right,
- * no fused multiply-add), z(idx) = (sum of the four 16-bit lanes of raw(idx) - 2^17) * sqrt(3) * 2^-16 on stream 2 under `seed`.
- * `factors` is a HOST array of `order` DEVICE pointers to float64 I_m x rank
- * matrices.  order <= 8.
+ *   out[idx] = sum_{s<rank} prod_{m<order} A_m[i_m, s] + f32(sigma) * f32(z(idx))
+ * evaluated in float32 with every multiply and add rounded to nearest (product
+ * over m left to right, sum over s left to right, no fused multiply-add);
+ * z(idx) = (sum of the four 16-bit lanes of raw(idx) - 2^17) * (sqrt(3) * 2^-16),
+ * in float64, on stream 2 under `seed`.  `factors` is a HOST array of `order`
+ * DEVICE pointers to float32 I_m x rank matrices.  order <= 8.
  */
 deinsum_status deinsum_gen_cp_f32(uint64_t seed, int order, const int64_t *dims, int rank,
-                                  const double *const *factors, double sigma, float *out,
+                                  const float *const *factors, double sigma, float *out,
                                   deinsum_stream_t stream);
 
 #ifdef __cplusplus

@@ -49,6 +49,20 @@ class _PlanInfo(ctypes.Structure):
                 ("alg_flops", ctypes.c_double), ("n_units", ctypes.c_int64)]
 
 
+class _Request(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("dims", ctypes.c_int64 * 8), ("rank", ctypes.c_int),
+                ("sweeps", ctypes.c_int), ("seed", ctypes.c_uint64), ("cp_rank", ctypes.c_int),
+                ("noise", ctypes.c_double), ("cp_factors", ctypes.POINTER(ctypes.c_void_p)),
+                ("init_factors", ctypes.POINTER(ctypes.c_void_p)), ("arrival_s", ctypes.c_double),
+                ("want_factors", ctypes.c_int)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int), ("arrival_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double), ("gen_ms", ctypes.c_double),
+                ("sweeps", ctypes.c_int), ("fit", ctypes.c_double)]
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -92,6 +106,22 @@ def load():
         lib.deinsum_cpals_status.restype = i32
         lib.deinsum_cpals_destroy.argtypes = [vp]
         lib.deinsum_cpals_destroy.restype = None
+        lib.deinsum_server_clock.argtypes = []
+        lib.deinsum_server_clock.restype = ctypes.c_double
+        lib.deinsum_server_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)]
+        lib.deinsum_server_create.restype = i32
+        lib.deinsum_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(i64)]
+        lib.deinsum_server_submit.restype = i32
+        lib.deinsum_server_poll.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.deinsum_server_poll.restype = i32
+        lib.deinsum_server_take.argtypes = [vp, i64, ctypes.POINTER(_Result), vp, vp, vp]
+        lib.deinsum_server_take.restype = i32
+        lib.deinsum_server_destroy.argtypes = [vp]
+        lib.deinsum_server_destroy.restype = None
+        lib.deinsum_plan_workspace_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        lib.deinsum_plan_workspace_bytes.restype = i32
+        lib.deinsum_plan_bind_workspace.argtypes = [vp, vp, ctypes.c_size_t, vp]
+        lib.deinsum_plan_bind_workspace.restype = i32
         lib.deinsum_mttkrp_noalloc.argtypes = [i32, ctypes.POINTER(i64), i32, i32, vp, ctypes.POINTER(vp), vp, vp]
         lib.deinsum_mttkrp_noalloc.restype = i32
         lib.deinsum_gen_uniform_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, vp, vp]
@@ -311,6 +341,85 @@ class CPALS:
             pass
 
 
+class Server:
+    """CP-ALS serving loop (``deinsum_server_*``): continuous batching under an HBM budget."""
+
+    def __init__(self, hbm_budget_bytes: int, slots: int, prec: str = "split_bf16"):
+        h = ctypes.c_void_p()
+        _check(load().deinsum_server_create(int(hbm_budget_bytes), int(slots), PRECS[prec], ctypes.byref(h)),
+               "deinsum_server_create")
+        self._h = h
+        self._keep = {}
+
+    @staticmethod
+    def clock() -> float:
+        return float(load().deinsum_server_clock())
+
+    def submit(self, dims, rank, sweeps, seed, cp_factors, init_factors, noise=0.0, arrival=None,
+               want_factors=False) -> int:
+        """Queue one request; ``cp_factors`` / ``init_factors`` are host float32 arrays (I_m x rank)."""
+        import numpy as np
+        order = len(dims)
+        cpf = [np.ascontiguousarray(f, dtype=np.float32) for f in cp_factors]
+        ini = [np.ascontiguousarray(f, dtype=np.float32) for f in init_factors]
+        q = _Request()
+        q.order = order
+        for m, d in enumerate(dims):
+            q.dims[m] = int(d)
+        q.rank, q.sweeps, q.seed = int(rank), int(sweeps), int(seed)
+        q.cp_rank = int(cpf[0].shape[1])
+        q.noise = float(noise)
+        cp_arr = (ctypes.c_void_p * order)(*[f.ctypes.data for f in cpf])
+        in_arr = (ctypes.c_void_p * order)(*[f.ctypes.data for f in ini])
+        q.cp_factors = ctypes.cast(cp_arr, ctypes.POINTER(ctypes.c_void_p))
+        q.init_factors = ctypes.cast(in_arr, ctypes.POINTER(ctypes.c_void_p))
+        q.arrival_s = self.clock() if arrival is None else float(arrival)
+        q.want_factors = int(bool(want_factors))
+        rid = ctypes.c_int64()
+        _check(load().deinsum_server_submit(self._h, ctypes.byref(q), ctypes.byref(rid)), "deinsum_server_submit")
+        self._keep[rid.value] = (tuple(int(d) for d in dims), int(rank), int(sweeps), bool(want_factors))
+        return rid.value
+
+    def poll(self):
+        a, w = ctypes.c_int(), ctypes.c_int()
+        _check(load().deinsum_server_poll(self._h, ctypes.byref(a), ctypes.byref(w)), "deinsum_server_poll")
+        return a.value, w.value
+
+    def take(self, rid: int):
+        """Result of a finished request as a dict, or None if it has not finished."""
+        import numpy as np
+        dims, rank, sweeps, want = self._keep[rid]
+        res = _Result()
+        fits = np.zeros(sweeps)
+        lam = np.zeros(rank)
+        fac = np.zeros(sum(d * rank for d in dims), dtype=np.float32) if want else None
+        st = load().deinsum_server_take(self._h, rid, ctypes.byref(res), fits.ctypes.data, lam.ctypes.data,
+                                        fac.ctypes.data if want else None)
+        if st != 0:
+            return None
+        del self._keep[rid]
+        out = {"id": res.id, "status": res.status, "arrival": res.arrival_s, "admit": res.admit_s,
+               "done": res.done_s, "gen_ms": res.gen_ms, "fit": res.fit, "fits": fits, "lambda": lam}
+        if want:
+            parts, o = [], 0
+            for d in dims:
+                parts.append(fac[o:o + d * rank].reshape(d, rank))
+                o += d * rank
+            out["factors"] = parts
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.deinsum_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def mttkrp_noalloc(X, factors, mode: int, out, stream=None):
     """Split-BF16 MTTKRP through ``deinsum_mttkrp_noalloc``: the library allocates no
     device memory for it (its scratch is a fixed array inside the library); the
@@ -337,9 +446,11 @@ def gen_uniform(seed: int, stream_id: int, shape, dtype=None, device="cuda", str
 
 
 def gen_cp(seed: int, dims, cp_factors, sigma: float, device="cuda", stream=None):
-    """Device float32 CP-plus-noise tensor; ``cp_factors`` are float64 CUDA tensors (I_m x rank)."""
+    """Device float32 CP-plus-noise tensor; ``cp_factors`` are CUDA tensors (I_m x rank),
+    rounded to float32 here if they are not float32 already."""
     import torch
     order = len(dims)
+    cp_factors = [f.to(torch.float32).contiguous() for f in cp_factors]
     t = torch.empty(tuple(dims), dtype=torch.float32, device=device)
     d = (ctypes.c_int64 * order)(*[int(x) for x in dims])
     fp = (ctypes.c_void_p * order)(*[_dev_ptr(f, "cp factor").value for f in cp_factors])

@@ -327,6 +327,7 @@ struct deinsum_cpals_s {
     deinsum_plan_t plans[DEINSUM_MAX_ORDER] = {nullptr};
     int device = -1;
     char *ws = nullptr;
+    bool ws_owned = true;
     float *M = nullptr;          // max_n I_n x R
     double *grams = nullptr;     // order x R x R
     double *normx2 = nullptr;    // 1
@@ -336,6 +337,33 @@ struct deinsum_cpals_s {
 
 namespace {
 constexpr int kSumBlocks = 1024;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// The handle's own workspace: M (max_n I_n x R float), the Grams (N x R x R
+// double), ||X||^2, the status word, the FP64 partial sums.
+size_t cpals_own_bytes(const deinsum_cpals_s *h) {
+    int64_t imax = 0;
+    for (int m = 0; m < h->order; ++m) imax = h->dims[m] > imax ? h->dims[m] : imax;
+    const size_t bM = round_up(size_t(imax) * h->R * 4, 256);
+    const size_t bG = round_up(size_t(h->order) * h->R * h->R * 8, 256);
+    return round_up(bM + bG + 256 + size_t(kSumBlocks) * 8, 1024);
+}
+
+void cpals_attach_own(deinsum_cpals_s *h, char *p, bool owned, int dev) {
+    int64_t imax = 0;
+    for (int m = 0; m < h->order; ++m) imax = h->dims[m] > imax ? h->dims[m] : imax;
+    const size_t bM = round_up(size_t(imax) * h->R * 4, 256);
+    const size_t bG = round_up(size_t(h->order) * h->R * h->R * 8, 256);
+    h->ws = p;
+    h->ws_owned = owned;
+    h->device = dev;
+    h->M = reinterpret_cast<float *>(h->ws);
+    h->grams = reinterpret_cast<double *>(h->ws + bM);
+    h->normx2 = reinterpret_cast<double *>(h->ws + bM + bG);
+    h->status = reinterpret_cast<int *>(h->ws + bM + bG + 8);
+    h->partial = reinterpret_cast<double *>(h->ws + bM + bG + 256);
+}
 
 std::string mttkrp_spec(int order, int mode) {
     const char *x = "abcdefgh";
@@ -393,24 +421,13 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
     if (cudaGetDevice(&dev) != cudaSuccess) return DEINSUM_ERR_CUDA;
     const int R = h->R;
     if (!h->ws) {
-        int64_t imax = 0;
-        for (int m = 0; m < h->order; ++m) imax = h->dims[m] > imax ? h->dims[m] : imax;
-        const size_t bM = (size_t(imax) * R * 4 + 255) / 256 * 256;
-        const size_t bG = (size_t(h->order) * R * R * 8 + 255) / 256 * 256;
-        const size_t total = bM + bG + 256 + size_t(kSumBlocks) * 8 + 256;
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, total);
+        cudaError_t e = cudaMalloc(&p, cpals_own_bytes(h));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? DEINSUM_ERR_OOM : DEINSUM_ERR_CUDA;
         }
-        h->ws = static_cast<char *>(p);
-        h->device = dev;
-        h->M = reinterpret_cast<float *>(h->ws);
-        h->grams = reinterpret_cast<double *>(h->ws + bM);
-        h->normx2 = reinterpret_cast<double *>(h->ws + bM + bG);
-        h->status = reinterpret_cast<int *>(h->ws + bM + bG + 8);
-        h->partial = reinterpret_cast<double *>(h->ws + bM + bG + 256);
+        cpals_attach_own(h, static_cast<char *>(p), true, dev);
     } else if (dev != h->device) {
         return DEINSUM_ERR_INVALID;
     }
@@ -471,6 +488,42 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
     return DEINSUM_OK;
 }
 
+deinsum_status deinsum_cpals_workspace_bytes(deinsum_cpals_t h, size_t *bytes) {
+    if (!h || !bytes) return DEINSUM_ERR_INVALID;
+    size_t total = cpals_own_bytes(h);
+    for (int n = 0; n < h->order; ++n) {
+        size_t b = 0;
+        deinsum_status st = deinsum_plan_workspace_bytes(h->plans[n], &b);
+        if (st != DEINSUM_OK) return st;
+        total += round_up(b, 1024);
+    }
+    *bytes = total;
+    return DEINSUM_OK;
+}
+
+deinsum_status deinsum_cpals_bind_workspace(deinsum_cpals_t h, void *workspace, size_t bytes,
+                                            deinsum_stream_t stream) {
+    if (!h || !workspace || h->ws) return DEINSUM_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(workspace) & 1023) return DEINSUM_ERR_ALIGN;
+    size_t need = 0;
+    deinsum_status st = deinsum_cpals_workspace_bytes(h, &need);
+    if (st != DEINSUM_OK) return st;
+    if (bytes < need) return DEINSUM_ERR_SHAPE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DEINSUM_ERR_CUDA;
+    char *p = static_cast<char *>(workspace);
+    cpals_attach_own(h, p, false, dev);
+    size_t off = cpals_own_bytes(h);
+    for (int n = 0; n < h->order; ++n) {
+        size_t b = 0;
+        deinsum_plan_workspace_bytes(h->plans[n], &b);
+        st = deinsum_plan_bind_workspace(h->plans[n], p + off, b, stream);
+        if (st != DEINSUM_OK) return st;
+        off += round_up(b, 1024);
+    }
+    return DEINSUM_OK;
+}
+
 deinsum_status deinsum_cpals_status(deinsum_cpals_t h) {
     if (!h) return DEINSUM_ERR_INVALID;
     if (!h->status) return DEINSUM_OK;
@@ -487,7 +540,7 @@ void deinsum_cpals_destroy(deinsum_cpals_t h) {
     if (!h) return;
     for (int n = 0; n < DEINSUM_MAX_ORDER; ++n)
         if (h->plans[n]) deinsum_destroy(h->plans[n]);
-    if (h->ws) {
+    if (h->ws && h->ws_owned) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (cur != h->device) cudaSetDevice(h->device);

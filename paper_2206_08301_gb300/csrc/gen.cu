@@ -46,12 +46,12 @@ __global__ void gen_uniform_f64_kernel(uint64_t s0, int64_t n, double *out) {
 struct CpArgs {
     int order, rank;
     int64_t dims[DEINSUM_MAX_ORDER];
-    const double *A[DEINSUM_MAX_ORDER];
-    double sigma;
+    const float *A[DEINSUM_MAX_ORDER];
+    float sigma;
     uint64_t noise_s0;
 };
 
-// X[idx] = f32( sum_s prod_m A_m[i_m, s] + sigma * z(idx) ), each double
+// X[idx] = sum_s prod_m A_m[i_m, s] + sigma * f32(z(idx)), each float
 // operation explicitly rounded (no contraction into FMA), in the order the
 // input module states.
 __global__ void gen_cp_f32_kernel(const __grid_constant__ CpArgs a, int64_t n, float *out) {
@@ -62,19 +62,19 @@ __global__ void gen_cp_f32_kernel(const __grid_constant__ CpArgs a, int64_t n, f
             idx[m] = rem % a.dims[m];
             rem /= a.dims[m];
         }
-        double acc = 0.0;
+        float acc = 0.f;
         for (int s = 0; s < a.rank; ++s) {
-            double term = a.A[0][idx[0] * a.rank + s];
-            for (int m = 1; m < a.order; ++m) term = __dmul_rn(term, a.A[m][idx[m] * a.rank + s]);
-            acc = __dadd_rn(acc, term);
+            float term = a.A[0][idx[0] * a.rank + s];
+            for (int m = 1; m < a.order; ++m) term = __fmul_rn(term, a.A[m][idx[m] * a.rank + s]);
+            acc = __fadd_rn(acc, term);
         }
-        if (a.sigma != 0.0) {
+        if (a.sigma != 0.f) {
             const uint64_t r = raw(a.noise_s0, uint64_t(i));
             const uint64_t sum = (r & 0xFFFFull) + ((r >> 16) & 0xFFFFull) + ((r >> 32) & 0xFFFFull) + (r >> 48);
-            const double z = __dmul_rn(double(int64_t(sum) - (int64_t(1) << 17)), kNoiseScale);
-            acc = __dadd_rn(acc, __dmul_rn(a.sigma, z));
+            const float z = __double2float_rn(__dmul_rn(double(int64_t(sum) - (int64_t(1) << 17)), kNoiseScale));
+            acc = __fadd_rn(acc, __fmul_rn(a.sigma, z));
         }
-        out[i] = __double2float_rn(acc);
+        out[i] = acc;
     }
 }
 
@@ -111,7 +111,7 @@ deinsum_status deinsum_gen_uniform_f64(uint64_t seed, uint64_t stream_id, int64_
 }
 
 deinsum_status deinsum_gen_cp_f32(uint64_t seed, int order, const int64_t *dims, int rank,
-                                  const double *const *factors, double sigma, float *out,
+                                  const float *const *factors, double sigma, float *out,
                                   deinsum_stream_t stream) {
     if (order < 1 || order > DEINSUM_MAX_ORDER || rank < 1 || !dims || !factors || !out)
         return DEINSUM_ERR_INVALID;
@@ -125,7 +125,7 @@ deinsum_status deinsum_gen_cp_f32(uint64_t seed, int order, const int64_t *dims,
         a.A[m] = factors[m];
         n *= dims[m];
     }
-    a.sigma = sigma;
+    a.sigma = float(sigma);  // rounded to nearest, as the input module does
     a.noise_s0 = state0(seed, 2);  // the noise stream of the input module
     gen_cp_f32_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(a, n, out);
     count_launch();

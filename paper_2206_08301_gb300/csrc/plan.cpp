@@ -49,6 +49,7 @@ struct deinsum_plan_s {
     int device = -1;
     int n_sm = 0;
     char *ws = nullptr;
+    bool ws_owned = true;
     size_t ws_bytes = 0;
     int64_t *d_units = nullptr;
     int64_t *d_col_begin = nullptr;
@@ -233,74 +234,100 @@ deinsum_status cuda_status(cudaError_t e) {
     return DEINSUM_ERR_CUDA;
 }
 
-// Allocate the workspace on the current device and upload the schedule.
-deinsum_status ensure_device_state(deinsum_plan_s *pl) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return DEINSUM_ERR_CUDA;
-    if (pl->ws && pl->device == dev) return DEINSUM_OK;
-    if (pl->ws) return DEINSUM_ERR_INVALID;  // a plan stays on its first device
-    int nsm = 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
-        return DEINSUM_ERR_CUDA;
-    pl->device = dev;
-    pl->n_sm = nsm;
+struct WsLayout {
+    size_t status = 0, units = 0, cols = 0, partial = 0, bsplit = 0, ttm0 = 0, ttm1 = 0, total = 0;
+};
 
+// Fix the device (the current one), the schedule (one unit per resident CTA:
+// the tensor-core kernel keeps one CTA per SM, the plain kernel as many as its
+// occupancy allows) and the workspace layout.
+deinsum_status plan_layout(deinsum_plan_s *pl, WsLayout &L) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DEINSUM_ERR_CUDA;
+    if (pl->device >= 0 && pl->device != dev) return DEINSUM_ERR_INVALID;  // a plan stays on its first device
+    if (pl->n_sm == 0) {
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+            return DEINSUM_ERR_CUDA;
+        pl->device = dev;
+        pl->n_sm = nsm;
+        if (pl->kind == DEINSUM_KIND_MTTKRP) {
+            int per_sm = 1;
+            if (pl->prec == DEINSUM_PREC_PLAIN)
+                per_sm = mttkrp_plain_ctas_per_sm(pl->dtype == DEINSUM_F64 ? 1 : 0, pl->geom.R_pad);
+            build_schedule(pl, int64_t(nsm) * per_sm);
+        }
+    }
     size_t off = 0;
-    size_t o_units = 0, o_cols = 0, o_partial = 0, o_bsplit = 0, o_ttm0 = 0, o_ttm1 = 0;
-    size_t o_status = off;
+    L.status = off;
     off = align_up(off + 256, 256);
     if (pl->kind == DEINSUM_KIND_MTTKRP) {
-        // one unit per resident CTA: the tensor-core kernel keeps one CTA per SM,
-        // the plain kernel as many as its occupancy allows
-        int per_sm = 1;
-        if (pl->prec == DEINSUM_PREC_PLAIN)
-            per_sm = mttkrp_plain_ctas_per_sm(pl->dtype == DEINSUM_F64 ? 1 : 0, pl->geom.R_pad);
-        build_schedule(pl, int64_t(nsm) * per_sm);
         const MttkrpGeom &g = pl->geom;
-        o_units = off;
+        L.units = off;
         off = align_up(off + pl->units.size() * sizeof(int64_t), 256);
-        o_cols = off;
+        L.cols = off;
         off = align_up(off + pl->col_unit_begin.size() * sizeof(int64_t), 256);
-        o_partial = off;
+        L.partial = off;
         off = align_up(off + size_t(pl->planned_units) * DEINSUM_BM * g.R_pad * elem_size(pl->dtype), 1024);
         if (pl->prec == DEINSUM_PREC_SPLIT_BF16) {
-            o_bsplit = off;
+            L.bsplit = off;
             off = align_up(off + size_t(g.n_kb) * 2 * g.R_pad * DEINSUM_BK * 2, 1024);
         }
     } else {
-        o_ttm0 = off;
+        L.ttm0 = off;
         off = align_up(off + size_t(pl->ttm_buf_elems) * elem_size(pl->dtype), 256);
-        o_ttm1 = off;
+        L.ttm1 = off;
         off = align_up(off + size_t(pl->ttm_buf_elems) * elem_size(pl->dtype), 256);
     }
+    L.total = off;
+    return DEINSUM_OK;
+}
+
+// Point the plan at workspace `ws` (>= the layout's bytes; 1024-byte aligned)
+// and upload the schedule and a cleared status word on `stream`.
+deinsum_status attach_workspace(deinsum_plan_s *pl, char *ws, const WsLayout &L, bool owned, cudaStream_t stream) {
+    pl->ws = ws;
+    pl->ws_owned = owned;
+    pl->ws_bytes = L.total;
+    pl->d_status = reinterpret_cast<int *>(pl->ws + L.status);
+    cudaError_t e = cudaMemsetAsync(pl->d_status, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (pl->kind == DEINSUM_KIND_MTTKRP) {
+        pl->d_units = reinterpret_cast<int64_t *>(pl->ws + L.units);
+        pl->d_col_begin = reinterpret_cast<int64_t *>(pl->ws + L.cols);
+        pl->d_partial = pl->ws + L.partial;
+        pl->d_bsplit = pl->prec == DEINSUM_PREC_SPLIT_BF16 ? pl->ws + L.bsplit : nullptr;
+        e = cudaMemcpyAsync(pl->d_units, pl->units.data(), pl->units.size() * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pl->d_col_begin, pl->col_unit_begin.data(),
+                                pl->col_unit_begin.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    } else {
+        pl->d_ttm[0] = pl->ws + L.ttm0;
+        pl->d_ttm[1] = pl->ws + L.ttm1;
+    }
+    return DEINSUM_OK;
+}
+
+// Allocate the workspace on the current device and upload the schedule.
+deinsum_status ensure_device_state(deinsum_plan_s *pl, cudaStream_t stream) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DEINSUM_ERR_CUDA;
+    if (pl->ws && pl->device == dev) return DEINSUM_OK;
+    if (pl->ws) return DEINSUM_ERR_INVALID;  // a plan stays on its first device
+    WsLayout L;
+    deinsum_status st = plan_layout(pl, L);
+    if (st != DEINSUM_OK) return st;
     void *ws = nullptr;
-    e = cudaMalloc(&ws, off);
+    cudaError_t e = cudaMalloc(&ws, L.total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_status(e);
     }
-    pl->ws = static_cast<char *>(ws);
-    pl->ws_bytes = off;
-    pl->d_status = reinterpret_cast<int *>(pl->ws + o_status);
-    e = cudaMemset(pl->d_status, 0, sizeof(int));
-    if (e != cudaSuccess) return cuda_status(e);
-    if (pl->kind == DEINSUM_KIND_MTTKRP) {
-        pl->d_units = reinterpret_cast<int64_t *>(pl->ws + o_units);
-        pl->d_col_begin = reinterpret_cast<int64_t *>(pl->ws + o_cols);
-        pl->d_partial = pl->ws + o_partial;
-        pl->d_bsplit = pl->prec == DEINSUM_PREC_SPLIT_BF16 ? pl->ws + o_bsplit : nullptr;
-        e = cudaMemcpy(pl->d_units, pl->units.data(), pl->units.size() * sizeof(int64_t),
-                       cudaMemcpyHostToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(pl->d_col_begin, pl->col_unit_begin.data(),
-                           pl->col_unit_begin.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return cuda_status(e);
-    } else {
-        pl->d_ttm[0] = pl->ws + o_ttm0;
-        pl->d_ttm[1] = pl->ws + o_ttm1;
-    }
-    return DEINSUM_OK;
+    st = attach_workspace(pl, static_cast<char *>(ws), L, true, stream);
+    if (st == DEINSUM_OK && cudaStreamSynchronize(stream) != cudaSuccess) st = DEINSUM_ERR_CUDA;
+    return st;
 }
 
 deinsum_status classify(deinsum_plan_s *pl, const Parsed &p, const int64_t *extents) {
@@ -620,7 +647,7 @@ deinsum_status deinsum_execute(deinsum_plan_t pl, const void *const *inputs, int
         if (reinterpret_cast<uintptr_t>(inputs[k]) % es) return DEINSUM_ERR_ALIGN;
     }
     if (reinterpret_cast<uintptr_t>(output) % es) return DEINSUM_ERR_ALIGN;
-    deinsum_status st = ensure_device_state(pl);
+    deinsum_status st = ensure_device_state(pl, static_cast<cudaStream_t>(stream));
     if (st != DEINSUM_OK) return st;
     if (pl->kind == DEINSUM_KIND_MTTKRP) return execute_mttkrp(pl, inputs, output, stream);
     return execute_ttmc(pl, inputs, output, stream);
@@ -630,6 +657,26 @@ deinsum_status deinsum_workspace_size(deinsum_plan_t pl, size_t *bytes) {
     if (!pl || !bytes) return DEINSUM_ERR_INVALID;
     *bytes = pl->ws_bytes;
     return DEINSUM_OK;
+}
+
+deinsum_status deinsum_plan_workspace_bytes(deinsum_plan_t pl, size_t *bytes) {
+    if (!pl || !bytes) return DEINSUM_ERR_INVALID;
+    WsLayout L;
+    deinsum_status st = plan_layout(pl, L);
+    if (st != DEINSUM_OK) return st;
+    *bytes = L.total;
+    return DEINSUM_OK;
+}
+
+deinsum_status deinsum_plan_bind_workspace(deinsum_plan_t pl, void *workspace, size_t bytes, deinsum_stream_t stream) {
+    if (!pl || !workspace) return DEINSUM_ERR_INVALID;
+    if (pl->ws) return DEINSUM_ERR_INVALID;  // already has a workspace
+    if (reinterpret_cast<uintptr_t>(workspace) & 1023) return DEINSUM_ERR_ALIGN;
+    WsLayout L;
+    deinsum_status st = plan_layout(pl, L);
+    if (st != DEINSUM_OK) return st;
+    if (bytes < L.total) return DEINSUM_ERR_SHAPE;
+    return attach_workspace(pl, static_cast<char *>(workspace), L, false, static_cast<cudaStream_t>(stream));
 }
 
 deinsum_status deinsum_plan_info(deinsum_plan_t pl, deinsum_plan_info_t *info) {
@@ -693,7 +740,7 @@ void deinsum_destroy(deinsum_plan_t pl) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
     }
-    if (pl->ws) {
+    if (pl->ws && pl->ws_owned) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (cur != pl->device) cudaSetDevice(pl->device);

@@ -34,11 +34,12 @@ bit for bit):
 
 Synthetic CP tensor
 -------------------
-``X[idx] = f32( sum_s prod_m A_m[i_m, s]  +  sigma * noise_z(idx) )``
-evaluated in float64 with the product taken over m = 0..N-1 left to right,
-the sum over s = 0..R-1 left to right, no fused multiply-add, then rounded to
-nearest float32.  numpy evaluates it with separate multiplies and adds, and
-the device kernel uses explicitly rounded double operations in the same order.
+``X[idx] = sum_s prod_m a_m[i_m, s]  +  f32(sigma) * f32(noise_z(idx))``
+evaluated in float32 (a_m = the generating factors rounded to float32) with
+every multiply and add rounded to nearest: the product over m = 0..N-1 left
+to right, the sum over s = 0..R-1 left to right, no fused multiply-add.
+numpy evaluates it with separate float32 multiplies and adds, and the device
+kernel uses explicitly rounded float32 operations in the same order.
 """
 from __future__ import annotations
 
@@ -152,20 +153,21 @@ def flat_index(dims, coords) -> np.ndarray:
 def cp_values(dims, cp_factors, sigma: float, seed: int, coords) -> np.ndarray:
     """Entries of the synthetic CP-plus-noise tensor at coordinate arrays ``coords``.
 
-    ``cp_factors[m]`` is the float64 generating factor of mode m (I_m x Rc).
-    Evaluated exactly as the module docstring states.
+    ``cp_factors[m]`` is the generating factor of mode m (I_m x Rc), rounded to
+    float32.  Evaluated exactly as the module docstring states.
     """
+    A = [np.asarray(f, dtype=np.float32) for f in cp_factors]
     shape = np.broadcast(*coords).shape
-    rc = cp_factors[0].shape[1]
-    acc = np.zeros(shape, dtype=np.float64)
+    rc = A[0].shape[1]
+    acc = np.zeros(shape, dtype=np.float32)
     for s in range(rc):
-        term = cp_factors[0][np.asarray(coords[0]), s]
+        term = A[0][np.asarray(coords[0]), s]
         for m in range(1, len(dims)):
-            term = term * cp_factors[m][np.asarray(coords[m]), s]
+            term = term * A[m][np.asarray(coords[m]), s]
         acc = acc + term
     if sigma != 0.0:
-        z = noise_z(seed, STREAM_NOISE, flat_index(dims, coords))
-        acc = acc + np.float64(sigma) * z
+        z = noise_z(seed, STREAM_NOISE, flat_index(dims, coords)).astype(np.float32)
+        acc = acc + np.float32(sigma) * z
     return acc.astype(np.float32)
 
 
@@ -176,25 +178,26 @@ def cp_slab(seed: int, dims, cp_factors, sigma: float, mode: int, row: int) -> n
     product over modes is still formed left to right in mode order (the fixed
     index enters as a scalar at its position) and the sum over s left to right.
     """
+    A = [np.asarray(f, dtype=np.float32) for f in cp_factors]
     order = len(dims)
-    rc = cp_factors[0].shape[1]
+    rc = A[0].shape[1]
     shape = tuple(d for m, d in enumerate(dims) if m != mode)
-    acc = np.zeros(shape, dtype=np.float64)
+    acc = np.zeros(shape, dtype=np.float32)
     for s in range(rc):
         term = None
         for m in range(order):
             if m == mode:
-                v = cp_factors[m][row, s]
-                term = np.float64(v) if term is None else term * v
+                v = A[m][row, s]
+                term = np.float32(v) if term is None else term * v
             else:
-                col = cp_factors[m][:, s]
+                col = A[m][:, s]
                 term = col.copy() if term is None else np.multiply.outer(term, col)
         acc = acc + term
     if sigma != 0.0:
         coords = np.meshgrid(*[np.arange(d) if m != mode else np.array([row]) for m, d in enumerate(dims)],
                              indexing="ij", sparse=True)
         flat = flat_index(dims, coords).reshape(shape)
-        acc = acc + np.float64(sigma) * noise_z(seed, STREAM_NOISE, flat)
+        acc = acc + np.float32(sigma) * noise_z(seed, STREAM_NOISE, flat).astype(np.float32)
     return acc.astype(np.float32)
 
 
