@@ -178,6 +178,87 @@ def run_once(args):
     return 0
 
 
+def _serving_requests(n, seed):
+    """Synthetic CP-ALS requests: extents U{64..1024} per mode, R U{8..64}, rank-R CP
+    tensor with N(0,1) factors + 1e-2 noise, 10 sweeps, N(0,1) initial factors."""
+    from paper_2206_08301_gb300 import inputs
+    ext = inputs.draw_int(seed, 0, 64, 1024, 3 * n).reshape(n, 3)
+    ranks = inputs.draw_int(seed, 1, 8, 64, n)
+    reqs = []
+    for k in range(n):
+        dims = tuple(int(d) for d in ext[k])
+        R = int(ranks[k])
+        s = seed * 100003 + k
+        cpf = [inputs.factor_normal(s, m, d, R, stream_base=inputs.STREAM_CP).astype(np.float32)
+               for m, d in enumerate(dims)]
+        ini = [inputs.factor_normal(s, m, d, R, stream_base=inputs.STREAM_INIT).astype(np.float32)
+               for m, d in enumerate(dims)]
+        reqs.append(dict(dims=dims, rank=R, sweeps=10, seed=s, cp_factors=cpf, init_factors=ini, noise=1e-2))
+    return reqs
+
+
+def _serve_run(reqs, slots, prec, rate, budget, seed):
+    """Serve `reqs` with Poisson arrivals at `rate` req/s (None: all at t=0).
+    Returns (makespan s, latencies s, gen ms, statuses, fits)."""
+    import paper_2206_08301_gb300 as dz
+    srv = dz.Server(budget, slots, prec)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
+    t0 = srv.clock()
+    arrivals = t0 + np.cumsum(gaps)
+    ids, out, nxt = [], {}, 0
+    while len(out) < len(reqs):
+        now = srv.clock()
+        while nxt < len(reqs) and arrivals[nxt] <= now:
+            ids.append(srv.submit(arrival=float(arrivals[nxt]), **reqs[nxt]))
+            nxt += 1
+        srv.poll()
+        for i in ids:
+            if i not in out:
+                r = srv.take(i)
+                if r is not None:
+                    out[i] = r
+    srv.close()
+    res = [out[i] for i in ids]
+    lat = np.array([r["done"] - r["arrival"] for r in res])
+    span = max(r["done"] for r in res) - t0
+    return span, lat, np.array([r["gen_ms"] for r in res]), [r["status"] for r in res], [r["fit"] for r in res]
+
+
+def run_serving(args):
+    """CP-ALS serving: continuous batching (4 slots, split-BF16) under Poisson arrivals at
+    0.5/0.8/1.0/1.2x the measured one-at-a-time split-BF16 service rate, against one-at-a-time
+    plain FP32 solves (1 slot) at the same arrival rate."""
+    import torch
+    budget = 64 << 30
+    reqs = _serving_requests(args.requests, 7)
+    torch.cuda.synchronize()
+    _serve_run(reqs[:8], 1, "split_bf16", None, budget, 1)            # warm-up
+    span1, lat1, _, st1, _ = _serve_run(reqs, 1, "split_bf16", None, budget, 1)
+    mu = len(reqs) / span1
+    rows = []
+    for f in (0.5, 0.8, 1.0, 1.2):
+        span, lat, gen, st, fits = _serve_run(reqs, 4, "split_bf16", f * mu, budget, 11)
+        rows.append({"load": f, "arrival_rate": f * mu, "req_s": len(reqs) / span,
+                     "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                     "gen_ms_mean": float(gen.mean()), "ok": int(sum(s == 0 for s in st)),
+                     "fit_min": float(min(fits))})
+    spanp, latp, _, stp, _ = _serve_run(reqs, 1, "plain", mu, budget, 11)
+    line = {"metric": "CP-ALS serving req/s and p50/p99 latency", "unit": "req/s", "n_gpus": 1,
+            "requests": len(reqs), "sweeps": 10, "data": "synthetic",
+            "config": {"workload": "Poisson CP-ALS requests: extents U{64..1024}, R U{8..64}, rank-R CP N(0,1) "
+                                   "+ 1e-2 noise, 10 sweeps, X generated on the device per request",
+                       "hbm_budget_gb": budget / 2 ** 30, "slots": 4},
+            "one_at_a_time_split": {"req_s": mu, "p50_ms": 1e3 * float(np.percentile(lat1, 50)),
+                                    "p99_ms": 1e3 * float(np.percentile(lat1, 99))},
+            "continuous_batching_split": rows,
+            "one_at_a_time_plain_at_rate_mu": {"req_s": len(reqs) / spanp,
+                                               "p50_ms": 1e3 * float(np.percentile(latp, 50)),
+                                               "p99_ms": 1e3 * float(np.percentile(latp, 99))}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -218,9 +299,14 @@ def main():
                     help="profiling driver: one execute per mode of --modes at extent --n, no timing")
     ap.add_argument("--n", type=int, default=N_EXT, help="extent of each mode (--once only)")
     ap.add_argument("--modes", default="0,1,2", help="modes to run (--once only)")
+    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving"],
+                    help="mttkrp: the benchmark line; serving: the CP-ALS serving measurement")
+    ap.add_argument("--requests", type=int, default=128, help="requests of the serving workload")
     args = ap.parse_args()
     if args.once:
         return run_once(args)
+    if args.workload == "serving" and args.impl == "native":
+        return run_serving(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
