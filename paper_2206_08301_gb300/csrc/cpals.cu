@@ -30,40 +30,30 @@ namespace {
 constexpr int kMaxR = 64;
 
 // G = U^T U in FP64 (U: I x R float, row-major).  One block per row r1 of G;
-// threads stride over the rows of U, block-reduce each column r2.
-__global__ void gram_kernel(const float *__restrict__ U, int64_t I, int R, double *__restrict__ G) {
+// thread (r2, slice) sums rows slice, slice + 4, ... of U[i, r1] U[i, r2].
+__global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ U, int64_t I, int R,
+                                                   double *__restrict__ G) {
     const int r1 = blockIdx.x;
-    __shared__ double red[kMaxR][33];
-    double acc[kMaxR];
-    for (int r2 = 0; r2 < R; ++r2) acc[r2] = 0.0;
-    for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
-        const double a = double(U[i * R + r1]);
-        for (int r2 = 0; r2 < R; ++r2) acc[r2] += a * double(U[i * R + r2]);
-    }
-    // warp reduce then one value per warp
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r2 = 0; r2 < R; ++r2) {
-        double v = acc[r2];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) red[r2][warp] = v;
-    }
+    const int r2 = threadIdx.x & 63, sl = threadIdx.x >> 6;
+    __shared__ double red[4][64];
+    double acc = 0.0;
+    if (r2 < R)
+        for (int64_t i = sl; i < I; i += 4) acc += double(U[i * R + r1]) * double(U[i * R + r2]);
+    red[sl][r2] = acc;
     __syncthreads();
-    const int nwarps = blockDim.x >> 5;
-    for (int r2 = threadIdx.x; r2 < R; r2 += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < nwarps; ++w) s += red[r2][w];
-        G[r1 * R + r2] = s;
-    }
+    if (sl == 0 && r2 < R) G[r1 * R + r2] = (red[0][r2] + red[1][r2]) + (red[2][r2] + red[3][r2]);
 }
 
-// Per block: V = Hadamard of the Grams of every mode except `mode`, its
-// Cholesky factor L (V = L L^T), then for the block's rows i of M the two
-// triangular solves L y = M[i]^T, L^T z = y, written as U_n[i] = z (float).
-// A pivot that is not positive (V singular to FP64 precision) is replaced by
-// the smallest positive pivot scale, and the status word records it.
-__global__ void solve_kernel(const float *__restrict__ M, float *__restrict__ Un, int64_t I, int R,
-                             const double *__restrict__ grams, int order, int mode, int *status) {
-    __shared__ double L[kMaxR][kMaxR + 1];
+// One block: V = Hadamard of the Grams of every mode except `mode`, its
+// Cholesky factor L (V = L L^T), then W = V^{-1} = L^{-T} L^{-1}, written to
+// global memory for apply_kernel.  A pivot that is not positive (V singular
+// to FP64 precision) is replaced by a tiny positive value and the status word
+// records it.
+__global__ void __launch_bounds__(256) inverse_kernel(const double *__restrict__ grams, int order, int mode, int R,
+                                                      double *__restrict__ W, int *status) {
+    extern __shared__ double inv_smem[];   // L and L^{-1}, kMaxR x (kMaxR + 1) each
+    double(*L)[kMaxR + 1] = reinterpret_cast<double(*)[kMaxR + 1]>(inv_smem);
+    double(*Li)[kMaxR + 1] = reinterpret_cast<double(*)[kMaxR + 1]>(inv_smem + kMaxR * (kMaxR + 1));
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         const int a = e / R, b = e % R;
         double v = 1.0;
@@ -100,19 +90,39 @@ __global__ void solve_kernel(const float *__restrict__ M, float *__restrict__ Un
         }
         __syncthreads();
     }
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < I; i += int64_t(gridDim.x) * blockDim.x) {
-        double y[kMaxR];
-        for (int a = 0; a < R; ++a) {
-            double s = double(M[i * R + a]);
-            for (int p = 0; p < a; ++p) s -= L[a][p] * y[p];
-            y[a] = s / L[a][a];
+    // column j of L^{-1} by forward substitution (one thread per column)
+    for (int j = threadIdx.x; j < R; j += blockDim.x) {
+        for (int i = 0; i < j; ++i) Li[i][j] = 0.0;
+        for (int i = j; i < R; ++i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int p = j; p < i; ++p) s -= L[i][p] * Li[p][j];
+            Li[i][j] = s / L[i][i];
         }
-        for (int a = R - 1; a >= 0; --a) {
-            double s = y[a];
-            for (int p = a + 1; p < R; ++p) s -= L[p][a] * y[p];
-            y[a] = s / L[a][a];
-        }
-        for (int a = 0; a < R; ++a) Un[i * R + a] = float(y[a]);
+    }
+    __syncthreads();
+    // W = L^{-T} L^{-1}: W[a][b] = sum_{p >= max(a, b)} Li[p][a] Li[p][b]
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        const int a = e / R, b = e % R;
+        double s = 0.0;
+        for (int p = a > b ? a : b; p < R; ++p) s += Li[p][a] * Li[p][b];
+        W[e] = s;
+    }
+}
+
+// U_n[i, b] = sum_a M[i, a] W[a, b]  (FP64 products of the FP32 MTTKRP rows, rounded once to FP32).
+__global__ void __launch_bounds__(256) apply_kernel(const float *__restrict__ M, const double *__restrict__ W,
+                                                    float *__restrict__ Un, int64_t I, int R) {
+    __shared__ double Ws[kMaxR * kMaxR];
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ws[e] = W[e];
+    __syncthreads();
+    const int64_t n = I * R;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = e / R;
+        const int b = int(e - i * R);
+        const float *m = M + i * R;
+        double s = 0.0;
+        for (int a = 0; a < R; ++a) s += double(m[a]) * Ws[a * R + b];
+        Un[e] = float(s);
     }
 }
 
@@ -332,11 +342,13 @@ struct deinsum_cpals_s {
     double *grams = nullptr;     // order x R x R
     double *normx2 = nullptr;    // 1
     double *partial = nullptr;   // kSumBlocks
+    double *W = nullptr;         // R x R inverse of the Gram-Hadamard matrix
     int *status = nullptr;       // 1
 };
 
 namespace {
 constexpr int kSumBlocks = 1024;
+constexpr size_t kInvSmem = size_t(2) * kMaxR * (kMaxR + 1) * sizeof(double);
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -347,7 +359,7 @@ size_t cpals_own_bytes(const deinsum_cpals_s *h) {
     for (int m = 0; m < h->order; ++m) imax = h->dims[m] > imax ? h->dims[m] : imax;
     const size_t bM = round_up(size_t(imax) * h->R * 4, 256);
     const size_t bG = round_up(size_t(h->order) * h->R * h->R * 8, 256);
-    return round_up(bM + bG + 256 + size_t(kSumBlocks) * 8, 1024);
+    return round_up(bM + bG + 256 + size_t(kSumBlocks) * 8 + size_t(h->R) * h->R * 8, 1024);
 }
 
 void cpals_attach_own(deinsum_cpals_s *h, char *p, bool owned, int dev) {
@@ -363,6 +375,7 @@ void cpals_attach_own(deinsum_cpals_s *h, char *p, bool owned, int dev) {
     h->normx2 = reinterpret_cast<double *>(h->ws + bM + bG);
     h->status = reinterpret_cast<int *>(h->ws + bM + bG + 8);
     h->partial = reinterpret_cast<double *>(h->ws + bM + bG + 256);
+    h->W = h->partial + kSumBlocks;
 }
 
 std::string mttkrp_spec(int order, int mode) {
@@ -432,6 +445,9 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
         return DEINSUM_ERR_INVALID;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kInvSmem)) !=
+        cudaSuccess)
+        return DEINSUM_ERR_CUDA;
     int64_t nx = 1;
     for (int m = 0; m < h->order; ++m) nx *= h->dims[m];
     // ||X||^2 and the Grams of the initial factors
@@ -454,11 +470,13 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
             deinsum_status st = deinsum_execute(h->plans[n], ins.data(), h->order, h->M, stream);
             if (st != DEINSUM_OK) return st;
             const int64_t I = h->dims[n];
-            int blocks = int((I + 127) / 128);
-            solve_kernel<<<blocks, 128, 0, s>>>(h->M, factors[n], I, R, h->grams, h->order, n, h->status);
+            inverse_kernel<<<1, 256, kInvSmem, s>>>(h->grams, h->order, n, R, h->W, h->status);
+            int blocks = int((I * R + 255) / 256);
+            if (blocks > 1024) blocks = 1024;
+            apply_kernel<<<blocks, 256, 0, s>>>(h->M, h->W, factors[n], I, R);
             normalize_kernel<<<R, 256, 0, s>>>(factors[n], I, R, lambda);
             gram_kernel<<<R, 256, 0, s>>>(factors[n], I, R, h->grams + size_t(n) * R * R);
-            count_launch(3);
+            count_launch(4);
         }
         const int last = h->order - 1;
         if (sw + 1 < sweeps) {

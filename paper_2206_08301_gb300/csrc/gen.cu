@@ -54,27 +54,53 @@ struct CpArgs {
 // X[idx] = sum_s prod_m A_m[i_m, s] + sigma * f32(z(idx)), each float
 // operation explicitly rounded (no contraction into FMA), in the order the
 // input module states.
-__global__ void gen_cp_f32_kernel(const __grid_constant__ CpArgs a, int64_t n, float *out) {
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+// Each thread owns 4 consecutive entries of one row (all modes but the last
+// fixed): the row's partial products w[s] = A_0[i_0, s] * ... * A_{N-2}[i_{N-2}, s]
+// are formed once (the same left-to-right products the definition forms),
+// then every entry multiplies them by the last factor's row and sums over s.
+constexpr int kGenMaxRank = 64;
+
+__global__ void __launch_bounds__(256) gen_cp_f32_kernel(const __grid_constant__ CpArgs a, int64_t n, float *out) {
+    const int N = a.order, R = a.rank;
+    const int64_t K = a.dims[N - 1];
+    const int64_t kq = (K + 3) / 4;
+    const int64_t chunks = (n / K) * kq;
+    const float *Alast = a.A[N - 1];
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < chunks; c += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t row = c / kq;
+        const int64_t k0 = (c - row * kq) * 4;
         int64_t idx[DEINSUM_MAX_ORDER];
-        int64_t rem = i;
-        for (int m = a.order - 1; m >= 0; --m) {
+        int64_t rem = row;
+        for (int m = N - 2; m >= 0; --m) {
             idx[m] = rem % a.dims[m];
             rem /= a.dims[m];
         }
-        float acc = 0.f;
-        for (int s = 0; s < a.rank; ++s) {
-            float term = a.A[0][idx[0] * a.rank + s];
-            for (int m = 1; m < a.order; ++m) term = __fmul_rn(term, a.A[m][idx[m] * a.rank + s]);
-            acc = __fadd_rn(acc, term);
+        float w[kGenMaxRank];
+        #pragma unroll
+        for (int s = 0; s < kGenMaxRank; ++s) {
+            if (s < R && N > 1) {
+                float t = a.A[0][idx[0] * R + s];
+                for (int m = 1; m < N - 1; ++m) t = __fmul_rn(t, a.A[m][idx[m] * R + s]);
+                w[s] = t;
+            }
         }
-        if (a.sigma != 0.f) {
-            const uint64_t r = raw(a.noise_s0, uint64_t(i));
-            const uint64_t sum = (r & 0xFFFFull) + ((r >> 16) & 0xFFFFull) + ((r >> 32) & 0xFFFFull) + (r >> 48);
-            const float z = __double2float_rn(__dmul_rn(double(int64_t(sum) - (int64_t(1) << 17)), kNoiseScale));
-            acc = __fadd_rn(acc, __fmul_rn(a.sigma, z));
+        for (int q = 0; q < 4; ++q) {
+            const int64_t k = k0 + q;
+            if (k >= K) break;
+            const float *ar = Alast + k * R;
+            float acc = 0.f;
+            #pragma unroll
+            for (int s = 0; s < kGenMaxRank; ++s)
+                if (s < R) acc = __fadd_rn(acc, N > 1 ? __fmul_rn(w[s], __ldg(ar + s)) : __ldg(ar + s));
+            const int64_t i = row * K + k;
+            if (a.sigma != 0.f) {
+                const uint64_t r = raw(a.noise_s0, uint64_t(i));
+                const uint64_t sum = (r & 0xFFFFull) + ((r >> 16) & 0xFFFFull) + ((r >> 32) & 0xFFFFull) + (r >> 48);
+                const float z = __double2float_rn(__dmul_rn(double(int64_t(sum) - (int64_t(1) << 17)), kNoiseScale));
+                acc = __fadd_rn(acc, __fmul_rn(a.sigma, z));
+            }
+            out[i] = acc;
         }
-        out[i] = acc;
     }
 }
 
@@ -115,6 +141,7 @@ deinsum_status deinsum_gen_cp_f32(uint64_t seed, int order, const int64_t *dims,
                                   deinsum_stream_t stream) {
     if (order < 1 || order > DEINSUM_MAX_ORDER || rank < 1 || !dims || !factors || !out)
         return DEINSUM_ERR_INVALID;
+    if (rank > kGenMaxRank) return DEINSUM_ERR_SHAPE;
     CpArgs a{};
     a.order = order;
     a.rank = rank;
