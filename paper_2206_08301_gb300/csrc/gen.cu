@@ -60,46 +60,70 @@ struct CpArgs {
 // then every entry multiplies them by the last factor's row and sums over s.
 constexpr int kGenMaxRank = 64;
 
+// Tiles of 16 rows x 64 entries of the last mode: blockIdx.x picks the
+// 64-wide chunk k, whose last-factor rows are staged once (As[s][k]); the
+// block then walks row tiles, forms the rows' partial products into
+// ws[s][row], and thread (row group, k) produces 4 rows x 1 entry.
+constexpr int kGenRows = 16, kGenK = 64;
+
 __global__ void __launch_bounds__(256) gen_cp_f32_kernel(const __grid_constant__ CpArgs a, int64_t n, float *out) {
+    extern __shared__ float gsm[];
     const int N = a.order, R = a.rank;
+    float *As = gsm;                       // [R][kGenK]
+    float *ws = gsm + R * kGenK;           // [R][kGenRows]
     const int64_t K = a.dims[N - 1];
-    const int64_t kq = (K + 3) / 4;
-    const int64_t chunks = (n / K) * kq;
+    const int64_t rows = n / K;
+    const int64_t k0 = int64_t(blockIdx.x) * kGenK;
     const float *Alast = a.A[N - 1];
-    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < chunks; c += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t row = c / kq;
-        const int64_t k0 = (c - row * kq) * 4;
-        int64_t idx[DEINSUM_MAX_ORDER];
-        int64_t rem = row;
-        for (int m = N - 2; m >= 0; --m) {
-            idx[m] = rem % a.dims[m];
-            rem /= a.dims[m];
-        }
-        float w[kGenMaxRank];
-        #pragma unroll
-        for (int s = 0; s < kGenMaxRank; ++s) {
-            if (s < R && N > 1) {
-                float t = a.A[0][idx[0] * R + s];
+    for (int e = threadIdx.x; e < R * kGenK; e += blockDim.x) {
+        const int s = e / kGenK, kk = e % kGenK;
+        As[e] = (k0 + kk < K) ? Alast[(k0 + kk) * R + s] : 0.f;
+    }
+    const int kk = threadIdx.x & (kGenK - 1), rg = threadIdx.x >> 6;   // rows 4 rg .. 4 rg + 3
+    const int64_t k = k0 + kk;
+    const int64_t rtiles = (rows + kGenRows - 1) / kGenRows;
+    for (int64_t rt = blockIdx.y; rt < rtiles; rt += gridDim.y) {
+        const int64_t r0 = rt * kGenRows;
+        __syncthreads();
+        for (int e = threadIdx.x; e < R * kGenRows; e += blockDim.x) {
+            const int s = e / kGenRows, rl = e % kGenRows;
+            const int64_t row = r0 + rl;
+            float t = 1.f;
+            if (row < rows && N > 1) {
+                int64_t idx[DEINSUM_MAX_ORDER];
+                int64_t rem = row;
+                for (int m = N - 2; m >= 0; --m) {
+                    idx[m] = rem % a.dims[m];
+                    rem /= a.dims[m];
+                }
+                t = a.A[0][idx[0] * R + s];
                 for (int m = 1; m < N - 1; ++m) t = __fmul_rn(t, a.A[m][idx[m] * R + s]);
-                w[s] = t;
             }
+            ws[e] = t;
         }
-        for (int q = 0; q < 4; ++q) {
-            const int64_t k = k0 + q;
-            if (k >= K) break;
-            const float *ar = Alast + k * R;
-            float acc = 0.f;
+        __syncthreads();
+        if (k >= K) continue;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int s = 0; s < R; ++s) {
+            const float4 w4 = *reinterpret_cast<const float4 *>(ws + s * kGenRows + 4 * rg);
+            const float av = As[s * kGenK + kk];
+            const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
             #pragma unroll
-            for (int s = 0; s < kGenMaxRank; ++s)
-                if (s < R) acc = __fadd_rn(acc, N > 1 ? __fmul_rn(w[s], __ldg(ar + s)) : __ldg(ar + s));
+            for (int q = 0; q < 4; ++q) acc[q] = __fadd_rn(acc[q], N > 1 ? __fmul_rn(wv[q], av) : av);
+        }
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t row = r0 + 4 * rg + q;
+            if (row >= rows) break;
             const int64_t i = row * K + k;
+            float v = acc[q];
             if (a.sigma != 0.f) {
                 const uint64_t r = raw(a.noise_s0, uint64_t(i));
                 const uint64_t sum = (r & 0xFFFFull) + ((r >> 16) & 0xFFFFull) + ((r >> 32) & 0xFFFFull) + (r >> 48);
                 const float z = __double2float_rn(__dmul_rn(double(int64_t(sum) - (int64_t(1) << 17)), kNoiseScale));
-                acc = __fadd_rn(acc, __fmul_rn(a.sigma, z));
+                v = __fadd_rn(v, __fmul_rn(a.sigma, z));
             }
-            out[i] = acc;
+            out[i] = v;
         }
     }
 }
@@ -154,7 +178,16 @@ deinsum_status deinsum_gen_cp_f32(uint64_t seed, int order, const int64_t *dims,
     }
     a.sigma = float(sigma);  // rounded to nearest, as the input module does
     a.noise_s0 = state0(seed, 2);  // the noise stream of the input module
-    gen_cp_f32_kernel<<<grid_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(a, n, out);
+    const int64_t K = dims[order - 1];
+    const int64_t ktiles = (K + kGenK - 1) / kGenK;
+    const int64_t rtiles = (n / K + kGenRows - 1) / kGenRows;
+    int64_t gy = (int64_t(152) * 8 + ktiles - 1) / ktiles;
+    if (gy > rtiles) gy = rtiles;
+    if (gy > 65535) gy = 65535;
+    if (gy < 1) gy = 1;
+    if (ktiles > 0x7FFFFFFF) return DEINSUM_ERR_SHAPE;
+    const size_t smem = size_t(rank) * (kGenK + kGenRows) * sizeof(float);
+    gen_cp_f32_kernel<<<dim3(unsigned(ktiles), unsigned(gy)), 256, smem, static_cast<cudaStream_t>(stream)>>>(a, n, out);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DEINSUM_OK : DEINSUM_ERR_CUDA;
 }

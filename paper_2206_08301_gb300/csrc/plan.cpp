@@ -207,7 +207,8 @@ void build_schedule(deinsum_plan_s *pl, int64_t target) {
     const MttkrpGeom &g = pl->geom;
     pl->units.clear();
     pl->col_unit_begin.assign(size_t(g.n_cols + 1), 0);
-    int64_t per_col = std::max<int64_t>(1, (target + g.n_cols - 1) / g.n_cols);
+    // at most `target` units (one wave of resident CTAs) unless there are more columns
+    int64_t per_col = std::max<int64_t>(1, target / g.n_cols);
     per_col = std::min<int64_t>(per_col, g.fg_per_col);
     for (int64_t c = 0; c < g.n_cols; ++c) {
         pl->col_unit_begin[size_t(c)] = int64_t(pl->units.size() / 3);
