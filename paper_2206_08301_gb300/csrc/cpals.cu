@@ -36,9 +36,21 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ U, 
     const int r1 = blockIdx.x;
     const int r2 = threadIdx.x & 63, sl = threadIdx.x >> 6;
     __shared__ double red[4][64];
+    // FP32 partial sums of 8 products, accumulated in FP64 (the FP64 pipe is narrow)
     double acc = 0.0;
-    if (r2 < R)
-        for (int64_t i = sl; i < I; i += 4) acc += double(U[i * R + r1]) * double(U[i * R + r2]);
+    if (r2 < R) {
+        float part = 0.f;
+        int cnt = 0;
+        for (int64_t i = sl; i < I; i += 4) {
+            part = fmaf(U[i * R + r1], U[i * R + r2], part);
+            if (++cnt == 8) {
+                acc += double(part);
+                part = 0.f;
+                cnt = 0;
+            }
+        }
+        acc += double(part);
+    }
     red[sl][r2] = acc;
     __syncthreads();
     if (sl == 0 && r2 < R) G[r1 * R + r2] = (red[0][r2] + red[1][r2]) + (red[2][r2] + red[3][r2]);
@@ -90,13 +102,17 @@ __global__ void __launch_bounds__(256) inverse_kernel(const double *__restrict__
         }
         __syncthreads();
     }
-    // column j of L^{-1} by forward substitution (one thread per column)
-    for (int j = threadIdx.x; j < R; j += blockDim.x) {
-        for (int i = 0; i < j; ++i) Li[i][j] = 0.0;
-        for (int i = j; i < R; ++i) {
-            double s = (i == j) ? 1.0 : 0.0;
-            for (int p = j; p < i; ++p) s -= L[i][p] * Li[p][j];
-            Li[i][j] = s / L[i][i];
+    // L^{-1} by elimination on [L | I], all threads per step: row k of the
+    // right-hand side is divided by L[k][k], then removed from the rows below
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) Li[e / R][e % R] = (e / R == e % R) ? 1.0 : 0.0;
+    for (int k = 0; k < R; ++k) {
+        __syncthreads();
+        for (int j = threadIdx.x; j <= k; j += blockDim.x) Li[k][j] /= L[k][k];
+        __syncthreads();
+        const int rows_below = R - k - 1;
+        for (int e = threadIdx.x; e < rows_below * (k + 1); e += blockDim.x) {
+            const int i = k + 1 + e / (k + 1), j = e % (k + 1);
+            Li[i][j] -= L[i][k] * Li[k][j];
         }
     }
     __syncthreads();
@@ -131,9 +147,19 @@ __global__ void normalize_kernel(float *__restrict__ U, int64_t I, int R, double
     const int r = blockIdx.x;
     __shared__ double red[32];
     double s = 0.0;
-    for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
-        const double v = double(U[i * R + r]);
-        s += v * v;
+    {
+        float part = 0.f;
+        int cnt = 0;
+        for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
+            const float v = U[i * R + r];
+            part = fmaf(v, v, part);
+            if (++cnt == 16) {
+                s += double(part);
+                part = 0.f;
+                cnt = 0;
+            }
+        }
+        s += double(part);
     }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -155,9 +181,20 @@ __global__ void normalize_kernel(float *__restrict__ U, int64_t I, int R, double
 // ||X||^2 in FP64: per-block partial sums, then a single-block finish.
 __global__ void sumsq_partial_kernel(const float *__restrict__ X, int64_t n, double *__restrict__ partial) {
     double s = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        const double v = double(X[i]);
-        s += v * v;
+    {
+        float part = 0.f;
+        int cnt = 0;
+        for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+             i += int64_t(gridDim.x) * blockDim.x) {
+            const float v = X[i];
+            part = fmaf(v, v, part);
+            if (++cnt == 16) {
+                s += double(part);
+                part = 0.f;
+                cnt = 0;
+            }
+        }
+        s += double(part);
     }
     __shared__ double red[32];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
@@ -189,33 +226,48 @@ __global__ void sum_kernel(const double *__restrict__ partial, int n, double *__
 __global__ void fit_kernel(const float *__restrict__ M, const float *__restrict__ U, int64_t I, int R,
                            const double *__restrict__ lambda, const double *__restrict__ grams, int order,
                            const double *__restrict__ normx2, double *__restrict__ fit_out) {
-    __shared__ double red[32];
-    __shared__ double colsum[kMaxR];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = int(blockDim.x >> 5);
-    for (int r = 0; r < R; ++r) {
-        double s = 0.0;
-        for (int64_t i = threadIdx.x; i < I; i += blockDim.x) s += double(M[i * R + r]) * double(U[i * R + r]);
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-        if (lane == 0) red[warp] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < nw; ++w) t += red[w];
-            colsum[r] = t;
+    // blockDim = 256: thread (r = tid % 64, slice = tid / 64) sums rows slice,
+    // slice + 4, ... of M[i, r] U[i, r] (FP32 partials of 8, FP64 accumulation);
+    // every thread also takes a share of the R x R terms of ||Xhat||^2
+    __shared__ double red[4][64];
+    __shared__ double xr[256];
+    const int r = threadIdx.x & 63, sl = threadIdx.x >> 6;
+    double acc = 0.0;
+    if (r < R) {
+        float part = 0.f;
+        int cnt = 0;
+        for (int64_t i = sl; i < I; i += 4) {
+            part = fmaf(M[i * R + r], U[i * R + r], part);
+            if (++cnt == 8) {
+                acc += double(part);
+                part = 0.f;
+                cnt = 0;
+            }
         }
+        acc += double(part);
+        acc *= lambda[r];
+    }
+    red[sl][r] = acc;
+    double xh = 0.0;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        const int a = e / R, b = e % R;
+        double h = lambda[a] * lambda[b];
+        for (int m = 0; m < order; ++m) h *= grams[(size_t(m) * R + a) * R + b];
+        xh += h;
+    }
+    xr[threadIdx.x] = xh;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (int(threadIdx.x) < w) xr[threadIdx.x] += xr[threadIdx.x + w];
         __syncthreads();
     }
+    if (threadIdx.x < 64) red[0][threadIdx.x] = (red[0][threadIdx.x] + red[1][threadIdx.x]) +
+                                                 (red[2][threadIdx.x] + red[3][threadIdx.x]);
+    __syncthreads();
     if (threadIdx.x == 0) {
         double inner = 0.0;
-        for (int r = 0; r < R; ++r) inner += lambda[r] * colsum[r];
-        double xhat2 = 0.0;
-        for (int a = 0; a < R; ++a)
-            for (int b = 0; b < R; ++b) {
-                double h = 1.0;
-                for (int m = 0; m < order; ++m) h *= grams[(size_t(m) * R + a) * R + b];
-                xhat2 += lambda[a] * h * lambda[b];
-            }
-        const double res2 = fmax(0.0, *normx2 + xhat2 - 2.0 * inner);
+        for (int q = 0; q < R; ++q) inner += red[0][q];
+        const double res2 = fmax(0.0, *normx2 + xr[0] - 2.0 * inner);
         *fit_out = 1.0 - sqrt(res2) / sqrt(*normx2);
     }
 }
