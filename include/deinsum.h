@@ -184,6 +184,48 @@ deinsum_status deinsum_set_kernel_timing(deinsum_plan_t plan, int enable);
 deinsum_status deinsum_kernel_time(deinsum_plan_t plan, double *total_ms, int64_t *launches);
 
 /*
+ * Batched MTTKRP: `n` instances (each an MTTKRP einsum with its own extents
+ * and rank <= 64, float32) computed together.  With DEINSUM_PREC_SPLIT_BF16
+ * they run in ONE persistent tensor-core launch (plus a factor-split and a
+ * reduction launch) replayed from a CUDA graph captured on the first execute
+ * with a given set of pointers: every instance's rows are cut into work units
+ * of about total / (SMs x unit_div) bytes of X, assigned to the CTAs largest
+ * first.  With DEINSUM_PREC_PLAIN every instance runs as its own plain launch.
+ * Results are deterministic and equal to the single-instance split path.
+ */
+typedef struct deinsum_batch_s *deinsum_batch_t;
+
+/* Host only.  einsums[i], extents[i] (n_extents[i] values) as for deinsum_plan.
+ * The unit granularity comes from the autotune cache when the batch signature
+ * (count, size, rank mix) is known, else unit_div = 4. */
+deinsum_status deinsum_plan_batched(int n, const char *const *einsums, const int64_t *const *extents,
+                                    const int *n_extents, deinsum_dtype dtype, deinsum_prec prec,
+                                    deinsum_batch_t *out);
+
+/* inputs[i]: HOST array of DEVICE pointers of instance i's operands (string
+ * order); outputs[i]: DEVICE pointer of its output.  Asynchronous on `stream`;
+ * the first call with a new set of pointers uploads the instance tables,
+ * launches once and captures the graph (so it must not run under an outer
+ * stream capture); later calls with the same pointers replay the graph. */
+deinsum_status deinsum_execute_batched(deinsum_batch_t b, const void *const *const *inputs, void *const *outputs,
+                                       deinsum_stream_t stream);
+
+/* Time the split-BF16 batch with unit_div in {1, 2, 4, 8, 16} on the device,
+ * keep the fastest (and, if DEINSUM_AUTOTUNE_CACHE names a file, append it
+ * there for later plans with the same signature).  Synchronous. */
+deinsum_status deinsum_batched_autotune(deinsum_batch_t b, const void *const *const *inputs,
+                                        void *const *outputs, deinsum_stream_t stream, double *best_ms);
+
+/* Units, grid, unit divisor and algorithmic bytes (sum over the instances). */
+deinsum_status deinsum_batched_info(deinsum_batch_t b, int64_t *n_units, int *grid, int *unit_div,
+                                    double *alg_bytes);
+
+/* After synchronising: DEINSUM_OK or DEINSUM_ERR_TIMEOUT (a bounded wait gave up). */
+deinsum_status deinsum_batched_status(deinsum_batch_t b);
+
+void deinsum_batched_destroy(deinsum_batch_t b);
+
+/*
  * CP-ALS on the device.  The paper names CP decomposition as the computation
  * MTTKRP serves (Sec. I); the ALS steps follow Kolda & Bader (SIAM Review
  * 2009, Sec. 3.4).  Per sweep, for n = 0..N-1 (Gauss-Seidel): M = MTTKRP_n

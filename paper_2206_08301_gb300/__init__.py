@@ -106,6 +106,21 @@ def load():
         lib.deinsum_cpals_status.restype = i32
         lib.deinsum_cpals_destroy.argtypes = [vp]
         lib.deinsum_cpals_destroy.restype = None
+        lib.deinsum_plan_batched.argtypes = [i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(i32), i32, i32, ctypes.POINTER(vp)]
+        lib.deinsum_plan_batched.restype = i32
+        lib.deinsum_execute_batched.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(vp), vp]
+        lib.deinsum_execute_batched.restype = i32
+        lib.deinsum_batched_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(vp), vp,
+                                                 ctypes.POINTER(ctypes.c_double)]
+        lib.deinsum_batched_autotune.restype = i32
+        lib.deinsum_batched_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                             ctypes.POINTER(ctypes.c_double)]
+        lib.deinsum_batched_info.restype = i32
+        lib.deinsum_batched_status.argtypes = [vp]
+        lib.deinsum_batched_status.restype = i32
+        lib.deinsum_batched_destroy.argtypes = [vp]
+        lib.deinsum_batched_destroy.restype = None
         lib.deinsum_server_clock.argtypes = []
         lib.deinsum_server_clock.restype = ctypes.c_double
         lib.deinsum_server_create.argtypes = [ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)]
@@ -332,6 +347,60 @@ class CPALS:
     def close(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.deinsum_cpals_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Batched MTTKRP (``deinsum_plan_batched`` / ``deinsum_execute_batched`` / ...)."""
+
+    def __init__(self, einsums, extents, prec: str = "split_bf16"):
+        n = len(einsums)
+        self.n = n
+        self._enc = [e.encode() for e in einsums]
+        es = (ctypes.c_char_p * n)(*self._enc)
+        self._ext = [(ctypes.c_int64 * len(x))(*[int(v) for v in x]) for x in extents]
+        ex = (ctypes.c_void_p * n)(*[ctypes.cast(x, ctypes.c_void_p).value for x in self._ext])
+        ne = (ctypes.c_int * n)(*[len(x) for x in extents])
+        h = ctypes.c_void_p()
+        _check(load().deinsum_plan_batched(n, es, ex, ne, 0, PRECS[prec], ctypes.byref(h)), "deinsum_plan_batched")
+        self._h = h
+
+    def _marshal(self, inputs, outputs):
+        self._ins = [(ctypes.c_void_p * len(ops))(*[_dev_ptr(t, "operand").value for t in ops]) for ops in inputs]
+        ip = (ctypes.c_void_p * self.n)(*[ctypes.cast(x, ctypes.c_void_p).value for x in self._ins])
+        op = (ctypes.c_void_p * self.n)(*[_dev_ptr(t, "output").value for t in outputs])
+        return ip, op
+
+    def __call__(self, inputs, outputs, stream=None):
+        ip, op = self._marshal(inputs, outputs)
+        _check(load().deinsum_execute_batched(self._h, ip, op, _stream_ptr(stream)), "deinsum_execute_batched")
+        return outputs
+
+    def autotune(self, inputs, outputs, stream=None) -> float:
+        ip, op = self._marshal(inputs, outputs)
+        ms = ctypes.c_double()
+        _check(load().deinsum_batched_autotune(self._h, ip, op, _stream_ptr(stream), ctypes.byref(ms)),
+               "deinsum_batched_autotune")
+        return float(ms.value)
+
+    def info(self) -> dict:
+        nu, g, d, b = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(load().deinsum_batched_info(self._h, ctypes.byref(nu), ctypes.byref(g), ctypes.byref(d),
+                                           ctypes.byref(b)), "deinsum_batched_info")
+        return {"units": nu.value, "grid": g.value, "unit_div": d.value, "alg_bytes": b.value}
+
+    def status(self) -> int:
+        return int(load().deinsum_batched_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.deinsum_batched_destroy(self._h)
             self._h = None
 
     def __del__(self):

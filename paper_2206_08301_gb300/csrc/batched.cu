@@ -1,0 +1,557 @@
+// Batched MTTKRP: many instances of uneven extents and ranks in one
+// persistent tensor-core launch, replayed from a captured CUDA graph.
+//
+// Host side: every instance is classified by a regular plan (Sec. III-B MTTKRP
+// einsum); its row view is cut into work units (column of 128 output rows x a
+// range of fiber groups) of about `unit_bytes` of X each; the units of all
+// instances are assigned to the CTAs largest first (LPT: each unit goes to the
+// least-loaded CTA), so that one launch of one CTA per SM finishes them
+// together.  The granularity is picked by an autotuner that times candidate
+// schedules on the device and remembers the winner per batch signature.
+// Device side: a batched split of the instances' inner factors, the batched
+// tensor-core kernel (mttkrp_tc.cu), and a batched fixed-order reduction of
+// the unit partials into each instance's output.  With plain precision the
+// batch runs as separate launches of the plain kernel (the baseline).
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <new>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "sm100.cuh"
+
+namespace deinsum {
+namespace {
+
+constexpr int BM = DEINSUM_BM;
+constexpr int BK = DEINSUM_BK;
+
+struct SplitInst {
+    const float *U;
+    unsigned char *out;
+    int64_t K_in;
+    int R, RP, n_kb;
+};
+
+struct RedInst {
+    float *out;
+    int64_t I;
+    int R, RP;
+    int64_t rows_per_col, G;
+    int narrow;
+    int64_t col_table;  // first entry of this instance's column table in red_col
+};
+
+__global__ void batched_split_kernel(const SplitInst *__restrict__ si) {
+    const SplitInst s = si[blockIdx.y];
+    const int64_t total = int64_t(s.n_kb) * 2 * s.RP * BK;
+    for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int k = int(idx % BK);
+        const int n = int((idx / BK) % (2 * s.RP));
+        const int64_t kb = idx / (int64_t(BK) * 2 * s.RP);
+        const int r = n % s.RP;
+        const int64_t kr = kb * BK + k;
+        const float v = (r < s.R && kr < s.K_in) ? s.U[kr * s.R + r] : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 e = n < s.RP ? h : __float2bfloat16_rn(v - __bfloat162float(h));
+        *reinterpret_cast<__nv_bfloat16 *>(s.out + size_t(kb) * (2 * s.RP * BK * 2) +
+                                           sm100::sw128_offset(uint32_t(n), uint32_t(k))) = e;
+    }
+}
+
+// out_i[col*rows_per_col + r, c] = sum over the splits of the column, in order,
+// (and over the G row groups of narrow tiles) of the unit partials.
+__global__ void batched_reduce_kernel(const RedInst *__restrict__ ri, const int64_t *__restrict__ red_col,
+                                      const int64_t *__restrict__ red_off, const float *__restrict__ partial) {
+    const RedInst r = ri[blockIdx.y];
+    const int64_t n = r.I * r.R;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t row = e / r.R;
+        const int c = int(e - row * r.R);
+        const int64_t col = row / r.rows_per_col;
+        const int64_t i = row - col * r.rows_per_col;
+        float s = 0.f;
+        for (int64_t k = red_col[r.col_table + col]; k < red_col[r.col_table + col + 1]; ++k) {
+            const float *p = partial + red_off[k];
+            if (r.narrow) {
+                for (int64_t g = 0; g < r.G; ++g) s += p[(g * r.I + i) * r.RP + c];
+            } else {
+                s += p[i * r.RP + c];
+            }
+        }
+        r.out[e] = s;
+    }
+}
+
+size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Inst {
+    int order = 0, mode = 0, R = 0, n_ops = 0;
+    int64_t dims[DEINSUM_MAX_ORDER] = {0};
+    int opmode[DEINSUM_MAX_ORDER + 1] = {0};
+    MttkrpGeom g{};
+    double xbytes = 0.0;
+};
+
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune_cache;  // batch signature -> unit divisor
+bool g_tune_loaded = false;
+
+void load_tune_cache() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("DEINSUM_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    int div = 0;
+    while (std::fscanf(f, "%255s %d", key, &div) == 2) g_tune_cache[key] = div;
+    std::fclose(f);
+}
+
+void store_tune_cache(const std::string &key, int div) {
+    g_tune_cache[key] = div;
+    const char *path = std::getenv("DEINSUM_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d\n", key.c_str(), div);
+    std::fclose(f);
+}
+
+}  // namespace
+}  // namespace deinsum
+
+using namespace deinsum;
+
+struct deinsum_batch_s {
+    int n = 0;
+    deinsum_prec prec = DEINSUM_PREC_SPLIT_BF16;
+    std::vector<deinsum_plan_t> plans;
+    std::vector<Inst> inst;
+    double total_bytes = 0.0;
+    std::string signature;
+    int unit_div = 4;   // units of about total / (grid * unit_div) bytes
+    int n_sm = 0, grid = 0;
+    // schedule (host)
+    std::vector<int64_t> units;      // 5 per unit, grouped by CTA
+    std::vector<int64_t> cta_begin;  // grid + 1
+    std::vector<int64_t> red_off;    // partial offsets, per instance, column, split
+    std::vector<int64_t> red_col;    // per instance: n_cols + 1 starts into red_off
+    std::vector<int64_t> red_col_base;
+    std::vector<size_t> bsplit_off;
+    size_t partial_floats = 0, bsplit_bytes = 0;
+    // device
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t o_status = 0, o_insts = 0, o_split = 0, o_red = 0, o_units = 0, o_cta = 0, o_redoff = 0, o_redcol = 0,
+           o_bsplit = 0, o_partial = 0, o_end = 0;
+    char *staging = nullptr;  // pinned: insts + split table + reduce table
+    size_t staging_bytes = 0;
+    bool tables_uploaded = false;
+    std::vector<const void *> ptrs;  // cached pointers of the last execute
+    cudaGraphExec_t gexec = nullptr;
+};
+
+namespace {
+
+void destroy_graph(deinsum_batch_s *b) {
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+}
+
+// Units of about total / (grid * unit_div) bytes of X; LPT assignment to CTAs.
+void build_batch_schedule(deinsum_batch_s *b) {
+    const int64_t target_units = int64_t(b->n_sm) * b->unit_div;
+    const double unit_bytes = std::max(1.0, b->total_bytes / double(target_units));
+    struct U {
+        int64_t inst, col, f0, f1, off;
+        double cost;
+    };
+    std::vector<U> all;
+    b->red_off.clear();
+    b->red_col.clear();
+    b->red_col_base.assign(size_t(b->n), 0);
+    b->bsplit_off.assign(size_t(b->n), 0);
+    b->partial_floats = 0;
+    b->bsplit_bytes = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const MttkrpGeom &g = b->inst[size_t(i)].g;
+        const int64_t max_units = g.n_cols * g.fg_per_col;
+        int64_t want = int64_t(std::ceil(b->inst[size_t(i)].xbytes / unit_bytes));
+        want = std::max<int64_t>(1, std::min(want, max_units));
+        const int64_t per_col = std::min<int64_t>(g.fg_per_col, std::max<int64_t>(1, (want + g.n_cols - 1) / g.n_cols));
+        b->red_col_base[size_t(i)] = int64_t(b->red_col.size());
+        for (int64_t c = 0; c < g.n_cols; ++c) {
+            b->red_col.push_back(int64_t(b->red_off.size()));
+            for (int64_t s = 0; s < per_col; ++s) {
+                const int64_t f0 = g.fg_per_col * s / per_col, f1 = g.fg_per_col * (s + 1) / per_col;
+                if (f1 <= f0) continue;
+                const int64_t off = int64_t(b->partial_floats);
+                b->partial_floats += size_t(BM) * size_t(g.R_pad);
+                b->red_off.push_back(off);
+                all.push_back({i, c, f0, f1, off, double(f1 - f0) * double(g.n_kb)});
+            }
+        }
+        b->red_col.push_back(int64_t(b->red_off.size()));
+        b->bsplit_off[size_t(i)] = b->bsplit_bytes;
+        b->bsplit_bytes += up(size_t(g.n_kb) * 2 * size_t(g.R_pad) * BK * 2, 1024);
+    }
+    b->grid = int(std::min<int64_t>(b->n_sm, int64_t(all.size())));
+    if (b->grid < 1) b->grid = 1;
+    std::vector<size_t> order(all.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return all[x].cost > all[y].cost; });
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < b->grid; ++c) heap.push({0.0, c});
+    std::vector<std::vector<size_t>> per_cta(size_t(b->grid));
+    for (size_t k : order) {
+        Load top = heap.top();
+        heap.pop();
+        per_cta[size_t(top.second)].push_back(k);
+        heap.push({top.first + all[k].cost, top.second});
+    }
+    b->units.clear();
+    b->cta_begin.assign(size_t(b->grid) + 1, 0);
+    for (int c = 0; c < b->grid; ++c) {
+        b->cta_begin[size_t(c)] = int64_t(b->units.size() / 5);
+        for (size_t k : per_cta[size_t(c)]) {
+            const U &u = all[k];
+            b->units.insert(b->units.end(), {u.inst, u.col, u.f0, u.f1, u.off});
+        }
+    }
+    b->cta_begin[size_t(b->grid)] = int64_t(b->units.size() / 5);
+}
+
+deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
+    size_t off = 0;
+    auto take = [&](size_t bytes, size_t align) {
+        off = up(off, align);
+        const size_t r = off;
+        off += bytes;
+        return r;
+    };
+    b->o_status = take(256, 256);
+    b->o_insts = take(sizeof(MttkrpArgs) * size_t(b->n), 128);
+    b->o_split = take(sizeof(SplitInst) * size_t(b->n), 64);
+    b->o_red = take(sizeof(RedInst) * size_t(b->n), 64);
+    b->o_units = take(b->units.size() * 8, 256);
+    b->o_cta = take(b->cta_begin.size() * 8, 256);
+    b->o_redoff = take(b->red_off.size() * 8, 256);
+    b->o_redcol = take(b->red_col.size() * 8, 256);
+    b->o_bsplit = take(b->bsplit_bytes, 1024);
+    b->o_partial = take(b->partial_floats * 4, 1024);
+    b->o_end = up(off, 1024);
+    if (b->o_end > b->ws_bytes) {
+        if (b->ws) cudaFree(b->ws);
+        b->ws = nullptr;
+        b->ws_bytes = 0;
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, b->o_end);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? DEINSUM_ERR_OOM : DEINSUM_ERR_CUDA;
+        }
+        b->ws = static_cast<char *>(p);
+        b->ws_bytes = b->o_end;
+    }
+    const size_t stage = up(sizeof(MttkrpArgs) * size_t(b->n), 128) + up(sizeof(SplitInst) * size_t(b->n), 64) +
+                         up(sizeof(RedInst) * size_t(b->n), 64);
+    if (stage > b->staging_bytes) {
+        if (b->staging) cudaFreeHost(b->staging);
+        b->staging = nullptr;
+        if (cudaMallocHost(reinterpret_cast<void **>(&b->staging), stage) != cudaSuccess) return DEINSUM_ERR_OOM;
+        b->staging_bytes = stage;
+    }
+    cudaMemsetAsync(b->ws + b->o_status, 0, 256, s);
+    cudaMemcpyAsync(b->ws + b->o_units, b->units.data(), b->units.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->ws + b->o_cta, b->cta_begin.data(), b->cta_begin.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->ws + b->o_redoff, b->red_off.data(), b->red_off.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->ws + b->o_redcol, b->red_col.data(), b->red_col.size() * 8, cudaMemcpyHostToDevice, s);
+    b->tables_uploaded = true;
+    b->ptrs.clear();  // instance tables must be rebuilt for the new layout
+    destroy_graph(b);
+    return cudaGetLastError() == cudaSuccess ? DEINSUM_OK : DEINSUM_ERR_CUDA;
+}
+
+// Instance arguments (pointers, TMA descriptors), split and reduce tables.
+deinsum_status upload_instances(deinsum_batch_s *b, const void *const *const *inputs, void *const *outputs,
+                                cudaStream_t s) {
+    cudaStreamSynchronize(s);  // the staging buffer may still feed an earlier copy
+    MttkrpArgs *A = reinterpret_cast<MttkrpArgs *>(b->staging);
+    SplitInst *S = reinterpret_cast<SplitInst *>(b->staging + up(sizeof(MttkrpArgs) * size_t(b->n), 128));
+    RedInst *Rd = reinterpret_cast<RedInst *>(reinterpret_cast<char *>(S) + up(sizeof(SplitInst) * size_t(b->n), 64));
+    for (int i = 0; i < b->n; ++i) {
+        const Inst &in = b->inst[size_t(i)];
+        MttkrpArgs &a = A[i];
+        std::memset(static_cast<void *>(&a), 0, sizeof(a));
+        mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, inputs[i][0], &a);
+        a.X = inputs[i][0];
+        for (int k = 1; k < in.n_ops; ++k) a.U[in.opmode[k]] = inputs[i][k];
+        a.Bsplit = b->ws + b->o_bsplit + b->bsplit_off[size_t(i)];
+        a.status = reinterpret_cast<int *>(b->ws + b->o_status);
+        const int inner = a.g.kcase == 0 ? a.g.order - 1 : a.g.order - 2;
+        S[i] = {static_cast<const float *>(a.U[inner]), static_cast<unsigned char *>(const_cast<void *>(a.Bsplit)),
+                a.g.K_in, a.g.R, a.g.R_pad, a.g.n_kb};
+        Rd[i] = {static_cast<float *>(outputs[i]), a.g.I, a.g.R, a.g.R_pad, a.g.rows_per_col, a.g.G, a.g.narrow,
+                 b->red_col_base[size_t(i)]};
+    }
+    const size_t bytes = up(sizeof(MttkrpArgs) * size_t(b->n), 128) + up(sizeof(SplitInst) * size_t(b->n), 64) +
+                         up(sizeof(RedInst) * size_t(b->n), 64);
+    // the three tables are laid out back to back in the workspace as in the staging buffer
+    cudaMemcpyAsync(b->ws + b->o_insts, b->staging, bytes, cudaMemcpyHostToDevice, s);
+    return cudaGetLastError() == cudaSuccess ? DEINSUM_OK : DEINSUM_ERR_CUDA;
+}
+
+int max_kb(const deinsum_batch_s *b) {
+    int m = 1;
+    for (auto &i : b->inst) m = std::max(m, i.g.n_kb);
+    return m;
+}
+
+deinsum_status launch_batch(deinsum_batch_s *b, cudaStream_t s) {
+    const int64_t maxtot = int64_t(max_kb(b)) * 2 * 64 * BK;
+    int gx = int(std::min<int64_t>(64, (maxtot + 255) / 256));
+    batched_split_kernel<<<dim3(unsigned(gx), unsigned(b->n)), 256, 0, s>>>(
+        reinterpret_cast<const SplitInst *>(b->ws + b->o_split));
+    count_launch();
+    BatchArgs ba;
+    ba.insts = reinterpret_cast<const MttkrpArgs *>(b->ws + b->o_insts);
+    ba.units = reinterpret_cast<const int64_t *>(b->ws + b->o_units);
+    ba.cta_begin = reinterpret_cast<const int64_t *>(b->ws + b->o_cta);
+    ba.partial = reinterpret_cast<float *>(b->ws + b->o_partial);
+    ba.status = reinterpret_cast<int *>(b->ws + b->o_status);
+    if (launch_mttkrp_tc_batched(ba, b->grid, s)) return DEINSUM_ERR_CUDA;
+    int64_t maxo = 1;
+    for (auto &i : b->inst) maxo = std::max<int64_t>(maxo, i.g.I * i.g.R);
+    int rx = int(std::min<int64_t>(64, (maxo + 255) / 256));
+    batched_reduce_kernel<<<dim3(unsigned(rx), unsigned(b->n)), 256, 0, s>>>(
+        reinterpret_cast<const RedInst *>(b->ws + b->o_red), reinterpret_cast<const int64_t *>(b->ws + b->o_redcol),
+        reinterpret_cast<const int64_t *>(b->ws + b->o_redoff), reinterpret_cast<const float *>(b->ws + b->o_partial));
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DEINSUM_OK : DEINSUM_ERR_CUDA;
+}
+
+deinsum_status ensure_ready(deinsum_batch_s *b, const void *const *const *inputs, void *const *outputs,
+                            cudaStream_t s) {
+    if (b->n_sm == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return DEINSUM_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return DEINSUM_ERR_CUDA;
+    }
+    if (!b->tables_uploaded) {
+        build_batch_schedule(b);
+        deinsum_status st = layout_and_upload(b, s);
+        if (st != DEINSUM_OK) return st;
+    }
+    std::vector<const void *> p;
+    for (int i = 0; i < b->n; ++i) {
+        for (int k = 0; k < b->inst[size_t(i)].n_ops; ++k) p.push_back(inputs[i][k]);
+        p.push_back(outputs[i]);
+    }
+    if (p != b->ptrs) {
+        destroy_graph(b);
+        deinsum_status st = upload_instances(b, inputs, outputs, s);
+        if (st != DEINSUM_OK) return st;
+        b->ptrs = p;
+    }
+    return DEINSUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+deinsum_status deinsum_plan_batched(int n, const char *const *einsums, const int64_t *const *extents,
+                                    const int *n_extents, deinsum_dtype dtype, deinsum_prec prec,
+                                    deinsum_batch_t *out) {
+    if (!out || n < 1 || !einsums || !extents || !n_extents) return DEINSUM_ERR_INVALID;
+    *out = nullptr;
+    if (dtype != DEINSUM_F32) return DEINSUM_ERR_DTYPE;
+    deinsum_batch_s *b = new (std::nothrow) deinsum_batch_s();
+    if (!b) return DEINSUM_ERR_OOM;
+    b->n = n;
+    b->prec = prec;
+    b->plans.assign(size_t(n), nullptr);
+    b->inst.resize(size_t(n));
+    char sig[64];
+    std::snprintf(sig, sizeof(sig), "n%d", n);
+    b->signature = sig;
+    for (int i = 0; i < n; ++i) {
+        deinsum_status st = deinsum_plan(einsums[i], extents[i], n_extents[i], dtype, prec, &b->plans[size_t(i)]);
+        if (st != DEINSUM_OK) {
+            deinsum_batched_destroy(b);
+            return st;
+        }
+        deinsum_plan_info_t info;
+        deinsum_plan_info(b->plans[size_t(i)], &info);
+        if (info.kind != DEINSUM_KIND_MTTKRP) {
+            deinsum_batched_destroy(b);
+            return DEINSUM_ERR_UNSUPPORTED;
+        }
+        Inst &in = b->inst[size_t(i)];
+        in.order = info.order;
+        in.mode = info.mode;
+        in.n_ops = info.order;
+        in.R = int(info.ranks[(info.mode + 1) % info.order]);
+        for (int m = 0; m < in.order; ++m) in.dims[m] = info.dims[m];
+        for (int k = 1; k < in.n_ops; ++k) in.opmode[k] = deinsum_internal_operand_mode(b->plans[size_t(i)], k);
+        MttkrpArgs tmp;
+        std::memset(static_cast<void *>(&tmp), 0, sizeof(tmp));
+        mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, nullptr, &tmp);
+        in.g = tmp.g;
+        in.xbytes = 4.0;
+        for (int m = 0; m < in.order; ++m) in.xbytes *= double(in.dims[m]);
+        b->total_bytes += in.xbytes;
+    }
+    // signature for the autotune cache: count, total size and rank mix, rounded
+    int rhist[4] = {0, 0, 0, 0};
+    for (auto &in : b->inst) rhist[in.R <= 8 ? 0 : in.R <= 16 ? 1 : in.R <= 32 ? 2 : 3]++;
+    std::snprintf(sig, sizeof(sig), "n%d_gb%.1f_r%d.%d.%d.%d", n, b->total_bytes / 1e9, rhist[0], rhist[1], rhist[2],
+                  rhist[3]);
+    b->signature = sig;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        load_tune_cache();
+        auto it = g_tune_cache.find(b->signature);
+        if (it != g_tune_cache.end()) b->unit_div = it->second;
+    }
+    *out = b;
+    return DEINSUM_OK;
+}
+
+deinsum_status deinsum_execute_batched(deinsum_batch_t b, const void *const *const *inputs, void *const *outputs,
+                                       deinsum_stream_t stream) {
+    if (!b || !inputs || !outputs) return DEINSUM_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (b->prec == DEINSUM_PREC_PLAIN) {
+        for (int i = 0; i < b->n; ++i) {
+            deinsum_status st = deinsum_execute(b->plans[size_t(i)], inputs[i], b->inst[size_t(i)].n_ops, outputs[i], stream);
+            if (st != DEINSUM_OK) return st;
+        }
+        return DEINSUM_OK;
+    }
+    for (int i = 0; i < b->n; ++i)
+        for (int k = 0; k < b->inst[size_t(i)].n_ops; ++k)
+            if (!inputs[i] || !inputs[i][k] || (reinterpret_cast<uintptr_t>(inputs[i][k]) & 3)) return DEINSUM_ERR_INVALID;
+    deinsum_status st = ensure_ready(b, inputs, outputs, s);
+    if (st != DEINSUM_OK) return st;
+    if (!b->gexec) {
+        // first run with these pointers: launch directly (sets kernel attributes), then capture
+        st = launch_batch(b, s);
+        if (st != DEINSUM_OK) return st;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DEINSUM_ERR_CUDA;
+        st = launch_batch(b, s);
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (st != DEINSUM_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return DEINSUM_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&b->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->gexec = nullptr;
+            cudaGetLastError();
+            return DEINSUM_ERR_CUDA;
+        }
+        return DEINSUM_OK;
+    }
+    return cudaGraphLaunch(b->gexec, s) == cudaSuccess ? DEINSUM_OK : DEINSUM_ERR_CUDA;
+}
+
+deinsum_status deinsum_batched_autotune(deinsum_batch_t b, const void *const *const *inputs, void *const *outputs,
+                                        deinsum_stream_t stream, double *best_ms) {
+    if (!b || !inputs || !outputs) return DEINSUM_ERR_INVALID;
+    if (b->prec != DEINSUM_PREC_SPLIT_BF16) return DEINSUM_ERR_DTYPE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int cand[] = {1, 2, 4, 8, 16};
+    int best = b->unit_div;
+    double best_t = 1e30;
+    for (int div : cand) {
+        b->unit_div = div;
+        b->tables_uploaded = false;
+        deinsum_status st = ensure_ready(b, inputs, outputs, s);
+        if (st != DEINSUM_OK) return st;
+        for (int r = 0; r < 2; ++r) launch_batch(b, s);
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch_batch(b, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / 3.0 < best_t) {
+            best_t = ms / 3.0;
+            best = div;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->unit_div = best;
+    b->tables_uploaded = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        store_tune_cache(b->signature, best);
+    }
+    if (best_ms) *best_ms = best_t;
+    return ensure_ready(b, inputs, outputs, s);
+}
+
+deinsum_status deinsum_batched_info(deinsum_batch_t b, int64_t *n_units, int *grid, int *unit_div, double *alg_bytes) {
+    if (!b) return DEINSUM_ERR_INVALID;
+    if (n_units) *n_units = int64_t(b->units.size() / 5);
+    if (grid) *grid = b->grid;
+    if (unit_div) *unit_div = b->unit_div;
+    if (alg_bytes) {
+        double t = 0.0;
+        for (int i = 0; i < b->n; ++i) {
+            deinsum_plan_info_t info;
+            deinsum_plan_info(b->plans[size_t(i)], &info);
+            t += info.alg_bytes;
+        }
+        *alg_bytes = t;
+    }
+    return DEINSUM_OK;
+}
+
+deinsum_status deinsum_batched_status(deinsum_batch_t b) {
+    if (!b) return DEINSUM_ERR_INVALID;
+    if (!b->ws) return DEINSUM_OK;
+    int v = 0;
+    if (cudaMemcpy(&v, b->ws + b->o_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return DEINSUM_ERR_CUDA;
+    return v == 0 ? DEINSUM_OK : DEINSUM_ERR_TIMEOUT;
+}
+
+void deinsum_batched_destroy(deinsum_batch_t b) {
+    if (!b) return;
+    destroy_graph(b);
+    for (auto p : b->plans)
+        if (p) deinsum_destroy(p);
+    if (b->ws) cudaFree(b->ws);
+    if (b->staging) cudaFreeHost(b->staging);
+    delete b;
+}
+
+}  // extern "C"

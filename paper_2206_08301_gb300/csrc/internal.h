@@ -83,6 +83,21 @@ struct MttkrpArgs {
     int *status;                       // device status word
 };
 
+// Many MTTKRP instances in one persistent launch of the tensor-core kernel:
+// per-instance arguments (geometry, TMA descriptor of X, factor pointers,
+// split factor tiles) live in device memory; every CTA walks its own list of
+// units, each unit = (instance, column, first fiber group, end, offset of its
+// 128 x R_pad partial block in `partial`).
+struct BatchArgs {
+    const MttkrpArgs *insts;
+    const int64_t *units;       // 5 per unit
+    const int64_t *cta_begin;   // units of CTA c: cta_begin[c] .. cta_begin[c+1] - 1
+    float *partial;
+    int *status;
+};
+int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, void *stream);
+size_t mttkrp_tc_batched_smem_bytes();
+
 // Launch helpers implemented in the .cu files.  They return a CUDA error code
 // (0 on success) and increment the library's launch counter.
 int launch_mttkrp_plain_f32(const MttkrpArgs &a, int n_sm, void *stream);
@@ -101,6 +116,8 @@ int launch_ttm_plain_f64(const double *X, const double *U, double *Y, int64_t A,
                          int64_t B, int64_t Rm, void *stream);
 
 void count_launch(int n = 1);
+
+int deinsum_internal_operand_mode(deinsum_plan_t pl, int k);
 
 // Row view (and TMA descriptor of X when possible) of a one-off split-BF16
 // MTTKRP, computed without heap or device allocation.

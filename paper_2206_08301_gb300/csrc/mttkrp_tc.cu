@@ -549,6 +549,359 @@ int launch_tc_rp(const MttkrpArgs &a, int n_sm, void *stream) {
     return int(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// Batched form: the same pipeline, but every unit names its instance, whose
+// arguments are read from device memory, and every CTA walks the unit list
+// the host assigned to it (largest first).  The accumulator and factor-tile
+// shapes follow the instance's padded rank (<= 64): MMA N = 2 R_pad is a
+// runtime field of the instruction descriptor.
+// ---------------------------------------------------------------------------
+struct BIter {
+    const BatchArgs *b;
+    const MttkrpArgs *a;
+    int64_t u, uend, col, fg, fg1, tile, o, part_off;
+    int kb;
+    bool done;
+    __device__ __forceinline__ void load_unit() {
+        while (u < uend) {
+            const int64_t *r = b->units + 5 * u;
+            a = b->insts + r[0];
+            col = r[1];
+            fg = r[2];
+            fg1 = r[3];
+            part_off = r[4];
+            if (fg < fg1) {
+                kb = 0;
+                tile = fg / a->g.O;
+                o = fg - tile * a->g.O;
+                done = false;
+                return;
+            }
+            ++u;
+        }
+        done = true;
+    }
+    __device__ __forceinline__ void init(const BatchArgs *bb) {
+        b = bb;
+        u = b->cta_begin[blockIdx.x];
+        uend = b->cta_begin[blockIdx.x + 1];
+        load_unit();
+    }
+    __device__ __forceinline__ void next() {
+        if (++kb < a->g.n_kb) return;
+        kb = 0;
+        if (++fg < fg1) {
+            if (++o == a->g.O) { o = 0; ++tile; }
+            return;
+        }
+        ++u;
+        load_unit();
+    }
+    __device__ __forceinline__ Iter as_iter() const {
+        Iter t;
+        t.u = u; t.col = col; t.fg = fg; t.fg1 = fg1; t.tile = tile; t.o = o; t.kb = kb; t.done = done;
+        return t;
+    }
+};
+
+constexpr int RPB = 64;  // the batched kernel is shaped for the largest padded rank
+
+__global__ void __launch_bounds__(TcCfg<RPB>::THREADS, 1)
+mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
+    using C = TcCfg<RPB>;
+    constexpr int RS = C::RS, AS = C::AS;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *raw_base = smem;
+    unsigned char *a_base = smem + RS * C::RAW_BYTES;
+    float *Lrow = reinterpret_cast<float *>(a_base + AS * C::ASTAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(a_base + AS * C::ASTAGE_BYTES + C::LROW_BYTES);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    int *status = bargs.status;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
+    auto raw_addr = [&](int s) { return raw_s + uint32_t(s) * C::RAW_BYTES; };
+    auto a_hi = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES; };
+    auto a_lo = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + C::A_BYTES; };
+    auto b_t = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + 2 * C::A_BYTES; };
+    auto raw_full = [&](int s) { return smem_u32(bars + s); };
+    auto raw_empty = [&](int s) { return smem_u32(bars + RS + s); };
+    auto a_full = [&](int s) { return smem_u32(bars + 2 * RS + s); };
+    auto bfull = [&](int s) { return smem_u32(bars + 2 * RS + AS + s); };
+    auto a_empty = [&](int s) { return smem_u32(bars + 2 * RS + 2 * AS + s); };
+    auto accf = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + b); };
+    auto acce = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + 2 + b); };
+    const uint32_t drain = smem_u32(bars + 2 * RS + 3 * AS + 4);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RS; ++s) {
+            mbar_init(raw_full(s), 1);
+            mbar_init(raw_empty(s), CONV_WARPS);
+        }
+        for (int s = 0; s < AS; ++s) {
+            mbar_init(a_full(s), CONV_WARPS);
+            mbar_init(bfull(s), 1);
+            mbar_init(a_empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), EPI_WARPS);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == C::MMA_WARP) {
+        tmem_alloc(smem_u32(tmem_holder), C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp < CONV_WARPS) {
+        // ----------------------------------------------------------- converters
+        const int pt = threadIdx.x;
+        const bool issuer = (pt == 0);
+        BIter it;
+        it.init(&bargs);
+        uint32_t bpar = 0, bused = 0;
+        for (int64_t chunk = 0; !it.done; ++chunk) {
+            const MttkrpArgs &a = *it.a;
+            float4 v[8];
+            const int rs = int(chunk % RS);
+            if (a.use_tma) {
+                const uint32_t rj = uint32_t(chunk / RS);
+                if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
+                conv_read_smem(a, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
+            } else {
+                conv_read_global(a, it.as_iter(), pt, v);
+            }
+            const int as = int(chunk % AS);
+            const uint32_t aj = uint32_t(chunk / AS);
+            if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status))) break;
+            if (issuer) {
+                const uint32_t bbytes = uint32_t(2 * a.g.R_pad * BK * 2);
+                mbar_arrive_expect_tx(bfull(as), bbytes);
+                bulk_g2s(b_t(as), static_cast<const char *>(a.Bsplit) + size_t(it.kb) * bbytes, bbytes, bfull(as));
+                bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
+                bused |= 1u << as;
+            }
+            conv_store(a.g, pt, a_hi(as), a_lo(as), v);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(a_full(as));
+                if (a.use_tma) mbar_arrive(raw_empty(rs));
+            }
+            it.next();
+        }
+        if (issuer) {
+            for (int s = 0; s < AS; ++s)
+                if ((bused >> s) & 1u) mbar_wait(bfull(s), (bpar >> s) & 1u, abort_flag, status);
+        }
+    } else if (warp == C::TMA_WARP) {
+        // ------------------------------------------------------------------ TMA
+        if (lane == 0) {
+            BIter it;
+            it.init(&bargs);
+            int last_rs = -1;
+            uint32_t last_par = 0;
+            const MttkrpArgs *fenced = nullptr;
+            for (int64_t chunk = 0; !it.done; ++chunk) {
+                const MttkrpArgs &a = *it.a;
+                if (a.use_tma && fenced != it.a) {
+                    fence_tensormap_acquire(&a.xmap);
+                    fenced = it.a;
+                }
+                if (a.use_tma) {
+                    const int rs = int(chunk % RS);
+                    const uint32_t rj = uint32_t(chunk / RS);
+                    if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status)) break;
+                    mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
+                    const int kc = it.kb * BK;
+                    if (a.g.kcase == 0) {
+                        const int c2 = a.g.narrow ? 0 : int(it.col * BM);
+                        const int c3 = a.g.narrow ? int(it.tile * a.g.G) : int(it.tile);
+                        tma_load_4d(raw_addr(rs), &a.xmap, kc, int(it.o), c2, c3, raw_full(rs));
+                    } else {
+                        tma_load_3d(raw_addr(rs), &a.xmap, int(it.col * BM), kc, int(it.o), raw_full(rs));
+                    }
+                    last_rs = rs;
+                    last_par = rj & 1u;
+                }
+                it.next();
+            }
+            if (last_rs >= 0) mbar_wait(raw_full(last_rs), last_par, abort_flag, status);
+        }
+        __syncwarp();
+    } else if (warp == C::MMA_WARP) {
+        // -------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            BIter it;
+            it.init(&bargs);
+            int64_t chunk = 0, fgi = 0;
+            bool ok = true;
+            uint32_t dcol = 0, idesc = 0;
+            while (ok && !it.done) {
+                const MttkrpArgs &a = *it.a;
+                const int b = int(fgi & 1);
+                if (it.kb == 0) {
+                    const uint32_t jb = uint32_t(fgi >> 1);
+                    if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
+                    tc_fence_after();
+                    dcol = tmem + uint32_t(b * C::N);
+                    idesc = idesc_bf16_f32(BM, 2 * a.g.R_pad);
+                }
+                const int s = int(chunk % AS);
+                const uint32_t j = uint32_t(chunk / AS);
+                if (!mbar_wait(a_full(s), j & 1u, abort_flag, status) ||
+                    !mbar_wait(bfull(s), j & 1u, abort_flag, status)) { ok = false; break; }
+                tc_fence_after();
+                const uint64_t dh = desc_kmajor_sw128(a_hi(s));
+                const uint64_t dl = desc_kmajor_sw128(a_lo(s));
+                const uint64_t db = desc_kmajor_sw128(b_t(s));
+                #pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint64_t adv = uint64_t(kk * 32) >> 4;
+                    mma_bf16(dcol, dh + adv, db + adv, idesc, (it.kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_bf16(dcol, dl + adv, db + adv, idesc, 1u);
+                }
+                mma_commit(a_empty(s));
+                ++chunk;
+                if (it.kb == a.g.n_kb - 1) {
+                    mma_commit(accf(b));
+                    ++fgi;
+                }
+                it.next();
+            }
+            mma_commit(drain);
+            mbar_wait(drain, 0, abort_flag, status);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------- epilogue
+        const int quad = warp & 3;
+        const int l = quad * 32 + lane;
+        BIter it;
+        it.init(&bargs);
+        int64_t fgi = 0;
+        bool ok = true;
+        while (ok && !it.done) {
+            const int64_t u = it.u;
+            const MttkrpArgs &a = *it.a;
+            const MttkrpGeom &g = a.g;
+            const int rp = g.R_pad;
+            const int64_t ucol = it.col;
+            const bool lane_weights = g.kcase == 0 && g.narrow && g.n_lmodes > 0;
+            float *part = bargs.partial + it.part_off + int64_t(l) * rp;
+            bool first_flush = true;
+            float acc[RPB];
+            #pragma unroll
+            for (int c = 0; c < RPB; ++c) acc[c] = 0.f;
+            auto flush = [&]() {
+                #pragma unroll
+                for (int c = 0; c < RPB; c += 4) {
+                    if (c < rp) {
+                        float4 sv = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+                        if (!first_flush) {
+                            const float4 pv = *reinterpret_cast<const float4 *>(part + c);
+                            sv.x += pv.x; sv.y += pv.y; sv.z += pv.z; sv.w += pv.w;
+                        }
+                        *reinterpret_cast<float4 *>(part + c) = sv;
+                    }
+                    acc[c] = acc[c + 1] = acc[c + 2] = acc[c + 3] = 0.f;
+                }
+                first_flush = false;
+            };
+            int64_t tile = -1;
+            int folded = 0;
+            float lw_lane0 = 0.f, lw_lane1 = 0.f;
+            while (!it.done && it.u == u) {
+                if (it.tile != tile) {
+                    tile = it.tile;
+                    if (lane_weights) {
+                        lw_lane0 = 1.f;
+                        lw_lane1 = 1.f;
+                        const int64_t rowbase = tile_rowbase(g, ucol, tile);
+                        const bool v = row_valid(g, ucol, rowbase, l);
+                        const int64_t p = tile * g.G + l / g.I;
+                        for (int c = 0; c < rp; ++c) Lrow[c * BM + l] = (v && c < g.R) ? row_weight(a, p, c) : 0.f;
+                    } else if (g.kcase == 0 && g.n_lmodes > 0) {
+                        lw_lane0 = lane < g.R ? row_weight(a, tile, lane) : 0.f;
+                        lw_lane1 = lane + 32 < g.R ? row_weight(a, tile, lane + 32) : 0.f;
+                    } else {
+                        lw_lane0 = 1.f;
+                        lw_lane1 = 1.f;
+                    }
+                }
+                const float w0 = lane < g.R ? lw_lane0 * outer_weight(a, it.o, lane) : 0.f;
+                const float w1 = lane + 32 < g.R ? lw_lane1 * outer_weight(a, it.o, lane + 32) : 0.f;
+                const int b = int(fgi & 1);
+                const uint32_t jb = uint32_t(fgi >> 1);
+                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
+                #pragma unroll
+                for (int c = 0; c < RPB; c += 16) {
+                    if (c < rp) {
+                        uint32_t hi[16], lo[16];
+                        tmem_ld16(taddr + uint32_t(c), hi);
+                        tmem_ld16(taddr + uint32_t(rp + c), lo);
+                        tmem_wait_ld();
+                        #pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int col = c + q;
+                            float w = __shfl_sync(0xffffffffu, col < 32 ? w0 : w1, col & 31);
+                            if (lane_weights) w *= Lrow[col * BM + l];
+                            acc[col] = fmaf(w, __uint_as_float(hi[q]) + __uint_as_float(lo[q]), acc[col]);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce(b));
+                ++fgi;
+                if (++folded == kFoldEvery) {
+                    folded = 0;
+                    flush();
+                }
+                for (int kb = 0; kb < g.n_kb; ++kb) it.next();
+            }
+            if (!ok) break;
+            flush();
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == C::MMA_WARP) {
+        tc_fence_after();
+        tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+}
+
+}  // namespace
+
+size_t mttkrp_tc_batched_smem_bytes() { return TcCfg<RPB>::SMEM; }
+
+int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, void *stream) {
+    using C = TcCfg<RPB>;
+    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(C::SMEM));
+    if (e != cudaSuccess) return int(e);
+    mttkrp_tc_batched_kernel<<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(b);
+    count_launch();
+    return int(cudaGetLastError());
+}
+
+namespace {
 }  // namespace
 
 size_t mttkrp_tc_smem_bytes(int R_pad) {

@@ -571,6 +571,9 @@ deinsum_status execute_ttmc(deinsum_plan_s *pl, const void *const *inputs, void 
 
 namespace deinsum {
 
+// Mode of X that einsum operand k (k >= 1) is contracted with.
+int deinsum_internal_operand_mode(deinsum_plan_t pl, int k) { return pl->operand_mode[k]; }
+
 // Row view and TMA descriptor of a one-off split-BF16 MTTKRP, for the entry
 // point that allocates nothing: fills a->g and, when X allows it, a->xmap.
 // Uses a plan object on the stack whose containers stay empty (no heap use).
