@@ -165,6 +165,7 @@ struct deinsum_batch_s {
     bool tables_uploaded = false;
     std::vector<const void *> ptrs;  // cached pointers of the last execute
     cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;  // capture stream
 };
 
 namespace {
@@ -457,10 +458,13 @@ deinsum_status deinsum_execute_batched(deinsum_batch_t b, const void *const *con
         // first run with these pointers: launch directly (sets kernel attributes), then capture
         st = launch_batch(b, s);
         if (st != DEINSUM_OK) return st;
+        // capture on the plan's own stream (the caller's may be the legacy default
+        // stream, which cannot be captured); the graph is launched on the caller's
+        if (!b->cap && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return DEINSUM_ERR_CUDA;
         cudaGraph_t graph = nullptr;
-        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DEINSUM_ERR_CUDA;
-        st = launch_batch(b, s);
-        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DEINSUM_ERR_CUDA;
+        st = launch_batch(b, b->cap);
+        cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
         if (st != DEINSUM_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             cudaGetLastError();
@@ -549,6 +553,7 @@ void deinsum_batched_destroy(deinsum_batch_t b) {
     destroy_graph(b);
     for (auto p : b->plans)
         if (p) deinsum_destroy(p);
+    if (b->cap) cudaStreamDestroy(b->cap);
     if (b->ws) cudaFree(b->ws);
     if (b->staging) cudaFreeHost(b->staging);
     delete b;
