@@ -669,12 +669,15 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         BIter it;
         it.init(&bargs);
         uint32_t bpar = 0, bused = 0;
+        // the raw ring carries only the chunks of TMA-loaded instances: count those apart
+        int64_t tchunk = 0;
         for (int64_t chunk = 0; !it.done; ++chunk) {
             const MttkrpArgs &a = *it.a;
             float4 v[8];
-            const int rs = int(chunk % RS);
+            const int rs = int(tchunk % RS);
             if (a.use_tma) {
-                const uint32_t rj = uint32_t(chunk / RS);
+                const uint32_t rj = uint32_t(tchunk / RS);
+                ++tchunk;
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
                 conv_read_smem(a, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
             } else {
@@ -711,15 +714,17 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             int last_rs = -1;
             uint32_t last_par = 0;
             const MttkrpArgs *fenced = nullptr;
-            for (int64_t chunk = 0; !it.done; ++chunk) {
+            int64_t tchunk = 0;  // chunks of TMA-loaded instances only (the raw ring's sequence)
+            while (!it.done) {
                 const MttkrpArgs &a = *it.a;
                 if (a.use_tma && fenced != it.a) {
                     fence_tensormap_acquire(&a.xmap);
                     fenced = it.a;
                 }
                 if (a.use_tma) {
-                    const int rs = int(chunk % RS);
-                    const uint32_t rj = uint32_t(chunk / RS);
+                    const int rs = int(tchunk % RS);
+                    const uint32_t rj = uint32_t(tchunk / RS);
+                    ++tchunk;
                     if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status)) break;
                     mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                     const int kc = it.kb * BK;
