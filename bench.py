@@ -259,6 +259,78 @@ def run_serving(args):
     return 0
 
 
+def run_batched(args):
+    """512 uneven order-3 MTTKRP instances (extents U{32..384}, R in {8,16,32,64}, mode U{0,1,2},
+    X uniform[-1,1) float32): one graph-replayed persistent split-BF16 launch (autotuned unit
+    size) against 512 separate plain launches and 512 separate split launches."""
+    import torch
+    import oracle
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    n, seed = args.instances, 33
+    ext = inputs.draw_int(seed, 0, 32, 384, 3 * n).reshape(n, 3)
+    ranks = np.array([8, 16, 32, 64])[inputs.draw_int(seed, 1, 0, 3, n)]
+    modes = inputs.draw_int(seed, 2, 0, 2, n)
+    einsums, extents, ins, outs, facs = [], [], [], [], []
+    for k in range(n):
+        dims = tuple(int(d) for d in ext[k])
+        R, mode = int(ranks[k]), int(modes[k])
+        X = dz.gen_uniform(seed * 10000 + k, inputs.STREAM_X, dims)
+        U = [torch.from_numpy(inputs.factor_normal(seed * 10000 + k, m, d, R).astype(np.float32)).cuda()
+             for m, d in enumerate(dims)]
+        einsums.append(dz.mttkrp_einsum(3, mode))
+        extents.append(list(dims) + [R])
+        ins.append([X] + [U[m] for m in range(3) if m != mode])
+        outs.append(torch.empty(dims[mode], R, device="cuda"))
+        facs.append(U)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+
+    def timed(fn, reps):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    bsplit = dz.Batch(einsums, extents, "split_bf16")
+    with torch.cuda.stream(stream):
+        tune_ms = bsplit.autotune(ins, outs, stream=stream)
+    t_batch = timed(lambda: bsplit(ins, outs, stream=stream), args.steps)
+    info = bsplit.info()
+    status = bsplit.status()
+    # accuracy on a sample of instances (FP64 oracle on 4 sampled rows of each)
+    errs = []
+    for k in range(0, n, max(1, n // 16)):
+        dims, mode = tuple(int(d) for d in ext[k]), int(modes[k])
+        rows = inputs.sample_rows(seed * 10000 + k, dims[mode], 4)
+        Xh = ins[k][0]
+        slabs = np.stack([Xh.select(mode, int(r)).cpu().numpy().ravel() for r in rows])
+        ref = oracle.mttkrp_rows(dims, mode, slabs, [f.cpu().numpy() for f in facs[k]])
+        errs.append(oracle.rel_error(outs[k][torch.from_numpy(rows).cuda()].cpu().numpy(), ref))
+    bplain = dz.Batch(einsums, extents, "plain")
+    t_plain = timed(lambda: bplain(ins, outs, stream=stream), max(1, args.steps // 2))
+    plans = [dz.Plan(e, x, "float32", "split_bf16") for e, x in zip(einsums, extents)]
+    t_sep = timed(lambda: [p(*i, out=o, stream=stream) for p, i, o in zip(plans, ins, outs)], max(1, args.steps // 2))
+    gb = info["alg_bytes"] / 1e9
+    line = {"metric": "batched MTTKRP GB/s (one persistent launch vs separate launches)", "unit": "GB/s",
+            "value": gb / (t_batch * 1e-3), "n_gpus": 1, "instances": n, "data": "synthetic",
+            "config": {"workload": f"{n} order-3 MTTKRP instances, extents U{{32..384}}, R in {{8,16,32,64}}, "
+                                   "mode U{0,1,2}, X uniform[-1,1) float32", "alg_gb": gb,
+                       "units": info["units"], "grid": info["grid"], "unit_div_autotuned": info["unit_div"]},
+            "batched_split_ms": t_batch, "separate_plain_launches_ms": t_plain,
+            "separate_split_launches_ms": t_sep, "speedup_vs_plain_launches": t_plain / t_batch,
+            "speedup_vs_separate_split": t_sep / t_batch, "autotune_best_ms": tune_ms,
+            "rel_err_max_sampled": max(errs), "device_status": status}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -299,14 +371,17 @@ def main():
                     help="profiling driver: one execute per mode of --modes at extent --n, no timing")
     ap.add_argument("--n", type=int, default=N_EXT, help="extent of each mode (--once only)")
     ap.add_argument("--modes", default="0,1,2", help="modes to run (--once only)")
-    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving"],
-                    help="mttkrp: the benchmark line; serving: the CP-ALS serving measurement")
+    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving", "batched"],
+                    help="mttkrp: the benchmark line; serving / batched: the serving and batched measurements")
     ap.add_argument("--requests", type=int, default=128, help="requests of the serving workload")
+    ap.add_argument("--instances", type=int, default=512, help="instances of the batched workload")
     args = ap.parse_args()
     if args.once:
         return run_once(args)
     if args.workload == "serving" and args.impl == "native":
         return run_serving(args)
+    if args.workload == "batched" and args.impl == "native":
+        return run_batched(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
