@@ -343,7 +343,7 @@ void deinsum_server_destroy(deinsum_server_t s);
  * synchronisation of cudaMalloc / cudaFree.  It computes the same mode-`mode`
  * MTTKRP as deinsum_plan + deinsum_execute with DEINSUM_PREC_SPLIT_BF16 and
  * the same kernels, but keeps its scratch (schedule, per-unit partial sums,
- * split factor tiles, status word) in one fixed device array of about 9 MiB
+ * split factor tiles, weight tables, status word) in one fixed device array of about 13 MiB
  * inside the library, which every GPU that loads the library holds until the
  * process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
  *
@@ -356,7 +356,11 @@ void deinsum_server_destroy(deinsum_server_t s);
  *   out          DEVICE pointer to the I_n x R row-major float32 output (overwritten).
  * Limits of the fixed scratch: I_n <= 32768 (at most 256 blocks of 128 output
  * rows); the mode contracted on the tensor cores (I_{N-1}, or I_{N-2} when
- * n = N-1) at most 16384 for R <= 16, 8192 for R <= 32, 4096 for R <= 64.
+ * n = N-1) at most 16384 for R <= 16, 8192 for R <= 32, 4096 for R <= 64;
+ * the weight tables, (P' + O') x R_pad floats, at most 2^20 floats, where
+ * P' = I_0 ... I_{n-1} when 0 < n < N-1 (else 0), O' = I_{n+1} ... I_{N-2}
+ * when n < N-2, I_0 ... I_{N-3} when n = N-1 and N > 2 (else 0), and R_pad is
+ * R rounded up to 16, 32 or 64.
  * Larger problems return DEINSUM_ERR_SHAPE without launching anything.
  * Returns DEINSUM_ERR_INVALID for NULL pointers or a bad order / mode,
  * DEINSUM_ERR_ALIGN for pointers not 4-byte aligned, DEINSUM_ERR_CUDA when a

@@ -154,12 +154,14 @@ struct deinsum_batch_s {
     std::vector<int64_t> red_col;    // per instance: n_cols + 1 starts into red_off
     std::vector<int64_t> red_col_base;
     std::vector<size_t> bsplit_off;
-    size_t partial_floats = 0, bsplit_bytes = 0;
+    std::vector<size_t> wtab_off;    // per instance: its weight tables (L, then O)
+    size_t partial_floats = 0, bsplit_bytes = 0, wtab_bytes = 0;
+    int64_t max_wtab_floats = 0;
     // device
     char *ws = nullptr;
     size_t ws_bytes = 0;
     size_t o_status = 0, o_insts = 0, o_split = 0, o_red = 0, o_units = 0, o_cta = 0, o_redoff = 0, o_redcol = 0,
-           o_bsplit = 0, o_partial = 0, o_end = 0;
+           o_bsplit = 0, o_wtab = 0, o_partial = 0, o_end = 0;
     char *staging = nullptr;  // pinned: insts + split table + reduce table
     size_t staging_bytes = 0;
     bool tables_uploaded = false;
@@ -190,8 +192,11 @@ void build_batch_schedule(deinsum_batch_s *b) {
     b->red_col.clear();
     b->red_col_base.assign(size_t(b->n), 0);
     b->bsplit_off.assign(size_t(b->n), 0);
+    b->wtab_off.assign(size_t(b->n), 0);
     b->partial_floats = 0;
     b->bsplit_bytes = 0;
+    b->wtab_bytes = 0;
+    b->max_wtab_floats = 0;
     for (int i = 0; i < b->n; ++i) {
         const MttkrpGeom &g = b->inst[size_t(i)].g;
         const int64_t max_units = g.n_cols * g.fg_per_col;
@@ -213,6 +218,10 @@ void build_batch_schedule(deinsum_batch_s *b) {
         b->red_col.push_back(int64_t(b->red_off.size()));
         b->bsplit_off[size_t(i)] = b->bsplit_bytes;
         b->bsplit_bytes += up(size_t(g.n_kb) * 2 * size_t(g.R_pad) * BK * 2, 1024);
+        const size_t wf = weight_table_floats_l(g) + weight_table_floats_o(g);
+        b->wtab_off[size_t(i)] = b->wtab_bytes;
+        b->wtab_bytes += up(wf * 4, 256);
+        b->max_wtab_floats = std::max<int64_t>(b->max_wtab_floats, int64_t(wf));
     }
     b->grid = int(std::min<int64_t>(b->n_sm, int64_t(all.size())));
     if (b->grid < 1) b->grid = 1;
@@ -258,6 +267,7 @@ deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
     b->o_redoff = take(b->red_off.size() * 8, 256);
     b->o_redcol = take(b->red_col.size() * 8, 256);
     b->o_bsplit = take(b->bsplit_bytes, 1024);
+    b->o_wtab = take(b->wtab_bytes, 256);
     b->o_partial = take(b->partial_floats * 4, 1024);
     b->o_end = up(off, 1024);
     if (b->o_end > b->ws_bytes) {
@@ -307,6 +317,8 @@ deinsum_status upload_instances(deinsum_batch_s *b, const void *const *const *in
         a.X = inputs[i][0];
         for (int k = 1; k < in.n_ops; ++k) a.U[in.opmode[k]] = inputs[i][k];
         a.Bsplit = b->ws + b->o_bsplit + b->bsplit_off[size_t(i)];
+        a.Lw = reinterpret_cast<float *>(b->ws + b->o_wtab + b->wtab_off[size_t(i)]);
+        a.Ow = a.Lw + weight_table_floats_l(a.g);
         a.status = reinterpret_cast<int *>(b->ws + b->o_status);
         const int inner = a.g.kcase == 0 ? a.g.order - 1 : a.g.order - 2;
         S[i] = {static_cast<const float *>(a.U[inner]), static_cast<unsigned char *>(const_cast<void *>(a.Bsplit)),
@@ -333,6 +345,9 @@ deinsum_status launch_batch(deinsum_batch_s *b, cudaStream_t s) {
     batched_split_kernel<<<dim3(unsigned(gx), unsigned(b->n)), 256, 0, s>>>(
         reinterpret_cast<const SplitInst *>(b->ws + b->o_split));
     count_launch();
+    if (launch_weight_tables_batched(reinterpret_cast<const MttkrpArgs *>(b->ws + b->o_insts), b->n,
+                                     b->max_wtab_floats, s))
+        return DEINSUM_ERR_CUDA;
     BatchArgs ba;
     ba.insts = reinterpret_cast<const MttkrpArgs *>(b->ws + b->o_insts);
     ba.units = reinterpret_cast<const int64_t *>(b->ws + b->o_units);

@@ -7,7 +7,7 @@
 //     run over q = (o, k), where k indexes the last mode I_{N-1} (the "inner"
 //     mode contracted on the tensor cores, stride 1 in memory) and o the modes
 //     n+1..N-2 ("outer" modes).  Rows are grouped 128 to a tile: one p and 128
-//     consecutive i_n when I_n >= 128 ("wide"), else G = floor(128/I_n)
+//     consecutive i_n when I_n >= 128 ("wide"), else G = min(floor(128/I_n), 32)
 //     consecutive p with all I_n rows each ("narrow").
 //   case 1 (n = N-1, "M-contiguous"): a row is one i_n; its elements run over
 //     p = (o, k) with k indexing mode N-2 (inner) and o modes 0..N-3 (outer);
@@ -37,6 +37,7 @@
 #define DEINSUM_MAX_ORDER 8
 #define DEINSUM_BM 128
 #define DEINSUM_BK 64
+#define DEINSUM_GMAX 32  // most p values in one narrow tile (bounds the weight-ring slots)
 
 namespace deinsum {
 
@@ -76,6 +77,8 @@ struct MttkrpArgs {
     const void *X;
     const void *U[DEINSUM_MAX_ORDER];  // factor of each mode (U[mode] unused)
     const void *Bsplit;                // split-BF16 tiles of the inner factor (TC path)
+    float *Lw;                         // TC path, n_lmodes > 0: P x R_pad row weights (weight_tables)
+    float *Ow;                         // TC path, n_outer > 0:  O x R_pad fiber weights
     const int64_t *units;              // n_units x 3: column, first fiber group, end
     int64_t n_units;
     float *partial;                    // n_units x 128 x R_pad (F32 paths)
@@ -104,6 +107,13 @@ int launch_mttkrp_plain_f32(const MttkrpArgs &a, int n_sm, void *stream);
 int launch_mttkrp_plain_f64(const MttkrpArgs &a, int n_sm, void *stream);
 int launch_mttkrp_tc(const MttkrpArgs &a, int n_sm, void *stream);
 int launch_split_inner_factor(const MttkrpArgs &a, void *bsplit, void *stream);
+// Weight tables of the tensor-core kernel (a.Lw, a.Ow; sizes below).
+int launch_weight_tables(const MttkrpArgs &a, void *stream);
+// The same for n instances whose arguments are in device memory (max_floats: the largest L + O table).
+int launch_weight_tables_batched(const MttkrpArgs *insts, int n, int64_t max_floats, void *stream);
+// Floats of the two tables: P x R_pad (if n_lmodes > 0) and O x R_pad (if n_outer > 0).
+inline size_t weight_table_floats_l(const MttkrpGeom &g) { return g.n_lmodes > 0 ? size_t(g.P) * size_t(g.R_pad) : 0; }
+inline size_t weight_table_floats_o(const MttkrpGeom &g) { return g.n_outer > 0 ? size_t(g.O) * size_t(g.R_pad) : 0; }
 int launch_mttkrp_reduce_f32(const MttkrpArgs &a, const int64_t *col_unit_begin, void *out, void *stream);
 int launch_mttkrp_reduce_f64(const MttkrpArgs &a, const int64_t *col_unit_begin, void *out, void *stream);
 size_t mttkrp_tc_smem_bytes(int R_pad);

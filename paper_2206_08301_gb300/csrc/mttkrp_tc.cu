@@ -53,10 +53,16 @@ template <int RP> struct TcCfg {
     static constexpr int A_BYTES = BM * BK * 2;            // one of hi / lo
     static constexpr int B_BYTES = N * BK * 2;
     static constexpr int ASTAGE_BYTES = 2 * A_BYTES + B_BYTES;
-    static constexpr int LROW_BYTES = BM * RP * 4;         // per-row weights of narrow tiles
+    // weight ring: one slot per fiber group in flight, holding its Ofac row
+    // (RP floats) and then its L rows (one per p of the tile, at most GMAX)
+    static constexpr int WSLOTS = 4;
+    static constexpr int WSLOT_FLOATS = (DEINSUM_GMAX + 1) * RP;
+    static constexpr int WBUF_BYTES = WSLOTS * WSLOT_FLOATS * 4;
     static constexpr int TMEM_COLS = 2 * N;                // two accumulators
-    static constexpr int NBARS = 2 * RS + 3 * AS + 4 + 1;
-    static constexpr size_t SMEM = size_t(RS) * RAW_BYTES + size_t(AS) * ASTAGE_BYTES + LROW_BYTES + 1024 + 256;
+    static constexpr int NBARS = 2 * RS + 3 * AS + 4 + 1 + 2 * WSLOTS;
+    static constexpr size_t SMEM = size_t(RS) * RAW_BYTES + size_t(AS) * ASTAGE_BYTES + WBUF_BYTES + 1024 + 512;
+    static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB per-CTA limit");
+    static_assert(NBARS * 8 + 8 <= 512, "barrier area");
 };
 
 struct Iter {
@@ -239,6 +245,64 @@ __device__ __forceinline__ float row_weight(const MttkrpArgs &a, int64_t p, int 
     return v;
 }
 
+// Weight tables (one pass before the tensor-core kernel, so that its epilogue
+// reads each fiber group's weights as whole rows, copied ahead by the TMA warp):
+//   Lw[p, c] = row_weight(p, c)    (n_lmodes > 0), p < P
+//   Ow[o, c] = outer_weight(o, c)  (n_outer > 0),  o < O
+// for c < R_pad, zero for c >= R (the products in the same order as above).
+__device__ __forceinline__ void weight_tables_body(const MttkrpArgs &a, int64_t t0, int64_t stride) {
+    const MttkrpGeom &g = a.g;
+    const int rp = g.R_pad;
+    const int64_t nl = g.n_lmodes > 0 ? g.P * rp : 0;
+    const int64_t no = g.n_outer > 0 ? g.O * rp : 0;
+    for (int64_t t = t0; t < nl + no; t += stride) {
+        if (t < nl) {
+            const int64_t p = t / rp;
+            const int c = int(t - p * rp);
+            a.Lw[t] = c < g.R ? row_weight(a, p, c) : 0.f;
+        } else {
+            const int64_t u = t - nl;
+            const int64_t o = u / rp;
+            const int c = int(u - o * rp);
+            a.Ow[u] = c < g.R ? outer_weight(a, o, c) : 0.f;
+        }
+    }
+}
+
+__global__ void weight_tables_kernel(const __grid_constant__ MttkrpArgs a) {
+    weight_tables_body(a, int64_t(blockIdx.x) * blockDim.x + threadIdx.x, int64_t(gridDim.x) * blockDim.x);
+}
+
+__global__ void batched_weight_tables_kernel(const MttkrpArgs *__restrict__ insts) {
+    weight_tables_body(insts[blockIdx.y], int64_t(blockIdx.x) * blockDim.x + threadIdx.x,
+                       int64_t(gridDim.x) * blockDim.x);
+}
+
+// Copy the weights of fiber group (tile, o) into a weight-ring slot (TMA warp,
+// one thread): Ofac(o) at floats [0, rp), then the L rows of the tile's p
+// values at [rp, ...), completing on `bar` (a plain arrive when there are none).
+__device__ __forceinline__ void load_fg_weights(const MttkrpArgs &a, int64_t tile, int64_t o, uint32_t dst,
+                                                uint32_t bar) {
+    const MttkrpGeom &g = a.g;
+    const uint32_t rowb = uint32_t(g.R_pad) * 4u;
+    uint32_t bytes = 0, nl = 0;
+    int64_t p0 = 0;
+    if (g.n_outer > 0) bytes += rowb;
+    if (g.n_lmodes > 0) {
+        p0 = g.narrow ? tile * g.G : tile;
+        const int64_t rows = g.narrow ? (g.P - p0 < g.G ? g.P - p0 : g.G) : 1;
+        nl = uint32_t(rows);
+        bytes += nl * rowb;
+    }
+    if (bytes == 0) {
+        mbar_arrive(bar);
+        return;
+    }
+    mbar_arrive_expect_tx(bar, bytes);
+    if (g.n_outer > 0) bulk_g2s(dst, a.Ow + o * g.R_pad, rowb, bar);
+    if (nl) bulk_g2s(dst + rowb, a.Lw + p0 * g.R_pad, nl * rowb, bar);
+}
+
 template <int RP>
 __global__ void __launch_bounds__(TcCfg<RP>::THREADS, 1)
 mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
@@ -249,8 +313,8 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *raw_base = smem;
     unsigned char *a_base = smem + RS * C::RAW_BYTES;
-    float *Lrow = reinterpret_cast<float *>(a_base + AS * C::ASTAGE_BYTES);   // [RP][BM], thread-private columns
-    uint64_t *bars = reinterpret_cast<uint64_t *>(a_base + AS * C::ASTAGE_BYTES + C::LROW_BYTES);
+    float *wbuf = reinterpret_cast<float *>(a_base + AS * C::ASTAGE_BYTES);   // weight ring
+    uint64_t *bars = reinterpret_cast<uint64_t *>(a_base + AS * C::ASTAGE_BYTES + C::WBUF_BYTES);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
@@ -268,6 +332,9 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     auto accf = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + b); };
     auto acce = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + 2 + b); };
     const uint32_t drain = smem_u32(bars + 2 * RS + 3 * AS + 4);
+    auto wfull = [&](int s) { return smem_u32(bars + 2 * RS + 3 * AS + 5 + s); };
+    auto wempty = [&](int s) { return smem_u32(bars + 2 * RS + 3 * AS + 5 + C::WSLOTS + s); };
+    auto wslot_addr = [&](int s) { return smem_u32(wbuf) + uint32_t(s) * uint32_t(C::WSLOT_FLOATS) * 4u; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < RS; ++s) {
@@ -284,6 +351,10 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             mbar_init(acce(b), EPI_WARPS);
         }
         mbar_init(drain, 1);
+        for (int s = 0; s < C::WSLOTS; ++s) {
+            mbar_init(wfull(s), 1);
+            mbar_init(wempty(s), EPI_WARPS);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -341,30 +412,44 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         }
     } else if (warp == C::TMA_WARP) {
         // ------------------------------------------------------------------ TMA
-        if (lane == 0 && a.use_tma) {
+        // (also the weight ring: every fiber group's weight rows, whether or not X goes by TMA)
+        if (lane == 0) {
             Iter it;
             it.init(a);
-            int last_rs = -1;
-            uint32_t last_par = 0;
+            int last_rs = -1, last_ws = -1;
+            uint32_t last_par = 0, last_wpar = 0;
+            int64_t fgi = 0;
             for (int64_t chunk = 0; !it.done; ++chunk) {
-                const int rs = int(chunk % RS);
-                const uint32_t rj = uint32_t(chunk / RS);
-                if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, a.status)) break;
-                mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
-                const int kc = it.kb * BK;
-                if (g.kcase == 0) {
-                    const int c2 = g.narrow ? 0 : int(it.col * BM);
-                    const int c3 = g.narrow ? int(it.tile * g.G) : int(it.tile);
-                    tma_load_4d(raw_addr(rs), &a.xmap, kc, int(it.o), c2, c3, raw_full(rs));
-                } else {
-                    tma_load_3d(raw_addr(rs), &a.xmap, int(it.col * BM), kc, int(it.o), raw_full(rs));
+                if (it.kb == 0) {
+                    const int ws = int(fgi % C::WSLOTS);
+                    const uint32_t wj = uint32_t(fgi / C::WSLOTS);
+                    if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, a.status)) break;
+                    load_fg_weights(a, it.tile, it.o, wslot_addr(ws), wfull(ws));
+                    last_ws = ws;
+                    last_wpar = wj & 1u;
+                    ++fgi;
                 }
-                last_rs = rs;
-                last_par = rj & 1u;
+                if (a.use_tma) {
+                    const int rs = int(chunk % RS);
+                    const uint32_t rj = uint32_t(chunk / RS);
+                    if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, a.status)) break;
+                    mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
+                    const int kc = it.kb * BK;
+                    if (g.kcase == 0) {
+                        const int c2 = g.narrow ? 0 : int(it.col * BM);
+                        const int c3 = g.narrow ? int(it.tile * g.G) : int(it.tile);
+                        tma_load_4d(raw_addr(rs), &a.xmap, kc, int(it.o), c2, c3, raw_full(rs));
+                    } else {
+                        tma_load_3d(raw_addr(rs), &a.xmap, int(it.col * BM), kc, int(it.o), raw_full(rs));
+                    }
+                    last_rs = rs;
+                    last_par = rj & 1u;
+                }
                 it.next(a);
             }
-            // the last load has landed before exit (the earlier ones were consumed)
+            // the last loads have landed before exit (the earlier ones were consumed)
             if (last_rs >= 0) mbar_wait(raw_full(last_rs), last_par, abort_flag, a.status);
+            if (last_ws >= 0) mbar_wait(wfull(last_ws), last_wpar, abort_flag, a.status);
         }
         __syncwarp();
     } else if (warp == C::MMA_WARP) {
@@ -419,6 +504,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
         const int l = quad * 32 + lane;            // tile row of this thread
         const bool lane_weights = g.kcase == 0 && g.narrow && g.n_lmodes > 0;
+        const int lg = g.narrow ? int(l / g.I) : 0;   // narrow: p offset of row l within its tile
         Iter it;
         it.init(a);
         int64_t fgi = 0;
@@ -447,31 +533,29 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             };
             int64_t tile = -1;
             int folded = 0;
-            float lw_lane0 = 0.f, lw_lane1 = 0.f;  // lane-independent row weights (wide tiles), columns lane, lane+32
+            bool rv = true;  // narrow tiles: this thread's row holds a valid (p, i_n)
             while (!it.done && it.u == u) {
                 if (it.tile != tile) {
                     tile = it.tile;
-                    if (lane_weights) {
-                        // narrow tile: row l belongs to p = tile*G + l / I_n
-                        lw_lane0 = 1.f;
-                        lw_lane1 = 1.f;
-                        const int64_t rowbase = tile_rowbase(g, ucol, tile);
-                        const bool v = row_valid(g, ucol, rowbase, l);
-                        const int64_t p = tile * g.G + l / g.I;
-                        #pragma unroll 4
-                        for (int c = 0; c < RP; ++c)
-                            Lrow[c * BM + l] = (v && c < g.R) ? row_weight(a, p, c) : 0.f;
-                    } else if (g.kcase == 0 && g.n_lmodes > 0) {
-                        lw_lane0 = lane < g.R ? row_weight(a, tile, lane) : 0.f;
-                        if (RP > 32) lw_lane1 = lane + 32 < g.R ? row_weight(a, tile, lane + 32) : 0.f;
-                    } else {
-                        lw_lane0 = 1.f;
-                        lw_lane1 = 1.f;
-                    }
+                    if (lane_weights) rv = row_valid(g, ucol, tile_rowbase(g, ucol, tile), l);
                 }
-                // weights of this fiber group: lane c holds column c (and c + 32)
-                const float w0 = lane < g.R ? lw_lane0 * outer_weight(a, it.o, lane) : 0.f;
-                const float w1 = (RP > 32 && lane + 32 < g.R) ? lw_lane1 * outer_weight(a, it.o, lane + 32) : 0.f;
+                // weights of this fiber group, from its ring slot: lane c holds column c (and c + 32)
+                const int ws = int(fgi % C::WSLOTS);
+                const uint32_t wj = uint32_t(fgi / C::WSLOTS);
+                if (!__all_sync(0xffffffffu, mbar_wait(wfull(ws), wj & 1u, abort_flag, a.status))) {
+                    ok = false;
+                    break;
+                }
+                const float *wsl = wbuf + ws * C::WSLOT_FLOATS;
+                const float *lrow = wsl + RP * (1 + lg);   // narrow: L row of this thread's p
+                float w0 = g.n_outer > 0 ? wsl[lane] : 1.f;
+                float w1 = (RP > 32 && g.n_outer > 0) ? wsl[lane + 32] : 1.f;
+                if (!lane_weights && g.n_lmodes > 0) {
+                    w0 = wsl[RP + lane] * w0;
+                    if (RP > 32) w1 = wsl[RP + lane + 32] * w1;
+                }
+                if (lane >= g.R) w0 = 0.f;
+                if (RP <= 32 || lane + 32 >= g.R) w1 = 0.f;
                 const int b = int(fgi & 1);
                 const uint32_t jb = uint32_t(fgi >> 1);
                 if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, a.status))) {
@@ -490,13 +574,17 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     for (int q = 0; q < 16; ++q) {
                         const int col = c + q;
                         float w = __shfl_sync(0xffffffffu, col < 32 ? w0 : w1, col & 31);
-                        if (lane_weights) w *= Lrow[col * BM + l];
+                        if (lane_weights) w *= rv ? lrow[col] : 0.f;
                         acc[col] = fmaf(w, __uint_as_float(hi[q]) + __uint_as_float(lo[q]), acc[col]);
                     }
                 }
                 tc_fence_before();
+                fence_proxy_async_smem();   // the slot's reads before its next bulk-copy write
                 __syncwarp();
-                if (lane == 0) mbar_arrive(acce(b));
+                if (lane == 0) {
+                    mbar_arrive(wempty(ws));
+                    mbar_arrive(acce(b));
+                }
                 ++fgi;
                 if (++folded == kFoldEvery) {
                     folded = 0;
@@ -614,8 +702,8 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *raw_base = smem;
     unsigned char *a_base = smem + RS * C::RAW_BYTES;
-    float *Lrow = reinterpret_cast<float *>(a_base + AS * C::ASTAGE_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(a_base + AS * C::ASTAGE_BYTES + C::LROW_BYTES);
+    float *wbuf = reinterpret_cast<float *>(a_base + AS * C::ASTAGE_BYTES);   // weight ring
+    uint64_t *bars = reinterpret_cast<uint64_t *>(a_base + AS * C::ASTAGE_BYTES + C::WBUF_BYTES);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
     int *status = bargs.status;
@@ -634,6 +722,9 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     auto accf = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + b); };
     auto acce = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + 2 + b); };
     const uint32_t drain = smem_u32(bars + 2 * RS + 3 * AS + 4);
+    auto wfull = [&](int s) { return smem_u32(bars + 2 * RS + 3 * AS + 5 + s); };
+    auto wempty = [&](int s) { return smem_u32(bars + 2 * RS + 3 * AS + 5 + C::WSLOTS + s); };
+    auto wslot_addr = [&](int s) { return smem_u32(wbuf) + uint32_t(s) * uint32_t(C::WSLOT_FLOATS) * 4u; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < RS; ++s) {
@@ -650,6 +741,10 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             mbar_init(acce(b), EPI_WARPS);
         }
         mbar_init(drain, 1);
+        for (int s = 0; s < C::WSLOTS; ++s) {
+            mbar_init(wfull(s), 1);
+            mbar_init(wempty(s), EPI_WARPS);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -708,15 +803,26 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         }
     } else if (warp == C::TMA_WARP) {
         // ------------------------------------------------------------------ TMA
+        // (also the weight ring: every fiber group's weight rows, whether or not X goes by TMA)
         if (lane == 0) {
             BIter it;
             it.init(&bargs);
-            int last_rs = -1;
-            uint32_t last_par = 0;
+            int last_rs = -1, last_ws = -1;
+            uint32_t last_par = 0, last_wpar = 0;
             const MttkrpArgs *fenced = nullptr;
             int64_t tchunk = 0;  // chunks of TMA-loaded instances only (the raw ring's sequence)
+            int64_t fgi = 0;
             while (!it.done) {
                 const MttkrpArgs &a = *it.a;
+                if (it.kb == 0) {
+                    const int ws = int(fgi % C::WSLOTS);
+                    const uint32_t wj = uint32_t(fgi / C::WSLOTS);
+                    if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, status)) break;
+                    load_fg_weights(a, it.tile, it.o, wslot_addr(ws), wfull(ws));
+                    last_ws = ws;
+                    last_wpar = wj & 1u;
+                    ++fgi;
+                }
                 if (a.use_tma && fenced != it.a) {
                     fence_tensormap_acquire(&a.xmap);
                     fenced = it.a;
@@ -741,6 +847,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 it.next();
             }
             if (last_rs >= 0) mbar_wait(raw_full(last_rs), last_par, abort_flag, status);
+            if (last_ws >= 0) mbar_wait(wfull(last_ws), last_wpar, abort_flag, status);
         }
         __syncwarp();
     } else if (warp == C::MMA_WARP) {
@@ -824,27 +931,29 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             };
             int64_t tile = -1;
             int folded = 0;
-            float lw_lane0 = 0.f, lw_lane1 = 0.f;
+            bool rv = true;  // narrow tiles: this thread's row holds a valid (p, i_n)
+            const int lg = g.narrow ? int(l / g.I) : 0;
             while (!it.done && it.u == u) {
                 if (it.tile != tile) {
                     tile = it.tile;
-                    if (lane_weights) {
-                        lw_lane0 = 1.f;
-                        lw_lane1 = 1.f;
-                        const int64_t rowbase = tile_rowbase(g, ucol, tile);
-                        const bool v = row_valid(g, ucol, rowbase, l);
-                        const int64_t p = tile * g.G + l / g.I;
-                        for (int c = 0; c < rp; ++c) Lrow[c * BM + l] = (v && c < g.R) ? row_weight(a, p, c) : 0.f;
-                    } else if (g.kcase == 0 && g.n_lmodes > 0) {
-                        lw_lane0 = lane < g.R ? row_weight(a, tile, lane) : 0.f;
-                        lw_lane1 = lane + 32 < g.R ? row_weight(a, tile, lane + 32) : 0.f;
-                    } else {
-                        lw_lane0 = 1.f;
-                        lw_lane1 = 1.f;
-                    }
+                    if (lane_weights) rv = row_valid(g, ucol, tile_rowbase(g, ucol, tile), l);
                 }
-                const float w0 = lane < g.R ? lw_lane0 * outer_weight(a, it.o, lane) : 0.f;
-                const float w1 = lane + 32 < g.R ? lw_lane1 * outer_weight(a, it.o, lane + 32) : 0.f;
+                const int ws = int(fgi % C::WSLOTS);
+                const uint32_t wj = uint32_t(fgi / C::WSLOTS);
+                if (!__all_sync(0xffffffffu, mbar_wait(wfull(ws), wj & 1u, abort_flag, status))) {
+                    ok = false;
+                    break;
+                }
+                const float *wsl = wbuf + ws * C::WSLOT_FLOATS;
+                const float *lrow = wsl + rp * (1 + lg);
+                float w0 = g.n_outer > 0 ? wsl[lane] : 1.f;
+                float w1 = (rp > 32 && g.n_outer > 0) ? wsl[lane + 32] : 1.f;
+                if (!lane_weights && g.n_lmodes > 0) {
+                    w0 = wsl[rp + lane] * w0;
+                    if (rp > 32) w1 = wsl[rp + lane + 32] * w1;
+                }
+                if (lane >= g.R) w0 = 0.f;
+                if (rp <= 32 || lane + 32 >= g.R) w1 = 0.f;
                 const int b = int(fgi & 1);
                 const uint32_t jb = uint32_t(fgi >> 1);
                 if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) {
@@ -864,14 +973,18 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                         for (int q = 0; q < 16; ++q) {
                             const int col = c + q;
                             float w = __shfl_sync(0xffffffffu, col < 32 ? w0 : w1, col & 31);
-                            if (lane_weights) w *= Lrow[col * BM + l];
+                            if (lane_weights) w *= rv ? lrow[col] : 0.f;
                             acc[col] = fmaf(w, __uint_as_float(hi[q]) + __uint_as_float(lo[q]), acc[col]);
                         }
                     }
                 }
                 tc_fence_before();
+                fence_proxy_async_smem();   // the slot's reads before its next bulk-copy write
                 __syncwarp();
-                if (lane == 0) mbar_arrive(acce(b));
+                if (lane == 0) {
+                    mbar_arrive(wempty(ws));
+                    mbar_arrive(acce(b));
+                }
                 ++fgi;
                 if (++folded == kFoldEvery) {
                     folded = 0;
@@ -926,6 +1039,25 @@ int launch_split_inner_factor(const MttkrpArgs &a, void *bsplit, void *stream) {
     if (blocks > 4096) blocks = 4096;
     split_inner_factor_kernel<<<unsigned(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         static_cast<const float *>(a.U[inner]), static_cast<unsigned char *>(bsplit), g.K_in, g.R, g.R_pad, g.n_kb);
+    count_launch();
+    return int(cudaGetLastError());
+}
+
+int launch_weight_tables(const MttkrpArgs &a, void *stream) {
+    const int64_t total = int64_t(weight_table_floats_l(a.g) + weight_table_floats_o(a.g));
+    if (total == 0) return 0;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 2048) blocks = 2048;
+    weight_tables_kernel<<<unsigned(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(a);
+    count_launch();
+    return int(cudaGetLastError());
+}
+
+int launch_weight_tables_batched(const MttkrpArgs *insts, int n, int64_t max_floats, void *stream) {
+    if (max_floats == 0) return 0;
+    int64_t bx = (max_floats + 255) / 256;
+    if (bx > 64) bx = 64;
+    batched_weight_tables_kernel<<<dim3(unsigned(bx), unsigned(n)), 256, 0, static_cast<cudaStream_t>(stream)>>>(insts);
     count_launch();
     return int(cudaGetLastError());
 }

@@ -5,8 +5,8 @@
 // HBM budget), or latency-critical loops where the implicit device
 // synchronisation of cudaMalloc / cudaFree is not acceptable.  This entry
 // point runs the same kernels as deinsum_execute for a split-BF16 MTTKRP, but
-// its scratch (schedule table, per-unit partial sums, split factor tiles and
-// status word) lives in one fixed file-scope device array, so no call
+// its scratch (schedule table, per-unit partial sums, split factor tiles,
+// weight tables and status word) lives in one fixed file-scope device array, so no call
 // allocates device memory.  The array is created with the library's module
 // on every GPU that loads it and is held until the process exits.
 #include <cuda_runtime.h>
@@ -30,7 +30,9 @@ constexpr size_t kOffBsplit = 16384;                        // split factor tile
 constexpr size_t kBsplitBytes = size_t(1) << 20;            // 64 tiles at rank 64
 constexpr size_t kOffPartial = kOffBsplit + kBsplitBytes;
 constexpr size_t kPartialBytes = size_t(kMaxUnits) * DEINSUM_BM * 64 * 4;  // 8 MiB
-constexpr size_t kScratchBytes = kOffPartial + kPartialBytes;
+constexpr size_t kOffWtab = kOffPartial + kPartialBytes;
+constexpr size_t kWtabBytes = size_t(1) << 22;              // weight tables, 1 Mi floats
+constexpr size_t kScratchBytes = kOffWtab + kWtabBytes;
 static_assert(kOffCols + size_t(kMaxCols + 1) * 8 <= kOffBsplit, "scratch layout overlap");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -111,8 +113,10 @@ extern "C" deinsum_status deinsum_mttkrp_noalloc(int order, const int64_t *dims,
     if (per_col > g.fg_per_col) per_col = g.fg_per_col;
     const int64_t n_units = g.n_cols * per_col;
     const size_t bsplit_bytes = size_t(g.n_kb) * 2 * size_t(g.R_pad) * DEINSUM_BK * 2;
+    const size_t wtab_floats_l = weight_table_floats_l(g);
     if (g.n_cols > kMaxCols || n_units > kMaxUnits || bsplit_bytes > kBsplitBytes ||
-        size_t(n_units) * DEINSUM_BM * size_t(g.R_pad) * 4 > kPartialBytes)
+        size_t(n_units) * DEINSUM_BM * size_t(g.R_pad) * 4 > kPartialBytes ||
+        (wtab_floats_l + weight_table_floats_o(g)) * 4 > kWtabBytes)
         return DEINSUM_ERR_SHAPE;
 
     for (int m = 0; m < order; ++m) a.U[m] = (m == mode) ? nullptr : factors[m];
@@ -122,6 +126,8 @@ extern "C" deinsum_status deinsum_mttkrp_noalloc(int order, const int64_t *dims,
     a.partial = reinterpret_cast<float *>(scratch + kOffPartial);
     a.status = reinterpret_cast<int *>(scratch + kOffStatus);
     a.Bsplit = scratch + kOffBsplit;
+    a.Lw = reinterpret_cast<float *>(scratch + kOffWtab);
+    a.Ow = a.Lw + wtab_floats_l;
     int64_t *cols = reinterpret_cast<int64_t *>(scratch + kOffCols);
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -131,6 +137,7 @@ extern "C" deinsum_status deinsum_mttkrp_noalloc(int order, const int64_t *dims,
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return DEINSUM_ERR_CUDA;
     int err = launch_split_inner_factor(a, scratch + kOffBsplit, stream);
+    if (!err) err = launch_weight_tables(a, stream);
     if (!err) err = launch_mttkrp_tc(a, n_sm, stream);
     if (!err) err = launch_mttkrp_reduce_f32(a, cols, out, stream);
     return err ? DEINSUM_ERR_CUDA : DEINSUM_OK;

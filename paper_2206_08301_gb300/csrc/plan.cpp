@@ -55,6 +55,7 @@ struct deinsum_plan_s {
     int64_t *d_col_begin = nullptr;
     void *d_partial = nullptr;
     void *d_bsplit = nullptr;
+    float *d_wtab = nullptr;   // weight tables of the tensor-core kernel (L, then O)
     int *d_status = nullptr;
     void *d_ttm[2] = {nullptr, nullptr};
 
@@ -169,7 +170,7 @@ void build_mttkrp_geometry(deinsum_plan_s *pl) {
         g.n_lmodes = n;
         g.narrow = g.I < DEINSUM_BM ? 1 : 0;
         if (g.narrow) {
-            g.G = std::max<int64_t>(1, std::min<int64_t>(DEINSUM_BM / g.I, g.P));
+            g.G = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(DEINSUM_BM / g.I, DEINSUM_GMAX), g.P));
             g.n_cols = 1;
             g.tiles_per_col = (g.P + g.G - 1) / g.G;
             g.rows_per_col = g.I;
@@ -236,7 +237,7 @@ deinsum_status cuda_status(cudaError_t e) {
 }
 
 struct WsLayout {
-    size_t status = 0, units = 0, cols = 0, partial = 0, bsplit = 0, ttm0 = 0, ttm1 = 0, total = 0;
+    size_t status = 0, units = 0, cols = 0, partial = 0, bsplit = 0, wtab = 0, ttm0 = 0, ttm1 = 0, total = 0;
 };
 
 // Fix the device (the current one), the schedule (one unit per resident CTA:
@@ -273,6 +274,8 @@ deinsum_status plan_layout(deinsum_plan_s *pl, WsLayout &L) {
         if (pl->prec == DEINSUM_PREC_SPLIT_BF16) {
             L.bsplit = off;
             off = align_up(off + size_t(g.n_kb) * 2 * g.R_pad * DEINSUM_BK * 2, 1024);
+            L.wtab = off;
+            off = align_up(off + (weight_table_floats_l(g) + weight_table_floats_o(g)) * sizeof(float), 256);
         }
     } else {
         L.ttm0 = off;
@@ -298,6 +301,7 @@ deinsum_status attach_workspace(deinsum_plan_s *pl, char *ws, const WsLayout &L,
         pl->d_col_begin = reinterpret_cast<int64_t *>(pl->ws + L.cols);
         pl->d_partial = pl->ws + L.partial;
         pl->d_bsplit = pl->prec == DEINSUM_PREC_SPLIT_BF16 ? pl->ws + L.bsplit : nullptr;
+        pl->d_wtab = pl->prec == DEINSUM_PREC_SPLIT_BF16 ? reinterpret_cast<float *>(pl->ws + L.wtab) : nullptr;
         e = cudaMemcpyAsync(pl->d_units, pl->units.data(), pl->units.size() * sizeof(int64_t),
                             cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess)
@@ -520,6 +524,8 @@ deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, voi
         a.partial = static_cast<float *>(pl->d_partial);
         if (pl->prec == DEINSUM_PREC_SPLIT_BF16) {
             a.Bsplit = pl->d_bsplit;
+            a.Lw = pl->d_wtab;
+            a.Ow = pl->d_wtab + weight_table_floats_l(pl->geom);
             if (encode_x_map(pl, a.X)) {
                 a.xmap = pl->xmap;
                 a.use_tma = 1;
@@ -527,6 +533,7 @@ deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, voi
                 a.raw_pitch = pl->xmap_pitch;
             }
             err = launch_split_inner_factor(a, pl->d_bsplit, stream);
+            if (!err) err = launch_weight_tables(a, stream);
             const long ti = timing_begin(pl, stream);
             if (!err) err = launch_mttkrp_tc(a, pl->n_sm, stream);
             timing_end(pl, ti, stream);
