@@ -331,6 +331,74 @@ def run_batched(args):
     return 0
 
 
+def run_ttmc(args):
+    """TTMc X 256^4 FP32 uniform[-1,1), U1..U3 256x32 N(0,1), `ijkl,jb,kc,ld->ibcd`: the fused split-BF16
+    path (last two modes on the tensor cores, T1 on chip) against the plain FP32 chain of TTMs."""
+    import torch
+    import oracle
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    seed, n, R = 4096, 256, 32
+    dims = (n,) * 4
+    spec = dz.ttmc_einsum(4, 0)
+    X = dz.gen_uniform(seed, inputs.STREAM_X, dims)
+    Us = [inputs.factor_normal(seed, m, n, R).astype(np.float32) for m in range(4)]
+    Ud = [torch.from_numpy(u).cuda() for u in Us]
+    out = torch.empty(n, R, R, R, device="cuda")
+    stream = torch.cuda.Stream()
+    plans = {p: dz.Plan(spec, list(dims) + [R, R, R], "float32", p) for p in ("split_bf16", "plain")}
+
+    def timed(plan, steps, kernel=False):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                plan(X, *Ud[1:], out=out, stream=stream)
+        stream.synchronize()
+        if kernel:
+            plan.set_kernel_timing(True)
+            plan.kernel_time()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(steps):
+                plan(X, *Ud[1:], out=out, stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        k = plan.kernel_time() if kernel else (0.0, 0)
+        plan.set_kernel_timing(False)
+        return e0.elapsed_time(e1) / steps, k
+
+    launches0 = dz.kernel_launch_count()
+    ms, (kms, kn) = timed(plans["split_bf16"], args.steps, kernel=True)
+    launches = dz.kernel_launch_count() - launches0
+    status = plans["split_bf16"].last_device_status()
+    rows = inputs.sample_rows(seed, n, 2, tag=7)
+    got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+    ms_plain, _ = timed(plans["plain"], max(1, args.steps // 2))
+    del X
+    slabs = np.stack([inputs.uniform_slab(seed, dims, 0, int(r)).ravel() for r in rows])
+    ref = oracle.ttmc_rows(dims, 0, slabs, Us)
+    info = plans["split_bf16"].info()
+    gb = info["alg_bytes"] / 1e9
+    x_bytes = 4.0 * n ** 4
+    t2_bytes = 4.0 * n * n * R * R
+    kern_ms = kms / max(1, kn)
+    peak, peak_kind = _peaks()
+    achieved = (x_bytes + t2_bytes) / (kern_ms * 1e-3) / 1e9 if kn else None
+    line = {"metric": "TTMc GB/s (algorithmic bytes |X| + factors + Y per step)", "unit": "GB/s",
+            "value": gb / (ms * 1e-3), "n_gpus": 1, "steps": args.steps, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "TTMc ijkl,jb,kc,ld->ibcd, X 256^4 FP32 uniform[-1,1), U 256x32 N(0,1)",
+                       "arith": "split-BF16 tcgen05 (modes l then k fused, T1 on chip) + plain FP32 TTM over j",
+                       "l2": "inputs larger than L2 (X = 17.2 GB)", "alg_gb": gb},
+            "roofline": {"bound": "hbm", "kernel": "ttmc_fused_kernel", "kernel_ms_avg": kern_ms,
+                         "bytes_per_launch": x_bytes + t2_bytes, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak if achieved else None, "peak_kind": peak_kind},
+            "plain_chain_ms": ms_plain, "speedup_vs_plain_chain": ms_plain / ms,
+            "rel_err_sampled_rows": oracle.rel_error(got, ref), "gpu_launches": launches, "device_status": status}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -371,8 +439,8 @@ def main():
                     help="profiling driver: one execute per mode of --modes at extent --n, no timing")
     ap.add_argument("--n", type=int, default=N_EXT, help="extent of each mode (--once only)")
     ap.add_argument("--modes", default="0,1,2", help="modes to run (--once only)")
-    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving", "batched"],
-                    help="mttkrp: the benchmark line; serving / batched: the serving and batched measurements")
+    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving", "batched", "ttmc"],
+                    help="mttkrp: the benchmark line; serving / batched / ttmc: the other measurements")
     ap.add_argument("--requests", type=int, default=128, help="requests of the serving workload")
     ap.add_argument("--instances", type=int, default=512, help="instances of the batched workload")
     args = ap.parse_args()
@@ -382,6 +450,8 @@ def main():
         return run_serving(args)
     if args.workload == "batched" and args.impl == "native":
         return run_batched(args)
+    if args.workload == "ttmc" and args.impl == "native":
+        return run_ttmc(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -101,6 +101,27 @@ struct BatchArgs {
 int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, void *stream);
 size_t mttkrp_tc_batched_smem_bytes();
 
+// Fused last-two-mode stage of a TTMc keeping a mode n < N-2 (ttmc_tc.cu):
+//   T2[s, c, d] = sum_{k, l} X[s, k, l] U_{N-2}[k, c] U_{N-1}[l, d]
+// for every slab s (flat index over modes 0..N-3), k over I_{N-2}, l over
+// I_{N-1}.  The contraction over l runs on the tensor cores (split BF16, 128 k
+// at a time), the one over k on CUDA cores in FP32; T1 = X U_{N-1} stays on chip.
+struct TtmcArgs {
+    CUtensorMap xmap;     // 3-D {I_{N-1}, I_{N-2}, S}, box {64, min(I_{N-2}, 128), 1}
+    uint32_t box_bytes;
+    MttkrpGeom g;         // converter view of a chunk: case 0, I = I_{N-2}, narrow = I < 128, G = 1
+    const void *Bsplit;   // split-BF16 tiles of U_{N-1} (R_pad 32, n_kb tiles)
+    const float *U2pad;   // U_{N-2} as n_kt*128 rows x 32 FP32, zero beyond I_{N-2} x R_{N-2}
+    float *T2;            // S x R_{N-2} x R_{N-1}, row-major
+    int64_t S;            // slabs
+    int n_kt;             // tiles of 128 along k
+    int n_kb;             // chunks of 64 along l
+    int R2, R3;           // R_{N-2}, R_{N-1} (<= 32)
+    int *status;
+};
+int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream);
+int launch_ttmc_pad_factor(const float *U, int64_t rows, int R, float *out, int n_kt, void *stream);
+
 // Launch helpers implemented in the .cu files.  They return a CUDA error code
 // (0 on success) and increment the library's launch counter.
 int launch_mttkrp_plain_f32(const MttkrpArgs &a, int n_sm, void *stream);

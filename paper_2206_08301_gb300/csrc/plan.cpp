@@ -44,6 +44,14 @@ struct deinsum_plan_s {
     // TTMc: contraction order and intermediate sizes
     std::vector<int> ttm_order;
     int64_t ttm_buf_elems = 0;
+    // split-BF16 TTMc: the last two modes fused on the tensor cores (ttmc_tc.cu),
+    // then the plain chain over the rest of the contracted modes
+    bool ttmc_fused = false;
+    std::vector<int> ttm_rest;     // chain order of the remaining modes
+    int64_t t2_elems = 0;          // S x R_{N-2} x R_{N-1}
+    int64_t rest_buf_elems = 0;    // largest intermediate of the remaining chain
+    int64_t t_S = 0;               // slabs
+    int t_nkt = 0, t_nkb = 0;
 
     // device state (after the first execute)
     int device = -1;
@@ -58,6 +66,9 @@ struct deinsum_plan_s {
     float *d_wtab = nullptr;   // weight tables of the tensor-core kernel (L, then O)
     int *d_status = nullptr;
     void *d_ttm[2] = {nullptr, nullptr};
+    float *d_t2 = nullptr;
+    void *d_tbsplit = nullptr;
+    float *d_u2pad = nullptr;
 
     // TMA descriptor of X, re-encoded when X moves
     CUtensorMap xmap{};
@@ -237,7 +248,8 @@ deinsum_status cuda_status(cudaError_t e) {
 }
 
 struct WsLayout {
-    size_t status = 0, units = 0, cols = 0, partial = 0, bsplit = 0, wtab = 0, ttm0 = 0, ttm1 = 0, total = 0;
+    size_t status = 0, units = 0, cols = 0, partial = 0, bsplit = 0, wtab = 0, ttm0 = 0, ttm1 = 0, t2 = 0, tb = 0, u2 = 0,
+           total = 0;
 };
 
 // Fix the device (the current one), the schedule (one unit per resident CTA:
@@ -277,6 +289,17 @@ deinsum_status plan_layout(deinsum_plan_s *pl, WsLayout &L) {
             L.wtab = off;
             off = align_up(off + (weight_table_floats_l(g) + weight_table_floats_o(g)) * sizeof(float), 256);
         }
+    } else if (pl->ttmc_fused) {
+        L.t2 = off;
+        off = align_up(off + size_t(pl->t2_elems) * sizeof(float), 256);
+        L.ttm0 = off;
+        off = align_up(off + size_t(pl->rest_buf_elems) * sizeof(float), 256);
+        L.ttm1 = off;
+        off = align_up(off + size_t(pl->rest_buf_elems) * sizeof(float), 1024);
+        L.tb = off;   // split tiles of U_{N-1}: n_kb x 2*32 rows x 64 BF16
+        off = align_up(off + size_t(pl->t_nkb) * 2 * 32 * DEINSUM_BK * 2, 1024);
+        L.u2 = off;   // U_{N-2} padded to n_kt*128 rows x 32
+        off = align_up(off + size_t(pl->t_nkt) * DEINSUM_BM * 32 * sizeof(float), 256);
     } else {
         L.ttm0 = off;
         off = align_up(off + size_t(pl->ttm_buf_elems) * elem_size(pl->dtype), 256);
@@ -311,6 +334,11 @@ deinsum_status attach_workspace(deinsum_plan_s *pl, char *ws, const WsLayout &L,
     } else {
         pl->d_ttm[0] = pl->ws + L.ttm0;
         pl->d_ttm[1] = pl->ws + L.ttm1;
+        if (pl->ttmc_fused) {
+            pl->d_t2 = reinterpret_cast<float *>(pl->ws + L.t2);
+            pl->d_tbsplit = pl->ws + L.tb;
+            pl->d_u2pad = reinterpret_cast<float *>(pl->ws + L.u2);
+        }
     }
     return DEINSUM_OK;
 }
@@ -414,6 +442,58 @@ void plan_ttmc_chain(deinsum_plan_s *pl) {
         mx = std::max(mx, sz);
     }
     pl->ttm_buf_elems = std::max<int64_t>(mx, 1);
+}
+
+// Split-BF16 TTMc: modes N-2 and N-1 are contracted by the fused kernel;
+// the other contracted modes follow in the same greedy order on
+// T2 = [I_0 .. I_{N-3}, R_{N-2}, R_{N-1}].  Offered when the kept mode is
+// below N-2 and R_{N-2}, R_{N-1} <= 32; I_{N-1} must be a multiple of 4 (rows of
+// X 16-byte aligned for the tensor map).
+deinsum_status plan_ttmc_fused(deinsum_plan_s *pl) {
+    const int N = pl->order, n = pl->mode;
+    if (N < 3 || n >= N - 2) return DEINSUM_ERR_UNSUPPORTED;
+    if (pl->ranks[N - 2] > 32 || pl->ranks[N - 1] > 32) return DEINSUM_ERR_UNSUPPORTED;
+    if (pl->dims[N - 1] % 4 != 0) return DEINSUM_ERR_UNSUPPORTED;
+    const int64_t lim = int64_t(1) << 31;
+    int64_t S = 1;
+    for (int m = 0; m < N - 2; ++m) S *= pl->dims[m];
+    if (S >= lim || pl->dims[N - 2] >= lim || pl->dims[N - 1] >= lim) return DEINSUM_ERR_UNSUPPORTED;
+    pl->ttmc_fused = true;
+    pl->t_S = S;
+    pl->t_nkt = int((pl->dims[N - 2] + DEINSUM_BM - 1) / DEINSUM_BM);
+    pl->t_nkb = int((pl->dims[N - 1] + DEINSUM_BK - 1) / DEINSUM_BK);
+    pl->t2_elems = S * pl->ranks[N - 2] * pl->ranks[N - 1];
+    pl->ttm_rest.clear();
+    for (int m : pl->ttm_order)
+        if (m < N - 2) pl->ttm_rest.push_back(m);
+    int64_t cur[DEINSUM_MAX_ORDER];
+    for (int m = 0; m < N; ++m) cur[m] = (m >= N - 2) ? pl->ranks[m] : pl->dims[m];
+    int64_t mx = 1;
+    for (size_t s = 0; s + 1 < pl->ttm_rest.size(); ++s) {
+        cur[pl->ttm_rest[s]] = pl->ranks[pl->ttm_rest[s]];
+        int64_t sz = 1;
+        for (int m = 0; m < N; ++m) sz *= cur[m];
+        mx = std::max(mx, sz);
+    }
+    pl->rest_buf_elems = mx;
+    // converter view of one raw chunk (128 k rows x 64 l): case 0, one slab per tile
+    MttkrpGeom &g = pl->geom;
+    std::memset(&g, 0, sizeof(g));
+    g.order = N;
+    g.mode = N - 2;
+    g.kcase = 0;
+    g.I = pl->dims[N - 2];
+    g.narrow = g.I < DEINSUM_BM ? 1 : 0;
+    g.G = 1;
+    g.P = S;
+    g.K_in = pl->dims[N - 1];
+    g.Q = g.K_in;
+    g.O = 1;
+    g.R = int(pl->ranks[N - 1]);
+    g.R_pad = 32;
+    g.n_kb = pl->t_nkb;
+    g.vec_ok = 1;
+    return DEINSUM_OK;
 }
 
 double alg_flops(const deinsum_plan_s *pl) {
@@ -547,7 +627,81 @@ deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, voi
     return err ? DEINSUM_ERR_CUDA : DEINSUM_OK;
 }
 
+// 3-D tensor map of X for the fused TTMc kernel: {I_{N-1}, I_{N-2}, S}, box
+// {64, min(I_{N-2}, 128), 1}; cached per X pointer.
+bool encode_ttmc_map(deinsum_plan_s *pl, const void *X) {
+    if (pl->xmap_ptr == X) return pl->xmap_ok != 0;
+    pl->xmap_ptr = X;
+    pl->xmap_ok = 0;
+    auto enc = tensor_map_encoder();
+    if (!enc || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return false;
+    const int N = pl->order;
+    const int64_t L = pl->dims[N - 1], K = pl->dims[N - 2];
+    cuuint64_t dims[3] = {cuuint64_t(L), cuuint64_t(K), cuuint64_t(pl->t_S)};
+    cuuint64_t strides[2] = {cuuint64_t(L) * 4, cuuint64_t(L * K) * 4};
+    cuuint32_t box[3] = {DEINSUM_BK, cuuint32_t(std::min<int64_t>(K, DEINSUM_BM)), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    pl->xmap_box_bytes = uint32_t(4 * box[0] * box[1]);
+    CUresult r = enc(&pl->xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(X), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    pl->xmap_ok = (r == CUDA_SUCCESS) ? 1 : 0;
+    return pl->xmap_ok != 0;
+}
+
+deinsum_status execute_ttmc_fused(deinsum_plan_s *pl, const void *const *inputs, void *output, void *stream) {
+    const int N = pl->order;
+    const void *U[DEINSUM_MAX_ORDER] = {nullptr};
+    for (int k = 1; k < pl->n_operands; ++k) U[pl->operand_mode[k]] = inputs[k];
+    if (!encode_ttmc_map(pl, inputs[0])) return DEINSUM_ERR_ALIGN;
+    // split tiles of U_{N-1} (the same layout as the MTTKRP inner factor)
+    MttkrpArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    sa.g = pl->geom;
+    sa.U[N - 1] = U[N - 1];
+    int err = launch_split_inner_factor(sa, pl->d_tbsplit, stream);
+    if (!err)
+        err = launch_ttmc_pad_factor(static_cast<const float *>(U[N - 2]), pl->dims[N - 2], int(pl->ranks[N - 2]),
+                                     pl->d_u2pad, pl->t_nkt, stream);
+    TtmcArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.xmap = pl->xmap;
+    t.box_bytes = pl->xmap_box_bytes;
+    t.g = pl->geom;
+    t.Bsplit = pl->d_tbsplit;
+    t.U2pad = pl->d_u2pad;
+    t.T2 = pl->ttm_rest.empty() ? static_cast<float *>(output) : pl->d_t2;
+    t.S = pl->t_S;
+    t.n_kt = pl->t_nkt;
+    t.n_kb = pl->t_nkb;
+    t.R2 = int(pl->ranks[N - 2]);
+    t.R3 = int(pl->ranks[N - 1]);
+    t.status = pl->d_status;
+    if (!err) {
+        const long ti = timing_begin(pl, stream);
+        err = launch_ttmc_fused(t, pl->n_sm, stream);
+        timing_end(pl, ti, stream);
+    }
+    // the remaining modes on T2 with the plain TTM kernel
+    int64_t cur[DEINSUM_MAX_ORDER];
+    for (int m = 0; m < N; ++m) cur[m] = (m >= N - 2) ? pl->ranks[m] : pl->dims[m];
+    const void *src = t.T2;
+    for (size_t s = 0; s < pl->ttm_rest.size() && !err; ++s) {
+        const int m = pl->ttm_rest[s];
+        int64_t A = 1, B = 1;
+        for (int k = 0; k < m; ++k) A *= cur[k];
+        for (int k = m + 1; k < N; ++k) B *= cur[k];
+        void *dst = (s + 1 == pl->ttm_rest.size()) ? output : pl->d_ttm[s % 2];
+        err = launch_ttm_plain_f32(static_cast<const float *>(src), static_cast<const float *>(U[m]),
+                                   static_cast<float *>(dst), A, cur[m], B, pl->ranks[m], stream);
+        cur[m] = pl->ranks[m];
+        src = dst;
+    }
+    return err ? DEINSUM_ERR_CUDA : DEINSUM_OK;
+}
+
 deinsum_status execute_ttmc(deinsum_plan_s *pl, const void *const *inputs, void *output, void *stream) {
+    if (pl->ttmc_fused) return execute_ttmc_fused(pl, inputs, output, stream);
     const void *U[DEINSUM_MAX_ORDER] = {nullptr};
     for (int k = 1; k < pl->n_operands; ++k) U[pl->operand_mode[k]] = inputs[k];
     int64_t cur[DEINSUM_MAX_ORDER];
@@ -636,8 +790,8 @@ deinsum_status deinsum_plan(const char *einsum, const int64_t *extents, int n_ex
             if (R > 64) st = DEINSUM_ERR_UNSUPPORTED;
             else build_mttkrp_geometry(pl);
         } else {
-            if (prec == DEINSUM_PREC_SPLIT_BF16) st = DEINSUM_ERR_DTYPE;  // split TTMc not offered yet
-            else plan_ttmc_chain(pl);
+            plan_ttmc_chain(pl);
+            if (prec == DEINSUM_PREC_SPLIT_BF16) st = plan_ttmc_fused(pl);
         }
     }
     if (st != DEINSUM_OK) {

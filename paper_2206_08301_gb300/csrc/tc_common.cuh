@@ -1,0 +1,109 @@
+// Device pieces shared by the tensor-core kernels (MTTKRP, batched MTTKRP,
+// fused TTMc): tile constants, the case-0 / case-1 row view of a 128 x 64
+// chunk, and the converters that read a raw FP32 chunk and write its split
+// BF16 hi / lo operand tiles in the 128-byte-swizzled K-major layout.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "internal.h"
+#include "sm100.cuh"
+
+namespace deinsum {
+namespace {
+
+using namespace sm100;
+
+constexpr int BM = DEINSUM_BM;
+constexpr int BK = DEINSUM_BK;
+constexpr int CONV_WARPS = 8;
+constexpr int EPI_WARPS = 4;
+
+// Case 0 rows of a tile: row l of tile t is the (p, i_n) pair with flat index
+// rowbase + l in the P x I_n row space, where rowbase = t*G*I_n (narrow: the
+// tile holds G consecutive p with all I_n rows) or t*I_n + col*128 (wide).
+__device__ __forceinline__ int64_t tile_rowbase(const MttkrpGeom &g, int64_t col, int64_t t) {
+    return g.narrow ? t * g.G * g.I : t * g.I + col * BM;
+}
+__device__ __forceinline__ bool row_valid(const MttkrpGeom &g, int64_t col, int64_t rowbase, int l) {
+    if (g.kcase == 1) return col * BM + l < g.I;
+    if (g.narrow) return l < g.G * g.I && rowbase + l < g.P * g.I;
+    return col * BM + l < g.I;
+}
+
+// ---------------------------------------------------------------------------
+// Converter inputs.  Each of the 256 converter threads owns 32 values of a chunk:
+//   case 0: rows rsub + 16 j (j < 8), k = 4 k4 .. 4 k4 + 3   (pt = 16 rsub + k4)
+//   case 1: row pt % 128, k = 32 (pt / 128) .. + 31
+// ---------------------------------------------------------------------------
+
+// From the raw tile the TMA wrote (out-of-bounds rows and k were zero-filled
+// by the TMA; narrow rows beyond G*I_n, which the box does not cover, are zeroed here).
+__device__ __forceinline__ void conv_read_smem(const MttkrpGeom &g, int pitch, const float *raw, int pt,
+                                               float4 (&v)[8]) {
+    if (g.kcase == 0) {
+        const int k4 = pt & 15, rsub = pt >> 4;
+        const int nrows = g.narrow ? int(g.G * g.I) : BM;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int row = rsub + 16 * j;
+            v[j] = row < nrows ? *reinterpret_cast<const float4 *>(raw + row * BK + 4 * k4)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+        const int row = pt & (BM - 1), kh = pt >> 7;
+        const bool rv = row < pitch;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float e[4];
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) e[q] = rv ? raw[(32 * kh + 4 * j + q) * pitch + row] : 0.f;
+            v[j] = make_float4(e[0], e[1], e[2], e[3]);
+        }
+    }
+}
+
+__device__ __forceinline__ void conv_read_smem(const MttkrpArgs &a, const float *raw, int pt, float4 (&v)[8]) {
+    conv_read_smem(a.g, a.raw_pitch, raw, pt, v);
+}
+
+// Split and store the thread's 32 values into the stage's A_hi / A_lo tiles.
+__device__ __forceinline__ void conv_store(const MttkrpGeom &g, int pt, uint32_t a_hi, uint32_t a_lo,
+                                           const float4 (&v)[8]) {
+    if (g.kcase == 0) {
+        // 16 lanes cover one 128-byte swizzled row: conflict-free 8-byte stores
+        const int k4 = pt & 15, rsub = pt >> 4;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t row = uint32_t(rsub + 16 * j);
+            const uint32_t off = sw128_offset(row, uint32_t(4 * k4));
+            uint32_t h0, l0, h1, l1;
+            split2(v[j].x, v[j].y, h0, l0);
+            split2(v[j].z, v[j].w, h1, l1);
+            sts64(a_hi + off, h0, h1);
+            sts64(a_lo + off, l0, l1);
+        }
+    } else {
+        // eight consecutive lanes hold eight consecutive rows: their 16-byte
+        // stores land in distinct swizzled bank groups
+        const int row = pt & (BM - 1), kh = pt >> 7;
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 x0 = v[2 * q], x1 = v[2 * q + 1];
+            uint32_t h[4], lo[4];
+            split2(x0.x, x0.y, h[0], lo[0]);
+            split2(x0.z, x0.w, h[1], lo[1]);
+            split2(x1.x, x1.y, h[2], lo[2]);
+            split2(x1.z, x1.w, h[3], lo[3]);
+            const uint32_t off = sw128_offset(uint32_t(row), uint32_t(32 * kh + 8 * q));
+            sts128(a_hi + off, h[0], h[1], h[2], h[3]);
+            sts128(a_lo + off, lo[0], lo[1], lo[2], lo[3]);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace deinsum

@@ -1,0 +1,436 @@
+// Fused TTMc stage on the tcgen05 tensor cores (sm_103a).
+//
+// A TTMc keeping mode n (Sec. III-B, Table IV: Y = X x_m U_m over every
+// m != n) contracts every other mode of X with its factor.  When n < N-2 the
+// last two modes are contracted here in a single pass over X:
+//   T2[s, c, d] = sum_{k, l} X[s, k, l] U_{N-2}[k, c] U_{N-1}[l, d],
+// s a slab (flat index over modes 0..N-3).  Per slab and 128-row k tile:
+//   stage 1 (tensor cores): T1[k, d] = sum_l X[s, k, l] U_{N-1}[l, d] with the
+//     MTTKRP pipeline -- TMA ring of raw FP32 chunks (128 k x 64 l), converter
+//     warps splitting them into BF16 hi / lo operand tiles, one thread issuing
+//     tcgen05.mma against the split factor tiles, FP32 accumulation in TMEM;
+//   stage 2 (CUDA cores, FP32): each epilogue warp moves the 32 T1 rows of its
+//     TMEM lane quadrant to shared memory and adds U_{N-2}[those rows]^T T1 into
+//     its own partial R_{N-2} x R_{N-1} block (4 x 8 outputs per thread, so that
+//     the shared-memory reads stay a small share of the bandwidth stage 1 leaves);
+//     at the end of a slab the four partials are added in a fixed order.  The
+//     factor rows of the next k tile are bulk-copied one tile ahead into a
+//     two-slot ring by the epilogue itself, so the X stream never waits on stage 2.
+// T1 never reaches HBM; T2 (R_{N-2} R_{N-1} / (I_{N-2} I_{N-1}) of X) is written
+// once, and the remaining modes are contracted by the plain TTM chain.  Each
+// CTA owns a contiguous range of slabs, so every T2 block is produced by one
+// CTA in a fixed order (deterministic, no reduction pass).
+//
+// Warp roles: 0-7 converters, 8-11 epilogue (stage 2), 12 TMEM + MMA issue,
+// 13 TMA.  Every wait is bounded (mbar_wait); the epilogue warps meet only
+// through mbarriers (ufree: U slot reads done; pdone / rdone: slab partials
+// written / read), so a time-out anywhere ends every role.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "internal.h"
+#include "sm100.cuh"
+#include "tc_common.cuh"
+
+namespace deinsum {
+namespace {
+
+struct TtmcCfg {
+    static constexpr int RP = 32;                          // padded R_{N-1} and R_{N-2}
+    static constexpr int N = 2 * RP;                       // rows of the split factor tile (hi, then lo)
+    static constexpr int RS = 3;                           // raw X stages
+    static constexpr int AS = 2;                           // operand stages
+    static constexpr int MMA_WARP = CONV_WARPS + EPI_WARPS;
+    static constexpr int TMA_WARP = MMA_WARP + 1;
+    static constexpr int WARPS = TMA_WARP + 1;
+    static constexpr int THREADS = WARPS * 32;
+    static constexpr int RAW_BYTES = BM * BK * 4;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = N * BK * 2;
+    static constexpr int ASTAGE_BYTES = 2 * A_BYTES + B_BYTES;
+    static constexpr int T1_BYTES = BM * RP * 4;           // one T1 tile, FP32, 16-byte slots swizzled by row
+    static constexpr int USLOTS = 2;
+    static constexpr int USLOT_BYTES = BM * RP * 4;        // 128 rows of U_{N-2}, 32 columns
+    static constexpr int TMEM_COLS = 2 * N;                // two accumulators of N columns
+    static constexpr int NBARS = 2 * RS + 3 * AS + 4 + 1 + USLOTS + 3;
+    static constexpr size_t SMEM = size_t(RS) * RAW_BYTES + size_t(AS) * ASTAGE_BYTES + T1_BYTES +
+                                   size_t(USLOTS) * USLOT_BYTES + 1024 + 512;
+    static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB per-CTA limit");
+    static_assert(NBARS * 8 + 8 <= 512, "barrier area");
+};
+
+// Chunks of one CTA: slabs [s, s1), then k tiles, then l chunks.
+struct TIter {
+    int64_t s, s1;
+    int kt, kb;
+    bool done;
+    __device__ __forceinline__ void init(int64_t S) {
+        s = S * blockIdx.x / gridDim.x;
+        s1 = S * (blockIdx.x + 1) / gridDim.x;
+        kt = 0;
+        kb = 0;
+        done = s >= s1;
+    }
+    __device__ __forceinline__ void next(int n_kb, int n_kt) {
+        if (++kb < n_kb) return;
+        kb = 0;
+        if (++kt < n_kt) return;
+        kt = 0;
+        if (++s >= s1) done = true;
+    }
+};
+
+// T1 tile in shared memory: row r holds 32 floats as eight 16-byte slots,
+// logical slot x stored at slot x ^ (r & 7) (conflict-free row writes and
+// column-block reads).
+__device__ __forceinline__ float4 *t1_slot(float *t1s, int r, int x) {
+    return reinterpret_cast<float4 *>(t1s + r * TtmcCfg::RP) + (x ^ (r & 7));
+}
+
+__global__ void __launch_bounds__(TtmcCfg::THREADS, 1)
+ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
+    using C = TtmcCfg;
+    constexpr int RS = C::RS, AS = C::AS, RP = C::RP;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *raw_base = smem;
+    unsigned char *a_base = smem + RS * C::RAW_BYTES;
+    float *t1s = reinterpret_cast<float *>(a_base + AS * C::ASTAGE_BYTES);
+    float *ubuf = t1s + C::T1_BYTES / 4;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ubuf) + C::USLOTS * C::USLOT_BYTES);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    int *status = a.status;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
+    auto raw_addr = [&](int s) { return raw_s + uint32_t(s) * C::RAW_BYTES; };
+    auto a_hi = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES; };
+    auto a_lo = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + C::A_BYTES; };
+    auto b_t = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + 2 * C::A_BYTES; };
+    auto raw_full = [&](int s) { return smem_u32(bars + s); };
+    auto raw_empty = [&](int s) { return smem_u32(bars + RS + s); };
+    auto a_full = [&](int s) { return smem_u32(bars + 2 * RS + s); };
+    auto bfull = [&](int s) { return smem_u32(bars + 2 * RS + AS + s); };
+    auto a_empty = [&](int s) { return smem_u32(bars + 2 * RS + 2 * AS + s); };
+    auto accf = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + b); };
+    auto acce = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + 2 + b); };
+    const uint32_t drain = smem_u32(bars + 2 * RS + 3 * AS + 4);
+    auto ufull = [&](int s) { return smem_u32(bars + 2 * RS + 3 * AS + 5 + s); };
+    const uint32_t ufree = smem_u32(bars + 2 * RS + 3 * AS + 5 + C::USLOTS);
+    const uint32_t pdone = smem_u32(bars + 2 * RS + 3 * AS + 6 + C::USLOTS);
+    const uint32_t rdone = smem_u32(bars + 2 * RS + 3 * AS + 7 + C::USLOTS);
+    auto uslot_addr = [&](int s) { return smem_u32(ubuf) + uint32_t(s) * C::USLOT_BYTES; };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RS; ++s) {
+            mbar_init(raw_full(s), 1);
+            mbar_init(raw_empty(s), CONV_WARPS);
+        }
+        for (int s = 0; s < AS; ++s) {
+            mbar_init(a_full(s), CONV_WARPS);
+            mbar_init(bfull(s), 1);
+            mbar_init(a_empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), EPI_WARPS);
+        }
+        mbar_init(drain, 1);
+        for (int s = 0; s < C::USLOTS; ++s) mbar_init(ufull(s), 1);
+        mbar_init(ufree, EPI_WARPS);
+        mbar_init(pdone, EPI_WARPS);
+        mbar_init(rdone, EPI_WARPS);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == C::MMA_WARP) {
+        tmem_alloc(smem_u32(tmem_holder), C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp < CONV_WARPS) {
+        // ----------------------------------------------------------- converters
+        const int pt = threadIdx.x;
+        const bool issuer = (pt == 0);
+        const char *bsrc = static_cast<const char *>(a.Bsplit);
+        TIter it;
+        it.init(a.S);
+        uint32_t bpar = 0, bused = 0;
+        for (int64_t chunk = 0; !it.done; ++chunk) {
+            float4 v[8];
+            const int rs = int(chunk % RS);
+            const uint32_t rj = uint32_t(chunk / RS);
+            if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
+            conv_read_smem(a.g, BM, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
+            const int as = int(chunk % AS);
+            const uint32_t aj = uint32_t(chunk / AS);
+            if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status))) break;
+            if (issuer) {
+                mbar_arrive_expect_tx(bfull(as), C::B_BYTES);
+                bulk_g2s(b_t(as), bsrc + size_t(it.kb) * C::B_BYTES, C::B_BYTES, bfull(as));
+                bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
+                bused |= 1u << as;
+            }
+            conv_store(a.g, pt, a_hi(as), a_lo(as), v);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(a_full(as));
+                mbar_arrive(raw_empty(rs));
+            }
+            it.next(a.n_kb, a.n_kt);
+        }
+        if (issuer) {  // every bulk copy into this CTA's smem has landed before exit
+            for (int s = 0; s < AS; ++s)
+                if ((bused >> s) & 1u) mbar_wait(bfull(s), (bpar >> s) & 1u, abort_flag, status);
+        }
+    } else if (warp == C::TMA_WARP) {
+        // ------------------------------------------------------------------ TMA
+        // raw X chunks
+        if (lane == 0) {
+            TIter it;
+            it.init(a.S);
+            int last_rs = -1;
+            uint32_t last_par = 0;
+            for (int64_t chunk = 0; !it.done; ++chunk) {
+                const int rs = int(chunk % RS);
+                const uint32_t rj = uint32_t(chunk / RS);
+                if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status)) break;
+                mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
+                tma_load_3d(raw_addr(rs), &a.xmap, it.kb * BK, it.kt * BM, int(it.s), raw_full(rs));
+                last_rs = rs;
+                last_par = rj & 1u;
+                it.next(a.n_kb, a.n_kt);
+            }
+            // the last copy has landed before exit (the earlier ones were consumed)
+            if (last_rs >= 0) mbar_wait(raw_full(last_rs), last_par, abort_flag, status);
+        }
+        __syncwarp();
+    } else if (warp == C::MMA_WARP) {
+        // -------------------------------------------------------------- MMA issue
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16_f32(BM, C::N);
+            TIter it;
+            it.init(a.S);
+            const int64_t nfg = (it.s1 - it.s) * a.n_kt;
+            int64_t chunk = 0;
+            bool ok = true;
+            for (int64_t fgi = 0; ok && fgi < nfg; ++fgi) {
+                const int b = int(fgi & 1);
+                const uint32_t jb = uint32_t(fgi >> 1);
+                if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t dcol = tmem + uint32_t(b * C::N);
+                for (int kb = 0; kb < a.n_kb; ++kb) {
+                    const int s = int(chunk % AS);
+                    const uint32_t j = uint32_t(chunk / AS);
+                    if (!mbar_wait(a_full(s), j & 1u, abort_flag, status) ||
+                        !mbar_wait(bfull(s), j & 1u, abort_flag, status)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t dh = desc_kmajor_sw128(a_hi(s));
+                    const uint64_t dl = desc_kmajor_sw128(a_lo(s));
+                    const uint64_t db = desc_kmajor_sw128(b_t(s));
+                    #pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t adv = uint64_t(kk * 32) >> 4;  // 32 bytes per K=16 step
+                        mma_bf16(dcol, dh + adv, db + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(dcol, dl + adv, db + adv, idesc, 1u);
+                    }
+                    mma_commit(a_empty(s));
+                    ++chunk;
+                }
+                if (!ok) break;
+                mma_commit(accf(b));
+            }
+            // all issued MMAs have completed before TMEM is released
+            mma_commit(drain);
+            mbar_wait(drain, 0, abort_flag, status);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------- epilogue (stage 2)
+        const int quad = warp & 3;                 // TMEM lanes (= tile rows) 32*quad .. 32*quad+31
+        const int row = quad * 32 + lane;          // the T1 row this thread moves to smem
+        const int cb = lane >> 2, dg = lane & 3;   // stage 2: T2[4 cb .. 4 cb + 3, 8 dg .. 8 dg + 7]
+        const int et = threadIdx.x - CONV_WARPS * 32;
+        float acc[4][8];
+        #pragma unroll
+        for (int i = 0; i < 4; ++i)
+            #pragma unroll
+            for (int q = 0; q < 8; ++q) acc[i][q] = 0.f;
+        TIter it;
+        it.init(a.S);
+        const int64_t nfg = (it.s1 - it.s) * a.n_kt;
+        int64_t s = it.s;
+        int kt = 0;
+        uint32_t slab = 0;                         // slabs finished by this CTA
+        // U_{N-2} rows of tile kt of fiber group f go to slot f % 2; one thread copies
+        // them one group ahead (groups 0 and 1 now, group f + 1 once every warp is
+        // done with group f - 1)
+        const bool uissuer = (et == 0);
+        auto load_u = [&](int64_t f, int ktile) {
+            const int us = int(f % C::USLOTS);
+            mbar_arrive_expect_tx(ufull(us), C::USLOT_BYTES);
+            bulk_g2s(uslot_addr(us), a.U2pad + size_t(ktile) * BM * RP, C::USLOT_BYTES, ufull(us));
+        };
+        if (uissuer) {
+            if (nfg > 0) load_u(0, 0);
+            if (nfg > 1) load_u(1, 1 % a.n_kt);
+        }
+        for (int64_t fgi = 0; fgi < nfg; ++fgi) {
+            const int b = int(fgi & 1);
+            const uint32_t jb = uint32_t(fgi >> 1);
+            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) break;
+            tc_fence_after();
+            // the block of t1s this warp writes held the previous slab's partials:
+            // every warp has finished reading them
+            if (kt == 0 && !__all_sync(0xffffffffu, mbar_wait(rdone, (slab & 1u) ^ 1u, abort_flag, status))) break;
+            const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
+            #pragma unroll
+            for (int c0 = 0; c0 < RP; c0 += 16) {
+                uint32_t hi[16], lo[16];
+                tmem_ld16(taddr + uint32_t(c0), hi);
+                tmem_ld16(taddr + uint32_t(RP + c0), lo);
+                tmem_wait_ld();
+                #pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const int q = 4 * x;
+                    *t1_slot(t1s, row, c0 / 4 + x) =
+                        make_float4(__uint_as_float(hi[q]) + __uint_as_float(lo[q]),
+                                    __uint_as_float(hi[q + 1]) + __uint_as_float(lo[q + 1]),
+                                    __uint_as_float(hi[q + 2]) + __uint_as_float(lo[q + 2]),
+                                    __uint_as_float(hi[q + 3]) + __uint_as_float(lo[q + 3]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce(b));
+            {
+                // every warp has finished group fgi - 1, whose slot the next group uses
+                bool ok = true;
+                if (uissuer && fgi >= 1 && fgi + 1 < nfg) {
+                    ok = mbar_wait(ufree, uint32_t((fgi - 1) & 1), abort_flag, status);
+                    if (ok) load_u(fgi + 1, (kt + 1) % a.n_kt);
+                }
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
+            const int us = int(fgi % C::USLOTS);
+            const uint32_t uj = uint32_t(fgi / C::USLOTS);
+            if (!__all_sync(0xffffffffu, mbar_wait(ufull(us), uj & 1u, abort_flag, status))) break;
+            // stage 2 over this warp's 32 rows (rows past I_{N-2} are zero in both
+            // operands: TMA zero fill and the padded factor)
+            const float *u = ubuf + us * (C::USLOT_BYTES / 4) + 4 * cb;
+            #pragma unroll 1
+            for (int r0 = quad * 32; r0 < quad * 32 + 32; r0 += 4) {
+                float4 w[4], x0[4], x1[4];
+                #pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    w[i] = *reinterpret_cast<const float4 *>(u + (r0 + i) * RP);
+                    x0[i] = *t1_slot(t1s, r0 + i, 2 * dg);
+                    x1[i] = *t1_slot(t1s, r0 + i, 2 * dg + 1);
+                }
+                #pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float wc[4] = {w[i].x, w[i].y, w[i].z, w[i].w};
+                    const float xd[8] = {x0[i].x, x0[i].y, x0[i].z, x0[i].w, x1[i].x, x1[i].y, x1[i].z, x1[i].w};
+                    #pragma unroll
+                    for (int cc = 0; cc < 4; ++cc)
+                        #pragma unroll
+                        for (int q = 0; q < 8; ++q) acc[cc][q] = fmaf(wc[cc], xd[q], acc[cc][q]);
+                }
+            }
+            fence_proxy_async_smem();   // the slot's reads before its next bulk-copy write
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ufree);
+            if (++kt == a.n_kt) {
+                // slab done: the warp's partial block goes to its own 32 rows of t1s
+                // (32 x 32 floats, c-major), then the four partials are added in warp order
+                float *pw = t1s + quad * 32 * RP;
+                #pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    float4 *dst = reinterpret_cast<float4 *>(pw + (4 * cb + cc) * RP + 8 * dg);
+                    dst[0] = make_float4(acc[cc][0], acc[cc][1], acc[cc][2], acc[cc][3]);
+                    dst[1] = make_float4(acc[cc][4], acc[cc][5], acc[cc][6], acc[cc][7]);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(pdone);
+                if (!__all_sync(0xffffffffu, mbar_wait(pdone, slab & 1u, abort_flag, status))) break;
+                // this warp reduces rows c = 8 quad .. 8 quad + 7 of the block
+                const int c = 8 * quad + (lane >> 2), d0 = 8 * (lane & 3);
+                float sum[8];
+                #pragma unroll
+                for (int q = 0; q < 8; ++q) sum[q] = 0.f;
+                #pragma unroll
+                for (int wq = 0; wq < 4; ++wq) {
+                    const float4 *src = reinterpret_cast<const float4 *>(t1s + wq * 32 * RP + c * RP + d0);
+                    const float4 p0 = src[0], p1 = src[1];
+                    sum[0] += p0.x; sum[1] += p0.y; sum[2] += p0.z; sum[3] += p0.w;
+                    sum[4] += p1.x; sum[5] += p1.y; sum[6] += p1.z; sum[7] += p1.w;
+                }
+                if (c < a.R2) {
+                    float *dst = a.T2 + (s * a.R2 + c) * a.R3;
+                    #pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (d0 + q < a.R3) dst[d0 + q] = sum[q];
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(rdone);
+                #pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    #pragma unroll
+                    for (int q = 0; q < 8; ++q) acc[i][q] = 0.f;
+                kt = 0;
+                ++s;
+                ++slab;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == C::MMA_WARP) {
+        tc_fence_after();
+        tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+}
+
+// U (rows x R, row-major) -> out (n_kt*128 rows x 32), zero beyond rows x R.
+__global__ void pad_factor_kernel(const float *__restrict__ U, int64_t rows, int R, float *__restrict__ out,
+                                  int64_t total) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = i / TtmcCfg::RP;
+        const int c = int(i - r * TtmcCfg::RP);
+        out[i] = (r < rows && c < R) ? U[r * R + c] : 0.f;
+    }
+}
+
+}  // namespace
+
+int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream) {
+    using C = TtmcCfg;
+    cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
+    if (e != cudaSuccess) return int(e);
+    int64_t grid = a.S < n_sm ? a.S : n_sm;
+    if (grid < 1) grid = 1;
+    ttmc_fused_kernel<<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
+    count_launch();
+    return int(cudaGetLastError());
+}
+
+int launch_ttmc_pad_factor(const float *U, int64_t rows, int R, float *out, int n_kt, void *stream) {
+    const int64_t total = int64_t(n_kt) * BM * TtmcCfg::RP;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    pad_factor_kernel<<<unsigned(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(U, rows, R, out, total);
+    count_launch();
+    return int(cudaGetLastError());
+}
+
+}  // namespace deinsum

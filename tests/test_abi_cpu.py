@@ -126,3 +126,25 @@ def test_einsum_builders():
     assert dz.mttkrp_einsum(3, 0) == "abc,br,cr->ar"
     assert dz.mttkrp_einsum(5, 2) == "abcde,ar,br,dr,er->cr"
     assert dz.ttmc_einsum(4, 0) == "abcd,bt,cu,dv->atuv"
+
+
+def test_split_ttmc_plan_rules(lib):
+    """Split-BF16 TTMc is the fused last-two-mode kernel: kept mode below N-2,
+    R_{N-2}, R_{N-1} <= 32 and I_{N-1} a multiple of 4; other shapes are refused
+    at plan time (status 2) rather than silently run another way."""
+    ok = dz.Plan(dz.ttmc_einsum(4, 0), [20, 30, 130, 64, 5, 16, 12], prec="split_bf16")
+    assert ok.info()["kind"] == "ttmc"
+    dz.Plan(dz.ttmc_einsum(3, 0), [50, 300, 132, 17, 31], prec="split_bf16")
+    dz.Plan(dz.ttmc_einsum(5, 2), [6, 7, 8, 90, 44, 4, 6, 9, 32], prec="split_bf16")
+    for spec, ext in [
+        (dz.ttmc_einsum(4, 3), [20, 30, 130, 64, 5, 16, 12]),   # kept mode N-1
+        (dz.ttmc_einsum(4, 2), [20, 30, 130, 64, 5, 16, 12]),   # kept mode N-2
+        (dz.ttmc_einsum(4, 0), [20, 30, 130, 64, 5, 16, 33]),   # R_{N-1} > 32
+        (dz.ttmc_einsum(4, 0), [20, 30, 130, 64, 5, 40, 12]),   # R_{N-2} > 32
+        (dz.ttmc_einsum(4, 0), [20, 30, 130, 66, 5, 16, 12]),   # I_{N-1} % 4 != 0
+    ]:
+        with pytest.raises(dz.DeinsumError) as e:
+            dz.Plan(spec, ext, prec="split_bf16")
+        assert e.value.status == 2, (spec, ext)
+    # the plain precision takes every TTMc shape
+    dz.Plan(dz.ttmc_einsum(4, 3), [20, 30, 130, 64, 5, 16, 12], prec="plain")

@@ -102,3 +102,20 @@ def test_ttmc_256_order4_plain():
     ref = oracle.ttmc_rows(dims, 0, slabs, Us)
     _check(Y[torch.from_numpy(rows).cuda()].cpu().numpy(), ref)
     torch.cuda.empty_cache()
+
+
+def test_ttmc_256_order4_split():
+    # the benchmark workload: X 256^4 FP32, R = 32, keep mode 0, fused split-BF16 path
+    seed, n, R = 4096, 256, 32
+    dims = (n,) * 4
+    X = dz.gen_uniform(seed, inputs.STREAM_X, dims)
+    Us = [inputs.factor_normal(seed, m, n, R).astype(np.float32) for m in range(4)]
+    Ud = [torch.from_numpy(u).cuda() for u in Us]
+    Y = dz.ttmc(X, Ud, 0, prec="split_bf16")
+    torch.cuda.synchronize()
+    del X
+    rows = inputs.sample_rows(seed, n, 2, tag=7)
+    slabs = np.stack([inputs.uniform_slab(seed, dims, 0, int(r)).ravel() for r in rows])
+    ref = oracle.ttmc_rows(dims, 0, slabs, Us)
+    _check(Y[torch.from_numpy(rows).cuda()].cpu().numpy(), ref)
+    torch.cuda.empty_cache()

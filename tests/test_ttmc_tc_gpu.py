@@ -1,0 +1,92 @@
+"""Split-BF16 TTMc (fused last-two-mode tensor-core kernel + plain chain) against the FP64 oracle.
+
+Gate: relative Frobenius error <= 1e-5 and element-wise <= 1e-4 of the largest
+oracle entry (the FP32-accurate tolerance of the TTMc contract).  Cases cover
+ragged k tiles (I_{N-2} not a multiple of 128), ragged l chunks (I_{N-1} not a
+multiple of 64), a k extent below one tile, ranks below the padded 32, orders
+3 to 5 and every kept mode the fused path takes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_08301_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2206_08301_gb300 as dz  # noqa: E402
+
+
+def _check(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    err = oracle.rel_error(got, ref)
+    assert err <= 1e-5, f"relative Frobenius error {err:.3e}"
+    worst = np.abs(got - ref).max() / np.abs(ref).max()
+    assert worst <= 1e-4, f"max element error {worst:.3e}"
+    return err
+
+
+CASES = [
+    # (dims, keep, ranks of the contracted modes in mode order)
+    ((36, 40, 200, 68), 0, (8, 24, 32)),      # two k tiles (ragged), two l chunks (ragged)
+    ((20, 30, 130, 64), 1, (5, 16, 12)),      # keep mode 1: the chain contracts mode 0 afterwards
+    ((50, 300, 132), 0, (17, 31)),            # order 3: the fused kernel writes Y directly
+    ((70, 40, 100), 0, (32, 20)),             # k extent below one tile (narrow box)
+    ((6, 7, 8, 90, 44), 0, (3, 5, 32, 7)),    # order 5, two more chain stages
+    ((6, 7, 8, 90, 44), 2, (4, 6, 9, 32)),    # order 5, kept mode in the middle
+]
+
+
+@pytest.mark.parametrize("dims,keep,ranks", CASES)
+def test_split_ttmc_matches_oracle(dims, keep, ranks):
+    seed = 31 + sum(dims) + keep
+    X = inputs.tensor_uniform_f32(seed, dims)
+    rk = iter(ranks)
+    Us = [None if m == keep else inputs.factor_normal(seed, m, d, next(rk)).astype(np.float32)
+          for m, d in enumerate(dims)]
+    Xd = torch.from_numpy(X).cuda()
+    Ud = [None if u is None else torch.from_numpy(u).cuda() for u in Us]
+    Y = dz.ttmc(Xd, Ud, keep, prec="split_bf16")
+    torch.cuda.synchronize()
+    ref = oracle.ttmc(X, Us, keep)
+    assert Y.shape == ref.shape
+    _check(Y.cpu().numpy(), ref)
+    # against the plain FP32 chain as well
+    P = dz.ttmc(Xd, Ud, keep, prec="plain")
+    torch.cuda.synchronize()
+    assert oracle.rel_error(Y.cpu().numpy().astype(np.float64), P.cpu().numpy().astype(np.float64)) <= 1e-5
+
+
+def test_split_ttmc_is_bitwise_deterministic():
+    dims, keep = (24, 33, 260, 96), 0
+    X = torch.from_numpy(inputs.tensor_uniform_f32(5, dims)).cuda()
+    U = [None] + [torch.from_numpy(inputs.factor_normal(5, m, dims[m], 32).astype(np.float32)).cuda()
+                  for m in (1, 2, 3)]
+    a = dz.ttmc(X, U, keep, prec="split_bf16").clone()
+    b = dz.ttmc(X, U, keep, prec="split_bf16")
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_split_ttmc_rank1_closed_form():
+    # X = a o b o c o d  =>  Y[i, :, :, :] = a_i (U1^T b) o (U2^T c) o (U3^T d)
+    n = (40, 50, 150, 72)
+    vec = [inputs.factor_normal(77, m, n[m], 1).astype(np.float32)[:, 0] for m in range(4)]
+    X = np.einsum("i,j,k,l->ijkl", *[v.astype(np.float64) for v in vec]).astype(np.float32)
+    U = [None] + [inputs.factor_normal(77, 10 + m, n[m], r).astype(np.float32) for m, r in ((1, 9), (2, 32), (3, 17))]
+    Y = dz.ttmc(torch.from_numpy(X).cuda(), [None if u is None else torch.from_numpy(u).cuda() for u in U], 0,
+                prec="split_bf16")
+    torch.cuda.synchronize()
+    ref = oracle.ttmc(X, U, 0)
+    _check(Y.cpu().numpy(), ref)
+
+
+def test_split_ttmc_rejects_misaligned_x():
+    dims = (8, 9, 130, 64)
+    buf = torch.zeros(int(np.prod(dims)) + 1, device="cuda")
+    X = buf[1:].view(dims)              # 4-byte aligned, not 16-byte aligned: no tensor map
+    U = [None] + [torch.ones(dims[m], 4, device="cuda") for m in (1, 2, 3)]
+    with pytest.raises(dz.DeinsumError) as e:
+        dz.ttmc(X, U, 0, prec="split_bf16")
+    assert e.value.status == 5
