@@ -115,18 +115,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_2206_08301_gb300", "csrc", "mttkrp_tc.cu"), "rb") as fh:
+def _kernel_source_hash(source="mttkrp_tc.cu"):
+    with open(os.path.join(ROOT, "paper_2206_08301_gb300", "csrc", source), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def _traffic_per_launch(prec):
+def _traffic_per_launch(prec, source="mttkrp_tc.cu"):
     """DRAM bytes per launch of the main kernel from the committed ncu summary, if still current."""
     try:
         with open(TRAFFIC_FILE) as fh:
             t = json.load(fh)
         e = t.get(prec)
-        if e and e.get("source_sha") == _kernel_source_hash():
+        if e and e.get("source_sha") == _kernel_source_hash(source):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -161,11 +161,21 @@ def cpu_oracle_sample(seed, budget_s: float):
 
 
 def run_once(args):
-    """One execute per requested mode (for ncu captures of a small case); prints 'ok'."""
+    """One execute per requested mode (for ncu captures of a small case); prints 'ok'.
+    With --workload ttmc: one split-BF16 TTMc ijkl,jb,kc,ld->ibcd at X n x n x 256 x 256, R = 32."""
     import torch
     import paper_2206_08301_gb300 as dz
     from paper_2206_08301_gb300 import inputs
     n = args.n
+    if args.workload == "ttmc":
+        dims = (n, n, 256, 256)
+        X = dz.gen_uniform(4096, inputs.STREAM_X, dims)
+        U = [None] + [torch.from_numpy(inputs.factor_normal(4096, m, dims[m], 32).astype(np.float32)).cuda()
+                      for m in (1, 2, 3)]
+        dz.ttmc(X, U, 0, prec=args.prec)
+        torch.cuda.synchronize()
+        print("ok")
+        return 0
     dims = (n, n, n)
     X = dz.gen_uniform(2024, inputs.STREAM_X, dims)
     U = [torch.from_numpy(inputs.factor_normal(2024, m, n, RANK_R, sigma=np.sqrt(1.0 / RANK_R))
@@ -392,7 +402,8 @@ def run_ttmc(args):
                        "l2": "inputs larger than L2 (X = 17.2 GB)", "alg_gb": gb},
             "roofline": {"bound": "hbm", "kernel": "ttmc_fused_kernel", "kernel_ms_avg": kern_ms,
                          "bytes_per_launch": x_bytes + t2_bytes, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak if achieved else None, "peak_kind": peak_kind},
+                         "unit": "GB/s", "frac": achieved / peak if achieved else None, "peak_kind": peak_kind,
+                         "traffic": _traffic_per_launch("ttmc_split_bf16", "ttmc_tc.cu")},
             "plain_chain_ms": ms_plain, "speedup_vs_plain_chain": ms_plain / ms,
             "rel_err_sampled_rows": oracle.rel_error(got, ref), "gpu_launches": launches, "device_status": status}
     print(json.dumps(line))
