@@ -148,3 +148,9 @@ def test_split_ttmc_plan_rules(lib):
         assert e.value.status == 2, (spec, ext)
     # the plain precision takes every TTMc shape
     dz.Plan(dz.ttmc_einsum(4, 3), [20, 30, 130, 64, 5, 16, 12], prec="plain")
+
+
+def test_graft_entry_imports():
+    import importlib
+    g = importlib.import_module("__graft_entry__")
+    assert callable(g.build) and callable(g.smoke)
