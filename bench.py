@@ -410,6 +410,85 @@ def run_ttmc(args):
     return 0
 
 
+def run_paper(args):
+    """The paper's own benchmark shapes (Table V, single-device sizes; uniform X, factors N(0,1)):
+    MTTKRP-O3-M{0,1,2} at 1024^3, R 24; MTTKRP-O5-M{0,2,4} at 64^5, R 24 (the order-5 extent
+    1024 of the table is read as 64, see the design notes); TTMc-O5-M0 at 60^5, R 24.  One JSON
+    line per benchmark: split-BF16 and plain FP32 times, GB/s of algorithmic bytes, the main
+    kernel's roofline fraction, and the relative error on sampled output rows."""
+    import torch
+    import oracle
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    peak, peak_kind = _peaks()
+    stream = torch.cuda.Stream()
+
+    def timed(plan, ops, out, steps):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                plan(*ops, out=out, stream=stream)
+        stream.synchronize()
+        plan.set_kernel_timing(True)
+        plan.kernel_time()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(steps):
+                plan(*ops, out=out, stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        kms, kn = plan.kernel_time()
+        plan.set_kernel_timing(False)
+        return e0.elapsed_time(e1) / steps, kms / max(1, kn)
+
+    cases = [("MTTKRP-O3-M%d" % m, "mttkrp", (1024,) * 3, m) for m in (0, 1, 2)]
+    cases += [("MTTKRP-O5-M%d" % m, "mttkrp", (64,) * 5, m) for m in (0, 2, 4)]
+    cases += [("TTMc-O5-M0", "ttmc", (60,) * 5, 0)]
+    R, seed = 24, 1301
+    X, dims_now = None, None
+    for name, kind, dims, mode in cases:
+        if dims != dims_now:
+            X = None
+            torch.cuda.empty_cache()
+            X = dz.gen_uniform(seed, inputs.STREAM_X, dims)
+            Us = [inputs.factor_normal(seed, m, d, R).astype(np.float32) for m, d in enumerate(dims)]
+            Ud = [torch.from_numpy(u).cuda() for u in Us]
+            dims_now = dims
+        N = len(dims)
+        if kind == "mttkrp":
+            spec, ext = dz.mttkrp_einsum(N, mode), list(dims) + [R]
+            out = torch.empty(dims[mode], R, device="cuda")
+        else:
+            spec, ext = dz.ttmc_einsum(N, mode), list(dims) + [R] * (N - 1)
+            out = torch.empty([dims[m] if m == mode else R for m in range(N)], device="cuda")
+        ops = [X] + [Ud[m] for m in range(N) if m != mode]
+        res = {}
+        for prec in ("split_bf16", "plain"):
+            plan = dz.Plan(spec, ext, "float32", prec)
+            ms, kms = timed(plan, ops, out, args.steps if prec == "split_bf16" else max(1, args.steps // 3))
+            res[prec] = (ms, kms, plan.info()["alg_bytes"])
+            if prec == "split_bf16":
+                rows = inputs.sample_rows(seed, dims[mode], 2, tag=mode)
+                got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+        slabs = np.stack([inputs.uniform_slab(seed, dims, mode, int(r)).ravel() for r in rows])
+        if kind == "mttkrp":
+            ref = oracle.mttkrp_rows(dims, mode, slabs, Us)
+            kernel, kbytes = "mttkrp_tc_kernel", 4.0 * float(np.prod(dims))
+        else:
+            ref = oracle.ttmc_rows(dims, mode, slabs, Us)
+            kernel = "ttmc_fused_kernel"
+            kbytes = 4.0 * float(np.prod(dims)) * (1.0 + R * R / (dims[-1] * dims[-2]))
+        ms, kms, ab = res["split_bf16"]
+        achieved = kbytes / (kms * 1e-3) / 1e9
+        print(json.dumps({"benchmark": name, "dims": list(dims), "R": R, "mode": mode, "unit": "GB/s",
+                          "value": ab / (ms * 1e-3) / 1e9, "ms": ms, "plain_fp32_ms": res["plain"][0],
+                          "speedup_vs_plain": res["plain"][0] / ms,
+                          "roofline": {"bound": "hbm", "kernel": kernel, "kernel_ms": kms, "achieved": achieved,
+                                       "peak": peak, "frac": achieved / peak, "peak_kind": peak_kind},
+                          "rel_err_sampled_rows": oracle.rel_error(got, ref)}), flush=True)
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -450,7 +529,7 @@ def main():
                     help="profiling driver: one execute per mode of --modes at extent --n, no timing")
     ap.add_argument("--n", type=int, default=N_EXT, help="extent of each mode (--once only)")
     ap.add_argument("--modes", default="0,1,2", help="modes to run (--once only)")
-    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving", "batched", "ttmc"],
+    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving", "batched", "ttmc", "paper"],
                     help="mttkrp: the benchmark line; serving / batched / ttmc: the other measurements")
     ap.add_argument("--requests", type=int, default=128, help="requests of the serving workload")
     ap.add_argument("--instances", type=int, default=512, help="instances of the batched workload")
@@ -463,6 +542,8 @@ def main():
         return run_batched(args)
     if args.workload == "ttmc" and args.impl == "native":
         return run_ttmc(args)
+    if args.workload == "paper" and args.impl == "native":
+        return run_paper(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

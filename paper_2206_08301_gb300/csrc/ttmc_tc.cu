@@ -14,8 +14,9 @@
 //     its own partial R_{N-2} x R_{N-1} block (4 x 8 outputs per thread, so that
 //     the shared-memory reads stay a small share of the bandwidth stage 1 leaves);
 //     at the end of a slab the four partials are added in a fixed order.  The
-//     factor rows of the next k tile are bulk-copied one tile ahead into a
-//     two-slot ring by the epilogue itself, so the X stream never waits on stage 2.
+//     factor rows of a k tile sit in one of two shared-memory slots: copied once
+//     when I_{N-2} <= 256, else one tile ahead by the epilogue itself, so the X
+//     stream never waits on stage 2.
 // T1 never reaches HBM; T2 (R_{N-2} R_{N-1} / (I_{N-2} I_{N-1}) of X) is written
 // once, and the remaining modes are contracted by the plain TTM chain.  Each
 // CTA owns a contiguous range of slabs, so every T2 block is produced by one
@@ -271,18 +272,23 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         int64_t s = it.s;
         int kt = 0;
         uint32_t slab = 0;                         // slabs finished by this CTA
-        // U_{N-2} rows of tile kt of fiber group f go to slot f % 2; one thread copies
-        // them one group ahead (groups 0 and 1 now, group f + 1 once every warp is
-        // done with group f - 1)
+        // U_{N-2} rows of k tile kt.  With at most two tiles (I_{N-2} <= 256) every tile
+        // is copied once into slot kt and stays; otherwise the rows of fiber group f go
+        // to slot f % 2, copied by one thread one group ahead (groups 0 and 1 now, group
+        // f + 1 once every warp is done with group f - 1).
         const bool uissuer = (et == 0);
-        auto load_u = [&](int64_t f, int ktile) {
-            const int us = int(f % C::USLOTS);
+        const bool uresident = a.n_kt <= C::USLOTS;
+        auto load_u = [&](int us, int ktile) {
             mbar_arrive_expect_tx(ufull(us), C::USLOT_BYTES);
             bulk_g2s(uslot_addr(us), a.U2pad + size_t(ktile) * BM * RP, C::USLOT_BYTES, ufull(us));
         };
-        if (uissuer) {
-            if (nfg > 0) load_u(0, 0);
-            if (nfg > 1) load_u(1, 1 % a.n_kt);
+        if (uissuer && nfg > 0) {
+            if (uresident) {
+                for (int t = 0; t < a.n_kt; ++t) load_u(t, t);
+            } else {
+                load_u(0, 0);
+                if (nfg > 1) load_u(1, 1 % a.n_kt);
+            }
         }
         for (int64_t fgi = 0; fgi < nfg; ++fgi) {
             const int b = int(fgi & 1);
@@ -315,20 +321,23 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             {
                 // every warp has finished group fgi - 1, whose slot the next group uses
                 bool ok = true;
-                if (uissuer && fgi >= 1 && fgi + 1 < nfg) {
+                if (uissuer && !uresident && fgi >= 1 && fgi + 1 < nfg) {
                     ok = mbar_wait(ufree, uint32_t((fgi - 1) & 1), abort_flag, status);
-                    if (ok) load_u(fgi + 1, (kt + 1) % a.n_kt);
+                    if (ok) load_u(int((fgi + 1) % C::USLOTS), (kt + 1) % a.n_kt);
                 }
                 if (!__all_sync(0xffffffffu, ok)) break;
             }
-            const int us = int(fgi % C::USLOTS);
-            const uint32_t uj = uint32_t(fgi / C::USLOTS);
+            const int us = uresident ? kt : int(fgi % C::USLOTS);
+            const uint32_t uj = uresident ? 0u : uint32_t(fgi / C::USLOTS);
             if (!__all_sync(0xffffffffu, mbar_wait(ufull(us), uj & 1u, abort_flag, status))) break;
-            // stage 2 over this warp's 32 rows (rows past I_{N-2} are zero in both
-            // operands: TMA zero fill and the padded factor)
+            // stage 2 over this warp's rows that lie inside I_{N-2}, in groups of four
+            // (the rows past it are zero in both operands: TMA zero fill and the
+            // padded factor, so a partial group is harmless)
             const float *u = ubuf + us * (C::USLOT_BYTES / 4) + 4 * cb;
+            const int64_t left = a.g.I - int64_t(kt) * BM - quad * 32;
+            const int nrows = left <= 0 ? 0 : (left >= 32 ? 32 : int((left + 3) & ~int64_t(3)));
             #pragma unroll 1
-            for (int r0 = quad * 32; r0 < quad * 32 + 32; r0 += 4) {
+            for (int r0 = quad * 32; r0 < quad * 32 + nrows; r0 += 4) {
                 float4 w[4], x0[4], x1[4];
                 #pragma unroll
                 for (int i = 0; i < 4; ++i) {

@@ -119,3 +119,20 @@ def test_ttmc_256_order4_split():
     ref = oracle.ttmc_rows(dims, 0, slabs, Us)
     _check(Y[torch.from_numpy(rows).cuda()].cpu().numpy(), ref)
     torch.cuda.empty_cache()
+
+
+def test_ttmc_60_order5_split():
+    # TTMc-O5-M0 of the paper's benchmark table: X 60^5, R^n = 24 (fused last two modes + chain)
+    seed, n, R = 1301, 60, 24
+    dims = (n,) * 5
+    X = dz.gen_uniform(seed, inputs.STREAM_X, dims)
+    Us = [inputs.factor_normal(seed, m, n, R).astype(np.float32) for m in range(5)]
+    Ud = [torch.from_numpy(u).cuda() for u in Us]
+    Y = dz.ttmc(X, Ud, 0, prec="split_bf16")
+    torch.cuda.synchronize()
+    del X
+    rows = inputs.sample_rows(seed, n, 2, tag=3)
+    slabs = np.stack([inputs.uniform_slab(seed, dims, 0, int(r)).ravel() for r in rows])
+    ref = oracle.ttmc_rows(dims, 0, slabs, Us)
+    _check(Y[torch.from_numpy(rows).cuda()].cpu().numpy(), ref)
+    torch.cuda.empty_cache()
