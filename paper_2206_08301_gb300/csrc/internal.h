@@ -8,7 +8,9 @@
 //     mode contracted on the tensor cores, stride 1 in memory) and o the modes
 //     n+1..N-2 ("outer" modes).  Rows are grouped 128 to a tile: one p and 128
 //     consecutive i_n when I_n >= 128 ("wide"), else G = min(floor(128/I_n), 32)
-//     consecutive p with all I_n rows each ("narrow").
+//     consecutive p with all I_n rows each ("narrow").  On the tensor-core path,
+//     when there is no p to pack (P = 1), the G groups run over consecutive outer
+//     indices o instead ("opack"; also in case 1 with I_n < 128).
 //   case 1 (n = N-1, "M-contiguous"): a row is one i_n; its elements run over
 //     p = (o, k) with k indexing mode N-2 (inner) and o modes 0..N-3 (outer);
 //     consecutive rows are adjacent in memory.
@@ -58,17 +60,20 @@ struct MttkrpGeom {
     int64_t O;            // product of outer extents (1 if none)
     int outer_mode[DEINSUM_MAX_ORDER];
     int64_t outer_dim[DEINSUM_MAX_ORDER];
-    int64_t G;            // narrow: p values per tile (else 1)
+    int64_t G;            // narrow: p values (o values with opack) per tile, else 1
     int64_t n_cols;       // columns of 128 output rows (narrow: 1)
     int64_t tiles_per_col;
-    int64_t fg_per_col;   // tiles_per_col * O
+    int64_t fg_per_col;   // tiles_per_col * O_iter
     int64_t rows_per_col; // min(I, 128)
+    int opack;            // tensor-core path, I < 128 and no p to pack (case 0 with P = 1, or
+                          // case 1): tile rows are (o_local, i_n), G consecutive outer indices
+    int64_t O_iter;       // outer indices iterated per tile: O, or 1 with opack (folded into the tile)
 };
 
 struct MttkrpArgs {
     // TMA descriptor of X for the tensor-core kernel (valid when use_tma != 0):
-    //   case 0: 4-D {K_in, O, I, P}, box {64, 1, min(I,128), G}
-    //   case 1: 3-D {I, K_in, O},    box {min(I,128), 64, 1}
+    //   case 0: 4-D {K_in, O, I, P}, box {64, 1, min(I,128), G}  (opack: {K_in, I, O, P}, box {64, I, G, 1})
+    //   case 1: 3-D {I, K_in, O},    box {min(I,128), 64, 1}     (opack: box {I, 64, G})
     CUtensorMap xmap;     // (the type carries its own 128-byte alignment)
     int use_tma;
     uint32_t box_bytes;   // bytes one box load writes (out-of-bounds parts are zero-filled)

@@ -73,8 +73,8 @@ struct Iter {
             fg1 = a.units[3 * u + 2];
             if (fg < fg1) {
                 kb = 0;
-                tile = fg / a.g.O;
-                o = fg - tile * a.g.O;
+                tile = fg / a.g.O_iter;
+                o = fg - tile * a.g.O_iter;
                 done = false;
                 return;
             }
@@ -91,7 +91,7 @@ struct Iter {
         if (++kb < a.g.n_kb) return;
         kb = 0;
         if (++fg < fg1) {
-            if (++o == a.g.O) { o = 0; ++tile; }
+            if (++o == a.g.O_iter) { o = 0; ++tile; }
             return;
         }
         u += gridDim.x;
@@ -100,11 +100,48 @@ struct Iter {
 };
 
 // From global memory with per-element bounds checks (rows not 16-byte aligned).
+template <bool OPACK>
 __device__ __forceinline__ void conv_read_global(const MttkrpArgs &a, const Iter &it, int pt, float4 (&v)[8]) {
     const MttkrpGeom &g = a.g;
     const float *X = static_cast<const float *>(a.X);
     const int64_t k0 = int64_t(it.kb) * BK;
-    if (g.kcase == 0) {
+    if (OPACK && g.kcase == 0) {
+        // row l = gq * I_n + i (P = 1): X[i, o0 + gq, k]
+        const int k4 = pt & 15, rsub = pt >> 4;
+        const int64_t kpos = k0 + 4 * k4;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int l = rsub + 16 * j;
+            float e[4] = {0.f, 0.f, 0.f, 0.f};
+            if (opack_row_valid(g, it.tile, l)) {
+                const int gq = int(l / g.I);
+                const int64_t i = l - gq * g.I;
+                const float *pr = X + i * g.Q + (it.tile * g.G + gq) * g.K_in + kpos;
+                #pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (kpos + q < g.K_in) e[q] = __ldg(pr + q);
+            }
+            v[j] = make_float4(e[0], e[1], e[2], e[3]);
+        }
+    } else if (OPACK) {
+        // case 1, row l = gq * I_n + i: X[o0 + gq, k, i]
+        const int row = pt & (BM - 1), kh = pt >> 7;
+        const bool rv = opack_row_valid(g, it.tile, row);
+        const int gq = int(row / g.I);
+        const int64_t i = row - gq * g.I;
+        const int64_t kbase = k0 + 32 * kh;
+        const float *base = X + ((it.tile * g.G + gq) * g.K_in + kbase) * g.I + i;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float e[4];
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int kk = 4 * j + q;
+                e[q] = (rv && kbase + kk < g.K_in) ? __ldg(base + int64_t(kk) * g.I) : 0.f;
+            }
+            v[j] = make_float4(e[0], e[1], e[2], e[3]);
+        }
+    } else if (g.kcase == 0) {
         const int k4 = pt & 15, rsub = pt >> 4;
         const int64_t rowbase = tile_rowbase(g, it.col, it.tile);
         const int64_t kpos = k0 + 4 * k4;
@@ -196,12 +233,23 @@ __global__ void batched_weight_tables_kernel(const MttkrpArgs *__restrict__ inst
 }
 
 // Copy the weights of fiber group (tile, o) into a weight-ring slot (TMA warp,
-// one thread): Ofac(o) at floats [0, rp), then the L rows of the tile's p
-// values at [rp, ...), completing on `bar` (a plain arrive when there are none).
+// one thread): the row common to the tile at floats [0, rp), then one row per
+// row group at [rp, ...) -- Ofac(o) and the L rows of the tile's p values, or,
+// with opack, L(0) and the Ofac rows of the tile's outer indices -- completing
+// on `bar` (a plain arrive when there are none).
 __device__ __forceinline__ void load_fg_weights(const MttkrpArgs &a, int64_t tile, int64_t o, uint32_t dst,
                                                 uint32_t bar) {
     const MttkrpGeom &g = a.g;
     const uint32_t rowb = uint32_t(g.R_pad) * 4u;
+    if (g.opack) {
+        const int64_t o0 = tile * g.G;
+        const uint32_t no = uint32_t(g.O - o0 < g.G ? g.O - o0 : g.G);
+        const uint32_t bytes = (g.n_lmodes > 0 ? rowb : 0u) + no * rowb;
+        mbar_arrive_expect_tx(bar, bytes);
+        if (g.n_lmodes > 0) bulk_g2s(dst, a.Lw, rowb, bar);
+        bulk_g2s(dst + rowb, a.Ow + o0 * g.R_pad, no * rowb, bar);
+        return;
+    }
     uint32_t bytes = 0, nl = 0;
     int64_t p0 = 0;
     if (g.n_outer > 0) bytes += rowb;
@@ -220,7 +268,7 @@ __device__ __forceinline__ void load_fg_weights(const MttkrpArgs &a, int64_t til
     if (nl) bulk_g2s(dst + rowb, a.Lw + p0 * g.R_pad, nl * rowb, bar);
 }
 
-template <int RP>
+template <int RP, bool OP>
 __global__ void __launch_bounds__(TcCfg<RP>::THREADS, 1)
 mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     using C = TcCfg<RP>;
@@ -298,9 +346,9 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             if (a.use_tma) {
                 const uint32_t rj = uint32_t(chunk / RS);
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, a.status))) break;
-                conv_read_smem(a, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
+                conv_read_smem_t<OP>(a.g, a.raw_pitch, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
             } else {
-                conv_read_global(a, it, pt, v);
+                conv_read_global<OP>(a, it, pt, v);
             }
             const int as = int(chunk % AS);
             const uint32_t aj = uint32_t(chunk / AS);
@@ -352,7 +400,11 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, a.status)) break;
                     mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                     const int kc = it.kb * BK;
-                    if (g.kcase == 0) {
+                    if (OP) {
+                        const int o0 = int(it.tile * g.G);
+                        if (g.kcase == 0) tma_load_4d(raw_addr(rs), &a.xmap, kc, 0, o0, 0, raw_full(rs));
+                        else tma_load_3d(raw_addr(rs), &a.xmap, 0, kc, o0, raw_full(rs));
+                    } else if (g.kcase == 0) {
                         const int c2 = g.narrow ? 0 : int(it.col * BM);
                         const int c3 = g.narrow ? int(it.tile * g.G) : int(it.tile);
                         tma_load_4d(raw_addr(rs), &a.xmap, kc, int(it.o), c2, c3, raw_full(rs));
@@ -420,7 +472,8 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         // ------------------------------------------------------------- epilogue
         const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
         const int l = quad * 32 + lane;            // tile row of this thread
-        const bool lane_weights = g.kcase == 0 && g.narrow && g.n_lmodes > 0;
+        const bool lane_weights = OP || (g.kcase == 0 && g.narrow && g.n_lmodes > 0);  // per-row weights
+        const bool has_common = OP ? g.n_lmodes > 0 : g.n_outer > 0;   // a row common to the tile
         const int lg = g.narrow ? int(l / g.I) : 0;   // narrow: p offset of row l within its tile
         Iter it;
         it.init(a);
@@ -454,7 +507,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             while (!it.done && it.u == u) {
                 if (it.tile != tile) {
                     tile = it.tile;
-                    if (lane_weights) rv = row_valid(g, ucol, tile_rowbase(g, ucol, tile), l);
+                    if (lane_weights) rv = OP ? opack_row_valid(g, tile, l) : row_valid(g, ucol, tile_rowbase(g, ucol, tile), l);
                 }
                 // weights of this fiber group, from its ring slot: lane c holds column c (and c + 32)
                 const int ws = int(fgi % C::WSLOTS);
@@ -465,8 +518,8 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 }
                 const float *wsl = wbuf + ws * C::WSLOT_FLOATS;
                 const float *lrow = wsl + RP * (1 + lg);   // narrow: L row of this thread's p
-                float w0 = g.n_outer > 0 ? wsl[lane] : 1.f;
-                float w1 = (RP > 32 && g.n_outer > 0) ? wsl[lane + 32] : 1.f;
+                float w0 = has_common ? wsl[lane] : 1.f;
+                float w1 = (RP > 32 && has_common) ? wsl[lane + 32] : 1.f;
                 if (!lane_weights && g.n_lmodes > 0) {
                     w0 = wsl[RP + lane] * w0;
                     if (RP > 32) w1 = wsl[RP + lane + 32] * w1;
@@ -541,17 +594,22 @@ __global__ void split_inner_factor_kernel(const float *__restrict__ U, unsigned 
     }
 }
 
-template <int RP>
-int launch_tc_rp(const MttkrpArgs &a, int n_sm, void *stream) {
+template <int RP, bool OP>
+int launch_tc_rp_op(const MttkrpArgs &a, int n_sm, void *stream) {
     using C = TcCfg<RP>;
-    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_kernel<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_kernel<RP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(C::SMEM));
     if (e != cudaSuccess) return int(e);
     int64_t grid = a.n_units < n_sm ? a.n_units : n_sm;
     if (grid < 1) grid = 1;
-    mttkrp_tc_kernel<RP><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
+    mttkrp_tc_kernel<RP, OP><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
     count_launch();
     return int(cudaGetLastError());
+}
+
+template <int RP>
+int launch_tc_rp(const MttkrpArgs &a, int n_sm, void *stream) {
+    return a.g.opack ? launch_tc_rp_op<RP, true>(a, n_sm, stream) : launch_tc_rp_op<RP, false>(a, n_sm, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -577,8 +635,8 @@ struct BIter {
             part_off = r[4];
             if (fg < fg1) {
                 kb = 0;
-                tile = fg / a->g.O;
-                o = fg - tile * a->g.O;
+                tile = fg / a->g.O_iter;
+                o = fg - tile * a->g.O_iter;
                 done = false;
                 return;
             }
@@ -596,7 +654,7 @@ struct BIter {
         if (++kb < a->g.n_kb) return;
         kb = 0;
         if (++fg < fg1) {
-            if (++o == a->g.O) { o = 0; ++tile; }
+            if (++o == a->g.O_iter) { o = 0; ++tile; }
             return;
         }
         ++u;
@@ -693,7 +751,8 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
                 conv_read_smem(a, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
             } else {
-                conv_read_global(a, it.as_iter(), pt, v);
+                if (a.g.opack) conv_read_global<true>(a, it.as_iter(), pt, v);
+                else conv_read_global<false>(a, it.as_iter(), pt, v);
             }
             const int as = int(chunk % AS);
             const uint32_t aj = uint32_t(chunk / AS);
@@ -751,7 +810,11 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                     if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status)) break;
                     mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                     const int kc = it.kb * BK;
-                    if (a.g.kcase == 0) {
+                    if (a.g.opack) {
+                        const int o0 = int(it.tile * a.g.G);
+                        if (a.g.kcase == 0) tma_load_4d(raw_addr(rs), &a.xmap, kc, 0, o0, 0, raw_full(rs));
+                        else tma_load_3d(raw_addr(rs), &a.xmap, 0, kc, o0, raw_full(rs));
+                    } else if (a.g.kcase == 0) {
                         const int c2 = a.g.narrow ? 0 : int(it.col * BM);
                         const int c3 = a.g.narrow ? int(it.tile * a.g.G) : int(it.tile);
                         tma_load_4d(raw_addr(rs), &a.xmap, kc, int(it.o), c2, c3, raw_full(rs));
@@ -825,7 +888,8 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             const MttkrpGeom &g = a.g;
             const int rp = g.R_pad;
             const int64_t ucol = it.col;
-            const bool lane_weights = g.kcase == 0 && g.narrow && g.n_lmodes > 0;
+            const bool lane_weights = g.opack || (g.kcase == 0 && g.narrow && g.n_lmodes > 0);  // per-row weights
+            const bool has_common = g.opack ? g.n_lmodes > 0 : g.n_outer > 0;   // a row common to the tile
             float *part = bargs.partial + it.part_off + int64_t(l) * rp;
             bool first_flush = true;
             float acc[RPB];
@@ -853,7 +917,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             while (!it.done && it.u == u) {
                 if (it.tile != tile) {
                     tile = it.tile;
-                    if (lane_weights) rv = row_valid(g, ucol, tile_rowbase(g, ucol, tile), l);
+                    if (lane_weights) rv = g.opack ? opack_row_valid(g, tile, l) : row_valid(g, ucol, tile_rowbase(g, ucol, tile), l);
                 }
                 const int ws = int(fgi % C::WSLOTS);
                 const uint32_t wj = uint32_t(fgi / C::WSLOTS);
@@ -863,8 +927,8 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 }
                 const float *wsl = wbuf + ws * C::WSLOT_FLOATS;
                 const float *lrow = wsl + rp * (1 + lg);
-                float w0 = g.n_outer > 0 ? wsl[lane] : 1.f;
-                float w1 = (rp > 32 && g.n_outer > 0) ? wsl[lane + 32] : 1.f;
+                float w0 = has_common ? wsl[lane] : 1.f;
+                float w1 = (rp > 32 && has_common) ? wsl[lane + 32] : 1.f;
                 if (!lane_weights && g.n_lmodes > 0) {
                     w0 = wsl[rp + lane] * w0;
                     if (rp > 32) w1 = wsl[rp + lane + 32] * w1;

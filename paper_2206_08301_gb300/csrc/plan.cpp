@@ -210,7 +210,23 @@ void build_mttkrp_geometry(deinsum_plan_s *pl) {
     g.O = 1;
     for (int k = 0; k < g.n_outer; ++k) g.O *= g.outer_dim[k];
     g.n_kb = int((g.K_in + DEINSUM_BK - 1) / DEINSUM_BK);
-    g.fg_per_col = g.tiles_per_col * g.O;
+    g.O_iter = g.O;
+    g.opack = 0;
+    // Tensor-core path with short rows (I_n < 128) and no leading index to pack into a
+    // tile (case 0 with P = 1, or case 1): pack G consecutive outer indices instead,
+    // tile row g*I_n + i_n (the partial rows of the G groups are summed by the reduction
+    // like the narrow p groups).
+    if (pl->prec == DEINSUM_PREC_SPLIT_BF16 && pl->dtype == DEINSUM_F32 && g.I < DEINSUM_BM && g.O > 1 &&
+        (g.kcase == 1 || g.P == 1)) {
+        g.opack = 1;
+        g.narrow = 1;
+        g.G = std::min<int64_t>(std::min<int64_t>(DEINSUM_BM / g.I, DEINSUM_GMAX), g.O);
+        g.n_cols = 1;
+        g.tiles_per_col = (g.O + g.G - 1) / g.G;
+        g.rows_per_col = g.I;
+        g.O_iter = 1;
+    }
+    g.fg_per_col = g.tiles_per_col * g.O_iter;
 }
 
 // Split every column's fiber groups into contiguous units, about `target`
@@ -493,6 +509,7 @@ deinsum_status plan_ttmc_fused(deinsum_plan_s *pl) {
     g.R_pad = 32;
     g.n_kb = pl->t_nkb;
     g.vec_ok = 1;
+    g.O_iter = 1;
     return DEINSUM_OK;
 }
 
@@ -542,8 +559,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // Tiled tensor map of X for the tensor-core kernel (see MttkrpArgs):
-//   case 0: dims {K_in, O, I, P}, box {64, 1, min(I,128), G}
-//   case 1: dims {I, K_in, O},    box {min(I,128), 64, 1}
+//   case 0: dims {K_in, O, I, P}, box {64, 1, min(I,128), G}; opack {K_in, I, O, P}, box {64, I, G, 1}
+//   case 1: dims {I, K_in, O},    box {min(I,128), 64, 1 (opack: G)}
 // Needs 16-byte aligned X and rows (vec_ok) and coordinates within int32.
 bool encode_x_map(deinsum_plan_s *pl, const void *X) {
     if (pl->xmap_ptr == X) return pl->xmap_ok != 0;
@@ -556,7 +573,15 @@ bool encode_x_map(deinsum_plan_s *pl, const void *X) {
     cuuint64_t dims[4], strides[3];
     cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
     cuuint32_t rank;
-    if (g.kcase == 0) {
+    if (g.kcase == 0 && g.opack) {
+        // {K_in, I, O, P}: a box of G outer indices x all I_n rows lands as [o][i][k]
+        if (g.K_in >= lim || g.O >= lim || g.I >= lim || g.P >= lim) return false;
+        rank = 4;
+        dims[0] = cuuint64_t(g.K_in); dims[1] = cuuint64_t(g.I); dims[2] = cuuint64_t(g.O); dims[3] = cuuint64_t(g.P);
+        strides[0] = cuuint64_t(g.Q) * 4; strides[1] = cuuint64_t(g.K_in) * 4; strides[2] = cuuint64_t(g.I * g.Q) * 4;
+        box[0] = DEINSUM_BK; box[1] = cuuint32_t(g.I); box[2] = cuuint32_t(g.G); box[3] = 1;
+        pl->xmap_pitch = DEINSUM_BK;
+    } else if (g.kcase == 0) {
         if (g.K_in >= lim || g.O >= lim || g.I >= lim || g.P >= lim) return false;
         rank = 4;
         dims[0] = cuuint64_t(g.K_in); dims[1] = cuuint64_t(g.O); dims[2] = cuuint64_t(g.I); dims[3] = cuuint64_t(g.P);
@@ -566,11 +591,13 @@ bool encode_x_map(deinsum_plan_s *pl, const void *X) {
         box[3] = cuuint32_t(g.narrow ? g.G : 1);
         pl->xmap_pitch = DEINSUM_BK;
     } else {
+        // {I, K_in, O}: box {min(I,128), 64, G}, landing as [o][k][i] (G = 1 unless opack)
         if (g.K_in >= lim || g.O >= lim || g.I >= lim) return false;
         rank = 3;
         dims[0] = cuuint64_t(g.I); dims[1] = cuuint64_t(g.K_in); dims[2] = cuuint64_t(g.O);
         strides[0] = cuuint64_t(g.I) * 4; strides[1] = cuuint64_t(g.I * g.K_in) * 4;
-        box[0] = cuuint32_t(std::min<int64_t>(g.I, DEINSUM_BM)); box[1] = DEINSUM_BK; box[2] = 1;
+        box[0] = cuuint32_t(std::min<int64_t>(g.I, DEINSUM_BM)); box[1] = DEINSUM_BK;
+        box[2] = cuuint32_t(g.opack ? g.G : 1);
         pl->xmap_pitch = int(box[0]);
     }
     uint64_t bytes = 4;

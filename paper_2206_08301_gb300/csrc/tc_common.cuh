@@ -28,6 +28,10 @@ constexpr int EPI_WARPS = 4;
 __device__ __forceinline__ int64_t tile_rowbase(const MttkrpGeom &g, int64_t col, int64_t t) {
     return g.narrow ? t * g.G * g.I : t * g.I + col * BM;
 }
+// opack tiles: row l = g * I_n + i_n of tile t holds outer index t*G + g.
+__device__ __forceinline__ bool opack_row_valid(const MttkrpGeom &g, int64_t t, int l) {
+    return l < g.G * g.I && t * g.G + l / g.I < g.O;
+}
 __device__ __forceinline__ bool row_valid(const MttkrpGeom &g, int64_t col, int64_t rowbase, int l) {
     if (g.kcase == 1) return col * BM + l < g.I;
     if (g.narrow) return l < g.G * g.I && rowbase + l < g.P * g.I;
@@ -42,8 +46,11 @@ __device__ __forceinline__ bool row_valid(const MttkrpGeom &g, int64_t col, int6
 
 // From the raw tile the TMA wrote (out-of-bounds rows and k were zero-filled
 // by the TMA; narrow rows beyond G*I_n, which the box does not cover, are zeroed here).
-__device__ __forceinline__ void conv_read_smem(const MttkrpGeom &g, int pitch, const float *raw, int pt,
-                                               float4 (&v)[8]) {
+// OPACK: the tile packs outer indices (see MttkrpGeom::opack); a compile-time
+// flag so that kernels without packing keep the plain case-1 read.
+template <bool OPACK>
+__device__ __forceinline__ void conv_read_smem_t(const MttkrpGeom &g, int pitch, const float *raw, int pt,
+                                                 float4 (&v)[8]) {
     if (g.kcase == 0) {
         const int k4 = pt & 15, rsub = pt >> 4;
         const int nrows = g.narrow ? int(g.G * g.I) : BM;
@@ -53,7 +60,7 @@ __device__ __forceinline__ void conv_read_smem(const MttkrpGeom &g, int pitch, c
             v[j] = row < nrows ? *reinterpret_cast<const float4 *>(raw + row * BK + 4 * k4)
                                : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-    } else {
+    } else if (!OPACK) {
         const int row = pt & (BM - 1), kh = pt >> 7;
         const bool rv = row < pitch;
         #pragma unroll
@@ -63,9 +70,28 @@ __device__ __forceinline__ void conv_read_smem(const MttkrpGeom &g, int pitch, c
             for (int q = 0; q < 4; ++q) e[q] = rv ? raw[(32 * kh + 4 * j + q) * pitch + row] : 0.f;
             v[j] = make_float4(e[0], e[1], e[2], e[3]);
         }
+    } else {
+        // opack: the box lands as [o][k][i] with G outer groups, tile row = gq * I_n + i
+        const int row = pt & (BM - 1), kh = pt >> 7;
+        const int gq = row / pitch, i = row - gq * pitch;
+        const bool rv = gq < g.G;
+        const float *rb = raw + gq * BK * pitch + i;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float e[4];
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) e[q] = rv ? rb[(32 * kh + 4 * j + q) * pitch] : 0.f;
+            v[j] = make_float4(e[0], e[1], e[2], e[3]);
+        }
     }
 }
 
+// run-time choice (kernels that serve both kinds of tile)
+__device__ __forceinline__ void conv_read_smem(const MttkrpGeom &g, int pitch, const float *raw, int pt,
+                                               float4 (&v)[8]) {
+    if (g.opack) conv_read_smem_t<true>(g, pitch, raw, pt, v);
+    else conv_read_smem_t<false>(g, pitch, raw, pt, v);
+}
 __device__ __forceinline__ void conv_read_smem(const MttkrpArgs &a, const float *raw, int pt, float4 (&v)[8]) {
     conv_read_smem(a.g, a.raw_pitch, raw, pt, v);
 }

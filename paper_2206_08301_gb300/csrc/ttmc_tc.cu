@@ -169,7 +169,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             const int rs = int(chunk % RS);
             const uint32_t rj = uint32_t(chunk / RS);
             if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
-            conv_read_smem(a.g, BM, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
+            conv_read_smem_t<false>(a.g, BM, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
             const int as = int(chunk % AS);
             const uint32_t aj = uint32_t(chunk / AS);
             if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status))) break;

@@ -57,6 +57,13 @@ SMALL_CASES = [
     ((12, 9, 10, 11, 16), 8),  # order 5, rank 8
     ((500, 300), 64),          # order 2 (a matrix product), rank 64
     ((129, 3, 257), 5),        # odd extents around the tile sizes
+    # short output rows with nothing to pack but outer indices (mode 0 with P = 1, and the last
+    # mode): the tensor-core path packs G outer indices per tile; aligned (TMA) and not
+    ((50, 70, 60), 32),        # mode 0: G = 2 outer indices per tile; mode 2: G = 2 as well
+    ((40, 6, 7, 8, 36), 24),   # order 5, mode 0: O = 336 outer indices, G = 3; mode 4: G = 2
+    ((1, 50, 70, 60), 16),     # mode 1 with P = 1 and an L row common to the tile
+    ((50, 70, 61), 32),        # K_in % 4 != 0 (no TMA, bounds-checked loads) with packing in mode 0
+    ((30, 40, 51), 64),        # last mode I = 51 (no TMA in mode 2) with packing; rank 64
 ]
 
 
