@@ -412,7 +412,8 @@ def run_ttmc(args):
 
 def run_paper(args):
     """The paper's own benchmark shapes (Table V, single-device sizes; uniform X, factors N(0,1)):
-    MTTKRP-O3-M{0,1,2} at 1024^3, R 24; MTTKRP-O5-M{0,2,4} at 64^5, R 24 (the order-5 extent
+    MTTKRP-O3-M{0,1,2} at 1024^3, R 24; the running example of Sec. II-A (MTTKRP + MM,
+    ijk,ja,ka,al->il) at 1024^3, R 24, L 64; MTTKRP-O5-M{0,2,4} at 64^5, R 24 (the order-5 extent
     1024 of the table is read as 64, see the design notes); TTMc-O5-M0 at 60^5, R 24.  One JSON
     line per benchmark: split-BF16 and plain FP32 times, GB/s of algorithmic bytes, the main
     kernel's roofline fraction, and the relative error on sampled output rows."""
@@ -442,6 +443,7 @@ def run_paper(args):
         return e0.elapsed_time(e1) / steps, kms / max(1, kn)
 
     cases = [("MTTKRP-O3-M%d" % m, "mttkrp", (1024,) * 3, m) for m in (0, 1, 2)]
+    cases += [("MTTKRP+MM-O3-M0", "mm", (1024,) * 3, 0)]   # the running example ijk,ja,ka,al->il, L = 64
     cases += [("MTTKRP-O5-M%d" % m, "mttkrp", (64,) * 5, m) for m in (0, 2, 4)]
     cases += [("TTMc-O5-M0", "ttmc", (60,) * 5, 0)]
     R, seed = 24, 1301
@@ -458,10 +460,16 @@ def run_paper(args):
         if kind == "mttkrp":
             spec, ext = dz.mttkrp_einsum(N, mode), list(dims) + [R]
             out = torch.empty(dims[mode], R, device="cuda")
+        elif kind == "mm":
+            Cm = inputs.factor_normal(seed, 9, R, 64).astype(np.float32)
+            spec, ext = dz.mttkrp_mm_einsum(N, mode), list(dims) + [R, 64]
+            out = torch.empty(dims[mode], 64, device="cuda")
         else:
             spec, ext = dz.ttmc_einsum(N, mode), list(dims) + [R] * (N - 1)
             out = torch.empty([dims[m] if m == mode else R for m in range(N)], device="cuda")
         ops = [X] + [Ud[m] for m in range(N) if m != mode]
+        if kind == "mm":
+            ops.append(torch.from_numpy(Cm).cuda())
         res = {}
         for prec in ("split_bf16", "plain"):
             plan = dz.Plan(spec, ext, "float32", prec)
@@ -471,8 +479,10 @@ def run_paper(args):
                 rows = inputs.sample_rows(seed, dims[mode], 2, tag=mode)
                 got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
         slabs = np.stack([inputs.uniform_slab(seed, dims, mode, int(r)).ravel() for r in rows])
-        if kind == "mttkrp":
+        if kind in ("mttkrp", "mm"):
             ref = oracle.mttkrp_rows(dims, mode, slabs, Us)
+            if kind == "mm":
+                ref = ref @ Cm.astype(np.float64)
             kernel, kbytes = "mttkrp_tc_kernel", 4.0 * float(np.prod(dims))
         else:
             ref = oracle.ttmc_rows(dims, mode, slabs, Us)

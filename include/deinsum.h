@@ -96,6 +96,7 @@ typedef struct {
     double alg_bytes;         /* |X| + factor bytes + output bytes (compulsory traffic) */
     double alg_flops;         /* 2 x multiply-adds of the FLOP-minimal binary chain */
     int64_t n_units;          /* work units of the main kernel (0 before the first execute) */
+    int64_t mm_cols;          /* MTTKRP followed by a matrix product: L (columns of C); else 0 */
 } deinsum_plan_info_t;
 
 /*
@@ -108,8 +109,16 @@ typedef struct {
  *              one rank letter, output "<kept letter><rank letter>".  TTMc: N-1
  *              factors with distinct rank letters, output = X's letters with each
  *              contracted letter replaced by its rank letter in place.
+ *              MTTKRP (order >= 3) followed by a matrix product (the running
+ *              example of Sec. II-A, "ijk,ja,ka,al->il"): the MTTKRP operands, then one
+ *              more operand "<rank letter><new letter>" (C, R x L), output
+ *              "<kept letter><new letter>"; the product with C is applied in the
+ *              final reduction, so the I_n x R MTTKRP result never reaches HBM.
  *              Anything else returns DEINSUM_ERR_UNSUPPORTED (paper Sec. III-A
  *              semantics: repeated letters are summed, output letters kept).
+ *              TTMc with SPLIT_BF16 is the fused kernel of the last two modes:
+ *              it needs the kept mode below N-2, R_{N-2}, R_{N-1} <= 32 and
+ *              I_{N-1} a multiple of 4 (else DEINSUM_ERR_UNSUPPORTED).
  *   extents    one positive extent per distinct letter, in order of first
  *              appearance in `einsum` (host array of n_extents values).
  *   dtype      tensor element type.

@@ -6,6 +6,8 @@ OpenMP over output rows) through ctypes and adds:
 
 * ``einsum_naive`` -- the n-ary brute-force loop nest of Listing 1 (Sec. II),
   pure Python, for tiny inputs;
+* ``mttkrp_mm`` -- the MTTKRP + MM running example of Sec. II-A (the MTTKRP,
+  then one library matrix product);
 * ``cpals`` -- the CP-ALS reference (Kolda & Bader, SIAM Review 2009, Sec. 3.4),
   plain numpy in float64 (the paper names CP decomposition only as the
   motivation of MTTKRP, Sec. I).
@@ -184,6 +186,14 @@ def rel_error(got, ref) -> float:
 # Listing 1 (Sec. II): the n-ary loop nest, one loop per distinct index,
 # accumulating the product of every operand into the output.  Pure Python.
 # ---------------------------------------------------------------------------
+
+def mttkrp_mm(X, factors, mode: int, C) -> np.ndarray:
+    """MTTKRP followed by a matrix product, the running example of Sec. II-A
+    (``ijk,ja,ka,al->il``): the mode-``mode`` MTTKRP of X, then times C (R x L),
+    in float64; the product is a library matrix multiply of the two factors of
+    the binary chain the section writes out (Listing 2: KRP, TDOT, then MM)."""
+    return mttkrp(X, factors, mode) @ np.asarray(C, dtype=np.float64)
+
 
 def einsum_naive(spec: str, *operands) -> np.ndarray:
     """Brute-force einsum ``spec`` ("ab,bc->ac" form, explicit output) over float64 operands."""

@@ -18,7 +18,8 @@ import ctypes
 import os
 import threading
 
-__all__ = ["DeinsumError", "Plan", "mttkrp", "ttmc", "mttkrp_einsum", "ttmc_einsum",
+__all__ = ["DeinsumError", "Plan", "mttkrp", "ttmc", "mttkrp_einsum", "ttmc_einsum", "mttkrp_mm",
+           "mttkrp_mm_einsum",
            "gen_uniform", "gen_cp", "kernel_launch_count", "library_path", "load"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -46,7 +47,7 @@ class _PlanInfo(ctypes.Structure):
                 ("dtype", ctypes.c_int), ("prec", ctypes.c_int),
                 ("dims", ctypes.c_int64 * 8), ("ranks", ctypes.c_int64 * 8),
                 ("out_elems", ctypes.c_int64), ("alg_bytes", ctypes.c_double),
-                ("alg_flops", ctypes.c_double), ("n_units", ctypes.c_int64)]
+                ("alg_flops", ctypes.c_double), ("n_units", ctypes.c_int64), ("mm_cols", ctypes.c_int64)]
 
 
 class _Request(ctypes.Structure):
@@ -212,7 +213,7 @@ class Plan:
         return {"kind": KINDS[info.kind], "order": info.order, "mode": info.mode,
                 "dims": list(info.dims[:info.order]), "ranks": list(info.ranks[:info.order]),
                 "out_elems": info.out_elems, "alg_bytes": info.alg_bytes, "alg_flops": info.alg_flops,
-                "n_units": info.n_units}
+                "n_units": info.n_units, "mm_cols": info.mm_cols}
 
     def workspace_size(self) -> int:
         n = ctypes.c_size_t()
@@ -269,6 +270,26 @@ def mttkrp_einsum(order: int, mode: int) -> str:
     x = _XL[:order]
     fac = [x[m] + "r" for m in range(order) if m != mode]
     return ",".join([x] + fac) + "->" + x[mode] + "r"
+
+
+def mttkrp_mm_einsum(order: int, mode: int) -> str:
+    """MTTKRP followed by a matrix product, the running example of Sec. II-A
+    (``ijk,ja,ka,al->il`` for order 3, mode 0): the MTTKRP operands, then C = "r l"."""
+    x = _XL[:order]
+    fac = [x[m] + "r" for m in range(order) if m != mode]
+    return ",".join([x] + fac + ["rl"]) + "->" + x[mode] + "l"
+
+
+def mttkrp_mm(X, factors, mode: int, C, prec: str = "plain", out=None, stream=None):
+    """``mttkrp(X, factors, mode) @ C`` with the product applied in the final reduction."""
+    import torch
+    order = X.dim()
+    R = next(f.shape[1] for m, f in enumerate(factors) if m != mode)
+    spec = mttkrp_mm_einsum(order, mode)
+    extents = list(X.shape) + [R, C.shape[1]]
+    dtype = "float64" if X.dtype == torch.float64 else "float32"
+    plan = _cached_plan(spec, extents, dtype, prec)
+    return plan(X, *[factors[m] for m in range(order) if m != mode], C, out=out, stream=stream)
 
 
 def ttmc_einsum(order: int, keep: int) -> str:

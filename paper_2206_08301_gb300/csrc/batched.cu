@@ -418,7 +418,7 @@ deinsum_status deinsum_plan_batched(int n, const char *const *einsums, const int
         }
         deinsum_plan_info_t info;
         deinsum_plan_info(b->plans[size_t(i)], &info);
-        if (info.kind != DEINSUM_KIND_MTTKRP) {
+        if (info.kind != DEINSUM_KIND_MTTKRP || info.mm_cols != 0) {   // plain MTTKRP instances only
             deinsum_batched_destroy(b);
             return DEINSUM_ERR_UNSUPPORTED;
         }

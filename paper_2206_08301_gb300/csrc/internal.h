@@ -140,8 +140,12 @@ int launch_weight_tables_batched(const MttkrpArgs *insts, int n, int64_t max_flo
 // Floats of the two tables: P x R_pad (if n_lmodes > 0) and O x R_pad (if n_outer > 0).
 inline size_t weight_table_floats_l(const MttkrpGeom &g) { return g.n_lmodes > 0 ? size_t(g.P) * size_t(g.R_pad) : 0; }
 inline size_t weight_table_floats_o(const MttkrpGeom &g) { return g.n_outer > 0 ? size_t(g.O) * size_t(g.R_pad) : 0; }
-int launch_mttkrp_reduce_f32(const MttkrpArgs &a, const int64_t *col_unit_begin, void *out, void *stream);
-int launch_mttkrp_reduce_f64(const MttkrpArgs &a, const int64_t *col_unit_begin, void *out, void *stream);
+// The final reduction of the unit partials into the I_n x R output; with C (R x L,
+// device) it writes out = M C instead (I_n x L), the MTTKRP + MM epilogue.
+int launch_mttkrp_reduce_f32(const MttkrpArgs &a, const int64_t *col_unit_begin, void *out, void *stream,
+                             const void *C = nullptr, int64_t L = 0);
+int launch_mttkrp_reduce_f64(const MttkrpArgs &a, const int64_t *col_unit_begin, void *out, void *stream,
+                             const void *C = nullptr, int64_t L = 0);
 size_t mttkrp_tc_smem_bytes(int R_pad);
 int mttkrp_plain_ctas_per_sm(int f64, int R_pad);  // resident CTAs per SM of the plain kernel
 

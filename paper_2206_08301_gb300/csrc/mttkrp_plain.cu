@@ -310,8 +310,51 @@ __global__ void mttkrp_reduce_kernel(const T *__restrict__ partial, const int64_
     out[idx] = s;
 }
 
+// MTTKRP followed by a matrix product (Sec. II-A running example): per output
+// row, M[row, :] is summed from the unit partials in the same fixed order as
+// above into shared memory, then out[row, l] = sum_r M[row, r] C[r, l] (r in
+// order).  M never reaches HBM.
 template <typename T>
-int launch_reduce(const MttkrpArgs &a, const T *partial, const int64_t *col_begin, void *out, void *stream) {
+__global__ void mttkrp_reduce_mm_kernel(const T *__restrict__ partial, const int64_t *__restrict__ col_begin,
+                                        const T *__restrict__ C, T *__restrict__ out, int64_t I, int R, int RP,
+                                        int64_t rows_per_col, int64_t G, int narrow, int64_t L) {
+    __shared__ T m[64];
+    for (int64_t row = blockIdx.x; row < I; row += gridDim.x) {
+        const int64_t col = row / rows_per_col;
+        const int64_t i = row - col * rows_per_col;
+        for (int r = threadIdx.x; r < R; r += blockDim.x) {
+            T s = T(0);
+            for (int64_t u = col_begin[col]; u < col_begin[col + 1]; ++u) {
+                const T *p = partial + u * BM * RP;
+                if (narrow) {
+                    for (int64_t gi = 0; gi < G; ++gi) s += p[(gi * I + i) * RP + r];
+                } else {
+                    s += p[i * RP + r];
+                }
+            }
+            m[r] = s;
+        }
+        __syncthreads();
+        for (int64_t l = threadIdx.x; l < L; l += blockDim.x) {
+            T acc = T(0);
+            for (int r = 0; r < R; ++r) acc += m[r] * C[int64_t(r) * L + l];
+            out[row * L + l] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+int launch_reduce(const MttkrpArgs &a, const T *partial, const int64_t *col_begin, void *out, void *stream,
+                  const void *C, int64_t L) {
+    if (C) {
+        const int64_t blocks = a.g.I < 8192 ? a.g.I : 8192;
+        mttkrp_reduce_mm_kernel<T><<<unsigned(blocks), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+            partial, col_begin, static_cast<const T *>(C), static_cast<T *>(out), a.g.I, a.g.R, a.g.R_pad,
+            a.g.rows_per_col, a.g.G, a.g.narrow, L);
+        count_launch();
+        return int(cudaGetLastError());
+    }
     const int64_t n = a.g.I * a.g.R;
     const int threads = 256;
     const int64_t blocks = (n + threads - 1) / threads;
@@ -348,11 +391,13 @@ int mttkrp_plain_ctas_per_sm(int f64, int R_pad) { return f64 ? plain_ctas_per_s
 
 int launch_mttkrp_plain_f32(const MttkrpArgs &a, int n_sm, void *stream) { return launch_plain<float>(a, n_sm, stream); }
 int launch_mttkrp_plain_f64(const MttkrpArgs &a, int n_sm, void *stream) { return launch_plain<double>(a, n_sm, stream); }
-int launch_mttkrp_reduce_f32(const MttkrpArgs &a, const int64_t *col_begin, void *out, void *stream) {
-    return launch_reduce<float>(a, a.partial, col_begin, out, stream);
+int launch_mttkrp_reduce_f32(const MttkrpArgs &a, const int64_t *col_begin, void *out, void *stream,
+                             const void *C, int64_t L) {
+    return launch_reduce<float>(a, a.partial, col_begin, out, stream, C, L);
 }
-int launch_mttkrp_reduce_f64(const MttkrpArgs &a, const int64_t *col_begin, void *out, void *stream) {
-    return launch_reduce<double>(a, a.partial64, col_begin, out, stream);
+int launch_mttkrp_reduce_f64(const MttkrpArgs &a, const int64_t *col_begin, void *out, void *stream,
+                             const void *C, int64_t L) {
+    return launch_reduce<double>(a, a.partial64, col_begin, out, stream, C, L);
 }
 
 }  // namespace deinsum

@@ -33,7 +33,8 @@ struct deinsum_plan_s {
     int64_t dims[DEINSUM_MAX_ORDER] = {0};
     int64_t ranks[DEINSUM_MAX_ORDER] = {0};
     int n_operands = 0;
-    int operand_mode[DEINSUM_MAX_ORDER + 1] = {0};  // operand k >= 1 -> mode of X
+    int operand_mode[DEINSUM_MAX_ORDER + 2] = {0};  // operand k >= 1 -> mode of X (the MM operand: -1)
+    int64_t mm_cols = 0;                            // MTTKRP + MM: L, the columns of C (R x L); else 0
 
     // MTTKRP
     MttkrpGeom geom{};
@@ -386,9 +387,12 @@ deinsum_status classify(deinsum_plan_s *pl, const Parsed &p, const int64_t *exte
     for (int a = 0; a < N; ++a)
         for (int b = a + 1; b < N; ++b)
             if (x[a] == x[b]) return DEINSUM_ERR_UNSUPPORTED;  // diagonal access of X
-    if (int(p.ins.size()) != N) return DEINSUM_ERR_UNSUPPORTED;
+    // MTTKRP + MM (Sec. II-A running example, order >= 3; at order 2 it would be a
+    // matrix chain): one more operand "<rank letter><new letter>"
+    const bool mm = N >= 3 && int(p.ins.size()) == N + 1;
+    if (int(p.ins.size()) != N && !mm) return DEINSUM_ERR_UNSUPPORTED;
     pl->order = N;
-    pl->n_operands = N;
+    pl->n_operands = int(p.ins.size());
     for (int m = 0; m < N; ++m) pl->dims[m] = extents[letter_index(p, x[m])];
     std::vector<int> used(size_t(N), 0);
     std::vector<char> rank_letter(size_t(N), 0);
@@ -412,6 +416,19 @@ deinsum_status classify(deinsum_plan_s *pl, const Parsed &p, const int64_t *exte
     char r0 = rank_letter[size_t((kept + 1) % N)];
     for (int m = 0; m < N; ++m)
         if (m != kept && rank_letter[size_t(m)] != r0) same_rank = false;
+    if (mm) {
+        // the last operand is C = "<r><l>" with l new; output "<kept><l>"
+        const std::string &c = p.ins[size_t(N)];
+        if (!same_rank || c.size() != 2 || c[0] != r0 || c[1] == r0 || x.find(c[1]) != std::string::npos)
+            return DEINSUM_ERR_UNSUPPORTED;
+        if (p.out.size() != 2 || p.out[0] != x[size_t(kept)] || p.out[1] != c[1]) return DEINSUM_ERR_UNSUPPORTED;
+        pl->kind = DEINSUM_KIND_MTTKRP;
+        int64_t R = extents[letter_index(p, r0)];
+        for (int m = 0; m < N; ++m) pl->ranks[m] = (m == kept) ? pl->dims[m] : R;
+        pl->operand_mode[N] = -1;
+        pl->mm_cols = extents[letter_index(p, c[1])];
+        return DEINSUM_OK;
+    }
     if (same_rank && p.out.size() == 2 && p.out[0] == x[size_t(kept)] && p.out[1] == r0) {
         pl->kind = DEINSUM_KIND_MTTKRP;
         int64_t R = extents[letter_index(p, r0)];
@@ -516,7 +533,9 @@ deinsum_status plan_ttmc_fused(deinsum_plan_s *pl) {
 double alg_flops(const deinsum_plan_s *pl) {
     double x = 1.0;
     for (int m = 0; m < pl->order; ++m) x *= double(pl->dims[m]);
-    if (pl->kind == DEINSUM_KIND_MTTKRP) return 2.0 * x * double(pl->ranks[(pl->mode + 1) % pl->order]);
+    if (pl->kind == DEINSUM_KIND_MTTKRP)
+        return 2.0 * x * double(pl->ranks[(pl->mode + 1) % pl->order]) +
+               2.0 * double(pl->dims[pl->mode]) * double(pl->ranks[(pl->mode + 1) % pl->order]) * double(pl->mm_cols);
     double cur[DEINSUM_MAX_ORDER];
     for (int m = 0; m < pl->order; ++m) cur[m] = double(pl->dims[m]);
     double f = 0.0;
@@ -536,7 +555,11 @@ double alg_bytes(const deinsum_plan_s *pl) {
         x *= double(pl->dims[m]);
         if (m != pl->mode) fac += double(pl->dims[m]) * double(pl->ranks[m]);
     }
-    if (pl->kind == DEINSUM_KIND_MTTKRP)
+    if (pl->kind == DEINSUM_KIND_MTTKRP && pl->mm_cols > 0) {
+        const double R = double(pl->ranks[(pl->mode + 1) % pl->order]);
+        fac += R * double(pl->mm_cols);                          // C
+        out = double(pl->dims[pl->mode]) * double(pl->mm_cols);  // I_n x L
+    } else if (pl->kind == DEINSUM_KIND_MTTKRP)
         out = double(pl->dims[pl->mode]) * double(pl->ranks[(pl->mode + 1) % pl->order]);
     else
         for (int m = 0; m < pl->order; ++m) out *= double(pl->ranks[m]);
@@ -611,11 +634,13 @@ bool encode_x_map(deinsum_plan_s *pl, const void *X) {
 }
 
 deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, void *output, void *stream) {
+    const void *mm_c = pl->mm_cols > 0 ? inputs[pl->n_operands - 1] : nullptr;  // C of MTTKRP + MM
     MttkrpArgs a;
     std::memset(&a, 0, sizeof(a));
     a.g = pl->geom;
     a.X = inputs[0];
-    for (int k = 1; k < pl->n_operands; ++k) a.U[pl->operand_mode[k]] = inputs[k];
+    for (int k = 1; k < pl->n_operands; ++k)
+        if (pl->operand_mode[k] >= 0) a.U[pl->operand_mode[k]] = inputs[k];
     a.units = pl->d_units;
     a.n_units = pl->planned_units;
     a.status = pl->d_status;
@@ -626,7 +651,7 @@ deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, voi
         const long ti = timing_begin(pl, stream);
         err = launch_mttkrp_plain_f64(a, pl->n_sm, stream);
         timing_end(pl, ti, stream);
-        if (!err) err = launch_mttkrp_reduce_f64(a, pl->d_col_begin, output, stream);
+        if (!err) err = launch_mttkrp_reduce_f64(a, pl->d_col_begin, output, stream, mm_c, pl->mm_cols);
     } else {
         a.partial = static_cast<float *>(pl->d_partial);
         if (pl->prec == DEINSUM_PREC_SPLIT_BF16) {
@@ -649,7 +674,7 @@ deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, voi
             err = launch_mttkrp_plain_f32(a, pl->n_sm, stream);
             timing_end(pl, ti, stream);
         }
-        if (!err) err = launch_mttkrp_reduce_f32(a, pl->d_col_begin, output, stream);
+        if (!err) err = launch_mttkrp_reduce_f32(a, pl->d_col_begin, output, stream, mm_c, pl->mm_cols);
     }
     return err ? DEINSUM_ERR_CUDA : DEINSUM_OK;
 }
@@ -884,7 +909,8 @@ deinsum_status deinsum_plan_info(deinsum_plan_t pl, deinsum_plan_info_t *info) {
         info->ranks[m] = pl->ranks[m];
     }
     if (pl->kind == DEINSUM_KIND_MTTKRP) {
-        info->out_elems = pl->dims[pl->mode] * pl->ranks[(pl->mode + 1) % pl->order];
+        info->out_elems = pl->dims[pl->mode] * (pl->mm_cols > 0 ? pl->mm_cols : pl->ranks[(pl->mode + 1) % pl->order]);
+        info->mm_cols = pl->mm_cols;
     } else {
         info->out_elems = 1;
         for (int m = 0; m < pl->order; ++m) info->out_elems *= pl->ranks[m];

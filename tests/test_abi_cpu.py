@@ -68,7 +68,8 @@ def test_plan_classifies_table_iv_patterns(lib, spec, kind, mode):
     ("ijk,ja,ka", 1),             # no output
     ("ijk,ja,ka->i a", 2),        # spaces are removed -> "ia"... handled below
     ("ij1,ja->ia", 1),            # bad character
-    ("ijk,ja,ka,al->il", 2),      # MTTKRP + MM: not offered
+    ("ijk,ja,ka,al->ia", 2),      # MTTKRP + MM with the rank letter kept in the output
+    ("ijk,ja,ka,al,lm->im", 2),   # MTTKRP + two matrix products: not offered
     ("ij,jk,kl->il", 2),          # 2MM chain: not offered
     ("iik,ia,ka->ia", 2),         # diagonal of X
     ("ijk,ja,kb->iba", 2),        # TTMc with permuted output modes: not offered
@@ -154,3 +155,28 @@ def test_graft_entry_imports():
     import importlib
     g = importlib.import_module("__graft_entry__")
     assert callable(g.build) and callable(g.smoke)
+
+
+def test_mttkrp_mm_plan(lib):
+    """MTTKRP + MM (Sec. II-A running example ijk,ja,ka,al->il): an extra trailing
+    operand <rank><new letter> and output <kept><new letter>."""
+    p = dz.Plan("ijk,ja,ka,al->il", [100, 30, 40, 24, 16])
+    info = p.info()
+    assert info["kind"] == "mttkrp" and info["mode"] == 0 and info["mm_cols"] == 16
+    assert info["out_elems"] == 100 * 16
+    x = 100 * 30 * 40
+    assert info["alg_flops"] == 2.0 * x * 24 + 2.0 * 100 * 24 * 16
+    assert info["alg_bytes"] == 4.0 * (x + 30 * 24 + 40 * 24 + 24 * 16 + 100 * 16)
+    assert dz.mttkrp_mm_einsum(3, 0) == "abc,br,cr,rl->al"
+    dz.Plan(dz.mttkrp_mm_einsum(4, 3), [5, 6, 7, 8, 9, 10], prec="split_bf16")
+    for spec in ["ijk,ja,ka,ak->il",     # C's second letter is a letter of X
+                 "ijk,ja,ka,bl->il",     # C does not start with the rank letter
+                 "ijk,ja,ka,al->ia",     # output keeps the rank letter
+                 "ijk,ja,kb,al->il"]:    # factors do not share one rank letter
+        with pytest.raises(dz.DeinsumError) as e:
+            letters = []
+            for c in spec.replace(",", "").replace("->", ""):
+                if c not in letters:
+                    letters.append(c)
+            dz.Plan(spec, [4] * len(letters))
+        assert e.value.status == 2, spec

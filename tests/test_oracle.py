@@ -64,6 +64,26 @@ def test_mttkrp_matches_listing1_bruteforce(dims):
         np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("dims", [(3, 4, 2), (2, 3, 2, 3)])
+def test_mttkrp_mm_matches_listing1_bruteforce(dims):
+    """MTTKRP + MM, the running example of Sec. II-A (``ijk,ja,ka,al->il`` for order 3,
+    mode 0), against the brute-force n-ary loop nest of Listing 1, in every mode."""
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal(dims)
+    U = _factors(rng, dims, 3)
+    C = rng.standard_normal((3, 4))
+    for mode in range(len(dims)):
+        ops = [X] + [U[m] for m in range(len(dims)) if m != mode] + [C]
+        spec = _mttkrp_spec(len(dims), mode)
+        lhs, out = spec.split("->")
+        ref = oracle.einsum_naive(lhs + ",rz->" + out[0] + "z", *ops)
+        np.testing.assert_allclose(oracle.mttkrp_mm(X, U, mode, C), ref, rtol=1e-13, atol=1e-13)
+    # a transposed C (square case) must not pass: the product is not symmetric in C
+    Cs = rng.standard_normal((3, 3))
+    got = oracle.mttkrp_mm(X, U, 0, Cs)
+    assert not np.allclose(got, oracle.mttkrp_mm(X, U, 0, Cs.T))
+
+
 @pytest.mark.parametrize("dims", [(6, 7, 5), (4, 5, 3, 6), (3, 4, 2, 3, 5)])
 def test_mttkrp_matches_factored_krp_tdot(dims):
     rng = np.random.default_rng(2)

@@ -196,3 +196,22 @@ def test_ttmc_f64():
     Us = [inputs.factor_normal(3, m, d, r) for m, (d, r) in enumerate(zip(dims, ranks))]
     got = dz.ttmc(torch.from_numpy(X).cuda(), [torch.from_numpy(u).cuda() for u in Us], 0).cpu().numpy()
     _check(got, oracle.ttmc(X, Us, 0), "plain64")
+
+
+@pytest.mark.parametrize("prec", ["plain", "split_bf16", "plain64"])
+@pytest.mark.parametrize("dims,R,L", [((160, 96, 136), 24, 40), ((20, 30, 17, 64), 32, 7), ((50, 70, 60), 16, 64)])
+def test_mttkrp_mm_all_modes(dims, R, L, prec):
+    """MTTKRP + MM (Sec. II-A running example, product applied in the final reduction)."""
+    seed = 23
+    dtype = np.float64 if prec == "plain64" else np.float32
+    X = inputs.tensor_uniform_f32(seed, dims).astype(dtype)
+    Us = _factors(seed, dims, R, dtype=dtype)
+    C = inputs.factor_normal(seed, 9, R, L).astype(dtype)
+    Xd = torch.from_numpy(X).cuda()
+    Ud = [torch.from_numpy(u).cuda() for u in Us]
+    Cd = torch.from_numpy(C).cuda()
+    for mode in range(len(dims)):
+        got = dz.mttkrp_mm(Xd, Ud, mode, Cd, prec="plain" if prec == "plain64" else prec)
+        torch.cuda.synchronize()
+        assert tuple(got.shape) == (dims[mode], L)
+        _check(got.cpu().numpy(), oracle.mttkrp_mm(X, Us, mode, C), "plain32" if prec == "plain" else prec)
