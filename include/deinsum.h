@@ -413,6 +413,70 @@ deinsum_status deinsum_gen_cp_f32(uint64_t seed, int order, const int64_t *dims,
                                   const float *const *factors, double sigma, float *out,
                                   deinsum_stream_t stream);
 
+/*
+ * Block distribution and redistribution (paper Sec. II-C/D, Sec. V), host only.
+ *
+ * An iteration space of extents N_0..N_{D-1} is distributed over a Cartesian grid
+ * of P_0 x .. x P_{D-1} processes, one block per process (Eqs. (12)-(13)): along
+ * dimension j the block size is B_j = ceil(N_j / P_j) and process coordinate p_j
+ * holds indices [p_j B_j, min((p_j + 1) B_j, N_j)).  Ranks number the grid
+ * row-major (the last dimension fastest, as MPI_Cart_create without reordering).
+ * A tensor on the grid uses some of its dimensions (`dims[t]` = the grid
+ * dimension of tensor mode t); its blocks are replicated over the sub-grids of
+ * the unused dimensions (the MPI_Cart_sub view of the paper's listing).
+ */
+typedef struct {
+    int ndim;              /* D, 1..8 */
+    int64_t extent[8];     /* N_j >= 1 */
+    int procs[8];          /* P_j >= 1 */
+} deinsum_grid_t;
+
+/* B_j = ceil(N_j / P_j) (0 on bad arguments). */
+int64_t deinsum_grid_block(const deinsum_grid_t *g, int j);
+/* Coordinates of `rank` (HOST array of ndim ints) / rank of `coords` (-1 if out of range). */
+deinsum_status deinsum_grid_coords(const deinsum_grid_t *g, int64_t rank, int *coords);
+int64_t deinsum_grid_rank(const deinsum_grid_t *g, const int *coords);
+/* The block of `rank`: [lo[j], hi[j]) per dimension (HOST arrays of ndim values). */
+deinsum_status deinsum_grid_block_range(const deinsum_grid_t *g, int64_t rank, int64_t *lo, int64_t *hi);
+/* MPI_Cart_sub semantics: the sub-grid keeping the dimensions with remain[j] != 0.
+ * `color` numbers the sub-grid (row-major over the dropped coordinates), `key` is
+ * the rank inside it (row-major over the kept coordinates). */
+deinsum_status deinsum_grid_sub(const deinsum_grid_t *g, const int *remain, int64_t rank, int64_t *color,
+                                int64_t *key);
+
+/* One dimension of a redistribution from block size Bx to By (Eqs. (20)-(24)):
+ * with p^(y) B^(y) = xi B^(x) + lambda, the offsets o^(y) of y-block py fall into
+ * k = ceil((By + lambda) / Bx) runs; run m, o^(y) in [oy_lo, oy_hi), comes from
+ * x-process px = xi + m at offsets [ox_lo, ox_hi). */
+typedef struct {
+    int64_t px;
+    int64_t oy_lo, oy_hi;
+    int64_t ox_lo, ox_hi;
+} deinsum_dim_part_t;
+/* Fills parts[0..k) and returns k (-1 on bad arguments or k > max_parts).  Blocks
+ * are taken as full (B^(y) offsets); clip against the extent for a last block. */
+int deinsum_redist_dim_partitions(int64_t Bx, int64_t By, int64_t py, deinsum_dim_part_t *parts, int max_parts);
+/* Message matching (Eq. (25)): the y-process coordinates [*py_lo, *py_hi) whose
+ * blocks meet x-block px (before clipping to the grid). */
+void deinsum_redist_match(int64_t Bx, int64_t By, int64_t px, int64_t *py_lo, int64_t *py_hi);
+
+/* One message of a redistribution: the peer rank and the box [lo, hi) of global
+ * tensor coordinates (one entry per tensor mode). */
+typedef struct {
+    int64_t peer;
+    int64_t lo[8], hi[8];
+} deinsum_msg_t;
+/* The messages `rank` sends (sending != 0, rank on gx) or receives (rank on gy)
+ * when a tensor of `order` modes moves from its block distribution on gx
+ * (modes on grid dimensions xdims) to the one on gy (ydims); extents must agree.
+ * A block replicated on gx is sent once, by its replica with zero coordinates in
+ * the unused dimensions; every replica on gy receives its part.  Between two
+ * ranks there is at most one message (the intersection of two blocks is one box).
+ * Writes up to max_msgs entries to msgs (may be NULL to count) and returns the
+ * number of messages, or -1 on bad arguments or when max_msgs is too small. */
+int deinsum_redist_plan(const deinsum_grid_t *gx, const int *xdims, const deinsum_grid_t *gy, const int *ydims,
+                        int order, int64_t rank, int sending, deinsum_msg_t *msgs, int max_msgs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,8 @@ import threading
 
 __all__ = ["DeinsumError", "Plan", "mttkrp", "ttmc", "mttkrp_einsum", "ttmc_einsum", "mttkrp_mm",
            "mttkrp_mm_einsum",
-           "gen_uniform", "gen_cp", "kernel_launch_count", "library_path", "load"]
+           "gen_uniform", "gen_cp", "kernel_launch_count", "library_path", "load",
+           "Grid", "redist_dim_partitions", "redist_match", "redist_plan"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "libdeinsum.so")
@@ -99,6 +100,14 @@ def load():
         lib.deinsum_set_kernel_timing.restype = i32
         lib.deinsum_kernel_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         lib.deinsum_kernel_time.restype = i32
+        lib.deinsum_grid_block.restype = i64
+        lib.deinsum_grid_rank.restype = i64
+        lib.deinsum_grid_coords.restype = i32
+        lib.deinsum_grid_block_range.restype = i32
+        lib.deinsum_grid_sub.restype = i32
+        lib.deinsum_redist_dim_partitions.restype = i32
+        lib.deinsum_redist_match.restype = None
+        lib.deinsum_redist_plan.restype = i32
         lib.deinsum_cpals_create.argtypes = [i32, ctypes.POINTER(i64), i32, i32, ctypes.POINTER(vp)]
         lib.deinsum_cpals_create.restype = i32
         lib.deinsum_cpals_run.argtypes = [vp, vp, ctypes.POINTER(vp), vp, i32, vp, vp]
@@ -553,3 +562,102 @@ def gen_cp(seed: int, dims, cp_factors, sigma: float, device="cuda", stream=None
 def kernel_launch_count() -> int:
     """Kernels the library has launched in this process (all entry points)."""
     return int(load().deinsum_kernel_launch_count())
+
+
+# ---------------------------------------------------------------------------
+# Block distribution and redistribution (``deinsum_grid_*`` / ``deinsum_redist_*``,
+# host only; paper Sec. II-C/D and Sec. V)
+# ---------------------------------------------------------------------------
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("extent", ctypes.c_int64 * 8), ("procs", ctypes.c_int * 8)]
+
+
+class _DimPart(ctypes.Structure):
+    _fields_ = [("px", ctypes.c_int64), ("oy_lo", ctypes.c_int64), ("oy_hi", ctypes.c_int64),
+                ("ox_lo", ctypes.c_int64), ("ox_hi", ctypes.c_int64)]
+
+
+class _Msg(ctypes.Structure):
+    _fields_ = [("peer", ctypes.c_int64), ("lo", ctypes.c_int64 * 8), ("hi", ctypes.c_int64 * 8)]
+
+
+class Grid:
+    """A Cartesian process grid over an iteration space, block-distributed (one block per process)."""
+
+    def __init__(self, extents, procs):
+        if len(extents) != len(procs):
+            raise ValueError("one process count per dimension")
+        self.extents = [int(e) for e in extents]
+        self.procs = [int(p) for p in procs]
+        self._g = _Grid(len(extents), (ctypes.c_int64 * 8)(*self.extents), (ctypes.c_int * 8)(*self.procs))
+
+    @property
+    def size(self) -> int:
+        n = 1
+        for p in self.procs:
+            n *= p
+        return n
+
+    def block(self, j: int) -> int:
+        return int(load().deinsum_grid_block(ctypes.byref(self._g), j))
+
+    def coords(self, rank: int):
+        c = (ctypes.c_int * 8)()
+        _check(load().deinsum_grid_coords(ctypes.byref(self._g), ctypes.c_int64(rank), c), "deinsum_grid_coords")
+        return tuple(c[: len(self.procs)])
+
+    def rank(self, coords) -> int:
+        c = (ctypes.c_int * 8)(*[int(x) for x in coords])
+        return int(load().deinsum_grid_rank(ctypes.byref(self._g), c))
+
+    def block_range(self, rank: int):
+        lo, hi = (ctypes.c_int64 * 8)(), (ctypes.c_int64 * 8)()
+        _check(load().deinsum_grid_block_range(ctypes.byref(self._g), ctypes.c_int64(rank), lo, hi),
+               "deinsum_grid_block_range")
+        n = len(self.procs)
+        return tuple(lo[:n]), tuple(hi[:n])
+
+    def sub(self, remain, rank: int):
+        """(color, key) of ``rank`` in the sub-grid keeping the dimensions with remain[j] true."""
+        r = (ctypes.c_int * 8)(*[1 if x else 0 for x in remain])
+        color, key = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().deinsum_grid_sub(ctypes.byref(self._g), r, ctypes.c_int64(rank), ctypes.byref(color),
+                                       ctypes.byref(key)), "deinsum_grid_sub")
+        return int(color.value), int(key.value)
+
+
+def redist_dim_partitions(Bx: int, By: int, py: int):
+    """The runs of one dimension of a redistribution (Eqs. 20-24): [(px, (oy_lo, oy_hi), (ox_lo, ox_hi))]."""
+    parts = (_DimPart * 64)()
+    k = load().deinsum_redist_dim_partitions(ctypes.c_int64(Bx), ctypes.c_int64(By), ctypes.c_int64(py), parts, 64)
+    if k < 0:
+        raise ValueError("bad block sizes")
+    return [(p.px, (p.oy_lo, p.oy_hi), (p.ox_lo, p.ox_hi)) for p in parts[:k]]
+
+
+def redist_match(Bx: int, By: int, px: int):
+    """Message matching (Eq. 25): the half-open range of y-coordinates meeting x-block px."""
+    lo, hi = ctypes.c_int64(), ctypes.c_int64()
+    load().deinsum_redist_match(ctypes.c_int64(Bx), ctypes.c_int64(By), ctypes.c_int64(px), ctypes.byref(lo),
+                                ctypes.byref(hi))
+    return int(lo.value), int(hi.value)
+
+
+def redist_plan(gx: "Grid", xdims, gy: "Grid", ydims, rank: int, sending: bool):
+    """Messages of ``rank`` for moving a tensor from its block distribution on ``gx`` (modes on grid
+    dimensions ``xdims``) to the one on ``gy``: [(peer, lo, hi)] with boxes in global coordinates."""
+    order = len(xdims)
+    xd = (ctypes.c_int * 8)(*xdims)
+    yd = (ctypes.c_int * 8)(*ydims)
+    lib = load()
+    n = lib.deinsum_redist_plan(ctypes.byref(gx._g), xd, ctypes.byref(gy._g), yd, order, ctypes.c_int64(rank),
+                                int(bool(sending)), None, 0)
+    if n < 0:
+        raise ValueError("bad redistribution arguments")
+    msgs = (_Msg * max(1, n))()
+    n2 = lib.deinsum_redist_plan(ctypes.byref(gx._g), xd, ctypes.byref(gy._g), yd, order, ctypes.c_int64(rank),
+                                 int(bool(sending)), msgs, n)
+    if n2 != n:
+        raise RuntimeError("redistribution plan changed between calls")
+    return [(int(m.peer), tuple(m.lo[:order]), tuple(m.hi[:order])) for m in msgs[:n]]
