@@ -24,6 +24,7 @@ timed region is bracketed by barriers and the max over ranks is reported
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -66,9 +67,11 @@ def _alg_bytes_one_mode():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 10 ms; only the samples whose
+    timestamps fall inside the timed region (mark_start .. mark_stop) are reported (with
+    the last sample before it when the region is shorter than the sampling interval)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -76,43 +79,71 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = f"/tmp/deinsum_clocks_{os.getpid()}.csv"
+        self.t0 = self.t1 = None
 
     def start(self):
+        """Start sampling and return once the first sample has been written (or after 5 s)."""
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        deadline = time.time() + 5.0
+        while time.time() < deadline and os.path.getsize(self.path) == 0:
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_stop(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.03)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as fh:
             for line in fh:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
+                if len(parts) < 10:
                     continue
                 try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
+                    rows.append((self._stamp(parts[0]), float(parts[2]), float(parts[3]), parts[6:10]))
                 except ValueError:
                     continue
-                for name, val in zip(names, parts[5:9]):
-                    if val.lower() == "active":
-                        reasons.add(name)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [r for r in rows if r[0] is not None and self.t0 is not None and self.t0 <= r[0] <= self.t1]
+        if not inside:   # a region shorter than the interval: the sample just before it
+            before = [r for r in rows if r[0] is not None and self.t0 is not None and r[0] < self.t0]
+            inside = before[-1:] if before else rows[:1]
+        reasons = set()
+        for r in inside:
+            for name, val in zip(names, r[3]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        sm = [r[1] for r in inside]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "interval_ms": 10, "region_ms": (self.t1 - self.t0) * 1e3 if self.t0 and self.t1 else None}
 
 
 def _kernel_source_hash(source="mttkrp_tc.cu"):
@@ -499,6 +530,56 @@ def run_paper(args):
     return 0
 
 
+def run_cpals(args):
+    """CP-ALS sweeps on X 1024^3 = rank-32 CP tensor (N(0,1) factors) + 1e-2 noise, R = 32,
+    split-BF16: the dimension tree (modes 0 and 1 share X x_2 U_2, two X streams per sweep)
+    against the plain three-MTTKRP sweep, both from the same start.  A run of S sweeps and one
+    of a single sweep are timed; their difference over S - 1 is the steady-state sweep (fit by
+    the expansion), the rest the per-run cost (||X||^2, final residual fit, set-up)."""
+    import torch
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    n, R, seed, sweeps = 1024, 32, 77, max(4, args.steps)
+    dims = (n, n, n)
+    A = [torch.from_numpy(inputs.factor_normal(seed, m, n, R, stream_base=inputs.STREAM_CP).astype(np.float32)).cuda()
+         for m in range(3)]
+    X = dz.gen_cp(seed, dims, A, 1e-2)
+    init = [torch.from_numpy(inputs.factor_normal(seed, m, n, R, stream_base=inputs.STREAM_INIT).astype(np.float32))
+            .cuda() for m in range(3)]
+    stream = torch.cuda.Stream()
+    res = {}
+    for tree in (True, False):
+        cp = dz.CPALS(dims, R, "split_bf16")
+        cp.set_dimension_tree(tree)
+        F = [u.clone() for u in init]
+        t = {}
+        with torch.cuda.stream(stream):
+            cp.run(X, F, 1, stream=stream)          # first run: workspace, warm-up
+            for S in (1, sweeps):
+                F = [u.clone() for u in init]
+                e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+                e0.record(stream)
+                lam, fits = cp.run(X, F, S, stream=stream)
+                e1.record(stream)
+                stream.synchronize()
+                t[S] = e0.elapsed_time(e1)
+        per = (t[sweeps] - t[1]) / (sweeps - 1)
+        res[tree] = (per, t[1] - per, float(fits[-1]), cp.uses_dimension_tree, cp.status())
+    xb = 4.0 * n ** 3
+    arm = {}
+    for tree, key, streams in ((True, "dimension_tree", 2), (False, "three_mttkrps", 3)):
+        per, fixed, fit, used, st = res[tree]
+        arm[key] = {"ms_per_sweep": per, "ms_per_run_fixed": fixed, "x_streams_per_sweep": streams,
+                    "final_fit": fit, "used": used, "status": st, "x_gbs": streams * xb / (per * 1e-3) / 1e9}
+    line = {"metric": "CP-ALS ms per sweep (1024^3, R 32), steady state", "unit": "ms", "higher_is_better": False,
+            "value": res[True][0], "sweeps": sweeps, "data": "synthetic",
+            "config": {"workload": "CP-ALS on X 1024^3 FP32 = rank-32 CP (N(0,1) factors) + 1e-2 noise, R 32, "
+                                   "split-BF16 MTTKRPs, FP64 solves"},
+            **arm, "speedup": res[False][0] / res[True][0]}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -539,7 +620,7 @@ def main():
                     help="profiling driver: one execute per mode of --modes at extent --n, no timing")
     ap.add_argument("--n", type=int, default=N_EXT, help="extent of each mode (--once only)")
     ap.add_argument("--modes", default="0,1,2", help="modes to run (--once only)")
-    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving", "batched", "ttmc", "paper"],
+    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving", "batched", "ttmc", "paper", "cpals"],
                     help="mttkrp: the benchmark line; serving / batched / ttmc: the other measurements")
     ap.add_argument("--requests", type=int, default=128, help="requests of the serving workload")
     ap.add_argument("--instances", type=int, default=512, help="instances of the batched workload")
@@ -554,6 +635,8 @@ def main():
         return run_ttmc(args)
     if args.workload == "paper" and args.impl == "native":
         return run_paper(args)
+    if args.workload == "cpals" and args.impl == "native":
+        return run_cpals(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -601,6 +684,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    clocks.mark_start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         ev0.record(stream)
@@ -609,6 +693,7 @@ def main():
         ev1.record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
+    clocks.mark_stop()
     if dist:
         dist.barrier()
     clk = clocks.stop()

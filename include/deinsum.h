@@ -243,6 +243,11 @@ void deinsum_batched_destroy(deinsum_batch_t b);
  * lambda; a zero column keeps lambda = 0), G_n = U_n^T U_n; after the sweep
  * fit = 1 - ||X - [[lambda; U]]|| / ||X|| from ||X||^2 + ||Xhat||^2 - 2<X, Xhat>.
  * Grams, Hadamard products, Cholesky, solves, norms and the fit are FP64.
+ *
+ * Dimension tree (order 3, SPLIT_BF16, rank <= 32, I_2 a multiple of 4, X
+ * 16-byte aligned; on by default): modes 0 and 1 of a sweep share
+ * T = X x_2 U_2 (I_0 x I_1 x rank, computed once on the tensor cores), so X is
+ * read twice per sweep instead of three times; the handle's workspace grows by T.
  */
 typedef struct deinsum_cpals_s *deinsum_cpals_t;
 
@@ -270,6 +275,11 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
 deinsum_status deinsum_cpals_workspace_bytes(deinsum_cpals_t h, size_t *bytes);
 deinsum_status deinsum_cpals_bind_workspace(deinsum_cpals_t h, void *workspace, size_t bytes,
                                             deinsum_stream_t stream);
+
+/* Enable (default) or disable the dimension tree for later runs; and whether runs
+ * use it (1 when the shape allows it and it is enabled). */
+deinsum_status deinsum_cpals_set_dimension_tree(deinsum_cpals_t h, int enable);
+int deinsum_cpals_uses_dimension_tree(deinsum_cpals_t h);
 
 /* After synchronising the stream: DEINSUM_OK, DEINSUM_ERR_TIMEOUT if an MTTKRP
  * wait gave up, DEINSUM_ERR_INVALID if a Gram-Hadamard matrix was not positive

@@ -374,6 +374,14 @@ class CPALS:
     def status(self) -> int:
         return int(load().deinsum_cpals_status(self._h))
 
+    def set_dimension_tree(self, enable: bool):
+        """Share X x_2 U_2 between modes 0 and 1 of each sweep (order 3, rank <= 32; default on)."""
+        _check(load().deinsum_cpals_set_dimension_tree(self._h, int(bool(enable))), "deinsum_cpals_set_dimension_tree")
+
+    @property
+    def uses_dimension_tree(self) -> bool:
+        return bool(load().deinsum_cpals_uses_dimension_tree(self._h))
+
     def close(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.deinsum_cpals_destroy(self._h)

@@ -13,8 +13,16 @@
 // Only the MTTKRP runs in (split) FP32; every R x R quantity, the solves, the
 // norms and the fit are FP64.  Everything stays on the device; the host only
 // enqueues kernels.
+//
+// Dimension tree (order 3, split-BF16, R <= 32, I_2 a multiple of 4): modes 0
+// and 1 share the partial contraction T = X x_2 U_2 (T[i, j, r] = sum_k X[i, j, k]
+// U_2[k, r], an I_0 x I_1 x R tensor written once by the tensor-core TTM kernel):
+//   M_0[i, r] = sum_j T[i, j, r] U_1[j, r],   M_1[j, r] = sum_i T[i, j, r] U_0[i, r],
+// the latter with U_0 already updated -- T depends only on U_2, which the sweep
+// updates last.  X is then streamed twice per sweep instead of three times.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -28,6 +36,50 @@ namespace deinsum {
 namespace {
 
 constexpr int kMaxR = 64;
+
+// Dimension tree: M_0[i, r] = sum_j T[i, j, r] U_1[j, r].  One block per i; thread
+// (r, jg) sums j = jg, jg + 4, ...; the four partial sums are added in order.
+__global__ void __launch_bounds__(128) tree_m0_kernel(const float *__restrict__ T, const float *__restrict__ U1,
+                                                      float *__restrict__ M, int64_t J, int R) {
+    const int64_t i = blockIdx.x;
+    const int r = threadIdx.x & 31, jg = threadIdx.x >> 5;
+    __shared__ float red[4][32];
+    float acc = 0.f;
+    if (r < R)
+        for (int64_t j = jg; j < J; j += 4) acc = fmaf(T[(i * J + j) * R + r], U1[j * R + r], acc);
+    red[jg][r] = acc;
+    __syncthreads();
+    if (threadIdx.x < R) M[i * R + threadIdx.x] = ((red[0][r] + red[1][r]) + red[2][r]) + red[3][r];
+}
+
+// Dimension tree: M_1[j, r] = sum_i T[i, j, r] U_0[i, r].  Block (jb, is): four j, the
+// i of slice is (kTreeSplit slices); thread (j, r) runs over them in order into
+// part[is][j][r]; tree_m1_sum adds the slices in order.
+constexpr int kTreeSplit = 8;
+__global__ void __launch_bounds__(128) tree_m1_kernel(const float *__restrict__ T, const float *__restrict__ U0,
+                                                      float *__restrict__ part, int64_t I, int64_t J, int R) {
+    const int r = threadIdx.x & 31;
+    const int64_t j = int64_t(blockIdx.x) * 4 + (threadIdx.x >> 5);
+    if (r >= R || j >= J) return;
+    const int64_t i0 = I * blockIdx.y / kTreeSplit, i1 = I * (blockIdx.y + 1) / kTreeSplit;
+    float acc = 0.f;
+    #pragma unroll 4
+    for (int64_t i = i0; i < i1; ++i) acc = fmaf(T[(i * J + j) * R + r], U0[i * R + r], acc);
+    part[(int64_t(blockIdx.y) * J + j) * R + r] = acc;
+}
+
+__global__ void tree_m1_sum(const float *__restrict__ part, float *__restrict__ M, int64_t n) {
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+        float v = 0.f;
+        for (int q = 0; q < kTreeSplit; ++q) v += part[q * n + e];
+        M[e] = v;
+    }
+}
+
+bool tree_eligible(int order, const int64_t *dims, int R, deinsum_prec prec) {
+    return order == 3 && prec == DEINSUM_PREC_SPLIT_BF16 && R <= 32 && dims[2] % 4 == 0 &&
+           dims[0] < (int64_t(1) << 31) && dims[1] < (int64_t(1) << 31) && dims[2] < (int64_t(1) << 31);
+}
 
 // G = U^T U in FP64 (U: I x R float, row-major).  One block per row r1 of G;
 // thread (r2, slice) sums rows slice, slice + 4, ... of U[i, r1] U[i, r2].
@@ -179,23 +231,39 @@ __global__ void normalize_kernel(float *__restrict__ U, int64_t I, int R, double
 }
 
 // ||X||^2 in FP64: per-block partial sums, then a single-block finish.
-__global__ void sumsq_partial_kernel(const float *__restrict__ X, int64_t n, double *__restrict__ partial) {
+// ||X||^2 partial sums: each thread takes four float4 loads per step (independent,
+// so they are in flight together), accumulates up to a few thousand squares in four
+// FP32 partials, and the block adds the threads' sums in FP64.  (||X||^2 only
+// enters the fit; FP32 partials of <= 2^13 squares keep it to ~1e-6 relative.)
+__global__ void __launch_bounds__(256) sumsq_partial_kernel(const float *__restrict__ X, int64_t n,
+                                                            double *__restrict__ partial) {
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nth = int64_t(gridDim.x) * blockDim.x;
+    const bool vec = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    const int64_t n4 = vec ? n / 4 : 0;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
     double s = 0.0;
-    {
-        float part = 0.f;
-        int cnt = 0;
-        for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-             i += int64_t(gridDim.x) * blockDim.x) {
-            const float v = X[i];
-            part = fmaf(v, v, part);
-            if (++cnt == 16) {
-                s += double(part);
-                part = 0.f;
-                cnt = 0;
-            }
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+    int steps = 0;
+    int64_t i = tid;
+    for (; i + 3 * nth < n4; i += 4 * nth) {
+        const float4 a = X4[i], b = X4[i + nth], c = X4[i + 2 * nth], d = X4[i + 3 * nth];
+        p0 = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, p0))));
+        p1 = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, p1))));
+        p2 = fmaf(c.x, c.x, fmaf(c.y, c.y, fmaf(c.z, c.z, fmaf(c.w, c.w, p2))));
+        p3 = fmaf(d.x, d.x, fmaf(d.y, d.y, fmaf(d.z, d.z, fmaf(d.w, d.w, p3))));
+        if (++steps == 512) {   // 2^13 squares per partial
+            s += (double(p0) + double(p1)) + (double(p2) + double(p3));
+            p0 = p1 = p2 = p3 = 0.f;
+            steps = 0;
         }
-        s += double(part);
     }
+    for (; i < n4; i += nth) {
+        const float4 a = X4[i];
+        p0 = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, p0))));
+    }
+    s += (double(p0) + double(p1)) + (double(p2) + double(p3));
+    for (int64_t e = 4 * n4 + tid; e < n; e += nth) s += double(X[e]) * double(X[e]);
     __shared__ double red[32];
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -273,12 +341,13 @@ __global__ void fit_kernel(const float *__restrict__ M, const float *__restrict_
 }
 
 // Direct residual ||X - Xhat||^2 with Xhat = [[lambda; U]]: X is viewed as
-// rows (all modes but the last) x K (the last mode).  A block handles tiles of
-// 64 rows x 64 k: W[row, r] = lambda_r prod_{m < N-1} U_m[i_m(row), r] and the
-// last factor's chunk are staged in shared memory (r-major), each thread forms
-// 4 x 4 reconstructed entries in FP32 (R multiply-adds each), squares the
-// residuals, sums them in FP32 over its tile and adds the tile sum to an FP64
-// per-block partial.  Accurate where the expansion of the fit cancels.
+// rows (all modes but the last) x K (the last mode).  A block takes 64-row tiles and
+// sweeps their k in chunks of 64: W[row, r] = lambda_r prod_{m < N-1} U_m[i_m(row), r]
+// (once per row tile) and the last factor's chunk are staged in shared memory
+// (r-major), each thread forms 4 x 4 reconstructed entries in FP32 (R
+// multiply-adds each), squares the residuals, sums them in FP32 over its chunk
+// and adds that sum to an FP64 per-block partial.  Accurate where the expansion
+// of the fit cancels.
 struct ResidualArgs {
     const float *X;
     const float *U[DEINSUM_MAX_ORDER];
@@ -300,8 +369,10 @@ __global__ void __launch_bounds__(256) residual_kernel(const ResidualArgs a) {
     const int t = threadIdx.x, tr = t >> 4, tk = t & 15;
     const float *C = a.U[a.order - 1];
     double block_sum = 0.0;
-    for (int64_t tile = blockIdx.x; tile < rtiles * ktiles; tile += gridDim.x) {
-        const int64_t r0 = (tile / ktiles) * 64, k0 = (tile % ktiles) * 64;
+    // a row tile's weights W[row, r] = lambda_r prod_{m < N-1} U_m[i_m(row), r] are built
+    // once (FP64 products, stored in FP32) and reused for every k tile of the row
+    for (int64_t rt = blockIdx.x; rt < rtiles; rt += gridDim.x) {
+        const int64_t r0 = rt * 64;
         __syncthreads();
         for (int e = t; e < 64 * R; e += 256) {
             const int rl = e / R, r = e % R;
@@ -319,6 +390,9 @@ __global__ void __launch_bounds__(256) residual_kernel(const ResidualArgs a) {
             }
             Ws[r][rl] = w;
         }
+        for (int64_t kt = 0; kt < ktiles; ++kt) {
+        const int64_t k0 = kt * 64;
+        __syncthreads();
         for (int e = t; e < 64 * R; e += 256) {
             const int kl = e / R, r = e % R;
             Cs[r][kl] = (k0 + kl < K) ? C[(k0 + kl) * R + r] : 0.f;
@@ -349,6 +423,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const ResidualArgs a) {
             }
         }
         block_sum += double(s);
+        }
     }
     for (int off = 16; off > 0; off >>= 1) block_sum += __shfl_down_sync(0xffffffffu, block_sum, off);
     if ((t & 31) == 0) red[t >> 5] = block_sum;
@@ -396,6 +471,15 @@ struct deinsum_cpals_s {
     double *partial = nullptr;   // kSumBlocks
     double *W = nullptr;         // R x R inverse of the Gram-Hadamard matrix
     int *status = nullptr;       // 1
+    // dimension tree (see the top of the file)
+    bool tree_ok = false;        // the shape allows it
+    bool tree_on = true;         // enabled (deinsum_cpals_set_dimension_tree)
+    float *T = nullptr;          // I_0 x I_1 x R
+    unsigned char *tb = nullptr; // split-BF16 tiles of U_2
+    CUtensorMap tmap{};
+    const void *tmap_ptr = nullptr;
+    bool tmap_ok = false;
+    uint32_t tmap_box = 0;
 };
 
 namespace {
@@ -406,12 +490,23 @@ size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // The handle's own workspace: M (max_n I_n x R float), the Grams (N x R x R
 // double), ||X||^2, the status word, the FP64 partial sums.
+size_t tree_T_bytes(const deinsum_cpals_s *h) {
+    return h->tree_ok ? round_up(size_t(h->dims[0]) * size_t(h->dims[1]) * size_t(h->R) * 4, 1024) : 0;
+}
+size_t tree_tb_bytes(const deinsum_cpals_s *h) {
+    // split tiles of U_2, then the kTreeSplit partial blocks of M_1
+    return h->tree_ok ? round_up(size_t((h->dims[2] + 63) / 64) * 2 * 32 * 64 * 2, 1024) +
+                            round_up(size_t(kTreeSplit) * size_t(h->dims[1]) * size_t(h->R) * 4, 1024)
+                      : 0;
+}
+
 size_t cpals_own_bytes(const deinsum_cpals_s *h) {
     int64_t imax = 0;
     for (int m = 0; m < h->order; ++m) imax = h->dims[m] > imax ? h->dims[m] : imax;
     const size_t bM = round_up(size_t(imax) * h->R * 4, 256);
     const size_t bG = round_up(size_t(h->order) * h->R * h->R * 8, 256);
-    return round_up(bM + bG + 256 + size_t(kSumBlocks) * 8 + size_t(h->R) * h->R * 8, 1024);
+    return round_up(bM + bG + 256 + size_t(kSumBlocks) * 8 + size_t(h->R) * h->R * 8, 1024) + tree_T_bytes(h) +
+           tree_tb_bytes(h);
 }
 
 void cpals_attach_own(deinsum_cpals_s *h, char *p, bool owned, int dev) {
@@ -428,6 +523,9 @@ void cpals_attach_own(deinsum_cpals_s *h, char *p, bool owned, int dev) {
     h->status = reinterpret_cast<int *>(h->ws + bM + bG + 8);
     h->partial = reinterpret_cast<double *>(h->ws + bM + bG + 256);
     h->W = h->partial + kSumBlocks;
+    const size_t base = round_up(bM + bG + 256 + size_t(kSumBlocks) * 8 + size_t(h->R) * h->R * 8, 1024);
+    h->T = h->tree_ok ? reinterpret_cast<float *>(h->ws + base) : nullptr;
+    h->tb = h->tree_ok ? reinterpret_cast<unsigned char *>(h->ws + base + tree_T_bytes(h)) : nullptr;
 }
 
 std::string mttkrp_spec(int order, int mode) {
@@ -463,6 +561,7 @@ deinsum_status deinsum_cpals_create(int order, const int64_t *dims, int rank, de
         if (dims[m] < 1) { delete h; return DEINSUM_ERR_SHAPE; }
         h->dims[m] = dims[m];
     }
+    h->tree_ok = tree_eligible(order, dims, rank, prec);
     for (int n = 0; n < order; ++n) {
         std::vector<int64_t> ext(dims, dims + order);
         ext.push_back(rank);
@@ -513,14 +612,56 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
     }
     if (cudaGetLastError() != cudaSuccess) return DEINSUM_ERR_CUDA;
     std::vector<const void *> ins(size_t(h->order));
+    // dimension tree for this X (its tensor map needs 16-byte aligned rows)
+    bool tree = h->tree_ok && h->tree_on;
+    if (tree && h->tmap_ptr != X) {
+        h->tmap_ptr = X;
+        h->tmap_ok = encode_ttm_last_map(X, h->dims[0], h->dims[1], h->dims[2], &h->tmap, &h->tmap_box);
+    }
+    tree = tree && h->tmap_ok;
+    TtmcArgs ta;
+    MttkrpArgs sa;
+    if (tree) {
+        std::memset(&ta, 0, sizeof(ta));
+        ta.xmap = h->tmap;
+        ta.box_bytes = h->tmap_box;
+        ttm_last_geometry(3, h->dims[0], h->dims[1], h->dims[2], R, &ta.g);
+        ta.Bsplit = h->tb;
+        ta.T2 = h->T;
+        ta.S = h->dims[0];
+        ta.n_kt = int((h->dims[1] + 127) / 128);
+        ta.n_kb = ta.g.n_kb;
+        ta.R3 = R;
+        ta.status = h->status;
+        std::memset(&sa, 0, sizeof(sa));
+        sa.g = ta.g;
+    }
+    int nsm = 0;
+    if (tree && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return DEINSUM_ERR_CUDA;
     for (int sw = 0; sw < sweeps; ++sw) {
         for (int n = 0; n < h->order; ++n) {
-            ins[0] = X;
-            int k = 1;
-            for (int m = 0; m < h->order; ++m)
-                if (m != n) ins[size_t(k++)] = factors[m];
-            deinsum_status st = deinsum_execute(h->plans[n], ins.data(), h->order, h->M, stream);
-            if (st != DEINSUM_OK) return st;
+            if (tree && n == 0) {
+                // T = X x_2 U_2 (one stream of X), then M_0 from T
+                sa.U[2] = factors[2];
+                if (launch_split_inner_factor(sa, h->tb, stream) || launch_ttm_last_tc(ta, nsm, stream))
+                    return DEINSUM_ERR_CUDA;
+                tree_m0_kernel<<<unsigned(h->dims[0]), 128, 0, s>>>(h->T, factors[1], h->M, h->dims[1], R);
+                count_launch();
+            } else if (tree && n == 1) {
+                float *part = reinterpret_cast<float *>(h->tb + round_up(size_t((h->dims[2] + 63) / 64) * 8192, 1024));
+                tree_m1_kernel<<<dim3(unsigned((h->dims[1] + 3) / 4), kTreeSplit), 128, 0, s>>>(
+                    h->T, factors[0], part, h->dims[0], h->dims[1], R);
+                const int64_t nm = h->dims[1] * R;
+                tree_m1_sum<<<unsigned(std::min<int64_t>(1024, (nm + 255) / 256)), 256, 0, s>>>(part, h->M, nm);
+                count_launch(2);
+            } else {
+                ins[0] = X;
+                int k = 1;
+                for (int m = 0; m < h->order; ++m)
+                    if (m != n) ins[size_t(k++)] = factors[m];
+                deinsum_status st = deinsum_execute(h->plans[n], ins.data(), h->order, h->M, stream);
+                if (st != DEINSUM_OK) return st;
+            }
             const int64_t I = h->dims[n];
             inverse_kernel<<<1, 256, kInvSmem, s>>>(h->grams, h->order, n, R, h->W, h->status);
             int blocks = int((I * R + 255) / 256);
@@ -593,6 +734,14 @@ deinsum_status deinsum_cpals_bind_workspace(deinsum_cpals_t h, void *workspace, 
     }
     return DEINSUM_OK;
 }
+
+deinsum_status deinsum_cpals_set_dimension_tree(deinsum_cpals_t h, int enable) {
+    if (!h) return DEINSUM_ERR_INVALID;
+    h->tree_on = enable != 0;
+    return DEINSUM_OK;
+}
+
+int deinsum_cpals_uses_dimension_tree(deinsum_cpals_t h) { return h && h->tree_ok && h->tree_on ? 1 : 0; }
 
 deinsum_status deinsum_cpals_status(deinsum_cpals_t h) {
     if (!h) return DEINSUM_ERR_INVALID;

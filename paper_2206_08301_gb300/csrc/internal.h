@@ -125,6 +125,14 @@ struct TtmcArgs {
     int *status;
 };
 int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream);
+// The same pipeline without stage 2: T[s, k, d] = sum_l X[s, k, l] U_{N-1}[l, d] written to
+// a.T2 (S x I_{N-2} x R_{N-1}); a.U2pad and a.R2 are unused (the TTM over the last mode).
+int launch_ttm_last_tc(const TtmcArgs &a, int n_sm, void *stream);
+// 3-D tensor map of X for those kernels ({I_{N-1}, I_{N-2}, S}, box {64, min(I_{N-2}, 128), 1});
+// false when X or its rows are not 16-byte aligned.
+bool encode_ttm_last_map(const void *X, int64_t S, int64_t K, int64_t L, CUtensorMap *map, uint32_t *box_bytes);
+// Their converter view of a chunk (case 0, I = K, narrow when K < 128, R_pad 32, ceil(L/64) chunks).
+void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, MttkrpGeom *g);
 int launch_ttmc_pad_factor(const float *U, int64_t rows, int R, float *out, int n_kt, void *stream);
 
 // Launch helpers implemented in the .cu files.  They return a CUDA error code

@@ -509,24 +509,7 @@ deinsum_status plan_ttmc_fused(deinsum_plan_s *pl) {
         mx = std::max(mx, sz);
     }
     pl->rest_buf_elems = mx;
-    // converter view of one raw chunk (128 k rows x 64 l): case 0, one slab per tile
-    MttkrpGeom &g = pl->geom;
-    std::memset(&g, 0, sizeof(g));
-    g.order = N;
-    g.mode = N - 2;
-    g.kcase = 0;
-    g.I = pl->dims[N - 2];
-    g.narrow = g.I < DEINSUM_BM ? 1 : 0;
-    g.G = 1;
-    g.P = S;
-    g.K_in = pl->dims[N - 1];
-    g.Q = g.K_in;
-    g.O = 1;
-    g.R = int(pl->ranks[N - 1]);
-    g.R_pad = 32;
-    g.n_kb = pl->t_nkb;
-    g.vec_ok = 1;
-    g.O_iter = 1;
+    ttm_last_geometry(N, S, pl->dims[N - 2], pl->dims[N - 1], int(pl->ranks[N - 1]), &pl->geom);
     return DEINSUM_OK;
 }
 
@@ -684,20 +667,9 @@ deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, voi
 bool encode_ttmc_map(deinsum_plan_s *pl, const void *X) {
     if (pl->xmap_ptr == X) return pl->xmap_ok != 0;
     pl->xmap_ptr = X;
-    pl->xmap_ok = 0;
-    auto enc = tensor_map_encoder();
-    if (!enc || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return false;
     const int N = pl->order;
-    const int64_t L = pl->dims[N - 1], K = pl->dims[N - 2];
-    cuuint64_t dims[3] = {cuuint64_t(L), cuuint64_t(K), cuuint64_t(pl->t_S)};
-    cuuint64_t strides[2] = {cuuint64_t(L) * 4, cuuint64_t(L * K) * 4};
-    cuuint32_t box[3] = {DEINSUM_BK, cuuint32_t(std::min<int64_t>(K, DEINSUM_BM)), 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    pl->xmap_box_bytes = uint32_t(4 * box[0] * box[1]);
-    CUresult r = enc(&pl->xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(X), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    pl->xmap_ok = (r == CUDA_SUCCESS) ? 1 : 0;
+    pl->xmap_ok = encode_ttm_last_map(X, pl->t_S, pl->dims[N - 2], pl->dims[N - 1], &pl->xmap, &pl->xmap_box_bytes)
+                      ? 1 : 0;
     return pl->xmap_ok != 0;
 }
 
@@ -783,6 +755,45 @@ deinsum_status execute_ttmc(deinsum_plan_s *pl, const void *const *inputs, void 
 }  // namespace
 
 namespace deinsum {
+
+// Converter view of one raw chunk (128 k rows x 64 l) of the last-mode TTM kernels:
+// case 0, one slab per tile, R_pad 32 (split factor tiles of U_{N-1}).
+void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, MttkrpGeom *g) {
+    std::memset(g, 0, sizeof(*g));
+    g->order = order;
+    g->mode = order - 2;
+    g->kcase = 0;
+    g->I = K;
+    g->narrow = K < DEINSUM_BM ? 1 : 0;
+    g->G = 1;
+    g->P = S;
+    g->K_in = L;
+    g->Q = L;
+    g->O = 1;
+    g->R = R;
+    g->R_pad = 32;
+    g->n_kb = int((L + DEINSUM_BK - 1) / DEINSUM_BK);
+    g->vec_ok = 1;
+    g->O_iter = 1;
+}
+
+// 3-D tensor map of X viewed as S slabs x K rows x L (the last mode contiguous):
+// dims {L, K, S}, box {64, min(K, 128), 1}.
+bool encode_ttm_last_map(const void *X, int64_t S, int64_t K, int64_t L, CUtensorMap *map, uint32_t *box_bytes) {
+    auto enc = tensor_map_encoder();
+    const int64_t lim = int64_t(1) << 31;
+    if (!enc || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || L % 4 != 0 || S >= lim || K >= lim || L >= lim)
+        return false;
+    cuuint64_t dims[3] = {cuuint64_t(L), cuuint64_t(K), cuuint64_t(S)};
+    cuuint64_t strides[2] = {cuuint64_t(L) * 4, cuuint64_t(L * K) * 4};
+    cuuint32_t box[3] = {DEINSUM_BK, cuuint32_t(std::min<int64_t>(K, DEINSUM_BM)), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    *box_bytes = uint32_t(4 * box[0] * box[1]);
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(X), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 // Mode of X that einsum operand k (k >= 1) is contracted with.
 int deinsum_internal_operand_mode(deinsum_plan_t pl, int k) { return pl->operand_mode[k]; }

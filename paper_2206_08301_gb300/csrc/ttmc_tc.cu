@@ -90,6 +90,9 @@ __device__ __forceinline__ float4 *t1_slot(float *t1s, int r, int x) {
     return reinterpret_cast<float4 *>(t1s + r * TtmcCfg::RP) + (x ^ (r & 7));
 }
 
+// STORE: the epilogue writes the T1 tiles to HBM (a.T2 as S x I_{N-2} x R_{N-1}:
+// the TTM over the last mode alone) instead of running stage 2.
+template <bool STORE>
 __global__ void __launch_bounds__(TtmcCfg::THREADS, 1)
 ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     using C = TtmcCfg;
@@ -255,6 +258,58 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             mbar_wait(drain, 0, abort_flag, status);
         }
         __syncwarp();
+    } else if constexpr (STORE) {
+        // ------------------------------------------- epilogue: T1 tiles to HBM
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        TIter it;
+        it.init(a.S);
+        const int64_t nfg = (it.s1 - it.s) * a.n_kt;
+        int64_t s = it.s;
+        int kt = 0;
+        const bool vec = (a.R3 & 3) == 0;
+        for (int64_t fgi = 0; fgi < nfg; ++fgi) {
+            const int b = int(fgi & 1);
+            const uint32_t jb = uint32_t(fgi >> 1);
+            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) break;
+            tc_fence_after();
+            const int64_t k = int64_t(kt) * BM + row;
+            const bool valid = k < a.g.I;
+            float *dst = a.T2 + (s * a.g.I + k) * a.R3;
+            const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
+            #pragma unroll
+            for (int c0 = 0; c0 < RP; c0 += 16) {
+                uint32_t hi[16], lo[16];
+                tmem_ld16(taddr + uint32_t(c0), hi);
+                tmem_ld16(taddr + uint32_t(RP + c0), lo);
+                tmem_wait_ld();
+                if (valid) {
+                    #pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        const int d = c0 + 4 * x;
+                        const float4 v4 = make_float4(__uint_as_float(hi[4 * x]) + __uint_as_float(lo[4 * x]),
+                                                      __uint_as_float(hi[4 * x + 1]) + __uint_as_float(lo[4 * x + 1]),
+                                                      __uint_as_float(hi[4 * x + 2]) + __uint_as_float(lo[4 * x + 2]),
+                                                      __uint_as_float(hi[4 * x + 3]) + __uint_as_float(lo[4 * x + 3]));
+                        if (vec) {
+                            if (d < a.R3) *reinterpret_cast<float4 *>(dst + d) = v4;
+                        } else {
+                            if (d < a.R3) dst[d] = v4.x;
+                            if (d + 1 < a.R3) dst[d + 1] = v4.y;
+                            if (d + 2 < a.R3) dst[d + 2] = v4.z;
+                            if (d + 3 < a.R3) dst[d + 3] = v4.w;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce(b));
+            if (++kt == a.n_kt) {
+                kt = 0;
+                ++s;
+            }
+        }
     } else {
         // ------------------------------------------------- epilogue (stage 2)
         const int quad = warp & 3;                 // TMEM lanes (= tile rows) 32*quad .. 32*quad+31
@@ -422,16 +477,23 @@ __global__ void pad_factor_kernel(const float *__restrict__ U, int64_t rows, int
 
 }  // namespace
 
-int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream) {
+namespace {
+template <bool STORE>
+int launch_ttmc_variant(const TtmcArgs &a, int n_sm, void *stream) {
     using C = TtmcCfg;
-    cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
+    cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel<STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(C::SMEM));
     if (e != cudaSuccess) return int(e);
     int64_t grid = a.S < n_sm ? a.S : n_sm;
     if (grid < 1) grid = 1;
-    ttmc_fused_kernel<<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
+    ttmc_fused_kernel<STORE><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
     count_launch();
     return int(cudaGetLastError());
 }
+}  // namespace
+
+int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream) { return launch_ttmc_variant<false>(a, n_sm, stream); }
+int launch_ttm_last_tc(const TtmcArgs &a, int n_sm, void *stream) { return launch_ttmc_variant<true>(a, n_sm, stream); }
 
 int launch_ttmc_pad_factor(const float *U, int64_t rows, int R, float *out, int n_kt, void *stream) {
     const int64_t total = int64_t(n_kt) * BM * TtmcCfg::RP;

@@ -95,3 +95,38 @@ def test_cpals_order4_and_rank64():
     lam, fits = dz.CPALS(dims, rank, "split_bf16").run(torch.from_numpy(X).cuda(), F, 1)
     ref_f, ref_lam, ref_fits = oracle.cpals(X, [u.astype(np.float64) for u in init], 1)
     assert abs(float(fits[0]) - ref_fits[0]) <= 1e-4
+
+
+@pytest.mark.parametrize("dims,rank", [((40, 50, 36), 6), ((130, 140, 72), 32), ((90, 30, 200), 17)])
+def test_cpals_dimension_tree_per_step_parity(dims, rank):
+    """Order 3, rank <= 32: modes 0 and 1 share T = X x_2 U_2 (one tensor-core pass).  Every
+    sweep matches the FP64 reference from the same start, with the tree on and off."""
+    X, init = _problem(11, dims, rank, 1e-2)
+    Xd = torch.from_numpy(X).cuda()
+    results = {}
+    for tree in (True, False):
+        F = [torch.from_numpy(u).cuda() for u in init]
+        cp = dz.CPALS(dims, rank, "split_bf16")
+        cp.set_dimension_tree(tree)
+        assert cp.uses_dimension_tree == tree
+        for sweep in range(3):
+            before = [f.cpu().numpy().astype(np.float64) for f in F]
+            lam, fits = cp.run(Xd, F, 1)
+            torch.cuda.synchronize()
+            assert cp.status() == 0
+            ref_f, ref_lam, ref_fits = oracle.cpals(X, before, 1)
+            for m in range(3):
+                err = oracle.rel_error(F[m].cpu().numpy(), ref_f[m])
+                assert err <= 1e-4, f"tree {tree} sweep {sweep} factor {m}: {err:.2e}"
+            assert abs(float(fits[0]) - ref_fits[0]) <= 1e-4
+        results[tree] = [f.cpu().numpy().astype(np.float64) for f in F]
+    for m in range(3):
+        assert oracle.rel_error(results[True][m], results[False][m]) <= 1e-4
+
+
+def test_cpals_dimension_tree_only_where_it_applies():
+    assert dz.CPALS((40, 50, 36), 8, "split_bf16").uses_dimension_tree
+    assert not dz.CPALS((40, 50, 30), 8, "split_bf16").uses_dimension_tree     # I_2 % 4 != 0
+    assert not dz.CPALS((40, 50, 36), 40, "split_bf16").uses_dimension_tree    # rank > 32
+    assert not dz.CPALS((40, 50, 36), 8, "plain").uses_dimension_tree
+    assert not dz.CPALS((20, 24, 18, 22), 8, "split_bf16").uses_dimension_tree  # order 4
