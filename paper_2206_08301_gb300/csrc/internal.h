@@ -9,8 +9,8 @@
 //     n+1..N-2 ("outer" modes).  Rows are grouped 128 to a tile: one p and 128
 //     consecutive i_n when I_n >= 128 ("wide"), else G = min(floor(128/I_n), 32)
 //     consecutive p with all I_n rows each ("narrow").  On the tensor-core path,
-//     when there is no p to pack (P = 1), the G groups run over consecutive outer
-//     indices o instead ("opack"; also in case 1 with I_n < 128).
+//     when there is no p to pack (P = 1) and I_n <= 64, the G groups run over
+//     consecutive outer indices o instead ("opack"; also in case 1 with I_n <= 64).
 //   case 1 (n = N-1, "M-contiguous"): a row is one i_n; its elements run over
 //     p = (o, k) with k indexing mode N-2 (inner) and o modes 0..N-3 (outer);
 //     consecutive rows are adjacent in memory.
@@ -65,8 +65,8 @@ struct MttkrpGeom {
     int64_t tiles_per_col;
     int64_t fg_per_col;   // tiles_per_col * O_iter
     int64_t rows_per_col; // min(I, 128)
-    int opack;            // tensor-core path, I < 128 and no p to pack (case 0 with P = 1, or
-                          // case 1): tile rows are (o_local, i_n), G consecutive outer indices
+    int opack;            // tensor-core path, I <= 64 and no p to pack (case 0 with P = 1, or
+                          // case 1): tile rows are (o_local, i_n), G >= 2 consecutive outer indices
     int64_t O_iter;       // outer indices iterated per tile: O, or 1 with opack (folded into the tile)
 };
 

@@ -114,8 +114,8 @@ __device__ __forceinline__ void conv_read_global(const MttkrpArgs &a, const Iter
             const int l = rsub + 16 * j;
             float e[4] = {0.f, 0.f, 0.f, 0.f};
             if (opack_row_valid(g, it.tile, l)) {
-                const int gq = int(l / g.I);
-                const int64_t i = l - gq * g.I;
+                const int gq = l / int(g.I);
+                const int64_t i = l - gq * int(g.I);
                 const float *pr = X + i * g.Q + (it.tile * g.G + gq) * g.K_in + kpos;
                 #pragma unroll
                 for (int q = 0; q < 4; ++q)
@@ -127,8 +127,8 @@ __device__ __forceinline__ void conv_read_global(const MttkrpArgs &a, const Iter
         // case 1, row l = gq * I_n + i: X[o0 + gq, k, i]
         const int row = pt & (BM - 1), kh = pt >> 7;
         const bool rv = opack_row_valid(g, it.tile, row);
-        const int gq = int(row / g.I);
-        const int64_t i = row - gq * g.I;
+        const int gq = row / int(g.I);
+        const int64_t i = row - gq * int(g.I);
         const int64_t kbase = k0 + 32 * kh;
         const float *base = X + ((it.tile * g.G + gq) * g.K_in + kbase) * g.I + i;
         #pragma unroll
@@ -171,6 +171,42 @@ __device__ __forceinline__ void conv_read_global(const MttkrpArgs &a, const Iter
             }
             v[j] = make_float4(e[0], e[1], e[2], e[3]);
         }
+    }
+}
+
+// Case 1 from global memory for the MN-major operand (the thread layout of
+// conv_read_smem_mn): row m of the tile is i_n = col * 128 + m at outer index o,
+// or with opack i_n = m - gq I_n at outer index tile * G + gq; X[o, k, i_n].
+template <bool OPACK>
+__device__ __forceinline__ void conv_read_global_mn(const MttkrpArgs &a, const Iter &it, int pt, float4 (&v)[8]) {
+    const MttkrpGeom &g = a.g;
+    const float *X = static_cast<const float *>(a.X);
+    const int64_t kbase = int64_t(it.kb) * BK + 8 * (pt >> 5);
+    const float *src[4];
+    bool rv[4];
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int m = 4 * (pt & 31) + q;
+        int64_t o, i;
+        if (OPACK) {
+            const int gq = m / int(g.I);
+            i = m - gq * int(g.I);
+            o = it.tile * g.G + gq;
+            rv[q] = opack_row_valid(g, it.tile, m);
+        } else {
+            i = it.col * BM + m;
+            o = it.o;
+            rv[q] = i < g.I;
+        }
+        src[q] = X + (o * g.K_in + kbase) * g.I + i;
+    }
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool kv = kbase + j < g.K_in;
+        float e[4];
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = (kv && rv[q]) ? __ldg(src[q] + int64_t(j) * g.I) : 0.f;
+        v[j] = make_float4(e[0], e[1], e[2], e[3]);
     }
 }
 
@@ -268,7 +304,7 @@ __device__ __forceinline__ void load_fg_weights(const MttkrpArgs &a, int64_t til
     if (nl) bulk_g2s(dst + rowb, a.Lw + p0 * g.R_pad, nl * rowb, bar);
 }
 
-template <int RP, bool OP>
+template <int RP, bool OP, bool MN>
 __global__ void __launch_bounds__(TcCfg<RP>::THREADS, 1)
 mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     using C = TcCfg<RP>;
@@ -339,6 +375,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         const char *bsrc = static_cast<const char *>(a.Bsplit);
         Iter it;
         it.init(a);
+        const MnPos mp = mn_pos(a.raw_pitch > 0 ? a.raw_pitch : BM, OP ? int(g.G) : 1, pt);
         uint32_t bpar = 0, bused = 0;  // per operand stage: parity of the last B copy, copy issued
         for (int64_t chunk = 0; !it.done; ++chunk) {
             float4 v[8];
@@ -346,7 +383,17 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             if (a.use_tma) {
                 const uint32_t rj = uint32_t(chunk / RS);
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, a.status))) break;
-                conv_read_smem_t<OP>(a.g, a.raw_pitch, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
+                const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES);
+                if (MN) conv_read_smem_mn(mp, a.raw_pitch, raw, pt, v);
+                else conv_read_smem_t<OP>(a.g, a.raw_pitch, raw, pt, v);
+                // hand the raw stage back to the TMA warp before the split, so that its next
+                // load overlaps it: the proxy fence orders these generic reads before that
+                // async-proxy write (an mbarrier release alone does not)
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(raw_empty(rs));
+            } else if (MN) {
+                conv_read_global_mn<OP>(a, it, pt, v);
             } else {
                 conv_read_global<OP>(a, it, pt, v);
             }
@@ -359,16 +406,12 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
                 bused |= 1u << as;
             }
-            conv_store(g, pt, a_hi(as), a_lo(as), v);
-            // the proxy fence orders this thread's generic smem accesses (the A
-            // stores, and the raw-tile reads whose values were just consumed)
-            // before the tensor-core reads and the next TMA write of the stages
+            if (MN) conv_store_mn(pt, a_hi(as), a_lo(as), v);
+            else conv_store(g, pt, a_hi(as), a_lo(as), v);
+            // the proxy fence orders this thread's A stores before the tensor-core reads
             fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(a_full(as));
-                if (a.use_tma) mbar_arrive(raw_empty(rs));
-            }
+            if (lane == 0) mbar_arrive(a_full(as));
             it.next(a);
         }
         if (issuer) {  // every bulk copy into this CTA's smem has landed before exit
@@ -424,7 +467,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     } else if (warp == C::MMA_WARP) {
         // -------------------------------------------------------------- MMA issue
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(BM, C::N);
+            constexpr uint32_t idesc = idesc_bf16_f32(BM, C::N) | (MN ? kIdescAMnMajor : 0u);
             int64_t chunk = 0, nfg = 0;
             {   // count the fiber groups of this CTA
                 Iter it;
@@ -448,14 +491,18 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     if (!mbar_wait(a_full(s), j & 1u, abort_flag, a.status) ||
                         !mbar_wait(bfull(s), j & 1u, abort_flag, a.status)) { ok = false; break; }
                     tc_fence_after();
-                    const uint64_t dh = desc_kmajor_sw128(a_hi(s));
-                    const uint64_t dl = desc_kmajor_sw128(a_lo(s));
+                    const uint64_t dh = MN ? desc_mnmajor_sw128(a_hi(s), kMnAtomStride, kMnKGroupStride)
+                                           : desc_kmajor_sw128(a_hi(s));
+                    const uint64_t dl = MN ? desc_mnmajor_sw128(a_lo(s), kMnAtomStride, kMnKGroupStride)
+                                           : desc_kmajor_sw128(a_lo(s));
                     const uint64_t db = desc_kmajor_sw128(b_t(s));
                     #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t adv = uint64_t(kk * 32) >> 4;  // 32 bytes per K=16 step
-                        mma_bf16(dcol, dh + adv, db + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                        mma_bf16(dcol, dl + adv, db + adv, idesc, 1u);
+                        // K = 16 per step: 32 bytes along a K-major row, two 8-k groups of an MN-major tile
+                        const uint64_t adv = uint64_t(kk * 32) >> 4;
+                        const uint64_t adv_a = MN ? uint64_t(kk * 2 * kMnKGroupStride) >> 4 : adv;
+                        mma_bf16(dcol, dh + adv_a, db + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(dcol, dl + adv_a, db + adv, idesc, 1u);
                     }
                     mma_commit(a_empty(s));
                     ++chunk;
@@ -594,22 +641,27 @@ __global__ void split_inner_factor_kernel(const float *__restrict__ U, unsigned 
     }
 }
 
-template <int RP, bool OP>
+template <int RP, bool OP, bool MN>
 int launch_tc_rp_op(const MttkrpArgs &a, int n_sm, void *stream) {
     using C = TcCfg<RP>;
-    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_kernel<RP, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_kernel<RP, OP, MN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(C::SMEM));
     if (e != cudaSuccess) return int(e);
     int64_t grid = a.n_units < n_sm ? a.n_units : n_sm;
     if (grid < 1) grid = 1;
-    mttkrp_tc_kernel<RP, OP><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
+    mttkrp_tc_kernel<RP, OP, MN><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
     count_launch();
     return int(cudaGetLastError());
 }
 
+// case 1 (rows contiguous in memory) takes the MN-major A operand
 template <int RP>
 int launch_tc_rp(const MttkrpArgs &a, int n_sm, void *stream) {
-    return a.g.opack ? launch_tc_rp_op<RP, true>(a, n_sm, stream) : launch_tc_rp_op<RP, false>(a, n_sm, stream);
+    if (a.g.kcase == 1)
+        return a.g.opack ? launch_tc_rp_op<RP, true, true>(a, n_sm, stream)
+                         : launch_tc_rp_op<RP, false, true>(a, n_sm, stream);
+    return a.g.opack ? launch_tc_rp_op<RP, true, false>(a, n_sm, stream)
+                     : launch_tc_rp_op<RP, false, false>(a, n_sm, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -750,6 +802,9 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 ++tchunk;
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
                 conv_read_smem(a, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
+                fence_proxy_async_smem();   // these generic reads before the stage's next TMA write
+                __syncwarp();
+                if (lane == 0) mbar_arrive(raw_empty(rs));
             } else {
                 if (a.g.opack) conv_read_global<true>(a, it.as_iter(), pt, v);
                 else conv_read_global<false>(a, it.as_iter(), pt, v);
@@ -767,10 +822,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             conv_store(a.g, pt, a_hi(as), a_lo(as), v);
             fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(a_full(as));
-                if (a.use_tma) mbar_arrive(raw_empty(rs));
-            }
+            if (lane == 0) mbar_arrive(a_full(as));
             it.next();
         }
         if (issuer) {

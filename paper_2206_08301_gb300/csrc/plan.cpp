@@ -213,11 +213,12 @@ void build_mttkrp_geometry(deinsum_plan_s *pl) {
     g.n_kb = int((g.K_in + DEINSUM_BK - 1) / DEINSUM_BK);
     g.O_iter = g.O;
     g.opack = 0;
-    // Tensor-core path with short rows (I_n < 128) and no leading index to pack into a
-    // tile (case 0 with P = 1, or case 1): pack G consecutive outer indices instead,
+    // Tensor-core path with short rows (I_n <= 64) and no leading index to pack into a
+    // tile (case 0 with P = 1, or case 1): pack G >= 2 consecutive outer indices instead,
     // tile row g*I_n + i_n (the partial rows of the G groups are summed by the reduction
-    // like the narrow p groups).
-    if (pl->prec == DEINSUM_PREC_SPLIT_BF16 && pl->dtype == DEINSUM_F32 && g.I < DEINSUM_BM && g.O > 1 &&
+    // like the narrow p groups).  With 64 < I_n < 128 a tile holds one group anyway and
+    // packing would only add index arithmetic.
+    if (pl->prec == DEINSUM_PREC_SPLIT_BF16 && pl->dtype == DEINSUM_F32 && 2 * g.I <= DEINSUM_BM && g.O > 1 &&
         (g.kcase == 1 || g.P == 1)) {
         g.opack = 1;
         g.narrow = 1;

@@ -153,6 +153,24 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor, MN-major operand in the 128-byte swizzle
+// layout: atoms of 64 MN elements (128 B) x 8 k (k-rows 128 B apart, 16-byte
+// chunk c of k-row r stored at chunk c ^ (r % 8)); the leading-byte offset is
+// the stride between atoms along MN, the stride-byte offset the stride between
+// groups of 8 k.
+__device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr & 0x3FFFF) >> 4);       // start address >> 4, bits 0-13
+    d |= uint64_t((lbo >> 4) & 0x3FFF) << 16;    // leading byte offset, bits 16-29
+    d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;    // stride byte offset, bits 32-45
+    d |= uint64_t(1) << 46;                      // descriptor version, bits 46-47
+    d |= uint64_t(2) << 61;                      // layout: 128-byte swizzle, bits 61-63
+    return d;
+}
+
+// Instruction-descriptor bit selecting an MN-major A operand (bit 15, "transpose A").
+constexpr uint32_t kIdescAMnMajor = 1u << 15;
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
 // both operands K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
@@ -212,6 +230,16 @@ __device__ __forceinline__ void sts64(uint32_t addr, uint32_t a, uint32_t b) {
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
+
+// Byte offset of element (m, k) of an MN-major 128B-swizzled bf16 operand tile of
+// 128 rows x 64 k: atom (k / 8, m / 64) at byte (2 (k / 8) + m / 64) * 1024, so the
+// MN atom stride is 1024 B and the stride between groups of 8 k is 2048 B.
+__host__ __device__ __forceinline__ uint32_t sw128_mn_offset(uint32_t m, uint32_t k) {
+    return ((k >> 3) * 2u + (m >> 6)) * 1024u + (k & 7u) * 128u + (((((m & 63u) >> 3) ^ (k & 7u)) & 7u) << 4) +
+           (m & 7u) * 2u;
+}
+constexpr uint32_t kMnAtomStride = 1024;   // between the two 64-row halves
+constexpr uint32_t kMnKGroupStride = 2048; // between groups of 8 k
 
 // Byte offset of element (row, k) of a K-major 128B-swizzled bf16 operand tile
 // (64 k per row): atoms of 8 rows x 128 B.

@@ -28,9 +28,10 @@ constexpr int EPI_WARPS = 4;
 __device__ __forceinline__ int64_t tile_rowbase(const MttkrpGeom &g, int64_t col, int64_t t) {
     return g.narrow ? t * g.G * g.I : t * g.I + col * BM;
 }
-// opack tiles: row l = g * I_n + i_n of tile t holds outer index t*G + g.
+// opack tiles: row l = g * I_n + i_n of tile t holds outer index t*G + g (I_n <= 64,
+// so the division is a 32-bit one).
 __device__ __forceinline__ bool opack_row_valid(const MttkrpGeom &g, int64_t t, int l) {
-    return l < g.G * g.I && t * g.G + l / g.I < g.O;
+    return l < int(g.G * g.I) && t * g.G + l / int(g.I) < g.O;
 }
 __device__ __forceinline__ bool row_valid(const MttkrpGeom &g, int64_t col, int64_t rowbase, int l) {
     if (g.kcase == 1) return col * BM + l < g.I;
@@ -94,6 +95,67 @@ __device__ __forceinline__ void conv_read_smem(const MttkrpGeom &g, int pitch, c
 }
 __device__ __forceinline__ void conv_read_smem(const MttkrpArgs &a, const float *raw, int pt, float4 (&v)[8]) {
     conv_read_smem(a.g, a.raw_pitch, raw, pt, v);
+}
+
+// ---------------------------------------------------------------------------
+// Case 1 with an MN-major A operand: the raw tile already runs along the tile
+// rows for a fixed k, so the converters keep that order (no transpose).  The
+// raw tile holds G groups (G = 1 without opack) of `pitch` rows: row
+// m = gq * pitch + i at raw[gq * 64 * pitch + k * pitch + i]; rows past the
+// groups read as zero.  Thread pt (warp w = pt / 32, lane) holds k = 8 w + j
+// (j < 8) of rows 4 lane .. 4 lane + 3.  Its positions are fixed for a launch.
+// ---------------------------------------------------------------------------
+struct MnPos {
+    int off[4];      // raw offsets of the four rows at k = 0
+    uint32_t valid;  // bit q: row 4 lane + q is inside the groups
+    bool vec;        // pitch % 4 == 0: the four rows are one aligned float4
+};
+__device__ __forceinline__ MnPos mn_pos(int pitch, int groups, int pt) {
+    MnPos p;
+    p.valid = 0;
+    p.vec = (pitch & 3) == 0;
+    const int m0 = 4 * (pt & 31);
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int m = m0 + q, gq = m / pitch, i = m - gq * pitch;
+        p.off[q] = gq * BK * pitch + i;
+        if (gq < groups) p.valid |= 1u << q;
+    }
+    return p;
+}
+__device__ __forceinline__ void conv_read_smem_mn(const MnPos &p, int pitch, const float *raw, int pt,
+                                                  float4 (&v)[8]) {
+    const int kb0 = 8 * (pt >> 5);
+    if (p.vec) {
+        const bool rv = p.valid != 0;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j)
+            v[j] = rv ? *reinterpret_cast<const float4 *>(raw + p.off[0] + (kb0 + j) * pitch)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float e[4];
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) e[q] = ((p.valid >> q) & 1u) ? raw[p.off[q] + (kb0 + j) * pitch] : 0.f;
+            v[j] = make_float4(e[0], e[1], e[2], e[3]);
+        }
+    }
+}
+// Split and store: lanes 0-15 fill one 128-byte k-row of the first 64-row atom,
+// lanes 16-31 the same k-row of the second (two wavefronts per 8-byte store).
+__device__ __forceinline__ void conv_store_mn(int pt, uint32_t a_hi, uint32_t a_lo, const float4 (&v)[8]) {
+    const int kb0 = 8 * (pt >> 5);
+    const uint32_t m0 = uint32_t(4 * (pt & 31));
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t off = sw128_mn_offset(m0, uint32_t(kb0 + j));
+        uint32_t h0, l0, h1, l1;
+        split2(v[j].x, v[j].y, h0, l0);
+        split2(v[j].z, v[j].w, h1, l1);
+        sts64(a_hi + off, h0, h1);
+        sts64(a_lo + off, l0, l1);
+    }
 }
 
 // Split and store the thread's 32 values into the stage's A_hi / A_lo tiles.

@@ -173,6 +173,12 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             const uint32_t rj = uint32_t(chunk / RS);
             if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
             conv_read_smem_t<false>(a.g, BM, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
+            // hand the raw stage back to the TMA warp before the split, so that its next
+            // load overlaps it: the proxy fence orders these generic reads before that
+            // async-proxy write (an mbarrier release alone does not)
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(raw_empty(rs));
             const int as = int(chunk % AS);
             const uint32_t aj = uint32_t(chunk / AS);
             if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status))) break;
@@ -183,12 +189,9 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 bused |= 1u << as;
             }
             conv_store(a.g, pt, a_hi(as), a_lo(as), v);
-            fence_proxy_async_smem();
+            fence_proxy_async_smem();   // the A stores before the tensor-core reads
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(a_full(as));
-                mbar_arrive(raw_empty(rs));
-            }
+            if (lane == 0) mbar_arrive(a_full(as));
             it.next(a.n_kb, a.n_kt);
         }
         if (issuer) {  // every bulk copy into this CTA's smem has landed before exit

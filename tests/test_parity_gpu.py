@@ -64,6 +64,13 @@ SMALL_CASES = [
     ((1, 50, 70, 60), 16),     # mode 1 with P = 1 and an L row common to the tile
     ((50, 70, 61), 32),        # K_in % 4 != 0 (no TMA, bounds-checked loads) with packing in mode 0
     ((30, 40, 51), 64),        # last mode I = 51 (no TMA in mode 2) with packing; rank 64
+    # order 2, last mode shorter than a tile and no outer index to pack: the raw tile is
+    # pitch I wide and rows past I read as zero (TMA for I = 100, loads for I = 90)
+    ((300, 100), 32),
+    ((260, 90), 16),
+    # mode 2: 64 < I = 100 < 128 with outer indices (one group per tile, not packed, TMA);
+    # mode 0: I = 20 with P = 1 (G = 6 outer indices packed per tile)
+    ((20, 30, 100), 16),
 ]
 
 
