@@ -193,11 +193,22 @@ def cpu_oracle_sample(seed, budget_s: float):
 
 def run_once(args):
     """One execute per requested mode (for ncu captures of a small case); prints 'ok'.
-    With --workload ttmc: one split-BF16 TTMc ijkl,jb,kc,ld->ibcd at X n x n x 256 x 256, R = 32."""
+    With --workload ttmc: one split-BF16 TTMc ijkl,jb,kc,ld->ibcd at X n x n x 256 x 256, R = 32.
+    With --workload paper: the order-5 TTMc of the paper's shapes (mode 0 kept, R = 24) at
+    X n x 60^4."""
     import torch
     import paper_2206_08301_gb300 as dz
     from paper_2206_08301_gb300 import inputs
     n = args.n
+    if args.workload == "paper":
+        dims, R = (n, 60, 60, 60, 60), 24
+        X = dz.gen_uniform(1301, inputs.STREAM_X, dims)
+        U = [None] + [torch.from_numpy(inputs.factor_normal(1301, m, dims[m], R).astype(np.float32)).cuda()
+                      for m in range(1, 5)]
+        dz.ttmc(X, U, 0, prec=args.prec)
+        torch.cuda.synchronize()
+        print("ok")
+        return 0
     if args.workload == "ttmc":
         dims = (n, n, 256, 256)
         X = dz.gen_uniform(4096, inputs.STREAM_X, dims)

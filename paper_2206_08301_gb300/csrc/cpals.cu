@@ -632,6 +632,7 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
         ta.n_kt = int((h->dims[1] + 127) / 128);
         ta.n_kb = ta.g.n_kb;
         ta.R3 = R;
+        ta.sg = 1;
         ta.status = h->status;
         std::memset(&sa, 0, sizeof(sa));
         sa.g = ta.g;

@@ -111,10 +111,12 @@ size_t mttkrp_tc_batched_smem_bytes();
 // for every slab s (flat index over modes 0..N-3), k over I_{N-2}, l over
 // I_{N-1}.  The contraction over l runs on the tensor cores (split BF16, 128 k
 // at a time), the one over k on CUDA cores in FP32; T1 = X U_{N-1} stays on chip.
+// Short slabs share a 128-row tile: sg = 2 (I_{N-2} <= 64) or 4 (<= 32) slabs at a
+// row pitch of 128 / sg, the rows past I_{N-2} zero-filled by the TMA.
 struct TtmcArgs {
-    CUtensorMap xmap;     // 3-D {I_{N-1}, I_{N-2}, S}, box {64, min(I_{N-2}, 128), 1}
+    CUtensorMap xmap;     // 3-D {I_{N-1}, I_{N-2}, S}, box {64, min(I_{N-2}, 128), 1}; sg > 1: {64, 128/sg, sg}
     uint32_t box_bytes;
-    MttkrpGeom g;         // converter view of a chunk: case 0, I = I_{N-2}, narrow = I < 128, G = 1
+    MttkrpGeom g;         // converter view of a chunk: case 0, I = I_{N-2}, narrow = I < 128 (sg = 1), G = 1
     const void *Bsplit;   // split-BF16 tiles of U_{N-1} (R_pad 32, n_kb tiles)
     const float *U2pad;   // U_{N-2} as n_kt*128 rows x 32 FP32, zero beyond I_{N-2} x R_{N-2}
     float *T2;            // S x R_{N-2} x R_{N-1}, row-major
@@ -122,17 +124,22 @@ struct TtmcArgs {
     int n_kt;             // tiles of 128 along k
     int n_kb;             // chunks of 64 along l
     int R2, R3;           // R_{N-2}, R_{N-1} (<= 32)
+    int sg;               // slabs per tile (1, 2 or 4; n_kt = 1 when sg > 1)
     int *status;
 };
+// Slabs per tile of the fused kernel for I_{N-2} = K.
+inline int ttmc_slab_group(int64_t K) { return K <= 32 ? 4 : (K <= 64 ? 2 : 1); }
 int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream);
 // The same pipeline without stage 2: T[s, k, d] = sum_l X[s, k, l] U_{N-1}[l, d] written to
-// a.T2 (S x I_{N-2} x R_{N-1}); a.U2pad and a.R2 are unused (the TTM over the last mode).
+// a.T2 (S x I_{N-2} x R_{N-1}); a.U2pad and a.R2 are unused (the TTM over the last mode; sg = 1).
 int launch_ttm_last_tc(const TtmcArgs &a, int n_sm, void *stream);
-// 3-D tensor map of X for those kernels ({I_{N-1}, I_{N-2}, S}, box {64, min(I_{N-2}, 128), 1});
-// false when X or its rows are not 16-byte aligned.
-bool encode_ttm_last_map(const void *X, int64_t S, int64_t K, int64_t L, CUtensorMap *map, uint32_t *box_bytes);
-// Their converter view of a chunk (case 0, I = K, narrow when K < 128, R_pad 32, ceil(L/64) chunks).
-void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, MttkrpGeom *g);
+// 3-D tensor map of X for those kernels ({I_{N-1}, I_{N-2}, S}, box {64, min(I_{N-2}, 128), 1},
+// or {64, 128/sg, sg} for sg > 1); false when X or its rows are not 16-byte aligned.
+bool encode_ttm_last_map(const void *X, int64_t S, int64_t K, int64_t L, CUtensorMap *map, uint32_t *box_bytes,
+                         int sg = 1);
+// Their converter view of a chunk (case 0, I = K, narrow when K < 128 and sg = 1 -- with sg > 1
+// the box fills all 128 rows --, R_pad 32, ceil(L/64) chunks).
+void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, MttkrpGeom *g, int sg = 1);
 int launch_ttmc_pad_factor(const float *U, int64_t rows, int R, float *out, int n_kt, void *stream);
 
 // Launch helpers implemented in the .cu files.  They return a CUDA error code

@@ -53,6 +53,7 @@ struct deinsum_plan_s {
     int64_t rest_buf_elems = 0;    // largest intermediate of the remaining chain
     int64_t t_S = 0;               // slabs
     int t_nkt = 0, t_nkb = 0;
+    int t_sg = 1;                  // slabs per tile of the fused kernel
 
     // device state (after the first execute)
     int device = -1;
@@ -494,6 +495,7 @@ deinsum_status plan_ttmc_fused(deinsum_plan_s *pl) {
     if (S >= lim || pl->dims[N - 2] >= lim || pl->dims[N - 1] >= lim) return DEINSUM_ERR_UNSUPPORTED;
     pl->ttmc_fused = true;
     pl->t_S = S;
+    pl->t_sg = ttmc_slab_group(pl->dims[N - 2]);
     pl->t_nkt = int((pl->dims[N - 2] + DEINSUM_BM - 1) / DEINSUM_BM);
     pl->t_nkb = int((pl->dims[N - 1] + DEINSUM_BK - 1) / DEINSUM_BK);
     pl->t2_elems = S * pl->ranks[N - 2] * pl->ranks[N - 1];
@@ -510,7 +512,7 @@ deinsum_status plan_ttmc_fused(deinsum_plan_s *pl) {
         mx = std::max(mx, sz);
     }
     pl->rest_buf_elems = mx;
-    ttm_last_geometry(N, S, pl->dims[N - 2], pl->dims[N - 1], int(pl->ranks[N - 1]), &pl->geom);
+    ttm_last_geometry(N, S, pl->dims[N - 2], pl->dims[N - 1], int(pl->ranks[N - 1]), &pl->geom, pl->t_sg);
     return DEINSUM_OK;
 }
 
@@ -664,12 +666,13 @@ deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, voi
 }
 
 // 3-D tensor map of X for the fused TTMc kernel: {I_{N-1}, I_{N-2}, S}, box
-// {64, min(I_{N-2}, 128), 1}; cached per X pointer.
+// {64, min(I_{N-2}, 128), 1} (or sg slabs of 128/sg rows); cached per X pointer.
 bool encode_ttmc_map(deinsum_plan_s *pl, const void *X) {
     if (pl->xmap_ptr == X) return pl->xmap_ok != 0;
     pl->xmap_ptr = X;
     const int N = pl->order;
-    pl->xmap_ok = encode_ttm_last_map(X, pl->t_S, pl->dims[N - 2], pl->dims[N - 1], &pl->xmap, &pl->xmap_box_bytes)
+    pl->xmap_ok = encode_ttm_last_map(X, pl->t_S, pl->dims[N - 2], pl->dims[N - 1], &pl->xmap, &pl->xmap_box_bytes,
+                                      pl->t_sg)
                       ? 1 : 0;
     return pl->xmap_ok != 0;
 }
@@ -701,6 +704,7 @@ deinsum_status execute_ttmc_fused(deinsum_plan_s *pl, const void *const *inputs,
     t.n_kb = pl->t_nkb;
     t.R2 = int(pl->ranks[N - 2]);
     t.R3 = int(pl->ranks[N - 1]);
+    t.sg = pl->t_sg;
     t.status = pl->d_status;
     if (!err) {
         const long ti = timing_begin(pl, stream);
@@ -759,13 +763,13 @@ namespace deinsum {
 
 // Converter view of one raw chunk (128 k rows x 64 l) of the last-mode TTM kernels:
 // case 0, one slab per tile, R_pad 32 (split factor tiles of U_{N-1}).
-void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, MttkrpGeom *g) {
+void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, MttkrpGeom *g, int sg) {
     std::memset(g, 0, sizeof(*g));
     g->order = order;
     g->mode = order - 2;
     g->kcase = 0;
     g->I = K;
-    g->narrow = K < DEINSUM_BM ? 1 : 0;
+    g->narrow = (sg == 1 && K < DEINSUM_BM) ? 1 : 0;
     g->G = 1;
     g->P = S;
     g->K_in = L;
@@ -779,17 +783,21 @@ void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, Mttkrp
 }
 
 // 3-D tensor map of X viewed as S slabs x K rows x L (the last mode contiguous):
-// dims {L, K, S}, box {64, min(K, 128), 1}.
-bool encode_ttm_last_map(const void *X, int64_t S, int64_t K, int64_t L, CUtensorMap *map, uint32_t *box_bytes) {
+// dims {L, K, S}, box {64, min(K, 128), 1}; with sg > 1 (K <= 128 / sg) the box is
+// {64, 128 / sg, sg}: sg slabs land 128 / sg rows apart, rows past K read as zero.
+bool encode_ttm_last_map(const void *X, int64_t S, int64_t K, int64_t L, CUtensorMap *map, uint32_t *box_bytes,
+                         int sg) {
     auto enc = tensor_map_encoder();
     const int64_t lim = int64_t(1) << 31;
     if (!enc || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || L % 4 != 0 || S >= lim || K >= lim || L >= lim)
         return false;
+    if (sg != 1 && (sg != ttmc_slab_group(K))) return false;
     cuuint64_t dims[3] = {cuuint64_t(L), cuuint64_t(K), cuuint64_t(S)};
     cuuint64_t strides[2] = {cuuint64_t(L) * 4, cuuint64_t(L * K) * 4};
-    cuuint32_t box[3] = {DEINSUM_BK, cuuint32_t(std::min<int64_t>(K, DEINSUM_BM)), 1};
+    cuuint32_t box[3] = {DEINSUM_BK, cuuint32_t(sg > 1 ? DEINSUM_BM / sg : std::min<int64_t>(K, DEINSUM_BM)),
+                         cuuint32_t(sg)};
     cuuint32_t estr[3] = {1, 1, 1};
-    *box_bytes = uint32_t(4 * box[0] * box[1]);
+    *box_bytes = uint32_t(4 * box[0] * box[1] * box[2]);
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(X), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

@@ -10,13 +10,15 @@
 //     warps splitting them into BF16 hi / lo operand tiles, one thread issuing
 //     tcgen05.mma against the split factor tiles, FP32 accumulation in TMEM;
 //   stage 2 (CUDA cores, FP32): each epilogue warp moves the 32 T1 rows of its
-//     TMEM lane quadrant to shared memory and adds U_{N-2}[those rows]^T T1 into
-//     its own partial R_{N-2} x R_{N-1} block (4 x 8 outputs per thread, so that
-//     the shared-memory reads stay a small share of the bandwidth stage 1 leaves);
-//     at the end of a slab the four partials are added in a fixed order.  The
-//     factor rows of a k tile sit in one of two shared-memory slots: copied once
-//     when I_{N-2} <= 256, else one tile ahead by the epilogue itself, so the X
-//     stream never waits on stage 2.
+//     TMEM lane quadrant to shared memory; once all four have, every epilogue
+//     thread adds U_{N-2}^T T1 over all rows of the tile into its own block of
+//     T2 (2 x 4, 4 x 4 or 4 x 8 outputs), kept in registers across the slab's k
+//     tiles and stored once -- no partial sums to combine.  Slabs with
+//     I_{N-2} <= 64 (<= 32) share a tile two (four) at a time, 128 / SG rows
+//     apart, so that short slabs still fill the tensor-core tile and every
+//     epilogue thread.  The factor rows of a k tile sit in one of two
+//     shared-memory slots: copied once when I_{N-2} <= 256, else one tile ahead
+//     by the epilogue itself, so the X stream never waits on stage 2.
 // T1 never reaches HBM; T2 (R_{N-2} R_{N-1} / (I_{N-2} I_{N-1}) of X) is written
 // once, and the remaining modes are contracted by the plain TTM chain.  Each
 // CTA owns a contiguous range of slabs, so every T2 block is produced by one
@@ -24,8 +26,8 @@
 //
 // Warp roles: 0-7 converters, 8-11 epilogue (stage 2), 12 TMEM + MMA issue,
 // 13 TMA.  Every wait is bounded (mbar_wait); the epilogue warps meet only
-// through mbarriers (ufree: U slot reads done; pdone / rdone: slab partials
-// written / read), so a time-out anywhere ends every role.
+// through mbarriers (ufree: U slot reads done; t1full / t1free: a tile's T1 rows
+// written to / read from shared memory), so a time-out anywhere ends every role.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -54,15 +56,18 @@ struct TtmcCfg {
     static constexpr int T1_BYTES = BM * RP * 4;           // one T1 tile, FP32, 16-byte slots swizzled by row
     static constexpr int USLOTS = 2;
     static constexpr int USLOT_BYTES = BM * RP * 4;        // 128 rows of U_{N-2}, 32 columns
-    static constexpr int TMEM_COLS = 2 * N;                // two accumulators of N columns
-    static constexpr int NBARS = 2 * RS + 3 * AS + 4 + 1 + USLOTS + 3;
+    static constexpr int NACC = 2;                         // TMEM accumulators of N columns (tiles in flight)
+    static constexpr int TMEM_COLS = NACC * N;
+    static constexpr int ACC_BAR = 2 * RS + 3 * AS;        // accf[NACC], acce[NACC], drain follow the rings
+    static constexpr int NBARS = ACC_BAR + 2 * NACC + 1 + USLOTS + 3;
     static constexpr size_t SMEM = size_t(RS) * RAW_BYTES + size_t(AS) * ASTAGE_BYTES + T1_BYTES +
                                    size_t(USLOTS) * USLOT_BYTES + 1024 + 512;
     static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB per-CTA limit");
     static_assert(NBARS * 8 + 8 <= 512, "barrier area");
 };
 
-// Chunks of one CTA: slabs [s, s1), then k tiles, then l chunks.
+// Chunks of one CTA: slab groups [s, s1) (one slab each unless slabs share a
+// tile), then k tiles, then l chunks.
 struct TIter {
     int64_t s, s1;
     int kt, kb;
@@ -91,12 +96,15 @@ __device__ __forceinline__ float4 *t1_slot(float *t1s, int r, int x) {
 }
 
 // STORE: the epilogue writes the T1 tiles to HBM (a.T2 as S x I_{N-2} x R_{N-1}:
-// the TTM over the last mode alone) instead of running stage 2.
-template <bool STORE>
+// the TTM over the last mode alone) instead of running stage 2.  SG: slabs per
+// tile (a.sg).
+template <bool STORE, int SG>
 __global__ void __launch_bounds__(TtmcCfg::THREADS, 1)
 ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     using C = TtmcCfg;
     constexpr int RS = C::RS, AS = C::AS, RP = C::RP;
+    static_assert(!STORE || SG == 1, "the last-mode TTM keeps one slab per tile");
+    const int64_t ngroups = (a.S + SG - 1) / SG;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *raw_base = smem;
@@ -119,13 +127,14 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     auto a_full = [&](int s) { return smem_u32(bars + 2 * RS + s); };
     auto bfull = [&](int s) { return smem_u32(bars + 2 * RS + AS + s); };
     auto a_empty = [&](int s) { return smem_u32(bars + 2 * RS + 2 * AS + s); };
-    auto accf = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + b); };
-    auto acce = [&](int b) { return smem_u32(bars + 2 * RS + 3 * AS + 2 + b); };
-    const uint32_t drain = smem_u32(bars + 2 * RS + 3 * AS + 4);
-    auto ufull = [&](int s) { return smem_u32(bars + 2 * RS + 3 * AS + 5 + s); };
-    const uint32_t ufree = smem_u32(bars + 2 * RS + 3 * AS + 5 + C::USLOTS);
-    const uint32_t pdone = smem_u32(bars + 2 * RS + 3 * AS + 6 + C::USLOTS);
-    const uint32_t rdone = smem_u32(bars + 2 * RS + 3 * AS + 7 + C::USLOTS);
+    constexpr int UB = C::ACC_BAR + 2 * C::NACC + 1;   // first barrier after the accumulators and drain
+    auto accf = [&](int b) { return smem_u32(bars + C::ACC_BAR + b); };
+    auto acce = [&](int b) { return smem_u32(bars + C::ACC_BAR + C::NACC + b); };
+    const uint32_t drain = smem_u32(bars + C::ACC_BAR + 2 * C::NACC);
+    auto ufull = [&](int s) { return smem_u32(bars + UB + s); };
+    const uint32_t ufree = smem_u32(bars + UB + C::USLOTS);
+    const uint32_t t1full = smem_u32(bars + UB + C::USLOTS + 1);
+    const uint32_t t1free = smem_u32(bars + UB + C::USLOTS + 2);
     auto uslot_addr = [&](int s) { return smem_u32(ubuf) + uint32_t(s) * C::USLOT_BYTES; };
 
     if (threadIdx.x == 0) {
@@ -138,15 +147,15 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             mbar_init(bfull(s), 1);
             mbar_init(a_empty(s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < C::NACC; ++b) {
             mbar_init(accf(b), 1);
             mbar_init(acce(b), EPI_WARPS);
         }
         mbar_init(drain, 1);
         for (int s = 0; s < C::USLOTS; ++s) mbar_init(ufull(s), 1);
         mbar_init(ufree, EPI_WARPS);
-        mbar_init(pdone, EPI_WARPS);
-        mbar_init(rdone, EPI_WARPS);
+        mbar_init(t1full, EPI_WARPS);
+        mbar_init(t1free, EPI_WARPS);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -165,7 +174,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         const bool issuer = (pt == 0);
         const char *bsrc = static_cast<const char *>(a.Bsplit);
         TIter it;
-        it.init(a.S);
+        it.init(ngroups);
         uint32_t bpar = 0, bused = 0;
         for (int64_t chunk = 0; !it.done; ++chunk) {
             float4 v[8];
@@ -203,7 +212,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         // raw X chunks
         if (lane == 0) {
             TIter it;
-            it.init(a.S);
+            it.init(ngroups);
             int last_rs = -1;
             uint32_t last_par = 0;
             for (int64_t chunk = 0; !it.done; ++chunk) {
@@ -211,7 +220,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 const uint32_t rj = uint32_t(chunk / RS);
                 if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status)) break;
                 mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
-                tma_load_3d(raw_addr(rs), &a.xmap, it.kb * BK, it.kt * BM, int(it.s), raw_full(rs));
+                tma_load_3d(raw_addr(rs), &a.xmap, it.kb * BK, it.kt * BM, int(it.s * SG), raw_full(rs));
                 last_rs = rs;
                 last_par = rj & 1u;
                 it.next(a.n_kb, a.n_kt);
@@ -225,13 +234,13 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16_f32(BM, C::N);
             TIter it;
-            it.init(a.S);
+            it.init(ngroups);
             const int64_t nfg = (it.s1 - it.s) * a.n_kt;
             int64_t chunk = 0;
             bool ok = true;
             for (int64_t fgi = 0; ok && fgi < nfg; ++fgi) {
-                const int b = int(fgi & 1);
-                const uint32_t jb = uint32_t(fgi >> 1);
+                const int b = int(fgi % C::NACC);
+                const uint32_t jb = uint32_t(fgi / C::NACC);
                 if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dcol = tmem + uint32_t(b * C::N);
@@ -266,14 +275,14 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
         TIter it;
-        it.init(a.S);
+        it.init(ngroups);
         const int64_t nfg = (it.s1 - it.s) * a.n_kt;
         int64_t s = it.s;
         int kt = 0;
         const bool vec = (a.R3 & 3) == 0;
         for (int64_t fgi = 0; fgi < nfg; ++fgi) {
-            const int b = int(fgi & 1);
-            const uint32_t jb = uint32_t(fgi >> 1);
+            const int b = int(fgi % C::NACC);
+            const uint32_t jb = uint32_t(fgi / C::NACC);
             if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) break;
             tc_fence_after();
             const int64_t k = int64_t(kt) * BM + row;
@@ -313,8 +322,11 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 ++s;
             }
         }
-    } else {
-        // ------------------------------------------------- epilogue (stage 2)
+    } else if constexpr (SG == 1) {
+        // ------------------------------------ epilogue (stage 2), one slab per tile
+        // Each warp adds U_{N-2}^T T1 over its own 32 rows into a partial block of the
+        // slab's T2 (4 x 8 outputs per thread); at the end of the slab the four partials
+        // are added in warp order (t1full: partials written, t1free: partials read).
         const int quad = warp & 3;                 // TMEM lanes (= tile rows) 32*quad .. 32*quad+31
         const int row = quad * 32 + lane;          // the T1 row this thread moves to smem
         const int cb = lane >> 2, dg = lane & 3;   // stage 2: T2[4 cb .. 4 cb + 3, 8 dg .. 8 dg + 7]
@@ -325,7 +337,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             #pragma unroll
             for (int q = 0; q < 8; ++q) acc[i][q] = 0.f;
         TIter it;
-        it.init(a.S);
+        it.init(ngroups);
         const int64_t nfg = (it.s1 - it.s) * a.n_kt;
         int64_t s = it.s;
         int kt = 0;
@@ -349,13 +361,13 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             }
         }
         for (int64_t fgi = 0; fgi < nfg; ++fgi) {
-            const int b = int(fgi & 1);
-            const uint32_t jb = uint32_t(fgi >> 1);
+            const int b = int(fgi % C::NACC);
+            const uint32_t jb = uint32_t(fgi / C::NACC);
             if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) break;
             tc_fence_after();
             // the block of t1s this warp writes held the previous slab's partials:
             // every warp has finished reading them
-            if (kt == 0 && !__all_sync(0xffffffffu, mbar_wait(rdone, (slab & 1u) ^ 1u, abort_flag, status))) break;
+            if (kt == 0 && !__all_sync(0xffffffffu, mbar_wait(t1free, (slab & 1u) ^ 1u, abort_flag, status))) break;
             const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
             #pragma unroll
             for (int c0 = 0; c0 < RP; c0 += 16) {
@@ -427,8 +439,8 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                     dst[1] = make_float4(acc[cc][4], acc[cc][5], acc[cc][6], acc[cc][7]);
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(pdone);
-                if (!__all_sync(0xffffffffu, mbar_wait(pdone, slab & 1u, abort_flag, status))) break;
+                if (lane == 0) mbar_arrive(t1full);
+                if (!__all_sync(0xffffffffu, mbar_wait(t1full, slab & 1u, abort_flag, status))) break;
                 // this warp reduces rows c = 8 quad .. 8 quad + 7 of the block
                 const int c = 8 * quad + (lane >> 2), d0 = 8 * (lane & 3);
                 float sum[8];
@@ -448,7 +460,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                         if (d0 + q < a.R3) dst[d0 + q] = sum[q];
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(rdone);
+                if (lane == 0) mbar_arrive(t1free);
                 #pragma unroll
                 for (int i = 0; i < 4; ++i)
                     #pragma unroll
@@ -456,6 +468,174 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 kt = 0;
                 ++s;
                 ++slab;
+            }
+        }
+    } else {
+        // ------------------------------- epilogue (stage 2), SG slabs per tile
+        // Thread et owns T2[s, c0 .. c0 + CB - 1, d0 .. d0 + DB - 1] of slab gsl of the tile.
+        constexpr int CB = SG == 1 ? 2 : 4;           // c per thread
+        constexpr int DB = SG == 4 ? 8 : 4;           // d per thread
+        constexpr int TPS = (RP / CB) * (RP / DB);    // threads per slab
+        static_assert(TPS * SG == EPI_WARPS * 32, "every epilogue thread owns outputs of one slab");
+        constexpr int KP = BM / SG;                   // tile rows per slab
+        const int quad = warp & 3;                    // TMEM lanes (= tile rows) 32*quad .. 32*quad+31
+        const int row = quad * 32 + lane;             // the T1 row this thread moves to smem
+        const int et = threadIdx.x - CONV_WARPS * 32;
+        const int gsl = et / TPS, tt = et % TPS;
+        const int c0 = (tt / (RP / DB)) * CB, d0 = (tt % (RP / DB)) * DB;
+        const int rbase = gsl * KP;                   // the slab's first row in the tile
+        float acc[CB][DB];
+        #pragma unroll
+        for (int i = 0; i < CB; ++i)
+            #pragma unroll
+            for (int q = 0; q < DB; ++q) acc[i][q] = 0.f;
+        TIter it;
+        it.init(ngroups);
+        const int64_t nfg = (it.s1 - it.s) * a.n_kt;
+        int64_t grp = it.s;
+        int kt = 0;
+        // U_{N-2} rows of k tile kt.  With at most two tiles (I_{N-2} <= 256) every tile
+        // is copied once into slot kt and stays; otherwise the rows of fiber group f go
+        // to slot f % 2, copied by one thread one group ahead (groups 0 and 1 now, group
+        // f + 1 once every warp is done with group f - 1).
+        const bool uissuer = (et == 0);
+        const bool uresident = a.n_kt <= C::USLOTS;
+        auto load_u = [&](int us, int ktile) {
+            mbar_arrive_expect_tx(ufull(us), C::USLOT_BYTES);
+            bulk_g2s(uslot_addr(us), a.U2pad + size_t(ktile) * BM * RP, C::USLOT_BYTES, ufull(us));
+        };
+        if (uissuer && nfg > 0) {
+            if (uresident) {
+                for (int t = 0; t < a.n_kt; ++t) load_u(t, t);
+            } else {
+                load_u(0, 0);
+                if (nfg > 1) load_u(1, 1 % a.n_kt);
+            }
+        }
+        const bool vec = (a.R3 & 3) == 0;
+        for (int64_t fgi = 0; fgi < nfg; ++fgi) {
+            const int b = int(fgi % C::NACC);
+            const uint32_t jb = uint32_t(fgi / C::NACC);
+            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) break;
+            tc_fence_after();
+            // every thread has finished reading the previous tile's rows from t1s
+            if (fgi > 0 && !__all_sync(0xffffffffu, mbar_wait(t1free, uint32_t((fgi - 1) & 1), abort_flag, status)))
+                break;
+            const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
+            #pragma unroll
+            for (int cc = 0; cc < RP; cc += 16) {
+                uint32_t hi[16], lo[16];
+                tmem_ld16(taddr + uint32_t(cc), hi);
+                tmem_ld16(taddr + uint32_t(RP + cc), lo);
+                tmem_wait_ld();
+                #pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const int q = 4 * x;
+                    *t1_slot(t1s, row, cc / 4 + x) =
+                        make_float4(__uint_as_float(hi[q]) + __uint_as_float(lo[q]),
+                                    __uint_as_float(hi[q + 1]) + __uint_as_float(lo[q + 1]),
+                                    __uint_as_float(hi[q + 2]) + __uint_as_float(lo[q + 2]),
+                                    __uint_as_float(hi[q + 3]) + __uint_as_float(lo[q + 3]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(acce(b));
+                mbar_arrive(t1full);
+            }
+            {
+                // every warp has finished group fgi - 1, whose slot the next group uses
+                bool ok = true;
+                if (uissuer && !uresident && fgi >= 1 && fgi + 1 < nfg) {
+                    ok = mbar_wait(ufree, uint32_t((fgi - 1) & 1), abort_flag, status);
+                    if (ok) load_u(int((fgi + 1) % C::USLOTS), (kt + 1) % a.n_kt);
+                }
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
+            const int us = uresident ? kt : int(fgi % C::USLOTS);
+            const uint32_t uj = uresident ? 0u : uint32_t(fgi / C::USLOTS);
+            if (!__all_sync(0xffffffffu, mbar_wait(ufull(us), uj & 1u, abort_flag, status))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(t1full, uint32_t(fgi & 1), abort_flag, status))) break;
+            // stage 2 over the slab's rows of this tile that lie inside I_{N-2} (the
+            // rest are zero in both operands: TMA zero fill and the padded factor)
+            const float *u = ubuf + us * (C::USLOT_BYTES / 4) + c0;
+            const int64_t left = a.g.I - int64_t(kt) * BM;
+            const int nk = SG > 1 ? int(a.g.I) : (left >= BM ? BM : int(left));
+            // rows in batches of KB: all of a batch's loads first, then its FMAs, so that
+            // one warp per scheduler does not wait out a shared-memory latency per row
+            constexpr int KB = SG == 4 ? 4 : 8;
+            auto row_fma = [&](const float (&uc)[CB], const float (&xd)[DB]) {
+                #pragma unroll
+                for (int i = 0; i < CB; ++i)
+                    #pragma unroll
+                    for (int q = 0; q < DB; ++q) acc[i][q] = fmaf(uc[i], xd[q], acc[i][q]);
+            };
+            auto row_load = [&](int k, float (&uc)[CB], float (&xd)[DB]) {
+                if constexpr (CB == 2) {
+                    const float2 w = *reinterpret_cast<const float2 *>(u + k * RP);
+                    uc[0] = w.x; uc[1] = w.y;
+                } else {
+                    const float4 w = *reinterpret_cast<const float4 *>(u + k * RP);
+                    uc[0] = w.x; uc[1] = w.y; uc[2] = w.z; uc[3] = w.w;
+                }
+                #pragma unroll
+                for (int x = 0; x < DB / 4; ++x) {
+                    const float4 v = *t1_slot(t1s, rbase + k, d0 / 4 + x);
+                    xd[4 * x] = v.x; xd[4 * x + 1] = v.y; xd[4 * x + 2] = v.z; xd[4 * x + 3] = v.w;
+                }
+            };
+            int k = 0;
+            #pragma unroll 1
+            for (; k + KB <= nk; k += KB) {
+                float uc[KB][CB], xd[KB][DB];
+                #pragma unroll
+                for (int j = 0; j < KB; ++j) row_load(k + j, uc[j], xd[j]);
+                #pragma unroll
+                for (int j = 0; j < KB; ++j) row_fma(uc[j], xd[j]);
+            }
+            #pragma unroll 1
+            for (; k < nk; ++k) {
+                float uc[CB], xd[DB];
+                row_load(k, uc, xd);
+                row_fma(uc, xd);
+            }
+            fence_proxy_async_smem();   // the U slot's reads before its next bulk-copy write
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(t1free);
+                mbar_arrive(ufree);
+            }
+            if (++kt == a.n_kt) {
+                // the slab is complete: this thread's block of T2
+                const int64_t sl = grp * SG + gsl;
+                if (sl < a.S) {
+                    #pragma unroll
+                    for (int i = 0; i < CB; ++i) {
+                        const int c = c0 + i;
+                        if (c >= a.R2) continue;
+                        float *dst = a.T2 + (sl * a.R2 + c) * a.R3;
+                        #pragma unroll
+                        for (int x = 0; x < DB / 4; ++x) {
+                            const int d = d0 + 4 * x;
+                            if (vec) {
+                                if (d < a.R3)
+                                    *reinterpret_cast<float4 *>(dst + d) =
+                                        make_float4(acc[i][4 * x], acc[i][4 * x + 1], acc[i][4 * x + 2], acc[i][4 * x + 3]);
+                            } else {
+                                #pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    if (d + q < a.R3) dst[d + q] = acc[i][4 * x + q];
+                            }
+                        }
+                    }
+                }
+                #pragma unroll
+                for (int i = 0; i < CB; ++i)
+                    #pragma unroll
+                    for (int q = 0; q < DB; ++q) acc[i][q] = 0.f;
+                kt = 0;
+                ++grp;
             }
         }
     }
@@ -481,22 +661,31 @@ __global__ void pad_factor_kernel(const float *__restrict__ U, int64_t rows, int
 }  // namespace
 
 namespace {
-template <bool STORE>
+template <bool STORE, int SG>
 int launch_ttmc_variant(const TtmcArgs &a, int n_sm, void *stream) {
     using C = TtmcCfg;
-    cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel<STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel<STORE, SG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(C::SMEM));
     if (e != cudaSuccess) return int(e);
-    int64_t grid = a.S < n_sm ? a.S : n_sm;
+    const int64_t groups = (a.S + SG - 1) / SG;
+    int64_t grid = groups < n_sm ? groups : n_sm;
     if (grid < 1) grid = 1;
-    ttmc_fused_kernel<STORE><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
+    ttmc_fused_kernel<STORE, SG><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
     count_launch();
     return int(cudaGetLastError());
 }
 }  // namespace
 
-int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream) { return launch_ttmc_variant<false>(a, n_sm, stream); }
-int launch_ttm_last_tc(const TtmcArgs &a, int n_sm, void *stream) { return launch_ttmc_variant<true>(a, n_sm, stream); }
+int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream) {
+    if (a.sg == 4) return launch_ttmc_variant<false, 4>(a, n_sm, stream);
+    if (a.sg == 2) return launch_ttmc_variant<false, 2>(a, n_sm, stream);
+    if (a.sg == 1) return launch_ttmc_variant<false, 1>(a, n_sm, stream);
+    return int(cudaErrorInvalidValue);
+}
+int launch_ttm_last_tc(const TtmcArgs &a, int n_sm, void *stream) {
+    if (a.sg != 1) return int(cudaErrorInvalidValue);
+    return launch_ttmc_variant<true, 1>(a, n_sm, stream);
+}
 
 int launch_ttmc_pad_factor(const float *U, int64_t rows, int R, float *out, int n_kt, void *stream) {
     const int64_t total = int64_t(n_kt) * BM * TtmcCfg::RP;

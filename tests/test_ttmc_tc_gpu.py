@@ -35,6 +35,14 @@ CASES = [
     ((70, 40, 100), 0, (32, 20)),             # k extent below one tile (narrow box)
     ((6, 7, 8, 90, 44), 0, (3, 5, 32, 7)),    # order 5, two more chain stages
     ((6, 7, 8, 90, 44), 2, (4, 6, 9, 32)),    # order 5, kept mode in the middle
+    # short slabs share a tile: I_{N-2} <= 64 two per tile, <= 32 four per tile; the slab
+    # counts leave a partial last group, and R_{N-1} = 10 takes the scalar stores of T2
+    ((31, 7, 60, 60), 0, (5, 24, 24)),        # two slabs per tile, S = 217
+    ((9, 13, 28, 36), 0, (6, 30, 10)),        # four slabs per tile, S = 117
+    ((5, 40, 33, 64), 1, (7, 32, 32)),        # two per tile, kept mode 1
+    ((70, 64, 20), 0, (32, 13)),              # order 3, I_{N-2} = 64 exactly
+    ((3, 5, 32, 8), 0, (2, 3, 4)),            # I_{N-2} = 32 exactly, one 8-wide l chunk
+    ((4, 6, 60, 60, 60), 0, (24, 24, 24, 24)),  # the paper's order-5 TTMc shape, fewer slabs
 ]
 
 
