@@ -118,13 +118,15 @@ struct TtmcArgs {
     uint32_t box_bytes;
     MttkrpGeom g;         // converter view of a chunk: case 0, I = I_{N-2}, narrow = I < 128 (sg = 1), G = 1
     const void *Bsplit;   // split-BF16 tiles of U_{N-1} (R_pad 32, n_kb tiles)
-    const float *U2pad;   // U_{N-2} as n_kt*128 rows x 32 FP32, zero beyond I_{N-2} x R_{N-2}
+    const float *U2pad;   // CUDA-core stage 2: U_{N-2} as n_kt*128 rows x 32 FP32, zero beyond I_{N-2} x R_{N-2}
+    const void *U2split;  // tensor-core stage 2 (tc2): split BF16 tiles of U_{N-2} (launch_ttmc_u2_split)
     float *T2;            // S x R_{N-2} x R_{N-1}, row-major
     int64_t S;            // slabs
     int n_kt;             // tiles of 128 along k
     int n_kb;             // chunks of 64 along l
     int R2, R3;           // R_{N-2}, R_{N-1} (<= 32)
     int sg;               // slabs per tile (1, 2 or 4; n_kt = 1 when sg > 1)
+    int tc2;              // stage 2 on the tensor cores (n_kt <= 2), else on CUDA cores (sg = 1)
     int *status;
 };
 // Slabs per tile of the fused kernel for I_{N-2} = K.
@@ -141,6 +143,11 @@ bool encode_ttm_last_map(const void *X, int64_t S, int64_t K, int64_t L, CUtenso
 // the box fills all 128 rows --, R_pad 32, ceil(L/64) chunks).
 void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, MttkrpGeom *g, int sg = 1);
 int launch_ttmc_pad_factor(const float *U, int64_t rows, int R, float *out, int n_kt, void *stream);
+// U_{N-2} (rows x R, rows <= 256) -> the tensor-core stage-2 operand: for k tile kt < n_kt,
+// part p (hi, lo) and half h of the tile, a 4 KB block at ((kt * 2 + p) * 2 + h) * 4096 holding
+// 32 rows c x 64 k (K-major, 128-byte swizzle), zero beyond rows x R.  n_kt * 16 KB in all.
+int launch_ttmc_u2_split(const float *U, int64_t rows, int R, void *out, int n_kt, void *stream);
+constexpr int kTtmcTc2MaxKt = 2;   // k tiles the tensor-core stage 2 keeps resident
 
 // Launch helpers implemented in the .cu files.  They return a CUDA error code
 // (0 on success) and increment the library's launch counter.

@@ -688,7 +688,13 @@ deinsum_status execute_ttmc_fused(deinsum_plan_s *pl, const void *const *inputs,
     sa.g = pl->geom;
     sa.U[N - 1] = U[N - 1];
     int err = launch_split_inner_factor(sa, pl->d_tbsplit, stream);
-    if (!err)
+    // stage 2 on the tensor cores while U_{N-2} fits on chip (I_{N-2} <= 256): its split
+    // tiles; otherwise the padded FP32 rows for the CUDA-core stage 2 (the same buffer size)
+    const bool tc2 = pl->t_nkt <= kTtmcTc2MaxKt;
+    if (!err && tc2)
+        err = launch_ttmc_u2_split(static_cast<const float *>(U[N - 2]), pl->dims[N - 2], int(pl->ranks[N - 2]),
+                                   pl->d_u2pad, pl->t_nkt, stream);
+    else if (!err)
         err = launch_ttmc_pad_factor(static_cast<const float *>(U[N - 2]), pl->dims[N - 2], int(pl->ranks[N - 2]),
                                      pl->d_u2pad, pl->t_nkt, stream);
     TtmcArgs t;
@@ -698,6 +704,8 @@ deinsum_status execute_ttmc_fused(deinsum_plan_s *pl, const void *const *inputs,
     t.g = pl->geom;
     t.Bsplit = pl->d_tbsplit;
     t.U2pad = pl->d_u2pad;
+    t.U2split = pl->d_u2pad;
+    t.tc2 = tc2 ? 1 : 0;
     t.T2 = pl->ttm_rest.empty() ? static_cast<float *>(output) : pl->d_t2;
     t.S = pl->t_S;
     t.n_kt = pl->t_nkt;

@@ -241,6 +241,14 @@ __host__ __device__ __forceinline__ uint32_t sw128_mn_offset(uint32_t m, uint32_
 constexpr uint32_t kMnAtomStride = 1024;   // between the two 64-row halves
 constexpr uint32_t kMnKGroupStride = 2048; // between groups of 8 k
 
+// The same for an MN-major tile of 64 rows (one atom along MN) x any k: atom k / 8
+// at byte (k / 8) * 1024 (stride 1024 B between groups of 8 k).
+__host__ __device__ __forceinline__ uint32_t sw128_mn64_offset(uint32_t n, uint32_t k) {
+    return (k >> 3) * 1024u + (k & 7u) * 128u + ((((n >> 3) ^ (k & 7u)) & 7u) << 4) + (n & 7u) * 2u;
+}
+// Instruction-descriptor bit selecting an MN-major B operand (bit 16, "transpose B").
+constexpr uint32_t kIdescBMnMajor = 1u << 16;
+
 // Byte offset of element (row, k) of a K-major 128B-swizzled bf16 operand tile
 // (64 k per row): atoms of 8 rows x 128 B.
 __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t k) {

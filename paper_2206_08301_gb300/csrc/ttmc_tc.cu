@@ -9,25 +9,32 @@
 //     MTTKRP pipeline -- TMA ring of raw FP32 chunks (128 k x 64 l), converter
 //     warps splitting them into BF16 hi / lo operand tiles, one thread issuing
 //     tcgen05.mma against the split factor tiles, FP32 accumulation in TMEM;
-//   stage 2 (CUDA cores, FP32): each epilogue warp moves the 32 T1 rows of its
-//     TMEM lane quadrant to shared memory; once all four have, every epilogue
-//     thread adds U_{N-2}^T T1 over all rows of the tile into its own block of
-//     T2 (2 x 4, 4 x 4 or 4 x 8 outputs), kept in registers across the slab's k
-//     tiles and stored once -- no partial sums to combine.  Slabs with
-//     I_{N-2} <= 64 (<= 32) share a tile two (four) at a time, 128 / SG rows
-//     apart, so that short slabs still fill the tensor-core tile and every
-//     epilogue thread.  The factor rows of a k tile sit in one of two
-//     shared-memory slots: copied once when I_{N-2} <= 256, else one tile ahead
-//     by the epilogue itself, so the X stream never waits on stage 2.
+//   stage 2 (tensor cores, I_{N-2} <= 256): the epilogue warps split each T1
+//     tile into BF16 hi / lo and write it to shared memory as an MN-major operand
+//     (row k, n = (part, d)); one epilogue thread issues
+//       D2[c, (p, d)] += sum_k U_{N-2}[k, c] T1_p[k, d]
+//     for both parts of U_{N-2} (resident split tiles, K-major) into a per-slab
+//     TMEM accumulator, and quadrant 0 reads D2 (lanes = c) once the slab is
+//     complete and writes T2.  Slabs with I_{N-2} <= 64 (<= 32) share a tile two
+//     (four) at a time, 128 / SG rows apart, each contracted over its own rows, so
+//     that short slabs still fill the tensor-core tile.  The stage-2 issue never
+//     blocks the stage-1 issue: separate threads, separate commits.
+//   stage 2 (CUDA cores, FP32, I_{N-2} > 256): each epilogue warp moves the 32 T1
+//     rows of its TMEM lane quadrant to shared memory and adds U_{N-2}^T T1 over
+//     them into its own partial block of T2; at the end of a slab the four
+//     partials are added in warp order.  The factor rows of a k tile sit in one
+//     of two shared-memory slots, copied one tile ahead by the epilogue itself.
 // T1 never reaches HBM; T2 (R_{N-2} R_{N-1} / (I_{N-2} I_{N-1}) of X) is written
 // once, and the remaining modes are contracted by the plain TTM chain.  Each
 // CTA owns a contiguous range of slabs, so every T2 block is produced by one
 // CTA in a fixed order (deterministic, no reduction pass).
 //
-// Warp roles: 0-7 converters, 8-11 epilogue (stage 2), 12 TMEM + MMA issue,
-// 13 TMA.  Every wait is bounded (mbar_wait); the epilogue warps meet only
-// through mbarriers (ufree: U slot reads done; t1full / t1free: a tile's T1 rows
-// written to / read from shared memory), so a time-out anywhere ends every role.
+// Warp roles: 0-7 converters, 8-11 epilogue (stage 2), 12 TMEM + stage-1 MMA
+// issue, 13 TMA.  Every wait is bounded (mbar_wait); the epilogue warps meet only
+// through mbarriers (tensor-core stage 2: b2full / b2free for the T1 operand,
+// d2full / d2free for the TMEM accumulators; CUDA-core stage 2: ufree for the U
+// slots, t1full / t1free for the partial blocks), so a time-out anywhere ends
+// every role.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -58,8 +65,17 @@ struct TtmcCfg {
     static constexpr int USLOT_BYTES = BM * RP * 4;        // 128 rows of U_{N-2}, 32 columns
     static constexpr int NACC = 2;                         // TMEM accumulators of N columns (tiles in flight)
     static constexpr int TMEM_COLS = NACC * N;
+    // tensor-core stage 2: the region after the operand stages holds the split U_{N-2}
+    // tiles (up to two k tiles, 16 KB each) and the split T1 tile B2 (128 k x 64 n, MN-major)
+    static constexpr int U2S_BYTES = kTtmcTc2MaxKt * 16384;
+    static constexpr int B2_BYTES = BM * 2 * RP * 2;
+    static_assert(U2S_BYTES + B2_BYTES == T1_BYTES + USLOTS * USLOT_BYTES, "the two stage-2 layouts share one region");
+    static constexpr int D2_SLOTS = 4;                     // TMEM accumulators of slabs' T2 (2 RP columns each)
+    static constexpr int TMEM_COLS_TC2 = 512;              // NACC * N + D2_SLOTS * 2 RP = 384, as a power of two
+    static_assert(NACC * N + D2_SLOTS * 2 * RP <= TMEM_COLS_TC2, "TMEM columns");
     static constexpr int ACC_BAR = 2 * RS + 3 * AS;        // accf[NACC], acce[NACC], drain follow the rings
-    static constexpr int NBARS = ACC_BAR + 2 * NACC + 1 + USLOTS + 3;
+    static constexpr int TC2_BAR = ACC_BAR + 2 * NACC + 1 + USLOTS + 3;   // u2full, b2full[2], b2free[2], d2full[], d2free[]
+    static constexpr int NBARS = TC2_BAR + 5 + 2 * D2_SLOTS + 1;   // + the stage-2 issuer's drain
     static constexpr size_t SMEM = size_t(RS) * RAW_BYTES + size_t(AS) * ASTAGE_BYTES + T1_BYTES +
                                    size_t(USLOTS) * USLOT_BYTES + 1024 + 512;
     static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB per-CTA limit");
@@ -97,21 +113,28 @@ __device__ __forceinline__ float4 *t1_slot(float *t1s, int r, int x) {
 
 // STORE: the epilogue writes the T1 tiles to HBM (a.T2 as S x I_{N-2} x R_{N-1}:
 // the TTM over the last mode alone) instead of running stage 2.  SG: slabs per
-// tile (a.sg).
-template <bool STORE, int SG>
+// tile (a.sg).  TC2: stage 2 on the tensor cores (a.tc2), else on CUDA cores.
+template <bool STORE, int SG, bool TC2>
 __global__ void __launch_bounds__(TtmcCfg::THREADS, 1)
 ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     using C = TtmcCfg;
     constexpr int RS = C::RS, AS = C::AS, RP = C::RP;
-    static_assert(!STORE || SG == 1, "the last-mode TTM keeps one slab per tile");
+    static_assert(!STORE || (SG == 1 && !TC2), "the last-mode TTM keeps one slab per tile");
+    static_assert(TC2 || SG == 1, "packed slabs take the tensor-core stage 2");
+    constexpr uint32_t kTmemCols = TC2 ? C::TMEM_COLS_TC2 : C::TMEM_COLS;
     const int64_t ngroups = (a.S + SG - 1) / SG;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *raw_base = smem;
     unsigned char *a_base = smem + RS * C::RAW_BYTES;
-    float *t1s = reinterpret_cast<float *>(a_base + AS * C::ASTAGE_BYTES);
+    unsigned char *region = a_base + AS * C::ASTAGE_BYTES;   // CUDA-core: t1s, U slots; TC2: U2 tiles, B2
+    float *t1s = reinterpret_cast<float *>(region);
     float *ubuf = t1s + C::T1_BYTES / 4;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ubuf) + C::USLOTS * C::USLOT_BYTES);
+    // TC2: the split U_{N-2} tiles (n_kt x 16 KB), then the B2 tiles: two when n_kt = 1, else one
+    const uint32_t u2s_addr = smem_u32(region);
+    const int nb2 = a.n_kt == 1 ? 2 : 1;
+    auto b2_addr = [&](int i) { return u2s_addr + uint32_t(a.n_kt + i) * 16384u; };
+    uint64_t *bars = reinterpret_cast<uint64_t *>(region + C::T1_BYTES + C::USLOTS * C::USLOT_BYTES);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
     int *status = a.status;
@@ -135,6 +158,12 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     const uint32_t ufree = smem_u32(bars + UB + C::USLOTS);
     const uint32_t t1full = smem_u32(bars + UB + C::USLOTS + 1);
     const uint32_t t1free = smem_u32(bars + UB + C::USLOTS + 2);
+    const uint32_t u2full = smem_u32(bars + C::TC2_BAR);
+    auto b2full = [&](int i) { return smem_u32(bars + C::TC2_BAR + 1 + i); };
+    auto b2free = [&](int i) { return smem_u32(bars + C::TC2_BAR + 3 + i); };
+    auto d2full = [&](int j) { return smem_u32(bars + C::TC2_BAR + 5 + j); };
+    auto d2free = [&](int j) { return smem_u32(bars + C::TC2_BAR + 5 + C::D2_SLOTS + j); };
+    const uint32_t drain2 = smem_u32(bars + C::TC2_BAR + 5 + 2 * C::D2_SLOTS);
     auto uslot_addr = [&](int s) { return smem_u32(ubuf) + uint32_t(s) * C::USLOT_BYTES; };
 
     if (threadIdx.x == 0) {
@@ -156,11 +185,21 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         mbar_init(ufree, EPI_WARPS);
         mbar_init(t1full, EPI_WARPS);
         mbar_init(t1free, EPI_WARPS);
+        mbar_init(u2full, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(b2full(i), EPI_WARPS);
+            mbar_init(b2free(i), 1);
+        }
+        for (int j = 0; j < C::D2_SLOTS; ++j) {
+            mbar_init(d2full(j), 1);
+            mbar_init(d2free(j), 1);
+        }
+        mbar_init(drain2, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
     if (warp == C::MMA_WARP) {
-        tmem_alloc(smem_u32(tmem_holder), C::TMEM_COLS);
+        tmem_alloc(smem_u32(tmem_holder), kTmemCols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -322,7 +361,173 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 ++s;
             }
         }
-    } else if constexpr (SG == 1) {
+    } else if constexpr (TC2) {
+        // ---------------------------------- epilogue (tensor-core stage 2 feed)
+        // Per tile: each thread takes its T1 row (TMEM lane = tile row = k) from the
+        // stage-1 accumulator, splits it into BF16 hi / lo and writes it as row k of an
+        // MN-major B2 tile (n = d for hi, 32 + d for lo).  The slabs a tile completes are
+        // written out one tile later (so that their stage-2 MMAs never hold up the next
+        // tile's feed): quadrant 0 (TMEM lanes 0-31 = c) reads each slab's D2 slot and
+        // writes T2[s, c, :].
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        TIter it;
+        it.init(ngroups);
+        const int64_t nfg = (it.s1 - it.s) * a.n_kt;
+        int64_t grp = it.s;
+        int kt = 0;
+        const bool vec = (a.R3 & 3) == 0;
+        bool ok = true;
+        int64_t pending = -1;                      // slab group whose T2 is still in TMEM
+        // The stage-2 MMAs are issued by lane 0 of quadrant 1 (its commits track only its
+        // own MMAs), so the stage-1 issue never waits on the B2 feed; quadrant 0 writes T2.
+        const bool issuer = (quad == 1 && lane == 0);
+        if (issuer && nfg > 0) {   // the split U_{N-2} tiles stay for the whole kernel
+            mbar_arrive_expect_tx(u2full, uint32_t(a.n_kt) * 16384u);
+            bulk_g2s(u2s_addr, a.U2split, uint32_t(a.n_kt) * 16384u, u2full);
+        }
+        // Stage 2 of tile t (B2 buffer bi): for each slab g of the tile and both parts q of
+        // U_{N-2} = U_hi + U_lo,  D2[slot][c, (p, d)] += sum_k U_q[k, c] T1_p[k, d],
+        // A = the split U_{N-2} block of part q (K-major, rows c; the rows past 32 that the
+        // M = 128 shape also reads come from the following blocks and only feed D rows that
+        // nobody reads), B = the split T1 tile (MN-major, n = (p, d)), k over the slab's
+        // rows of the tile.
+        auto issue_stage2 = [&](int64_t t, int bi) -> bool {
+            constexpr uint32_t idesc2 = idesc_bf16_f32(BM, 2 * RP) | kIdescBMnMajor;
+            constexpr int KP = BM / SG;            // tile rows of one slab
+            const int tk = int(t % a.n_kt);
+            const int64_t tg = t / a.n_kt;         // slab group within the CTA
+            if (!mbar_wait(b2full(bi), uint32_t((t / nb2) & 1), abort_flag, status)) return false;
+            if (t == 0 && !mbar_wait(u2full, 0u, abort_flag, status)) return false;
+            tc_fence_after();
+            for (int g = 0; g < SG; ++g) {
+                const int64_t j = tg * SG + g;     // slab index within the CTA
+                const int slot = int(j % C::D2_SLOTS);
+                // the slab that last used the slot has been written out
+                if (tk == 0 && !mbar_wait(d2free(slot), uint32_t((j / C::D2_SLOTS) & 1) ^ 1u, abort_flag, status))
+                    return false;
+                tc_fence_after();
+                const uint32_t dcol = tmem + uint32_t(C::NACC * C::N + slot * 2 * RP);
+                #pragma unroll
+                for (int ks = 0; ks < KP / 16; ++ks) {
+                    const int ku = 16 * ks;                       // k within the tile's k range
+                    const int h = ku >> 6, st = (ku & 63) >> 4;   // 64-k half, 16-k step in it
+                    const uint32_t ahi = u2s_addr + uint32_t(((tk * 2 + 0) * 2 + h) * 4096);
+                    const uint32_t alo = u2s_addr + uint32_t(((tk * 2 + 1) * 2 + h) * 4096);
+                    const uint64_t adv = uint64_t(st * 32) >> 4;
+                    const uint64_t db =
+                        desc_mnmajor_sw128(b2_addr(bi) + uint32_t(((g * KP + ku) >> 3) * 1024), 1024u, 1024u);
+                    mma_bf16(dcol, desc_kmajor_sw128(ahi) + adv, db, idesc2, (tk > 0 || ks > 0) ? 1u : 0u);
+                    mma_bf16(dcol, desc_kmajor_sw128(alo) + adv, db, idesc2, 1u);
+                }
+                if (tk == a.n_kt - 1) mma_commit(d2full(slot));
+            }
+            mma_commit(b2free(bi));
+            return true;
+        };
+        auto write_t2 = [&](int64_t pg) -> bool {
+            for (int g = 0; g < SG; ++g) {
+                const int64_t j = (pg - it.s) * SG + g;   // slab index within the CTA
+                const int slot = int(j % C::D2_SLOTS);
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait(d2full(slot), uint32_t((j / C::D2_SLOTS) & 1), abort_flag, status)))
+                    return false;
+                tc_fence_after();
+                const uint32_t d2 = tmem + uint32_t(C::NACC * C::N + slot * 2 * RP);   // lanes 0-31
+                uint32_t vh[2][16], vl[2][16];   // columns (hi part, d) and (lo part, d)
+                tmem_ld16(d2, vh[0]);
+                tmem_ld16(d2 + 16, vh[1]);
+                tmem_ld16(d2 + RP, vl[0]);
+                tmem_ld16(d2 + RP + 16, vl[1]);
+                tmem_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(d2free(slot));
+                const int64_t sl = pg * SG + g;
+                const int c = lane;
+                if (sl < a.S && c < a.R2) {
+                    float *dst = a.T2 + (sl * a.R2 + c) * a.R3;
+                    #pragma unroll
+                    for (int d = 0; d < RP; d += 4) {
+                        const uint32_t *h4 = &vh[d >> 4][d & 15], *l4 = &vl[d >> 4][d & 15];
+                        const float4 t4 = make_float4(__uint_as_float(h4[0]) + __uint_as_float(l4[0]),
+                                                      __uint_as_float(h4[1]) + __uint_as_float(l4[1]),
+                                                      __uint_as_float(h4[2]) + __uint_as_float(l4[2]),
+                                                      __uint_as_float(h4[3]) + __uint_as_float(l4[3]));
+                        if (vec) {
+                            if (d < a.R3) *reinterpret_cast<float4 *>(dst + d) = t4;
+                        } else {
+                            if (d < a.R3) dst[d] = t4.x;
+                            if (d + 1 < a.R3) dst[d + 1] = t4.y;
+                            if (d + 2 < a.R3) dst[d + 2] = t4.z;
+                            if (d + 3 < a.R3) dst[d + 3] = t4.w;
+                        }
+                    }
+                }
+            }
+            return true;
+        };
+        for (int64_t fgi = 0; ok && fgi < nfg; ++fgi) {
+            const int b = int(fgi % C::NACC);
+            const uint32_t jb = uint32_t(fgi / C::NACC);
+            const int bi = int(fgi % nb2);
+            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) break;
+            // the stage-2 MMAs of the tile that last used this B2 buffer have read it
+            if (fgi >= nb2 && !__all_sync(0xffffffffu, mbar_wait(b2free(bi), uint32_t(((fgi / nb2) & 1) ^ 1),
+                                                                 abort_flag, status)))
+                break;
+            tc_fence_after();
+            const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
+            uint32_t ph[RP / 2], pl[RP / 2];   // T1 row: packed BF16 pairs, hi and lo parts
+            #pragma unroll
+            for (int c0 = 0; c0 < RP; c0 += 16) {
+                uint32_t hi[16], lo[16];
+                tmem_ld16(taddr + uint32_t(c0), hi);
+                tmem_ld16(taddr + uint32_t(RP + c0), lo);
+                tmem_wait_ld();
+                #pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    split2(__uint_as_float(hi[2 * q]) + __uint_as_float(lo[2 * q]),
+                           __uint_as_float(hi[2 * q + 1]) + __uint_as_float(lo[2 * q + 1]), ph[c0 / 2 + q],
+                           pl[c0 / 2 + q]);
+            }
+            tc_fence_before();
+            const uint32_t b2 = b2_addr(bi);
+            #pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                sts128(b2 + sw128_mn64_offset(uint32_t(8 * ch), uint32_t(row)), ph[4 * ch], ph[4 * ch + 1],
+                       ph[4 * ch + 2], ph[4 * ch + 3]);
+                sts128(b2 + sw128_mn64_offset(uint32_t(RP + 8 * ch), uint32_t(row)), pl[4 * ch], pl[4 * ch + 1],
+                       pl[4 * ch + 2], pl[4 * ch + 3]);
+            }
+            fence_proxy_async_smem();   // the B2 stores before the tensor-core reads
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(acce(b));
+                mbar_arrive(b2full(bi));
+            }
+            if (quad == 0 && pending >= 0 && !write_t2(pending)) ok = false;   // the previous tile's slabs
+            pending = -1;
+            if (quad == 1) {
+                bool s2 = true;
+                if (issuer) s2 = issue_stage2(fgi, bi);
+                if (!__all_sync(0xffffffffu, s2)) ok = false;
+            }
+            if (++kt == a.n_kt) {
+                kt = 0;
+                pending = grp;
+                ++grp;
+            }
+        }
+        if (ok && quad == 0 && pending >= 0) write_t2(pending);
+        // the U_{N-2} copy has landed and every stage-2 MMA has completed before exit
+        // (and before TMEM is released), also when the loop ended early
+        if (issuer && nfg > 0) {
+            mbar_wait(u2full, 0u, abort_flag, status);
+            mma_commit(drain2);
+            mbar_wait(drain2, 0u, abort_flag, status);
+        }
+    } else {
         // ------------------------------------ epilogue (stage 2), one slab per tile
         // Each warp adds U_{N-2}^T T1 over its own 32 rows into a partial block of the
         // slab's T2 (4 x 8 outputs per thread); at the end of the slab the four partials
@@ -470,181 +675,13 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 ++slab;
             }
         }
-    } else {
-        // ------------------------------- epilogue (stage 2), SG slabs per tile
-        // Thread et owns T2[s, c0 .. c0 + CB - 1, d0 .. d0 + DB - 1] of slab gsl of the tile.
-        constexpr int CB = SG == 1 ? 2 : 4;           // c per thread
-        constexpr int DB = SG == 4 ? 8 : 4;           // d per thread
-        constexpr int TPS = (RP / CB) * (RP / DB);    // threads per slab
-        static_assert(TPS * SG == EPI_WARPS * 32, "every epilogue thread owns outputs of one slab");
-        constexpr int KP = BM / SG;                   // tile rows per slab
-        const int quad = warp & 3;                    // TMEM lanes (= tile rows) 32*quad .. 32*quad+31
-        const int row = quad * 32 + lane;             // the T1 row this thread moves to smem
-        const int et = threadIdx.x - CONV_WARPS * 32;
-        const int gsl = et / TPS, tt = et % TPS;
-        const int c0 = (tt / (RP / DB)) * CB, d0 = (tt % (RP / DB)) * DB;
-        const int rbase = gsl * KP;                   // the slab's first row in the tile
-        float acc[CB][DB];
-        #pragma unroll
-        for (int i = 0; i < CB; ++i)
-            #pragma unroll
-            for (int q = 0; q < DB; ++q) acc[i][q] = 0.f;
-        TIter it;
-        it.init(ngroups);
-        const int64_t nfg = (it.s1 - it.s) * a.n_kt;
-        int64_t grp = it.s;
-        int kt = 0;
-        // U_{N-2} rows of k tile kt.  With at most two tiles (I_{N-2} <= 256) every tile
-        // is copied once into slot kt and stays; otherwise the rows of fiber group f go
-        // to slot f % 2, copied by one thread one group ahead (groups 0 and 1 now, group
-        // f + 1 once every warp is done with group f - 1).
-        const bool uissuer = (et == 0);
-        const bool uresident = a.n_kt <= C::USLOTS;
-        auto load_u = [&](int us, int ktile) {
-            mbar_arrive_expect_tx(ufull(us), C::USLOT_BYTES);
-            bulk_g2s(uslot_addr(us), a.U2pad + size_t(ktile) * BM * RP, C::USLOT_BYTES, ufull(us));
-        };
-        if (uissuer && nfg > 0) {
-            if (uresident) {
-                for (int t = 0; t < a.n_kt; ++t) load_u(t, t);
-            } else {
-                load_u(0, 0);
-                if (nfg > 1) load_u(1, 1 % a.n_kt);
-            }
-        }
-        const bool vec = (a.R3 & 3) == 0;
-        for (int64_t fgi = 0; fgi < nfg; ++fgi) {
-            const int b = int(fgi % C::NACC);
-            const uint32_t jb = uint32_t(fgi / C::NACC);
-            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) break;
-            tc_fence_after();
-            // every thread has finished reading the previous tile's rows from t1s
-            if (fgi > 0 && !__all_sync(0xffffffffu, mbar_wait(t1free, uint32_t((fgi - 1) & 1), abort_flag, status)))
-                break;
-            const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
-            #pragma unroll
-            for (int cc = 0; cc < RP; cc += 16) {
-                uint32_t hi[16], lo[16];
-                tmem_ld16(taddr + uint32_t(cc), hi);
-                tmem_ld16(taddr + uint32_t(RP + cc), lo);
-                tmem_wait_ld();
-                #pragma unroll
-                for (int x = 0; x < 4; ++x) {
-                    const int q = 4 * x;
-                    *t1_slot(t1s, row, cc / 4 + x) =
-                        make_float4(__uint_as_float(hi[q]) + __uint_as_float(lo[q]),
-                                    __uint_as_float(hi[q + 1]) + __uint_as_float(lo[q + 1]),
-                                    __uint_as_float(hi[q + 2]) + __uint_as_float(lo[q + 2]),
-                                    __uint_as_float(hi[q + 3]) + __uint_as_float(lo[q + 3]));
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(acce(b));
-                mbar_arrive(t1full);
-            }
-            {
-                // every warp has finished group fgi - 1, whose slot the next group uses
-                bool ok = true;
-                if (uissuer && !uresident && fgi >= 1 && fgi + 1 < nfg) {
-                    ok = mbar_wait(ufree, uint32_t((fgi - 1) & 1), abort_flag, status);
-                    if (ok) load_u(int((fgi + 1) % C::USLOTS), (kt + 1) % a.n_kt);
-                }
-                if (!__all_sync(0xffffffffu, ok)) break;
-            }
-            const int us = uresident ? kt : int(fgi % C::USLOTS);
-            const uint32_t uj = uresident ? 0u : uint32_t(fgi / C::USLOTS);
-            if (!__all_sync(0xffffffffu, mbar_wait(ufull(us), uj & 1u, abort_flag, status))) break;
-            if (!__all_sync(0xffffffffu, mbar_wait(t1full, uint32_t(fgi & 1), abort_flag, status))) break;
-            // stage 2 over the slab's rows of this tile that lie inside I_{N-2} (the
-            // rest are zero in both operands: TMA zero fill and the padded factor)
-            const float *u = ubuf + us * (C::USLOT_BYTES / 4) + c0;
-            const int64_t left = a.g.I - int64_t(kt) * BM;
-            const int nk = SG > 1 ? int(a.g.I) : (left >= BM ? BM : int(left));
-            // rows in batches of KB: all of a batch's loads first, then its FMAs, so that
-            // one warp per scheduler does not wait out a shared-memory latency per row
-            constexpr int KB = SG == 4 ? 4 : 8;
-            auto row_fma = [&](const float (&uc)[CB], const float (&xd)[DB]) {
-                #pragma unroll
-                for (int i = 0; i < CB; ++i)
-                    #pragma unroll
-                    for (int q = 0; q < DB; ++q) acc[i][q] = fmaf(uc[i], xd[q], acc[i][q]);
-            };
-            auto row_load = [&](int k, float (&uc)[CB], float (&xd)[DB]) {
-                if constexpr (CB == 2) {
-                    const float2 w = *reinterpret_cast<const float2 *>(u + k * RP);
-                    uc[0] = w.x; uc[1] = w.y;
-                } else {
-                    const float4 w = *reinterpret_cast<const float4 *>(u + k * RP);
-                    uc[0] = w.x; uc[1] = w.y; uc[2] = w.z; uc[3] = w.w;
-                }
-                #pragma unroll
-                for (int x = 0; x < DB / 4; ++x) {
-                    const float4 v = *t1_slot(t1s, rbase + k, d0 / 4 + x);
-                    xd[4 * x] = v.x; xd[4 * x + 1] = v.y; xd[4 * x + 2] = v.z; xd[4 * x + 3] = v.w;
-                }
-            };
-            int k = 0;
-            #pragma unroll 1
-            for (; k + KB <= nk; k += KB) {
-                float uc[KB][CB], xd[KB][DB];
-                #pragma unroll
-                for (int j = 0; j < KB; ++j) row_load(k + j, uc[j], xd[j]);
-                #pragma unroll
-                for (int j = 0; j < KB; ++j) row_fma(uc[j], xd[j]);
-            }
-            #pragma unroll 1
-            for (; k < nk; ++k) {
-                float uc[CB], xd[DB];
-                row_load(k, uc, xd);
-                row_fma(uc, xd);
-            }
-            fence_proxy_async_smem();   // the U slot's reads before its next bulk-copy write
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(t1free);
-                mbar_arrive(ufree);
-            }
-            if (++kt == a.n_kt) {
-                // the slab is complete: this thread's block of T2
-                const int64_t sl = grp * SG + gsl;
-                if (sl < a.S) {
-                    #pragma unroll
-                    for (int i = 0; i < CB; ++i) {
-                        const int c = c0 + i;
-                        if (c >= a.R2) continue;
-                        float *dst = a.T2 + (sl * a.R2 + c) * a.R3;
-                        #pragma unroll
-                        for (int x = 0; x < DB / 4; ++x) {
-                            const int d = d0 + 4 * x;
-                            if (vec) {
-                                if (d < a.R3)
-                                    *reinterpret_cast<float4 *>(dst + d) =
-                                        make_float4(acc[i][4 * x], acc[i][4 * x + 1], acc[i][4 * x + 2], acc[i][4 * x + 3]);
-                            } else {
-                                #pragma unroll
-                                for (int q = 0; q < 4; ++q)
-                                    if (d + q < a.R3) dst[d + q] = acc[i][4 * x + q];
-                            }
-                        }
-                    }
-                }
-                #pragma unroll
-                for (int i = 0; i < CB; ++i)
-                    #pragma unroll
-                    for (int q = 0; q < DB; ++q) acc[i][q] = 0.f;
-                kt = 0;
-                ++grp;
-            }
-        }
     }
 
     tc_fence_before();
     __syncthreads();
     if (warp == C::MMA_WARP) {
         tc_fence_after();
-        tmem_dealloc(tmem, C::TMEM_COLS);
+        tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -661,37 +698,73 @@ __global__ void pad_factor_kernel(const float *__restrict__ U, int64_t rows, int
 }  // namespace
 
 namespace {
-template <bool STORE, int SG>
+template <bool STORE, int SG, bool TC2>
 int launch_ttmc_variant(const TtmcArgs &a, int n_sm, void *stream) {
     using C = TtmcCfg;
-    cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel<STORE, SG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(C::SMEM));
+    cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel<STORE, SG, TC2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
     if (e != cudaSuccess) return int(e);
     const int64_t groups = (a.S + SG - 1) / SG;
     int64_t grid = groups < n_sm ? groups : n_sm;
     if (grid < 1) grid = 1;
-    ttmc_fused_kernel<STORE, SG><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
+    ttmc_fused_kernel<STORE, SG, TC2><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
     count_launch();
     return int(cudaGetLastError());
 }
 }  // namespace
 
 int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream) {
-    if (a.sg == 4) return launch_ttmc_variant<false, 4>(a, n_sm, stream);
-    if (a.sg == 2) return launch_ttmc_variant<false, 2>(a, n_sm, stream);
-    if (a.sg == 1) return launch_ttmc_variant<false, 1>(a, n_sm, stream);
-    return int(cudaErrorInvalidValue);
+    if (a.tc2) {
+        if (a.n_kt > kTtmcTc2MaxKt) return int(cudaErrorInvalidValue);
+        if (a.sg == 4) return launch_ttmc_variant<false, 4, true>(a, n_sm, stream);
+        if (a.sg == 2) return launch_ttmc_variant<false, 2, true>(a, n_sm, stream);
+        if (a.sg == 1) return launch_ttmc_variant<false, 1, true>(a, n_sm, stream);
+        return int(cudaErrorInvalidValue);
+    }
+    if (a.sg != 1) return int(cudaErrorInvalidValue);
+    return launch_ttmc_variant<false, 1, false>(a, n_sm, stream);
 }
 int launch_ttm_last_tc(const TtmcArgs &a, int n_sm, void *stream) {
-    if (a.sg != 1) return int(cudaErrorInvalidValue);
-    return launch_ttmc_variant<true, 1>(a, n_sm, stream);
+    if (a.sg != 1 || a.tc2) return int(cudaErrorInvalidValue);
+    return launch_ttmc_variant<true, 1, false>(a, n_sm, stream);
 }
+
+namespace {
+// U (rows x R) -> split BF16 blocks ((kt * 2 + p) * 2 + h) * 4096: 32 rows c x 64 k,
+// K-major 128-byte swizzle; hi = bf16(u), lo = bf16(u - hi); zero beyond rows x R.
+__global__ void u2_split_kernel(const float *__restrict__ U, int64_t rows, int R, unsigned char *__restrict__ out,
+                                int64_t total) {
+    for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int kq = int(idx & 63);
+        const int c = int((idx >> 6) & 31);
+        const int h = int((idx >> 11) & 1);
+        const int p = int((idx >> 12) & 1);
+        const int64_t kt = idx >> 13;
+        const int64_t k = kt * BM + h * 64 + kq;
+        const float v = (c < R && k < rows) ? U[k * R + c] : 0.f;
+        const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+        const __nv_bfloat16 e = p == 0 ? hb : __float2bfloat16_rn(v - __bfloat162float(hb));
+        *reinterpret_cast<__nv_bfloat16 *>(out + size_t(((kt * 2 + p) * 2 + h) * 4096) +
+                                           sw128_offset(uint32_t(c), uint32_t(kq))) = e;
+    }
+}
+}  // namespace
 
 int launch_ttmc_pad_factor(const float *U, int64_t rows, int R, float *out, int n_kt, void *stream) {
     const int64_t total = int64_t(n_kt) * BM * TtmcCfg::RP;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     pad_factor_kernel<<<unsigned(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(U, rows, R, out, total);
+    count_launch();
+    return int(cudaGetLastError());
+}
+
+int launch_ttmc_u2_split(const float *U, int64_t rows, int R, void *out, int n_kt, void *stream) {
+    if (n_kt < 1 || n_kt > kTtmcTc2MaxKt || R > TtmcCfg::RP) return int(cudaErrorInvalidValue);
+    const int64_t total = int64_t(n_kt) * 2 * 2 * 32 * 64;
+    u2_split_kernel<<<unsigned((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        U, rows, R, static_cast<unsigned char *>(out), total);
     count_launch();
     return int(cudaGetLastError());
 }
