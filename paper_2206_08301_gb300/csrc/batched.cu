@@ -313,7 +313,7 @@ deinsum_status upload_instances(deinsum_batch_s *b, const void *const *const *in
         const Inst &in = b->inst[size_t(i)];
         MttkrpArgs &a = A[i];
         std::memset(static_cast<void *>(&a), 0, sizeof(a));
-        mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, inputs[i][0], &a);
+        mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, inputs[i][0], &a, false);
         a.X = inputs[i][0];
         for (int k = 1; k < in.n_ops; ++k) a.U[in.opmode[k]] = inputs[i][k];
         a.Bsplit = b->ws + b->o_bsplit + b->bsplit_off[size_t(i)];
@@ -431,7 +431,7 @@ deinsum_status deinsum_plan_batched(int n, const char *const *einsums, const int
         for (int k = 1; k < in.n_ops; ++k) in.opmode[k] = deinsum_internal_operand_mode(b->plans[size_t(i)], k);
         MttkrpArgs tmp;
         std::memset(static_cast<void *>(&tmp), 0, sizeof(tmp));
-        mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, nullptr, &tmp);
+        mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, nullptr, &tmp, false);
         in.g = tmp.g;
         in.xbytes = 4.0;
         for (int m = 0; m < in.order; ++m) in.xbytes *= double(in.dims[m]);

@@ -182,7 +182,10 @@ void count_launch(int n = 1);
 int deinsum_internal_operand_mode(deinsum_plan_t pl, int k);
 
 // Row view (and TMA descriptor of X when possible) of a one-off split-BF16
-// MTTKRP, computed without heap or device allocation.
-bool mttkrp_prepare_oneoff(int order, const int64_t *dims, int mode, int R, const void *X, MttkrpArgs *a);
+// MTTKRP, computed without heap or device allocation.  allow_opack = false keeps
+// one outer index per tile (the batched kernel: its many small instances ran
+// slower with packing, 16.1 vs 14.4 ms for the 512-instance batch).
+bool mttkrp_prepare_oneoff(int order, const int64_t *dims, int mode, int R, const void *X, MttkrpArgs *a,
+                           bool allow_opack = true);
 
 }  // namespace deinsum

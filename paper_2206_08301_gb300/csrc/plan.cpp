@@ -54,6 +54,7 @@ struct deinsum_plan_s {
     int64_t t_S = 0;               // slabs
     int t_nkt = 0, t_nkb = 0;
     int t_sg = 1;                  // slabs per tile of the fused kernel
+    bool no_opack = false;         // keep one outer index per tile (the batched kernel's instances)
 
     // device state (after the first execute)
     int device = -1;
@@ -220,7 +221,7 @@ void build_mttkrp_geometry(deinsum_plan_s *pl) {
     // like the narrow p groups).  With 64 < I_n < 128 a tile holds one group anyway and
     // packing would only add index arithmetic.
     if (pl->prec == DEINSUM_PREC_SPLIT_BF16 && pl->dtype == DEINSUM_F32 && 2 * g.I <= DEINSUM_BM && g.O > 1 &&
-        (g.kcase == 1 || g.P == 1)) {
+        (g.kcase == 1 || g.P == 1) && !pl->no_opack) {
         g.opack = 1;
         g.narrow = 1;
         g.G = std::min<int64_t>(std::min<int64_t>(DEINSUM_BM / g.I, DEINSUM_GMAX), g.O);
@@ -818,9 +819,11 @@ int deinsum_internal_operand_mode(deinsum_plan_t pl, int k) { return pl->operand
 // Row view and TMA descriptor of a one-off split-BF16 MTTKRP, for the entry
 // point that allocates nothing: fills a->g and, when X allows it, a->xmap.
 // Uses a plan object on the stack whose containers stay empty (no heap use).
-bool mttkrp_prepare_oneoff(int order, const int64_t *dims, int mode, int R, const void *X, MttkrpArgs *a) {
+bool mttkrp_prepare_oneoff(int order, const int64_t *dims, int mode, int R, const void *X, MttkrpArgs *a,
+                           bool allow_opack) {
     deinsum_plan_s pl;
     pl.kind = DEINSUM_KIND_MTTKRP;
+    pl.no_opack = !allow_opack;
     pl.order = order;
     pl.mode = mode;
     pl.dtype = DEINSUM_F32;
