@@ -587,12 +587,33 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     tmem_ld16(taddr + uint32_t(c), hi);
                     tmem_ld16(taddr + uint32_t(RP + c), lo);
                     tmem_wait_ld();
-                    #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int col = c + q;
-                        float w = __shfl_sync(0xffffffffu, col < 32 ? w0 : w1, col & 31);
-                        if (lane_weights) w *= rv ? lrow[col] : 0.f;
-                        acc[col] = fmaf(w, __uint_as_float(hi[q]) + __uint_as_float(lo[q]), acc[col]);
+                    if constexpr (OP) {
+                        // packed outer indices (per-row weights): this thread's row-group row
+                        // (zero for an invalid row) times the row common to the tile, read as
+                        // float4 from the slot (both are zero past R)
+                        #pragma unroll
+                        for (int q4 = 0; q4 < 4; ++q4) {
+                            const int col = c + 4 * q4;
+                            float4 w4 = rv ? *reinterpret_cast<const float4 *>(lrow + col)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (has_common) {
+                                const float4 cw = *reinterpret_cast<const float4 *>(wsl + col);
+                                w4.x *= cw.x; w4.y *= cw.y; w4.z *= cw.z; w4.w *= cw.w;
+                            }
+                            const int q = 4 * q4;
+                            acc[col] = fmaf(w4.x, __uint_as_float(hi[q]) + __uint_as_float(lo[q]), acc[col]);
+                            acc[col + 1] = fmaf(w4.y, __uint_as_float(hi[q + 1]) + __uint_as_float(lo[q + 1]), acc[col + 1]);
+                            acc[col + 2] = fmaf(w4.z, __uint_as_float(hi[q + 2]) + __uint_as_float(lo[q + 2]), acc[col + 2]);
+                            acc[col + 3] = fmaf(w4.w, __uint_as_float(hi[q + 3]) + __uint_as_float(lo[q + 3]), acc[col + 3]);
+                        }
+                    } else {
+                        #pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int col = c + q;
+                            float w = __shfl_sync(0xffffffffu, col < 32 ? w0 : w1, col & 31);
+                            if (lane_weights) w *= rv ? lrow[col] : 0.f;
+                            acc[col] = fmaf(w, __uint_as_float(hi[q]) + __uint_as_float(lo[q]), acc[col]);
+                        }
                     }
                 }
                 tc_fence_before();
