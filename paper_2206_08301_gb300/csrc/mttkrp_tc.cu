@@ -304,9 +304,12 @@ __device__ __forceinline__ void load_fg_weights(const MttkrpArgs &a, int64_t til
     if (nl) bulk_g2s(dst + rowb, a.Lw + p0 * g.R_pad, nl * rowb, bar);
 }
 
-template <int RP, bool OP, bool MN>
+// OP: outer indices packed into the tile; MN: MN-major A operand (the last mode);
+// PW: per-row weights (packed outer indices, or narrow tiles of several p with L rows).
+template <int RP, bool OP, bool MN, bool PW>
 __global__ void __launch_bounds__(TcCfg<RP>::THREADS, 1)
 mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
+    static_assert(!OP || PW, "packed outer indices weight every row group");
     using C = TcCfg<RP>;
     constexpr int RS = C::RS, AS = C::AS;
     const MttkrpGeom &g = a.g;
@@ -519,7 +522,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         // ------------------------------------------------------------- epilogue
         const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
         const int l = quad * 32 + lane;            // tile row of this thread
-        const bool lane_weights = OP || (g.kcase == 0 && g.narrow && g.n_lmodes > 0);  // per-row weights
+        constexpr bool lane_weights = PW;          // per-row weights (the launcher's choice)
         const bool has_common = OP ? g.n_lmodes > 0 : g.n_outer > 0;   // a row common to the tile
         const int lg = g.narrow ? int(l / g.I) : 0;   // narrow: p offset of row l within its tile
         Iter it;
@@ -587,10 +590,10 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     tmem_ld16(taddr + uint32_t(c), hi);
                     tmem_ld16(taddr + uint32_t(RP + c), lo);
                     tmem_wait_ld();
-                    if constexpr (OP) {
-                        // packed outer indices (per-row weights): this thread's row-group row
-                        // (zero for an invalid row) times the row common to the tile, read as
-                        // float4 from the slot (both are zero past R)
+                    if constexpr (PW) {
+                        // per-row weights: this thread's row-group row (zero for an invalid
+                        // row) times the row common to the tile, read as float4 from the slot
+                        // (both are zero past R)
                         #pragma unroll
                         for (int q4 = 0; q4 < 4; ++q4) {
                             const int col = c + 4 * q4;
@@ -610,8 +613,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                         #pragma unroll
                         for (int q = 0; q < 16; ++q) {
                             const int col = c + q;
-                            float w = __shfl_sync(0xffffffffu, col < 32 ? w0 : w1, col & 31);
-                            if (lane_weights) w *= rv ? lrow[col] : 0.f;
+                            const float w = __shfl_sync(0xffffffffu, col < 32 ? w0 : w1, col & 31);
                             acc[col] = fmaf(w, __uint_as_float(hi[q]) + __uint_as_float(lo[q]), acc[col]);
                         }
                     }
@@ -662,27 +664,31 @@ __global__ void split_inner_factor_kernel(const float *__restrict__ U, unsigned 
     }
 }
 
-template <int RP, bool OP, bool MN>
+template <int RP, bool OP, bool MN, bool PW>
 int launch_tc_rp_op(const MttkrpArgs &a, int n_sm, void *stream) {
     using C = TcCfg<RP>;
-    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_kernel<RP, OP, MN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(C::SMEM));
+    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_kernel<RP, OP, MN, PW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
     if (e != cudaSuccess) return int(e);
     int64_t grid = a.n_units < n_sm ? a.n_units : n_sm;
     if (grid < 1) grid = 1;
-    mttkrp_tc_kernel<RP, OP, MN><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
+    mttkrp_tc_kernel<RP, OP, MN, PW><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
     count_launch();
     return int(cudaGetLastError());
 }
 
-// case 1 (rows contiguous in memory) takes the MN-major A operand
+// case 1 (rows contiguous in memory) takes the MN-major A operand; tiles whose row
+// groups carry their own weights (packed outer indices, or several p with L rows)
+// the per-row-weight epilogue
 template <int RP>
 int launch_tc_rp(const MttkrpArgs &a, int n_sm, void *stream) {
-    if (a.g.kcase == 1)
-        return a.g.opack ? launch_tc_rp_op<RP, true, true>(a, n_sm, stream)
-                         : launch_tc_rp_op<RP, false, true>(a, n_sm, stream);
-    return a.g.opack ? launch_tc_rp_op<RP, true, false>(a, n_sm, stream)
-                     : launch_tc_rp_op<RP, false, false>(a, n_sm, stream);
+    const MttkrpGeom &g = a.g;
+    if (g.kcase == 1)
+        return g.opack ? launch_tc_rp_op<RP, true, true, true>(a, n_sm, stream)
+                       : launch_tc_rp_op<RP, false, true, false>(a, n_sm, stream);
+    if (g.opack) return launch_tc_rp_op<RP, true, false, true>(a, n_sm, stream);
+    if (g.narrow && g.n_lmodes > 0) return launch_tc_rp_op<RP, false, false, true>(a, n_sm, stream);
+    return launch_tc_rp_op<RP, false, false, false>(a, n_sm, stream);
 }
 
 // ---------------------------------------------------------------------------
