@@ -387,7 +387,9 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 const uint32_t rj = uint32_t(chunk / RS);
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, a.status))) break;
                 const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES);
-                if (MN) conv_read_smem_mn(mp, a.raw_pitch, raw, pt, v);
+                if (MN && !OP && a.raw_pitch == BM) conv_read_smem_mn128(raw, pt, v);
+                else if (MN) conv_read_smem_mn(mp, a.raw_pitch, raw, pt, v);
+                else if (!g.narrow) conv_read_smem_wide(raw, pt, v);
                 else conv_read_smem_t<OP>(a.g, a.raw_pitch, raw, pt, v);
                 // hand the raw stage back to the TMA warp before the split, so that its next
                 // load overlaps it: the proxy fence orders these generic reads before that

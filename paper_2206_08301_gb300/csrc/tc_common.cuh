@@ -87,6 +87,13 @@ __device__ __forceinline__ void conv_read_smem_t(const MttkrpGeom &g, int pitch,
     }
 }
 
+// Case 0 with a full 128-row tile (not narrow): plain float4 reads, rows 16 apart.
+__device__ __forceinline__ void conv_read_smem_wide(const float *raw, int pt, float4 (&v)[8]) {
+    const float4 *r = reinterpret_cast<const float4 *>(raw + (pt >> 4) * BK) + (pt & 15);
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = r[j * (16 * BK / 4)];
+}
+
 // run-time choice (kernels that serve both kinds of tile)
 __device__ __forceinline__ void conv_read_smem(const MttkrpGeom &g, int pitch, const float *raw, int pt,
                                                float4 (&v)[8]) {
@@ -142,14 +149,24 @@ __device__ __forceinline__ void conv_read_smem_mn(const MnPos &p, int pitch, con
         }
     }
 }
+// The common case (one group of 128 rows: pitch 128, every row inside): plain
+// float4 reads 512 bytes apart.
+__device__ __forceinline__ void conv_read_smem_mn128(const float *raw, int pt, float4 (&v)[8]) {
+    const float4 *r = reinterpret_cast<const float4 *>(raw + 8 * (pt >> 5) * BM) + (pt & 31);
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = r[j * (BM / 4)];
+}
 // Split and store: lanes 0-15 fill one 128-byte k-row of the first 64-row atom,
 // lanes 16-31 the same k-row of the second (two wavefronts per 8-byte store).
+// The warp's eight k (one 8-k group) are one atom row each: offset = atom base
+// + 128 j + 16 (c ^ j) + 8 (lane & 1), c the lane's 16-byte chunk.
 __device__ __forceinline__ void conv_store_mn(int pt, uint32_t a_hi, uint32_t a_lo, const float4 (&v)[8]) {
-    const int kb0 = 8 * (pt >> 5);
-    const uint32_t m0 = uint32_t(4 * (pt & 31));
+    const int lane = pt & 31;
+    const uint32_t base = uint32_t((pt >> 5) * 2 + (lane >> 4)) * 1024u + uint32_t(lane & 1) * 8u;
+    const uint32_t c = uint32_t((lane & 15) >> 1);
     #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const uint32_t off = sw128_mn_offset(m0, uint32_t(kb0 + j));
+        const uint32_t off = base + uint32_t(j) * 128u + ((c ^ uint32_t(j)) << 4);
         uint32_t h0, l0, h1, l1;
         split2(v[j].x, v[j].y, h0, l0);
         split2(v[j].z, v[j].w, h1, l1);
@@ -162,12 +179,14 @@ __device__ __forceinline__ void conv_store_mn(int pt, uint32_t a_hi, uint32_t a_
 __device__ __forceinline__ void conv_store(const MttkrpGeom &g, int pt, uint32_t a_hi, uint32_t a_lo,
                                            const float4 (&v)[8]) {
     if (g.kcase == 0) {
-        // 16 lanes cover one 128-byte swizzled row: conflict-free 8-byte stores
+        // 16 lanes cover one 128-byte swizzled row: conflict-free 8-byte stores.  Rows
+        // rsub + 16 j share row & 7, so sw128_offset(rsub + 16 j, 4 k4) = base + 2048 j.
         const int k4 = pt & 15, rsub = pt >> 4;
+        const uint32_t base = uint32_t(rsub >> 3) * 1024u + uint32_t(rsub & 7) * 128u +
+                              ((uint32_t((k4 >> 1) ^ (rsub & 7)) & 7u) << 4) + uint32_t(k4 & 1) * 8u;
         #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const uint32_t row = uint32_t(rsub + 16 * j);
-            const uint32_t off = sw128_offset(row, uint32_t(4 * k4));
+            const uint32_t off = base + 2048u * uint32_t(j);
             uint32_t h0, l0, h1, l1;
             split2(v[j].x, v[j].y, h0, l0);
             split2(v[j].z, v[j].w, h1, l1);

@@ -220,7 +220,9 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             const int rs = int(chunk % RS);
             const uint32_t rj = uint32_t(chunk / RS);
             if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
-            conv_read_smem_t<false>(a.g, BM, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
+            const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES);
+            if (!a.g.narrow) conv_read_smem_wide(raw, pt, v);
+            else conv_read_smem_t<false>(a.g, BM, raw, pt, v);
             // hand the raw stage back to the TMA warp before the split, so that its next
             // load overlaps it: the proxy fence orders these generic reads before that
             // async-proxy write (an mbarrier release alone does not)
