@@ -389,7 +389,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES);
                 if (MN && !OP && a.raw_pitch == BM) conv_read_smem_mn128(raw, pt, v);
                 else if (MN) conv_read_smem_mn(mp, a.raw_pitch, raw, pt, v);
-                else if (!g.narrow) conv_read_smem_wide(raw, pt, v);
+                else if (!g.narrow || g.G * g.I == BM) conv_read_smem_wide(raw, pt, v);   // all 128 rows
                 else conv_read_smem_t<OP>(a.g, a.raw_pitch, raw, pt, v);
                 // hand the raw stage back to the TMA warp before the split, so that its next
                 // load overlaps it: the proxy fence orders these generic reads before that
@@ -830,7 +830,9 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 const uint32_t rj = uint32_t(tchunk / RS);
                 ++tchunk;
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
-                conv_read_smem(a, reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES), pt, v);
+                const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES);
+                if (a.g.kcase == 0 && (!a.g.narrow || a.g.G * a.g.I == BM)) conv_read_smem_wide(raw, pt, v);
+                else conv_read_smem(a, raw, pt, v);
                 fence_proxy_async_smem();   // these generic reads before the stage's next TMA write
                 __syncwarp();
                 if (lane == 0) mbar_arrive(raw_empty(rs));

@@ -116,11 +116,13 @@ struct MnPos {
     int off[4];      // raw offsets of the four rows at k = 0
     uint32_t valid;  // bit q: row 4 lane + q is inside the groups
     bool vec;        // pitch % 4 == 0: the four rows are one aligned float4
+    bool full;       // vec, and groups x pitch >= 128: every row of the tile is inside (same for all threads)
 };
 __device__ __forceinline__ MnPos mn_pos(int pitch, int groups, int pt) {
     MnPos p;
     p.valid = 0;
     p.vec = (pitch & 3) == 0;
+    p.full = p.vec && groups * pitch >= BM;
     const int m0 = 4 * (pt & 31);
     #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -133,7 +135,12 @@ __device__ __forceinline__ MnPos mn_pos(int pitch, int groups, int pt) {
 __device__ __forceinline__ void conv_read_smem_mn(const MnPos &p, int pitch, const float *raw, int pt,
                                                   float4 (&v)[8]) {
     const int kb0 = 8 * (pt >> 5);
-    if (p.vec) {
+    if (p.full) {
+        // every row of the tile is inside a group: unconditional float4 reads
+        const float *r = raw + p.off[0] + kb0 * pitch;
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = *reinterpret_cast<const float4 *>(r + j * pitch);
+    } else if (p.vec) {
         const bool rv = p.valid != 0;
         #pragma unroll
         for (int j = 0; j < 8; ++j)
