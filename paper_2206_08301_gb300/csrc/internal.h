@@ -179,6 +179,35 @@ int launch_ttm_plain_f64(const double *X, const double *U, double *Y, int64_t A,
 
 void count_launch(int n = 1);
 
+// Units per column of 128 output rows (each column's fiber groups cut into that many
+// contiguous units) such that the busiest of `target` persistent CTAs, which take units
+// round-robin, is as close as possible to the mean: it runs ceil(units / target) units
+// of up to ceil(fg_per_col / per_col) fiber groups.  The smallest count within 1 % of
+// the best is taken (fewer partial blocks to reduce); at most max_units units.
+inline int64_t balanced_units_per_col(int64_t n_cols, int64_t fg_per_col, int64_t target, int64_t max_units) {
+    if (n_cols < 1 || fg_per_col < 1 || target < 1) return 1;
+    const double mean = double(n_cols) * double(fg_per_col) / double(target);
+    auto eff = [&](int64_t p) {
+        const int64_t units = n_cols * p;
+        const int64_t waves = (units + target - 1) / target;
+        const int64_t fg_unit = (fg_per_col + p - 1) / p;
+        return mean / double(waves * fg_unit);
+    };
+    int64_t lo = target / n_cols;
+    if (lo < 1) lo = 1;
+    if (lo > fg_per_col) lo = fg_per_col;
+    int64_t best = lo;
+    double best_eff = eff(lo);
+    for (int64_t p = lo + 1; p <= 8 * lo + 8 && p <= fg_per_col && n_cols * p <= max_units; ++p) {
+        const double e = eff(p);
+        if (e > best_eff + 0.01) {
+            best = p;
+            best_eff = e;
+        }
+    }
+    return best;
+}
+
 int deinsum_internal_operand_mode(deinsum_plan_t pl, int k);
 
 // Row view (and TMA descriptor of X when possible) of a one-off split-BF16

@@ -11,6 +11,7 @@
 // on every GPU that loads it and is held until the process exits.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -108,9 +109,9 @@ extern "C" deinsum_status deinsum_mttkrp_noalloc(int order, const int64_t *dims,
     std::memset(&a, 0, sizeof(a));
     mttkrp_prepare_oneoff(order, dims, mode, rank, X, &a);
     const MttkrpGeom &g = a.g;
-    const int64_t per_col_want = (int64_t(n_sm) + g.n_cols - 1) / g.n_cols;
-    int64_t per_col = per_col_want < 1 ? 1 : per_col_want;
-    if (per_col > g.fg_per_col) per_col = g.fg_per_col;
+    const int64_t max_units_here = std::min<int64_t>(
+        kMaxUnits, int64_t(kPartialBytes / (size_t(DEINSUM_BM) * size_t(g.R_pad) * 4)));
+    const int64_t per_col = balanced_units_per_col(g.n_cols, g.fg_per_col, n_sm, max_units_here);
     const int64_t n_units = g.n_cols * per_col;
     const size_t bsplit_bytes = size_t(g.n_kb) * 2 * size_t(g.R_pad) * DEINSUM_BK * 2;
     const size_t wtab_floats_l = weight_table_floats_l(g);

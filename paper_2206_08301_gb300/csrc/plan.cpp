@@ -239,9 +239,8 @@ void build_schedule(deinsum_plan_s *pl, int64_t target) {
     const MttkrpGeom &g = pl->geom;
     pl->units.clear();
     pl->col_unit_begin.assign(size_t(g.n_cols + 1), 0);
-    // at most `target` units (one wave of resident CTAs) unless there are more columns
-    int64_t per_col = std::max<int64_t>(1, target / g.n_cols);
-    per_col = std::min<int64_t>(per_col, g.fg_per_col);
+    // whole waves of `target` persistent CTAs, as evenly loaded as the fiber-group counts allow
+    const int64_t per_col = balanced_units_per_col(g.n_cols, g.fg_per_col, target, 8 * target);
     for (int64_t c = 0; c < g.n_cols; ++c) {
         pl->col_unit_begin[size_t(c)] = int64_t(pl->units.size() / 3);
         for (int64_t s = 0; s < per_col; ++s) {
