@@ -405,7 +405,9 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             const int as = int(chunk % AS);
             const uint32_t aj = uint32_t(chunk / AS);
             if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, a.status))) break;
-            if (issuer) {
+            // with a single inner chunk (n_kb = 1) every chunk uses the same factor tile:
+            // each operand stage copies it once and keeps it
+            if (issuer && (g.n_kb != 1 || aj == 0)) {
                 mbar_arrive_expect_tx(bfull(as), C::B_BYTES);
                 bulk_g2s(b_t(as), bsrc + size_t(it.kb) * C::B_BYTES, C::B_BYTES, bfull(as));
                 bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
@@ -494,7 +496,10 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     const int s = int(chunk % AS);
                     const uint32_t j = uint32_t(chunk / AS);
                     if (!mbar_wait(a_full(s), j & 1u, abort_flag, a.status) ||
-                        !mbar_wait(bfull(s), j & 1u, abort_flag, a.status)) { ok = false; break; }
+                        ((g.n_kb != 1 || j == 0) && !mbar_wait(bfull(s), j & 1u, abort_flag, a.status))) {
+                        ok = false;
+                        break;
+                    }
                     tc_fence_after();
                     const uint64_t dh = MN ? desc_mnmajor_sw128(a_hi(s), kMnAtomStride, kMnKGroupStride)
                                            : desc_kmajor_sw128(a_hi(s));

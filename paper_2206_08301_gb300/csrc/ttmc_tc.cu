@@ -232,7 +232,9 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             const int as = int(chunk % AS);
             const uint32_t aj = uint32_t(chunk / AS);
             if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status))) break;
-            if (issuer) {
+            // a single l chunk (n_kb = 1): every chunk uses the same factor tile, which each
+            // operand stage copies once and keeps
+            if (issuer && (a.n_kb != 1 || aj == 0)) {
                 mbar_arrive_expect_tx(bfull(as), C::B_BYTES);
                 bulk_g2s(b_t(as), bsrc + size_t(it.kb) * C::B_BYTES, C::B_BYTES, bfull(as));
                 bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
@@ -289,7 +291,10 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                     const int s = int(chunk % AS);
                     const uint32_t j = uint32_t(chunk / AS);
                     if (!mbar_wait(a_full(s), j & 1u, abort_flag, status) ||
-                        !mbar_wait(bfull(s), j & 1u, abort_flag, status)) { ok = false; break; }
+                        ((a.n_kb != 1 || j == 0) && !mbar_wait(bfull(s), j & 1u, abort_flag, status))) {
+                        ok = false;
+                        break;
+                    }
                     tc_fence_after();
                     const uint64_t dh = desc_kmajor_sw128(a_hi(s));
                     const uint64_t dl = desc_kmajor_sw128(a_lo(s));
