@@ -16,7 +16,8 @@
 //     consecutive rows are adjacent in memory.
 //
 // The inner contraction over k runs in chunks of 64 (BK).  For a fixed tile
-// and outer index o ("fiber group"), the chunks are accumulated into
+// and outer index o (and, on the tensor-core path, a segment of at most 16
+// chunks of k: a "fiber group"), the chunks are accumulated into
 // T[row, r] = sum_k X[row, (o, k)] U_inner[k, r]; the fiber group is then
 // folded into the row's accumulator with the weight
 //   w[row, r] = L(p(row))[r] * Ofac(o)[r],
@@ -68,6 +69,8 @@ struct MttkrpGeom {
     int opack;            // tensor-core path, I <= 64 and no p to pack (case 0 with P = 1, or
                           // case 1): tile rows are (o_local, i_n), G >= 2 consecutive outer indices
     int64_t O_iter;       // outer indices iterated per tile: O, or 1 with opack (folded into the tile)
+    int kseg;             // tensor-core path: segments of the inner range per (tile, o) -- each a fiber
+    int n_kb_seg;         //   group of at most n_kb_seg chunks, so that TMEM accumulates <= 1024 k
 };
 
 struct MttkrpArgs {
@@ -81,6 +84,8 @@ struct MttkrpArgs {
     MttkrpGeom g;
     const void *X;
     const void *U[DEINSUM_MAX_ORDER];  // factor of each mode (U[mode] unused)
+    const void *Uk2;                   // merged inner mode: the inner factor is the Khatri-Rao
+    int64_t K_minor;                   //   product, row k = U[inner][k / K_minor] * Uk2[k % K_minor]
     const void *Bsplit;                // split-BF16 tiles of the inner factor (TC path)
     float *Lw;                         // TC path, n_lmodes > 0: P x R_pad row weights (weight_tables)
     float *Ow;                         // TC path, n_outer > 0:  O x R_pad fiber weights

@@ -64,17 +64,25 @@ template <int RP> struct TcCfg {
 
 struct Iter {
     int64_t u, col, fg, fg1, tile, o;
-    int kb;
+    int seg, kb, kb_lo, kb_hi;   // kb: the chunk's index along the inner mode; [kb_lo, kb_hi): the group's
     bool done;
+    __device__ __forceinline__ void set_fg(const MttkrpGeom &g) {
+        const int64_t per_tile = g.O_iter * g.kseg;
+        tile = fg / per_tile;
+        const int64_t rem = fg - tile * per_tile;
+        o = rem / g.kseg;
+        seg = int(rem - o * g.kseg);
+        kb_lo = seg * g.n_kb_seg;
+        kb_hi = kb_lo + g.n_kb_seg < g.n_kb ? kb_lo + g.n_kb_seg : g.n_kb;
+        kb = kb_lo;
+    }
     __device__ __forceinline__ void load_unit(const MttkrpArgs &a) {
         while (u < a.n_units) {
             col = a.units[3 * u];
             fg = a.units[3 * u + 1];
             fg1 = a.units[3 * u + 2];
             if (fg < fg1) {
-                kb = 0;
-                tile = fg / a.g.O_iter;
-                o = fg - tile * a.g.O_iter;
+                set_fg(a.g);
                 done = false;
                 return;
             }
@@ -86,16 +94,19 @@ struct Iter {
         u = blockIdx.x;
         load_unit(a);
     }
-    // advance by one chunk
-    __device__ __forceinline__ void next(const MttkrpArgs &a) {
-        if (++kb < a.g.n_kb) return;
-        kb = 0;
+    // to the next fiber group
+    __device__ __forceinline__ void next_fg(const MttkrpArgs &a) {
         if (++fg < fg1) {
-            if (++o == a.g.O_iter) { o = 0; ++tile; }
+            set_fg(a.g);
             return;
         }
         u += gridDim.x;
         load_unit(a);
+    }
+    // advance by one chunk
+    __device__ __forceinline__ void next(const MttkrpArgs &a) {
+        if (++kb < kb_hi) return;
+        next_fg(a);
     }
 };
 
@@ -435,7 +446,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             uint32_t last_par = 0, last_wpar = 0;
             int64_t fgi = 0;
             for (int64_t chunk = 0; !it.done; ++chunk) {
-                if (it.kb == 0) {
+                if (it.kb == it.kb_lo) {
                     const int ws = int(fgi % C::WSLOTS);
                     const uint32_t wj = uint32_t(fgi / C::WSLOTS);
                     if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, a.status)) break;
@@ -475,24 +486,18 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         // -------------------------------------------------------------- MMA issue
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_bf16_f32(BM, C::N) | (MN ? kIdescAMnMajor : 0u);
-            int64_t chunk = 0, nfg = 0;
-            {   // count the fiber groups of this CTA
-                Iter it;
-                it.init(a);
-                while (!it.done) {
-                    nfg += it.fg1 - it.fg;
-                    it.u += gridDim.x;
-                    it.load_unit(a);
-                }
-            }
+            int64_t chunk = 0;
+            Iter itm;   // this CTA's fiber groups, for their chunk counts
+            itm.init(a);
             bool ok = true;
-            for (int64_t fgi = 0; ok && fgi < nfg; ++fgi) {
+            for (int64_t fgi = 0; ok && !itm.done; ++fgi, itm.next_fg(a)) {
+                const int nkb = itm.kb_hi - itm.kb_lo;
                 const int b = int(fgi & 1);
                 const uint32_t jb = uint32_t(fgi >> 1);
                 if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, a.status)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dcol = tmem + uint32_t(b * C::N);
-                for (int kb = 0; kb < g.n_kb; ++kb) {
+                for (int kb = 0; kb < nkb; ++kb) {
                     const int s = int(chunk % AS);
                     const uint32_t j = uint32_t(chunk / AS);
                     if (!mbar_wait(a_full(s), j & 1u, abort_flag, a.status) ||
@@ -637,7 +642,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     folded = 0;
                     flush();
                 }
-                for (int kb = 0; kb < g.n_kb; ++kb) it.next(a);  // to the next fiber group
+                it.next_fg(a);   // to the next fiber group
             }
             if (!ok) break;
             flush();
@@ -654,8 +659,10 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
 
 // Inner factor -> split BF16 tiles: tile kb holds rows n < RP = hi(U[64 kb + k, n]),
 // rows RP + n = lo(...), zero beyond R and beyond K_in, in the 128B-swizzled K-major layout.
-__global__ void split_inner_factor_kernel(const float *__restrict__ U, unsigned char *__restrict__ out,
-                                          int64_t K_in, int R, int RP, int n_kb) {
+// With Ub (a merged inner mode) the factor row k is the Khatri-Rao row
+// U[k / Ib, n] * Ub[k % Ib, n], formed in FP32.
+__global__ void split_inner_factor_kernel(const float *__restrict__ U, const float *__restrict__ Ub, int64_t Ib,
+                                          unsigned char *__restrict__ out, int64_t K_in, int R, int RP, int n_kb) {
     const int64_t total = int64_t(n_kb) * 2 * RP * BK;
     for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
          idx += int64_t(gridDim.x) * blockDim.x) {
@@ -664,7 +671,8 @@ __global__ void split_inner_factor_kernel(const float *__restrict__ U, unsigned 
         const int64_t kb = idx / (int64_t(BK) * 2 * RP);
         const int r = n % RP;
         const int64_t kr = kb * BK + k;
-        const float v = (r < R && kr < K_in) ? U[kr * R + r] : 0.f;
+        float v = 0.f;
+        if (r < R && kr < K_in) v = Ub ? U[(kr / Ib) * R + r] * Ub[(kr % Ib) * R + r] : U[kr * R + r];
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         const __nv_bfloat16 e = n < RP ? h : __float2bfloat16_rn(v - __bfloat162float(h));
         *reinterpret_cast<__nv_bfloat16 *>(out + size_t(kb) * (2 * RP * BK * 2) + sw128_offset(uint32_t(n), uint32_t(k))) = e;
@@ -749,6 +757,7 @@ struct BIter {
     __device__ __forceinline__ Iter as_iter() const {
         Iter t;
         t.u = u; t.col = col; t.fg = fg; t.fg1 = fg1; t.tile = tile; t.o = o; t.kb = kb; t.done = done;
+        t.seg = 0; t.kb_lo = 0; t.kb_hi = a->g.n_kb;
         return t;
     }
 };
@@ -1107,7 +1116,8 @@ int launch_split_inner_factor(const MttkrpArgs &a, void *bsplit, void *stream) {
     int64_t blocks = (total + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     split_inner_factor_kernel<<<unsigned(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        static_cast<const float *>(a.U[inner]), static_cast<unsigned char *>(bsplit), g.K_in, g.R, g.R_pad, g.n_kb);
+        static_cast<const float *>(a.U[inner]), static_cast<const float *>(a.Uk2), a.K_minor > 0 ? a.K_minor : 1,
+        static_cast<unsigned char *>(bsplit), g.K_in, g.R, g.R_pad, g.n_kb);
     count_launch();
     return int(cudaGetLastError());
 }

@@ -55,6 +55,8 @@ struct deinsum_plan_s {
     int t_nkt = 0, t_nkb = 0;
     int t_sg = 1;                  // slabs per tile of the fused kernel
     bool no_opack = false;         // keep one outer index per tile (the batched kernel's instances)
+    int merge = 0;                 // tensor-core MTTKRP: the inner mode merged with its neighbour (see
+                                   // choose_inner_merge); geom is then the order-(N-1) view
 
     // device state (after the first execute)
     int device = -1;
@@ -158,16 +160,35 @@ int letter_index(const Parsed &p, char c) {
 
 int pad_rank(int R) { return R <= 16 ? 16 : (R <= 32 ? 32 : 64); }
 
-// The row view and schedule of the MTTKRP kernels (see internal.h).
+// Chunks of 64 k one fiber group accumulates in TMEM at most.  The accumulation over the
+// k steps of a group is where the split-BF16 path loses accuracy as groups grow: 16
+// chunks (64 MMA k-steps) give a relative error of about 4e-6, 64 chunks about 1.1e-5.
+constexpr int kMaxSegChunks = 16;
+
+// The row view and schedule of the MTTKRP kernels (see internal.h).  With pl->merge the
+// view is the order-(N-1) tensor in which the inner mode and its neighbour are one mode
+// (modes N-2, N-1 for n < N-2; N-3, N-2 for n = N-1): the MTTKRP regrouped by the
+// einsum's associativity, the merged factor being the Khatri-Rao product of the two.
 void build_mttkrp_geometry(deinsum_plan_s *pl) {
     MttkrpGeom &g = pl->geom;
     std::memset(&g, 0, sizeof(g));
-    const int N = pl->order, n = pl->mode;
-    g.order = N;
-    g.mode = n;
+    int N = pl->order, n = pl->mode;
     g.R = int(pl->ranks[(n + 1) % N]);
     g.R_pad = pad_rank(g.R);
     for (int m = 0; m < N; ++m) g.dims[m] = pl->dims[m];
+    if (pl->merge) {
+        if (n < N - 2) {
+            g.dims[N - 2] *= g.dims[N - 1];
+        } else {
+            g.dims[N - 3] *= g.dims[N - 2];
+            g.dims[N - 2] = g.dims[N - 1];
+            n = N - 2;
+        }
+        g.dims[N - 1] = 0;
+        --N;
+    }
+    g.order = N;
+    g.mode = n;
     g.P = 1;
     g.Q = 1;
     for (int m = 0; m < n; ++m) g.P *= g.dims[m];
@@ -230,7 +251,15 @@ void build_mttkrp_geometry(deinsum_plan_s *pl) {
         g.rows_per_col = g.I;
         g.O_iter = 1;
     }
-    g.fg_per_col = g.tiles_per_col * g.O_iter;
+    // tensor-core path: at most 16 chunks (1024 k) accumulate in TMEM per fiber group; a
+    // longer inner range is cut into segments, each its own fiber group (same weights)
+    g.kseg = 1;
+    g.n_kb_seg = g.n_kb;
+    if (pl->prec == DEINSUM_PREC_SPLIT_BF16 && pl->dtype == DEINSUM_F32 && !pl->no_opack && g.n_kb > kMaxSegChunks) {
+        g.n_kb_seg = kMaxSegChunks;
+        g.kseg = (g.n_kb + kMaxSegChunks - 1) / kMaxSegChunks;
+    }
+    g.fg_per_col = g.tiles_per_col * g.O_iter * g.kseg;
 }
 
 // Split every column's fiber groups into contiguous units, about `target`
@@ -484,6 +513,32 @@ void plan_ttmc_chain(deinsum_plan_s *pl) {
 // T2 = [I_0 .. I_{N-3}, R_{N-2}, R_{N-1}].  Offered when the kept mode is
 // below N-2 and R_{N-2}, R_{N-1} <= 32; I_{N-1} must be a multiple of 4 (rows of
 // X 16-byte aligned for the tensor map).
+// Merge the inner mode of a tensor-core MTTKRP with its neighbour when the inner mode is
+// short (at most two 64-wide chunks, so that every fiber group would be one or two chunks
+// and the epilogue and its handshakes would run per 32 KB of X) and the merged view still
+// fills its tiles: rows of 128 or more, several leading indices p, or outer indices left
+// to pack.  Split BF16 only.
+void choose_inner_merge(deinsum_plan_s *pl) {
+    pl->merge = 0;
+    if (pl->kind != DEINSUM_KIND_MTTKRP || pl->prec != DEINSUM_PREC_SPLIT_BF16 || pl->dtype != DEINSUM_F32) return;
+    const int N = pl->order, n = pl->mode;
+    if (N < 3) return;
+    const int64_t lim = int64_t(1) << 31;
+    int64_t P = 1, O = 1;
+    const int64_t I = pl->dims[n];
+    if (n < N - 2) {
+        if (pl->dims[N - 1] > 2 * DEINSUM_BK || pl->dims[N - 2] * pl->dims[N - 1] >= lim) return;
+        for (int m = 0; m < n; ++m) P *= pl->dims[m];
+        for (int m = n + 1; m < N - 2; ++m) O *= pl->dims[m];
+    } else if (n == N - 1) {
+        if (pl->dims[N - 2] > 2 * DEINSUM_BK || pl->dims[N - 3] * pl->dims[N - 2] >= lim) return;
+        for (int m = 0; m < N - 3; ++m) O *= pl->dims[m];
+    } else {
+        return;
+    }
+    if (I >= DEINSUM_BM || P >= 2 || O >= 2) pl->merge = 1;
+}
+
 deinsum_status plan_ttmc_fused(deinsum_plan_s *pl) {
     const int N = pl->order, n = pl->mode;
     if (N < 3 || n >= N - 2) return DEINSUM_ERR_UNSUPPORTED;
@@ -627,6 +682,13 @@ deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, voi
     a.X = inputs[0];
     for (int k = 1; k < pl->n_operands; ++k)
         if (pl->operand_mode[k] >= 0) a.U[pl->operand_mode[k]] = inputs[k];
+    if (pl->merge) {   // the view's inner factor: Khatri-Rao of the two merged modes
+        const int N = pl->order;
+        const int minor = pl->mode < N - 2 ? N - 1 : N - 2;
+        a.Uk2 = a.U[minor];
+        a.K_minor = pl->dims[minor];
+        if (pl->mode == N - 1) a.U[N - 2] = nullptr;   // the view's output mode
+    }
     a.units = pl->d_units;
     a.n_units = pl->planned_units;
     a.status = pl->d_status;
@@ -869,8 +931,12 @@ deinsum_status deinsum_plan(const char *einsum, const int64_t *extents, int n_ex
     if (st == DEINSUM_OK) {
         if (pl->kind == DEINSUM_KIND_MTTKRP) {
             int64_t R = pl->ranks[(pl->mode + 1) % pl->order];
-            if (R > 64) st = DEINSUM_ERR_UNSUPPORTED;
-            else build_mttkrp_geometry(pl);
+            if (R > 64) {
+                st = DEINSUM_ERR_UNSUPPORTED;
+            } else {
+                choose_inner_merge(pl);
+                build_mttkrp_geometry(pl);
+            }
         } else {
             plan_ttmc_chain(pl);
             if (prec == DEINSUM_PREC_SPLIT_BF16) st = plan_ttmc_fused(pl);

@@ -52,8 +52,10 @@ def test_batched_split_matches_oracle_and_single_path():
     for (dims, R, mode, X, U), out, ops in zip(items, outs, ins):
         got = out.cpu().numpy()
         assert oracle.rel_error(got, oracle.mttkrp(X, U, mode)) <= 1e-5
+        # the single-plan path may regroup the contraction (a merged inner mode), so the two
+        # GPU results are each within 1e-5 of the oracle and within 2e-5 of each other
         single = dz.mttkrp(ops[0], [torch.from_numpy(u).cuda() for u in U], mode, prec="split_bf16")
-        assert oracle.rel_error(got, single.cpu().numpy().astype(np.float64)) <= 1e-5
+        assert oracle.rel_error(got, single.cpu().numpy().astype(np.float64)) <= 2e-5
 
 
 def test_batched_graph_replay_is_bitwise_deterministic():
