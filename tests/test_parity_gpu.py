@@ -71,6 +71,14 @@ SMALL_CASES = [
     # mode 2: 64 < I = 100 < 128 with outer indices (one group per tile, not packed, TMA);
     # mode 0: I = 20 with P = 1 (G = 6 outer indices packed per tile)
     ((20, 30, 100), 16),
+    # inner mode of 2100: three fiber groups per (tile, o) on the tensor-core path (16, 16
+    # and 1 chunks of 64)
+    ((3, 5, 2100), 8),
+    # short inner modes merged with their neighbour: the last mode (K = 33 merged with 9,
+    # G = 3 outer indices packed), and mode 0 of a view whose merged inner mode (60 x 64)
+    # needs four fiber groups per (tile, o)
+    ((7, 9, 33, 40), 16),
+    ((8, 40, 60, 64), 24),
 ]
 
 
