@@ -261,11 +261,12 @@ deinsum_status deinsum_cpals_create(int order, const int64_t *dims, int rank, de
  *   factors  HOST array of `order` DEVICE float32 I_m x rank matrices: the
  *            initial factors on entry, the (column-normalised) result on exit.
  *   lambda   DEVICE float64[rank]: the column norms after the last update.
- *   fits     DEVICE float64[sweeps]: the fit after every sweep.  The last one is
- *            computed from the residual ||X - Xhat|| directly (FP32 reconstruction,
- *            FP64 sum: accurate to ~1e-7 near convergence); the earlier ones from
- *            the expansion above, whose FP32-level MTTKRP input limits them to
- *            ~1e-3 absolute once the fit approaches 1.
+ *   fits     DEVICE float64[sweeps]: the fit after every sweep, from the expansion
+ *            above; its FP32-level MTTKRP input makes it cancel once the residual is
+ *            small (~1e-3 absolute as the fit approaches 1).  So when the last sweep's
+ *            residual^2 is below 1e-2 ||X||^2, the last fit is computed from the
+ *            residual ||X - Xhat|| directly instead (FP32 reconstruction, FP64 sum:
+ *            ~1e-7); above that the expansion is within ~5e-5 and is kept.
  * The first call allocates the handle's workspace (one cudaMalloc). */
 deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const *factors, double *lambda,
                                  int sweeps, double *fits, deinsum_stream_t stream);

@@ -291,9 +291,15 @@ __global__ void sum_kernel(const double *__restrict__ partial, int n, double *__
 
 // fit after a sweep (one block): inner = sum_r lambda_r sum_i M[i, r] U[i, r]
 // over the last mode; normXhat^2 = lambda^T (Hadamard_m G_m) lambda.
+// The final fit takes the direct residual only when the expansion can cancel: its
+// error in res^2 is about twice the MTTKRP's relative error times ||X||^2 (~1e-5 ||X||^2
+// on the split path), i.e. below 5e-5 in the fit while res^2 >= 1e-2 ||X||^2.
+constexpr double kDirectResidualBelow = 1e-2;
+
 __global__ void fit_kernel(const float *__restrict__ M, const float *__restrict__ U, int64_t I, int R,
                            const double *__restrict__ lambda, const double *__restrict__ grams, int order,
-                           const double *__restrict__ normx2, double *__restrict__ fit_out) {
+                           const double *__restrict__ normx2, double *__restrict__ fit_out,
+                           int *__restrict__ need_direct) {
     // blockDim = 256: thread (r = tid % 64, slice = tid / 64) sums rows slice,
     // slice + 4, ... of M[i, r] U[i, r] (FP32 partials of 8, FP64 accumulation);
     // every thread also takes a share of the R x R terms of ||Xhat||^2
@@ -337,6 +343,7 @@ __global__ void fit_kernel(const float *__restrict__ M, const float *__restrict_
         for (int q = 0; q < R; ++q) inner += red[0][q];
         const double res2 = fmax(0.0, *normx2 + xr[0] - 2.0 * inner);
         *fit_out = 1.0 - sqrt(res2) / sqrt(*normx2);
+        if (need_direct) *need_direct = res2 < kDirectResidualBelow * *normx2 ? 1 : 0;
     }
 }
 
@@ -355,12 +362,17 @@ struct ResidualArgs {
     int order, R;
     const double *lambda;
     double *partial;  // gridDim.x
+    const int *need;  // 0: the expansion's fit stands, nothing to compute
 };
 
 __global__ void __launch_bounds__(256) residual_kernel(const ResidualArgs a) {
     __shared__ float Ws[kMaxR][64 + 4];
     __shared__ float Cs[kMaxR][64 + 4];
     __shared__ double red[8];
+    if (a.need && *a.need == 0) {   // the same value for every thread
+        if (threadIdx.x == 0) a.partial[blockIdx.x] = 0.0;
+        return;
+    }
     const int R = a.R;
     const int64_t K = a.dims[a.order - 1];
     int64_t rows = 1;
@@ -435,9 +447,11 @@ __global__ void __launch_bounds__(256) residual_kernel(const ResidualArgs a) {
     }
 }
 
-// fit = 1 - sqrt(residual^2) / ||X|| from the summed residual partials (one block).
+// fit = 1 - sqrt(residual^2) / ||X|| from the summed residual partials (one block),
+// when the direct residual was needed (*need != 0); else the expansion's fit stays.
 __global__ void fit_from_residual_kernel(const double *__restrict__ partial, int n, const double *__restrict__ normx2,
-                                         double *__restrict__ fit_out) {
+                                         double *__restrict__ fit_out, const int *__restrict__ need) {
+    if (need && *need == 0) return;
     __shared__ double red[32];
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
@@ -673,13 +687,15 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
             count_launch(4);
         }
         const int last = h->order - 1;
-        if (sw + 1 < sweeps) {
-            // expansion of the residual from quantities the sweep already has
-            fit_kernel<<<1, 256, 0, s>>>(h->M, factors[last], h->dims[last], R, lambda, h->grams, h->order,
-                                         h->normx2, fits + sw);
-            count_launch();
-        } else {
-            // final fit from the residual itself: the expansion cancels near convergence
+        // expansion of the residual from quantities the sweep already has; after the last
+        // sweep it also decides whether the direct residual is needed (it cancels when small)
+        int *need_direct = reinterpret_cast<int *>(h->normx2 + 1);
+        fit_kernel<<<1, 256, 0, s>>>(h->M, factors[last], h->dims[last], R, lambda, h->grams, h->order, h->normx2,
+                                     fits + sw, sw + 1 < sweeps ? nullptr : need_direct);
+        count_launch();
+        if (sw + 1 == sweeps) {
+            // final fit from the residual itself when the expansion may have cancelled (the
+            // flag fit_kernel just set; otherwise both kernels return at once)
             ResidualArgs ra;
             std::memset(&ra, 0, sizeof(ra));
             ra.X = X;
@@ -691,8 +707,9 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
             ra.R = R;
             ra.lambda = lambda;
             ra.partial = h->partial;
+            ra.need = need_direct;
             residual_kernel<<<kSumBlocks, 256, 0, s>>>(ra);
-            fit_from_residual_kernel<<<1, 256, 0, s>>>(h->partial, kSumBlocks, h->normx2, fits + sw);
+            fit_from_residual_kernel<<<1, 256, 0, s>>>(h->partial, kSumBlocks, h->normx2, fits + sw, need_direct);
             count_launch(2);
         }
         if (cudaGetLastError() != cudaSuccess) return DEINSUM_ERR_CUDA;

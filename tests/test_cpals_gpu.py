@@ -130,3 +130,24 @@ def test_cpals_dimension_tree_only_where_it_applies():
     assert not dz.CPALS((40, 50, 36), 40, "split_bf16").uses_dimension_tree    # rank > 32
     assert not dz.CPALS((40, 50, 36), 8, "plain").uses_dimension_tree
     assert not dz.CPALS((20, 24, 18, 22), 8, "split_bf16").uses_dimension_tree  # order 4
+
+
+def test_cpals_final_fit_from_the_expansion_when_the_residual_is_large():
+    """With heavy noise the final residual is large, so the final fit comes from the
+    expansion rather than a second pass over X; it must still equal the FP64 direct
+    residual of the GPU's own final factors within 1e-4."""
+    dims, rank = (48, 40, 36), 5
+    X, init = _problem(7, dims, rank, 1.0)
+    Xd = torch.from_numpy(X).cuda()
+    F = [torch.from_numpy(u).cuda() for u in init]
+    cp = dz.CPALS(dims, rank, "split_bf16")
+    lam, fits = cp.run(Xd, F, 6)
+    torch.cuda.synchronize()
+    assert cp.status() == 0
+    U = [f.cpu().numpy().astype(np.float64) for f in F]
+    lamh = lam.cpu().numpy()
+    Xhat = np.einsum("r,ir,jr,kr->ijk", lamh, *U)
+    x64 = X.astype(np.float64)
+    direct = 1.0 - np.linalg.norm(x64 - Xhat) / np.linalg.norm(x64)
+    assert direct < 0.9, f"the residual should be large here (fit {direct:.4f})"
+    assert abs(float(fits[-1]) - direct) <= 1e-4
