@@ -836,8 +836,17 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         uint32_t bpar = 0, bused = 0;
         // the raw ring carries only the chunks of TMA-loaded instances: count those apart
         int64_t tchunk = 0;
+        // last-mode instances (case 1; the batch packs no outer indices) take the MN-major
+        // operand; their row positions in the raw tile are set up when the instance changes
+        const MttkrpArgs *mp_for = nullptr;
+        MnPos mp;
         for (int64_t chunk = 0; !it.done; ++chunk) {
             const MttkrpArgs &a = *it.a;
+            const bool mn = a.g.kcase == 1;
+            if (mn && mp_for != it.a) {
+                mp = mn_pos(a.raw_pitch > 0 ? a.raw_pitch : BM, 1, pt);
+                mp_for = it.a;
+            }
             float4 v[8];
             const int rs = int(tchunk % RS);
             if (a.use_tma) {
@@ -845,14 +854,17 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 ++tchunk;
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
                 const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES);
-                if (a.g.kcase == 0 && (!a.g.narrow || a.g.G * a.g.I == BM)) conv_read_smem_wide(raw, pt, v);
+                if (mn && a.raw_pitch == BM) conv_read_smem_mn128(raw, pt, v);
+                else if (mn) conv_read_smem_mn(mp, a.raw_pitch, raw, pt, v);
+                else if (!a.g.narrow || a.g.G * a.g.I == BM) conv_read_smem_wide(raw, pt, v);
                 else conv_read_smem(a, raw, pt, v);
                 fence_proxy_async_smem();   // these generic reads before the stage's next TMA write
                 __syncwarp();
                 if (lane == 0) mbar_arrive(raw_empty(rs));
+            } else if (mn) {
+                conv_read_global_mn<false>(a, it.as_iter(), pt, v);
             } else {
-                if (a.g.opack) conv_read_global<true>(a, it.as_iter(), pt, v);
-                else conv_read_global<false>(a, it.as_iter(), pt, v);
+                conv_read_global<false>(a, it.as_iter(), pt, v);
             }
             const int as = int(chunk % AS);
             const uint32_t aj = uint32_t(chunk / AS);
@@ -864,7 +876,8 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
                 bused |= 1u << as;
             }
-            conv_store(a.g, pt, a_hi(as), a_lo(as), v);
+            if (mn) conv_store_mn(pt, a_hi(as), a_lo(as), v);
+            else conv_store(a.g, pt, a_hi(as), a_lo(as), v);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(a_full(as));
@@ -935,6 +948,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             int64_t chunk = 0, fgi = 0;
             bool ok = true;
             uint32_t dcol = 0, idesc = 0;
+            bool mn = false;
             while (ok && !it.done) {
                 const MttkrpArgs &a = *it.a;
                 const int b = int(fgi & 1);
@@ -943,21 +957,25 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                     if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
                     tc_fence_after();
                     dcol = tmem + uint32_t(b * C::N);
-                    idesc = idesc_bf16_f32(BM, 2 * a.g.R_pad);
+                    mn = a.g.kcase == 1;   // the last mode: MN-major A (see the converters)
+                    idesc = idesc_bf16_f32(BM, 2 * a.g.R_pad) | (mn ? kIdescAMnMajor : 0u);
                 }
                 const int s = int(chunk % AS);
                 const uint32_t j = uint32_t(chunk / AS);
                 if (!mbar_wait(a_full(s), j & 1u, abort_flag, status) ||
                     !mbar_wait(bfull(s), j & 1u, abort_flag, status)) { ok = false; break; }
                 tc_fence_after();
-                const uint64_t dh = desc_kmajor_sw128(a_hi(s));
-                const uint64_t dl = desc_kmajor_sw128(a_lo(s));
+                const uint64_t dh = mn ? desc_mnmajor_sw128(a_hi(s), kMnAtomStride, kMnKGroupStride)
+                                       : desc_kmajor_sw128(a_hi(s));
+                const uint64_t dl = mn ? desc_mnmajor_sw128(a_lo(s), kMnAtomStride, kMnKGroupStride)
+                                       : desc_kmajor_sw128(a_lo(s));
                 const uint64_t db = desc_kmajor_sw128(b_t(s));
                 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
                     const uint64_t adv = uint64_t(kk * 32) >> 4;
-                    mma_bf16(dcol, dh + adv, db + adv, idesc, (it.kb > 0 || kk > 0) ? 1u : 0u);
-                    mma_bf16(dcol, dl + adv, db + adv, idesc, 1u);
+                    const uint64_t adv_a = mn ? uint64_t(kk * 2 * kMnKGroupStride) >> 4 : adv;
+                    mma_bf16(dcol, dh + adv_a, db + adv, idesc, (it.kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_bf16(dcol, dl + adv_a, db + adv, idesc, 1u);
                 }
                 mma_commit(a_empty(s));
                 ++chunk;
