@@ -220,6 +220,11 @@ def run_once(args):
         return 0
     dims = (n, n, n)
     X = dz.gen_uniform(2024, inputs.STREAM_X, dims)
+    if args.x_offset:   # X starting args.x_offset floats into its buffer (rows not 16-byte aligned)
+        buf = torch.empty(X.numel() + args.x_offset, device="cuda")
+        Xo = buf[args.x_offset:].view(dims)
+        Xo.copy_(X)
+        X = Xo
     U = [torch.from_numpy(inputs.factor_normal(2024, m, n, RANK_R, sigma=np.sqrt(1.0 / RANK_R))
                           .astype(np.float32)).cuda() for m in range(3)]
     for mode in [int(m) for m in args.modes.split(",")]:
@@ -227,6 +232,54 @@ def run_once(args):
         p(X, *[U[m] for m in range(3) if m != mode])
     torch.cuda.synchronize()
     print("ok")
+    return 0
+
+
+def run_unaligned(args):
+    """MTTKRP order 3, R = 32, split-BF16, per mode: X 1024^3 aligned (tensor map), X 1024^3
+    starting one float into its buffer and X 1023^3 (rows not 16-byte aligned: row-class tensor
+    maps).  Main-kernel time from CUDA events around it (average of --steps launches after 3
+    warm-up ones); X (4.3 GB) is larger than L2."""
+    import torch
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    stream = torch.cuda.Stream()
+    peak, peak_kind = _peaks()
+    out_cases = []
+    for dims, off in [((1024, 1024, 1024), 0), ((1024, 1024, 1024), 1), ((1023, 1023, 1023), 0)]:
+        X = dz.gen_uniform(5, inputs.STREAM_X, dims)
+        if off:
+            buf = torch.empty(X.numel() + off, device="cuda")
+            Xo = buf[off:].view(dims)
+            Xo.copy_(X)
+            del X
+            X = Xo
+        U = [torch.from_numpy(inputs.factor_normal(5, m, d, RANK_R, sigma=np.sqrt(1.0 / RANK_R))
+                              .astype(np.float32)).cuda() for m, d in enumerate(dims)]
+        for mode in range(3):
+            p = dz.Plan(dz.mttkrp_einsum(3, mode), list(dims) + [RANK_R], "float32", "split_bf16")
+            ops = [X] + [U[m] for m in range(3) if m != mode]
+            out = torch.empty(dims[mode], RANK_R, device="cuda")
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    p(*ops, out=out, stream=stream)
+            stream.synchronize()
+            p.set_kernel_timing(True)
+            p.kernel_time()
+            with torch.cuda.stream(stream):
+                for _ in range(args.steps):
+                    p(*ops, out=out, stream=stream)
+            stream.synchronize()
+            kms, kn = p.kernel_time()
+            kms /= max(1, kn)
+            gbs = 4.0 * float(np.prod(dims)) / kms / 1e6
+            out_cases.append({"dims": list(dims), "x_offset_floats": off, "mode": mode,
+                              "kernel_ms": round(kms, 4), "GB/s": round(gbs, 1),
+                              "frac": round(gbs / peak, 3)})
+        del X, U
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "MTTKRP main-kernel GB/s, aligned and unaligned rows", "unit": "GB/s",
+                      "peak": peak, "peak_kind": peak_kind, "data": "synthetic", "cases": out_cases}))
     return 0
 
 
@@ -631,7 +684,9 @@ def main():
                     help="profiling driver: one execute per mode of --modes at extent --n, no timing")
     ap.add_argument("--n", type=int, default=N_EXT, help="extent of each mode (--once only)")
     ap.add_argument("--modes", default="0,1,2", help="modes to run (--once only)")
-    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving", "batched", "ttmc", "paper", "cpals"],
+    ap.add_argument("--x-offset", type=int, default=0,
+                    help="--once: X starts this many floats into its buffer (rows not 16-byte aligned)")
+    ap.add_argument("--workload", default="mttkrp", choices=["mttkrp", "serving", "batched", "ttmc", "paper", "cpals", "unaligned"],
                     help="mttkrp: the benchmark line; serving / batched / ttmc: the other measurements")
     ap.add_argument("--requests", type=int, default=128, help="requests of the serving workload")
     ap.add_argument("--instances", type=int, default=512, help="instances of the batched workload")
@@ -642,6 +697,8 @@ def main():
         return run_serving(args)
     if args.workload == "batched" and args.impl == "native":
         return run_batched(args)
+    if args.workload == "unaligned" and args.impl == "native":
+        return run_unaligned(args)
     if args.workload == "ttmc" and args.impl == "native":
         return run_ttmc(args)
     if args.workload == "paper" and args.impl == "native":

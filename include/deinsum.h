@@ -19,9 +19,10 @@
  *     the einsum term "i_m r".
  *   - Every tensor pointer passed to an execute call is a DEVICE pointer owned
  *     by the caller; the library never frees it.  Pointers to float32 data must
- *     be 4-byte aligned, to float64 data 8-byte aligned; the vectorised load
- *     path is taken when X is 16-byte aligned and its rows allow it, otherwise
- *     a scalar path runs (same result).
+ *     be 4-byte aligned, to float64 data 8-byte aligned; X is loaded by tiled
+ *     tensor-memory copies when X and its rows are 16-byte aligned, otherwise
+ *     (split-BF16) by four copies per tile, one per class of rows congruent
+ *     mod 4, or by per-thread loads; every path gives the same bits.
  *   - Outputs are overwritten (beta = 0): Listing 1 accumulates into a zeroed
  *     output, which is the same value.
  *   - Calls return a status and never throw or abort.  Execute calls are

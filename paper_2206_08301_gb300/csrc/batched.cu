@@ -314,6 +314,7 @@ deinsum_status upload_instances(deinsum_batch_s *b, const void *const *const *in
         MttkrpArgs &a = A[i];
         std::memset(static_cast<void *>(&a), 0, sizeof(a));
         mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, inputs[i][0], &a, false);
+        a.row_classes = 0;   // the batched kernel loads unaligned rows per thread
         a.X = inputs[i][0];
         for (int k = 1; k < in.n_ops; ++k) a.U[in.opmode[k]] = inputs[i][k];
         a.Bsplit = b->ws + b->o_bsplit + b->bsplit_off[size_t(i)];

@@ -40,7 +40,7 @@
 #define DEINSUM_MAX_ORDER 8
 #define DEINSUM_BM 128
 #define DEINSUM_BK 64
-#define DEINSUM_GMAX 32  // most p values in one narrow tile (bounds the weight-ring slots)
+#define DEINSUM_GMAX 16  // most p values in one narrow tile (bounds the weight-ring slots)
 
 namespace deinsum {
 
@@ -80,6 +80,14 @@ struct MttkrpArgs {
     CUtensorMap xmap;     // (the type carries its own 128-byte alignment)
     int use_tma;
     uint32_t box_bytes;   // bytes one box load writes (out-of-bounds parts are zero-filled)
+    // Rows not 16-byte aligned (no xmap), no packed outer indices: four 2-D tensor maps, one per
+    // class c of rows (case 0: rows r = p I + i of Q words) or k lines (case 1: lines o K_in + k
+    // of I words) congruent to c mod 4.  Members of a class start at the same word offset d_c
+    // within their 16-byte granule and lie 4 Q (4 I) words apart, a multiple of 16 bytes, so
+    // map c has base = its first member's start rounded down to 16 bytes, inner extent
+    // Q + d_c (I + d_c), row stride 4 Q (4 I); see encode_x_rowclass_maps.
+    CUtensorMap xrow[4];
+    int row_classes;
     int raw_pitch;        // elements per row of the raw tile in shared memory
     MttkrpGeom g;
     const void *X;
@@ -144,6 +152,11 @@ int launch_ttm_last_tc(const TtmcArgs &a, int n_sm, void *stream);
 // or {64, 128/sg, sg} for sg > 1); false when X or its rows are not 16-byte aligned.
 bool encode_ttm_last_map(const void *X, int64_t S, int64_t K, int64_t L, CUtensorMap *map, uint32_t *box_bytes,
                          int sg = 1);
+
+// The four row-class tensor maps of an MTTKRP row view (MttkrpArgs::xrow) for X whose rows are
+// not 16-byte aligned; false with packed outer indices, fewer than 4 rows (lines), extents
+// beyond int32 coordinates or no encoder.
+bool encode_x_rowclass_maps(const MttkrpGeom &g, const void *X, CUtensorMap *maps);
 // Their converter view of a chunk (case 0, I = K, narrow when K < 128 and sg = 1 -- with sg > 1
 // the box fills all 128 rows --, R_pad 32, ceil(L/64) chunks).
 void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, MttkrpGeom *g, int sg = 1);

@@ -15,10 +15,12 @@
 // Warp roles (one CTA per SM, persistent over units):
 //   warps 0-7    converters: raw FP32 tile (smem) -> split -> 128B-swizzled K-major
 //                A tiles; one thread also bulk-copies the split factor tile B.
-//                Without TMA (unaligned rows) they load X from global themselves.
+//                With packed outer indices and rows that are not 16-byte aligned
+//                they load X from global themselves.
 //   warps 8-11   epilogue: TMEM -> registers, weight, accumulate, write partials.
 //   warp 12      TMEM allocation and the single-thread MMA issue.
-//   warp 13      TMA: tiled tensor loads of raw X tiles into a ring of RS stages.
+//   warp 13      TMA: tiled tensor loads of raw X tiles into a ring of RS stages
+//                (rows not 16-byte aligned: four loads per chunk, one per row class).
 // Rings: raw X (RS stages: raw_full / raw_empty), operand tiles (AS stages:
 // a_full / bfull / a_empty), two TMEM accumulators (accf / acce).  Every wait
 // is bounded (mbar_wait) and warp-uniform where a warp barrier follows.
@@ -38,6 +40,22 @@ using namespace sm100;
 
 constexpr int kFoldEvery = 64;  // fiber groups accumulated in registers before a flush
 
+// Raw tiles of rows that are not 16-byte aligned, loaded through the four row-class tensor
+// maps (MttkrpArgs::xrow).  A chunk is four boxes, one per class c, each member row padded by
+// 4 words so that the box can start at the 16-byte granule of the row's first element:
+//   case 0: class c = rows of the tile with (global row) = c mod 4: 32 rows of BK + 4 words;
+//           tile row l is row l / 4 of the box of class (rowbase + l) mod 4
+//   case 1: class c = k lines with (o K_in + k) = c mod 4: 16 lines of BM + 4 words;
+//           chunk line kl is line kl / 4 of the box of class (o K_in + k0 + kl) mod 4
+// and a member's first element sits d words into its slot, d = its word address mod 4.
+constexpr int kRcPitch0 = BK + 4, kRcRows0 = BM / 4;
+constexpr int kRcPitch1 = BM + 4, kRcRows1 = BK / 4;
+constexpr int kRcBox0 = kRcRows0 * kRcPitch0 * 4;   // bytes of one class box
+constexpr int kRcBox1 = kRcRows1 * kRcPitch1 * 4;
+constexpr int kRcRawBytes = 4 * kRcBox0;
+static_assert(4 * kRcBox1 <= kRcRawBytes, "case-1 class boxes in a raw stage");
+static_assert(kRcRawBytes % 1024 == 0 && kRcBox0 % 128 == 0 && kRcBox1 % 128 == 0, "box alignment");
+
 template <int RP> struct TcCfg {
     static constexpr int N = 2 * RP;                       // MMA N: hi and lo columns of the factor
     static constexpr int RS = RP <= 32 ? 4 : 3;            // raw X stages
@@ -46,7 +64,8 @@ template <int RP> struct TcCfg {
     static constexpr int TMA_WARP = MMA_WARP + 1;
     static constexpr int WARPS = TMA_WARP + 1;
     static constexpr int THREADS = WARPS * 32;
-    static constexpr int RAW_BYTES = BM * BK * 4;
+    static constexpr int RAW_BYTES = BM * BK * 4;          // one box of the tensor map
+    static constexpr int RAW_STAGE = kRcRawBytes;          // stage stride: also holds four class boxes
     static constexpr int A_BYTES = BM * BK * 2;            // one of hi / lo
     static constexpr int B_BYTES = N * BK * 2;
     static constexpr int ASTAGE_BYTES = 2 * A_BYTES + B_BYTES;
@@ -57,8 +76,9 @@ template <int RP> struct TcCfg {
     static constexpr int WBUF_BYTES = WSLOTS * WSLOT_FLOATS * 4;
     static constexpr int TMEM_COLS = 2 * N;                // two accumulators
     static constexpr int NBARS = 2 * RS + 3 * AS + 4 + 1 + 2 * WSLOTS;
-    static constexpr size_t SMEM = size_t(RS) * RAW_BYTES + size_t(AS) * ASTAGE_BYTES + WBUF_BYTES + 1024 + 512;
+    static constexpr size_t SMEM = size_t(RS) * RAW_STAGE + size_t(AS) * ASTAGE_BYTES + WBUF_BYTES + 1024 + 512;
     static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB per-CTA limit");
+    static_assert(RAW_BYTES <= RAW_STAGE, "a tensor-map box fits a raw stage");
     static_assert(NBARS * 8 + 8 <= 512, "barrier area");
 };
 
@@ -221,6 +241,160 @@ __device__ __forceinline__ void conv_read_global_mn(const MttkrpArgs &a, const I
     }
 }
 
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+
+// Words d .. d + 3 from the 16-byte aligned address `addr` on, d uniform across the warp (the
+// switch does not diverge): one aligned load for d = 0, two otherwise.
+__device__ __forceinline__ float4 lds_words(uint32_t addr, int d) {
+    const float4 a = lds128(addr);
+    if (d == 0) return a;
+    const float4 b = lds128(addr + 16u);
+    if (d == 1) return make_float4(a.y, a.z, a.w, b.x);
+    if (d == 2) return make_float4(a.z, a.w, b.x, b.y);
+    return make_float4(a.w, b.x, b.y, b.z);
+}
+
+__device__ __forceinline__ uint64_t word_index(const void *p) {
+    return uint64_t(reinterpret_cast<uintptr_t>(p) >> 2);
+}
+
+// Converter thread -> rows for the row-class tiles of case 0: the two half-warps of warp w take
+// rsub = (w mod 4) + 8 (w / 4) and rsub + 4, so that every row of a warp (rsub + 16 j) is in
+// one class and starts at one word offset.  Returned in the packed form conv_store reads
+// (16 rsub + k4); a bijection of 0..255.
+__device__ __forceinline__ int rowcls_thread(int pt) {
+    const int w = pt >> 5, h = (pt >> 4) & 1;
+    return (((w & 3) + 8 * (w >> 2) + 4 * h) << 4) | (pt & 15);
+}
+
+// Case 0 from the four class boxes (thread layout: rows rsub + 16 j, k = 4 k4 .. + 3 with
+// pt = 16 rsub + k4 from rowcls_thread).  Row rsub + 16 j is box row rsub / 4 + 4 j of class
+// (rowbase + rsub) mod 4, and the class's word offset d is the same for the whole warp.
+// Rows outside the tile and k >= K_in read as zero.
+__device__ __forceinline__ void conv_read_rowcls(const MttkrpGeom &g, const void *X, int64_t col, int64_t tile,
+                                                 int64_t o, int kb, const float *raw, int pt, float4 (&v)[8]) {
+    const int k4 = pt & 15, rsub = pt >> 4;
+    const int64_t rowbase = tile_rowbase(g, col, tile);
+    const int64_t k0 = int64_t(kb) * BK;
+    const uint64_t w0 = word_index(X) + uint64_t(rowbase + rsub) * uint64_t(g.Q) + uint64_t(o * g.K_in + k0);
+    const int d = int(w0 & 3u);
+    const int c = int(uint64_t(rowbase + rsub) & 3u);
+    const uint32_t r = smem_u32(raw) + uint32_t(((c * kRcRows0 + (rsub >> 2)) * kRcPitch0 + 4 * k4) * 4);
+    constexpr uint32_t JS = 4u * kRcPitch0 * 4u;   // bytes between box rows rsub / 4 + 4 j
+    switch (d) {
+        case 0:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds128(r + JS * j);
+            break;
+        case 1:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(r + JS * j, 1);
+            break;
+        case 2:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(r + JS * j, 2);
+            break;
+        default:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(r + JS * j, 3);
+            break;
+    }
+    const bool rows_full = g.narrow ? (g.G * g.I == BM && rowbase + BM <= g.P * g.I) : col * BM + BM <= g.I;
+    if (rows_full && k0 + BK <= g.K_in) return;
+    const int64_t kpos = k0 + 4 * k4;
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool rv = row_valid(g, col, rowbase, rsub + 16 * j);
+        v[j].x = (rv && kpos < g.K_in) ? v[j].x : 0.f;
+        v[j].y = (rv && kpos + 1 < g.K_in) ? v[j].y : 0.f;
+        v[j].z = (rv && kpos + 2 < g.K_in) ? v[j].z : 0.f;
+        v[j].w = (rv && kpos + 3 < g.K_in) ? v[j].w : 0.f;
+    }
+}
+
+// Case 1 from the four class boxes, in the thread layout of conv_read_smem_mn128 (k line
+// kl = 8 w + j, rows m = 4 lane .. + 3): line kl is box line kl / 4 of class (L0 + kl) mod 4,
+// L0 = o K_in + k0; its word offset d is uniform across the warp.  Rows i_n >= I and
+// k >= K_in read as zero.
+__device__ __forceinline__ void conv_read_rowcls_mn(const MttkrpGeom &g, const void *X, int64_t col, int64_t o,
+                                                    int kb, const float *raw, int pt, float4 (&v)[8]) {
+    const int w = pt >> 5, lane = pt & 31;
+    const int64_t k0 = int64_t(kb) * BK;
+    const uint64_t L0 = uint64_t(o * g.K_in + k0);
+    const uint64_t e0 = word_index(X) + (L0 + uint64_t(8 * w)) * uint64_t(g.I) + uint64_t(col * BM);
+    const uint32_t r = smem_u32(raw) + uint32_t(lane * 16);
+    // lines j and j + 4 are in one class (box lines kl / 4 and kl / 4 + 1): one offset per pair
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int kl = 8 * w + j;
+        const int c = int((L0 + uint64_t(kl)) & 3u);
+        const int d = int((e0 + uint64_t(j) * uint64_t(g.I)) & 3u);
+        const uint32_t p0 = r + uint32_t((c * kRcRows1 + (kl >> 2)) * kRcPitch1 * 4);
+        const uint32_t p1 = p0 + uint32_t(kRcPitch1 * 4);
+        if (d == 0) {
+            v[j] = lds128(p0);
+            v[j + 4] = lds128(p1);
+        } else {
+            const float4 a0 = lds128(p0), b0 = lds128(p0 + 16u), a1 = lds128(p1), b1 = lds128(p1 + 16u);
+            if (d == 1) {
+                v[j] = make_float4(a0.y, a0.z, a0.w, b0.x);
+                v[j + 4] = make_float4(a1.y, a1.z, a1.w, b1.x);
+            } else if (d == 2) {
+                v[j] = make_float4(a0.z, a0.w, b0.x, b0.y);
+                v[j + 4] = make_float4(a1.z, a1.w, b1.x, b1.y);
+            } else {
+                v[j] = make_float4(a0.w, b0.x, b0.y, b0.z);
+                v[j + 4] = make_float4(a1.w, b1.x, b1.y, b1.z);
+            }
+        }
+    }
+    if (k0 + BK <= g.K_in && col * BM + BM <= g.I) return;
+    const int64_t m0 = col * BM + 4 * lane;
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool kv = k0 + 8 * w + j < g.K_in;
+        v[j].x = (kv && m0 < g.I) ? v[j].x : 0.f;
+        v[j].y = (kv && m0 + 1 < g.I) ? v[j].y : 0.f;
+        v[j].z = (kv && m0 + 2 < g.I) ? v[j].z : 0.f;
+        v[j].w = (kv && m0 + 3 < g.I) ? v[j].w : 0.f;
+    }
+}
+
+// One chunk through the row-class maps (one thread): the four boxes into raw stage `dst`.
+// Box c starts at the class's first row (line) of the chunk and, along the row, at the chunk's
+// first element rounded down to its 16-byte granule (a multiple of 4 words, as a tiled load
+// requires); rows past the class's last member are zero-filled.
+__device__ __forceinline__ void rowcls_load(const MttkrpArgs &a, int64_t col, int64_t tile, int64_t o, int kb,
+                                            uint32_t dst, uint32_t bar) {
+    const MttkrpGeom &g = a.g;
+    const int64_t k0 = int64_t(kb) * BK;
+    const uint64_t xw = word_index(a.X);
+    if (g.kcase == 0) {
+        mbar_arrive_expect_tx(bar, 4 * kRcBox0);
+        const int64_t rowbase = tile_rowbase(g, col, tile);
+        #pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t rc = rowbase + ((c - rowbase) & 3);        // first tile row of class c
+            const uint64_t dc = (xw + uint64_t(c) * uint64_t(g.Q)) & 3u; // class offset in its granule
+            const int64_t x = int64_t(dc) + o * g.K_in + k0;          // chunk start within the map row
+            tma_load_2d(dst + uint32_t(c * kRcBox0), &a.xrow[c], int(x & ~int64_t(3)), int((rc - c) >> 2), bar);
+        }
+    } else {
+        mbar_arrive_expect_tx(bar, 4 * kRcBox1);
+        const int64_t L0 = o * g.K_in + k0;
+        #pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t lc = L0 + ((c - L0) & 3);                  // first chunk line of class c
+            tma_load_2d(dst + uint32_t(c * kRcBox1), &a.xrow[c], int(col * BM), int((lc - c) >> 2), bar);
+        }
+    }
+}
+
 // Product of the outer factors' entries at outer index o (row-major over the
 // outer modes), column c.
 __device__ __forceinline__ float outer_weight(const MttkrpArgs &a, int64_t o, int c) {
@@ -317,17 +491,20 @@ __device__ __forceinline__ void load_fg_weights(const MttkrpArgs &a, int64_t til
 
 // OP: outer indices packed into the tile; MN: MN-major A operand (the last mode);
 // PW: per-row weights (packed outer indices, or narrow tiles of several p with L rows).
-template <int RP, bool OP, bool MN, bool PW>
+// RC: X through the four row-class tensor maps (rows not 16-byte aligned); otherwise through
+// the tensor map when a.use_tma, else per-thread loads.
+template <int RP, bool OP, bool MN, bool PW, bool RC>
 __global__ void __launch_bounds__(TcCfg<RP>::THREADS, 1)
 mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     static_assert(!OP || PW, "packed outer indices weight every row group");
+    static_assert(!(OP && RC), "row classes are not used with packed outer indices");
     using C = TcCfg<RP>;
     constexpr int RS = C::RS, AS = C::AS;
     const MttkrpGeom &g = a.g;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *raw_base = smem;
-    unsigned char *a_base = smem + RS * C::RAW_BYTES;
+    unsigned char *a_base = smem + RS * C::RAW_STAGE;
     float *wbuf = reinterpret_cast<float *>(a_base + AS * C::ASTAGE_BYTES);   // weight ring
     uint64_t *bars = reinterpret_cast<uint64_t *>(a_base + AS * C::ASTAGE_BYTES + C::WBUF_BYTES);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
@@ -335,7 +512,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
-    auto raw_addr = [&](int s) { return raw_s + uint32_t(s) * C::RAW_BYTES; };
+    auto raw_addr = [&](int s) { return raw_s + uint32_t(s) * C::RAW_STAGE; };
     auto a_hi = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES; };
     auto a_lo = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + C::A_BYTES; };
     auto b_t = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + 2 * C::A_BYTES; };
@@ -394,11 +571,14 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         for (int64_t chunk = 0; !it.done; ++chunk) {
             float4 v[8];
             const int rs = int(chunk % RS);
-            if (a.use_tma) {
+            if (RC || a.use_tma) {
                 const uint32_t rj = uint32_t(chunk / RS);
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, a.status))) break;
-                const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES);
-                if (MN && !OP && a.raw_pitch == BM) conv_read_smem_mn128(raw, pt, v);
+                const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_STAGE);
+                if (RC) {
+                    if (MN) conv_read_rowcls_mn(g, a.X, it.col, it.o, it.kb, raw, pt, v);
+                    else conv_read_rowcls(g, a.X, it.col, it.tile, it.o, it.kb, raw, rowcls_thread(pt), v);
+                } else if (MN && !OP && a.raw_pitch == BM) conv_read_smem_mn128(raw, pt, v);
                 else if (MN) conv_read_smem_mn(mp, a.raw_pitch, raw, pt, v);
                 else if (!g.narrow || g.G * g.I == BM) conv_read_smem_wide(raw, pt, v);   // all 128 rows
                 else conv_read_smem_t<OP>(a.g, a.raw_pitch, raw, pt, v);
@@ -425,7 +605,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 bused |= 1u << as;
             }
             if (MN) conv_store_mn(pt, a_hi(as), a_lo(as), v);
-            else conv_store(g, pt, a_hi(as), a_lo(as), v);
+            else conv_store(g, RC ? rowcls_thread(pt) : pt, a_hi(as), a_lo(as), v);
             // the proxy fence orders this thread's A stores before the tensor-core reads
             fence_proxy_async_smem();
             __syncwarp();
@@ -455,21 +635,25 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     last_wpar = wj & 1u;
                     ++fgi;
                 }
-                if (a.use_tma) {
+                if (RC || a.use_tma) {
                     const int rs = int(chunk % RS);
                     const uint32_t rj = uint32_t(chunk / RS);
                     if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, a.status)) break;
-                    mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                     const int kc = it.kb * BK;
-                    if (OP) {
+                    if (RC) {
+                        rowcls_load(a, it.col, it.tile, it.o, it.kb, raw_addr(rs), raw_full(rs));
+                    } else if (OP) {
+                        mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                         const int o0 = int(it.tile * g.G);
                         if (g.kcase == 0) tma_load_4d(raw_addr(rs), &a.xmap, kc, 0, o0, 0, raw_full(rs));
                         else tma_load_3d(raw_addr(rs), &a.xmap, 0, kc, o0, raw_full(rs));
                     } else if (g.kcase == 0) {
+                        mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                         const int c2 = g.narrow ? 0 : int(it.col * BM);
                         const int c3 = g.narrow ? int(it.tile * g.G) : int(it.tile);
                         tma_load_4d(raw_addr(rs), &a.xmap, kc, int(it.o), c2, c3, raw_full(rs));
                     } else {
+                        mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                         tma_load_3d(raw_addr(rs), &a.xmap, int(it.col * BM), kc, int(it.o), raw_full(rs));
                     }
                     last_rs = rs;
@@ -679,15 +863,15 @@ __global__ void split_inner_factor_kernel(const float *__restrict__ U, const flo
     }
 }
 
-template <int RP, bool OP, bool MN, bool PW>
+template <int RP, bool OP, bool MN, bool PW, bool RC = false>
 int launch_tc_rp_op(const MttkrpArgs &a, int n_sm, void *stream) {
     using C = TcCfg<RP>;
-    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_kernel<RP, OP, MN, PW>,
+    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_kernel<RP, OP, MN, PW, RC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
     if (e != cudaSuccess) return int(e);
     int64_t grid = a.n_units < n_sm ? a.n_units : n_sm;
     if (grid < 1) grid = 1;
-    mttkrp_tc_kernel<RP, OP, MN, PW><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
+    mttkrp_tc_kernel<RP, OP, MN, PW, RC><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
     count_launch();
     return int(cudaGetLastError());
 }
@@ -698,6 +882,11 @@ int launch_tc_rp_op(const MttkrpArgs &a, int n_sm, void *stream) {
 template <int RP>
 int launch_tc_rp(const MttkrpArgs &a, int n_sm, void *stream) {
     const MttkrpGeom &g = a.g;
+    if (a.row_classes && !a.use_tma && !g.opack) {   // rows not 16-byte aligned
+        if (g.kcase == 1) return launch_tc_rp_op<RP, false, true, false, true>(a, n_sm, stream);
+        if (g.narrow && g.n_lmodes > 0) return launch_tc_rp_op<RP, false, false, true, true>(a, n_sm, stream);
+        return launch_tc_rp_op<RP, false, false, false, true>(a, n_sm, stream);
+    }
     if (g.kcase == 1)
         return g.opack ? launch_tc_rp_op<RP, true, true, true>(a, n_sm, stream)
                        : launch_tc_rp_op<RP, false, true, false>(a, n_sm, stream);
@@ -771,7 +960,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *raw_base = smem;
-    unsigned char *a_base = smem + RS * C::RAW_BYTES;
+    unsigned char *a_base = smem + RS * C::RAW_STAGE;
     float *wbuf = reinterpret_cast<float *>(a_base + AS * C::ASTAGE_BYTES);   // weight ring
     uint64_t *bars = reinterpret_cast<uint64_t *>(a_base + AS * C::ASTAGE_BYTES + C::WBUF_BYTES);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
@@ -780,7 +969,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
-    auto raw_addr = [&](int s) { return raw_s + uint32_t(s) * C::RAW_BYTES; };
+    auto raw_addr = [&](int s) { return raw_s + uint32_t(s) * C::RAW_STAGE; };
     auto a_hi = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES; };
     auto a_lo = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + C::A_BYTES; };
     auto b_t = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + 2 * C::A_BYTES; };
@@ -834,7 +1023,9 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         BIter it;
         it.init(&bargs);
         uint32_t bpar = 0, bused = 0;
-        // the raw ring carries only the chunks of TMA-loaded instances: count those apart
+        // the raw ring carries only the chunks of TMA-loaded instances: count those apart.
+        // Instances whose rows are not 16-byte aligned take the per-thread loads here (the
+        // row-class path in this one kernel for all instances measured slower overall).
         int64_t tchunk = 0;
         // last-mode instances (case 1; the batch packs no outer indices) take the MN-major
         // operand; their row positions in the raw tile are set up when the instance changes
@@ -853,7 +1044,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 const uint32_t rj = uint32_t(tchunk / RS);
                 ++tchunk;
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
-                const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES);
+                const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_STAGE);
                 if (mn && a.raw_pitch == BM) conv_read_smem_mn128(raw, pt, v);
                 else if (mn) conv_read_smem_mn(mp, a.raw_pitch, raw, pt, v);
                 else if (!a.g.narrow || a.g.G * a.g.I == BM) conv_read_smem_wide(raw, pt, v);
@@ -918,17 +1109,19 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                     const uint32_t rj = uint32_t(tchunk / RS);
                     ++tchunk;
                     if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status)) break;
-                    mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                     const int kc = it.kb * BK;
                     if (a.g.opack) {
+                        mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                         const int o0 = int(it.tile * a.g.G);
                         if (a.g.kcase == 0) tma_load_4d(raw_addr(rs), &a.xmap, kc, 0, o0, 0, raw_full(rs));
                         else tma_load_3d(raw_addr(rs), &a.xmap, 0, kc, o0, raw_full(rs));
                     } else if (a.g.kcase == 0) {
+                        mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                         const int c2 = a.g.narrow ? 0 : int(it.col * BM);
                         const int c3 = a.g.narrow ? int(it.tile * a.g.G) : int(it.tile);
                         tma_load_4d(raw_addr(rs), &a.xmap, kc, int(it.o), c2, c3, raw_full(rs));
                     } else {
+                        mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                         tma_load_3d(raw_addr(rs), &a.xmap, int(it.col * BM), kc, int(it.o), raw_full(rs));
                     }
                     last_rs = rs;

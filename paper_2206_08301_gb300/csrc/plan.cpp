@@ -81,6 +81,10 @@ struct deinsum_plan_s {
     int xmap_ok = 0;
     uint32_t xmap_box_bytes = 0;
     int xmap_pitch = 0;
+    // row-class tensor maps of X (rows not 16-byte aligned), re-encoded when X moves
+    CUtensorMap xrow[4]{};
+    const void *xrow_ptr = nullptr;
+    int xrow_ok = 0;
 
     // benchmark timing of the main kernel
     bool timing = false;
@@ -712,6 +716,16 @@ deinsum_status execute_mttkrp(deinsum_plan_s *pl, const void *const *inputs, voi
                 a.box_bytes = pl->xmap_box_bytes;
                 a.raw_pitch = pl->xmap_pitch;
             }
+            if (!a.use_tma && !a.g.opack) {   // unaligned rows: the four row-class maps
+                if (pl->xrow_ptr != a.X) {
+                    pl->xrow_ptr = a.X;
+                    pl->xrow_ok = encode_x_rowclass_maps(a.g, a.X, pl->xrow) ? 1 : 0;
+                }
+                if (pl->xrow_ok) {
+                    for (int c = 0; c < 4; ++c) a.xrow[c] = pl->xrow[c];
+                    a.row_classes = 1;
+                }
+            }
             err = launch_split_inner_factor(a, pl->d_bsplit, stream);
             if (!err) err = launch_weight_tables(a, stream);
             const long ti = timing_begin(pl, stream);
@@ -831,6 +845,37 @@ deinsum_status execute_ttmc(deinsum_plan_s *pl, const void *const *inputs, void 
 
 namespace deinsum {
 
+// Row classes (MttkrpArgs::xrow): class c holds the rows (case 0) or k lines (case 1) whose
+// index is c mod 4.  Map c is 2-D {len + d_c, members of the class} with row stride 4 len
+// words, based at the 16-byte granule holding the start of member 0 (row or line c), where
+// len = Q (case 0) or I (case 1) and d_c = that start's word offset in its granule; the
+// kernels load boxes of {BK + 4, BM / 4} (case 0) or {BM + 4, BK / 4} (case 1).  Every
+// address a box can reach lies in a granule that holds an element of X.
+bool encode_x_rowclass_maps(const MttkrpGeom &g, const void *X, CUtensorMap *maps) {
+    auto enc = tensor_map_encoder();
+    if (!enc || g.opack || (reinterpret_cast<uintptr_t>(X) & 3) != 0) return false;
+    const int64_t lim = int64_t(1) << 31;
+    const int64_t len = g.kcase == 0 ? g.Q : g.I;                     // words per row (line)
+    const int64_t n = g.kcase == 0 ? g.P * g.I : g.O * g.K_in;       // rows (lines)
+    if (n < 4 || len + 3 >= lim || n >= 4 * lim) return false;
+    const uintptr_t xw = reinterpret_cast<uintptr_t>(X) >> 2;
+    for (int c = 0; c < 4; ++c) {
+        const uintptr_t start = xw + uintptr_t(c) * uintptr_t(len);   // word address of member 0
+        const int64_t d = int64_t(start & 3);
+        void *base = reinterpret_cast<void *>((start - uintptr_t(d)) << 2);
+        cuuint64_t dims[2] = {cuuint64_t(len + d), cuuint64_t((n - c + 3) / 4)};
+        cuuint64_t strides[1] = {cuuint64_t(4 * len) * 4};
+        cuuint32_t box[2] = {g.kcase == 0 ? cuuint32_t(DEINSUM_BK + 4) : cuuint32_t(DEINSUM_BM + 4),
+                             g.kcase == 0 ? cuuint32_t(DEINSUM_BM / 4) : cuuint32_t(DEINSUM_BK / 4)};
+        cuuint32_t estr[2] = {1, 1};
+        if (enc(&maps[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
 // Converter view of one raw chunk (128 k rows x 64 l) of the last-mode TTM kernels:
 // case 0, one slab per tile, R_pad 32 (split factor tiles of U_{N-1}).
 void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, MttkrpGeom *g, int sg) {
@@ -903,6 +948,8 @@ bool mttkrp_prepare_oneoff(int order, const int64_t *dims, int mode, int R, cons
         a->box_bytes = pl.xmap_box_bytes;
         a->raw_pitch = pl.xmap_pitch;
     }
+    a->row_classes = 0;
+    if (!a->use_tma && !a->g.opack && encode_x_rowclass_maps(a->g, X, a->xrow)) a->row_classes = 1;
     return true;
 }
 

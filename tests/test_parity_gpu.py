@@ -95,13 +95,37 @@ def test_mttkrp_small_all_modes(dims, R, prec):
 
 
 @pytest.mark.parametrize("prec", ["plain", "split_bf16"])
-def test_mttkrp_misaligned_x_takes_scalar_path(prec):
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_mttkrp_misaligned_x(prec, offset):
+    """X 4-byte but not 16-byte aligned: no tensor map; the tensor-core path copies each
+    row with one bulk copy from its first 16-byte granule (every word offset)."""
     dims, R = (130, 66, 128), 32
     X = inputs.tensor_uniform_f32(5, dims)
     Us = _factors(5, dims, R)
     for mode in range(3):
-        got = _run_mttkrp(X, Us, mode, prec, offset=1)
+        got = _run_mttkrp(X, Us, mode, prec, offset=offset)
         _check(got, oracle.mttkrp(X, Us, mode), "plain32" if prec == "plain" else prec)
+
+
+# Unaligned rows on the per-row bulk-copy path: several 128-row columns with a ragged last
+# one, narrow tiles of G p values (I < 128, P > 1) and a ragged last tile, last modes with
+# odd I over several columns, inner ranges with a ragged last chunk, a merged inner mode.
+BULK_CASES = [
+    ((131, 45, 263), 32),      # K_in = 263: four offsets along a row; mode 2: I = 263, 3 columns
+    ((7, 37, 11, 129), 16),    # mode 1: narrow tiles (I = 37, G = 3), P = 7; mode 3: I = 129
+    ((3, 301, 77), 64),        # rank 64; mode 2: I = 77, O = 3 outer indices, not packed (P = 1)
+    ((9, 15, 5, 47), 8),       # short modes: merged inner (5 x 47) in modes 0, 1
+]
+
+
+@pytest.mark.parametrize("dims,R", BULK_CASES)
+def test_mttkrp_bulk_row_path(dims, R):
+    X = inputs.tensor_uniform_f32(23, dims)
+    Us = _factors(23, dims, R)
+    for mode in range(len(dims)):
+        for offset in (0, 3):
+            _check(_run_mttkrp(X, Us, mode, "split_bf16", offset=offset), oracle.mttkrp(X, Us, mode),
+                   "split_bf16")
 
 
 @pytest.mark.parametrize("prec", ["plain", "split_bf16"])
@@ -138,13 +162,15 @@ def test_mttkrp_bitwise_deterministic(prec):
 
 
 @pytest.mark.parametrize("dims,R", [((64, 64, 64, 64), 24), ((48, 40, 96, 64), 32), ((256, 300, 64), 16)])
-def test_tma_and_register_paths_agree_bitwise(dims, R):
-    """An aligned X goes through the TMA raw-tile ring, an X offset by one element
-    through the per-thread register loads; the split and the MMAs are the same, so
-    the outputs must be identical bit for bit (catches a stage reused too early)."""
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_tma_and_bulk_row_paths_agree_bitwise(dims, R, offset):
+    """An aligned X goes through the tensor-map raw-tile ring, an X offset by 1-3 elements
+    through per-row bulk copies (or, with packed outer indices, per-thread loads); the
+    split and the MMAs are the same, so the outputs must be identical bit for bit
+    (catches a stage reused too early or a row read at the wrong word offset)."""
     X = torch.from_numpy(inputs.tensor_uniform_f32(17, dims)).cuda()
-    buf = torch.empty(X.numel() + 1, device="cuda")
-    Xu = buf[1:].view(dims)
+    buf = torch.empty(X.numel() + offset, device="cuda")
+    Xu = buf[offset:].view(dims)
     Xu.copy_(X)
     U = [torch.from_numpy(u).cuda() for u in _factors(17, dims, R)]
     for mode in range(len(dims)):
