@@ -97,8 +97,8 @@ def test_mttkrp_small_all_modes(dims, R, prec):
 @pytest.mark.parametrize("prec", ["plain", "split_bf16"])
 @pytest.mark.parametrize("offset", [1, 2, 3])
 def test_mttkrp_misaligned_x(prec, offset):
-    """X 4-byte but not 16-byte aligned: no tensor map; the tensor-core path copies each
-    row with one bulk copy from its first 16-byte granule (every word offset)."""
+    """X 4-byte but not 16-byte aligned: no tiled tensor map of the row view; the tensor-core
+    path loads through the four row-class maps (every word offset of X)."""
     dims, R = (130, 66, 128), 32
     X = inputs.tensor_uniform_f32(5, dims)
     Us = _factors(5, dims, R)
@@ -107,10 +107,10 @@ def test_mttkrp_misaligned_x(prec, offset):
         _check(got, oracle.mttkrp(X, Us, mode), "plain32" if prec == "plain" else prec)
 
 
-# Unaligned rows on the per-row bulk-copy path: several 128-row columns with a ragged last
-# one, narrow tiles of G p values (I < 128, P > 1) and a ragged last tile, last modes with
-# odd I over several columns, inner ranges with a ragged last chunk, a merged inner mode.
-BULK_CASES = [
+# Unaligned rows on the row-class path: several 128-row columns with a ragged last one,
+# narrow tiles of G p values (I < 128, P > 1) and a ragged last tile, last modes with odd I
+# over several columns, inner ranges with a ragged last chunk, a merged inner mode.
+ROWCLASS_CASES = [
     ((131, 45, 263), 32),      # K_in = 263: four offsets along a row; mode 2: I = 263, 3 columns
     ((7, 37, 11, 129), 16),    # mode 1: narrow tiles (I = 37, G = 3), P = 7; mode 3: I = 129
     ((3, 301, 77), 64),        # rank 64; mode 2: I = 77, O = 3 outer indices, not packed (P = 1)
@@ -118,8 +118,8 @@ BULK_CASES = [
 ]
 
 
-@pytest.mark.parametrize("dims,R", BULK_CASES)
-def test_mttkrp_bulk_row_path(dims, R):
+@pytest.mark.parametrize("dims,R", ROWCLASS_CASES)
+def test_mttkrp_rowclass_path(dims, R):
     X = inputs.tensor_uniform_f32(23, dims)
     Us = _factors(23, dims, R)
     for mode in range(len(dims)):
@@ -163,9 +163,9 @@ def test_mttkrp_bitwise_deterministic(prec):
 
 @pytest.mark.parametrize("dims,R", [((64, 64, 64, 64), 24), ((48, 40, 96, 64), 32), ((256, 300, 64), 16)])
 @pytest.mark.parametrize("offset", [1, 2, 3])
-def test_tma_and_bulk_row_paths_agree_bitwise(dims, R, offset):
+def test_tma_and_rowclass_paths_agree_bitwise(dims, R, offset):
     """An aligned X goes through the tensor-map raw-tile ring, an X offset by 1-3 elements
-    through per-row bulk copies (or, with packed outer indices, per-thread loads); the
+    through the row-class maps (or, with packed outer indices, per-thread loads); the
     split and the MMAs are the same, so the outputs must be identical bit for bit
     (catches a stage reused too early or a row read at the wrong word offset)."""
     X = torch.from_numpy(inputs.tensor_uniform_f32(17, dims)).cuda()
