@@ -104,6 +104,7 @@ struct Inst {
     int opmode[DEINSUM_MAX_ORDER + 1] = {0};
     MttkrpGeom g{};
     double xbytes = 0.0;
+    bool rc = false;   // rows not 16-byte aligned: the row-class kernel's unit list
 };
 
 std::mutex g_tune_mutex;
@@ -146,10 +147,11 @@ struct deinsum_batch_s {
     double total_bytes = 0.0;
     std::string signature;
     int unit_div = 4;   // units of about total / (grid * unit_div) bytes
-    int n_sm = 0, grid = 0;
+    int n_sm = 0, grid = 0;          // grid: the larger of the two launches
+    int grid_t = 0, grid_r = 0;      // launches over tensor-map / per-thread instances, row-class ones
     // schedule (host)
-    std::vector<int64_t> units;      // 5 per unit, grouped by CTA
-    std::vector<int64_t> cta_begin;  // grid + 1
+    std::vector<int64_t> units;      // 5 per unit, grouped by CTA: the first launch's units, then the second's
+    std::vector<int64_t> cta_begin;  // grid_t + 1, then grid_r + 1 (indices into units)
     std::vector<int64_t> red_off;    // partial offsets, per instance, column, split
     std::vector<int64_t> red_col;    // per instance: n_cols + 1 starts into red_off
     std::vector<int64_t> red_col_base;
@@ -223,31 +225,39 @@ void build_batch_schedule(deinsum_batch_s *b) {
         b->wtab_bytes += up(wf * 4, 256);
         b->max_wtab_floats = std::max<int64_t>(b->max_wtab_floats, int64_t(wf));
     }
-    b->grid = int(std::min<int64_t>(b->n_sm, int64_t(all.size())));
-    if (b->grid < 1) b->grid = 1;
-    std::vector<size_t> order(all.size());
-    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return all[x].cost > all[y].cost; });
-    using Load = std::pair<double, int>;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (int c = 0; c < b->grid; ++c) heap.push({0.0, c});
-    std::vector<std::vector<size_t>> per_cta(size_t(b->grid));
-    for (size_t k : order) {
-        Load top = heap.top();
-        heap.pop();
-        per_cta[size_t(top.second)].push_back(k);
-        heap.push({top.first + all[k].cost, top.second});
-    }
+    // two unit lists (instances on the tensor map or per-thread loads; row-class instances),
+    // each assigned to its launch's CTAs largest first onto the least-loaded CTA
     b->units.clear();
-    b->cta_begin.assign(size_t(b->grid) + 1, 0);
-    for (int c = 0; c < b->grid; ++c) {
-        b->cta_begin[size_t(c)] = int64_t(b->units.size() / 5);
-        for (size_t k : per_cta[size_t(c)]) {
-            const U &u = all[k];
-            b->units.insert(b->units.end(), {u.inst, u.col, u.f0, u.f1, u.off});
+    b->cta_begin.clear();
+    auto assign = [&](bool rc) {
+        std::vector<size_t> order;
+        for (size_t k = 0; k < all.size(); ++k)
+            if (b->inst[size_t(all[k].inst)].rc == rc) order.push_back(k);
+        const int grid = int(std::min<int64_t>(b->n_sm, int64_t(order.size())));
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return all[x].cost > all[y].cost; });
+        using Load = std::pair<double, int>;
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+        for (int c = 0; c < grid; ++c) heap.push({0.0, c});
+        std::vector<std::vector<size_t>> per_cta(static_cast<size_t>(grid));
+        for (size_t k : order) {
+            Load top = heap.top();
+            heap.pop();
+            per_cta[size_t(top.second)].push_back(k);
+            heap.push({top.first + all[k].cost, top.second});
         }
-    }
-    b->cta_begin[size_t(b->grid)] = int64_t(b->units.size() / 5);
+        for (int c = 0; c < grid; ++c) {
+            b->cta_begin.push_back(int64_t(b->units.size() / 5));
+            for (size_t k : per_cta[size_t(c)]) {
+                const U &u = all[k];
+                b->units.insert(b->units.end(), {u.inst, u.col, u.f0, u.f1, u.off});
+            }
+        }
+        b->cta_begin.push_back(int64_t(b->units.size() / 5));
+        return grid;
+    };
+    b->grid_t = assign(false);
+    b->grid_r = assign(true);
+    b->grid = std::max(1, std::max(b->grid_t, b->grid_r));
 }
 
 deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
@@ -314,7 +324,8 @@ deinsum_status upload_instances(deinsum_batch_s *b, const void *const *const *in
         MttkrpArgs &a = A[i];
         std::memset(static_cast<void *>(&a), 0, sizeof(a));
         mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, inputs[i][0], &a, false);
-        a.row_classes = 0;   // the batched kernel loads unaligned rows per thread
+        if (in.rc && !a.row_classes) return DEINSUM_ERR_CUDA;   // the maps of a planned row-class instance
+        if (!in.rc) a.row_classes = 0;
         a.X = inputs[i][0];
         for (int k = 1; k < in.n_ops; ++k) a.U[in.opmode[k]] = inputs[i][k];
         a.Bsplit = b->ws + b->o_bsplit + b->bsplit_off[size_t(i)];
@@ -352,10 +363,17 @@ deinsum_status launch_batch(deinsum_batch_s *b, cudaStream_t s) {
     BatchArgs ba;
     ba.insts = reinterpret_cast<const MttkrpArgs *>(b->ws + b->o_insts);
     ba.units = reinterpret_cast<const int64_t *>(b->ws + b->o_units);
-    ba.cta_begin = reinterpret_cast<const int64_t *>(b->ws + b->o_cta);
     ba.partial = reinterpret_cast<float *>(b->ws + b->o_partial);
     ba.status = reinterpret_cast<int *>(b->ws + b->o_status);
-    if (launch_mttkrp_tc_batched(ba, b->grid, s)) return DEINSUM_ERR_CUDA;
+    const int64_t *cta = reinterpret_cast<const int64_t *>(b->ws + b->o_cta);
+    if (b->grid_t > 0) {
+        ba.cta_begin = cta;
+        if (launch_mttkrp_tc_batched(ba, b->grid_t, false, s)) return DEINSUM_ERR_CUDA;
+    }
+    if (b->grid_r > 0) {
+        ba.cta_begin = cta + (b->grid_t + 1);
+        if (launch_mttkrp_tc_batched(ba, b->grid_r, true, s)) return DEINSUM_ERR_CUDA;
+    }
     int64_t maxo = 1;
     for (auto &i : b->inst) maxo = std::max<int64_t>(maxo, i.g.I * i.g.R);
     int rx = int(std::min<int64_t>(64, (maxo + 255) / 256));
@@ -434,6 +452,7 @@ deinsum_status deinsum_plan_batched(int n, const char *const *einsums, const int
         std::memset(static_cast<void *>(&tmp), 0, sizeof(tmp));
         mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, nullptr, &tmp, false);
         in.g = tmp.g;
+        in.rc = !tmp.g.vec_ok && rowclass_supported(tmp.g);   // X itself 4-byte aligned suffices
         in.xbytes = 4.0;
         for (int m = 0; m < in.order; ++m) in.xbytes *= double(in.dims[m]);
         b->total_bytes += in.xbytes;

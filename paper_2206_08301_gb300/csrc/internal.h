@@ -116,7 +116,9 @@ struct BatchArgs {
     float *partial;
     int *status;
 };
-int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, void *stream);
+// rc: every instance of the unit list loads X through its row-class maps (row_classes set);
+// otherwise through its tensor map (use_tma) or per-thread loads.
+int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, bool rc, void *stream);
 size_t mttkrp_tc_batched_smem_bytes();
 
 // Fused last-two-mode stage of a TTMc keeping a mode n < N-2 (ttmc_tc.cu):
@@ -157,6 +159,8 @@ bool encode_ttm_last_map(const void *X, int64_t S, int64_t K, int64_t L, CUtenso
 // not 16-byte aligned; false with packed outer indices, fewer than 4 rows (lines), extents
 // beyond int32 coordinates or no encoder.
 bool encode_x_rowclass_maps(const MttkrpGeom &g, const void *X, CUtensorMap *maps);
+// Whether the geometry allows them (the conditions above other than X and the encoder).
+bool rowclass_supported(const MttkrpGeom &g);
 // Their converter view of a chunk (case 0, I = K, narrow when K < 128 and sg = 1 -- with sg > 1
 // the box fills all 128 rows --, R_pad 32, ceil(L/64) chunks).
 void ttm_last_geometry(int order, int64_t S, int64_t K, int64_t L, int R, MttkrpGeom *g, int sg = 1);

@@ -953,6 +953,9 @@ struct BIter {
 
 constexpr int RPB = 64;  // the batched kernel is shaped for the largest padded rank
 
+// RCB: every instance loads X through its row-class maps (one unit list per kind: the code of
+// both kinds in one kernel slows the tensor-map instances).
+template <bool RCB>
 __global__ void __launch_bounds__(TcCfg<RPB>::THREADS, 1)
 mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     using C = TcCfg<RPB>;
@@ -1023,9 +1026,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         BIter it;
         it.init(&bargs);
         uint32_t bpar = 0, bused = 0;
-        // the raw ring carries only the chunks of TMA-loaded instances: count those apart.
-        // Instances whose rows are not 16-byte aligned take the per-thread loads here (the
-        // row-class path in this one kernel for all instances measured slower overall).
+        // the raw ring carries only the chunks of TMA-loaded instances: count those apart
         int64_t tchunk = 0;
         // last-mode instances (case 1; the batch packs no outer indices) take the MN-major
         // operand; their row positions in the raw tile are set up when the instance changes
@@ -1040,12 +1041,15 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             }
             float4 v[8];
             const int rs = int(tchunk % RS);
-            if (a.use_tma) {
+            if (RCB || a.use_tma) {
                 const uint32_t rj = uint32_t(tchunk / RS);
                 ++tchunk;
                 if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
                 const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_STAGE);
-                if (mn && a.raw_pitch == BM) conv_read_smem_mn128(raw, pt, v);
+                if (RCB) {
+                    if (mn) conv_read_rowcls_mn(a.g, a.X, it.col, it.o, it.kb, raw, pt, v);
+                    else conv_read_rowcls(a.g, a.X, it.col, it.tile, it.o, it.kb, raw, rowcls_thread(pt), v);
+                } else if (mn && a.raw_pitch == BM) conv_read_smem_mn128(raw, pt, v);
                 else if (mn) conv_read_smem_mn(mp, a.raw_pitch, raw, pt, v);
                 else if (!a.g.narrow || a.g.G * a.g.I == BM) conv_read_smem_wide(raw, pt, v);
                 else conv_read_smem(a, raw, pt, v);
@@ -1068,7 +1072,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 bused |= 1u << as;
             }
             if (mn) conv_store_mn(pt, a_hi(as), a_lo(as), v);
-            else conv_store(a.g, pt, a_hi(as), a_lo(as), v);
+            else conv_store(a.g, RCB ? rowcls_thread(pt) : pt, a_hi(as), a_lo(as), v);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(a_full(as));
@@ -1100,17 +1104,22 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                     last_wpar = wj & 1u;
                     ++fgi;
                 }
-                if (a.use_tma && fenced != it.a) {
-                    fence_tensormap_acquire(&a.xmap);
+                if ((RCB || a.use_tma) && fenced != it.a) {
+                    if (RCB)
+                        for (int c = 0; c < 4; ++c) fence_tensormap_acquire(&a.xrow[c]);
+                    else
+                        fence_tensormap_acquire(&a.xmap);
                     fenced = it.a;
                 }
-                if (a.use_tma) {
+                if (RCB || a.use_tma) {
                     const int rs = int(tchunk % RS);
                     const uint32_t rj = uint32_t(tchunk / RS);
                     ++tchunk;
                     if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status)) break;
                     const int kc = it.kb * BK;
-                    if (a.g.opack) {
+                    if (RCB) {
+                        rowcls_load(a, it.col, it.tile, it.o, it.kb, raw_addr(rs), raw_full(rs));
+                    } else if (a.g.opack) {
                         mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                         const int o0 = int(it.tile * a.g.G);
                         if (a.g.kcase == 0) tma_load_4d(raw_addr(rs), &a.xmap, kc, 0, o0, 0, raw_full(rs));
@@ -1298,12 +1307,12 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
 
 size_t mttkrp_tc_batched_smem_bytes() { return TcCfg<RPB>::SMEM; }
 
-int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, void *stream) {
+int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, bool rc, void *stream) {
     using C = TcCfg<RPB>;
-    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(C::SMEM));
+    auto kern = rc ? mttkrp_tc_batched_kernel<true> : mttkrp_tc_batched_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
     if (e != cudaSuccess) return int(e);
-    mttkrp_tc_batched_kernel<<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(b);
+    kern<<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(b);
     count_launch();
     return int(cudaGetLastError());
 }

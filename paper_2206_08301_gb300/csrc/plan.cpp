@@ -851,13 +851,18 @@ namespace deinsum {
 // len = Q (case 0) or I (case 1) and d_c = that start's word offset in its granule; the
 // kernels load boxes of {BK + 4, BM / 4} (case 0) or {BM + 4, BK / 4} (case 1).  Every
 // address a box can reach lies in a granule that holds an element of X.
-bool encode_x_rowclass_maps(const MttkrpGeom &g, const void *X, CUtensorMap *maps) {
-    auto enc = tensor_map_encoder();
-    if (!enc || g.opack || (reinterpret_cast<uintptr_t>(X) & 3) != 0) return false;
+bool rowclass_supported(const MttkrpGeom &g) {
     const int64_t lim = int64_t(1) << 31;
     const int64_t len = g.kcase == 0 ? g.Q : g.I;                     // words per row (line)
     const int64_t n = g.kcase == 0 ? g.P * g.I : g.O * g.K_in;       // rows (lines)
-    if (n < 4 || len + 3 >= lim || n >= 4 * lim) return false;
+    return !g.opack && n >= 4 && len + 3 < lim && n < 4 * lim;
+}
+
+bool encode_x_rowclass_maps(const MttkrpGeom &g, const void *X, CUtensorMap *maps) {
+    auto enc = tensor_map_encoder();
+    if (!enc || !rowclass_supported(g) || (reinterpret_cast<uintptr_t>(X) & 3) != 0) return false;
+    const int64_t len = g.kcase == 0 ? g.Q : g.I;
+    const int64_t n = g.kcase == 0 ? g.P * g.I : g.O * g.K_in;
     const uintptr_t xw = reinterpret_cast<uintptr_t>(X) >> 2;
     for (int c = 0; c < 4; ++c) {
         const uintptr_t start = xw + uintptr_t(c) * uintptr_t(len);   // word address of member 0

@@ -91,3 +91,39 @@ def test_batched_autotune_keeps_results():
     torch.cuda.synchronize()
     for (dims, R, mode, X, U), out in zip(items, outs):
         assert oracle.rel_error(out.cpu().numpy(), oracle.mttkrp(X, U, mode)) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["aligned", "unaligned", "offset"])
+def test_batched_launch_groups(kind):
+    """Instances whose rows are 16-byte aligned run in the first launch (tensor map, or
+    per-thread loads when X itself starts off a 16-byte boundary), the others in the
+    row-class launch; a batch of one kind leaves the other launch empty."""
+    seed = 41
+    n = 12
+    ext = inputs.draw_int(seed, 0, 9, 70, 3 * n).reshape(n, 3)
+    ext = (ext | 1) if kind == "unaligned" else ((ext + 3) // 4 * 4)
+    ranks = np.array([8, 16, 32, 64])[inputs.draw_int(seed, 1, 0, 3, n)]
+    modes = inputs.draw_int(seed, 2, 0, 2, n)
+    einsums, extents, ins, outs, ref = [], [], [], [], []
+    for k in range(n):
+        dims = tuple(int(d) for d in ext[k])
+        R, mode = int(ranks[k]), int(modes[k])
+        X = inputs.tensor_uniform_f32(seed * 1000 + k, dims)
+        U = [inputs.factor_normal(seed * 1000 + k, m, d, R).astype(np.float32) for m, d in enumerate(dims)]
+        if kind == "offset":
+            buf = torch.empty(X.size + 1, device="cuda")
+            Xd = buf[1:].view(dims)
+            Xd.copy_(torch.from_numpy(X))
+        else:
+            Xd = torch.from_numpy(X).cuda()
+        einsums.append(dz.mttkrp_einsum(3, mode))
+        extents.append(list(dims) + [R])
+        ins.append([Xd] + [torch.from_numpy(U[m]).cuda() for m in range(3) if m != mode])
+        outs.append(torch.empty(dims[mode], R, device="cuda"))
+        ref.append(oracle.mttkrp(X, U, mode))
+    b = dz.Batch(einsums, extents, "split_bf16")
+    b(ins, outs)
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    for out, r in zip(outs, ref):
+        assert oracle.rel_error(out.cpu().numpy(), r) <= 1e-5
