@@ -113,8 +113,8 @@ def test_mttkrp_misaligned_x(prec, offset):
 ROWCLASS_CASES = [
     ((131, 45, 263), 32),      # K_in = 263: four offsets along a row; mode 2: I = 263, 3 columns
     ((7, 37, 11, 129), 16),    # mode 1: narrow tiles (I = 37, G = 3), P = 7; mode 3: I = 129
-    ((3, 301, 77), 64),        # rank 64; mode 2: I = 77, O = 3 outer indices, not packed (P = 1)
-    ((9, 15, 5, 47), 8),       # short modes: merged inner (5 x 47) in modes 0, 1
+    ((3, 301, 77), 64),        # rank 64; mode 1: I = 301, 3 columns; mode 2: I = 77 > 64 (not packed)
+    ((9, 15, 5, 47), 8),       # mode 1: merged inner mode (5 x 47); mode 2: 16 p values per tile
 ]
 
 
