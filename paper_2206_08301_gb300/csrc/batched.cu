@@ -104,7 +104,7 @@ struct Inst {
     int opmode[DEINSUM_MAX_ORDER + 1] = {0};
     MttkrpGeom g{};
     double xbytes = 0.0;
-    bool rc = false;   // rows not 16-byte aligned: the row-class kernel's unit list
+    int kind = 0;   // 0: tensor map or per-thread loads; 1 / 2: row classes, case 0 / case 1 (own launches)
 };
 
 std::mutex g_tune_mutex;
@@ -147,11 +147,11 @@ struct deinsum_batch_s {
     double total_bytes = 0.0;
     std::string signature;
     int unit_div = 4;   // units of about total / (grid * unit_div) bytes
-    int n_sm = 0, grid = 0;          // grid: the larger of the two launches
-    int grid_t = 0, grid_r = 0;      // launches over tensor-map / per-thread instances, row-class ones
+    int n_sm = 0, grid = 0;          // grid: the largest of the launches
+    int grids[3] = {0, 0, 0};        // CTAs of the launch over each instance kind
     // schedule (host)
-    std::vector<int64_t> units;      // 5 per unit, grouped by CTA: the first launch's units, then the second's
-    std::vector<int64_t> cta_begin;  // grid_t + 1, then grid_r + 1 (indices into units)
+    std::vector<int64_t> units;      // 5 per unit, grouped by CTA: kind 0's launch, then kind 1's, then kind 2's
+    std::vector<int64_t> cta_begin;  // grids[k] + 1 per kind, in that order (indices into units)
     std::vector<int64_t> red_off;    // partial offsets, per instance, column, split
     std::vector<int64_t> red_col;    // per instance: n_cols + 1 starts into red_off
     std::vector<int64_t> red_col_base;
@@ -225,14 +225,15 @@ void build_batch_schedule(deinsum_batch_s *b) {
         b->wtab_bytes += up(wf * 4, 256);
         b->max_wtab_floats = std::max<int64_t>(b->max_wtab_floats, int64_t(wf));
     }
-    // two unit lists (instances on the tensor map or per-thread loads; row-class instances),
-    // each assigned to its launch's CTAs largest first onto the least-loaded CTA
+    // one unit list per instance kind (tensor map or per-thread loads; row classes in case 0;
+    // row classes in case 1), each assigned to its launch's CTAs largest first onto the
+    // least-loaded CTA
     b->units.clear();
     b->cta_begin.clear();
-    auto assign = [&](bool rc) {
+    auto assign = [&](int kind) {
         std::vector<size_t> order;
         for (size_t k = 0; k < all.size(); ++k)
-            if (b->inst[size_t(all[k].inst)].rc == rc) order.push_back(k);
+            if (b->inst[size_t(all[k].inst)].kind == kind) order.push_back(k);
         const int grid = int(std::min<int64_t>(b->n_sm, int64_t(order.size())));
         std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return all[x].cost > all[y].cost; });
         using Load = std::pair<double, int>;
@@ -255,9 +256,11 @@ void build_batch_schedule(deinsum_batch_s *b) {
         b->cta_begin.push_back(int64_t(b->units.size() / 5));
         return grid;
     };
-    b->grid_t = assign(false);
-    b->grid_r = assign(true);
-    b->grid = std::max(1, std::max(b->grid_t, b->grid_r));
+    b->grid = 1;
+    for (int k = 0; k < 3; ++k) {
+        b->grids[k] = assign(k);
+        b->grid = std::max(b->grid, b->grids[k]);
+    }
 }
 
 deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
@@ -324,8 +327,8 @@ deinsum_status upload_instances(deinsum_batch_s *b, const void *const *const *in
         MttkrpArgs &a = A[i];
         std::memset(static_cast<void *>(&a), 0, sizeof(a));
         mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, inputs[i][0], &a, false);
-        if (in.rc && !a.row_classes) return DEINSUM_ERR_CUDA;   // the maps of a planned row-class instance
-        if (!in.rc) a.row_classes = 0;
+        if (in.kind && !a.row_classes) return DEINSUM_ERR_CUDA;   // the maps of a planned row-class instance
+        if (!in.kind) a.row_classes = 0;
         a.X = inputs[i][0];
         for (int k = 1; k < in.n_ops; ++k) a.U[in.opmode[k]] = inputs[i][k];
         a.Bsplit = b->ws + b->o_bsplit + b->bsplit_off[size_t(i)];
@@ -366,13 +369,12 @@ deinsum_status launch_batch(deinsum_batch_s *b, cudaStream_t s) {
     ba.partial = reinterpret_cast<float *>(b->ws + b->o_partial);
     ba.status = reinterpret_cast<int *>(b->ws + b->o_status);
     const int64_t *cta = reinterpret_cast<const int64_t *>(b->ws + b->o_cta);
-    if (b->grid_t > 0) {
-        ba.cta_begin = cta;
-        if (launch_mttkrp_tc_batched(ba, b->grid_t, false, s)) return DEINSUM_ERR_CUDA;
-    }
-    if (b->grid_r > 0) {
-        ba.cta_begin = cta + (b->grid_t + 1);
-        if (launch_mttkrp_tc_batched(ba, b->grid_r, true, s)) return DEINSUM_ERR_CUDA;
+    for (int k = 0; k < 3; ++k) {
+        if (b->grids[k] > 0) {
+            ba.cta_begin = cta;
+            if (launch_mttkrp_tc_batched(ba, b->grids[k], k, s)) return DEINSUM_ERR_CUDA;
+        }
+        cta += b->grids[k] + 1;
     }
     int64_t maxo = 1;
     for (auto &i : b->inst) maxo = std::max<int64_t>(maxo, i.g.I * i.g.R);
@@ -452,7 +454,8 @@ deinsum_status deinsum_plan_batched(int n, const char *const *einsums, const int
         std::memset(static_cast<void *>(&tmp), 0, sizeof(tmp));
         mttkrp_prepare_oneoff(in.order, in.dims, in.mode, in.R, nullptr, &tmp, false);
         in.g = tmp.g;
-        in.rc = !tmp.g.vec_ok && rowclass_supported(tmp.g);   // X itself 4-byte aligned suffices
+        // rows not 16-byte aligned: row classes (X itself 4-byte aligned suffices), one launch per case
+        in.kind = (!tmp.g.vec_ok && rowclass_supported(tmp.g)) ? (tmp.g.kcase == 1 ? 2 : 1) : 0;
         in.xbytes = 4.0;
         for (int m = 0; m < in.order; ++m) in.xbytes *= double(in.dims[m]);
         b->total_bytes += in.xbytes;

@@ -116,9 +116,10 @@ struct BatchArgs {
     float *partial;
     int *status;
 };
-// rc: every instance of the unit list loads X through its row-class maps (row_classes set);
-// otherwise through its tensor map (use_tma) or per-thread loads.
-int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, bool rc, void *stream);
+// kind 0: every instance of the unit list loads X through its tensor map (use_tma) or per
+// thread; kind 1 / 2: through its row-class maps (row_classes set), all of them case 0 /
+// case 1 (the last mode, MN-major operand).
+int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, int kind, void *stream);
 size_t mttkrp_tc_batched_smem_bytes();
 
 // Fused last-two-mode stage of a TTMc keeping a mode n < N-2 (ttmc_tc.cu):

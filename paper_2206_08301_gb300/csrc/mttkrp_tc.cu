@@ -953,9 +953,10 @@ struct BIter {
 
 constexpr int RPB = 64;  // the batched kernel is shaped for the largest padded rank
 
-// RCB: every instance loads X through its row-class maps (one unit list per kind: the code of
-// both kinds in one kernel slows the tensor-map instances).
-template <bool RCB>
+// RCB: every instance loads X through its row-class maps, all of them with the operand
+// layout MNB (MN-major A for last modes): one unit list per kind, because the code of
+// several kinds in one kernel slows each of them (instruction fetch).
+template <bool RCB, bool MNB>
 __global__ void __launch_bounds__(TcCfg<RPB>::THREADS, 1)
 mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     using C = TcCfg<RPB>;
@@ -1034,8 +1035,8 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         MnPos mp;
         for (int64_t chunk = 0; !it.done; ++chunk) {
             const MttkrpArgs &a = *it.a;
-            const bool mn = a.g.kcase == 1;
-            if (mn && mp_for != it.a) {
+            const bool mn = RCB ? MNB : a.g.kcase == 1;
+            if (!RCB && mn && mp_for != it.a) {
                 mp = mn_pos(a.raw_pitch > 0 ? a.raw_pitch : BM, 1, pt);
                 mp_for = it.a;
             }
@@ -1159,7 +1160,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                     if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
                     tc_fence_after();
                     dcol = tmem + uint32_t(b * C::N);
-                    mn = a.g.kcase == 1;   // the last mode: MN-major A (see the converters)
+                    mn = RCB ? MNB : a.g.kcase == 1;   // the last mode: MN-major A (see the converters)
                     idesc = idesc_bf16_f32(BM, 2 * a.g.R_pad) | (mn ? kIdescAMnMajor : 0u);
                 }
                 const int s = int(chunk % AS);
@@ -1307,9 +1308,10 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
 
 size_t mttkrp_tc_batched_smem_bytes() { return TcCfg<RPB>::SMEM; }
 
-int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, bool rc, void *stream) {
+int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, int kind, void *stream) {
     using C = TcCfg<RPB>;
-    auto kern = rc ? mttkrp_tc_batched_kernel<true> : mttkrp_tc_batched_kernel<false>;
+    auto kern = kind == 2 ? mttkrp_tc_batched_kernel<true, true>
+                          : (kind == 1 ? mttkrp_tc_batched_kernel<true, false> : mttkrp_tc_batched_kernel<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
     if (e != cudaSuccess) return int(e);
     kern<<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(b);
