@@ -366,8 +366,9 @@ def run_serving(args):
 
 def run_batched(args):
     """512 uneven order-3 MTTKRP instances (extents U{32..384}, R in {8,16,32,64}, mode U{0,1,2},
-    X uniform[-1,1) float32): one graph-replayed persistent split-BF16 launch (autotuned unit
-    size) against 512 separate plain launches and 512 separate split launches."""
+    X uniform[-1,1) float32): the graph-replayed persistent split-BF16 launches, one per
+    instance kind (autotuned unit size), against 512 separate plain launches and 512 separate
+    split launches."""
     import torch
     import oracle
     import paper_2206_08301_gb300 as dz
@@ -423,7 +424,7 @@ def run_batched(args):
     plans = [dz.Plan(e, x, "float32", "split_bf16") for e, x in zip(einsums, extents)]
     t_sep = timed(lambda: [p(*i, out=o, stream=stream) for p, i, o in zip(plans, ins, outs)], max(1, args.steps // 2))
     gb = info["alg_bytes"] / 1e9
-    line = {"metric": "batched MTTKRP GB/s (one persistent launch vs separate launches)", "unit": "GB/s",
+    line = {"metric": "batched MTTKRP GB/s (persistent launches vs separate launches)", "unit": "GB/s",
             "value": gb / (t_batch * 1e-3), "n_gpus": 1, "instances": n, "data": "synthetic",
             "config": {"workload": f"{n} order-3 MTTKRP instances, extents U{{32..384}}, R in {{8,16,32,64}}, "
                                    "mode U{0,1,2}, X uniform[-1,1) float32", "alg_gb": gb,

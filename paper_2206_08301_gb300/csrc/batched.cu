@@ -1,12 +1,14 @@
-// Batched MTTKRP: many instances of uneven extents and ranks in one
-// persistent tensor-core launch, replayed from a captured CUDA graph.
+// Batched MTTKRP: many instances of uneven extents and ranks in up to three
+// persistent tensor-core launches, replayed from a captured CUDA graph: one over
+// the instances whose rows are 16-byte aligned (tensor map), one per operand
+// layout over the others (row-class tensor maps).  Code for several kinds in one
+// kernel slowed all of them (instruction fetch), hence a launch per kind.
 //
 // Host side: every instance is classified by a regular plan (Sec. III-B MTTKRP
 // einsum); its row view is cut into work units (column of 128 output rows x a
-// range of fiber groups) of about `unit_bytes` of X each; the units of all
-// instances are assigned to the CTAs largest first (LPT: each unit goes to the
-// least-loaded CTA), so that one launch of one CTA per SM finishes them
-// together.  The granularity is picked by an autotuner that times candidate
+// range of fiber groups) of about `unit_bytes` of X each; the units of each kind
+// are assigned to the CTAs of its launch largest first (LPT: each unit goes to
+// the least-loaded CTA), so that one CTA per SM finishes them together.  The granularity is picked by an autotuner that times candidate
 // schedules on the device and remembers the winner per batch signature.
 // Device side: a batched split of the instances' inner factors, the batched
 // tensor-core kernel (mttkrp_tc.cu), and a batched fixed-order reduction of

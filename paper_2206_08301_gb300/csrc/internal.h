@@ -104,7 +104,7 @@ struct MttkrpArgs {
     int *status;                       // device status word
 };
 
-// Many MTTKRP instances in one persistent launch of the tensor-core kernel:
+// Many MTTKRP instances in persistent launches of the tensor-core kernel (one per kind):
 // per-instance arguments (geometry, TMA descriptor of X, factor pointers,
 // split factor tiles) live in device memory; every CTA walks its own list of
 // units, each unit = (instance, column, first fiber group, end, offset of its

@@ -1,4 +1,4 @@
-"""Batched MTTKRP: uneven instances in one persistent launch (graph-replayed).
+"""Batched MTTKRP: uneven instances in persistent launches, one per kind (graph-replayed).
 
 Each instance of the batch matches the FP64 oracle within the split-BF16 gate
 (relative Frobenius 1e-5) and the single-instance split path within 1e-5;
