@@ -98,6 +98,12 @@ typedef struct {
     double alg_flops;         /* 2 x multiply-adds of the FLOP-minimal binary chain */
     int64_t n_units;          /* work units of the main kernel (0 before the first execute) */
     int64_t mm_cols;          /* MTTKRP followed by a matrix product: L (columns of C); else 0 */
+    /* MTTKRP: the row view the kernels run (zero for TTMc) */
+    int view_merged;          /* the inner mode is merged with its neighbour (split-BF16) */
+    int view_packed;          /* tiles hold several outer indices (rows of at most 64) */
+    int64_t view_groups;      /* leading indices (or packed outer indices) per 128-row tile */
+    int view_aligned_rows;    /* rows are 16-byte aligned when X is: one tensor map */
+    int view_row_classes;     /* otherwise the four row-class maps serve them (split-BF16 F32) */
 } deinsum_plan_info_t;
 
 /*

@@ -48,7 +48,9 @@ class _PlanInfo(ctypes.Structure):
                 ("dtype", ctypes.c_int), ("prec", ctypes.c_int),
                 ("dims", ctypes.c_int64 * 8), ("ranks", ctypes.c_int64 * 8),
                 ("out_elems", ctypes.c_int64), ("alg_bytes", ctypes.c_double),
-                ("alg_flops", ctypes.c_double), ("n_units", ctypes.c_int64), ("mm_cols", ctypes.c_int64)]
+                ("alg_flops", ctypes.c_double), ("n_units", ctypes.c_int64), ("mm_cols", ctypes.c_int64),
+                ("view_merged", ctypes.c_int), ("view_packed", ctypes.c_int), ("view_groups", ctypes.c_int64),
+                ("view_aligned_rows", ctypes.c_int), ("view_row_classes", ctypes.c_int)]
 
 
 class _Request(ctypes.Structure):
@@ -222,7 +224,10 @@ class Plan:
         return {"kind": KINDS[info.kind], "order": info.order, "mode": info.mode,
                 "dims": list(info.dims[:info.order]), "ranks": list(info.ranks[:info.order]),
                 "out_elems": info.out_elems, "alg_bytes": info.alg_bytes, "alg_flops": info.alg_flops,
-                "n_units": info.n_units, "mm_cols": info.mm_cols}
+                "n_units": info.n_units, "mm_cols": info.mm_cols,
+                "view": {"merged": bool(info.view_merged), "packed": bool(info.view_packed),
+                         "groups": info.view_groups, "aligned_rows": bool(info.view_aligned_rows),
+                         "row_classes": bool(info.view_row_classes)}}
 
     def workspace_size(self) -> int:
         n = ctypes.c_size_t()

@@ -1066,6 +1066,15 @@ deinsum_status deinsum_plan_info(deinsum_plan_t pl, deinsum_plan_info_t *info) {
     info->alg_bytes = alg_bytes(pl);
     info->alg_flops = alg_flops(pl);
     info->n_units = pl->planned_units;
+    if (pl->kind == DEINSUM_KIND_MTTKRP) {
+        const MttkrpGeom &g = pl->geom;
+        info->view_merged = pl->merge ? 1 : 0;
+        info->view_packed = g.opack;
+        info->view_groups = g.G;
+        info->view_aligned_rows = g.vec_ok;
+        info->view_row_classes = (pl->prec == DEINSUM_PREC_SPLIT_BF16 && pl->dtype == DEINSUM_F32 && !g.vec_ok &&
+                                  rowclass_supported(g)) ? 1 : 0;
+    }
     return DEINSUM_OK;
 }
 

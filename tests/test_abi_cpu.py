@@ -180,3 +180,35 @@ def test_mttkrp_mm_plan(lib):
                     letters.append(c)
             dz.Plan(spec, [4] * len(letters))
         assert e.value.status == 2, spec
+
+
+def test_mttkrp_row_view_decisions(lib):
+    """The planner's row view: merged short inner modes, packed outer indices for short
+    rows, leading indices per tile (at most 16), and how X's rows are loaded (one tensor
+    map when the rows are 16-byte aligned, else the four row-class maps)."""
+    def view(dims, mode, prec="split_bf16", R=8):
+        return dz.Plan(dz.mttkrp_einsum(len(dims), mode), list(dims) + [R], "float32", prec).info()["view"]
+
+    for mode in range(3):   # 1024^3: aligned rows, no regrouping
+        assert view((1024, 1024, 1024), mode) == {"merged": False, "packed": False, "groups": 1,
+                                                  "aligned_rows": True, "row_classes": False}
+        v = view((1023, 1023, 1023), mode)
+        assert not v["aligned_rows"] and v["row_classes"]
+    # inner mode of 47 merged with its neighbour of 5: mode 0 then packs 14 outer indices of
+    # 9 rows; mode 1 takes 8 leading indices of 15 rows; mode 2 (not merged: its inner mode is
+    # the last one) is capped at 16 leading indices of 5 rows; the last mode packs again
+    assert view((9, 15, 5, 47), 0) == {"merged": True, "packed": True, "groups": 14,
+                                       "aligned_rows": False, "row_classes": False}
+    assert view((9, 15, 5, 47), 1) == {"merged": True, "packed": False, "groups": 8,
+                                       "aligned_rows": False, "row_classes": True}
+    assert view((9, 15, 5, 47), 2)["groups"] == 16 and not view((9, 15, 5, 47), 2)["merged"]
+    assert view((9, 15, 5, 47), 3)["packed"]
+    # a last mode of 77 rows is not packed (rows above 64) and takes the row classes
+    v = view((3, 301, 77), 2)
+    assert not v["packed"] and v["row_classes"]
+    assert view((40, 6, 7, 8, 36), 0)["packed"] and view((40, 6, 7, 8, 36), 0)["groups"] == 3
+    # the plain precision neither merges nor uses row classes
+    v = view((9, 15, 5, 47), 1, prec="plain")
+    assert not v["merged"] and not v["row_classes"]
+    # TTMc plans carry no MTTKRP view
+    assert dz.Plan(dz.ttmc_einsum(3, 0), [50, 300, 132, 17, 31], prec="split_bf16").info()["view"]["groups"] == 0
