@@ -172,10 +172,25 @@ deinsum_status deinsum_plan_bind_workspace(deinsum_plan_t plan, void *workspace,
 /* Fill *info with the plan summary.  Host only. */
 deinsum_status deinsum_plan_info(deinsum_plan_t plan, deinsum_plan_info_t *info);
 
-/* Device-side status of the plan's last execute: DEINSUM_OK, or
- * DEINSUM_ERR_TIMEOUT when a bounded wait inside a kernel gave up.  Reads one
- * word from the device (synchronous); call after synchronising the stream. */
+/* Device-side status of the plan's executes since the workspace was attached or
+ * since the previous call: DEINSUM_OK, or DEINSUM_ERR_TIMEOUT when a bounded
+ * wait inside a kernel gave up (that execute's output is then incomplete; the
+ * kernel stopped every role, let its own copies and MMAs finish and returned).
+ * Reads one word from the device and, if it was set, clears it (synchronous);
+ * call after synchronising the stream. */
 deinsum_status deinsum_last_device_status(deinsum_plan_t plan);
+
+/* Limit, in nanoseconds, of every bounded wait inside the tensor-core kernels
+ * launched from now on (process-wide; 0 restores the default of 2 s).  The
+ * waits exist so that a stalled pipeline ends with DEINSUM_ERR_TIMEOUT instead of
+ * hanging the device; a very short limit makes a normal execute give up, which
+ * is how the failure path is tested.  Batched executes take the limit in force
+ * when their graph is captured.  Host only. */
+void deinsum_set_wait_limit_ns(uint64_t ns);
+
+/* Number of device (cudaMalloc) and pinned host (cudaMallocHost) allocations
+ * the library has made in this process (all entry points, all devices). */
+int64_t deinsum_alloc_count(void);
 
 /* Free the plan and its workspace.  NULL is ignored.  The device must not be
  * running an execute of this plan. */
@@ -240,7 +255,8 @@ deinsum_status deinsum_batched_autotune(deinsum_batch_t b, const void *const *co
 deinsum_status deinsum_batched_info(deinsum_batch_t b, int64_t *n_units, int *grid, int *unit_div,
                                     double *alg_bytes);
 
-/* After synchronising: DEINSUM_OK or DEINSUM_ERR_TIMEOUT (a bounded wait gave up). */
+/* After synchronising: DEINSUM_OK or DEINSUM_ERR_TIMEOUT (a bounded wait gave up
+ * in an execute since the previous call; the call clears the word). */
 deinsum_status deinsum_batched_status(deinsum_batch_t b);
 
 void deinsum_batched_destroy(deinsum_batch_t b);
@@ -293,9 +309,10 @@ deinsum_status deinsum_cpals_bind_workspace(deinsum_cpals_t h, void *workspace, 
 deinsum_status deinsum_cpals_set_dimension_tree(deinsum_cpals_t h, int enable);
 int deinsum_cpals_uses_dimension_tree(deinsum_cpals_t h);
 
-/* After synchronising the stream: DEINSUM_OK, DEINSUM_ERR_TIMEOUT if an MTTKRP
- * wait gave up, DEINSUM_ERR_INVALID if a Gram-Hadamard matrix was not positive
- * definite to FP64 precision (its pivot was floored). */
+/* After synchronising the stream: DEINSUM_OK, DEINSUM_ERR_TIMEOUT if a bounded
+ * wait of an MTTKRP or of the dimension-tree kernel gave up, DEINSUM_ERR_INVALID
+ * if a Gram-Hadamard matrix was not positive definite to FP64 precision (its
+ * pivot was floored).  Covers the handle's latest run. */
 deinsum_status deinsum_cpals_status(deinsum_cpals_t h);
 
 /* Free the handle, its plans and its workspace.  NULL is ignored. */
@@ -405,6 +422,13 @@ void deinsum_server_destroy(deinsum_server_t s);
 deinsum_status deinsum_mttkrp_noalloc(int order, const int64_t *dims, int mode, int rank,
                                       const float *X, const float *const *factors, float *out,
                                       deinsum_stream_t stream);
+
+/* Device-side status of the latest deinsum_mttkrp_noalloc call on the current
+ * device: DEINSUM_OK, or DEINSUM_ERR_TIMEOUT when a bounded wait inside its
+ * kernel gave up (the output is then incomplete).  Copies the status word out
+ * of the fixed array (synchronous, allocates nothing); call after synchronising
+ * the stream of that call.  DEINSUM_ERR_CUDA if the copy fails. */
+deinsum_status deinsum_mttkrp_noalloc_status(void);
 
 /*
  * Seeded synthetic inputs on the device.  These implement, bit for bit, the

@@ -169,17 +169,38 @@ def ttmc_rows(dims, keep: int, slabs, factors) -> np.ndarray:
 
 
 def frobenius(a) -> float:
+    """Frobenius norm sqrt(sum a^2) of an array of any shape (oracle_frobenius, long double sum)."""
     a = _f64(a).ravel()
     return float(_load().oracle_frobenius(_ptr(a), a.size))
 
 
 def rel_error(got, ref) -> float:
-    """Relative Frobenius error ||got - ref|| / ||ref|| (absolute when ||ref|| = 0)."""
+    """Relative Frobenius error ||got - ref|| / ||ref|| (absolute when ||ref|| = 0): the
+    parity gate of every floating-point result against this oracle (the paper fixes the
+    contraction, Sec. III-B, not a precision; this is the reading of "relative error")."""
     ref = _f64(ref)
-    diff = _f64(got) - ref
+    got = _f64(got)
+    if got.shape != ref.shape:
+        raise ValueError(f"shape mismatch {got.shape} vs {ref.shape}")
+    diff = got - ref
     nr = frobenius(ref)
     nd = frobenius(diff)
     return nd / nr if nr > 0 else nd
+
+
+def max_elem_error(got, ref) -> float:
+    """Largest element-wise deviation max |got - ref| relative to the largest oracle entry
+    max |ref| (absolute when ref is all zero; 0 for empty arrays): the element-wise backstop
+    beside rel_error, so that one wrong entry cannot hide in a large Frobenius norm."""
+    ref = _f64(ref)
+    got = _f64(got)
+    if ref.shape != got.shape:
+        raise ValueError(f"shape mismatch {got.shape} vs {ref.shape}")
+    if ref.size == 0:
+        return 0.0
+    worst = float(np.abs(got - ref).max())
+    scale = float(np.abs(ref).max())
+    return worst / scale if scale > 0 else worst
 
 
 # ---------------------------------------------------------------------------
@@ -229,14 +250,16 @@ def einsum_naive(spec: str, *operands) -> np.ndarray:
 # CP-ALS reference (Kolda & Bader 2009, Sec. 3.4, Fig. 3.3), float64 numpy.
 # ---------------------------------------------------------------------------
 
-def cpals_step(X, factors, lam, mode: int):
+def cpals_step(X, factors, lam, mode: int, perturb=None):
     """One ALS factor update of mode ``mode`` (Gauss-Seidel).
 
     V = Hadamard product of the Grams U_m^T U_m over m != mode; the update
     solves U_mode V = MTTKRP_mode(X) (V symmetric positive definite, by
     Cholesky), then normalises every column to unit 2-norm, the norms
     becoming lambda (a zero column keeps lambda = 0).
-    Returns the new factor list and lambda.
+    ``perturb(M, mode)``, if given, replaces the MTTKRP result before the solve
+    (the tests use it to measure how errors in M propagate through a sweep).
+    Returns the new factor list, lambda and the MTTKRP result used.
     """
     X = _f64(X)
     N = X.ndim
@@ -246,6 +269,8 @@ def cpals_step(X, factors, lam, mode: int):
         if m != mode:
             V = V * (factors[m].T @ factors[m])
     Mn = mttkrp(X, factors, mode)
+    if perturb is not None:
+        Mn = perturb(Mn, mode)
     L = np.linalg.cholesky(V)
     Y = np.linalg.solve(L, Mn.T)
     Un = np.linalg.solve(L.T, Y).T
@@ -276,14 +301,15 @@ def cp_fit(X, factors, lam, M_last=None, last_mode=None) -> float:
     return 1.0 - np.sqrt(res2) / np.sqrt(normX2)
 
 
-def cpals(X, init_factors, sweeps: int):
-    """``sweeps`` full ALS sweeps (modes 0..N-1 each); returns factors, lambda, fit history."""
+def cpals(X, init_factors, sweeps: int, perturb=None):
+    """``sweeps`` full ALS sweeps (modes 0..N-1 each); returns factors, lambda, fit history.
+    ``perturb`` as in cpals_step (applied to every MTTKRP result)."""
     factors = [_f64(f).copy() for f in init_factors]
     N = len(factors)
     lam = np.ones(factors[0].shape[1])
     fits = []
     for _ in range(sweeps):
         for n in range(N):
-            factors, lam, Mn = cpals_step(X, factors, lam, n)
+            factors, lam, Mn = cpals_step(X, factors, lam, n, perturb)
         fits.append(cp_fit(X, factors, lam, Mn, N - 1))
     return factors, lam, fits

@@ -8,8 +8,9 @@ compute entry point without the built library raises.
 
 Entry points mirror the C names: ``Plan`` (deinsum_plan / deinsum_execute /
 deinsum_plan_info / deinsum_workspace_size / deinsum_last_device_status /
-deinsum_destroy), ``gen_uniform`` / ``gen_cp`` (the seeded device generators)
-and ``kernel_launch_count``; ``mttkrp`` / ``ttmc`` build the einsum string of
+deinsum_destroy), ``gen_uniform`` / ``gen_cp`` (the seeded device generators),
+``kernel_launch_count`` / ``alloc_count`` / ``set_wait_limit_ns`` and
+``mttkrp_noalloc`` / ``mttkrp_noalloc_status``; ``mttkrp`` / ``ttmc`` build the einsum string of
 the paper's Table IV pattern for a given tensor and factor list.
 """
 from __future__ import annotations
@@ -20,7 +21,8 @@ import threading
 
 __all__ = ["DeinsumError", "Plan", "mttkrp", "ttmc", "mttkrp_einsum", "ttmc_einsum", "mttkrp_mm",
            "mttkrp_mm_einsum",
-           "gen_uniform", "gen_cp", "kernel_launch_count", "library_path", "load",
+           "gen_uniform", "gen_cp", "kernel_launch_count", "alloc_count", "set_wait_limit_ns",
+           "mttkrp_noalloc", "mttkrp_noalloc_status", "library_path", "load",
            "Grid", "redist_dim_partitions", "redist_match", "redist_plan"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -151,6 +153,12 @@ def load():
         lib.deinsum_plan_bind_workspace.restype = i32
         lib.deinsum_mttkrp_noalloc.argtypes = [i32, ctypes.POINTER(i64), i32, i32, vp, ctypes.POINTER(vp), vp, vp]
         lib.deinsum_mttkrp_noalloc.restype = i32
+        lib.deinsum_mttkrp_noalloc_status.argtypes = []
+        lib.deinsum_mttkrp_noalloc_status.restype = i32
+        lib.deinsum_set_wait_limit_ns.argtypes = [ctypes.c_uint64]
+        lib.deinsum_set_wait_limit_ns.restype = None
+        lib.deinsum_alloc_count.argtypes = []
+        lib.deinsum_alloc_count.restype = i64
         lib.deinsum_gen_uniform_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, vp, vp]
         lib.deinsum_gen_uniform_f32.restype = i32
         lib.deinsum_gen_uniform_f64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, vp, vp]
@@ -572,9 +580,26 @@ def gen_cp(seed: int, dims, cp_factors, sigma: float, device="cuda", stream=None
     return t
 
 
+def mttkrp_noalloc_status() -> int:
+    """Status of the latest ``deinsum_mttkrp_noalloc`` call on the current device
+    (``deinsum_mttkrp_noalloc_status``; 0 ok, 8 a bounded wait gave up); synchronise first."""
+    return int(load().deinsum_mttkrp_noalloc_status())
+
+
 def kernel_launch_count() -> int:
     """Kernels the library has launched in this process (all entry points)."""
     return int(load().deinsum_kernel_launch_count())
+
+
+def alloc_count() -> int:
+    """Device and pinned host allocations the library has made in this process (``deinsum_alloc_count``)."""
+    return int(load().deinsum_alloc_count())
+
+
+def set_wait_limit_ns(ns: int) -> None:
+    """Limit of the kernels' bounded waits for later launches (``deinsum_set_wait_limit_ns``;
+    0 restores the default 2 s)."""
+    load().deinsum_set_wait_limit_ns(int(ns))
 
 
 # ---------------------------------------------------------------------------

@@ -290,7 +290,7 @@ deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
         b->ws = nullptr;
         b->ws_bytes = 0;
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, b->o_end);
+        cudaError_t e = counted_malloc(&p, b->o_end);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? DEINSUM_ERR_OOM : DEINSUM_ERR_CUDA;
@@ -303,7 +303,7 @@ deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
     if (stage > b->staging_bytes) {
         if (b->staging) cudaFreeHost(b->staging);
         b->staging = nullptr;
-        if (cudaMallocHost(reinterpret_cast<void **>(&b->staging), stage) != cudaSuccess) return DEINSUM_ERR_OOM;
+        if (counted_malloc_host(reinterpret_cast<void **>(&b->staging), stage) != cudaSuccess) return DEINSUM_ERR_OOM;
         b->staging_bytes = stage;
     }
     cudaMemsetAsync(b->ws + b->o_status, 0, 256, s);
@@ -585,6 +585,7 @@ deinsum_status deinsum_batched_status(deinsum_batch_t b) {
     int v = 0;
     if (cudaMemcpy(&v, b->ws + b->o_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return DEINSUM_ERR_CUDA;
+    if (v != 0 && cudaMemset(b->ws + b->o_status, 0, sizeof(int)) != cudaSuccess) return DEINSUM_ERR_CUDA;
     return v == 0 ? DEINSUM_OK : DEINSUM_ERR_TIMEOUT;
 }
 

@@ -600,7 +600,7 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
     const int R = h->R;
     if (!h->ws) {
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, cpals_own_bytes(h));
+        cudaError_t e = counted_malloc(&p, cpals_own_bytes(h));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? DEINSUM_ERR_OOM : DEINSUM_ERR_CUDA;
@@ -766,10 +766,14 @@ deinsum_status deinsum_cpals_status(deinsum_cpals_t h) {
     if (!h->status) return DEINSUM_OK;
     int v = 0;
     if (cudaMemcpy(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DEINSUM_ERR_CUDA;
+    deinsum_status plans_st = DEINSUM_OK;
     for (int n = 0; n < h->order; ++n) {
-        deinsum_status st = deinsum_last_device_status(h->plans[n]);
-        if (st != DEINSUM_OK) return st;
+        const deinsum_status st = deinsum_last_device_status(h->plans[n]);
+        if (st != DEINSUM_OK && plans_st == DEINSUM_OK) plans_st = st;
     }
+    if (plans_st != DEINSUM_OK) return plans_st;
+    // bit 0: a bounded wait of the dimension-tree kernel gave up; bit 1: a floored pivot
+    if (v & 1) return DEINSUM_ERR_TIMEOUT;
     return v == 0 ? DEINSUM_OK : DEINSUM_ERR_INVALID;
 }
 

@@ -34,6 +34,7 @@
 #include <cstddef>
 
 #include <cuda.h>
+#include <cuda_runtime.h>
 
 #include "../../include/deinsum.h"
 
@@ -102,6 +103,7 @@ struct MttkrpArgs {
     float *partial;                    // n_units x 128 x R_pad (F32 paths)
     double *partial64;                 // n_units x 128 x R_pad (F64 path)
     int *status;                       // device status word
+    uint64_t wait_ns;                  // limit of a pipeline wait (set by the launcher)
 };
 
 // Many MTTKRP instances in persistent launches of the tensor-core kernel (one per kind):
@@ -115,6 +117,7 @@ struct BatchArgs {
     const int64_t *cta_begin;   // units of CTA c: cta_begin[c] .. cta_begin[c+1] - 1
     float *partial;
     int *status;
+    uint64_t wait_ns;           // limit of a pipeline wait (set by the launcher)
 };
 // kind 0: every instance of the unit list loads X through its tensor map (use_tma) or per
 // thread; kind 1 / 2: through its row-class maps (row_classes set), all of them case 0 /
@@ -144,6 +147,7 @@ struct TtmcArgs {
     int sg;               // slabs per tile (1, 2 or 4; n_kt = 1 when sg > 1)
     int tc2;              // stage 2 on the tensor cores (n_kt <= 2), else on CUDA cores (sg = 1)
     int *status;
+    uint64_t wait_ns;     // limit of a pipeline wait (set by the launcher)
 };
 // Slabs per tile of the fused kernel for I_{N-2} = K.
 inline int ttmc_slab_group(int64_t K) { return K <= 32 ? 4 : (K <= 64 ? 2 : 1); }
@@ -201,6 +205,14 @@ int launch_ttm_plain_f64(const double *X, const double *U, double *Y, int64_t A,
                          int64_t B, int64_t Rm, void *stream);
 
 void count_launch(int n = 1);
+
+// Limit (ns) of every bounded pipeline wait of the tensor-core kernels launched from now on:
+// 2 s unless deinsum_set_wait_limit_ns changed it.  Launchers copy it into the kernel arguments.
+uint64_t wait_limit_ns();
+
+// cudaMalloc / cudaMallocHost that count successful allocations (deinsum_alloc_count).
+cudaError_t counted_malloc(void **p, size_t bytes);
+cudaError_t counted_malloc_host(void **p, size_t bytes);
 
 // Units per column of 128 output rows (each column's fiber groups cut into that many
 // contiguous units) such that the busiest of `target` persistent CTAs, which take units

@@ -509,6 +509,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     uint64_t *bars = reinterpret_cast<uint64_t *>(a_base + AS * C::ASTAGE_BYTES + C::WBUF_BYTES);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    const uint64_t wlim = a.wait_ns;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
@@ -573,7 +574,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             const int rs = int(chunk % RS);
             if (RC || a.use_tma) {
                 const uint32_t rj = uint32_t(chunk / RS);
-                if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, a.status))) break;
+                if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, a.status, wlim))) break;
                 const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_STAGE);
                 if (RC) {
                     if (MN) conv_read_rowcls_mn(g, a.X, it.col, it.o, it.kb, raw, pt, v);
@@ -595,7 +596,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             }
             const int as = int(chunk % AS);
             const uint32_t aj = uint32_t(chunk / AS);
-            if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, a.status))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, a.status, wlim))) break;
             // with a single inner chunk (n_kb = 1) every chunk uses the same factor tile:
             // each operand stage copies it once and keeps it
             if (issuer && (g.n_kb != 1 || aj == 0)) {
@@ -614,7 +615,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         }
         if (issuer) {  // every bulk copy into this CTA's smem has landed before exit
             for (int s = 0; s < AS; ++s)
-                if ((bused >> s) & 1u) mbar_wait(bfull(s), (bpar >> s) & 1u, abort_flag, a.status);
+                if ((bused >> s) & 1u) mbar_drain(bfull(s), (bpar >> s) & 1u, a.status);
         }
     } else if (warp == C::TMA_WARP) {
         // ------------------------------------------------------------------ TMA
@@ -622,23 +623,23 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
         if (lane == 0) {
             Iter it;
             it.init(a);
-            int last_rs = -1, last_ws = -1;
-            uint32_t last_par = 0, last_wpar = 0;
+            // per raw stage / weight slot: a copy was issued into it, and that copy's parity
+            uint32_t r_used = 0, r_par = 0, w_used = 0, w_par = 0;
             int64_t fgi = 0;
             for (int64_t chunk = 0; !it.done; ++chunk) {
                 if (it.kb == it.kb_lo) {
                     const int ws = int(fgi % C::WSLOTS);
                     const uint32_t wj = uint32_t(fgi / C::WSLOTS);
-                    if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, a.status)) break;
+                    if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, a.status, wlim)) break;
                     load_fg_weights(a, it.tile, it.o, wslot_addr(ws), wfull(ws));
-                    last_ws = ws;
-                    last_wpar = wj & 1u;
+                    w_used |= 1u << ws;
+                    w_par = (w_par & ~(1u << ws)) | ((wj & 1u) << ws);
                     ++fgi;
                 }
                 if (RC || a.use_tma) {
                     const int rs = int(chunk % RS);
                     const uint32_t rj = uint32_t(chunk / RS);
-                    if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, a.status)) break;
+                    if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, a.status, wlim)) break;
                     const int kc = it.kb * BK;
                     if (RC) {
                         rowcls_load(a, it.col, it.tile, it.o, it.kb, raw_addr(rs), raw_full(rs));
@@ -656,14 +657,18 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                         mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                         tma_load_3d(raw_addr(rs), &a.xmap, int(it.col * BM), kc, int(it.o), raw_full(rs));
                     }
-                    last_rs = rs;
-                    last_par = rj & 1u;
+                    r_used |= 1u << rs;
+                    r_par = (r_par & ~(1u << rs)) | ((rj & 1u) << rs);
                 }
                 it.next(a);
             }
-            // the last loads have landed before exit (the earlier ones were consumed)
-            if (last_rs >= 0) mbar_wait(raw_full(last_rs), last_par, abort_flag, a.status);
-            if (last_ws >= 0) mbar_wait(wfull(last_ws), last_wpar, abort_flag, a.status);
+            // every copy issued into this CTA's shared memory has landed before exit, also
+            // when a role gave up and left some of them unconsumed (a completed phase
+            // returns at once)
+            for (int s2 = 0; s2 < RS; ++s2)
+                if ((r_used >> s2) & 1u) mbar_drain(raw_full(s2), (r_par >> s2) & 1u, a.status);
+            for (int s2 = 0; s2 < C::WSLOTS; ++s2)
+                if ((w_used >> s2) & 1u) mbar_drain(wfull(s2), (w_par >> s2) & 1u, a.status);
         }
         __syncwarp();
     } else if (warp == C::MMA_WARP) {
@@ -678,14 +683,14 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 const int nkb = itm.kb_hi - itm.kb_lo;
                 const int b = int(fgi & 1);
                 const uint32_t jb = uint32_t(fgi >> 1);
-                if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, a.status)) { ok = false; break; }
+                if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, a.status, wlim)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dcol = tmem + uint32_t(b * C::N);
                 for (int kb = 0; kb < nkb; ++kb) {
                     const int s = int(chunk % AS);
                     const uint32_t j = uint32_t(chunk / AS);
-                    if (!mbar_wait(a_full(s), j & 1u, abort_flag, a.status) ||
-                        ((g.n_kb != 1 || j == 0) && !mbar_wait(bfull(s), j & 1u, abort_flag, a.status))) {
+                    if (!mbar_wait(a_full(s), j & 1u, abort_flag, a.status, wlim) ||
+                        ((g.n_kb != 1 || j == 0) && !mbar_wait(bfull(s), j & 1u, abort_flag, a.status, wlim))) {
                         ok = false;
                         break;
                     }
@@ -711,7 +716,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             }
             // all issued MMAs have completed before TMEM is released
             mma_commit(drain);
-            mbar_wait(drain, 0, abort_flag, a.status);
+            mbar_drain(drain, 0, a.status);
         }
         __syncwarp();
     } else {
@@ -758,7 +763,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 // weights of this fiber group, from its ring slot: lane c holds column c (and c + 32)
                 const int ws = int(fgi % C::WSLOTS);
                 const uint32_t wj = uint32_t(fgi / C::WSLOTS);
-                if (!__all_sync(0xffffffffu, mbar_wait(wfull(ws), wj & 1u, abort_flag, a.status))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(wfull(ws), wj & 1u, abort_flag, a.status, wlim))) {
                     ok = false;
                     break;
                 }
@@ -774,7 +779,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 if (RP <= 32 || lane + 32 >= g.R) w1 = 0.f;
                 const int b = int(fgi & 1);
                 const uint32_t jb = uint32_t(fgi >> 1);
-                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, a.status))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, a.status, wlim))) {
                     ok = false;
                     break;
                 }
@@ -871,7 +876,9 @@ int launch_tc_rp_op(const MttkrpArgs &a, int n_sm, void *stream) {
     if (e != cudaSuccess) return int(e);
     int64_t grid = a.n_units < n_sm ? a.n_units : n_sm;
     if (grid < 1) grid = 1;
-    mttkrp_tc_kernel<RP, OP, MN, PW, RC><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
+    MttkrpArgs ka = a;
+    ka.wait_ns = wait_limit_ns();
+    mttkrp_tc_kernel<RP, OP, MN, PW, RC><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(ka);
     count_launch();
     return int(cudaGetLastError());
 }
@@ -970,6 +977,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
     int *status = bargs.status;
+    const uint64_t wlim = bargs.wait_ns;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
@@ -1045,7 +1053,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             if (RCB || a.use_tma) {
                 const uint32_t rj = uint32_t(tchunk / RS);
                 ++tchunk;
-                if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
+                if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status, wlim))) break;
                 const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_STAGE);
                 if (RCB) {
                     if (mn) conv_read_rowcls_mn(a.g, a.X, it.col, it.o, it.kb, raw, pt, v);
@@ -1064,7 +1072,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             }
             const int as = int(chunk % AS);
             const uint32_t aj = uint32_t(chunk / AS);
-            if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status, wlim))) break;
             if (issuer) {
                 const uint32_t bbytes = uint32_t(2 * a.g.R_pad * BK * 2);
                 mbar_arrive_expect_tx(bfull(as), bbytes);
@@ -1081,7 +1089,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         }
         if (issuer) {
             for (int s = 0; s < AS; ++s)
-                if ((bused >> s) & 1u) mbar_wait(bfull(s), (bpar >> s) & 1u, abort_flag, status);
+                if ((bused >> s) & 1u) mbar_drain(bfull(s), (bpar >> s) & 1u, status);
         }
     } else if (warp == C::TMA_WARP) {
         // ------------------------------------------------------------------ TMA
@@ -1089,8 +1097,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         if (lane == 0) {
             BIter it;
             it.init(&bargs);
-            int last_rs = -1, last_ws = -1;
-            uint32_t last_par = 0, last_wpar = 0;
+            uint32_t r_used = 0, r_par = 0, w_used = 0, w_par = 0;   // as in the single-instance kernel
             const MttkrpArgs *fenced = nullptr;
             int64_t tchunk = 0;  // chunks of TMA-loaded instances only (the raw ring's sequence)
             int64_t fgi = 0;
@@ -1099,10 +1106,10 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 if (it.kb == 0) {
                     const int ws = int(fgi % C::WSLOTS);
                     const uint32_t wj = uint32_t(fgi / C::WSLOTS);
-                    if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, status)) break;
+                    if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, status, wlim)) break;
                     load_fg_weights(a, it.tile, it.o, wslot_addr(ws), wfull(ws));
-                    last_ws = ws;
-                    last_wpar = wj & 1u;
+                    w_used |= 1u << ws;
+                    w_par = (w_par & ~(1u << ws)) | ((wj & 1u) << ws);
                     ++fgi;
                 }
                 if ((RCB || a.use_tma) && fenced != it.a) {
@@ -1116,7 +1123,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                     const int rs = int(tchunk % RS);
                     const uint32_t rj = uint32_t(tchunk / RS);
                     ++tchunk;
-                    if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status)) break;
+                    if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status, wlim)) break;
                     const int kc = it.kb * BK;
                     if (RCB) {
                         rowcls_load(a, it.col, it.tile, it.o, it.kb, raw_addr(rs), raw_full(rs));
@@ -1134,13 +1141,15 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                         mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                         tma_load_3d(raw_addr(rs), &a.xmap, int(it.col * BM), kc, int(it.o), raw_full(rs));
                     }
-                    last_rs = rs;
-                    last_par = rj & 1u;
+                    r_used |= 1u << rs;
+                    r_par = (r_par & ~(1u << rs)) | ((rj & 1u) << rs);
                 }
                 it.next();
             }
-            if (last_rs >= 0) mbar_wait(raw_full(last_rs), last_par, abort_flag, status);
-            if (last_ws >= 0) mbar_wait(wfull(last_ws), last_wpar, abort_flag, status);
+            for (int s2 = 0; s2 < RS; ++s2)
+                if ((r_used >> s2) & 1u) mbar_drain(raw_full(s2), (r_par >> s2) & 1u, status);
+            for (int s2 = 0; s2 < C::WSLOTS; ++s2)
+                if ((w_used >> s2) & 1u) mbar_drain(wfull(s2), (w_par >> s2) & 1u, status);
         }
         __syncwarp();
     } else if (warp == C::MMA_WARP) {
@@ -1157,7 +1166,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 const int b = int(fgi & 1);
                 if (it.kb == 0) {
                     const uint32_t jb = uint32_t(fgi >> 1);
-                    if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
+                    if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status, wlim)) { ok = false; break; }
                     tc_fence_after();
                     dcol = tmem + uint32_t(b * C::N);
                     mn = RCB ? MNB : a.g.kcase == 1;   // the last mode: MN-major A (see the converters)
@@ -1165,8 +1174,8 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 }
                 const int s = int(chunk % AS);
                 const uint32_t j = uint32_t(chunk / AS);
-                if (!mbar_wait(a_full(s), j & 1u, abort_flag, status) ||
-                    !mbar_wait(bfull(s), j & 1u, abort_flag, status)) { ok = false; break; }
+                if (!mbar_wait(a_full(s), j & 1u, abort_flag, status, wlim) ||
+                    !mbar_wait(bfull(s), j & 1u, abort_flag, status, wlim)) { ok = false; break; }
                 tc_fence_after();
                 const uint64_t dh = mn ? desc_mnmajor_sw128(a_hi(s), kMnAtomStride, kMnKGroupStride)
                                        : desc_kmajor_sw128(a_hi(s));
@@ -1189,7 +1198,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 it.next();
             }
             mma_commit(drain);
-            mbar_wait(drain, 0, abort_flag, status);
+            mbar_drain(drain, 0, status);
         }
         __syncwarp();
     } else {
@@ -1239,7 +1248,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 }
                 const int ws = int(fgi % C::WSLOTS);
                 const uint32_t wj = uint32_t(fgi / C::WSLOTS);
-                if (!__all_sync(0xffffffffu, mbar_wait(wfull(ws), wj & 1u, abort_flag, status))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(wfull(ws), wj & 1u, abort_flag, status, wlim))) {
                     ok = false;
                     break;
                 }
@@ -1255,7 +1264,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 if (rp <= 32 || lane + 32 >= g.R) w1 = 0.f;
                 const int b = int(fgi & 1);
                 const uint32_t jb = uint32_t(fgi >> 1);
-                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status, wlim))) {
                     ok = false;
                     break;
                 }
@@ -1314,13 +1323,12 @@ int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, int kind, void *strea
                           : (kind == 1 ? mttkrp_tc_batched_kernel<true, false> : mttkrp_tc_batched_kernel<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
     if (e != cudaSuccess) return int(e);
-    kern<<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(b);
+    BatchArgs kb = b;
+    kb.wait_ns = wait_limit_ns();
+    kern<<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(kb);
     count_launch();
     return int(cudaGetLastError());
 }
-
-namespace {
-}  // namespace
 
 size_t mttkrp_tc_smem_bytes(int R_pad) {
     switch (R_pad) {

@@ -27,7 +27,9 @@ constexpr int64_t kMaxCols = 256;                           // columns of 128 ou
 constexpr size_t kOffStatus = 0;
 constexpr size_t kOffUnits = 256;                           // kMaxUnits x 3 int64
 constexpr size_t kOffCols = kOffUnits + size_t(kMaxUnits) * 3 * 8;  // kMaxCols + 1 int64
-constexpr size_t kOffBsplit = 16384;                        // split factor tiles, 1024-aligned
+constexpr size_t kOffBsplit = 16384;                        // split factor tiles: offset a multiple of
+                                                            // 1024, address only 256-aligned (the array's
+                                                            // alignment); bulk copies need 16 bytes
 constexpr size_t kBsplitBytes = size_t(1) << 20;            // 64 tiles at rank 64
 constexpr size_t kOffPartial = kOffBsplit + kBsplitBytes;
 constexpr size_t kPartialBytes = size_t(kMaxUnits) * DEINSUM_BM * 64 * 4;  // 8 MiB
@@ -142,4 +144,16 @@ extern "C" deinsum_status deinsum_mttkrp_noalloc(int order, const int64_t *dims,
     if (!err) err = launch_mttkrp_tc(a, n_sm, stream);
     if (!err) err = launch_mttkrp_reduce_f32(a, cols, out, stream);
     return err ? DEINSUM_ERR_CUDA : DEINSUM_OK;
+}
+
+// The status word sits at the start of the array: read it on the current device with a
+// symbol copy (no allocation).  Each call of deinsum_mttkrp_noalloc clears it first, so it
+// describes the latest call on this device.
+extern "C" deinsum_status deinsum_mttkrp_noalloc_status(void) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_scratch, sizeof(int), kOffStatus, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return DEINSUM_ERR_CUDA;
+    }
+    return v == 0 ? DEINSUM_OK : DEINSUM_ERR_TIMEOUT;
 }

@@ -22,6 +22,24 @@ using namespace deinsum;
 namespace deinsum {
 static std::atomic<int64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static std::atomic<int64_t> g_allocs{0};
+cudaError_t counted_malloc(void **p, size_t bytes) {
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+cudaError_t counted_malloc_host(void **p, size_t bytes) {
+    const cudaError_t e = cudaMallocHost(p, bytes);
+    if (e == cudaSuccess) g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+static std::atomic<uint64_t> g_wait_limit_ns{0};
+uint64_t wait_limit_ns() {
+    const uint64_t v = g_wait_limit_ns.load(std::memory_order_relaxed);
+    return v ? v : 2000000000ull;
+}
 }  // namespace deinsum
 
 struct deinsum_plan_s {
@@ -405,7 +423,7 @@ deinsum_status ensure_device_state(deinsum_plan_s *pl, cudaStream_t stream) {
     deinsum_status st = plan_layout(pl, L);
     if (st != DEINSUM_OK) return st;
     void *ws = nullptr;
-    cudaError_t e = cudaMalloc(&ws, L.total);
+    cudaError_t e = counted_malloc(&ws, L.total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_status(e);
@@ -1084,8 +1102,13 @@ deinsum_status deinsum_last_device_status(deinsum_plan_t pl) {
     int v = 0;
     if (cudaMemcpy(&v, pl->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return DEINSUM_ERR_CUDA;
+    if (v != 0 && cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) return DEINSUM_ERR_CUDA;
     return v == 0 ? DEINSUM_OK : DEINSUM_ERR_TIMEOUT;
 }
+
+void deinsum_set_wait_limit_ns(uint64_t ns) { g_wait_limit_ns.store(ns, std::memory_order_relaxed); }
+
+int64_t deinsum_alloc_count(void) { return g_allocs.load(std::memory_order_relaxed); }
 
 deinsum_status deinsum_set_kernel_timing(deinsum_plan_t pl, int enable) {
     if (!pl) return DEINSUM_ERR_INVALID;

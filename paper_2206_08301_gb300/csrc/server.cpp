@@ -250,7 +250,7 @@ deinsum_status deinsum_server_create(size_t hbm_budget_bytes, int slots, deinsum
     if (!s) return DEINSUM_ERR_OOM;
     s->prec = prec;
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, hbm_budget_bytes);
+    cudaError_t e = deinsum::counted_malloc(&p, hbm_budget_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete s;
@@ -264,7 +264,7 @@ deinsum_status deinsum_server_create(size_t hbm_budget_bytes, int slots, deinsum
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreate(&sl.g0) != cudaSuccess || cudaEventCreate(&sl.g1) != cudaSuccess ||
-            cudaMallocHost(reinterpret_cast<void **>(&sl.host), (kMaxSweeps + 64) * sizeof(double)) != cudaSuccess) {
+            deinsum::counted_malloc_host(reinterpret_cast<void **>(&sl.host), (kMaxSweeps + 64) * sizeof(double)) != cudaSuccess) {
             deinsum_server_destroy(s);
             return DEINSUM_ERR_CUDA;
         }

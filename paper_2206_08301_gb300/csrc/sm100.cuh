@@ -45,11 +45,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Bit of the device status word that a bounded wait sets when it gives up.
+constexpr int kStatusTimeout = 1;
+// Default limit of a pipeline wait, and the limit of a drain (below), in nanoseconds.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr uint64_t kDrainLimitNs = 2000000000ull;
+
 // Wait for the phase of parity `parity` to complete, for at most `limit_ns`.
 // On time-out (or when another role already gave up, *abort != 0) it records
 // a failure in the device status word, raises *abort and returns false.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
-                                          uint64_t limit_ns = 2000000000ull) {
+                                          uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     while (true) {
@@ -58,8 +64,26 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
             if (mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
         if (globaltimer_ns() - t0 > limit_ns) {
-            atomicExch(status, 1);
+            atomicOr(status, kStatusTimeout);
             *abort = 1;
+            return false;
+        }
+    }
+}
+
+// Wait for the phase of parity `parity` to complete whether or not another role gave up:
+// used before a role exits, for the completion of bulk copies or MMAs that this thread
+// issued itself (they finish on their own, so this returns promptly even after an abort;
+// the limit only guards against a broken pipeline).  On time-out it sets the status word.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (true) {
+        #pragma unroll 1
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kDrainLimitNs) {
+            atomicOr(status, kStatusTimeout);
             return false;
         }
     }

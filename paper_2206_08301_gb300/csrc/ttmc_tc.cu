@@ -138,6 +138,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + C::NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
     int *status = a.status;
+    const uint64_t wlim = a.wait_ns;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
@@ -219,7 +220,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             float4 v[8];
             const int rs = int(chunk % RS);
             const uint32_t rj = uint32_t(chunk / RS);
-            if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status, wlim))) break;
             const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES);
             if (!a.g.narrow) conv_read_smem_wide(raw, pt, v);
             else conv_read_smem_t<false>(a.g, BM, raw, pt, v);
@@ -231,7 +232,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             if (lane == 0) mbar_arrive(raw_empty(rs));
             const int as = int(chunk % AS);
             const uint32_t aj = uint32_t(chunk / AS);
-            if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status, wlim))) break;
             // a single l chunk (n_kb = 1): every chunk uses the same factor tile, which each
             // operand stage copies once and keeps
             if (issuer && (a.n_kb != 1 || aj == 0)) {
@@ -248,7 +249,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         }
         if (issuer) {  // every bulk copy into this CTA's smem has landed before exit
             for (int s = 0; s < AS; ++s)
-                if ((bused >> s) & 1u) mbar_wait(bfull(s), (bpar >> s) & 1u, abort_flag, status);
+                if ((bused >> s) & 1u) mbar_drain(bfull(s), (bpar >> s) & 1u, status);
         }
     } else if (warp == C::TMA_WARP) {
         // ------------------------------------------------------------------ TMA
@@ -256,20 +257,21 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         if (lane == 0) {
             TIter it;
             it.init(ngroups);
-            int last_rs = -1;
-            uint32_t last_par = 0;
+            uint32_t r_used = 0, r_par = 0;   // per raw stage: a copy was issued, its parity
             for (int64_t chunk = 0; !it.done; ++chunk) {
                 const int rs = int(chunk % RS);
                 const uint32_t rj = uint32_t(chunk / RS);
-                if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status)) break;
+                if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status, wlim)) break;
                 mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                 tma_load_3d(raw_addr(rs), &a.xmap, it.kb * BK, it.kt * BM, int(it.s * SG), raw_full(rs));
-                last_rs = rs;
-                last_par = rj & 1u;
+                r_used |= 1u << rs;
+                r_par = (r_par & ~(1u << rs)) | ((rj & 1u) << rs);
                 it.next(a.n_kb, a.n_kt);
             }
-            // the last copy has landed before exit (the earlier ones were consumed)
-            if (last_rs >= 0) mbar_wait(raw_full(last_rs), last_par, abort_flag, status);
+            // every copy issued into this CTA's shared memory has landed before exit, also
+            // when a role gave up and left some of them unconsumed
+            for (int s2 = 0; s2 < RS; ++s2)
+                if ((r_used >> s2) & 1u) mbar_drain(raw_full(s2), (r_par >> s2) & 1u, status);
         }
         __syncwarp();
     } else if (warp == C::MMA_WARP) {
@@ -284,14 +286,14 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             for (int64_t fgi = 0; ok && fgi < nfg; ++fgi) {
                 const int b = int(fgi % C::NACC);
                 const uint32_t jb = uint32_t(fgi / C::NACC);
-                if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status)) { ok = false; break; }
+                if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status, wlim)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dcol = tmem + uint32_t(b * C::N);
                 for (int kb = 0; kb < a.n_kb; ++kb) {
                     const int s = int(chunk % AS);
                     const uint32_t j = uint32_t(chunk / AS);
-                    if (!mbar_wait(a_full(s), j & 1u, abort_flag, status) ||
-                        ((a.n_kb != 1 || j == 0) && !mbar_wait(bfull(s), j & 1u, abort_flag, status))) {
+                    if (!mbar_wait(a_full(s), j & 1u, abort_flag, status, wlim) ||
+                        ((a.n_kb != 1 || j == 0) && !mbar_wait(bfull(s), j & 1u, abort_flag, status, wlim))) {
                         ok = false;
                         break;
                     }
@@ -313,7 +315,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             }
             // all issued MMAs have completed before TMEM is released
             mma_commit(drain);
-            mbar_wait(drain, 0, abort_flag, status);
+            mbar_drain(drain, 0, status);
         }
         __syncwarp();
     } else if constexpr (STORE) {
@@ -329,7 +331,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         for (int64_t fgi = 0; fgi < nfg; ++fgi) {
             const int b = int(fgi % C::NACC);
             const uint32_t jb = uint32_t(fgi / C::NACC);
-            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status, wlim))) break;
             tc_fence_after();
             const int64_t k = int64_t(kt) * BM + row;
             const bool valid = k < a.g.I;
@@ -404,14 +406,14 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             constexpr int KP = BM / SG;            // tile rows of one slab
             const int tk = int(t % a.n_kt);
             const int64_t tg = t / a.n_kt;         // slab group within the CTA
-            if (!mbar_wait(b2full(bi), uint32_t((t / nb2) & 1), abort_flag, status)) return false;
-            if (t == 0 && !mbar_wait(u2full, 0u, abort_flag, status)) return false;
+            if (!mbar_wait(b2full(bi), uint32_t((t / nb2) & 1), abort_flag, status, wlim)) return false;
+            if (t == 0 && !mbar_wait(u2full, 0u, abort_flag, status, wlim)) return false;
             tc_fence_after();
             for (int g = 0; g < SG; ++g) {
                 const int64_t j = tg * SG + g;     // slab index within the CTA
                 const int slot = int(j % C::D2_SLOTS);
                 // the slab that last used the slot has been written out
-                if (tk == 0 && !mbar_wait(d2free(slot), uint32_t((j / C::D2_SLOTS) & 1) ^ 1u, abort_flag, status))
+                if (tk == 0 && !mbar_wait(d2free(slot), uint32_t((j / C::D2_SLOTS) & 1) ^ 1u, abort_flag, status, wlim))
                     return false;
                 tc_fence_after();
                 const uint32_t dcol = tmem + uint32_t(C::NACC * C::N + slot * 2 * RP);
@@ -437,7 +439,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 const int64_t j = (pg - it.s) * SG + g;   // slab index within the CTA
                 const int slot = int(j % C::D2_SLOTS);
                 if (!__all_sync(0xffffffffu,
-                                mbar_wait(d2full(slot), uint32_t((j / C::D2_SLOTS) & 1), abort_flag, status)))
+                                mbar_wait(d2full(slot), uint32_t((j / C::D2_SLOTS) & 1), abort_flag, status, wlim)))
                     return false;
                 tc_fence_after();
                 const uint32_t d2 = tmem + uint32_t(C::NACC * C::N + slot * 2 * RP);   // lanes 0-31
@@ -478,10 +480,10 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             const int b = int(fgi % C::NACC);
             const uint32_t jb = uint32_t(fgi / C::NACC);
             const int bi = int(fgi % nb2);
-            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status, wlim))) break;
             // the stage-2 MMAs of the tile that last used this B2 buffer have read it
             if (fgi >= nb2 && !__all_sync(0xffffffffu, mbar_wait(b2free(bi), uint32_t(((fgi / nb2) & 1) ^ 1),
-                                                                 abort_flag, status)))
+                                                                 abort_flag, status, wlim)))
                 break;
             tc_fence_after();
             const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
@@ -530,9 +532,9 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         // the U_{N-2} copy has landed and every stage-2 MMA has completed before exit
         // (and before TMEM is released), also when the loop ended early
         if (issuer && nfg > 0) {
-            mbar_wait(u2full, 0u, abort_flag, status);
+            mbar_drain(u2full, 0u, status);
             mma_commit(drain2);
-            mbar_wait(drain2, 0u, abort_flag, status);
+            mbar_drain(drain2, 0u, status);
         }
     } else {
         // ------------------------------------ epilogue (stage 2), one slab per tile
@@ -560,9 +562,11 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         // f + 1 once every warp is done with group f - 1).
         const bool uissuer = (et == 0);
         const bool uresident = a.n_kt <= C::USLOTS;
+        uint32_t u_loads[C::USLOTS] = {0u, 0u};   // copies issued into each slot (the issuer's count)
         auto load_u = [&](int us, int ktile) {
             mbar_arrive_expect_tx(ufull(us), C::USLOT_BYTES);
             bulk_g2s(uslot_addr(us), a.U2pad + size_t(ktile) * BM * RP, C::USLOT_BYTES, ufull(us));
+            ++u_loads[us];
         };
         if (uissuer && nfg > 0) {
             if (uresident) {
@@ -575,11 +579,11 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         for (int64_t fgi = 0; fgi < nfg; ++fgi) {
             const int b = int(fgi % C::NACC);
             const uint32_t jb = uint32_t(fgi / C::NACC);
-            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status, wlim))) break;
             tc_fence_after();
             // the block of t1s this warp writes held the previous slab's partials:
             // every warp has finished reading them
-            if (kt == 0 && !__all_sync(0xffffffffu, mbar_wait(t1free, (slab & 1u) ^ 1u, abort_flag, status))) break;
+            if (kt == 0 && !__all_sync(0xffffffffu, mbar_wait(t1free, (slab & 1u) ^ 1u, abort_flag, status, wlim))) break;
             const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
             #pragma unroll
             for (int c0 = 0; c0 < RP; c0 += 16) {
@@ -604,14 +608,14 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 // every warp has finished group fgi - 1, whose slot the next group uses
                 bool ok = true;
                 if (uissuer && !uresident && fgi >= 1 && fgi + 1 < nfg) {
-                    ok = mbar_wait(ufree, uint32_t((fgi - 1) & 1), abort_flag, status);
+                    ok = mbar_wait(ufree, uint32_t((fgi - 1) & 1), abort_flag, status, wlim);
                     if (ok) load_u(int((fgi + 1) % C::USLOTS), (kt + 1) % a.n_kt);
                 }
                 if (!__all_sync(0xffffffffu, ok)) break;
             }
             const int us = uresident ? kt : int(fgi % C::USLOTS);
             const uint32_t uj = uresident ? 0u : uint32_t(fgi / C::USLOTS);
-            if (!__all_sync(0xffffffffu, mbar_wait(ufull(us), uj & 1u, abort_flag, status))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(ufull(us), uj & 1u, abort_flag, status, wlim))) break;
             // stage 2 over this warp's rows that lie inside I_{N-2}, in groups of four
             // (the rows past it are zero in both operands: TMA zero fill and the
             // padded factor, so a partial group is harmless)
@@ -652,7 +656,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(t1full);
-                if (!__all_sync(0xffffffffu, mbar_wait(t1full, slab & 1u, abort_flag, status))) break;
+                if (!__all_sync(0xffffffffu, mbar_wait(t1full, slab & 1u, abort_flag, status, wlim))) break;
                 // this warp reduces rows c = 8 quad .. 8 quad + 7 of the block
                 const int c = 8 * quad + (lane >> 2), d0 = 8 * (lane & 3);
                 float sum[8];
@@ -682,6 +686,10 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 ++slab;
             }
         }
+        // the U copies have landed before exit, also when the loop ended early
+        if (uissuer)
+            for (int us = 0; us < C::USLOTS; ++us)
+                if (u_loads[us]) mbar_drain(ufull(us), (u_loads[us] - 1u) & 1u, status);
     }
 
     tc_fence_before();
@@ -714,7 +722,9 @@ int launch_ttmc_variant(const TtmcArgs &a, int n_sm, void *stream) {
     const int64_t groups = (a.S + SG - 1) / SG;
     int64_t grid = groups < n_sm ? groups : n_sm;
     if (grid < 1) grid = 1;
-    ttmc_fused_kernel<STORE, SG, TC2><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(a);
+    TtmcArgs ka = a;
+    ka.wait_ns = wait_limit_ns();
+    ttmc_fused_kernel<STORE, SG, TC2><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(ka);
     count_launch();
     return int(cudaGetLastError());
 }

@@ -1,7 +1,8 @@
 """Batched MTTKRP: uneven instances in persistent launches, one per kind (graph-replayed).
 
 Each instance of the batch matches the FP64 oracle within the split-BF16 gate
-(relative Frobenius 1e-5) and the single-instance split path within 1e-5;
+(relative Frobenius 1e-5, and element-wise within 1e-4 of the largest oracle
+entry) and the single-instance split path within 2e-5;
 graph replays are bit-identical; the plain batch equals per-instance plain
 executes bit for bit; the autotuner keeps the results.
 """
@@ -15,6 +16,14 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2206_08301_gb300 as dz  # noqa: E402
+
+
+def _gate(got, ref):
+    """The split-BF16 gate against the FP64 oracle: Frobenius 1e-5 and element-wise 1e-4."""
+    err = oracle.rel_error(got, ref)
+    worst = oracle.max_elem_error(got, ref)
+    assert err <= 1e-5, f"relative Frobenius error {err:.3e}"
+    assert worst <= 1e-4, f"max element error {worst:.3e} of max|ref|"
 
 
 def _batch(n, seed, lo=32, hi=160):
@@ -51,7 +60,7 @@ def test_batched_split_matches_oracle_and_single_path():
     assert b.status() == 0
     for (dims, R, mode, X, U), out, ops in zip(items, outs, ins):
         got = out.cpu().numpy()
-        assert oracle.rel_error(got, oracle.mttkrp(X, U, mode)) <= 1e-5
+        _gate(got, oracle.mttkrp(X, U, mode))
         # the single-plan path may regroup the contraction (a merged inner mode), so the two
         # GPU results are each within 1e-5 of the oracle and within 2e-5 of each other
         single = dz.mttkrp(ops[0], [torch.from_numpy(u).cuda() for u in U], mode, prec="split_bf16")
@@ -90,7 +99,7 @@ def test_batched_autotune_keeps_results():
     b(ins, outs)
     torch.cuda.synchronize()
     for (dims, R, mode, X, U), out in zip(items, outs):
-        assert oracle.rel_error(out.cpu().numpy(), oracle.mttkrp(X, U, mode)) <= 1e-5
+        _gate(out.cpu().numpy(), oracle.mttkrp(X, U, mode))
 
 
 @pytest.mark.parametrize("kind", ["aligned", "unaligned", "offset"])
@@ -126,4 +135,4 @@ def test_batched_launch_groups(kind):
     torch.cuda.synchronize()
     assert b.status() == 0
     for out, r in zip(outs, ref):
-        assert oracle.rel_error(out.cpu().numpy(), r) <= 1e-5
+        _gate(out.cpu().numpy(), r)

@@ -336,3 +336,24 @@ def test_uniform_slab_matches_whole_tensor():
     X = inputs.tensor_uniform_f32(3, dims)
     for mode in range(3):
         np.testing.assert_array_equal(inputs.uniform_slab(3, dims, mode, 2), np.take(X, 2, axis=mode))
+
+
+def test_cpals_perturbation_hook_is_neutral_and_linear():
+    # the hook that the CP-ALS tolerance derivation uses: the identity changes nothing, and
+    # a relative perturbation of size eps moves a well-conditioned sweep by O(eps)
+    rng = np.random.default_rng(12)
+    dims, R = (9, 8, 7), 3
+    A = [rng.standard_normal((d, R)) for d in dims]
+    X = np.einsum("ir,jr,kr->ijk", *A) + 1e-2 * rng.standard_normal(dims)
+    init = [a + 0.3 * rng.standard_normal(a.shape) for a in A]
+    f0, l0, fit0 = oracle.cpals(X, init, 2)
+    f1, l1, fit1 = oracle.cpals(X, init, 2, perturb=lambda M, m: M)
+    for a, b in zip(f0, f1):
+        assert np.array_equal(a, b)
+    assert np.array_equal(l0, l1) and fit0 == fit1
+    f2, l2, fit2 = oracle.cpals(X, init, 2, perturb=lambda M, m: M * (1.0 + 1e-7))
+    # a uniform scale of M scales the unnormalised update, which the normalisation removes
+    # from the factors and moves into lambda
+    for a, b in zip(f0, f2):
+        assert oracle.rel_error(b, a) <= 1e-12
+    assert abs(oracle.rel_error(l2, l0) - 1e-7) <= 1e-9

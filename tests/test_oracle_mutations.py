@@ -4,11 +4,19 @@ Each mutation edits one line of oracle.c (a dropped factor, a transposed
 factor index, a wrong output row, a skipped term, a wrong TTM operand index),
 compiles the copy with gcc into a temporary directory and checks that at least
 one pin (hand-worked example, rank-1 closed form, numpy einsum) now fails.
+The error metric that decides every parity test is mutated the same way: the
+C norm (no square root, |a| instead of a^2, a skipped element, a wrong
+operand) and the Python relative / element-wise errors (no division, the
+wrong norm in the denominator, the zero-reference branch returning 0, a sum
+instead of a difference, a mean instead of a maximum), each of which must
+break a pin of tests/test_oracle_metric.py.
 The real oracle is never modified.
 """
 import ctypes
+import inspect
 import os
 import subprocess
+import textwrap
 
 import numpy as np
 import pytest
@@ -45,6 +53,8 @@ def _build(tmp_path, name, old, new):
                                   ctypes.POINTER(_dp), _dp]
     lib.oracle_ttmc.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, _i64p, _dp,
                                 ctypes.POINTER(_dp), _dp]
+    lib.oracle_frobenius.argtypes = [_dp, ctypes.c_int64]
+    lib.oracle_frobenius.restype = ctypes.c_double
     return lib
 
 
@@ -102,3 +112,80 @@ def test_planted_mistake_is_caught(tmp_path, name):
     old, new = MUTATIONS[name]
     lib = _build(tmp_path, name, old, new)
     assert not _pins_pass(lib), f"mutation {name} slipped through the pins"
+
+
+# ---------------------------------------------------------------------------
+# the error metric
+# ---------------------------------------------------------------------------
+
+from test_oracle_metric import metric_pins_hold  # noqa: E402
+
+NORM_MUTATIONS = {
+    "no_square_root": ("return (double)__builtin_sqrtl(s);", "return (double)s;"),
+    "abs_instead_of_square": ("s += (long double)a[i] * (long double)a[i];", "s += (a[i] < 0 ? -a[i] : a[i]);"),
+    "skipped_element": ("for (int64_t i = 0; i < n; ++i) s +=", "for (int64_t i = 1; i < n; ++i) s +="),
+    "wrong_operand": ("s += (long double)a[i] * (long double)a[i];", "s += (long double)a[i] * (long double)a[0];"),
+}
+
+REL_MUTATIONS = {
+    "no_division": ("return nd / nr if nr > 0 else nd", "return nd"),
+    "wrong_denominator": ("nr = frobenius(ref)", "nr = frobenius(got)"),
+    "zero_reference_gives_zero": ("return nd / nr if nr > 0 else nd", "return nd / nr if nr > 0 else 0.0"),
+    "sum_not_difference": ("diff = got - ref", "diff = got + ref"),
+    "squared_ratio": ("return nd / nr if nr > 0 else nd", "return (nd / nr) ** 2 if nr > 0 else nd"),
+}
+
+ELEM_MUTATIONS = {
+    "mean_not_max": ("worst = float(np.abs(got - ref).max())", "worst = float(np.abs(got - ref).mean())"),
+    "no_scale": ("return worst / scale if scale > 0 else worst", "return worst"),
+    "signed_difference": ("worst = float(np.abs(got - ref).max())", "worst = float((got - ref).max())"),
+}
+
+
+def _norm_from(lib):
+    def frob(a):
+        a = np.ascontiguousarray(np.asarray(a), dtype=np.float64).ravel()
+        return float(lib.oracle_frobenius(a.ctypes.data_as(_dp), a.size))
+    return frob
+
+
+def _mutated_python(func, old, new, namespace):
+    src = textwrap.dedent(inspect.getsource(func))
+    assert src.count(old) == 1, (func.__name__, old)
+    ns = dict(namespace)
+    exec(src.replace(old, new), ns)
+    return ns[func.__name__]
+
+
+def test_unmutated_norm_passes_metric_pins(tmp_path):
+    lib = _build(tmp_path, "identity_norm", "#define ORACLE_MAX_ORDER 8", "#define ORACLE_MAX_ORDER 8")
+    frob = _norm_from(lib)
+    rel = _mutated_python(oracle.rel_error, "diff = got - ref", "diff = got - ref",
+                          {"_f64": oracle._f64, "frobenius": frob, "np": np})
+    assert metric_pins_hold(frob, rel, oracle.max_elem_error)
+
+
+@pytest.mark.parametrize("name", sorted(NORM_MUTATIONS))
+def test_planted_norm_mistake_is_caught(tmp_path, name):
+    old, new = NORM_MUTATIONS[name]
+    lib = _build(tmp_path, name, old, new)
+    frob = _norm_from(lib)
+    rel = _mutated_python(oracle.rel_error, "diff = got - ref", "diff = got - ref",
+                          {"_f64": oracle._f64, "frobenius": frob, "np": np})
+    assert not metric_pins_hold(frob, rel), f"norm mutation {name} slipped through the pins"
+
+
+@pytest.mark.parametrize("name", sorted(REL_MUTATIONS))
+def test_planted_rel_error_mistake_is_caught(name):
+    old, new = REL_MUTATIONS[name]
+    rel = _mutated_python(oracle.rel_error, old, new,
+                          {"_f64": oracle._f64, "frobenius": oracle.frobenius, "np": np})
+    assert not metric_pins_hold(oracle.frobenius, rel), f"rel_error mutation {name} slipped through"
+
+
+@pytest.mark.parametrize("name", sorted(ELEM_MUTATIONS))
+def test_planted_max_elem_error_mistake_is_caught(name):
+    old, new = ELEM_MUTATIONS[name]
+    elem = _mutated_python(oracle.max_elem_error, old, new, {"_f64": oracle._f64, "np": np})
+    assert not metric_pins_hold(oracle.frobenius, oracle.rel_error, elem), \
+        f"max_elem_error mutation {name} slipped through"
