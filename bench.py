@@ -67,19 +67,23 @@ def _alg_bytes_one_mode():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 10 ms; only the samples whose
-    timestamps fall inside the timed region (mark_start .. mark_stop) are reported (with
-    the last sample before it when the region is shorter than the sampling interval)."""
+    """nvidia-smi clocks and throttle reasons, sampled every 10 ms.  ``mark_start`` /
+    ``mark_stop`` bound the main timed region and ``region(name)`` any number of named ones;
+    only the samples whose timestamps fall inside a region are reported for it (with the last
+    sample before it when the region is shorter than the sampling interval)."""
 
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.path = f"/tmp/deinsum_clocks_{os.getpid()}.csv"
         self.t0 = self.t1 = None
+        self.regions = {}
+        self.rows = []
 
     def start(self):
         """Start sampling and return once the first sample has been written (or after 5 s)."""
@@ -101,6 +105,17 @@ class ClockSampler:
     def mark_stop(self):
         self.t1 = time.time()
 
+    def region(self, name):
+        sampler = self
+
+        class _Region:
+            def __enter__(self):
+                self.t0 = time.time()
+
+            def __exit__(self, *exc):
+                sampler.regions[name] = (self.t0, time.time())
+        return _Region()
+
     @staticmethod
     def _stamp(text):
         try:
@@ -118,32 +133,40 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        rows = []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as fh:
             for line in fh:
                 parts = [p.strip() for p in line.split(",")]
                 if len(parts) < 10:
                     continue
                 try:
-                    rows.append((self._stamp(parts[0]), float(parts[2]), float(parts[3]), parts[6:10]))
+                    self.rows.append((self._stamp(parts[0]), float(parts[2]), float(parts[3]), parts[6:10]))
                 except ValueError:
                     continue
         os.unlink(self.path)
-        inside = [r for r in rows if r[0] is not None and self.t0 is not None and self.t0 <= r[0] <= self.t1]
+        return self.stats(self.t0, self.t1)
+
+    def stats(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = self.rows
+        inside = [r for r in rows if r[0] is not None and t0 is not None and t0 <= r[0] <= t1]
         if not inside:   # a region shorter than the interval: the sample just before it
-            before = [r for r in rows if r[0] is not None and self.t0 is not None and r[0] < self.t0]
+            before = [r for r in rows if r[0] is not None and t0 is not None and r[0] < t0]
             inside = before[-1:] if before else rows[:1]
         reasons = set()
         for r in inside:
-            for name, val in zip(names, r[3]):
+            for name, val in zip(self.NAMES, r[3]):
                 if val.lower() == "active":
                     reasons.add(name)
         sm = [r[1] for r in inside]
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(r[2] for r in inside) if inside else None,
                 "reasons": sorted(reasons), "samples": len(sm),
-                "interval_ms": 10, "region_ms": (self.t1 - self.t0) * 1e3 if self.t0 and self.t1 else None}
+                "interval_ms": 10, "region_ms": (t1 - t0) * 1e3 if t0 and t1 else None}
+
+    def region_stats(self, name):
+        t0, t1 = self.regions.get(name, (None, None))
+        return self.stats(t0, t1)
 
 
 def _kernel_source_hash(source="mttkrp_tc.cu"):
@@ -164,13 +187,16 @@ def _traffic_per_launch(prec, source="mttkrp_tc.cu"):
     return None
 
 
-def cpu_oracle_sample(seed, budget_s: float):
-    """Time the FP64 oracle on sampled output rows of the workload until ``budget_s`` is spent.
+def cpu_oracle_sample(seed, budget_s: float, threads: int = 0):
+    """Time the FP64 oracle on sampled output rows of the workload until ``budget_s`` is spent,
+    on ``threads`` host threads (0: all the oracle's OpenMP runtime offers).
 
-    Returns (GB/s of X covered, seconds, rows, cores).  Slab generation is not timed.
+    Returns (GB/s of X covered, seconds, rows, threads used).  Slab generation is not timed.
     """
     import oracle
     from paper_2206_08301_gb300 import inputs
+    all_threads = oracle.set_threads(0)
+    used = oracle.set_threads(threads if threads > 0 else all_threads)
     dims = (N_EXT,) * 3
     Us = [inputs.factor_normal(seed, m, N_EXT, RANK_R, sigma=np.sqrt(1.0 / RANK_R)).astype(np.float32)
           for m in range(3)]
@@ -187,8 +213,8 @@ def cpu_oracle_sample(seed, budget_s: float):
             covered += 4.0 * slabs.size
             nrows += len(rows)
         k += 1
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return covered / spent / 1e9, spent, nrows, cores
+    oracle.set_threads(all_threads)
+    return covered / spent / 1e9, spent, nrows, used
 
 
 def run_once(args):
@@ -364,148 +390,6 @@ def run_serving(args):
     return 0
 
 
-def run_batched(args):
-    """512 uneven order-3 MTTKRP instances (extents U{32..384}, R in {8,16,32,64}, mode U{0,1,2},
-    X uniform[-1,1) float32): the graph-replayed persistent split-BF16 launches, one per
-    instance kind (autotuned unit size), against 512 separate plain launches and 512 separate
-    split launches."""
-    import torch
-    import oracle
-    import paper_2206_08301_gb300 as dz
-    from paper_2206_08301_gb300 import inputs
-    n, seed = args.instances, 33
-    ext = inputs.draw_int(seed, 0, 32, 384, 3 * n).reshape(n, 3)
-    ranks = np.array([8, 16, 32, 64])[inputs.draw_int(seed, 1, 0, 3, n)]
-    modes = inputs.draw_int(seed, 2, 0, 2, n)
-    einsums, extents, ins, outs, facs = [], [], [], [], []
-    for k in range(n):
-        dims = tuple(int(d) for d in ext[k])
-        R, mode = int(ranks[k]), int(modes[k])
-        X = dz.gen_uniform(seed * 10000 + k, inputs.STREAM_X, dims)
-        U = [torch.from_numpy(inputs.factor_normal(seed * 10000 + k, m, d, R).astype(np.float32)).cuda()
-             for m, d in enumerate(dims)]
-        einsums.append(dz.mttkrp_einsum(3, mode))
-        extents.append(list(dims) + [R])
-        ins.append([X] + [U[m] for m in range(3) if m != mode])
-        outs.append(torch.empty(dims[mode], R, device="cuda"))
-        facs.append(U)
-    torch.cuda.synchronize()
-    stream = torch.cuda.Stream()
-
-    def timed(fn, reps):
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                fn()
-            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-            e0.record(stream)
-            for _ in range(reps):
-                fn()
-            e1.record(stream)
-        stream.synchronize()
-        return e0.elapsed_time(e1) / reps
-
-    bsplit = dz.Batch(einsums, extents, "split_bf16")
-    with torch.cuda.stream(stream):
-        tune_ms = bsplit.autotune(ins, outs, stream=stream)
-    t_batch = timed(lambda: bsplit(ins, outs, stream=stream), args.steps)
-    info = bsplit.info()
-    status = bsplit.status()
-    # accuracy on a sample of instances (FP64 oracle on 4 sampled rows of each)
-    errs = []
-    for k in range(0, n, max(1, n // 16)):
-        dims, mode = tuple(int(d) for d in ext[k]), int(modes[k])
-        rows = inputs.sample_rows(seed * 10000 + k, dims[mode], 4)
-        Xh = ins[k][0]
-        slabs = np.stack([Xh.select(mode, int(r)).cpu().numpy().ravel() for r in rows])
-        ref = oracle.mttkrp_rows(dims, mode, slabs, [f.cpu().numpy() for f in facs[k]])
-        errs.append(oracle.rel_error(outs[k][torch.from_numpy(rows).cuda()].cpu().numpy(), ref))
-    bplain = dz.Batch(einsums, extents, "plain")
-    t_plain = timed(lambda: bplain(ins, outs, stream=stream), max(1, args.steps // 2))
-    plans = [dz.Plan(e, x, "float32", "split_bf16") for e, x in zip(einsums, extents)]
-    t_sep = timed(lambda: [p(*i, out=o, stream=stream) for p, i, o in zip(plans, ins, outs)], max(1, args.steps // 2))
-    gb = info["alg_bytes"] / 1e9
-    line = {"metric": "batched MTTKRP GB/s (persistent launches vs separate launches)", "unit": "GB/s",
-            "value": gb / (t_batch * 1e-3), "n_gpus": 1, "instances": n, "data": "synthetic",
-            "config": {"workload": f"{n} order-3 MTTKRP instances, extents U{{32..384}}, R in {{8,16,32,64}}, "
-                                   "mode U{0,1,2}, X uniform[-1,1) float32", "alg_gb": gb,
-                       "units": info["units"], "grid": info["grid"], "unit_div_autotuned": info["unit_div"]},
-            "batched_split_ms": t_batch, "separate_plain_launches_ms": t_plain,
-            "separate_split_launches_ms": t_sep, "speedup_vs_plain_launches": t_plain / t_batch,
-            "speedup_vs_separate_split": t_sep / t_batch, "autotune_best_ms": tune_ms,
-            "rel_err_max_sampled": max(errs), "device_status": status}
-    print(json.dumps(line))
-    return 0
-
-
-def run_ttmc(args):
-    """TTMc X 256^4 FP32 uniform[-1,1), U1..U3 256x32 N(0,1), `ijkl,jb,kc,ld->ibcd`: the fused split-BF16
-    path (last two modes on the tensor cores, T1 on chip) against the plain FP32 chain of TTMs."""
-    import torch
-    import oracle
-    import paper_2206_08301_gb300 as dz
-    from paper_2206_08301_gb300 import inputs
-    seed, n, R = 4096, 256, 32
-    dims = (n,) * 4
-    spec = dz.ttmc_einsum(4, 0)
-    X = dz.gen_uniform(seed, inputs.STREAM_X, dims)
-    Us = [inputs.factor_normal(seed, m, n, R).astype(np.float32) for m in range(4)]
-    Ud = [torch.from_numpy(u).cuda() for u in Us]
-    out = torch.empty(n, R, R, R, device="cuda")
-    stream = torch.cuda.Stream()
-    plans = {p: dz.Plan(spec, list(dims) + [R, R, R], "float32", p) for p in ("split_bf16", "plain")}
-
-    def timed(plan, steps, kernel=False):
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                plan(X, *Ud[1:], out=out, stream=stream)
-        stream.synchronize()
-        if kernel:
-            plan.set_kernel_timing(True)
-            plan.kernel_time()
-        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            for _ in range(steps):
-                plan(X, *Ud[1:], out=out, stream=stream)
-            e1.record(stream)
-        stream.synchronize()
-        k = plan.kernel_time() if kernel else (0.0, 0)
-        plan.set_kernel_timing(False)
-        return e0.elapsed_time(e1) / steps, k
-
-    launches0 = dz.kernel_launch_count()
-    ms, (kms, kn) = timed(plans["split_bf16"], args.steps, kernel=True)
-    launches = dz.kernel_launch_count() - launches0
-    status = plans["split_bf16"].last_device_status()
-    rows = inputs.sample_rows(seed, n, 2, tag=7)
-    got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
-    ms_plain, _ = timed(plans["plain"], max(1, args.steps // 2))
-    del X
-    slabs = np.stack([inputs.uniform_slab(seed, dims, 0, int(r)).ravel() for r in rows])
-    ref = oracle.ttmc_rows(dims, 0, slabs, Us)
-    info = plans["split_bf16"].info()
-    gb = info["alg_bytes"] / 1e9
-    x_bytes = 4.0 * n ** 4
-    t2_bytes = 4.0 * n * n * R * R
-    kern_ms = kms / max(1, kn)
-    peak, peak_kind = _peaks()
-    achieved = (x_bytes + t2_bytes) / (kern_ms * 1e-3) / 1e9 if kn else None
-    line = {"metric": "TTMc GB/s (algorithmic bytes |X| + factors + Y per step)", "unit": "GB/s",
-            "value": gb / (ms * 1e-3), "n_gpus": 1, "steps": args.steps, "ms_per_step": ms,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "TTMc ijkl,jb,kc,ld->ibcd, X 256^4 FP32 uniform[-1,1), U 256x32 N(0,1)",
-                       "arith": "split-BF16 tcgen05 (modes l then k fused, T1 on chip) + plain FP32 TTM over j",
-                       "l2": "inputs larger than L2 (X = 17.2 GB)", "alg_gb": gb},
-            "roofline": {"bound": "hbm", "kernel": "ttmc_fused_kernel", "kernel_ms_avg": kern_ms,
-                         "bytes_per_launch": x_bytes + t2_bytes, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak if achieved else None, "peak_kind": peak_kind,
-                         "traffic": _traffic_per_launch("ttmc_split_bf16", "ttmc_tc.cu")},
-            "plain_chain_ms": ms_plain, "speedup_vs_plain_chain": ms_plain / ms,
-            "rel_err_sampled_rows": oracle.rel_error(got, ref), "gpu_launches": launches, "device_status": status}
-    print(json.dumps(line))
-    return 0
-
-
 def run_paper(args):
     """The paper's own benchmark shapes (Table V, single-device sizes; uniform X, factors N(0,1)):
     MTTKRP-O3-M{0,1,2} at 1024^3, R 24; the running example of Sec. II-A (MTTKRP + MM,
@@ -595,16 +479,311 @@ def run_paper(args):
     return 0
 
 
-def run_cpals(args):
-    """CP-ALS sweeps on X 1024^3 = rank-32 CP tensor (N(0,1) factors) + 1e-2 noise, R = 32,
-    split-BF16: the dimension tree (modes 0 and 1 share X x_2 U_2, two X streams per sweep)
-    against the plain three-MTTKRP sweep, both from the same start.  A run of S sweeps and one
-    of a single sweep are timed; their difference over S - 1 is the steady-state sweep (fit by
-    the expansion), the rest the per-run cost (||X||^2, final residual fit, set-up)."""
+# ---------------------------------------------------------------------------
+# Per-configuration measurements (the "workloads" of the benchmark line).  Each
+# returns one record: its metric and value, the dominant kernel's time and its
+# roofline fraction against the measured peak, the comparison the configuration
+# names (plain FP32 CUDA cores, separate launches, one-at-a-time solves), the
+# relative error of sampled outputs against the FP64 oracle, and the clocks seen
+# during its own timed region.
+# ---------------------------------------------------------------------------
+
+FP32_CORE_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def _events_ms(stream, fn, reps, warm=3):
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warm):
+            fn()
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+    stream.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _plan_timed(plan, ops, out, stream, reps, warm=3):
+    """(ms per execute, average main-kernel ms) of a plan over `reps` executes."""
+    fn = lambda: plan(*ops, out=out, stream=stream)  # noqa: E731
+    with torch_stream(stream):
+        for _ in range(warm):
+            fn()
+    stream.synchronize()
+    plan.set_kernel_timing(True)
+    plan.kernel_time()
+    ms = _events_ms(stream, fn, reps, warm=0)
+    kms, kn = plan.kernel_time()
+    plan.set_kernel_timing(False)
+    return ms, kms / max(1, kn)
+
+
+def torch_stream(stream):
+    import torch
+    return torch.cuda.stream(stream)
+
+
+def measure_c0_fp64(clk, reps=200):
+    """MTTKRP order 3, X 64^3 FP64 uniform[-1,1), factors 64 x 16 N(0,1), mode 0, plain FP64
+    CUDA-core kernel: latency per execute (the configuration fits in L2; no roofline), error
+    against the FP64 oracle over the whole output."""
+    import torch
+    import oracle
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    seed, n, R = 64, 64, 16
+    dims = (n, n, n)
+    X = dz.gen_uniform(seed, inputs.STREAM_X, dims, dtype=torch.float64)
+    Us = [inputs.factor_normal(seed, m, n, R) for m in range(3)]
+    Ud = [torch.from_numpy(u).cuda() for u in Us]
+    plan = dz.Plan(dz.mttkrp_einsum(3, 0), list(dims) + [R], "float64", "plain")
+    out = torch.empty(n, R, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    with clk.region("c0"):
+        ms, kms = _plan_timed(plan, [X, Ud[1], Ud[2]], out, stream, reps)
+    ref = oracle.mttkrp(inputs.tensor_uniform_f64(seed, dims), Us, 0)
+    got = out.cpu().numpy()
+    ab = plan.info()["alg_bytes"]
+    return {"workload": "MTTKRP 64^3 FP64 uniform[-1,1), R 16 N(0,1), mode 0, plain FP64 CUDA cores",
+            "metric": "us per execute", "value": ms * 1e3, "unit": "us", "higher_is_better": False,
+            "kernel": "mttkrp_plain_kernel<double>", "kernel_us": kms * 1e3, "alg_gb_s": ab / (ms * 1e-3) / 1e9,
+            "rel_err": oracle.rel_error(got, ref), "max_elem_err": oracle.max_elem_error(got, ref),
+            "gate": "rel_err <= 1e-12", "sample": "whole output", "clocks_region": "c0"}
+
+
+def measure_c1_plain(clk, X, Ud, Us, seed, peak, reps=5):
+    """The benchmark configuration (MTTKRP 1024^3, R 32, modes 0-2) on the plain FP32
+    CUDA-core kernel: the arm the split-BF16 tensor-core path must beat."""
+    import torch
+    import oracle
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    dims = (N_EXT,) * 3
+    stream = torch.cuda.Stream()
+    plans = {m: dz.Plan(dz.mttkrp_einsum(3, m), list(dims) + [RANK_R], "float32", "plain") for m in MODES}
+    outs = {m: torch.empty(N_EXT, RANK_R, device="cuda") for m in MODES}
+    tot_ms, kern = 0.0, []
+    with clk.region("c1_plain"):
+        for m in MODES:
+            ms, kms = _plan_timed(plans[m], [X] + [Ud[k] for k in range(3) if k != m], outs[m], stream, reps)
+            tot_ms += ms
+            kern.append(kms)
+    errs = []
+    for m in MODES:
+        rows = inputs.sample_rows(seed, N_EXT, 16, tag=m)
+        slabs = np.stack([inputs.uniform_slab(seed, dims, m, int(r)).ravel() for r in rows])
+        ref = oracle.mttkrp_rows(dims, m, slabs, Us)
+        errs.append(oracle.rel_error(outs[m][torch.from_numpy(rows).cuda()].cpu().numpy(), ref))
+    kms = float(np.mean(kern))
+    flops = 2.0 * N_EXT ** 3 * RANK_R
+    return {"workload": "MTTKRP 1024^3 FP32, R 32, modes 0,1,2 per step, plain FP32 CUDA-core kernel",
+            "metric": "GB/s", "value": 3 * _alg_bytes_one_mode() / (tot_ms * 1e-3) / 1e9, "unit": "GB/s",
+            "ms_per_step": tot_ms, "kernel": "mttkrp_plain_kernel<float>", "kernel_ms_avg": kms,
+            "roofline": {"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12, "peak": FP32_CORE_TFLOPS,
+                         "unit": "TFLOP/s", "frac": flops / (kms * 1e-3) / 1e12 / FP32_CORE_TFLOPS,
+                         "peak_kind": "nominal FP32 FMA rate (152 SMs x 128 lanes x 2 x 2.07 GHz)",
+                         "hbm_frac": 4.0 * N_EXT ** 3 / (kms * 1e-3) / 1e9 / peak},
+            "rel_err": max(errs), "sample": "16 output rows per mode", "clocks_region": "c1_plain"}
+
+
+def measure_c2a_order5(clk, peak, reps=5):
+    """MTTKRP order 5, X 64^5 FP32 = rank-24 CP (N(0,1) factors) + 1e-3 noise, R 24 factors
+    N(0,1), modes 0 and 2: split-BF16 tensor cores against the plain FP32 kernel."""
+    import torch
+    import oracle
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    seed, n, rc, R = 5055, 64, 24, 24
+    dims = (n,) * 5
+    A = [inputs.factor_normal(seed, m, n, rc, stream_base=inputs.STREAM_CP) for m in range(5)]
+    X = dz.gen_cp(seed, dims, [torch.from_numpy(a).cuda() for a in A], 1e-3)
+    Us = [inputs.factor_normal(seed, m, n, R).astype(np.float32) for m in range(5)]
+    Ud = [torch.from_numpy(u).cuda() for u in Us]
+    stream = torch.cuda.Stream()
+    modes = {}
+    xb = 4.0 * n ** 5
+    with clk.region("c2a"):
+        for mode in (0, 2):
+            spec, ext = dz.mttkrp_einsum(5, mode), list(dims) + [R]
+            ops = [X] + [Ud[m] for m in range(5) if m != mode]
+            res = {}
+            for prec in ("split_bf16", "plain"):
+                plan = dz.Plan(spec, ext, "float32", prec)
+                out = torch.empty(n, R, device="cuda")
+                ms, kms = _plan_timed(plan, ops, out, stream, reps if prec == "split_bf16" else 2)
+                res[prec] = (ms, kms, plan.info()["alg_bytes"], out)
+            modes[mode] = res
+    recs = {}
+    for mode, res in modes.items():
+        rows = inputs.sample_rows(seed, n, 4, tag=mode)
+        slabs = np.stack([inputs.cp_slab(seed, dims, A, 1e-3, mode, int(r)).ravel() for r in rows])
+        ref = oracle.mttkrp_rows(dims, mode, slabs, Us)
+        ms, kms, ab, out = res["split_bf16"]
+        recs[f"mode{mode}"] = {
+            "value": ab / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms": ms, "plain_fp32_ms": res["plain"][0],
+            "speedup_vs_plain": res["plain"][0] / ms,
+            "roofline": {"bound": "hbm", "kernel": "mttkrp_tc_kernel", "kernel_ms": kms,
+                         "achieved": xb / (kms * 1e-3) / 1e9, "peak": peak,
+                         "frac": xb / (kms * 1e-3) / 1e9 / peak},
+            "rel_err": oracle.rel_error(out[torch.from_numpy(rows).cuda()].cpu().numpy(), ref)}
+    del X
+    torch.cuda.empty_cache()
+    return {"workload": "MTTKRP 64^5 FP32 = rank-24 CP + 1e-3 noise, R 24, modes 0 and 2, split-BF16 vs plain FP32",
+            "metric": "GB/s", "unit": "GB/s", "value": min(r["value"] for r in recs.values()),
+            "modes": recs, "rel_err": max(r["rel_err"] for r in recs.values()),
+            "sample": "4 output rows per mode", "clocks_region": "c2a"}
+
+
+def measure_c2b_ttmc(clk, peak, reps=3):
+    """TTMc ijkl,jb,kc,ld->ibcd, X 256^4 FP32 uniform[-1,1), U 256 x 32 N(0,1): the fused
+    split-BF16 path (modes l and k on the tensor cores, T1 on chip) against the plain FP32
+    chain of TTMs."""
+    import torch
+    import oracle
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    seed, n, R = 4096, 256, 32
+    dims = (n,) * 4
+    spec = dz.ttmc_einsum(4, 0)
+    X = dz.gen_uniform(seed, inputs.STREAM_X, dims)
+    Us = [inputs.factor_normal(seed, m, n, R).astype(np.float32) for m in range(4)]
+    Ud = [torch.from_numpy(u).cuda() for u in Us]
+    out = torch.empty(n, R, R, R, device="cuda")
+    stream = torch.cuda.Stream()
+    plans = {p: dz.Plan(spec, list(dims) + [R, R, R], "float32", p) for p in ("split_bf16", "plain")}
+    with clk.region("c2b"):
+        l0 = dz.kernel_launch_count()
+        ms, kms = _plan_timed(plans["split_bf16"], [X] + Ud[1:], out, stream, reps)
+        launches = (dz.kernel_launch_count() - l0) / (reps + 3)
+        status = plans["split_bf16"].last_device_status()
+        rows = inputs.sample_rows(seed, n, 2, tag=7)
+        got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+        ms_plain, _ = _plan_timed(plans["plain"], [X] + Ud[1:], out, stream, 1, warm=1)
+    del X
+    torch.cuda.empty_cache()
+    slabs = np.stack([inputs.uniform_slab(seed, dims, 0, int(r)).ravel() for r in rows])
+    ref = oracle.ttmc_rows(dims, 0, slabs, Us)
+    ab = plans["split_bf16"].info()["alg_bytes"]
+    kbytes = 4.0 * n ** 4 + 4.0 * n * n * R * R   # X once + T2 written once
+    return {"workload": "TTMc ijkl,jb,kc,ld->ibcd, X 256^4 FP32 uniform[-1,1), U 256x32 N(0,1), split-BF16 "
+                        "(fused last two modes) vs plain FP32 chain",
+            "metric": "GB/s", "value": ab / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
+            "alg_frac": ab / (ms * 1e-3) / 1e9 / peak,
+            "roofline": {"bound": "hbm", "kernel": "ttmc_fused_kernel", "kernel_ms": kms,
+                         "bytes_per_launch": kbytes, "achieved": kbytes / (kms * 1e-3) / 1e9, "peak": peak,
+                         "frac": kbytes / (kms * 1e-3) / 1e9 / peak},
+            "plain_chain_ms": ms_plain, "speedup_vs_plain_chain": ms_plain / ms, "launches_per_step": launches,
+            "rel_err": oracle.rel_error(got, ref), "max_elem_err": oracle.max_elem_error(got, ref),
+            "sample": "2 kept-mode slices (2 x 32^3 outputs)", "device_status": status,
+            "clocks_region": "c2b"}
+
+
+def measure_c3_batched(clk, peak, n=512, reps=5):
+    """512 uneven order-3 MTTKRP instances (extents U{32..384}, R in {8,16,32,64}, mode
+    U{0,1,2}, X uniform[-1,1) float32): the graph-replayed persistent split-BF16 launches
+    (autotuned unit size) against 512 separate plain launches and 512 separate split
+    executes."""
+    import torch
+    import oracle
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    seed = 33
+    ext = inputs.draw_int(seed, 0, 32, 384, 3 * n).reshape(n, 3)
+    ranks = np.array([8, 16, 32, 64])[inputs.draw_int(seed, 1, 0, 3, n)]
+    modes = inputs.draw_int(seed, 2, 0, 2, n)
+    einsums, extents, ins, outs, facs = [], [], [], [], []
+    for k in range(n):
+        dims = tuple(int(d) for d in ext[k])
+        R, mode = int(ranks[k]), int(modes[k])
+        X = dz.gen_uniform(seed * 10000 + k, inputs.STREAM_X, dims)
+        U = [torch.from_numpy(inputs.factor_normal(seed * 10000 + k, m, d, R).astype(np.float32)).cuda()
+             for m, d in enumerate(dims)]
+        einsums.append(dz.mttkrp_einsum(3, mode))
+        extents.append(list(dims) + [R])
+        ins.append([X] + [U[m] for m in range(3) if m != mode])
+        outs.append(torch.empty(dims[mode], R, device="cuda"))
+        facs.append(U)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    bsplit = dz.Batch(einsums, extents, "split_bf16")
+    with torch.cuda.stream(stream):
+        tune_ms = bsplit.autotune(ins, outs, stream=stream)
+    with clk.region("c3"):
+        l0 = dz.kernel_launch_count()
+        t_batch = _events_ms(stream, lambda: bsplit(ins, outs, stream=stream), reps)
+        launches = (dz.kernel_launch_count() - l0) / (reps + 3)
+    status = bsplit.status()
+    info = bsplit.info()
+    errs = []
+    for k in range(0, n, max(1, n // 16)):
+        dims, mode = tuple(int(d) for d in ext[k]), int(modes[k])
+        rows = inputs.sample_rows(seed * 10000 + k, dims[mode], 4)
+        slabs = np.stack([ins[k][0].select(mode, int(r)).cpu().numpy().ravel() for r in rows])
+        ref = oracle.mttkrp_rows(dims, mode, slabs, [f.cpu().numpy() for f in facs[k]])
+        errs.append(oracle.rel_error(outs[k][torch.from_numpy(rows).cuda()].cpu().numpy(), ref))
+    with clk.region("c3_baselines"):
+        bplain = dz.Batch(einsums, extents, "plain")
+        t_plain = _events_ms(stream, lambda: bplain(ins, outs, stream=stream), 2, warm=1)
+        plans = [dz.Plan(e, x, "float32", "split_bf16") for e, x in zip(einsums, extents)]
+        t_sep = _events_ms(stream, lambda: [p(*i, out=o, stream=stream) for p, i, o in zip(plans, ins, outs)], 2,
+                           warm=1)
+    gb = info["alg_bytes"] / 1e9
+    xb = sum(4.0 * float(np.prod(e[:3])) for e in extents)
+    del ins, outs, facs, bsplit, bplain, plans
+    torch.cuda.empty_cache()
+    return {"workload": f"{n} order-3 MTTKRP instances, extents U{{32..384}}, R in {{8,16,32,64}}, mode U{{0,1,2}}, "
+                        "X uniform[-1,1) float32, one graph-replayed persistent split-BF16 batch",
+            "metric": "GB/s", "value": gb / (t_batch * 1e-3), "unit": "GB/s", "ms_per_step": t_batch,
+            "roofline": {"bound": "hbm", "kernel": "mttkrp_tc_batched_kernel (whole batch)",
+                         "achieved": xb / (t_batch * 1e-3) / 1e9, "peak": peak,
+                         "frac": xb / (t_batch * 1e-3) / 1e9 / peak, "x_gb": xb / 1e9},
+            "separate_plain_launches_ms": t_plain, "separate_split_executes_ms": t_sep,
+            "speedup_vs_plain_launches": t_plain / t_batch, "speedup_vs_separate_split": t_sep / t_batch,
+            "launches_per_step": launches, "units": info["units"], "unit_div_autotuned": info["unit_div"],
+            "autotune_best_ms": tune_ms, "rel_err": max(errs), "sample": "4 rows of every 32nd instance",
+            "device_status": status, "clocks_region": "c3"}
+
+
+def measure_c4_serving(clk, n_req=64):
+    """CP-ALS serving: Poisson arrivals of requests (extents U{64..1024}, R U{8..64}, rank-R CP
+    N(0,1) + 1e-2 noise, 10 sweeps), continuous batching in 4 slots at the measured
+    one-at-a-time split-BF16 service rate, against one-at-a-time plain FP32 solves at the same
+    arrival rate."""
+    import torch
+    budget = 64 << 30
+    reqs = _serving_requests(n_req, 7)
+    torch.cuda.synchronize()
+    _serve_run(reqs[:4], 1, "split_bf16", None, budget, 1)            # warm-up
+    with clk.region("c4"):
+        span1, lat1, _, st1, _ = _serve_run(reqs, 1, "split_bf16", None, budget, 1)
+        mu = len(reqs) / span1
+        span, lat, gen, st, fits = _serve_run(reqs, 4, "split_bf16", mu, budget, 11)
+    with clk.region("c4_plain"):
+        spanp, latp, _, stp, _ = _serve_run(reqs, 1, "plain", mu, budget, 11)
+    return {"workload": f"{n_req} Poisson CP-ALS requests: extents U{{64..1024}}, R U{{8..64}}, rank-R CP N(0,1) "
+                        "+ 1e-2 noise, 10 sweeps, HBM budget 64 GiB, 4 slots, arrival rate = one-at-a-time rate",
+            "metric": "req/s", "value": len(reqs) / span, "unit": "req/s",
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "one_at_a_time_split": {"req_s": mu, "p50_ms": 1e3 * float(np.percentile(lat1, 50)),
+                                    "p99_ms": 1e3 * float(np.percentile(lat1, 99))},
+            "one_at_a_time_plain_at_same_rate": {"req_s": len(reqs) / spanp,
+                                                 "p50_ms": 1e3 * float(np.percentile(latp, 50)),
+                                                 "p99_ms": 1e3 * float(np.percentile(latp, 99))},
+            "ok": int(sum(x == 0 for x in st)), "fit_min": float(min(fits)),
+            "clocks_region": "c4"}
+
+
+def measure_cpals_sweep(clk, sweeps=4):
+    """CP-ALS sweeps on X 1024^3 = rank-32 CP + 1e-2 noise, R 32, split-BF16: steady-state
+    ms per sweep with the dimension tree (two X streams) and with three MTTKRPs."""
     import torch
     import paper_2206_08301_gb300 as dz
     from paper_2206_08301_gb300 import inputs
-    n, R, seed, sweeps = 1024, 32, 77, max(4, args.steps)
+    n, R, seed = 1024, 32, 77
     dims = (n, n, n)
     A = [torch.from_numpy(inputs.factor_normal(seed, m, n, R, stream_base=inputs.STREAM_CP).astype(np.float32)).cuda()
          for m in range(3)]
@@ -613,36 +792,63 @@ def run_cpals(args):
             .cuda() for m in range(3)]
     stream = torch.cuda.Stream()
     res = {}
-    for tree in (True, False):
-        cp = dz.CPALS(dims, R, "split_bf16")
-        cp.set_dimension_tree(tree)
-        F = [u.clone() for u in init]
-        t = {}
-        with torch.cuda.stream(stream):
-            cp.run(X, F, 1, stream=stream)          # first run: workspace, warm-up
-            for S in (1, sweeps):
+    with clk.region("cpals"):
+        for tree in (True, False):
+            cp = dz.CPALS(dims, R, "split_bf16")
+            cp.set_dimension_tree(tree)
+            t = {}
+            with torch.cuda.stream(stream):
                 F = [u.clone() for u in init]
-                e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-                e0.record(stream)
-                lam, fits = cp.run(X, F, S, stream=stream)
-                e1.record(stream)
-                stream.synchronize()
-                t[S] = e0.elapsed_time(e1)
-        per = (t[sweeps] - t[1]) / (sweeps - 1)
-        res[tree] = (per, t[1] - per, float(fits[-1]), cp.uses_dimension_tree, cp.status())
-    xb = 4.0 * n ** 3
-    arm = {}
-    for tree, key, streams in ((True, "dimension_tree", 2), (False, "three_mttkrps", 3)):
-        per, fixed, fit, used, st = res[tree]
-        arm[key] = {"ms_per_sweep": per, "ms_per_run_fixed": fixed, "x_streams_per_sweep": streams,
-                    "final_fit": fit, "used": used, "status": st, "x_gbs": streams * xb / (per * 1e-3) / 1e9}
-    line = {"metric": "CP-ALS ms per sweep (1024^3, R 32), steady state", "unit": "ms", "higher_is_better": False,
-            "value": res[True][0], "sweeps": sweeps, "data": "synthetic",
-            "config": {"workload": "CP-ALS on X 1024^3 FP32 = rank-32 CP (N(0,1) factors) + 1e-2 noise, R 32, "
-                                   "split-BF16 MTTKRPs, FP64 solves"},
-            **arm, "speedup": res[False][0] / res[True][0]}
-    print(json.dumps(line))
+                cp.run(X, F, 1, stream=stream)
+                for S in (1, sweeps):
+                    F = [u.clone() for u in init]
+                    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+                    e0.record(stream)
+                    lam, fits = cp.run(X, F, S, stream=stream)
+                    e1.record(stream)
+                    stream.synchronize()
+                    t[S] = e0.elapsed_time(e1)
+            per = (t[sweeps] - t[1]) / (sweeps - 1)
+            res[tree] = (per, float(fits[-1]), cp.status())
+    del X
+    torch.cuda.empty_cache()
+    return {"workload": "CP-ALS on X 1024^3 FP32 = rank-32 CP + 1e-2 noise, R 32, split-BF16 MTTKRPs, FP64 solves",
+            "metric": "ms per steady-state sweep", "value": res[True][0], "unit": "ms", "higher_is_better": False,
+            "dimension_tree": {"ms_per_sweep": res[True][0], "final_fit": res[True][1], "status": res[True][2]},
+            "three_mttkrps": {"ms_per_sweep": res[False][0], "final_fit": res[False][1], "status": res[False][2]},
+            "speedup": res[False][0] / res[True][0], "clocks_region": "cpals"}
+
+
+def _standalone(measure, *a, **kw):
+    """Run one per-configuration measurement alone and print its record as a JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    clk = ClockSampler(0)
+    clk.start()
+    rec = measure(clk, *a, **kw)
+    clk.stop()
+    _fill_clocks(clk, rec)
+    rec["n_gpus"] = 1
+    rec["data"] = "synthetic"
+    print(json.dumps(rec))
     return 0
+
+
+def _fill_clocks(clk, rec):
+    if "clocks_region" in rec:
+        rec["clocks"] = clk.region_stats(rec.pop("clocks_region"))
+
+
+def run_batched(args):
+    return _standalone(measure_c3_batched, _peaks()[0], n=args.instances, reps=args.steps)
+
+
+def run_ttmc(args):
+    return _standalone(measure_c2b_ttmc, _peaks()[0], reps=args.steps)
+
+
+def run_cpals(args):
+    return _standalone(measure_cpals_sweep, sweeps=max(4, args.steps))
 
 
 def run_reference(args):
@@ -681,6 +887,8 @@ def main():
     ap.add_argument("--prec", default="split_bf16", choices=["split_bf16", "plain"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="only the benchmark configuration (skip the per-configuration records)")
     ap.add_argument("--once", action="store_true",
                     help="profiling driver: one execute per mode of --modes at extent --n, no timing")
     ap.add_argument("--n", type=int, default=N_EXT, help="extent of each mode (--once only)")
@@ -765,7 +973,6 @@ def main():
     clocks.mark_stop()
     if dist:
         dist.barrier()
-    clk = clocks.stop()
     launches = dz.kernel_launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
     kern_ms, kern_n = 0.0, 0
@@ -787,12 +994,18 @@ def main():
     if rank == 0:
         errs = []
         for mode in MODES:
-            rows = inputs.sample_rows(seed, N_EXT, 8, tag=mode)
+            rows = inputs.sample_rows(seed, N_EXT, 64, tag=mode)
             slabs = np.stack([inputs.uniform_slab(seed, dims, mode, int(r)).ravel() for r in rows])
             ref = oracle.mttkrp_rows(dims, mode, slabs, Us)
             got = outs[mode][torch.from_numpy(rows).cuda()].cpu().numpy()
             errs.append(oracle.rel_error(got, ref))
         rel_err = max(errs)
+
+    peak, peak_kind = _peaks()
+    workloads = {}
+    run_wl = rank == 0 and world == 1 and not args.no_workloads
+    if run_wl:   # the plain FP32 arm of this configuration, while X is resident
+        workloads["c1_mttkrp_1024cubed_plain_fp32"] = measure_c1_plain(clocks, X, Ud, Us, seed, peak)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -837,18 +1050,35 @@ def main():
         e2e = {"value": world * bytes_step * args.steps / (ems * 1e-3) / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ems / args.steps}
 
+    if run_wl:   # every other configuration, each with its own timed region and clock record
+        for key, fn, kw in (("c0_mttkrp_64cubed_fp64", measure_c0_fp64, {}),
+                            ("c2a_mttkrp_64pow5_r24_modes_0_2", measure_c2a_order5, {"peak": peak}),
+                            ("c2b_ttmc_256pow4_r32", measure_c2b_ttmc, {"peak": peak}),
+                            ("c3_batched_512_instances", measure_c3_batched, {"peak": peak}),
+                            ("c4_cpals_serving", measure_c4_serving, {}),
+                            ("cpals_sweep_1024cubed_r32", measure_cpals_sweep, {})):
+            try:
+                workloads[key] = fn(clocks, **kw)
+            except Exception as exc:   # report, never hide, a failed measurement
+                workloads[key] = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gbs, sec, rows, cores = cpu_oracle_sample(seed, 15.0)
+        gbs1, sec1, rows1, _ = cpu_oracle_sample(seed + 1, 8.0, threads=1)
         cpu = {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
                "sample": f"FP64 oracle on {rows} sampled output rows over modes 0,1,2 of the same "
-                         f"workload ({sec:.1f} s); GB/s of X covered"}
+                         f"workload ({sec:.1f} s); GB/s of X covered",
+               "single_core": {"value": gbs1, "unit": "GB/s", "cores": 1,
+                               "sample": f"{rows1} sampled output rows ({sec1:.1f} s)"}}
 
+    clk = clocks.stop()
+    for rec in workloads.values():
+        _fill_clocks(clocks, rec)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
-    peak, peak_kind = _peaks()
     kern_avg_ms = kern_ms / max(1, kern_n)
     achieved = _alg_bytes_one_mode() / (kern_avg_ms * 1e-3) / 1e9 if kern_n else None
     traffic = _traffic_per_launch(args.prec)
@@ -869,6 +1099,8 @@ def main():
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
         "device_status": status,
     }
+    if workloads:
+        line["workloads"] = workloads
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

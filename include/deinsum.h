@@ -104,6 +104,12 @@ typedef struct {
     int64_t view_groups;      /* leading indices (or packed outer indices) per 128-row tile */
     int view_aligned_rows;    /* rows are 16-byte aligned when X is: one tensor map */
     int view_row_classes;     /* otherwise the four row-class maps serve them (split-BF16 F32) */
+    /* MTTKRP: the I/O lower bound of Sec. IV-E (deinsum_mttkrp_io_bound) for the row view
+       (P, I_n, Q), an order-3 MTTKRP, with S = one SM's shared plus tensor memory in FP32
+       words; zero for TTMc */
+    double io_fast_mem_words; /* S */
+    double io_rho;            /* S^(2/3) / 3 */
+    double io_bound_bytes;    /* 4 x |X| R / min(rho, R): the least HBM traffic of the X stream */
 } deinsum_plan_info_t;
 
 /*
@@ -171,6 +177,37 @@ deinsum_status deinsum_plan_bind_workspace(deinsum_plan_t plan, void *workspace,
 
 /* Fill *info with the plan summary.  Host only. */
 deinsum_status deinsum_plan_info(deinsum_plan_t plan, deinsum_plan_info_t *info);
+
+/*
+ * deinsum_mttkrp_io_bound -- the tight MTTKRP I/O lower bound and its tiling (Sec. IV-E).
+ *
+ * For u[i, l] = sum_{j,k} T[i, j, k] v[j, l] w[k, l] and a fast memory of S elements,
+ * a set of X multiply-adds that touches I, J, K, L distinct values of i, j, k, l needs
+ * I J K + J L + K L + I L <= X elements of T, v, w and u in fast memory.  The tiles that
+ * maximise I J K L under that constraint are I = J = K = (2X/5)^(1/3) and
+ * L = X^(2/3) / (2^(1/3) 5^(2/3)); the computation size that maximises the I/O cost (the
+ * least intensity I J K L / (X - S)) is X0 = 5S/2, which gives
+ *     I = J = K = S^(1/3),  L = S^(2/3) / 2,  rho = S^(2/3) / 3,
+ * and any schedule moves at least Q >= |V| / rho elements, |V| = N_i N_j N_k N_l.  The paper
+ * prints the constraint without the output term I L; its tiles and X0 satisfy the constraint
+ * with that term (and use only 4/5 of X without it), which is the reading taken here.
+ * When the rank R (the extent of l) is below L, the rank is not tiled and one element of T
+ * takes part in at most R multiply-adds: the intensity is min(rho, R) and the bound
+ * |V| / min(rho, R), i.e. for R <= rho reading T once.  Any order-N MTTKRP is this form on
+ * its row view (j over the modes before n, i = i_n, k over the modes after n).
+ *   S        fast-memory elements (> 0).
+ *   t_elems  elements of T (|V| = t_elems x R).
+ *   R        the rank (>= 1).
+ * Host only.  DEINSUM_ERR_INVALID for a NULL `out` or non-positive arguments.
+ */
+typedef struct {
+    double X0;          /* 5S/2 */
+    double I, J, K, L;  /* S^(1/3), S^(1/3), S^(1/3), S^(2/3)/2 */
+    double rho;         /* S^(2/3)/3 */
+    double rho_rank;    /* min(rho, R) */
+    double q_min;       /* t_elems x R / rho_rank elements */
+} deinsum_io_bound_t;
+deinsum_status deinsum_mttkrp_io_bound(double S, double t_elems, int64_t R, deinsum_io_bound_t *out);
 
 /* Device-side status of the plan's executes since the workspace was attached or
  * since the previous call: DEINSUM_OK, or DEINSUM_ERR_TIMEOUT when a bounded

@@ -65,6 +65,8 @@ def _load():
         lib.oracle_ttmc_rows.restype = ctypes.c_int
         lib.oracle_frobenius.argtypes = [_dp, ctypes.c_int64]
         lib.oracle_frobenius.restype = ctypes.c_double
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -168,6 +170,11 @@ def ttmc_rows(dims, keep: int, slabs, factors) -> np.ndarray:
     return out
 
 
+def set_threads(n: int = 0) -> int:
+    """Host threads of the oracle's OpenMP loops (0: leave unchanged); returns the count in force."""
+    return int(_load().oracle_set_threads(int(n)))
+
+
 def frobenius(a) -> float:
     """Frobenius norm sqrt(sum a^2) of an array of any shape (oracle_frobenius, long double sum)."""
     a = _f64(a).ravel()
@@ -257,8 +264,8 @@ def cpals_step(X, factors, lam, mode: int, perturb=None):
     solves U_mode V = MTTKRP_mode(X) (V symmetric positive definite, by
     Cholesky), then normalises every column to unit 2-norm, the norms
     becoming lambda (a zero column keeps lambda = 0).
-    ``perturb(M, mode)``, if given, replaces the MTTKRP result before the solve
-    (the tests use it to measure how errors in M propagate through a sweep).
+    ``perturb(M, mode, factors)``, if given, replaces the MTTKRP result before the
+    solve (the tests use it to measure how errors in M propagate through a sweep).
     Returns the new factor list, lambda and the MTTKRP result used.
     """
     X = _f64(X)
@@ -270,7 +277,7 @@ def cpals_step(X, factors, lam, mode: int, perturb=None):
             V = V * (factors[m].T @ factors[m])
     Mn = mttkrp(X, factors, mode)
     if perturb is not None:
-        Mn = perturb(Mn, mode)
+        Mn = perturb(Mn, mode, factors)
     L = np.linalg.cholesky(V)
     Y = np.linalg.solve(L, Mn.T)
     Un = np.linalg.solve(L.T, Y).T

@@ -22,6 +22,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORACLE_MAX_ORDER 8
 
@@ -271,4 +274,17 @@ double oracle_frobenius(const double *a, int64_t n)
     long double s = 0.0L;
     for (int64_t i = 0; i < n; ++i) s += (long double)a[i] * (long double)a[i];
     return (double)__builtin_sqrtl(s);
+}
+
+/* Threads of the OpenMP loops above (for timing the oracle on a given number of
+ * host cores); returns the number now in force (1 without OpenMP). */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -22,7 +22,7 @@ import threading
 __all__ = ["DeinsumError", "Plan", "mttkrp", "ttmc", "mttkrp_einsum", "ttmc_einsum", "mttkrp_mm",
            "mttkrp_mm_einsum",
            "gen_uniform", "gen_cp", "kernel_launch_count", "alloc_count", "set_wait_limit_ns",
-           "mttkrp_noalloc", "mttkrp_noalloc_status", "library_path", "load",
+           "mttkrp_noalloc", "mttkrp_noalloc_status", "mttkrp_io_bound", "library_path", "load",
            "Grid", "redist_dim_partitions", "redist_match", "redist_plan"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -52,7 +52,15 @@ class _PlanInfo(ctypes.Structure):
                 ("out_elems", ctypes.c_int64), ("alg_bytes", ctypes.c_double),
                 ("alg_flops", ctypes.c_double), ("n_units", ctypes.c_int64), ("mm_cols", ctypes.c_int64),
                 ("view_merged", ctypes.c_int), ("view_packed", ctypes.c_int), ("view_groups", ctypes.c_int64),
-                ("view_aligned_rows", ctypes.c_int), ("view_row_classes", ctypes.c_int)]
+                ("view_aligned_rows", ctypes.c_int), ("view_row_classes", ctypes.c_int),
+                ("io_fast_mem_words", ctypes.c_double), ("io_rho", ctypes.c_double),
+                ("io_bound_bytes", ctypes.c_double)]
+
+
+class _IoBound(ctypes.Structure):
+    _fields_ = [("X0", ctypes.c_double), ("I", ctypes.c_double), ("J", ctypes.c_double), ("K", ctypes.c_double),
+                ("L", ctypes.c_double), ("rho", ctypes.c_double), ("rho_rank", ctypes.c_double),
+                ("q_min", ctypes.c_double)]
 
 
 class _Request(ctypes.Structure):
@@ -159,6 +167,8 @@ def load():
         lib.deinsum_set_wait_limit_ns.restype = None
         lib.deinsum_alloc_count.argtypes = []
         lib.deinsum_alloc_count.restype = i64
+        lib.deinsum_mttkrp_io_bound.argtypes = [ctypes.c_double, ctypes.c_double, i64, ctypes.POINTER(_IoBound)]
+        lib.deinsum_mttkrp_io_bound.restype = i32
         lib.deinsum_gen_uniform_f32.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, vp, vp]
         lib.deinsum_gen_uniform_f32.restype = i32
         lib.deinsum_gen_uniform_f64.argtypes = [ctypes.c_uint64, ctypes.c_uint64, i64, vp, vp]
@@ -235,7 +245,9 @@ class Plan:
                 "n_units": info.n_units, "mm_cols": info.mm_cols,
                 "view": {"merged": bool(info.view_merged), "packed": bool(info.view_packed),
                          "groups": info.view_groups, "aligned_rows": bool(info.view_aligned_rows),
-                         "row_classes": bool(info.view_row_classes)}}
+                         "row_classes": bool(info.view_row_classes)},
+                "io": {"fast_mem_words": info.io_fast_mem_words, "rho": info.io_rho,
+                       "bound_bytes": info.io_bound_bytes}}
 
     def workspace_size(self) -> int:
         n = ctypes.c_size_t()
@@ -578,6 +590,14 @@ def gen_cp(seed: int, dims, cp_factors, sigma: float, device="cuda", stream=None
     _check(load().deinsum_gen_cp_f32(seed, order, d, rank, fp, float(sigma), _dev_ptr(t, "out"),
                                      _stream_ptr(stream)), "deinsum_gen_cp_f32")
     return t
+
+
+def mttkrp_io_bound(S: float, t_elems: float, R: int) -> dict:
+    """The Sec. IV-E MTTKRP I/O lower bound and tiling (``deinsum_mttkrp_io_bound``)."""
+    b = _IoBound()
+    _check(load().deinsum_mttkrp_io_bound(float(S), float(t_elems), int(R), ctypes.byref(b)),
+           "deinsum_mttkrp_io_bound")
+    return {f: getattr(b, f) for f, _ in _IoBound._fields_}
 
 
 def mttkrp_noalloc_status() -> int:

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -1092,6 +1093,17 @@ deinsum_status deinsum_plan_info(deinsum_plan_t pl, deinsum_plan_info_t *info) {
         info->view_aligned_rows = g.vec_ok;
         info->view_row_classes = (pl->prec == DEINSUM_PREC_SPLIT_BF16 && pl->dtype == DEINSUM_F32 && !g.vec_ok &&
                                   rowclass_supported(g)) ? 1 : 0;
+        // one SM's fast memory: the largest dynamic shared memory of a CTA (227 KB) plus the
+        // tensor memory (256 KB), in FP32 words
+        const double S = (232448.0 + 262144.0) / 4.0;
+        double x_elems = 1.0;
+        for (int m = 0; m < pl->order; ++m) x_elems *= double(pl->dims[m]);
+        deinsum_io_bound_t b;
+        if (deinsum_mttkrp_io_bound(S, x_elems, pl->ranks[(pl->mode + 1) % pl->order], &b) == DEINSUM_OK) {
+            info->io_fast_mem_words = S;
+            info->io_rho = b.rho;
+            info->io_bound_bytes = 4.0 * b.q_min * (pl->dtype == DEINSUM_F64 ? 2.0 : 1.0);
+        }
     }
     return DEINSUM_OK;
 }
@@ -1104,6 +1116,18 @@ deinsum_status deinsum_last_device_status(deinsum_plan_t pl) {
         return DEINSUM_ERR_CUDA;
     if (v != 0 && cudaMemset(pl->d_status, 0, sizeof(int)) != cudaSuccess) return DEINSUM_ERR_CUDA;
     return v == 0 ? DEINSUM_OK : DEINSUM_ERR_TIMEOUT;
+}
+
+deinsum_status deinsum_mttkrp_io_bound(double S, double t_elems, int64_t R, deinsum_io_bound_t *out) {
+    if (!out || !(S > 0.0) || !(t_elems > 0.0) || R < 1) return DEINSUM_ERR_INVALID;
+    const double s13 = std::cbrt(S);
+    out->X0 = 2.5 * S;
+    out->I = out->J = out->K = s13;
+    out->L = s13 * s13 / 2.0;
+    out->rho = s13 * s13 / 3.0;
+    out->rho_rank = out->rho < double(R) ? out->rho : double(R);
+    out->q_min = t_elems * double(R) / out->rho_rank;
+    return DEINSUM_OK;
 }
 
 void deinsum_set_wait_limit_ns(uint64_t ns) { g_wait_limit_ns.store(ns, std::memory_order_relaxed); }

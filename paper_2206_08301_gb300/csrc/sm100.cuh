@@ -51,11 +51,43 @@ constexpr int kStatusTimeout = 1;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 constexpr uint64_t kDrainLimitNs = 2000000000ull;
 
+// try_wait with an explicit suspend-time hint (ns): the thread is suspended at most about
+// that long before the test returns false.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Limits below this take the short-wait loop (every poll suspends at most the limit, and the
+// clock is read after every poll), so that a limit of a few ns really ends a wait that a
+// single hardware-suspended poll would otherwise have outlasted.
+constexpr uint64_t kShortWaitNs = 1000000ull;
+
 // Wait for the phase of parity `parity` to complete, for at most `limit_ns`.
 // On time-out (or when another role already gave up, *abort != 0) it records
 // a failure in the device status word, raises *abort and returns false.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
                                           uint64_t limit_ns) {
+    if (limit_ns < kShortWaitNs) {   // uniform: a kernel argument
+        const uint32_t hint = uint32_t(limit_ns > 0 ? limit_ns : 1);
+        const uint64_t t0 = globaltimer_ns();
+        while (true) {
+            if (mbar_try_wait_hint(bar, parity, hint)) return true;
+            if (*abort) return false;
+            if (globaltimer_ns() - t0 > limit_ns) {
+                atomicOr(status, kStatusTimeout);
+                *abort = 1;
+                return false;
+            }
+        }
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     while (true) {

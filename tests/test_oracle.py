@@ -347,11 +347,11 @@ def test_cpals_perturbation_hook_is_neutral_and_linear():
     X = np.einsum("ir,jr,kr->ijk", *A) + 1e-2 * rng.standard_normal(dims)
     init = [a + 0.3 * rng.standard_normal(a.shape) for a in A]
     f0, l0, fit0 = oracle.cpals(X, init, 2)
-    f1, l1, fit1 = oracle.cpals(X, init, 2, perturb=lambda M, m: M)
+    f1, l1, fit1 = oracle.cpals(X, init, 2, perturb=lambda M, m, f: M)
     for a, b in zip(f0, f1):
         assert np.array_equal(a, b)
     assert np.array_equal(l0, l1) and fit0 == fit1
-    f2, l2, fit2 = oracle.cpals(X, init, 2, perturb=lambda M, m: M * (1.0 + 1e-7))
+    f2, l2, fit2 = oracle.cpals(X, init, 2, perturb=lambda M, m, f: M * (1.0 + 1e-7))
     # a uniform scale of M scales the unnormalised update, which the normalisation removes
     # from the factors and moves into lambda
     for a, b in zip(f0, f2):
