@@ -304,17 +304,18 @@ __device__ __forceinline__ void conv_read_rowcls(const MttkrpGeom &g, const void
             for (int j = 0; j < 8; ++j) v[j] = lds_words(r + JS * j, 3);
             break;
     }
-    const bool rows_full = g.narrow ? (g.G * g.I == BM && rowbase + BM <= g.P * g.I) : col * BM + BM <= g.I;
-    if (rows_full && k0 + BK <= g.K_in) return;
-    const int64_t kpos = k0 + 4 * k4;
+    // Values a box brings in beyond the tile's own elements need no mask here.  Past K_in
+    // (the last chunk of a fiber group) they are the same row's next outer index, or zero
+    // past the row's end (out of the class map), and the split factor tile is zero for
+    // k >= K_in.  Past the tile's rows in a wide tile they are rows of the next leading index
+    // (or zero past the tensor), which reach only TMEM lanes and partial rows that the
+    // reduction never reads.  Narrow tiles do read every group's rows, so rows of leading
+    // indices past P are cleared.  (X is assumed finite: a non-finite value times a zero
+    // factor row would be NaN.)
+    if (!g.narrow || rowbase + BM <= g.P * g.I) return;
     #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const bool rv = row_valid(g, col, rowbase, rsub + 16 * j);
-        v[j].x = (rv && kpos < g.K_in) ? v[j].x : 0.f;
-        v[j].y = (rv && kpos + 1 < g.K_in) ? v[j].y : 0.f;
-        v[j].z = (rv && kpos + 2 < g.K_in) ? v[j].z : 0.f;
-        v[j].w = (rv && kpos + 3 < g.K_in) ? v[j].w : 0.f;
-    }
+    for (int j = 0; j < 8; ++j)
+        if (!row_valid(g, col, rowbase, rsub + 16 * j)) v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Case 1 from the four class boxes, in the thread layout of conv_read_smem_mn128 (k line
@@ -353,16 +354,10 @@ __device__ __forceinline__ void conv_read_rowcls_mn(const MttkrpGeom &g, const v
             }
         }
     }
-    if (k0 + BK <= g.K_in && col * BM + BM <= g.I) return;
-    const int64_t m0 = col * BM + 4 * lane;
-    #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const bool kv = k0 + 8 * w + j < g.K_in;
-        v[j].x = (kv && m0 < g.I) ? v[j].x : 0.f;
-        v[j].y = (kv && m0 + 1 < g.I) ? v[j].y : 0.f;
-        v[j].z = (kv && m0 + 2 < g.I) ? v[j].z : 0.f;
-        v[j].w = (kv && m0 + 3 < g.I) ? v[j].w : 0.f;
-    }
+    // No masks (as in conv_read_rowcls for wide tiles): lines past K_in belong to the next
+    // outer index and meet the zero rows of the split factor tile; rows past I are zero past
+    // the end of a line (out of the class map) and otherwise reach only TMEM lanes that the
+    // reduction never reads.
 }
 
 // One chunk through the row-class maps (one thread): the four boxes into raw stage `dst`.
@@ -493,8 +488,12 @@ __device__ __forceinline__ void load_fg_weights(const MttkrpArgs &a, int64_t til
 // PW: per-row weights (packed outer indices, or narrow tiles of several p with L rows).
 // RC: X through the four row-class tensor maps (rows not 16-byte aligned); otherwise through
 // the tensor map when a.use_tma, else per-thread loads.
+// Registers: 448 threads may hold up to 144 each (14 warps x 144 x 32 = 64,512 of 65,536).
+// The rank-64 instances with per-row weights (64 accumulators and a float4 weight row per
+// thread in the epilogue) spill 150-178 bytes at 128 and at most 40 at 144; the others run
+// without spills at 128 (given 144, ptxas spent it and spilled 16 bytes).
 template <int RP, bool OP, bool MN, bool PW, bool RC>
-__global__ void __launch_bounds__(TcCfg<RP>::THREADS, 1)
+__global__ void __maxnreg__(RP == 64 && PW ? 144 : 128)
 mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     static_assert(!OP || PW, "packed outer indices weight every row group");
     static_assert(!(OP && RC), "row classes are not used with packed outer indices");
@@ -964,7 +963,7 @@ constexpr int RPB = 64;  // the batched kernel is shaped for the largest padded 
 // layout MNB (MN-major A for last modes): one unit list per kind, because the code of
 // several kinds in one kernel slows each of them (instruction fetch).
 template <bool RCB, bool MNB>
-__global__ void __launch_bounds__(TcCfg<RPB>::THREADS, 1)
+__global__ void __maxnreg__(144)   // shaped for rank 64: see mttkrp_tc_kernel
 mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     using C = TcCfg<RPB>;
     constexpr int RS = C::RS, AS = C::AS;

@@ -65,35 +65,25 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity
     return ok != 0;
 }
 
-// Limits below this take the short-wait loop (every poll suspends at most the limit, and the
-// clock is read after every poll), so that a limit of a few ns really ends a wait that a
-// single hardware-suspended poll would otherwise have outlasted.
-constexpr uint64_t kShortWaitNs = 1000000ull;
+
+// Suspend-time hint of a poll for a wait limit: 10 ms normally, the limit itself when it is
+// shorter (a test limit of a few ns must not be outlasted by one hardware-suspended poll).
+__device__ __forceinline__ uint32_t wait_hint_ns(uint64_t limit_ns) {
+    return limit_ns >= 10000000ull ? 10000000u : (limit_ns > 0 ? uint32_t(limit_ns) : 1u);
+}
 
 // Wait for the phase of parity `parity` to complete, for at most `limit_ns`.
 // On time-out (or when another role already gave up, *abort != 0) it records
 // a failure in the device status word, raises *abort and returns false.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
                                           uint64_t limit_ns) {
-    if (limit_ns < kShortWaitNs) {   // uniform: a kernel argument
-        const uint32_t hint = uint32_t(limit_ns > 0 ? limit_ns : 1);
-        const uint64_t t0 = globaltimer_ns();
-        while (true) {
-            if (mbar_try_wait_hint(bar, parity, hint)) return true;
-            if (*abort) return false;
-            if (globaltimer_ns() - t0 > limit_ns) {
-                atomicOr(status, kStatusTimeout);
-                *abort = 1;
-                return false;
-            }
-        }
-    }
-    if (mbar_try_wait(bar, parity)) return true;
+    const uint32_t hint = wait_hint_ns(limit_ns);
+    if (mbar_try_wait_hint(bar, parity, hint)) return true;
     const uint64_t t0 = globaltimer_ns();
     while (true) {
         #pragma unroll 1
         for (int i = 0; i < 32; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
+            if (mbar_try_wait_hint(bar, parity, hint)) return true;
         if (*abort) return false;
         if (globaltimer_ns() - t0 > limit_ns) {
             atomicOr(status, kStatusTimeout);

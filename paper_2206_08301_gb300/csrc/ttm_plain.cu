@@ -3,9 +3,12 @@
 // used one mode at a time for the TTMc chain (the binary decomposition of
 // Sec. II-A).  Each TTM runs as a strided product C[m, n] = sum_k A(m,k) B(k,n)
 // with m the long dimension (a when B == 1, else b within one a), n = r, on a
-// 128 x 32 register-tiled CUDA-core kernel (FP32 or FP64 FMA).
+// 128 x 32 register-tiled CUDA-core kernel (FP32 or FP64 FMA); FP32 TTMs over a
+// middle mode with a trailing extent B >= 64, a multiple of 4, take the
+// 256 x 32 kernel with 16-byte loads below.
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 
 #include "internal.h"
@@ -77,8 +80,111 @@ ttm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ C, 
         }
 }
 
+// FP32 TTM over a middle mode with a contiguous trailing extent B (a multiple of 4, X and Y
+// 16-byte aligned): Y[a, r, b] = sum_i X[a, i, b] U[i, r].  A CTA takes one a, 256 b and 32 r;
+// thread (bg = lane, rg = warp) accumulates b = b0 + 4 bg .. + 3 and b0 + 128 + 4 bg .. + 3
+// for r = r0 + 4 rg .. + 3 (32 FMA per three 16-byte shared loads; the U value is a warp
+// broadcast).  Chunks of 16 i are read with 16-byte loads into registers one chunk ahead and
+// stored into the other of two shared-memory buffers.
+constexpr int SB = 256, SR = 32, SK = 16, STHREADS = 256;
+
+__global__ void __launch_bounds__(STHREADS)
+ttm_strided_f32_kernel(const float *__restrict__ X, const float *__restrict__ U, float *__restrict__ Y,
+                       int64_t I, int64_t B, int64_t R) {
+    __shared__ float4 xs[2][SK][SB / 4];
+    __shared__ float4 us[2][SK][SR / 4];
+    const int64_t nbt = (B + SB - 1) / SB, nrt = (R + SR - 1) / SR;
+    const int64_t bid = blockIdx.x;
+    const int64_t rt = bid % nrt;
+    const int64_t bt = (bid / nrt) % nbt;
+    const int64_t a = bid / (nrt * nbt);
+    const int64_t b0 = bt * SB, r0 = rt * SR;
+    const int t = threadIdx.x, bg = t & 31, rg = t >> 5;
+    const float *Xa = X + a * I * B;
+    // this thread's loads of a chunk: X rows k = (t >> 6) + 4 q (q < 4), float4 column t & 63;
+    // U row k = t >> 3 (t < 128), columns r0 + 4 (t & 7) .. + 3
+    const int xc = t & 63, xk = t >> 6;
+    const bool xcol_ok = b0 + 4 * xc < B;
+    const int uk = t >> 3, uc = t & 7;
+    float4 px[4], pu;
+    auto fetch = [&](int64_t i0) {
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t i = i0 + xk + 4 * q;
+            px[q] = (xcol_ok && i < I) ? *reinterpret_cast<const float4 *>(Xa + i * B + b0 + 4 * xc)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (t < 128) {
+            const int64_t i = i0 + uk;
+            float e[4];
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t r = r0 + 4 * uc + q;
+                e[q] = (i < I && r < R) ? U[i * R + r] : 0.f;
+            }
+            pu = make_float4(e[0], e[1], e[2], e[3]);
+        }
+    };
+    auto stash = [&](int buf) {
+        #pragma unroll
+        for (int q = 0; q < 4; ++q) xs[buf][xk + 4 * q][xc] = px[q];
+        if (t < 128) us[buf][uk][uc] = pu;
+    };
+    float acc[4][8];
+    #pragma unroll
+    for (int j = 0; j < 4; ++j)
+        #pragma unroll
+        for (int q = 0; q < 8; ++q) acc[j][q] = 0.f;
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t i0 = 0; i0 < I; i0 += SK) {
+        const bool more = i0 + SK < I;
+        if (more) fetch(i0 + SK);
+        #pragma unroll
+        for (int k = 0; k < SK; ++k) {
+            const float4 x0 = xs[buf][k][bg], x1 = xs[buf][k][32 + bg];
+            const float4 u = us[buf][k][rg];
+            const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            const float uv[4] = {u.x, u.y, u.z, u.w};
+            #pragma unroll
+            for (int j = 0; j < 4; ++j)
+                #pragma unroll
+                for (int q = 0; q < 8; ++q) acc[j][q] = fmaf(uv[j], xv[q], acc[j][q]);
+        }
+        if (more) {
+            stash(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t r = r0 + 4 * rg + j;
+        if (r >= R) continue;
+        float *yr = Y + (a * R + r) * B + b0;
+        if (b0 + 4 * bg < B)
+            *reinterpret_cast<float4 *>(yr + 4 * bg) = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+        if (b0 + 128 + 4 * bg < B)
+            *reinterpret_cast<float4 *>(yr + 128 + 4 * bg) = make_float4(acc[j][4], acc[j][5], acc[j][6], acc[j][7]);
+    }
+}
+
 template <typename T>
 int launch_ttm(const T *X, const T *U, T *Y, int64_t Aext, int64_t Im, int64_t Bext, int64_t Rm, void *stream) {
+    if constexpr (sizeof(T) == 4) {
+        if (Bext >= 64 && Bext % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+            (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
+            const int64_t blocks = Aext * ((Bext + SB - 1) / SB) * ((Rm + SR - 1) / SR);
+            if (blocks < 1 || blocks > 0x7FFFFFFFll) return int(cudaErrorInvalidValue);
+            ttm_strided_f32_kernel<<<unsigned(blocks), STHREADS, 0, static_cast<cudaStream_t>(stream)>>>(
+                reinterpret_cast<const float *>(X), reinterpret_cast<const float *>(U), reinterpret_cast<float *>(Y),
+                Im, Bext, Rm);
+            count_launch();
+            return int(cudaGetLastError());
+        }
+    }
     Strides s{};
     if (Bext == 1) {
         s.M = Aext; s.N = Rm; s.K = Im; s.batch = 1;
