@@ -488,12 +488,12 @@ __device__ __forceinline__ void load_fg_weights(const MttkrpArgs &a, int64_t til
 // PW: per-row weights (packed outer indices, or narrow tiles of several p with L rows).
 // RC: X through the four row-class tensor maps (rows not 16-byte aligned); otherwise through
 // the tensor map when a.use_tma, else per-thread loads.
-// Registers: 448 threads may hold up to 144 each (14 warps x 144 x 32 = 64,512 of 65,536).
-// The rank-64 instances with per-row weights (64 accumulators and a float4 weight row per
-// thread in the epilogue) spill 150-178 bytes at 128 and at most 40 at 144; the others run
-// without spills at 128 (given 144, ptxas spent it and spilled 16 bytes).
+// Registers: 128 per thread at most.  The launch check counts a block's warps rounded up
+// to a multiple of four (14 -> 16), and 16 x 32 x 128 is the SM's 65,536; a 144-register
+// build of this 448-thread kernel fails to launch.  The rank-64 instances with per-row
+// weights (64 accumulators and a float4 weight row per thread in the epilogue) spill there.
 template <int RP, bool OP, bool MN, bool PW, bool RC>
-__global__ void __maxnreg__(RP == 64 && PW ? 144 : 128)
+__global__ void __maxnreg__(128)
 mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     static_assert(!OP || PW, "packed outer indices weight every row group");
     static_assert(!(OP && RC), "row classes are not used with packed outer indices");
@@ -963,7 +963,7 @@ constexpr int RPB = 64;  // the batched kernel is shaped for the largest padded 
 // layout MNB (MN-major A for last modes): one unit list per kind, because the code of
 // several kinds in one kernel slows each of them (instruction fetch).
 template <bool RCB, bool MNB>
-__global__ void __maxnreg__(144)   // shaped for rank 64: see mttkrp_tc_kernel
+__global__ void __maxnreg__(128)   // the launch limit of 448 threads: see mttkrp_tc_kernel
 mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     using C = TcCfg<RPB>;
     constexpr int RS = C::RS, AS = C::AS;

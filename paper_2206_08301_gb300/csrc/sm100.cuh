@@ -66,18 +66,42 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity
 }
 
 
-// Suspend-time hint of a poll for a wait limit: 10 ms normally, the limit itself when it is
-// shorter (a test limit of a few ns must not be outlasted by one hardware-suspended poll).
-__device__ __forceinline__ uint32_t wait_hint_ns(uint64_t limit_ns) {
-    return limit_ns >= 10000000ull ? 10000000u : (limit_ns > 0 ? uint32_t(limit_ns) : 1u);
+// Non-blocking test of a phase (never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
+
+// Limits below this are a test regime (deinsum_set_wait_limit_ns): polls that never
+// suspend, with the clock read after each one.  A suspending try_wait may sleep until the
+// phase completes whatever its hint says, which would outlast a limit of a few ns.
+constexpr uint64_t kShortWaitNs = 1000000ull;
 
 // Wait for the phase of parity `parity` to complete, for at most `limit_ns`.
 // On time-out (or when another role already gave up, *abort != 0) it records
 // a failure in the device status word, raises *abort and returns false.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
                                           uint64_t limit_ns) {
-    const uint32_t hint = wait_hint_ns(limit_ns);
+    if (limit_ns < kShortWaitNs) {
+        const uint64_t t0 = globaltimer_ns();
+        while (true) {
+            if (mbar_test_wait(bar, parity)) return true;
+            if (*abort) return false;
+            if (globaltimer_ns() - t0 > limit_ns) {
+                atomicOr(status, kStatusTimeout);
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+    constexpr uint32_t hint = 10000000u;   // suspend-time hint of one poll: 10 ms
     if (mbar_try_wait_hint(bar, parity, hint)) return true;
     const uint64_t t0 = globaltimer_ns();
     while (true) {
