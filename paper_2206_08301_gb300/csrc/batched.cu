@@ -1,15 +1,18 @@
-// Batched MTTKRP: many instances of uneven extents and ranks in up to three
-// persistent tensor-core launches, replayed from a captured CUDA graph: one over
-// the instances whose rows are 16-byte aligned (tensor map), one per operand
-// layout over the others (row-class tensor maps).  Code for several kinds in one
-// kernel slowed all of them (instruction fetch), hence a launch per kind.
+// Batched MTTKRP: many instances of uneven extents and ranks in one persistent
+// tensor-core launch, replayed from a captured CUDA graph.  Instances whose rows
+// are 16-byte aligned load X through a tensor map, the others through four
+// row-class tensor maps; the kernel runs each unit in code specialised for its
+// instance's loads and operand layout, read once per unit.
 //
 // Host side: every instance is classified by a regular plan (Sec. III-B MTTKRP
 // einsum); its row view is cut into work units (column of 128 output rows x a
-// range of fiber groups) of about `unit_bytes` of X each; the units of each kind
-// are assigned to the CTAs of its launch largest first (LPT: each unit goes to
-// the least-loaded CTA), so that one CTA per SM finishes them together.  The granularity is picked by an autotuner that times candidate
-// schedules on the device and remembers the winner per batch signature.
+// range of fiber groups) of about `unit_bytes` of X each; the units are assigned
+// to the CTAs largest first (LPT: each unit goes to the least-loaded CTA, by a
+// cost per unit that counts its chunks and fiber-group epilogues), so that one
+// CTA per SM finishes them together, and each CTA's list is then grouped by
+// kind of instance, so that its warps run one specialised loop at a time.  The
+// granularity is picked by an autotuner that times candidate schedules on the
+// device and remembers the winner per batch signature.
 // Device side: a batched split of the instances' inner factors, the batched
 // tensor-core kernel (mttkrp_tc.cu), and a batched fixed-order reduction of
 // the unit partials into each instance's output.  With plain precision the
@@ -106,7 +109,7 @@ struct Inst {
     int opmode[DEINSUM_MAX_ORDER + 1] = {0};
     MttkrpGeom g{};
     double xbytes = 0.0;
-    int kind = 0;   // 0: tensor map or per-thread loads; 1 / 2: row classes, case 0 / case 1 (own launches)
+    int kind = 0;   // 0: tensor map (or per-thread loads); 1 / 2: row classes, case 0 / case 1
 };
 
 std::mutex g_tune_mutex;
@@ -149,11 +152,10 @@ struct deinsum_batch_s {
     double total_bytes = 0.0;
     std::string signature;
     int unit_div = 4;   // units of about total / (grid * unit_div) bytes
-    int n_sm = 0, grid = 0;          // grid: the largest of the launches
-    int grids[3] = {0, 0, 0};        // CTAs of the launch over each instance kind
+    int n_sm = 0, grid = 0;          // CTAs of the launch (one per SM, at most one per unit)
     // schedule (host)
-    std::vector<int64_t> units;      // 5 per unit, grouped by CTA: kind 0's launch, then kind 1's, then kind 2's
-    std::vector<int64_t> cta_begin;  // grids[k] + 1 per kind, in that order (indices into units)
+    std::vector<int64_t> units;      // 5 per unit, grouped by CTA
+    std::vector<int64_t> cta_begin;  // grid + 1 (indices into units)
     std::vector<int64_t> red_off;    // partial offsets, per instance, column, split
     std::vector<int64_t> red_col;    // per instance: n_cols + 1 starts into red_off
     std::vector<int64_t> red_col_base;
@@ -181,6 +183,14 @@ void destroy_graph(deinsum_batch_s *b) {
         cudaGraphExecDestroy(b->gexec);
         b->gexec = nullptr;
     }
+}
+
+// Relative time of a unit of `fgs` fiber groups: its 64-wide chunks (the converters' and
+// the TMA's work, a quarter more through the row-class maps, whose reads realign the
+// rows) plus one epilogue per fiber group (TMEM columns read, the instance's padded rank).
+double unit_cost(const Inst &in, int64_t fgs) {
+    const double chunk = in.kind ? 1.25 : 1.0;
+    return double(fgs) * (double(in.g.n_kb) * chunk + double(in.g.R_pad) / 128.0);
 }
 
 // Units of about total / (grid * unit_div) bytes of X; LPT assignment to CTAs.
@@ -216,7 +226,7 @@ void build_batch_schedule(deinsum_batch_s *b) {
                 const int64_t off = int64_t(b->partial_floats);
                 b->partial_floats += size_t(BM) * size_t(g.R_pad);
                 b->red_off.push_back(off);
-                all.push_back({i, c, f0, f1, off, double(f1 - f0) * double(g.n_kb)});
+                all.push_back({i, c, f0, f1, off, unit_cost(b->inst[size_t(i)], f1 - f0)});
             }
         }
         b->red_col.push_back(int64_t(b->red_off.size()));
@@ -227,42 +237,39 @@ void build_batch_schedule(deinsum_batch_s *b) {
         b->wtab_bytes += up(wf * 4, 256);
         b->max_wtab_floats = std::max<int64_t>(b->max_wtab_floats, int64_t(wf));
     }
-    // one unit list per instance kind (tensor map or per-thread loads; row classes in case 0;
-    // row classes in case 1), each assigned to its launch's CTAs largest first onto the
-    // least-loaded CTA
+    // all units over the CTAs of one launch, largest first onto the least-loaded CTA, then
+    // each CTA's list grouped by kind of instance (stable: largest first within a kind)
     b->units.clear();
     b->cta_begin.clear();
-    auto assign = [&](int kind) {
-        std::vector<size_t> order;
-        for (size_t k = 0; k < all.size(); ++k)
-            if (b->inst[size_t(all[k].inst)].kind == kind) order.push_back(k);
-        const int grid = int(std::min<int64_t>(b->n_sm, int64_t(order.size())));
-        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return all[x].cost > all[y].cost; });
-        using Load = std::pair<double, int>;
-        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-        for (int c = 0; c < grid; ++c) heap.push({0.0, c});
-        std::vector<std::vector<size_t>> per_cta(static_cast<size_t>(grid));
-        for (size_t k : order) {
-            Load top = heap.top();
-            heap.pop();
-            per_cta[size_t(top.second)].push_back(k);
-            heap.push({top.first + all[k].cost, top.second});
-        }
-        for (int c = 0; c < grid; ++c) {
-            b->cta_begin.push_back(int64_t(b->units.size() / 5));
-            for (size_t k : per_cta[size_t(c)]) {
-                const U &u = all[k];
-                b->units.insert(b->units.end(), {u.inst, u.col, u.f0, u.f1, u.off});
-            }
-        }
-        b->cta_begin.push_back(int64_t(b->units.size() / 5));
-        return grid;
-    };
-    b->grid = 1;
-    for (int k = 0; k < 3; ++k) {
-        b->grids[k] = assign(k);
-        b->grid = std::max(b->grid, b->grids[k]);
+    std::vector<size_t> order(all.size());
+    for (size_t k = 0; k < all.size(); ++k) order[k] = k;
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(b->n_sm, int64_t(all.size()))));
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return all[x].cost > all[y].cost; });
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < grid; ++c) heap.push({0.0, c});
+    std::vector<std::vector<size_t>> per_cta(static_cast<size_t>(grid));
+    for (size_t k : order) {
+        Load top = heap.top();
+        heap.pop();
+        per_cta[size_t(top.second)].push_back(k);
+        heap.push({top.first + all[k].cost, top.second});
     }
+    for (int c = 0; c < grid; ++c) {
+        std::vector<size_t> &lst = per_cta[size_t(c)];
+        auto key = [&](size_t k) {   // kind of load, then operand layout (the kernel's specialised loops)
+            const Inst &in = b->inst[size_t(all[k].inst)];
+            return 2 * in.kind + in.g.kcase;
+        };
+        std::stable_sort(lst.begin(), lst.end(), [&](size_t x, size_t y) { return key(x) < key(y); });
+        b->cta_begin.push_back(int64_t(b->units.size() / 5));
+        for (size_t k : lst) {
+            const U &u = all[k];
+            b->units.insert(b->units.end(), {u.inst, u.col, u.f0, u.f1, u.off});
+        }
+    }
+    b->cta_begin.push_back(int64_t(b->units.size() / 5));
+    b->grid = grid;
 }
 
 deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
@@ -370,14 +377,8 @@ deinsum_status launch_batch(deinsum_batch_s *b, cudaStream_t s) {
     ba.units = reinterpret_cast<const int64_t *>(b->ws + b->o_units);
     ba.partial = reinterpret_cast<float *>(b->ws + b->o_partial);
     ba.status = reinterpret_cast<int *>(b->ws + b->o_status);
-    const int64_t *cta = reinterpret_cast<const int64_t *>(b->ws + b->o_cta);
-    for (int k = 0; k < 3; ++k) {
-        if (b->grids[k] > 0) {
-            ba.cta_begin = cta;
-            if (launch_mttkrp_tc_batched(ba, b->grids[k], k, s)) return DEINSUM_ERR_CUDA;
-        }
-        cta += b->grids[k] + 1;
-    }
+    ba.cta_begin = reinterpret_cast<const int64_t *>(b->ws + b->o_cta);
+    if (launch_mttkrp_tc_batched(ba, b->grid, s)) return DEINSUM_ERR_CUDA;
     int64_t maxo = 1;
     for (auto &i : b->inst) maxo = std::max<int64_t>(maxo, i.g.I * i.g.R);
     int rx = int(std::min<int64_t>(64, (maxo + 255) / 256));

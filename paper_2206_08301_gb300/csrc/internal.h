@@ -106,11 +106,12 @@ struct MttkrpArgs {
     uint64_t wait_ns;                  // limit of a pipeline wait (set by the launcher)
 };
 
-// Many MTTKRP instances in persistent launches of the tensor-core kernel (one per kind):
-// per-instance arguments (geometry, TMA descriptor of X, factor pointers,
-// split factor tiles) live in device memory; every CTA walks its own list of
-// units, each unit = (instance, column, first fiber group, end, offset of its
-// 128 x R_pad partial block in `partial`).
+// Many MTTKRP instances in one persistent launch of the tensor-core kernel: per-instance
+// arguments (geometry, TMA descriptors of X, factor pointers, split factor tiles) live in
+// device memory; every CTA walks its own list of units, each unit = (instance, column,
+// first fiber group, end, offset of its 128 x R_pad partial block in `partial`).  The
+// kernel reads how an instance loads X (tensor map or row classes, the operand layout of
+// its mode) from its arguments, once per unit.
 struct BatchArgs {
     const MttkrpArgs *insts;
     const int64_t *units;       // 5 per unit
@@ -119,10 +120,7 @@ struct BatchArgs {
     int *status;
     uint64_t wait_ns;           // limit of a pipeline wait (set by the launcher)
 };
-// kind 0: every instance of the unit list loads X through its tensor map (use_tma) or per
-// thread; kind 1 / 2: through its row-class maps (row_classes set), all of them case 0 /
-// case 1 (the last mode, MN-major operand).
-int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, int kind, void *stream);
+int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, void *stream);
 size_t mttkrp_tc_batched_smem_bytes();
 
 // Fused last-two-mode stage of a TTMc keeping a mode n < N-2 (ttmc_tc.cu):

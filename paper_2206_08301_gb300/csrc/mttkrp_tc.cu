@@ -2,12 +2,16 @@
 //
 // Same row view and schedule as the plain kernel (internal.h): per fiber
 // group (tile of 128 rows, outer index o) the inner contraction
-//   T[row, n] = sum_k A[row, k] * B[n, k]
-// runs on the tensor cores with
-//   A = [X_hi | X_lo]   (128 rows, split on the fly: hi = bf16(x), lo = bf16(x - hi))
-//   B = [U_hi ; U_lo]   (2 R_pad rows: the inner factor's hi and lo parts)
-// so that T[:, r] + T[:, R_pad + r] = (X_hi + X_lo)(U_hi + U_lo)[:, r]: the four
-// split products with FP32 accumulation in TMEM.  The remaining Khatri-Rao
+//   T[row, r] = sum_k X[row, k] U[k, r]
+// runs on the tensor cores as split products with FP32 accumulation in TMEM,
+// hi = bf16(x), lo = bf16(x - hi), X_hi / X_lo split on the fly into 128-row operand
+// tiles and U_hi / U_lo the two halves (rows 0..R_pad-1, R_pad..2 R_pad-1) of the
+// split factor tile:
+//   single-instance kernel: X_hi [U_hi; U_lo] + X_lo [U_hi; U_lo] (N = 2 R_pad), so that
+//     T[:, r] + T[:, R_pad + r] holds all four products;
+//   batched kernel: X_hi U_hi + X_hi U_lo + X_lo U_hi into R_pad columns (the dropped
+//     X_lo U_lo is below 2^-16 * 2^-16 of |x u| per term).
+// The remaining Khatri-Rao
 // factors are applied as per-row weights when a fiber group is folded into the
 // row accumulator (fused KRP + TDOT, never materialising the Khatri-Rao rows in
 // HBM -- schedule P2 of Sec. IV-E; Sec. II-A decomposition).
@@ -28,6 +32,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 #include "sm100.cuh"
@@ -56,8 +61,16 @@ constexpr int kRcRawBytes = 4 * kRcBox0;
 static_assert(4 * kRcBox1 <= kRcRawBytes, "case-1 class boxes in a raw stage");
 static_assert(kRcRawBytes % 1024 == 0 && kRcBox0 % 128 == 0 && kRcBox1 % 128 == 0, "box alignment");
 
-template <int RP> struct TcCfg {
-    static constexpr int N = 2 * RP;                       // MMA N: hi and lo columns of the factor
+// THREE: three split products into one accumulator of RP columns (X_hi U_hi + X_hi U_lo +
+// X_lo U_hi); otherwise two MMAs with N = 2 RP (X_hi and X_lo against [U_hi; U_lo]) into an
+// accumulator whose column r holds the U_hi products and column RP + r the U_lo products,
+// all four split products.  Three products halve the epilogue's TMEM reads, but one
+// accumulator takes 12 dependent MMAs per 64-k chunk against 8, which measured slower
+// wherever the MMAs keep pace with HBM (1024^3: 0.687 against 0.652 ms), so only the
+// batched kernel, whose short fiber groups make the epilogue weigh more, uses them.
+template <int RP, bool THREE = false> struct TcCfg {
+    static constexpr int N = 2 * RP;                       // rows of the split factor tile: hi, then lo
+    static constexpr int ACC = THREE ? RP : 2 * RP;        // MMA N and accumulator columns
     static constexpr int RS = RP <= 32 ? 4 : 3;            // raw X stages
     static constexpr int AS = 2;                           // operand stages
     static constexpr int MMA_WARP = CONV_WARPS + EPI_WARPS;
@@ -74,7 +87,7 @@ template <int RP> struct TcCfg {
     static constexpr int WSLOTS = 4;
     static constexpr int WSLOT_FLOATS = (DEINSUM_GMAX + 1) * RP;
     static constexpr int WBUF_BYTES = WSLOTS * WSLOT_FLOATS * 4;
-    static constexpr int TMEM_COLS = 2 * N;                // two accumulators
+    static constexpr int TMEM_COLS = 2 * ACC < 32 ? 32 : 2 * ACC;   // two accumulators (allocation >= 32)
     static constexpr int NBARS = 2 * RS + 3 * AS + 4 + 1 + 2 * WSLOTS;
     static constexpr size_t SMEM = size_t(RS) * RAW_STAGE + size_t(AS) * ASTAGE_BYTES + WBUF_BYTES + 1024 + 512;
     static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB per-CTA limit");
@@ -364,11 +377,10 @@ __device__ __forceinline__ void conv_read_rowcls_mn(const MttkrpGeom &g, const v
 // Box c starts at the class's first row (line) of the chunk and, along the row, at the chunk's
 // first element rounded down to its 16-byte granule (a multiple of 4 words, as a tiled load
 // requires); rows past the class's last member are zero-filled.
-__device__ __forceinline__ void rowcls_load(const MttkrpArgs &a, int64_t col, int64_t tile, int64_t o, int kb,
-                                            uint32_t dst, uint32_t bar) {
-    const MttkrpGeom &g = a.g;
+__device__ __forceinline__ void rowcls_load(const MttkrpGeom &g, const void *X, const CUtensorMap *xrow, int64_t col,
+                                            int64_t tile, int64_t o, int kb, uint32_t dst, uint32_t bar) {
     const int64_t k0 = int64_t(kb) * BK;
-    const uint64_t xw = word_index(a.X);
+    const uint64_t xw = word_index(X);
     if (g.kcase == 0) {
         mbar_arrive_expect_tx(bar, 4 * kRcBox0);
         const int64_t rowbase = tile_rowbase(g, col, tile);
@@ -377,7 +389,7 @@ __device__ __forceinline__ void rowcls_load(const MttkrpArgs &a, int64_t col, in
             const int64_t rc = rowbase + ((c - rowbase) & 3);        // first tile row of class c
             const uint64_t dc = (xw + uint64_t(c) * uint64_t(g.Q)) & 3u; // class offset in its granule
             const int64_t x = int64_t(dc) + o * g.K_in + k0;          // chunk start within the map row
-            tma_load_2d(dst + uint32_t(c * kRcBox0), &a.xrow[c], int(x & ~int64_t(3)), int((rc - c) >> 2), bar);
+            tma_load_2d(dst + uint32_t(c * kRcBox0), &xrow[c], int(x & ~int64_t(3)), int((rc - c) >> 2), bar);
         }
     } else {
         mbar_arrive_expect_tx(bar, 4 * kRcBox1);
@@ -385,7 +397,7 @@ __device__ __forceinline__ void rowcls_load(const MttkrpArgs &a, int64_t col, in
         #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int64_t lc = L0 + ((c - L0) & 3);                  // first chunk line of class c
-            tma_load_2d(dst + uint32_t(c * kRcBox1), &a.xrow[c], int(col * BM), int((lc - c) >> 2), bar);
+            tma_load_2d(dst + uint32_t(c * kRcBox1), &xrow[c], int(col * BM), int((lc - c) >> 2), bar);
         }
     }
 }
@@ -453,17 +465,16 @@ __global__ void batched_weight_tables_kernel(const MttkrpArgs *__restrict__ inst
 // row group at [rp, ...) -- Ofac(o) and the L rows of the tile's p values, or,
 // with opack, L(0) and the Ofac rows of the tile's outer indices -- completing
 // on `bar` (a plain arrive when there are none).
-__device__ __forceinline__ void load_fg_weights(const MttkrpArgs &a, int64_t tile, int64_t o, uint32_t dst,
-                                                uint32_t bar) {
-    const MttkrpGeom &g = a.g;
+__device__ __forceinline__ void load_fg_weights(const MttkrpGeom &g, const float *Lw, const float *Ow, int64_t tile,
+                                                int64_t o, uint32_t dst, uint32_t bar) {
     const uint32_t rowb = uint32_t(g.R_pad) * 4u;
     if (g.opack) {
         const int64_t o0 = tile * g.G;
         const uint32_t no = uint32_t(g.O - o0 < g.G ? g.O - o0 : g.G);
         const uint32_t bytes = (g.n_lmodes > 0 ? rowb : 0u) + no * rowb;
         mbar_arrive_expect_tx(bar, bytes);
-        if (g.n_lmodes > 0) bulk_g2s(dst, a.Lw, rowb, bar);
-        bulk_g2s(dst + rowb, a.Ow + o0 * g.R_pad, no * rowb, bar);
+        if (g.n_lmodes > 0) bulk_g2s(dst, Lw, rowb, bar);
+        bulk_g2s(dst + rowb, Ow + o0 * g.R_pad, no * rowb, bar);
         return;
     }
     uint32_t bytes = 0, nl = 0;
@@ -480,8 +491,8 @@ __device__ __forceinline__ void load_fg_weights(const MttkrpArgs &a, int64_t til
         return;
     }
     mbar_arrive_expect_tx(bar, bytes);
-    if (g.n_outer > 0) bulk_g2s(dst, a.Ow + o * g.R_pad, rowb, bar);
-    if (nl) bulk_g2s(dst + rowb, a.Lw + p0 * g.R_pad, nl * rowb, bar);
+    if (g.n_outer > 0) bulk_g2s(dst, Ow + o * g.R_pad, rowb, bar);
+    if (nl) bulk_g2s(dst + rowb, Lw + p0 * g.R_pad, nl * rowb, bar);
 }
 
 // OP: outer indices packed into the tile; MN: MN-major A operand (the last mode);
@@ -630,7 +641,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     const int ws = int(fgi % C::WSLOTS);
                     const uint32_t wj = uint32_t(fgi / C::WSLOTS);
                     if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, a.status, wlim)) break;
-                    load_fg_weights(a, it.tile, it.o, wslot_addr(ws), wfull(ws));
+                    load_fg_weights(a.g, a.Lw, a.Ow, it.tile, it.o, wslot_addr(ws), wfull(ws));
                     w_used |= 1u << ws;
                     w_par = (w_par & ~(1u << ws)) | ((wj & 1u) << ws);
                     ++fgi;
@@ -641,7 +652,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, a.status, wlim)) break;
                     const int kc = it.kb * BK;
                     if (RC) {
-                        rowcls_load(a, it.col, it.tile, it.o, it.kb, raw_addr(rs), raw_full(rs));
+                        rowcls_load(a.g, a.X, a.xrow, it.col, it.tile, it.o, it.kb, raw_addr(rs), raw_full(rs));
                     } else if (OP) {
                         mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
                         const int o0 = int(it.tile * g.G);
@@ -673,7 +684,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     } else if (warp == C::MMA_WARP) {
         // -------------------------------------------------------------- MMA issue
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(BM, C::N) | (MN ? kIdescAMnMajor : 0u);
+            constexpr uint32_t idesc = idesc_bf16_f32(BM, C::ACC) | (MN ? kIdescAMnMajor : 0u);
             int64_t chunk = 0;
             Iter itm;   // this CTA's fiber groups, for their chunk counts
             itm.init(a);
@@ -684,7 +695,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 const uint32_t jb = uint32_t(fgi >> 1);
                 if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, a.status, wlim)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t dcol = tmem + uint32_t(b * C::N);
+                const uint32_t dcol = tmem + uint32_t(b * C::ACC);
                 for (int kb = 0; kb < nkb; ++kb) {
                     const int s = int(chunk % AS);
                     const uint32_t j = uint32_t(chunk / AS);
@@ -698,7 +709,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                                            : desc_kmajor_sw128(a_hi(s));
                     const uint64_t dl = MN ? desc_mnmajor_sw128(a_lo(s), kMnAtomStride, kMnKGroupStride)
                                            : desc_kmajor_sw128(a_lo(s));
-                    const uint64_t db = desc_kmajor_sw128(b_t(s));
+                    const uint64_t db = desc_kmajor_sw128(b_t(s));   // [U_hi; U_lo]: N = 2 RP rows
                     #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         // K = 16 per step: 32 bytes along a K-major row, two 8-k groups of an MN-major tile
@@ -759,7 +770,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     tile = it.tile;
                     if (lane_weights) rv = OP ? opack_row_valid(g, tile, l) : row_valid(g, ucol, tile_rowbase(g, ucol, tile), l);
                 }
-                // weights of this fiber group, from its ring slot: lane c holds column c (and c + 32)
+                // weights of this fiber group, from its ring slot (rows of R_pad floats, zero past R)
                 const int ws = int(fgi % C::WSLOTS);
                 const uint32_t wj = uint32_t(fgi / C::WSLOTS);
                 if (!__all_sync(0xffffffffu, mbar_wait(wfull(ws), wj & 1u, abort_flag, a.status, wlim))) {
@@ -768,14 +779,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 }
                 const float *wsl = wbuf + ws * C::WSLOT_FLOATS;
                 const float *lrow = wsl + RP * (1 + lg);   // narrow: L row of this thread's p
-                float w0 = has_common ? wsl[lane] : 1.f;
-                float w1 = (RP > 32 && has_common) ? wsl[lane + 32] : 1.f;
-                if (!lane_weights && g.n_lmodes > 0) {
-                    w0 = wsl[RP + lane] * w0;
-                    if (RP > 32) w1 = wsl[RP + lane + 32] * w1;
-                }
-                if (lane >= g.R) w0 = 0.f;
-                if (RP <= 32 || lane + 32 >= g.R) w1 = 0.f;
+                const bool wl = !lane_weights && g.n_lmodes > 0;   // one L row for the whole tile
                 const int b = int(fgi & 1);
                 const uint32_t jb = uint32_t(fgi >> 1);
                 if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, a.status, wlim))) {
@@ -783,39 +787,40 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                     break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
+                const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::ACC);
                 #pragma unroll
                 for (int c = 0; c < RP; c += 16) {
-                    uint32_t hi[16], lo[16];
-                    tmem_ld16(taddr + uint32_t(c), hi);
-                    tmem_ld16(taddr + uint32_t(RP + c), lo);
+                    uint32_t t[16], tl[16];   // the U_hi and U_lo columns of rank columns c .. c + 15
+                    tmem_ld16(taddr + uint32_t(c), t);
+                    tmem_ld16(taddr + uint32_t(RP + c), tl);
                     tmem_wait_ld();
-                    if constexpr (PW) {
-                        // per-row weights: this thread's row-group row (zero for an invalid
-                        // row) times the row common to the tile, read as float4 from the slot
-                        // (both are zero past R)
-                        #pragma unroll
-                        for (int q4 = 0; q4 < 4; ++q4) {
-                            const int col = c + 4 * q4;
-                            float4 w4 = rv ? *reinterpret_cast<const float4 *>(lrow + col)
-                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                    #pragma unroll
+                    for (int q = 0; q < 16; ++q) t[q] = __float_as_uint(__uint_as_float(t[q]) + __uint_as_float(tl[q]));
+                    #pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const int col = c + 4 * q4;
+                        float4 w4;
+                        if constexpr (PW) {
+                            // per-row weights: this thread's row-group row (zero for an invalid
+                            // row) times the row common to the tile
+                            w4 = rv ? *reinterpret_cast<const float4 *>(lrow + col) : make_float4(0.f, 0.f, 0.f, 0.f);
                             if (has_common) {
                                 const float4 cw = *reinterpret_cast<const float4 *>(wsl + col);
                                 w4.x *= cw.x; w4.y *= cw.y; w4.z *= cw.z; w4.w *= cw.w;
                             }
-                            const int q = 4 * q4;
-                            acc[col] = fmaf(w4.x, __uint_as_float(hi[q]) + __uint_as_float(lo[q]), acc[col]);
-                            acc[col + 1] = fmaf(w4.y, __uint_as_float(hi[q + 1]) + __uint_as_float(lo[q + 1]), acc[col + 1]);
-                            acc[col + 2] = fmaf(w4.z, __uint_as_float(hi[q + 2]) + __uint_as_float(lo[q + 2]), acc[col + 2]);
-                            acc[col + 3] = fmaf(w4.w, __uint_as_float(hi[q + 3]) + __uint_as_float(lo[q + 3]), acc[col + 3]);
+                        } else {
+                            // the same row for every thread (a broadcast read): Ofac(o), times L(p)
+                            w4 = has_common ? *reinterpret_cast<const float4 *>(wsl + col) : make_float4(1.f, 1.f, 1.f, 1.f);
+                            if (wl) {
+                                const float4 lw = *reinterpret_cast<const float4 *>(wsl + RP + col);
+                                w4.x *= lw.x; w4.y *= lw.y; w4.z *= lw.z; w4.w *= lw.w;
+                            }
                         }
-                    } else {
-                        #pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const int col = c + q;
-                            const float w = __shfl_sync(0xffffffffu, col < 32 ? w0 : w1, col & 31);
-                            acc[col] = fmaf(w, __uint_as_float(hi[q]) + __uint_as_float(lo[q]), acc[col]);
-                        }
+                        const int q = 4 * q4;
+                        acc[col] = fmaf(w4.x, __uint_as_float(t[q]), acc[col]);
+                        acc[col + 1] = fmaf(w4.y, __uint_as_float(t[q + 1]), acc[col + 1]);
+                        acc[col + 2] = fmaf(w4.z, __uint_as_float(t[q + 2]), acc[col + 2]);
+                        acc[col + 3] = fmaf(w4.w, __uint_as_float(t[q + 3]), acc[col + 3]);
                     }
                 }
                 tc_fence_before();
@@ -902,70 +907,51 @@ int launch_tc_rp(const MttkrpArgs &a, int n_sm, void *stream) {
 }
 
 // ---------------------------------------------------------------------------
-// Batched form: the same pipeline, but every unit names its instance, whose
-// arguments are read from device memory, and every CTA walks the unit list
-// the host assigned to it (largest first).  The accumulator and factor-tile
-// shapes follow the instance's padded rank (<= 64): MMA N = 2 R_pad is a
-// runtime field of the instruction descriptor.
+// Batched form: one persistent launch over the work units of every instance.
+// Each CTA walks the unit list the host assigned to it (largest first over the
+// CTAs, then grouped by how the unit's instance loads X); every unit names its
+// instance, whose arguments sit in device memory.  Each role reads a unit's
+// fields once and runs its chunks in code specialised for the instance's loads
+// (tensor map or row classes, K-major or MN-major operand) and, in the epilogue,
+// for its padded rank, so that all kinds of instance share one launch and one
+// tail.  The MMAs take the three split products into one accumulator of R_pad
+// columns (N = R_pad, a runtime field of the instruction descriptor).
 // ---------------------------------------------------------------------------
-struct BIter {
-    const BatchArgs *b;
-    const MttkrpArgs *a;
-    int64_t u, uend, col, fg, fg1, tile, o, part_off;
-    int kb;
-    bool done;
-    __device__ __forceinline__ void load_unit() {
-        while (u < uend) {
-            const int64_t *r = b->units + 5 * u;
-            a = b->insts + r[0];
-            col = r[1];
-            fg = r[2];
-            fg1 = r[3];
-            part_off = r[4];
-            if (fg < fg1) {
-                kb = 0;
-                tile = fg / a->g.O_iter;
-                o = fg - tile * a->g.O_iter;
-                done = false;
-                return;
-            }
-            ++u;
-        }
-        done = true;
-    }
-    __device__ __forceinline__ void init(const BatchArgs *bb) {
-        b = bb;
-        u = b->cta_begin[blockIdx.x];
-        uend = b->cta_begin[blockIdx.x + 1];
-        load_unit();
-    }
-    __device__ __forceinline__ void next() {
-        if (++kb < a->g.n_kb) return;
-        kb = 0;
-        if (++fg < fg1) {
-            if (++o == a->g.O_iter) { o = 0; ++tile; }
-            return;
-        }
-        ++u;
-        load_unit();
-    }
-    __device__ __forceinline__ Iter as_iter() const {
-        Iter t;
-        t.u = u; t.col = col; t.fg = fg; t.fg1 = fg1; t.tile = tile; t.o = o; t.kb = kb; t.done = done;
-        t.seg = 0; t.kb_lo = 0; t.kb_hi = a->g.n_kb;
-        return t;
-    }
-};
-
 constexpr int RPB = 64;  // the batched kernel is shaped for the largest padded rank
 
-// RCB: every instance loads X through its row-class maps, all of them with the operand
-// layout MNB (MN-major A for last modes): one unit list per kind, because the code of
-// several kinds in one kernel slows each of them (instruction fetch).
-template <bool RCB, bool MNB>
+// How a unit's instance reaches the converters (from its arguments; uniform per unit).
+enum BatchKind : int { BK_TMA_K = 0, BK_TMA_MN = 1, BK_RC_K = 2, BK_RC_MN = 3, BK_GL_K = 4, BK_GL_MN = 5 };
+__device__ __forceinline__ int batch_kind(const MttkrpArgs &a) {
+    const int mn = a.g.kcase == 1 ? 1 : 0;
+    return a.row_classes ? BK_RC_K + mn : (a.use_tma ? BK_TMA_K + mn : BK_GL_K + mn);
+}
+template <int K> using KindTag = std::integral_constant<int, K>;
+
+// The geometry fields the per-chunk code reads, copied once per unit from device memory
+// (the other fields of the local copy are never read).  K-major kinds fix kcase = 0 at
+// compile time, so the case-1 branches of the shared helpers drop out.
+template <bool MN>
+__device__ __forceinline__ void batch_geometry(MttkrpGeom &l, const MttkrpGeom &g) {
+    l.kcase = MN ? 1 : 0;
+    l.narrow = g.narrow;
+    l.opack = 0;
+    l.R = g.R;
+    l.R_pad = g.R_pad;
+    l.n_kb = g.n_kb;
+    l.n_lmodes = g.n_lmodes;
+    l.n_outer = g.n_outer;
+    l.P = g.P;
+    l.I = g.I;
+    l.Q = g.Q;
+    l.K_in = g.K_in;
+    l.O = g.O;
+    l.G = g.G;
+    l.O_iter = g.O_iter;
+}
+
 __global__ void __maxnreg__(128)   // the launch limit of 448 threads: see mttkrp_tc_kernel
 mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
-    using C = TcCfg<RPB>;
+    using C = TcCfg<RPB, true>;
     constexpr int RS = C::RS, AS = C::AS;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -977,6 +963,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
     int *status = bargs.status;
     const uint64_t wlim = bargs.wait_ns;
+    const int64_t ubeg = bargs.cta_begin[blockIdx.x], uend = bargs.cta_begin[blockIdx.x + 1];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
@@ -995,6 +982,9 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     auto wfull = [&](int s) { return smem_u32(bars + 2 * RS + 3 * AS + 5 + s); };
     auto wempty = [&](int s) { return smem_u32(bars + 2 * RS + 3 * AS + 5 + C::WSLOTS + s); };
     auto wslot_addr = [&](int s) { return smem_u32(wbuf) + uint32_t(s) * uint32_t(C::WSLOT_FLOATS) * 4u; };
+    // unit u: its instance's arguments and (column, first fiber group, end, partial offset)
+    auto unit_args = [&](int64_t u) -> const MttkrpArgs & { return bargs.insts[bargs.units[5 * u]]; };
+    auto unit_field = [&](int64_t u, int f) { return bargs.units[5 * u + f]; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < RS; ++s) {
@@ -1031,62 +1021,88 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         // ----------------------------------------------------------- converters
         const int pt = threadIdx.x;
         const bool issuer = (pt == 0);
-        BIter it;
-        it.init(&bargs);
-        uint32_t bpar = 0, bused = 0;
-        // the raw ring carries only the chunks of TMA-loaded instances: count those apart
-        int64_t tchunk = 0;
-        // last-mode instances (case 1; the batch packs no outer indices) take the MN-major
-        // operand; their row positions in the raw tile are set up when the instance changes
-        const MttkrpArgs *mp_for = nullptr;
-        MnPos mp;
-        for (int64_t chunk = 0; !it.done; ++chunk) {
-            const MttkrpArgs &a = *it.a;
-            const bool mn = RCB ? MNB : a.g.kcase == 1;
-            if (!RCB && mn && mp_for != it.a) {
-                mp = mn_pos(a.raw_pitch > 0 ? a.raw_pitch : BM, 1, pt);
-                mp_for = it.a;
+        uint32_t bpar = 0, bused = 0;      // per operand stage: parity of the last B copy, copy issued
+        int64_t chunk = 0, tchunk = 0;     // operand-ring and raw-ring sequence numbers
+        auto run = [&](auto kt, const MttkrpArgs &a, int64_t col, int64_t f0, int64_t f1) -> bool {
+            constexpr int K = decltype(kt)::value;
+            constexpr bool MN = (K & 1) != 0;
+            constexpr bool RING = K < BK_GL_K;   // X through the raw ring (tensor map or row classes)
+            MttkrpGeom g;
+            batch_geometry<MN>(g, a.g);
+            const void *X = a.X;
+            const char *bsrc = static_cast<const char *>(a.Bsplit);
+            const uint32_t bbytes = uint32_t(2 * g.R_pad * BK * 2);
+            const int pitch = a.raw_pitch;
+            const bool wide = !g.narrow || g.G * g.I == BM;
+            MnPos mp;
+            if constexpr (K == BK_TMA_MN) mp = mn_pos(pitch > 0 ? pitch : BM, 1, pt);
+            for (int64_t fg = f0; fg < f1; ++fg) {
+                const int64_t tile = fg / g.O_iter, o = fg - tile * g.O_iter;
+                for (int kb = 0; kb < g.n_kb; ++kb, ++chunk) {
+                    float4 v[8];
+                    if constexpr (RING) {
+                        const int rs = int(tchunk % RS);
+                        const uint32_t rj = uint32_t(tchunk / RS);
+                        ++tchunk;
+                        if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status, wlim)))
+                            return false;
+                        const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_STAGE);
+                        if constexpr (K == BK_RC_MN) {
+                            conv_read_rowcls_mn(g, X, col, o, kb, raw, pt, v);
+                        } else if constexpr (K == BK_RC_K) {
+                            conv_read_rowcls(g, X, col, tile, o, kb, raw, rowcls_thread(pt), v);
+                        } else if constexpr (K == BK_TMA_MN) {
+                            if (pitch == BM) conv_read_smem_mn128(raw, pt, v);
+                            else conv_read_smem_mn(mp, pitch, raw, pt, v);
+                        } else {
+                            if (wide) conv_read_smem_wide(raw, pt, v);
+                            else conv_read_smem_t<false>(g, pitch, raw, pt, v);
+                        }
+                        fence_proxy_async_smem();   // these generic reads before the stage's next TMA write
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(raw_empty(rs));
+                    } else {
+                        Iter it;
+                        it.col = col;
+                        it.tile = tile;
+                        it.o = o;
+                        it.kb = kb;
+                        if constexpr (MN) conv_read_global_mn<false>(a, it, pt, v);
+                        else conv_read_global<false>(a, it, pt, v);
+                    }
+                    const int as = int(chunk % AS);
+                    const uint32_t aj = uint32_t(chunk / AS);
+                    if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status, wlim)))
+                        return false;
+                    if (issuer) {
+                        mbar_arrive_expect_tx(bfull(as), bbytes);
+                        bulk_g2s(b_t(as), bsrc + size_t(kb) * bbytes, bbytes, bfull(as));
+                        bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
+                        bused |= 1u << as;
+                    }
+                    if constexpr (MN) conv_store_mn(pt, a_hi(as), a_lo(as), v);
+                    else conv_store(g, K == BK_RC_K ? rowcls_thread(pt) : pt, a_hi(as), a_lo(as), v);
+                    fence_proxy_async_smem();   // the A stores before the tensor-core reads
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(a_full(as));
+                }
             }
-            float4 v[8];
-            const int rs = int(tchunk % RS);
-            if (RCB || a.use_tma) {
-                const uint32_t rj = uint32_t(tchunk / RS);
-                ++tchunk;
-                if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status, wlim))) break;
-                const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_STAGE);
-                if (RCB) {
-                    if (mn) conv_read_rowcls_mn(a.g, a.X, it.col, it.o, it.kb, raw, pt, v);
-                    else conv_read_rowcls(a.g, a.X, it.col, it.tile, it.o, it.kb, raw, rowcls_thread(pt), v);
-                } else if (mn && a.raw_pitch == BM) conv_read_smem_mn128(raw, pt, v);
-                else if (mn) conv_read_smem_mn(mp, a.raw_pitch, raw, pt, v);
-                else if (!a.g.narrow || a.g.G * a.g.I == BM) conv_read_smem_wide(raw, pt, v);
-                else conv_read_smem(a, raw, pt, v);
-                fence_proxy_async_smem();   // these generic reads before the stage's next TMA write
-                __syncwarp();
-                if (lane == 0) mbar_arrive(raw_empty(rs));
-            } else if (mn) {
-                conv_read_global_mn<false>(a, it.as_iter(), pt, v);
-            } else {
-                conv_read_global<false>(a, it.as_iter(), pt, v);
+            return true;
+        };
+        bool ok = true;
+        for (int64_t u = ubeg; ok && u < uend; ++u) {
+            const MttkrpArgs &a = unit_args(u);
+            const int64_t col = unit_field(u, 1), f0 = unit_field(u, 2), f1 = unit_field(u, 3);
+            switch (batch_kind(a)) {
+                case BK_TMA_K: ok = run(KindTag<BK_TMA_K>{}, a, col, f0, f1); break;
+                case BK_TMA_MN: ok = run(KindTag<BK_TMA_MN>{}, a, col, f0, f1); break;
+                case BK_RC_K: ok = run(KindTag<BK_RC_K>{}, a, col, f0, f1); break;
+                case BK_RC_MN: ok = run(KindTag<BK_RC_MN>{}, a, col, f0, f1); break;
+                case BK_GL_K: ok = run(KindTag<BK_GL_K>{}, a, col, f0, f1); break;
+                default: ok = run(KindTag<BK_GL_MN>{}, a, col, f0, f1); break;
             }
-            const int as = int(chunk % AS);
-            const uint32_t aj = uint32_t(chunk / AS);
-            if (!__all_sync(0xffffffffu, mbar_wait(a_empty(as), (aj & 1u) ^ 1u, abort_flag, status, wlim))) break;
-            if (issuer) {
-                const uint32_t bbytes = uint32_t(2 * a.g.R_pad * BK * 2);
-                mbar_arrive_expect_tx(bfull(as), bbytes);
-                bulk_g2s(b_t(as), static_cast<const char *>(a.Bsplit) + size_t(it.kb) * bbytes, bbytes, bfull(as));
-                bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
-                bused |= 1u << as;
-            }
-            if (mn) conv_store_mn(pt, a_hi(as), a_lo(as), v);
-            else conv_store(a.g, RCB ? rowcls_thread(pt) : pt, a_hi(as), a_lo(as), v);
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(a_full(as));
-            it.next();
         }
-        if (issuer) {
+        if (issuer) {  // every bulk copy into this CTA's smem has landed before exit
             for (int s = 0; s < AS; ++s)
                 if ((bused >> s) & 1u) mbar_drain(bfull(s), (bpar >> s) & 1u, status);
         }
@@ -1094,57 +1110,73 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         // ------------------------------------------------------------------ TMA
         // (also the weight ring: every fiber group's weight rows, whether or not X goes by TMA)
         if (lane == 0) {
-            BIter it;
-            it.init(&bargs);
             uint32_t r_used = 0, r_par = 0, w_used = 0, w_par = 0;   // as in the single-instance kernel
+            int64_t tchunk = 0, fgi = 0;
             const MttkrpArgs *fenced = nullptr;
-            int64_t tchunk = 0;  // chunks of TMA-loaded instances only (the raw ring's sequence)
-            int64_t fgi = 0;
-            while (!it.done) {
-                const MttkrpArgs &a = *it.a;
-                if (it.kb == 0) {
-                    const int ws = int(fgi % C::WSLOTS);
-                    const uint32_t wj = uint32_t(fgi / C::WSLOTS);
-                    if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, status, wlim)) break;
-                    load_fg_weights(a, it.tile, it.o, wslot_addr(ws), wfull(ws));
-                    w_used |= 1u << ws;
-                    w_par = (w_par & ~(1u << ws)) | ((wj & 1u) << ws);
-                    ++fgi;
-                }
-                if ((RCB || a.use_tma) && fenced != it.a) {
-                    if (RCB)
+            auto run = [&](auto kt, const MttkrpArgs &a, int64_t col, int64_t f0, int64_t f1) -> bool {
+                constexpr int K = decltype(kt)::value;
+                constexpr bool MN = (K & 1) != 0;
+                constexpr bool RING = K < BK_GL_K;
+                MttkrpGeom g;
+                batch_geometry<MN>(g, a.g);
+                const float *Lw = a.Lw, *Ow = a.Ow;
+                const void *X = a.X;
+                const uint32_t box_bytes = a.box_bytes;
+                if (RING && fenced != &a) {   // the descriptors were written since the last launch
+                    if constexpr (K == BK_RC_K || K == BK_RC_MN)
                         for (int c = 0; c < 4; ++c) fence_tensormap_acquire(&a.xrow[c]);
                     else
                         fence_tensormap_acquire(&a.xmap);
-                    fenced = it.a;
+                    fenced = &a;
                 }
-                if (RCB || a.use_tma) {
-                    const int rs = int(tchunk % RS);
-                    const uint32_t rj = uint32_t(tchunk / RS);
-                    ++tchunk;
-                    if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status, wlim)) break;
-                    const int kc = it.kb * BK;
-                    if (RCB) {
-                        rowcls_load(a, it.col, it.tile, it.o, it.kb, raw_addr(rs), raw_full(rs));
-                    } else if (a.g.opack) {
-                        mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
-                        const int o0 = int(it.tile * a.g.G);
-                        if (a.g.kcase == 0) tma_load_4d(raw_addr(rs), &a.xmap, kc, 0, o0, 0, raw_full(rs));
-                        else tma_load_3d(raw_addr(rs), &a.xmap, 0, kc, o0, raw_full(rs));
-                    } else if (a.g.kcase == 0) {
-                        mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
-                        const int c2 = a.g.narrow ? 0 : int(it.col * BM);
-                        const int c3 = a.g.narrow ? int(it.tile * a.g.G) : int(it.tile);
-                        tma_load_4d(raw_addr(rs), &a.xmap, kc, int(it.o), c2, c3, raw_full(rs));
-                    } else {
-                        mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
-                        tma_load_3d(raw_addr(rs), &a.xmap, int(it.col * BM), kc, int(it.o), raw_full(rs));
+                for (int64_t fg = f0; fg < f1; ++fg) {
+                    const int64_t tile = fg / g.O_iter, o = fg - tile * g.O_iter;
+                    const int ws = int(fgi % C::WSLOTS);
+                    const uint32_t wj = uint32_t(fgi / C::WSLOTS);
+                    if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, status, wlim)) return false;
+                    load_fg_weights(g, Lw, Ow, tile, o, wslot_addr(ws), wfull(ws));
+                    w_used |= 1u << ws;
+                    w_par = (w_par & ~(1u << ws)) | ((wj & 1u) << ws);
+                    ++fgi;
+                    if constexpr (RING) {
+                        for (int kb = 0; kb < g.n_kb; ++kb) {
+                            const int rs = int(tchunk % RS);
+                            const uint32_t rj = uint32_t(tchunk / RS);
+                            ++tchunk;
+                            if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status, wlim)) return false;
+                            const int kc = kb * BK;
+                            if constexpr (K == BK_RC_K || K == BK_RC_MN) {
+                                rowcls_load(g, X, a.xrow, col, tile, o, kb, raw_addr(rs), raw_full(rs));
+                            } else if constexpr (K == BK_TMA_K) {
+                                mbar_arrive_expect_tx(raw_full(rs), box_bytes);
+                                const int c2 = g.narrow ? 0 : int(col * BM);
+                                const int c3 = g.narrow ? int(tile * g.G) : int(tile);
+                                tma_load_4d(raw_addr(rs), &a.xmap, kc, int(o), c2, c3, raw_full(rs));
+                            } else {
+                                mbar_arrive_expect_tx(raw_full(rs), box_bytes);
+                                tma_load_3d(raw_addr(rs), &a.xmap, int(col * BM), kc, int(o), raw_full(rs));
+                            }
+                            r_used |= 1u << rs;
+                            r_par = (r_par & ~(1u << rs)) | ((rj & 1u) << rs);
+                        }
                     }
-                    r_used |= 1u << rs;
-                    r_par = (r_par & ~(1u << rs)) | ((rj & 1u) << rs);
                 }
-                it.next();
+                return true;
+            };
+            bool ok = true;
+            for (int64_t u = ubeg; ok && u < uend; ++u) {
+                const MttkrpArgs &a = unit_args(u);
+                const int64_t col = unit_field(u, 1), f0 = unit_field(u, 2), f1 = unit_field(u, 3);
+                switch (batch_kind(a)) {
+                    case BK_TMA_K: ok = run(KindTag<BK_TMA_K>{}, a, col, f0, f1); break;
+                    case BK_TMA_MN: ok = run(KindTag<BK_TMA_MN>{}, a, col, f0, f1); break;
+                    case BK_RC_K: ok = run(KindTag<BK_RC_K>{}, a, col, f0, f1); break;
+                    case BK_RC_MN: ok = run(KindTag<BK_RC_MN>{}, a, col, f0, f1); break;
+                    case BK_GL_K: ok = run(KindTag<BK_GL_K>{}, a, col, f0, f1); break;
+                    default: ok = run(KindTag<BK_GL_MN>{}, a, col, f0, f1); break;
+                }
             }
+            // every copy issued into this CTA's shared memory has landed before exit
             for (int s2 = 0; s2 < RS; ++s2)
                 if ((r_used >> s2) & 1u) mbar_drain(raw_full(s2), (r_par >> s2) & 1u, status);
             for (int s2 = 0; s2 < C::WSLOTS; ++s2)
@@ -1154,48 +1186,53 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     } else if (warp == C::MMA_WARP) {
         // -------------------------------------------------------------- MMA issue
         if (lane == 0) {
-            BIter it;
-            it.init(&bargs);
             int64_t chunk = 0, fgi = 0;
-            bool ok = true;
-            uint32_t dcol = 0, idesc = 0;
-            bool mn = false;
-            while (ok && !it.done) {
-                const MttkrpArgs &a = *it.a;
-                const int b = int(fgi & 1);
-                if (it.kb == 0) {
+            auto run = [&](auto mt, const MttkrpArgs &a, int64_t f0, int64_t f1) -> bool {
+                constexpr bool MN = decltype(mt)::value != 0;   // the last mode: MN-major A
+                const int n_kb = a.g.n_kb;
+                const int rp = a.g.R_pad;
+                const uint32_t idesc = idesc_bf16_f32(BM, rp) | (MN ? kIdescAMnMajor : 0u);
+                const uint32_t blo = uint32_t(rp * 128);   // U_lo rows of the split factor tile
+                for (int64_t fg = f0; fg < f1; ++fg, ++fgi) {
+                    const int b = int(fgi & 1);
                     const uint32_t jb = uint32_t(fgi >> 1);
-                    if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status, wlim)) { ok = false; break; }
+                    if (!mbar_wait(acce(b), (jb & 1u) ^ 1u, abort_flag, status, wlim)) return false;
                     tc_fence_after();
-                    dcol = tmem + uint32_t(b * C::N);
-                    mn = RCB ? MNB : a.g.kcase == 1;   // the last mode: MN-major A (see the converters)
-                    idesc = idesc_bf16_f32(BM, 2 * a.g.R_pad) | (mn ? kIdescAMnMajor : 0u);
-                }
-                const int s = int(chunk % AS);
-                const uint32_t j = uint32_t(chunk / AS);
-                if (!mbar_wait(a_full(s), j & 1u, abort_flag, status, wlim) ||
-                    !mbar_wait(bfull(s), j & 1u, abort_flag, status, wlim)) { ok = false; break; }
-                tc_fence_after();
-                const uint64_t dh = mn ? desc_mnmajor_sw128(a_hi(s), kMnAtomStride, kMnKGroupStride)
-                                       : desc_kmajor_sw128(a_hi(s));
-                const uint64_t dl = mn ? desc_mnmajor_sw128(a_lo(s), kMnAtomStride, kMnKGroupStride)
-                                       : desc_kmajor_sw128(a_lo(s));
-                const uint64_t db = desc_kmajor_sw128(b_t(s));
-                #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk) {
-                    const uint64_t adv = uint64_t(kk * 32) >> 4;
-                    const uint64_t adv_a = mn ? uint64_t(kk * 2 * kMnKGroupStride) >> 4 : adv;
-                    mma_bf16(dcol, dh + adv_a, db + adv, idesc, (it.kb > 0 || kk > 0) ? 1u : 0u);
-                    mma_bf16(dcol, dl + adv_a, db + adv, idesc, 1u);
-                }
-                mma_commit(a_empty(s));
-                ++chunk;
-                if (it.kb == a.g.n_kb - 1) {
+                    const uint32_t dcol = tmem + uint32_t(b * C::ACC);
+                    for (int kb = 0; kb < n_kb; ++kb, ++chunk) {
+                        const int s = int(chunk % AS);
+                        const uint32_t j = uint32_t(chunk / AS);
+                        if (!mbar_wait(a_full(s), j & 1u, abort_flag, status, wlim) ||
+                            !mbar_wait(bfull(s), j & 1u, abort_flag, status, wlim))
+                            return false;
+                        tc_fence_after();
+                        const uint64_t dh = MN ? desc_mnmajor_sw128(a_hi(s), kMnAtomStride, kMnKGroupStride)
+                                               : desc_kmajor_sw128(a_hi(s));
+                        const uint64_t dl = MN ? desc_mnmajor_sw128(a_lo(s), kMnAtomStride, kMnKGroupStride)
+                                               : desc_kmajor_sw128(a_lo(s));
+                        const uint64_t db = desc_kmajor_sw128(b_t(s));
+                        const uint64_t dbl = desc_kmajor_sw128(b_t(s) + blo);
+                        #pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint64_t adv = uint64_t(kk * 32) >> 4;
+                            const uint64_t adv_a = MN ? uint64_t(kk * 2 * kMnKGroupStride) >> 4 : adv;
+                            mma_bf16(dcol, dh + adv_a, db + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                            mma_bf16(dcol, dh + adv_a, dbl + adv, idesc, 1u);
+                            mma_bf16(dcol, dl + adv_a, db + adv, idesc, 1u);
+                        }
+                        mma_commit(a_empty(s));
+                    }
                     mma_commit(accf(b));
-                    ++fgi;
                 }
-                it.next();
+                return true;
+            };
+            bool ok = true;
+            for (int64_t u = ubeg; ok && u < uend; ++u) {
+                const MttkrpArgs &a = unit_args(u);
+                const int64_t f0 = unit_field(u, 2), f1 = unit_field(u, 3);
+                ok = a.g.kcase == 1 ? run(KindTag<1>{}, a, f0, f1) : run(KindTag<0>{}, a, f0, f1);
             }
+            // all issued MMAs have completed before TMEM is released
             mma_commit(drain);
             mbar_drain(drain, 0, status);
         }
@@ -1204,34 +1241,30 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         // ------------------------------------------------------------- epilogue
         const int quad = warp & 3;
         const int l = quad * 32 + lane;
-        BIter it;
-        it.init(&bargs);
         int64_t fgi = 0;
-        bool ok = true;
-        while (ok && !it.done) {
-            const int64_t u = it.u;
-            const MttkrpArgs &a = *it.a;
-            const MttkrpGeom &g = a.g;
-            const int rp = g.R_pad;
-            const int64_t ucol = it.col;
-            const bool lane_weights = g.opack || (g.kcase == 0 && g.narrow && g.n_lmodes > 0);  // per-row weights
-            const bool has_common = g.opack ? g.n_lmodes > 0 : g.n_outer > 0;   // a row common to the tile
-            float *part = bargs.partial + it.part_off + int64_t(l) * rp;
+        auto run = [&](auto rt, const MttkrpArgs &a, int64_t col, int64_t f0, int64_t f1, int64_t part_off) -> bool {
+            constexpr int RP = decltype(rt)::value;
+            MttkrpGeom g;
+            batch_geometry<false>(g, a.g);
+            g.kcase = a.g.kcase;
+            // per-row weights: narrow case-0 tiles of several p with L rows
+            const bool lane_weights = g.kcase == 0 && g.narrow && g.n_lmodes > 0;
+            const bool has_common = g.n_outer > 0;                 // a row common to the tile
+            const bool wl = !lane_weights && g.n_lmodes > 0;       // one L row for the whole tile
+            float *part = bargs.partial + part_off + int64_t(l) * RP;
             bool first_flush = true;
-            float acc[RPB];
+            float acc[RP];
             #pragma unroll
-            for (int c = 0; c < RPB; ++c) acc[c] = 0.f;
+            for (int c = 0; c < RP; ++c) acc[c] = 0.f;
             auto flush = [&]() {
                 #pragma unroll
-                for (int c = 0; c < RPB; c += 4) {
-                    if (c < rp) {
-                        float4 sv = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
-                        if (!first_flush) {
-                            const float4 pv = *reinterpret_cast<const float4 *>(part + c);
-                            sv.x += pv.x; sv.y += pv.y; sv.z += pv.z; sv.w += pv.w;
-                        }
-                        *reinterpret_cast<float4 *>(part + c) = sv;
+                for (int c = 0; c < RP; c += 4) {
+                    float4 sv = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+                    if (!first_flush) {
+                        const float4 pv = *reinterpret_cast<const float4 *>(part + c);
+                        sv.x += pv.x; sv.y += pv.y; sv.z += pv.z; sv.w += pv.w;
                     }
+                    *reinterpret_cast<float4 *>(part + c) = sv;
                     acc[c] = acc[c + 1] = acc[c + 2] = acc[c + 3] = 0.f;
                 }
                 first_flush = false;
@@ -1240,49 +1273,44 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             int folded = 0;
             bool rv = true;  // narrow tiles: this thread's row holds a valid (p, i_n)
             const int lg = g.narrow ? int(l / g.I) : 0;
-            while (!it.done && it.u == u) {
-                if (it.tile != tile) {
-                    tile = it.tile;
-                    if (lane_weights) rv = g.opack ? opack_row_valid(g, tile, l) : row_valid(g, ucol, tile_rowbase(g, ucol, tile), l);
+            for (int64_t fg = f0; fg < f1; ++fg, ++fgi) {
+                const int64_t t = fg / g.O_iter;
+                if (t != tile) {
+                    tile = t;
+                    if (lane_weights) rv = row_valid(g, col, tile_rowbase(g, col, tile), l);
                 }
                 const int ws = int(fgi % C::WSLOTS);
                 const uint32_t wj = uint32_t(fgi / C::WSLOTS);
-                if (!__all_sync(0xffffffffu, mbar_wait(wfull(ws), wj & 1u, abort_flag, status, wlim))) {
-                    ok = false;
-                    break;
-                }
+                if (!__all_sync(0xffffffffu, mbar_wait(wfull(ws), wj & 1u, abort_flag, status, wlim))) return false;
                 const float *wsl = wbuf + ws * C::WSLOT_FLOATS;
-                const float *lrow = wsl + rp * (1 + lg);
-                float w0 = has_common ? wsl[lane] : 1.f;
-                float w1 = (rp > 32 && has_common) ? wsl[lane + 32] : 1.f;
-                if (!lane_weights && g.n_lmodes > 0) {
-                    w0 = wsl[rp + lane] * w0;
-                    if (rp > 32) w1 = wsl[rp + lane + 32] * w1;
-                }
-                if (lane >= g.R) w0 = 0.f;
-                if (rp <= 32 || lane + 32 >= g.R) w1 = 0.f;
+                const float *lrow = wsl + RP * (1 + lg);
                 const int b = int(fgi & 1);
                 const uint32_t jb = uint32_t(fgi >> 1);
-                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status, wlim))) {
-                    ok = false;
-                    break;
-                }
+                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status, wlim))) return false;
                 tc_fence_after();
-                const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
+                const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::ACC);
                 #pragma unroll
-                for (int c = 0; c < RPB; c += 16) {
-                    if (c < rp) {
-                        uint32_t hi[16], lo[16];
-                        tmem_ld16(taddr + uint32_t(c), hi);
-                        tmem_ld16(taddr + uint32_t(rp + c), lo);
-                        tmem_wait_ld();
-                        #pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const int col = c + q;
-                            float w = __shfl_sync(0xffffffffu, col < 32 ? w0 : w1, col & 31);
-                            if (lane_weights) w *= rv ? lrow[col] : 0.f;
-                            acc[col] = fmaf(w, __uint_as_float(hi[q]) + __uint_as_float(lo[q]), acc[col]);
+                for (int c = 0; c < RP; c += 16) {
+                    uint32_t tv[16];
+                    tmem_ld16(taddr + uint32_t(c), tv);
+                    tmem_wait_ld();
+                    #pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const int cc = c + 4 * q4;
+                        // weight rows are zero past R: no column mask
+                        float4 w4 = has_common ? *reinterpret_cast<const float4 *>(wsl + cc)
+                                               : make_float4(1.f, 1.f, 1.f, 1.f);
+                        if (lane_weights || wl) {
+                            const float4 lw = lane_weights
+                                ? (rv ? *reinterpret_cast<const float4 *>(lrow + cc) : make_float4(0.f, 0.f, 0.f, 0.f))
+                                : *reinterpret_cast<const float4 *>(wsl + RP + cc);
+                            w4.x *= lw.x; w4.y *= lw.y; w4.z *= lw.z; w4.w *= lw.w;
                         }
+                        const int q = 4 * q4;
+                        acc[cc] = fmaf(w4.x, __uint_as_float(tv[q]), acc[cc]);
+                        acc[cc + 1] = fmaf(w4.y, __uint_as_float(tv[q + 1]), acc[cc + 1]);
+                        acc[cc + 2] = fmaf(w4.z, __uint_as_float(tv[q + 2]), acc[cc + 2]);
+                        acc[cc + 3] = fmaf(w4.w, __uint_as_float(tv[q + 3]), acc[cc + 3]);
                     }
                 }
                 tc_fence_before();
@@ -1292,15 +1320,23 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                     mbar_arrive(wempty(ws));
                     mbar_arrive(acce(b));
                 }
-                ++fgi;
                 if (++folded == kFoldEvery) {
                     folded = 0;
                     flush();
                 }
-                for (int kb = 0; kb < g.n_kb; ++kb) it.next();
             }
-            if (!ok) break;
             flush();
+            return true;
+        };
+        bool ok = true;
+        for (int64_t u = ubeg; ok && u < uend; ++u) {
+            const MttkrpArgs &a = unit_args(u);
+            const int64_t col = unit_field(u, 1), f0 = unit_field(u, 2), f1 = unit_field(u, 3);
+            const int64_t off = unit_field(u, 4);
+            const int rp = a.g.R_pad;
+            ok = rp == 16 ? run(KindTag<16>{}, a, col, f0, f1, off)
+               : rp == 32 ? run(KindTag<32>{}, a, col, f0, f1, off)
+                          : run(KindTag<64>{}, a, col, f0, f1, off);
         }
     }
 
@@ -1314,17 +1350,16 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
 
 }  // namespace
 
-size_t mttkrp_tc_batched_smem_bytes() { return TcCfg<RPB>::SMEM; }
+size_t mttkrp_tc_batched_smem_bytes() { return TcCfg<RPB, true>::SMEM; }
 
-int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, int kind, void *stream) {
-    using C = TcCfg<RPB>;
-    auto kern = kind == 2 ? mttkrp_tc_batched_kernel<true, true>
-                          : (kind == 1 ? mttkrp_tc_batched_kernel<true, false> : mttkrp_tc_batched_kernel<false, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
+int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, void *stream) {
+    using C = TcCfg<RPB, true>;
+    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(C::SMEM));
     if (e != cudaSuccess) return int(e);
     BatchArgs kb = b;
     kb.wait_ns = wait_limit_ns();
-    kern<<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(kb);
+    mttkrp_tc_batched_kernel<<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(kb);
     count_launch();
     return int(cudaGetLastError());
 }

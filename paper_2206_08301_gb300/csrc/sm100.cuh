@@ -84,37 +84,38 @@ __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
 // phase completes whatever its hint says, which would outlast a limit of a few ns.
 constexpr uint64_t kShortWaitNs = 1000000ull;
 
+// The polling part of mbar_wait, out of line: the waits sit in every pipeline loop, and
+// inlined polling loops at each of them measurably slowed the kernels (instruction fetch).
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
+                                            uint64_t limit_ns) {
+    const uint64_t t0 = globaltimer_ns();
+    if (limit_ns < kShortWaitNs) {
+        while (true) {
+            if (mbar_test_wait(bar, parity)) return true;
+            if (*abort) return false;
+            if (globaltimer_ns() - t0 > limit_ns) break;
+        }
+    } else {
+        while (true) {
+            #pragma unroll 1
+            for (int i = 0; i < 32; ++i)
+                if (mbar_try_wait_hint(bar, parity, 10000000u)) return true;
+            if (*abort) return false;
+            if (globaltimer_ns() - t0 > limit_ns) break;
+        }
+    }
+    atomicOr(status, kStatusTimeout);
+    *abort = 1;
+    return false;
+}
+
 // Wait for the phase of parity `parity` to complete, for at most `limit_ns`.
 // On time-out (or when another role already gave up, *abort != 0) it records
 // a failure in the device status word, raises *abort and returns false.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
                                           uint64_t limit_ns) {
-    if (limit_ns < kShortWaitNs) {
-        const uint64_t t0 = globaltimer_ns();
-        while (true) {
-            if (mbar_test_wait(bar, parity)) return true;
-            if (*abort) return false;
-            if (globaltimer_ns() - t0 > limit_ns) {
-                atomicOr(status, kStatusTimeout);
-                *abort = 1;
-                return false;
-            }
-        }
-    }
-    constexpr uint32_t hint = 10000000u;   // suspend-time hint of one poll: 10 ms
-    if (mbar_try_wait_hint(bar, parity, hint)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    while (true) {
-        #pragma unroll 1
-        for (int i = 0; i < 32; ++i)
-            if (mbar_try_wait_hint(bar, parity, hint)) return true;
-        if (*abort) return false;
-        if (globaltimer_ns() - t0 > limit_ns) {
-            atomicOr(status, kStatusTimeout);
-            *abort = 1;
-            return false;
-        }
-    }
+    if (limit_ns >= kShortWaitNs && mbar_try_wait_hint(bar, parity, 10000000u)) return true;
+    return mbar_wait_slow(bar, parity, abort, status, limit_ns);
 }
 
 // Wait for the phase of parity `parity` to complete whether or not another role gave up:
