@@ -331,46 +331,65 @@ __device__ __forceinline__ void conv_read_rowcls(const MttkrpGeom &g, const void
         if (!row_valid(g, col, rowbase, rsub + 16 * j)) v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Case 1 from the four class boxes, in the thread layout of conv_read_smem_mn128 (k line
-// kl = 8 w + j, rows m = 4 lane .. + 3): line kl is box line kl / 4 of class (L0 + kl) mod 4,
-// L0 = o K_in + k0; its word offset d is uniform across the warp.  Rows i_n >= I and
-// k >= K_in read as zero.
+// Case 1 from the four class boxes.  Thread layout (warp w, lane): the warp holds the eight
+// k lines kl = r + 4 (8 h + j), j < 8, of one residue r = w mod 4 (h = w / 4), rows
+// m = 4 lane .. + 3 of each.  All of a warp's lines are members of one class, c = (L0 + r)
+// mod 4 with L0 = o K_in + k0, so they start at one word offset d within their 16-byte
+// granule: the offset is fixed for the chunk (one switch, as in case 0), and line kl is
+// box line kl / 4 = 8 h + j of that class.  conv_store_mn_cls writes them.
 __device__ __forceinline__ void conv_read_rowcls_mn(const MttkrpGeom &g, const void *X, int64_t col, int64_t o,
                                                     int kb, const float *raw, int pt, float4 (&v)[8]) {
     const int w = pt >> 5, lane = pt & 31;
+    const int r = w & 3, h = w >> 2;
     const int64_t k0 = int64_t(kb) * BK;
     const uint64_t L0 = uint64_t(o * g.K_in + k0);
-    const uint64_t e0 = word_index(X) + (L0 + uint64_t(8 * w)) * uint64_t(g.I) + uint64_t(col * BM);
-    const uint32_t r = smem_u32(raw) + uint32_t(lane * 16);
-    // lines j and j + 4 are in one class (box lines kl / 4 and kl / 4 + 1): one offset per pair
-    #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int kl = 8 * w + j;
-        const int c = int((L0 + uint64_t(kl)) & 3u);
-        const int d = int((e0 + uint64_t(j) * uint64_t(g.I)) & 3u);
-        const uint32_t p0 = r + uint32_t((c * kRcRows1 + (kl >> 2)) * kRcPitch1 * 4);
-        const uint32_t p1 = p0 + uint32_t(kRcPitch1 * 4);
-        if (d == 0) {
-            v[j] = lds128(p0);
-            v[j + 4] = lds128(p1);
-        } else {
-            const float4 a0 = lds128(p0), b0 = lds128(p0 + 16u), a1 = lds128(p1), b1 = lds128(p1 + 16u);
-            if (d == 1) {
-                v[j] = make_float4(a0.y, a0.z, a0.w, b0.x);
-                v[j + 4] = make_float4(a1.y, a1.z, a1.w, b1.x);
-            } else if (d == 2) {
-                v[j] = make_float4(a0.z, a0.w, b0.x, b0.y);
-                v[j + 4] = make_float4(a1.z, a1.w, b1.x, b1.y);
-            } else {
-                v[j] = make_float4(a0.w, b0.x, b0.y, b0.z);
-                v[j + 4] = make_float4(a1.w, b1.x, b1.y, b1.z);
-            }
-        }
+    const int c = int((L0 + uint64_t(r)) & 3u);
+    const int d = int((word_index(X) + (L0 + uint64_t(r)) * uint64_t(g.I) + uint64_t(col * BM)) & 3u);
+    const uint32_t p = smem_u32(raw) + uint32_t(((c * kRcRows1 + 8 * h) * kRcPitch1 + 4 * lane) * 4);
+    constexpr uint32_t JS = kRcPitch1 * 4u;   // bytes between box lines
+    switch (d) {
+        case 0:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds128(p + JS * j);
+            break;
+        case 1:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(p + JS * j, 1);
+            break;
+        case 2:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(p + JS * j, 2);
+            break;
+        default:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(p + JS * j, 3);
+            break;
     }
     // No masks (as in conv_read_rowcls for wide tiles): lines past K_in belong to the next
     // outer index and meet the zero rows of the split factor tile; rows past I are zero past
     // the end of a line (out of the class map) and otherwise reach only TMEM lanes that the
     // reduction never reads.
+}
+
+// Split and store in the thread layout of conv_read_rowcls_mn: k line kl = r + 4 (8 h + j)
+// of rows 4 lane .. + 3 goes to the MN-major tile at sw128_mn_offset(4 lane, kl) (8 bytes,
+// hi and lo tiles).  Per store, lanes 0-15 fill one 128-byte k-row of the first 64-row atom
+// and lanes 16-31 the same k-row of the second, as in conv_store_mn.
+__device__ __forceinline__ void conv_store_mn_cls(int pt, uint32_t a_hi, uint32_t a_lo, const float4 (&v)[8]) {
+    const int w = pt >> 5, lane = pt & 31;
+    const uint32_t r = uint32_t(w & 3), h = uint32_t(w >> 2);
+    const uint32_t cl = uint32_t((lane & 15) >> 1);
+    const uint32_t base = uint32_t(lane >> 4) * 1024u + uint32_t(lane & 1) * 8u + h * 8192u;
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t kr = r + 4u * uint32_t(j & 1);            // kl mod 8
+        const uint32_t off = base + uint32_t(j >> 1) * 2048u + kr * 128u + ((cl ^ kr) << 4);
+        uint32_t h0, l0, h1, l1;
+        split2(v[j].x, v[j].y, h0, l0);
+        split2(v[j].z, v[j].w, h1, l1);
+        sts64(a_hi + off, h0, h1);
+        sts64(a_lo + off, l0, l1);
+    }
 }
 
 // One chunk through the row-class maps (one thread): the four boxes into raw stage `dst`.
@@ -615,7 +634,8 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
                 bused |= 1u << as;
             }
-            if (MN) conv_store_mn(pt, a_hi(as), a_lo(as), v);
+            if (MN && RC) conv_store_mn_cls(pt, a_hi(as), a_lo(as), v);
+            else if (MN) conv_store_mn(pt, a_hi(as), a_lo(as), v);
             else conv_store(g, RC ? rowcls_thread(pt) : pt, a_hi(as), a_lo(as), v);
             // the proxy fence orders this thread's A stores before the tensor-core reads
             fence_proxy_async_smem();
@@ -1080,7 +1100,8 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                         bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
                         bused |= 1u << as;
                     }
-                    if constexpr (MN) conv_store_mn(pt, a_hi(as), a_lo(as), v);
+                    if constexpr (K == BK_RC_MN) conv_store_mn_cls(pt, a_hi(as), a_lo(as), v);
+                    else if constexpr (MN) conv_store_mn(pt, a_hi(as), a_lo(as), v);
                     else conv_store(g, K == BK_RC_K ? rowcls_thread(pt) : pt, a_hi(as), a_lo(as), v);
                     fence_proxy_async_smem();   // the A stores before the tensor-core reads
                     __syncwarp();

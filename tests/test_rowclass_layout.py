@@ -9,7 +9,9 @@ narrow tiles, ragged tails, several outer indices, both cases):
   - every word a box reads lies in a 16-byte granule that holds an element of X;
   - every box starts on a 16-byte multiple along the row (a tiled load's x rule);
   - each converter thread gets the values of X at its (row, k) and zero outside the tile;
-  - the thread remap of case 0 is a bijection, and each warp sees one class and offset.
+  - the thread remap of case 0 is a bijection, and each warp sees one class and offset
+    (in case 1 too: a warp holds the k lines of one residue mod 4);
+  - the case-1 store of that layout covers the MN-major tile once.
 The GPU parity tests run the kernels themselves on these layouts.
 """
 import numpy as np
@@ -122,23 +124,54 @@ def _case1(O, K, I, xoff):
                     lc = L0 + ((c - L0) & 3)
                     boxes.append(_fill(mem, maps, c, col * BM, (lc - c) >> 2, R1, P1, 4 * I, lo, hi))
                 full = k0 + BK <= K and col * BM + BM <= I
+                seen = {}
                 for pt in range(256):
                     w, lane = pt >> 5, pt & 31
-                    for j in range(4):           # lines j and j + 4 share class and offset
-                        kl = 8 * w + j
-                        c = (L0 + kl) & 3
-                        d = (xw + (L0 + 8 * w) * I + col * BM + j * I) & 3
-                        assert c == (L0 + kl + 4) & 3 and d == (xw + (L0 + kl + 4) * I + col * BM) & 3
-                        for jj, t in ((j, kl >> 2), (j + 4, (kl >> 2) + 1)):
-                            line = boxes[c][t]
-                            v = _words(line[4 * lane:4 * lane + 4], line[4 * lane + 4:4 * lane + 8], d)
-                            for q in range(4):
-                                m = col * BM + 4 * lane + q
-                                ok = k0 + 8 * w + jj < K and m < I
-                                if ok:
-                                    assert v[q] == X[(o * K + k0 + 8 * w + jj) * I + m]
-                                else:
-                                    assert not full
+                    r, h = w & 3, w >> 2
+                    c = (L0 + r) & 3                                   # one class per warp
+                    d = (xw + (L0 + r) * I + col * BM) & 3             # and one offset
+                    seen.setdefault(w, set()).add((c, d))
+                    for j in range(8):
+                        kl = r + 4 * (8 * h + j)
+                        assert (L0 + kl) & 3 == c and (xw + (L0 + kl) * I + col * BM) & 3 == d
+                        line = boxes[c][8 * h + j]
+                        v = _words(line[4 * lane:4 * lane + 4], line[4 * lane + 4:4 * lane + 8], d)
+                        for q in range(4):
+                            m = col * BM + 4 * lane + q
+                            ok = k0 + kl < K and m < I
+                            if ok:
+                                assert v[q] == X[(o * K + k0 + kl) * I + m]
+                            else:
+                                assert not full
+                assert all(len(s) == 1 for s in seen.values()), "offset not warp-uniform"
+
+
+def _sw128_mn_offset(m, k):
+    """Byte offset of element (m, k) of the MN-major 128-byte-swizzled tile (sm100.cuh)."""
+    return ((k >> 3) * 2 + (m >> 6)) * 1024 + (k & 7) * 128 + (((((m & 63) >> 3) ^ (k & 7)) & 7) << 4) + (m & 7) * 2
+
+
+def test_case1_class_store_covers_the_tile_once():
+    """conv_store_mn_cls: thread (warp w, lane) writes rows 4 lane .. + 3 of k line
+    kl = w % 4 + 4 (8 (w / 4) + j) at the tile's MN-major offset; every (m, k) once, and
+    each 16-lane half of a store fills one 128-byte k-row of one atom."""
+    seen = set()
+    for j in range(8):
+        for w in range(8):
+            r, h = w & 3, w >> 2
+            rows = {}
+            for lane in range(32):
+                cl = (lane & 15) >> 1
+                kl = r + 4 * (8 * h + j)
+                kr = r + 4 * (j & 1)
+                off = (lane >> 4) * 1024 + (lane & 1) * 8 + h * 8192 + (j >> 1) * 2048 + kr * 128 + ((cl ^ kr) << 4)
+                assert off == _sw128_mn_offset(4 * lane, kl)
+                for q in range(4):
+                    assert _sw128_mn_offset(4 * lane + q, kl) == off + 2 * q
+                    seen.add((4 * lane + q, kl))
+                rows.setdefault(lane >> 4, set()).add(off // 128)
+            assert all(len(v) == 1 for v in rows.values())
+    assert len(seen) == BM * BK
 
 
 def test_case0_thread_remap_is_a_bijection():
