@@ -132,6 +132,11 @@ size_t mttkrp_tc_batched_smem_bytes();
 // row pitch of 128 / sg, the rows past I_{N-2} zero-filled by the TMA.
 struct TtmcArgs {
     CUtensorMap xmap;     // 3-D {I_{N-1}, I_{N-2}, S}, box {64, min(I_{N-2}, 128), 1}; sg > 1: {64, 128/sg, sg}
+    // rows of X (I_{N-1} words) not 16-byte aligned: the four row-class maps of the case-0 view
+    // g (encode_x_rowclass_maps), X's address, and sg = 1
+    CUtensorMap xrow[4];
+    const void *X;
+    int row_classes;
     uint32_t box_bytes;
     MttkrpGeom g;         // converter view of a chunk: case 0, I = I_{N-2}, narrow = I < 128 (sg = 1), G = 1
     const void *Bsplit;   // split-BF16 tiles of U_{N-1} (R_pad 32, n_kb tiles)

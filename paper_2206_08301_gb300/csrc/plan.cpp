@@ -566,14 +566,20 @@ deinsum_status plan_ttmc_fused(deinsum_plan_s *pl) {
     const int N = pl->order, n = pl->mode;
     if (N < 3 || n >= N - 2) return DEINSUM_ERR_UNSUPPORTED;
     if (pl->ranks[N - 2] > 32 || pl->ranks[N - 1] > 32) return DEINSUM_ERR_UNSUPPORTED;
-    if (pl->dims[N - 1] % 4 != 0) return DEINSUM_ERR_UNSUPPORTED;
     const int64_t lim = int64_t(1) << 31;
     int64_t S = 1;
     for (int m = 0; m < N - 2; ++m) S *= pl->dims[m];
     if (S >= lim || pl->dims[N - 2] >= lim || pl->dims[N - 1] >= lim) return DEINSUM_ERR_UNSUPPORTED;
+    // rows of I_{N-1} words that are not 16-byte aligned take the row-class maps, one slab per tile
+    const bool rows16 = pl->dims[N - 1] % 4 == 0;
+    if (!rows16) {
+        MttkrpGeom g1;
+        ttm_last_geometry(N, S, pl->dims[N - 2], pl->dims[N - 1], int(pl->ranks[N - 1]), &g1, 1);
+        if (!rowclass_supported(g1)) return DEINSUM_ERR_UNSUPPORTED;
+    }
     pl->ttmc_fused = true;
     pl->t_S = S;
-    pl->t_sg = ttmc_slab_group(pl->dims[N - 2]);
+    pl->t_sg = rows16 ? ttmc_slab_group(pl->dims[N - 2]) : 1;
     pl->t_nkt = int((pl->dims[N - 2] + DEINSUM_BM - 1) / DEINSUM_BM);
     pl->t_nkb = int((pl->dims[N - 1] + DEINSUM_BK - 1) / DEINSUM_BK);
     pl->t2_elems = S * pl->ranks[N - 2] * pl->ranks[N - 1];
@@ -776,7 +782,27 @@ deinsum_status execute_ttmc_fused(deinsum_plan_s *pl, const void *const *inputs,
     const int N = pl->order;
     const void *U[DEINSUM_MAX_ORDER] = {nullptr};
     for (int k = 1; k < pl->n_operands; ++k) U[pl->operand_mode[k]] = inputs[k];
-    if (!encode_ttmc_map(pl, inputs[0])) return DEINSUM_ERR_ALIGN;
+    TtmcArgs t;
+    std::memset(&t, 0, sizeof(t));
+    if (encode_ttmc_map(pl, inputs[0])) {
+        t.xmap = pl->xmap;
+        t.box_bytes = pl->xmap_box_bytes;
+        t.g = pl->geom;
+        t.sg = pl->t_sg;
+    } else {
+        // rows not 16-byte aligned (I_{N-1} not a multiple of 4, or X itself): the four
+        // row-class maps of the one-slab-per-tile view, cached per X pointer
+        ttm_last_geometry(N, pl->t_S, pl->dims[N - 2], pl->dims[N - 1], int(pl->ranks[N - 1]), &t.g, 1);
+        if (pl->xrow_ptr != inputs[0]) {
+            pl->xrow_ptr = inputs[0];
+            pl->xrow_ok = encode_x_rowclass_maps(t.g, inputs[0], pl->xrow) ? 1 : 0;
+        }
+        if (!pl->xrow_ok) return DEINSUM_ERR_ALIGN;
+        for (int c = 0; c < 4; ++c) t.xrow[c] = pl->xrow[c];
+        t.X = inputs[0];
+        t.row_classes = 1;
+        t.sg = 1;
+    }
     // split tiles of U_{N-1} (the same layout as the MTTKRP inner factor)
     MttkrpArgs sa;
     std::memset(&sa, 0, sizeof(sa));
@@ -792,11 +818,6 @@ deinsum_status execute_ttmc_fused(deinsum_plan_s *pl, const void *const *inputs,
     else if (!err)
         err = launch_ttmc_pad_factor(static_cast<const float *>(U[N - 2]), pl->dims[N - 2], int(pl->ranks[N - 2]),
                                      pl->d_u2pad, pl->t_nkt, stream);
-    TtmcArgs t;
-    std::memset(&t, 0, sizeof(t));
-    t.xmap = pl->xmap;
-    t.box_bytes = pl->xmap_box_bytes;
-    t.g = pl->geom;
     t.Bsplit = pl->d_tbsplit;
     t.U2pad = pl->d_u2pad;
     t.U2split = pl->d_u2pad;
@@ -807,7 +828,6 @@ deinsum_status execute_ttmc_fused(deinsum_plan_s *pl, const void *const *inputs,
     t.n_kb = pl->t_nkb;
     t.R2 = int(pl->ranks[N - 2]);
     t.R3 = int(pl->ranks[N - 1]);
-    t.sg = pl->t_sg;
     t.status = pl->d_status;
     if (!err) {
         const long ti = timing_begin(pl, stream);

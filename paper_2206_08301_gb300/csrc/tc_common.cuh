@@ -219,5 +219,192 @@ __device__ __forceinline__ void conv_store(const MttkrpGeom &g, int pt, uint32_t
     }
 }
 
+// ---------------------------------------------------------------------------
+// Rows that are not 16-byte aligned: the row-class tensor maps (MTTKRP and TTMc)
+// ---------------------------------------------------------------------------
+
+// Raw tiles of rows that are not 16-byte aligned, loaded through the four row-class tensor
+// maps (MttkrpArgs::xrow).  A chunk is four boxes, one per class c, each member row padded by
+// 4 words so that the box can start at the 16-byte granule of the row's first element:
+//   case 0: class c = rows of the tile with (global row) = c mod 4: 32 rows of BK + 4 words;
+//           tile row l is row l / 4 of the box of class (rowbase + l) mod 4
+//   case 1: class c = k lines with (o K_in + k) = c mod 4: 16 lines of BM + 4 words;
+//           chunk line kl is line kl / 4 of the box of class (o K_in + k0 + kl) mod 4
+// and a member's first element sits d words into its slot, d = its word address mod 4.
+constexpr int kRcPitch0 = BK + 4, kRcRows0 = BM / 4;
+constexpr int kRcPitch1 = BM + 4, kRcRows1 = BK / 4;
+constexpr int kRcBox0 = kRcRows0 * kRcPitch0 * 4;   // bytes of one class box
+constexpr int kRcBox1 = kRcRows1 * kRcPitch1 * 4;
+constexpr int kRcRawBytes = 4 * kRcBox0;
+static_assert(4 * kRcBox1 <= kRcRawBytes, "case-1 class boxes in a raw stage");
+static_assert(kRcRawBytes % 1024 == 0 && kRcBox0 % 128 == 0 && kRcBox1 % 128 == 0, "box alignment");
+
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+
+// Words d .. d + 3 from the 16-byte aligned address `addr` on, d uniform across the warp (the
+// switch does not diverge): one aligned load for d = 0, two otherwise.
+__device__ __forceinline__ float4 lds_words(uint32_t addr, int d) {
+    const float4 a = lds128(addr);
+    if (d == 0) return a;
+    const float4 b = lds128(addr + 16u);
+    if (d == 1) return make_float4(a.y, a.z, a.w, b.x);
+    if (d == 2) return make_float4(a.z, a.w, b.x, b.y);
+    return make_float4(a.w, b.x, b.y, b.z);
+}
+
+__device__ __forceinline__ uint64_t word_index(const void *p) {
+    return uint64_t(reinterpret_cast<uintptr_t>(p) >> 2);
+}
+
+// Converter thread -> rows for the row-class tiles of case 0: the two half-warps of warp w take
+// rsub = (w mod 4) + 8 (w / 4) and rsub + 4, so that every row of a warp (rsub + 16 j) is in
+// one class and starts at one word offset.  Returned in the packed form conv_store reads
+// (16 rsub + k4); a bijection of 0..255.
+__device__ __forceinline__ int rowcls_thread(int pt) {
+    const int w = pt >> 5, h = (pt >> 4) & 1;
+    return (((w & 3) + 8 * (w >> 2) + 4 * h) << 4) | (pt & 15);
+}
+
+// Case 0 from the four class boxes (thread layout: rows rsub + 16 j, k = 4 k4 .. + 3 with
+// pt = 16 rsub + k4 from rowcls_thread).  Row rsub + 16 j is box row rsub / 4 + 4 j of class
+// (rowbase + rsub) mod 4, and the class's word offset d is the same for the whole warp.
+// Rows outside the tile and k >= K_in read as zero.
+__device__ __forceinline__ void conv_read_rowcls(const MttkrpGeom &g, const void *X, int64_t col, int64_t tile,
+                                                 int64_t o, int kb, const float *raw, int pt, float4 (&v)[8]) {
+    const int k4 = pt & 15, rsub = pt >> 4;
+    const int64_t rowbase = tile_rowbase(g, col, tile);
+    const int64_t k0 = int64_t(kb) * BK;
+    const uint64_t w0 = word_index(X) + uint64_t(rowbase + rsub) * uint64_t(g.Q) + uint64_t(o * g.K_in + k0);
+    const int d = int(w0 & 3u);
+    const int c = int(uint64_t(rowbase + rsub) & 3u);
+    const uint32_t r = smem_u32(raw) + uint32_t(((c * kRcRows0 + (rsub >> 2)) * kRcPitch0 + 4 * k4) * 4);
+    constexpr uint32_t JS = 4u * kRcPitch0 * 4u;   // bytes between box rows rsub / 4 + 4 j
+    switch (d) {
+        case 0:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds128(r + JS * j);
+            break;
+        case 1:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(r + JS * j, 1);
+            break;
+        case 2:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(r + JS * j, 2);
+            break;
+        default:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(r + JS * j, 3);
+            break;
+    }
+    // Values a box brings in beyond the tile's own elements need no mask here.  Past K_in
+    // (the last chunk of a fiber group) they are the same row's next outer index, or zero
+    // past the row's end (out of the class map), and the split factor tile is zero for
+    // k >= K_in.  Past the tile's rows in a wide tile they are rows of the next leading index
+    // (or zero past the tensor), which reach only TMEM lanes and partial rows that the
+    // reduction never reads.  Narrow tiles do read every group's rows, so rows of leading
+    // indices past P are cleared.  (X is assumed finite: a non-finite value times a zero
+    // factor row would be NaN.)
+    if (!g.narrow || rowbase + BM <= g.P * g.I) return;
+    #pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (!row_valid(g, col, rowbase, rsub + 16 * j)) v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Case 1 from the four class boxes.  Thread layout (warp w, lane): the warp holds the eight
+// k lines kl = r + 4 (8 h + j), j < 8, of one residue r = w mod 4 (h = w / 4), rows
+// m = 4 lane .. + 3 of each.  All of a warp's lines are members of one class, c = (L0 + r)
+// mod 4 with L0 = o K_in + k0, so they start at one word offset d within their 16-byte
+// granule: the offset is fixed for the chunk (one switch, as in case 0), and line kl is
+// box line kl / 4 = 8 h + j of that class.  conv_store_mn_cls writes them.
+__device__ __forceinline__ void conv_read_rowcls_mn(const MttkrpGeom &g, const void *X, int64_t col, int64_t o,
+                                                    int kb, const float *raw, int pt, float4 (&v)[8]) {
+    const int w = pt >> 5, lane = pt & 31;
+    const int r = w & 3, h = w >> 2;
+    const int64_t k0 = int64_t(kb) * BK;
+    const uint64_t L0 = uint64_t(o * g.K_in + k0);
+    const int c = int((L0 + uint64_t(r)) & 3u);
+    const int d = int((word_index(X) + (L0 + uint64_t(r)) * uint64_t(g.I) + uint64_t(col * BM)) & 3u);
+    const uint32_t p = smem_u32(raw) + uint32_t(((c * kRcRows1 + 8 * h) * kRcPitch1 + 4 * lane) * 4);
+    constexpr uint32_t JS = kRcPitch1 * 4u;   // bytes between box lines
+    switch (d) {
+        case 0:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds128(p + JS * j);
+            break;
+        case 1:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(p + JS * j, 1);
+            break;
+        case 2:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(p + JS * j, 2);
+            break;
+        default:
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = lds_words(p + JS * j, 3);
+            break;
+    }
+    // No masks (as in conv_read_rowcls for wide tiles): lines past K_in belong to the next
+    // outer index and meet the zero rows of the split factor tile; rows past I are zero past
+    // the end of a line (out of the class map) and otherwise reach only TMEM lanes that the
+    // reduction never reads.
+}
+
+// Split and store in the thread layout of conv_read_rowcls_mn: k line kl = r + 4 (8 h + j)
+// of rows 4 lane .. + 3 goes to the MN-major tile at sw128_mn_offset(4 lane, kl) (8 bytes,
+// hi and lo tiles).  Per store, lanes 0-15 fill one 128-byte k-row of the first 64-row atom
+// and lanes 16-31 the same k-row of the second, as in conv_store_mn.
+__device__ __forceinline__ void conv_store_mn_cls(int pt, uint32_t a_hi, uint32_t a_lo, const float4 (&v)[8]) {
+    const int w = pt >> 5, lane = pt & 31;
+    const uint32_t r = uint32_t(w & 3), h = uint32_t(w >> 2);
+    const uint32_t cl = uint32_t((lane & 15) >> 1);
+    const uint32_t base = uint32_t(lane >> 4) * 1024u + uint32_t(lane & 1) * 8u + h * 8192u;
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t kr = r + 4u * uint32_t(j & 1);            // kl mod 8
+        const uint32_t off = base + uint32_t(j >> 1) * 2048u + kr * 128u + ((cl ^ kr) << 4);
+        uint32_t h0, l0, h1, l1;
+        split2(v[j].x, v[j].y, h0, l0);
+        split2(v[j].z, v[j].w, h1, l1);
+        sts64(a_hi + off, h0, h1);
+        sts64(a_lo + off, l0, l1);
+    }
+}
+
+// One chunk through the row-class maps (one thread): the four boxes into raw stage `dst`.
+// Box c starts at the class's first row (line) of the chunk and, along the row, at the chunk's
+// first element rounded down to its 16-byte granule (a multiple of 4 words, as a tiled load
+// requires); rows past the class's last member are zero-filled.
+__device__ __forceinline__ void rowcls_load(const MttkrpGeom &g, const void *X, const CUtensorMap *xrow, int64_t col,
+                                            int64_t tile, int64_t o, int kb, uint32_t dst, uint32_t bar) {
+    const int64_t k0 = int64_t(kb) * BK;
+    const uint64_t xw = word_index(X);
+    if (g.kcase == 0) {
+        mbar_arrive_expect_tx(bar, 4 * kRcBox0);
+        const int64_t rowbase = tile_rowbase(g, col, tile);
+        #pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t rc = rowbase + ((c - rowbase) & 3);        // first tile row of class c
+            const uint64_t dc = (xw + uint64_t(c) * uint64_t(g.Q)) & 3u; // class offset in its granule
+            const int64_t x = int64_t(dc) + o * g.K_in + k0;          // chunk start within the map row
+            tma_load_2d(dst + uint32_t(c * kRcBox0), &xrow[c], int(x & ~int64_t(3)), int((rc - c) >> 2), bar);
+        }
+    } else {
+        mbar_arrive_expect_tx(bar, 4 * kRcBox1);
+        const int64_t L0 = o * g.K_in + k0;
+        #pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t lc = L0 + ((c - L0) & 3);                  // first chunk line of class c
+            tma_load_2d(dst + uint32_t(c * kRcBox1), &xrow[c], int(col * BM), int((lc - c) >> 2), bar);
+        }
+    }
+}
+
 }  // namespace
 }  // namespace deinsum

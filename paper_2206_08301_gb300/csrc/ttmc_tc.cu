@@ -47,16 +47,19 @@
 namespace deinsum {
 namespace {
 
-struct TtmcCfg {
+// RC: rows of X not 16-byte aligned, loaded through the four row-class tensor maps (four
+// class boxes per chunk, 34 KB a stage: two raw stages instead of three).
+template <bool RC = false> struct TtmcCfg {
     static constexpr int RP = 32;                          // padded R_{N-1} and R_{N-2}
     static constexpr int N = 2 * RP;                       // rows of the split factor tile (hi, then lo)
-    static constexpr int RS = 3;                           // raw X stages
+    static constexpr int RS = RC ? 2 : 3;                  // raw X stages
     static constexpr int AS = 2;                           // operand stages
     static constexpr int MMA_WARP = CONV_WARPS + EPI_WARPS;
     static constexpr int TMA_WARP = MMA_WARP + 1;
     static constexpr int WARPS = TMA_WARP + 1;
     static constexpr int THREADS = WARPS * 32;
-    static constexpr int RAW_BYTES = BM * BK * 4;
+    static constexpr int RAW_BYTES = BM * BK * 4;           // one box of the tensor map
+    static constexpr int RAW_STAGE = RC ? kRcRawBytes : RAW_BYTES;
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = N * BK * 2;
     static constexpr int ASTAGE_BYTES = 2 * A_BYTES + B_BYTES;
@@ -76,7 +79,7 @@ struct TtmcCfg {
     static constexpr int ACC_BAR = 2 * RS + 3 * AS;        // accf[NACC], acce[NACC], drain follow the rings
     static constexpr int TC2_BAR = ACC_BAR + 2 * NACC + 1 + USLOTS + 3;   // u2full, b2full[2], b2free[2], d2full[], d2free[]
     static constexpr int NBARS = TC2_BAR + 5 + 2 * D2_SLOTS + 1;   // + the stage-2 issuer's drain
-    static constexpr size_t SMEM = size_t(RS) * RAW_BYTES + size_t(AS) * ASTAGE_BYTES + T1_BYTES +
+    static constexpr size_t SMEM = size_t(RS) * RAW_STAGE + size_t(AS) * ASTAGE_BYTES + T1_BYTES +
                                    size_t(USLOTS) * USLOT_BYTES + 1024 + 512;
     static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB per-CTA limit");
     static_assert(NBARS * 8 + 8 <= 512, "barrier area");
@@ -108,25 +111,28 @@ struct TIter {
 // logical slot x stored at slot x ^ (r & 7) (conflict-free row writes and
 // column-block reads).
 __device__ __forceinline__ float4 *t1_slot(float *t1s, int r, int x) {
-    return reinterpret_cast<float4 *>(t1s + r * TtmcCfg::RP) + (x ^ (r & 7));
+    return reinterpret_cast<float4 *>(t1s + r * TtmcCfg<>::RP) + (x ^ (r & 7));
 }
 
 // STORE: the epilogue writes the T1 tiles to HBM (a.T2 as S x I_{N-2} x R_{N-1}:
 // the TTM over the last mode alone) instead of running stage 2.  SG: slabs per
 // tile (a.sg).  TC2: stage 2 on the tensor cores (a.tc2), else on CUDA cores.
-template <bool STORE, int SG, bool TC2>
-__global__ void __launch_bounds__(TtmcCfg::THREADS, 1)
+// RC: X through the row-class maps a.xrow (rows of I_{N-1} words not 16-byte aligned;
+// one slab per tile, the tile's rows s I_{N-2} + 128 kt + l as in the MTTKRP case-0 view).
+template <bool STORE, int SG, bool TC2, bool RC>
+__global__ void __launch_bounds__(TtmcCfg<RC>::THREADS, 1)
 ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
-    using C = TtmcCfg;
+    using C = TtmcCfg<RC>;
     constexpr int RS = C::RS, AS = C::AS, RP = C::RP;
     static_assert(!STORE || (SG == 1 && !TC2), "the last-mode TTM keeps one slab per tile");
     static_assert(TC2 || SG == 1, "packed slabs take the tensor-core stage 2");
+    static_assert(!RC || SG == 1, "row classes keep one slab per tile");
     constexpr uint32_t kTmemCols = TC2 ? C::TMEM_COLS_TC2 : C::TMEM_COLS;
     const int64_t ngroups = (a.S + SG - 1) / SG;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *raw_base = smem;
-    unsigned char *a_base = smem + RS * C::RAW_BYTES;
+    unsigned char *a_base = smem + RS * C::RAW_STAGE;
     unsigned char *region = a_base + AS * C::ASTAGE_BYTES;   // CUDA-core: t1s, U slots; TC2: U2 tiles, B2
     float *t1s = reinterpret_cast<float *>(region);
     float *ubuf = t1s + C::T1_BYTES / 4;
@@ -142,7 +148,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
-    auto raw_addr = [&](int s) { return raw_s + uint32_t(s) * C::RAW_BYTES; };
+    auto raw_addr = [&](int s) { return raw_s + uint32_t(s) * C::RAW_STAGE; };
     auto a_hi = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES; };
     auto a_lo = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + C::A_BYTES; };
     auto b_t = [&](int s) { return a_s + uint32_t(s) * C::ASTAGE_BYTES + 2 * C::A_BYTES; };
@@ -221,8 +227,9 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             const int rs = int(chunk % RS);
             const uint32_t rj = uint32_t(chunk / RS);
             if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status, wlim))) break;
-            const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_BYTES);
-            if (!a.g.narrow) conv_read_smem_wide(raw, pt, v);
+            const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_STAGE);
+            if constexpr (RC) conv_read_rowcls(a.g, a.X, it.kt, it.s, 0, it.kb, raw, rowcls_thread(pt), v);
+            else if (!a.g.narrow) conv_read_smem_wide(raw, pt, v);
             else conv_read_smem_t<false>(a.g, BM, raw, pt, v);
             // hand the raw stage back to the TMA warp before the split, so that its next
             // load overlaps it: the proxy fence orders these generic reads before that
@@ -241,7 +248,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 bpar = (bpar & ~(1u << as)) | ((aj & 1u) << as);
                 bused |= 1u << as;
             }
-            conv_store(a.g, pt, a_hi(as), a_lo(as), v);
+            conv_store(a.g, RC ? rowcls_thread(pt) : pt, a_hi(as), a_lo(as), v);
             fence_proxy_async_smem();   // the A stores before the tensor-core reads
             __syncwarp();
             if (lane == 0) mbar_arrive(a_full(as));
@@ -262,8 +269,12 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 const int rs = int(chunk % RS);
                 const uint32_t rj = uint32_t(chunk / RS);
                 if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status, wlim)) break;
-                mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
-                tma_load_3d(raw_addr(rs), &a.xmap, it.kb * BK, it.kt * BM, int(it.s * SG), raw_full(rs));
+                if constexpr (RC) {
+                    rowcls_load(a.g, a.X, a.xrow, it.kt, it.s, 0, it.kb, raw_addr(rs), raw_full(rs));
+                } else {
+                    mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
+                    tma_load_3d(raw_addr(rs), &a.xmap, it.kb * BK, it.kt * BM, int(it.s * SG), raw_full(rs));
+                }
                 r_used |= 1u << rs;
                 r_par = (r_par & ~(1u << rs)) | ((rj & 1u) << rs);
                 it.next(a.n_kb, a.n_kt);
@@ -704,8 +715,8 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
 __global__ void pad_factor_kernel(const float *__restrict__ U, int64_t rows, int R, float *__restrict__ out,
                                   int64_t total) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t r = i / TtmcCfg::RP;
-        const int c = int(i - r * TtmcCfg::RP);
+        const int64_t r = i / TtmcCfg<>::RP;
+        const int c = int(i - r * TtmcCfg<>::RP);
         out[i] = (r < rows && c < R) ? U[r * R + c] : 0.f;
     }
 }
@@ -713,10 +724,10 @@ __global__ void pad_factor_kernel(const float *__restrict__ U, int64_t rows, int
 }  // namespace
 
 namespace {
-template <bool STORE, int SG, bool TC2>
+template <bool STORE, int SG, bool TC2, bool RC = false>
 int launch_ttmc_variant(const TtmcArgs &a, int n_sm, void *stream) {
-    using C = TtmcCfg;
-    cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel<STORE, SG, TC2>,
+    using C = TtmcCfg<RC>;
+    cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel<STORE, SG, TC2, RC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
     if (e != cudaSuccess) return int(e);
     const int64_t groups = (a.S + SG - 1) / SG;
@@ -724,13 +735,21 @@ int launch_ttmc_variant(const TtmcArgs &a, int n_sm, void *stream) {
     if (grid < 1) grid = 1;
     TtmcArgs ka = a;
     ka.wait_ns = wait_limit_ns();
-    ttmc_fused_kernel<STORE, SG, TC2><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(ka);
+    ttmc_fused_kernel<STORE, SG, TC2, RC><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(ka);
     count_launch();
     return int(cudaGetLastError());
 }
 }  // namespace
 
 int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream) {
+    if (a.row_classes) {
+        if (a.sg != 1) return int(cudaErrorInvalidValue);
+        if (a.tc2) {
+            if (a.n_kt > kTtmcTc2MaxKt) return int(cudaErrorInvalidValue);
+            return launch_ttmc_variant<false, 1, true, true>(a, n_sm, stream);
+        }
+        return launch_ttmc_variant<false, 1, false, true>(a, n_sm, stream);
+    }
     if (a.tc2) {
         if (a.n_kt > kTtmcTc2MaxKt) return int(cudaErrorInvalidValue);
         if (a.sg == 4) return launch_ttmc_variant<false, 4, true>(a, n_sm, stream);
@@ -742,7 +761,7 @@ int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream) {
     return launch_ttmc_variant<false, 1, false>(a, n_sm, stream);
 }
 int launch_ttm_last_tc(const TtmcArgs &a, int n_sm, void *stream) {
-    if (a.sg != 1 || a.tc2) return int(cudaErrorInvalidValue);
+    if (a.sg != 1 || a.tc2 || a.row_classes) return int(cudaErrorInvalidValue);
     return launch_ttmc_variant<true, 1, false>(a, n_sm, stream);
 }
 
@@ -769,7 +788,7 @@ __global__ void u2_split_kernel(const float *__restrict__ U, int64_t rows, int R
 }  // namespace
 
 int launch_ttmc_pad_factor(const float *U, int64_t rows, int R, float *out, int n_kt, void *stream) {
-    const int64_t total = int64_t(n_kt) * BM * TtmcCfg::RP;
+    const int64_t total = int64_t(n_kt) * BM * TtmcCfg<>::RP;
     int64_t blocks = (total + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     pad_factor_kernel<<<unsigned(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(U, rows, R, out, total);
@@ -778,7 +797,7 @@ int launch_ttmc_pad_factor(const float *U, int64_t rows, int R, float *out, int 
 }
 
 int launch_ttmc_u2_split(const float *U, int64_t rows, int R, void *out, int n_kt, void *stream) {
-    if (n_kt < 1 || n_kt > kTtmcTc2MaxKt || R > TtmcCfg::RP) return int(cudaErrorInvalidValue);
+    if (n_kt < 1 || n_kt > kTtmcTc2MaxKt || R > TtmcCfg<>::RP) return int(cudaErrorInvalidValue);
     const int64_t total = int64_t(n_kt) * 2 * 2 * 32 * 64;
     u2_split_kernel<<<unsigned((total + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         U, rows, R, static_cast<unsigned char *>(out), total);

@@ -4,7 +4,8 @@ Gate: relative Frobenius error <= 1e-5 and element-wise <= 1e-4 of the largest
 oracle entry (the FP32-accurate tolerance of the TTMc contract).  Cases cover
 ragged k tiles (I_{N-2} not a multiple of 128), ragged l chunks (I_{N-1} not a
 multiple of 64), a k extent below one tile, ranks below the padded 32, orders
-3 to 5 and every kept mode the fused path takes.
+3 to 5, every kept mode the fused path takes, and rows of X that are not 16-byte
+aligned (the row-class tensor maps).
 """
 import numpy as np
 import pytest
@@ -92,11 +93,37 @@ def test_split_ttmc_rank1_closed_form():
     _check(Y.cpu().numpy(), ref)
 
 
-def test_split_ttmc_rejects_misaligned_x():
-    dims = (8, 9, 130, 64)
-    buf = torch.zeros(int(np.prod(dims)) + 1, device="cuda")
-    X = buf[1:].view(dims)              # 4-byte aligned, not 16-byte aligned: no tensor map
-    U = [None] + [torch.ones(dims[m], 4, device="cuda") for m in (1, 2, 3)]
-    with pytest.raises(dz.DeinsumError) as e:
-        dz.ttmc(X, U, 0, prec="split_bf16")
-    assert e.value.status == 5
+# Rows of X that are not 16-byte aligned (I_{N-1} not a multiple of 4, or X itself offset):
+# the row-class tensor maps, one slab per tile; tensor-core stage 2 (I_{N-2} <= 256) and
+# CUDA-core stage 2 (I_{N-2} > 256).
+ROWCLASS_CASES = [
+    # (dims, keep, ranks, X offset in floats)
+    ((8, 9, 130, 66), 0, (5, 16, 12), 0),       # I_{N-1} = 66: rows 8 bytes off, two l chunks
+    ((8, 9, 130, 64), 0, (5, 16, 12), 1),       # aligned shape, X one float into its buffer
+    ((31, 7, 60, 61), 0, (5, 24, 24), 0),       # short slabs (I_{N-2} = 60) one per tile
+    ((50, 300, 133), 0, (17, 31), 3),           # order 3, I_{N-2} = 300: CUDA-core stage 2
+    ((6, 7, 8, 90, 45), 0, (3, 5, 32, 7), 2),   # order 5, two chain stages after the fused pair
+    ((4, 6, 60, 60, 61), 0, (24, 24, 24, 24), 0),   # the paper's order-5 shape with an odd last mode
+]
+
+
+@pytest.mark.parametrize("dims,keep,ranks,offset", ROWCLASS_CASES)
+def test_split_ttmc_rowclass_matches_oracle(dims, keep, ranks, offset):
+    seed = 57 + sum(dims) + keep + offset
+    X = inputs.tensor_uniform_f32(seed, dims)
+    rk = iter(ranks)
+    Us = [None if m == keep else inputs.factor_normal(seed, m, d, next(rk)).astype(np.float32)
+          for m, d in enumerate(dims)]
+    buf = torch.empty(X.size + offset, device="cuda")
+    Xd = buf[offset:].view(dims)
+    Xd.copy_(torch.from_numpy(X))
+    Ud = [None if u is None else torch.from_numpy(u).cuda() for u in Us]
+    Y = dz.ttmc(Xd, Ud, keep, prec="split_bf16")
+    torch.cuda.synchronize()
+    ref = oracle.ttmc(X, Us, keep)
+    _check(Y.cpu().numpy(), ref)
+    # the same result as the tensor-map path where one exists (aligned copy of X)
+    if dims[-1] % 4 == 0:
+        A = dz.ttmc(torch.from_numpy(X).cuda(), Ud, keep, prec="split_bf16")
+        torch.cuda.synchronize()
+        assert oracle.rel_error(Y.cpu().numpy().astype(np.float64), A.cpu().numpy().astype(np.float64)) <= 1e-5
