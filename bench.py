@@ -169,9 +169,19 @@ class ClockSampler:
         return self.stats(t0, t1)
 
 
+# The sources each main kernel is compiled from (its .cu file and the headers it includes).
+KERNEL_SOURCES = {
+    "mttkrp_tc.cu": ("mttkrp_tc.cu", "mttkrp_tc.cuh", "tc_common.cuh", "sm100.cuh", "internal.h"),
+    "ttmc_tc.cu": ("ttmc_tc.cu", "tc_common.cuh", "sm100.cuh", "internal.h"),
+}
+
+
 def _kernel_source_hash(source="mttkrp_tc.cu"):
-    with open(os.path.join(ROOT, "paper_2206_08301_gb300", "csrc", source), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(source, (source,)):
+        with open(os.path.join(ROOT, "paper_2206_08301_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _traffic_per_launch(prec, source="mttkrp_tc.cu"):
@@ -675,7 +685,8 @@ def measure_c2b_ttmc(clk, peak, reps=3):
             "alg_frac": ab / (ms * 1e-3) / 1e9 / peak,
             "roofline": {"bound": "hbm", "kernel": "ttmc_fused_kernel", "kernel_ms": kms,
                          "bytes_per_launch": kbytes, "achieved": kbytes / (kms * 1e-3) / 1e9, "peak": peak,
-                         "frac": kbytes / (kms * 1e-3) / 1e9 / peak},
+                         "frac": kbytes / (kms * 1e-3) / 1e9 / peak,
+                         "traffic": _traffic_per_launch("ttmc_split_bf16", "ttmc_tc.cu")},
             "plain_chain_ms": ms_plain, "speedup_vs_plain_chain": ms_plain / ms, "launches_per_step": launches,
             "rel_err": oracle.rel_error(got, ref), "max_elem_err": oracle.max_elem_error(got, ref),
             "sample": "2 kept-mode slices (2 x 32^3 outputs)", "device_status": status,
