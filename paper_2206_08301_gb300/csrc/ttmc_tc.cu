@@ -11,11 +11,11 @@
 //     tcgen05.mma against the split factor tiles, FP32 accumulation in TMEM;
 //   stage 2 (tensor cores, I_{N-2} <= 256): the epilogue warps split each T1
 //     tile into BF16 hi / lo and write it to shared memory as an MN-major operand
-//     (row k, n = (part, d)); one epilogue thread issues
+//     (row k, n = (part, d)); a warp of its own issues
 //       D2[c, (p, d)] += sum_k U_{N-2}[k, c] T1_p[k, d]
 //     for both parts of U_{N-2} (resident split tiles, K-major) into a per-slab
-//     TMEM accumulator, and quadrant 0 reads D2 (lanes = c) once the slab is
-//     complete and writes T2.  Slabs with I_{N-2} <= 64 (<= 32) share a tile two
+//     TMEM accumulator (rows c on TMEM lanes 96 + c), and another warp reads D2 once
+//     the slab is complete and writes T2.  Slabs with I_{N-2} <= 64 (<= 32) share a tile two
 //     (four) at a time, 128 / SG rows apart, each contracted over its own rows, so
 //     that short slabs still fill the tensor-core tile.  The stage-2 issue never
 //     blocks the stage-1 issue: separate threads, separate commits.
@@ -30,7 +30,8 @@
 // CTA in a fixed order (deterministic, no reduction pass).
 //
 // Warp roles: 0-7 converters, 8-11 epilogue (stage 2), 12 TMEM + stage-1 MMA
-// issue, 13 TMA.  Every wait is bounded (mbar_wait); the epilogue warps meet only
+// issue, 13 TMA; with the tensor-core stage 2 also 14 (stage-2 MMA issue) and 15
+// (T2 write-out from TMEM lanes 96-127).  Every wait is bounded (mbar_wait); the epilogue warps meet only
 // through mbarriers (tensor-core stage 2: b2full / b2free for the T1 operand,
 // d2full / d2free for the TMEM accumulators; CUDA-core stage 2: ufree for the U
 // slots, t1full / t1free for the partial blocks), so a time-out anywhere ends
@@ -49,14 +50,19 @@ namespace {
 
 // RC: rows of X not 16-byte aligned, loaded through the four row-class tensor maps (four
 // class boxes per chunk, 34 KB a stage: two raw stages instead of three).
-template <bool RC = false> struct TtmcCfg {
+// TC2: stage 2 on the tensor cores, with two more warps: 14 issues the stage-2 MMAs and 15
+// reads the finished slabs' T2 out of TMEM (a 448-thread block is checked as 16 warps for
+// its registers anyway, so they cost no registers).
+template <bool RC = false, bool TC2 = false> struct TtmcCfg {
     static constexpr int RP = 32;                          // padded R_{N-1} and R_{N-2}
     static constexpr int N = 2 * RP;                       // rows of the split factor tile (hi, then lo)
     static constexpr int RS = RC ? 2 : 3;                  // raw X stages
     static constexpr int AS = 2;                           // operand stages
     static constexpr int MMA_WARP = CONV_WARPS + EPI_WARPS;
     static constexpr int TMA_WARP = MMA_WARP + 1;
-    static constexpr int WARPS = TMA_WARP + 1;
+    static constexpr int S2_WARP = TMA_WARP + 1;            // TC2: stage-2 issue (lane 0)
+    static constexpr int T2_WARP = TMA_WARP + 2;            // TC2: T2 writer (TMEM lanes 96-127)
+    static constexpr int WARPS = TC2 ? TMA_WARP + 3 : TMA_WARP + 1;
     static constexpr int THREADS = WARPS * 32;
     static constexpr int RAW_BYTES = BM * BK * 4;           // one box of the tensor map
     static constexpr int RAW_STAGE = RC ? kRcRawBytes : RAW_BYTES;
@@ -120,9 +126,9 @@ __device__ __forceinline__ float4 *t1_slot(float *t1s, int r, int x) {
 // RC: X through the row-class maps a.xrow (rows of I_{N-1} words not 16-byte aligned;
 // one slab per tile, the tile's rows s I_{N-2} + 128 kt + l as in the MTTKRP case-0 view).
 template <bool STORE, int SG, bool TC2, bool RC>
-__global__ void __launch_bounds__(TtmcCfg<RC>::THREADS, 1)
+__global__ void __launch_bounds__(TtmcCfg<RC, TC2>::THREADS, 1)
 ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
-    using C = TtmcCfg<RC>;
+    using C = TtmcCfg<RC, TC2>;
     constexpr int RS = C::RS, AS = C::AS, RP = C::RP;
     static_assert(!STORE || (SG == 1 && !TC2), "the last-mode TTM keeps one slab per tile");
     static_assert(TC2 || SG == 1, "packed slabs take the tensor-core stage 2");
@@ -382,36 +388,23 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             }
         }
     } else if constexpr (TC2) {
-        // ---------------------------------- epilogue (tensor-core stage 2 feed)
-        // Per tile: each thread takes its T1 row (TMEM lane = tile row = k) from the
-        // stage-1 accumulator, splits it into BF16 hi / lo and writes it as row k of an
-        // MN-major B2 tile (n = d for hi, 32 + d for lo).  The slabs a tile completes are
-        // written out one tile later (so that their stage-2 MMAs never hold up the next
-        // tile's feed): quadrant 0 (TMEM lanes 0-31 = c) reads each slab's D2 slot and
-        // writes T2[s, c, :].
-        const int quad = warp & 3;
-        const int row = quad * 32 + lane;
+        // ------------------------------ tensor-core stage 2: feed, issue, write-out
+        // Epilogue warps 8-11 (feed): per tile, each thread takes its T1 row (TMEM lane =
+        // tile row = k) from the stage-1 accumulator, splits it into BF16 hi / lo and writes
+        // it as row k of an MN-major B2 tile (n = d for hi, 32 + d for lo).
+        // Warp 14, lane 0 (issue): per tile, for each slab g of the tile and both parts q of
+        // U_{N-2} = U_hi + U_lo,  D2[slot][c, (p, d)] += sum_k U_q[k, c] T1_p[k, d], with
+        // A = the split U_{N-2} block of part q (K-major) placed so that its rows c land on
+        // the MMA's rows 96 + c (the window starts 96 rows before the block; the rows before
+        // it only feed D rows that nobody reads), B = the split T1 tile (MN-major,
+        // n = (p, d)), k over the slab's rows of the tile.  Its commits track only its own MMAs.
+        // Warp 15 (write-out): TMEM lanes 96-127 = c of each finished slab's D2 slot -> T2.
+        // The three meet only through mbarriers (b2full / b2free, d2full / d2free).
         TIter it;
         it.init(ngroups);
         const int64_t nfg = (it.s1 - it.s) * a.n_kt;
-        int64_t grp = it.s;
-        int kt = 0;
         const bool vec = (a.R3 & 3) == 0;
-        bool ok = true;
-        int64_t pending = -1;                      // slab group whose T2 is still in TMEM
-        // The stage-2 MMAs are issued by lane 0 of quadrant 1 (its commits track only its
-        // own MMAs), so the stage-1 issue never waits on the B2 feed; quadrant 0 writes T2.
-        const bool issuer = (quad == 1 && lane == 0);
-        if (issuer && nfg > 0) {   // the split U_{N-2} tiles stay for the whole kernel
-            mbar_arrive_expect_tx(u2full, uint32_t(a.n_kt) * 16384u);
-            bulk_g2s(u2s_addr, a.U2split, uint32_t(a.n_kt) * 16384u, u2full);
-        }
-        // Stage 2 of tile t (B2 buffer bi): for each slab g of the tile and both parts q of
-        // U_{N-2} = U_hi + U_lo,  D2[slot][c, (p, d)] += sum_k U_q[k, c] T1_p[k, d],
-        // A = the split U_{N-2} block of part q (K-major, rows c; the rows past 32 that the
-        // M = 128 shape also reads come from the following blocks and only feed D rows that
-        // nobody reads), B = the split T1 tile (MN-major, n = (p, d)), k over the slab's
-        // rows of the tile.
+        constexpr uint32_t kD2Lanes = 96u << 16;   // TMEM lane offset of the D2 rows c
         auto issue_stage2 = [&](int64_t t, int bi) -> bool {
             constexpr uint32_t idesc2 = idesc_bf16_f32(BM, 2 * RP) | kIdescBMnMajor;
             constexpr int KP = BM / SG;            // tile rows of one slab
@@ -432,8 +425,8 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 for (int ks = 0; ks < KP / 16; ++ks) {
                     const int ku = 16 * ks;                       // k within the tile's k range
                     const int h = ku >> 6, st = (ku & 63) >> 4;   // 64-k half, 16-k step in it
-                    const uint32_t ahi = u2s_addr + uint32_t(((tk * 2 + 0) * 2 + h) * 4096);
-                    const uint32_t alo = u2s_addr + uint32_t(((tk * 2 + 1) * 2 + h) * 4096);
+                    const uint32_t ahi = u2s_addr + uint32_t(((tk * 2 + 0) * 2 + h) * 4096) - 12288u;
+                    const uint32_t alo = u2s_addr + uint32_t(((tk * 2 + 1) * 2 + h) * 4096) - 12288u;
                     const uint64_t adv = uint64_t(st * 32) >> 4;
                     const uint64_t db =
                         desc_mnmajor_sw128(b2_addr(bi) + uint32_t(((g * KP + ku) >> 3) * 1024), 1024u, 1024u);
@@ -453,7 +446,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                                 mbar_wait(d2full(slot), uint32_t((j / C::D2_SLOTS) & 1), abort_flag, status, wlim)))
                     return false;
                 tc_fence_after();
-                const uint32_t d2 = tmem + uint32_t(C::NACC * C::N + slot * 2 * RP);   // lanes 0-31
+                const uint32_t d2 = tmem + kD2Lanes + uint32_t(C::NACC * C::N + slot * 2 * RP);   // lanes 96-127
                 uint32_t vh[2][16], vl[2][16];   // columns (hi part, d) and (lo part, d)
                 tmem_ld16(d2, vh[0]);
                 tmem_ld16(d2 + 16, vh[1]);
@@ -487,65 +480,66 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             }
             return true;
         };
-        for (int64_t fgi = 0; ok && fgi < nfg; ++fgi) {
-            const int b = int(fgi % C::NACC);
-            const uint32_t jb = uint32_t(fgi / C::NACC);
-            const int bi = int(fgi % nb2);
-            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status, wlim))) break;
-            // the stage-2 MMAs of the tile that last used this B2 buffer have read it
-            if (fgi >= nb2 && !__all_sync(0xffffffffu, mbar_wait(b2free(bi), uint32_t(((fgi / nb2) & 1) ^ 1),
-                                                                 abort_flag, status, wlim)))
-                break;
-            tc_fence_after();
-            const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
-            uint32_t ph[RP / 2], pl[RP / 2];   // T1 row: packed BF16 pairs, hi and lo parts
-            #pragma unroll
-            for (int c0 = 0; c0 < RP; c0 += 16) {
-                uint32_t hi[16], lo[16];
-                tmem_ld16(taddr + uint32_t(c0), hi);
-                tmem_ld16(taddr + uint32_t(RP + c0), lo);
-                tmem_wait_ld();
-                #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    split2(__uint_as_float(hi[2 * q]) + __uint_as_float(lo[2 * q]),
-                           __uint_as_float(hi[2 * q + 1]) + __uint_as_float(lo[2 * q + 1]), ph[c0 / 2 + q],
-                           pl[c0 / 2 + q]);
+        if (warp == C::S2_WARP) {
+            if (lane == 0 && nfg > 0) {
+                // the split U_{N-2} tiles stay for the whole kernel
+                mbar_arrive_expect_tx(u2full, uint32_t(a.n_kt) * 16384u);
+                bulk_g2s(u2s_addr, a.U2split, uint32_t(a.n_kt) * 16384u, u2full);
+                for (int64_t fgi = 0; fgi < nfg; ++fgi)
+                    if (!issue_stage2(fgi, int(fgi % nb2))) break;
+                // the U_{N-2} copy has landed and every stage-2 MMA has completed before exit
+                // (and before TMEM is released), also when the loop ended early
+                mbar_drain(u2full, 0u, status);
+                mma_commit(drain2);
+                mbar_drain(drain2, 0u, status);
             }
-            tc_fence_before();
-            const uint32_t b2 = b2_addr(bi);
-            #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) {
-                sts128(b2 + sw128_mn64_offset(uint32_t(8 * ch), uint32_t(row)), ph[4 * ch], ph[4 * ch + 1],
-                       ph[4 * ch + 2], ph[4 * ch + 3]);
-                sts128(b2 + sw128_mn64_offset(uint32_t(RP + 8 * ch), uint32_t(row)), pl[4 * ch], pl[4 * ch + 1],
-                       pl[4 * ch + 2], pl[4 * ch + 3]);
-            }
-            fence_proxy_async_smem();   // the B2 stores before the tensor-core reads
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(acce(b));
-                mbar_arrive(b2full(bi));
+        } else if (warp == C::T2_WARP) {
+            for (int64_t pg = it.s; pg < it.s1; ++pg)
+                if (!write_t2(pg)) break;
+        } else {
+            const int quad = warp & 3;
+            const int row = quad * 32 + lane;
+            for (int64_t fgi = 0; fgi < nfg; ++fgi) {
+                const int b = int(fgi % C::NACC);
+                const uint32_t jb = uint32_t(fgi / C::NACC);
+                const int bi = int(fgi % nb2);
+                if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, status, wlim))) break;
+                // the stage-2 MMAs of the tile that last used this B2 buffer have read it
+                if (fgi >= nb2 && !__all_sync(0xffffffffu, mbar_wait(b2free(bi), uint32_t(((fgi / nb2) & 1) ^ 1),
+                                                                     abort_flag, status, wlim)))
+                    break;
+                tc_fence_after();
+                const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::N);
+                uint32_t ph[RP / 2], pl[RP / 2];   // T1 row: packed BF16 pairs, hi and lo parts
+                #pragma unroll
+                for (int c0 = 0; c0 < RP; c0 += 16) {
+                    uint32_t hi[16], lo[16];
+                    tmem_ld16(taddr + uint32_t(c0), hi);
+                    tmem_ld16(taddr + uint32_t(RP + c0), lo);
+                    tmem_wait_ld();
+                    #pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        split2(__uint_as_float(hi[2 * q]) + __uint_as_float(lo[2 * q]),
+                               __uint_as_float(hi[2 * q + 1]) + __uint_as_float(lo[2 * q + 1]), ph[c0 / 2 + q],
+                               pl[c0 / 2 + q]);
+                }
+                tc_fence_before();
+                const uint32_t b2 = b2_addr(bi);
+                #pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    sts128(b2 + sw128_mn64_offset(uint32_t(8 * ch), uint32_t(row)), ph[4 * ch], ph[4 * ch + 1],
+                           ph[4 * ch + 2], ph[4 * ch + 3]);
+                    sts128(b2 + sw128_mn64_offset(uint32_t(RP + 8 * ch), uint32_t(row)), pl[4 * ch], pl[4 * ch + 1],
+                           pl[4 * ch + 2], pl[4 * ch + 3]);
+                }
+                fence_proxy_async_smem();   // the B2 stores before the tensor-core reads
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(acce(b));
+                    mbar_arrive(b2full(bi));
+                }
             }
-            if (quad == 0 && pending >= 0 && !write_t2(pending)) ok = false;   // the previous tile's slabs
-            pending = -1;
-            if (quad == 1) {
-                bool s2 = true;
-                if (issuer) s2 = issue_stage2(fgi, bi);
-                if (!__all_sync(0xffffffffu, s2)) ok = false;
-            }
-            if (++kt == a.n_kt) {
-                kt = 0;
-                pending = grp;
-                ++grp;
-            }
-        }
-        if (ok && quad == 0 && pending >= 0) write_t2(pending);
-        // the U_{N-2} copy has landed and every stage-2 MMA has completed before exit
-        // (and before TMEM is released), also when the loop ended early
-        if (issuer && nfg > 0) {
-            mbar_drain(u2full, 0u, status);
-            mma_commit(drain2);
-            mbar_drain(drain2, 0u, status);
         }
     } else {
         // ------------------------------------ epilogue (stage 2), one slab per tile
@@ -726,7 +720,7 @@ __global__ void pad_factor_kernel(const float *__restrict__ U, int64_t rows, int
 namespace {
 template <bool STORE, int SG, bool TC2, bool RC = false>
 int launch_ttmc_variant(const TtmcArgs &a, int n_sm, void *stream) {
-    using C = TtmcCfg<RC>;
+    using C = TtmcCfg<RC, TC2>;
     cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel<STORE, SG, TC2, RC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
     if (e != cudaSuccess) return int(e);
