@@ -534,8 +534,8 @@ void plan_ttmc_chain(deinsum_plan_s *pl) {
 // Split-BF16 TTMc: modes N-2 and N-1 are contracted by the fused kernel;
 // the other contracted modes follow in the same greedy order on
 // T2 = [I_0 .. I_{N-3}, R_{N-2}, R_{N-1}].  Offered when the kept mode is
-// below N-2 and R_{N-2}, R_{N-1} <= 32; I_{N-1} must be a multiple of 4 (rows of
-// X 16-byte aligned for the tensor map).
+// below N-2 and R_{N-2}, R_{N-1} <= 32; rows of X (I_{N-1} words) that are not
+// 16-byte aligned take the row-class tensor maps (one slab per tile).
 // Merge the inner mode of a tensor-core MTTKRP with its neighbour when the inner mode is
 // short (at most two 64-wide chunks, so that every fiber group would be one or two chunks
 // and the epilogue and its handshakes would run per 32 KB of X) and the merged view still
@@ -586,6 +586,15 @@ deinsum_status plan_ttmc_fused(deinsum_plan_s *pl) {
     pl->ttm_rest.clear();
     for (int m : pl->ttm_order)
         if (m < N - 2) pl->ttm_rest.push_back(m);
+    // among modes of equal R_m / I_m (the same flops either way) the lower mode first: its TTM
+    // then has the long trailing extent, which the strided TTM kernel tiles without a ragged
+    // edge, and the later, smaller stages take the ragged ones (60^5 R 24: 0.41 -> 0.37 ms)
+    std::stable_sort(pl->ttm_rest.begin(), pl->ttm_rest.end(), [&](int x, int y) {
+        const double rx = double(pl->ranks[x]) / double(pl->dims[x]);
+        const double ry = double(pl->ranks[y]) / double(pl->dims[y]);
+        if (rx != ry) return rx < ry;
+        return x < y;
+    });
     int64_t cur[DEINSUM_MAX_ORDER];
     for (int m = 0; m < N; ++m) cur[m] = (m >= N - 2) ? pl->ranks[m] : pl->dims[m];
     int64_t mx = 1;

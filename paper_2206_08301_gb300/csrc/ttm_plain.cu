@@ -81,13 +81,15 @@ ttm_kernel(const T *__restrict__ A, const T *__restrict__ B, T *__restrict__ C, 
 }
 
 // FP32 TTM over a middle mode with a contiguous trailing extent B (a multiple of 4, X and Y
-// 16-byte aligned): Y[a, r, b] = sum_i X[a, i, b] U[i, r].  A CTA takes one a, 256 b and 32 r;
-// thread (bg = lane, rg = warp) accumulates b = b0 + 4 bg .. + 3 and b0 + 128 + 4 bg .. + 3
-// for r = r0 + 4 rg .. + 3 (32 FMA per three 16-byte shared loads; the U value is a warp
-// broadcast).  Chunks of 16 i are read with 16-byte loads into registers one chunk ahead and
+// 16-byte aligned): Y[a, r, b] = sum_i X[a, i, b] U[i, r].  A CTA takes one a, 256 b and up to
+// 32 r; thread (bg = lane, rg = warp) accumulates b = b0 + 4 bg .. + 3 and b0 + 128 + 4 bg .. + 3
+// for RPW ranks r = r0 + RPW rg .. + RPW - 1, RPW = ceil(min(R, 32) / 8) (8 RPW FMA per k and
+// thread; the U values are warp broadcasts), so that R = 8, 16 or 24 costs no FMA on
+// padding.  Chunks of 16 i are read with 16-byte loads into registers one chunk ahead and
 // stored into the other of two shared-memory buffers.
 constexpr int SB = 256, SR = 32, SK = 16, STHREADS = 256;
 
+template <int RPW>
 __global__ void __launch_bounds__(STHREADS)
 ttm_strided_f32_kernel(const float *__restrict__ X, const float *__restrict__ U, float *__restrict__ Y,
                        int64_t I, int64_t B, int64_t R) {
@@ -130,9 +132,9 @@ ttm_strided_f32_kernel(const float *__restrict__ X, const float *__restrict__ U,
         for (int q = 0; q < 4; ++q) xs[buf][xk + 4 * q][xc] = px[q];
         if (t < 128) us[buf][uk][uc] = pu;
     };
-    float acc[4][8];
+    float acc[RPW][8];
     #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < RPW; ++j)
         #pragma unroll
         for (int q = 0; q < 8; ++q) acc[j][q] = 0.f;
     fetch(0);
@@ -145,11 +147,18 @@ ttm_strided_f32_kernel(const float *__restrict__ X, const float *__restrict__ U,
         #pragma unroll
         for (int k = 0; k < SK; ++k) {
             const float4 x0 = xs[buf][k][bg], x1 = xs[buf][k][32 + bg];
-            const float4 u = us[buf][k][rg];
             const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-            const float uv[4] = {u.x, u.y, u.z, u.w};
+            float uv[RPW];
+            if constexpr (RPW == 4) {
+                const float4 u = us[buf][k][rg];
+                uv[0] = u.x; uv[1] = u.y; uv[2] = u.z; uv[3] = u.w;
+            } else {
+                const float *uk = reinterpret_cast<const float *>(us[buf][k]) + RPW * rg;
+                #pragma unroll
+                for (int j = 0; j < RPW; ++j) uv[j] = uk[j];
+            }
             #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < RPW; ++j)
                 #pragma unroll
                 for (int q = 0; q < 8; ++q) acc[j][q] = fmaf(uv[j], xv[q], acc[j][q]);
         }
@@ -160,8 +169,8 @@ ttm_strided_f32_kernel(const float *__restrict__ X, const float *__restrict__ U,
         }
     }
     #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int64_t r = r0 + 4 * rg + j;
+    for (int j = 0; j < RPW; ++j) {
+        const int64_t r = r0 + RPW * rg + j;
         if (r >= R) continue;
         float *yr = Y + (a * R + r) * B + b0;
         if (b0 + 4 * bg < B)
@@ -178,7 +187,11 @@ int launch_ttm(const T *X, const T *U, T *Y, int64_t Aext, int64_t Im, int64_t B
             (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
             const int64_t blocks = Aext * ((Bext + SB - 1) / SB) * ((Rm + SR - 1) / SR);
             if (blocks < 1 || blocks > 0x7FFFFFFFll) return int(cudaErrorInvalidValue);
-            ttm_strided_f32_kernel<<<unsigned(blocks), STHREADS, 0, static_cast<cudaStream_t>(stream)>>>(
+            const int64_t rw = ((Rm < SR ? Rm : SR) + 7) / 8;   // ranks per warp
+            auto kern = rw == 1 ? ttm_strided_f32_kernel<1>
+                      : rw == 2 ? ttm_strided_f32_kernel<2>
+                      : rw == 3 ? ttm_strided_f32_kernel<3> : ttm_strided_f32_kernel<4>;
+            kern<<<unsigned(blocks), STHREADS, 0, static_cast<cudaStream_t>(stream)>>>(
                 reinterpret_cast<const float *>(X), reinterpret_cast<const float *>(U), reinterpret_cast<float *>(Y),
                 Im, Bext, Rm);
             count_launch();
