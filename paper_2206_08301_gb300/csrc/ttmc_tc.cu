@@ -133,6 +133,12 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     static_assert(!STORE || (SG == 1 && !TC2), "the last-mode TTM keeps one slab per tile");
     static_assert(TC2 || SG == 1, "packed slabs take the tensor-core stage 2");
     static_assert(!RC || SG == 1, "row classes keep one slab per tile");
+    // Packed short slabs (one 64-wide l chunk per tile at most once the tile is full, so the
+    // T1 feed runs per chunk): stage 1 takes three split products (X_hi U_hi + X_hi U_lo +
+    // X_lo U_hi) into RP accumulator columns, halving the feed's TMEM reads; the other
+    // variants keep two MMAs of N = 2 RP (four products), whose 8 dependent MMAs per chunk
+    // keep pace with long slabs where 12 did not.
+    constexpr bool S1THREE = TC2 && SG > 1;
     constexpr uint32_t kTmemCols = TC2 ? C::TMEM_COLS_TC2 : C::TMEM_COLS;
     const int64_t ngroups = (a.S + SG - 1) / SG;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -294,7 +300,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     } else if (warp == C::MMA_WARP) {
         // -------------------------------------------------------------- MMA issue
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(BM, C::N);
+            constexpr uint32_t idesc = idesc_bf16_f32(BM, S1THREE ? RP : C::N);
             TIter it;
             it.init(ngroups);
             const int64_t nfg = (it.s1 - it.s) * a.n_kt;
@@ -318,10 +324,12 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                     const uint64_t dh = desc_kmajor_sw128(a_hi(s));
                     const uint64_t dl = desc_kmajor_sw128(a_lo(s));
                     const uint64_t db = desc_kmajor_sw128(b_t(s));
+                    const uint64_t dbl = desc_kmajor_sw128(b_t(s) + uint32_t(RP * 128));   // U_lo rows
                     #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint64_t adv = uint64_t(kk * 32) >> 4;  // 32 bytes per K=16 step
                         mma_bf16(dcol, dh + adv, db + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                        if constexpr (S1THREE) mma_bf16(dcol, dh + adv, dbl + adv, idesc, 1u);
                         mma_bf16(dcol, dl + adv, db + adv, idesc, 1u);
                     }
                     mma_commit(a_empty(s));
@@ -516,13 +524,17 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 for (int c0 = 0; c0 < RP; c0 += 16) {
                     uint32_t hi[16], lo[16];
                     tmem_ld16(taddr + uint32_t(c0), hi);
-                    tmem_ld16(taddr + uint32_t(RP + c0), lo);
+                    if constexpr (!S1THREE) tmem_ld16(taddr + uint32_t(RP + c0), lo);
                     tmem_wait_ld();
                     #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        split2(__uint_as_float(hi[2 * q]) + __uint_as_float(lo[2 * q]),
-                               __uint_as_float(hi[2 * q + 1]) + __uint_as_float(lo[2 * q + 1]), ph[c0 / 2 + q],
-                               pl[c0 / 2 + q]);
+                    for (int q = 0; q < 8; ++q) {
+                        float x0 = __uint_as_float(hi[2 * q]), x1 = __uint_as_float(hi[2 * q + 1]);
+                        if constexpr (!S1THREE) {
+                            x0 += __uint_as_float(lo[2 * q]);
+                            x1 += __uint_as_float(lo[2 * q + 1]);
+                        }
+                        split2(x0, x1, ph[c0 / 2 + q], pl[c0 / 2 + q]);
+                    }
                 }
                 tc_fence_before();
                 const uint32_t b2 = b2_addr(bi);
