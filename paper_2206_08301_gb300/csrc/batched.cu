@@ -6,15 +6,16 @@
 //
 // Host side: every instance is classified by a regular plan (Sec. III-B MTTKRP
 // einsum); its row view is cut into work units (column of 128 output rows x a
-// range of fiber groups) of about `unit_bytes` of X each; the units are assigned
-// to the CTAs largest first (LPT: each unit goes to the least-loaded CTA, by a
-// cost per unit that counts its chunks and fiber-group epilogues), so that one
-// CTA per SM finishes them together, and each CTA's list is then grouped by
-// kind of instance, so that its warps run one specialised loop at a time.  The
-// granularity is picked by an autotuner that times candidate schedules on the
-// device and remembers the winner per batch signature.
+// range of fiber groups) of about `unit_bytes` of X each; the units form one list,
+// grouped by kind of instance and largest first within a kind (by a cost that counts
+// a unit's chunks and fiber-group epilogues), which the persistent CTAs take in order
+// from a device ticket counter: each CTA takes its next unit when it is ready for one,
+// so that they finish together whatever the cost model misjudges, and a CTA stays
+// within one kind's specialised loop for long stretches.  The granularity is picked by
+// an autotuner that times candidate schedules on the device and remembers the winner
+// per batch signature.
 // Device side: a batched split of the instances' inner factors, the batched
-// tensor-core kernel (mttkrp_tc.cu), and a batched fixed-order reduction of
+// tensor-core kernel (mttkrp_tc_batched.cu), and a batched fixed-order reduction of
 // the unit partials into each instance's output.  With plain precision the
 // batch runs as separate launches of the plain kernel (the baseline).
 #include <cuda_runtime.h>
@@ -154,8 +155,7 @@ struct deinsum_batch_s {
     int unit_div = 4;   // units of about total / (grid * unit_div) bytes
     int n_sm = 0, grid = 0;          // CTAs of the launch (one per SM, at most one per unit)
     // schedule (host)
-    std::vector<int64_t> units;      // 5 per unit, grouped by CTA
-    std::vector<int64_t> cta_begin;  // grid + 1 (indices into units)
+    std::vector<int64_t> units;      // 5 per unit, in the order the CTAs take them
     std::vector<int64_t> red_off;    // partial offsets, per instance, column, split
     std::vector<int64_t> red_col;    // per instance: n_cols + 1 starts into red_off
     std::vector<int64_t> red_col_base;
@@ -166,7 +166,7 @@ struct deinsum_batch_s {
     // device
     char *ws = nullptr;
     size_t ws_bytes = 0;
-    size_t o_status = 0, o_insts = 0, o_split = 0, o_red = 0, o_units = 0, o_cta = 0, o_redoff = 0, o_redcol = 0,
+    size_t o_status = 0, o_insts = 0, o_split = 0, o_red = 0, o_units = 0, o_ticket = 0, o_redoff = 0, o_redcol = 0,
            o_bsplit = 0, o_wtab = 0, o_partial = 0, o_end = 0;
     char *staging = nullptr;  // pinned: insts + split table + reduce table
     size_t staging_bytes = 0;
@@ -193,7 +193,7 @@ double unit_cost(const Inst &in, int64_t fgs) {
     return double(fgs) * (double(in.g.n_kb) * chunk + double(in.g.R_pad) / 128.0);
 }
 
-// Units of about total / (grid * unit_div) bytes of X; LPT assignment to CTAs.
+// Units of about total / (grid * unit_div) bytes of X, in the order the CTAs take them.
 void build_batch_schedule(deinsum_batch_s *b) {
     const int64_t target_units = int64_t(b->n_sm) * b->unit_div;
     const double unit_bytes = std::max(1.0, b->total_bytes / double(target_units));
@@ -237,39 +237,26 @@ void build_batch_schedule(deinsum_batch_s *b) {
         b->wtab_bytes += up(wf * 4, 256);
         b->max_wtab_floats = std::max<int64_t>(b->max_wtab_floats, int64_t(wf));
     }
-    // all units over the CTAs of one launch, largest first onto the least-loaded CTA, then
-    // each CTA's list grouped by kind of instance (stable: largest first within a kind)
+    // one global list of units that the launch's CTAs take in order from a device ticket
+    // counter: grouped by kind of instance (the kernel's specialised loops; a CTA then stays in
+    // one kind for long stretches), largest first within a kind, so that the last units taken
+    // are the smallest
     b->units.clear();
-    b->cta_begin.clear();
     std::vector<size_t> order(all.size());
     for (size_t k = 0; k < all.size(); ++k) order[k] = k;
-    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(b->n_sm, int64_t(all.size()))));
-    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return all[x].cost > all[y].cost; });
-    using Load = std::pair<double, int>;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (int c = 0; c < grid; ++c) heap.push({0.0, c});
-    std::vector<std::vector<size_t>> per_cta(static_cast<size_t>(grid));
+    auto key = [&](size_t k) {   // kind of load, then operand layout
+        const Inst &in = b->inst[size_t(all[k].inst)];
+        return 2 * in.kind + in.g.kcase;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        if (key(x) != key(y)) return key(x) < key(y);
+        return all[x].cost > all[y].cost;
+    });
     for (size_t k : order) {
-        Load top = heap.top();
-        heap.pop();
-        per_cta[size_t(top.second)].push_back(k);
-        heap.push({top.first + all[k].cost, top.second});
+        const U &u = all[k];
+        b->units.insert(b->units.end(), {u.inst, u.col, u.f0, u.f1, u.off});
     }
-    for (int c = 0; c < grid; ++c) {
-        std::vector<size_t> &lst = per_cta[size_t(c)];
-        auto key = [&](size_t k) {   // kind of load, then operand layout (the kernel's specialised loops)
-            const Inst &in = b->inst[size_t(all[k].inst)];
-            return 2 * in.kind + in.g.kcase;
-        };
-        std::stable_sort(lst.begin(), lst.end(), [&](size_t x, size_t y) { return key(x) < key(y); });
-        b->cta_begin.push_back(int64_t(b->units.size() / 5));
-        for (size_t k : lst) {
-            const U &u = all[k];
-            b->units.insert(b->units.end(), {u.inst, u.col, u.f0, u.f1, u.off});
-        }
-    }
-    b->cta_begin.push_back(int64_t(b->units.size() / 5));
-    b->grid = grid;
+    b->grid = int(std::max<int64_t>(1, std::min<int64_t>(b->n_sm, int64_t(all.size()))));
 }
 
 deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
@@ -285,7 +272,7 @@ deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
     b->o_split = take(sizeof(SplitInst) * size_t(b->n), 64);
     b->o_red = take(sizeof(RedInst) * size_t(b->n), 64);
     b->o_units = take(b->units.size() * 8, 256);
-    b->o_cta = take(b->cta_begin.size() * 8, 256);
+    b->o_ticket = take(8, 256);
     b->o_redoff = take(b->red_off.size() * 8, 256);
     b->o_redcol = take(b->red_col.size() * 8, 256);
     b->o_bsplit = take(b->bsplit_bytes, 1024);
@@ -315,7 +302,6 @@ deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
     }
     cudaMemsetAsync(b->ws + b->o_status, 0, 256, s);
     cudaMemcpyAsync(b->ws + b->o_units, b->units.data(), b->units.size() * 8, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(b->ws + b->o_cta, b->cta_begin.data(), b->cta_begin.size() * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(b->ws + b->o_redoff, b->red_off.data(), b->red_off.size() * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(b->ws + b->o_redcol, b->red_col.data(), b->red_col.size() * 8, cudaMemcpyHostToDevice, s);
     b->tables_uploaded = true;
@@ -377,7 +363,9 @@ deinsum_status launch_batch(deinsum_batch_s *b, cudaStream_t s) {
     ba.units = reinterpret_cast<const int64_t *>(b->ws + b->o_units);
     ba.partial = reinterpret_cast<float *>(b->ws + b->o_partial);
     ba.status = reinterpret_cast<int *>(b->ws + b->o_status);
-    ba.cta_begin = reinterpret_cast<const int64_t *>(b->ws + b->o_cta);
+    ba.n_units = int64_t(b->units.size() / 5);
+    ba.ticket = reinterpret_cast<unsigned long long *>(b->ws + b->o_ticket);
+    if (cudaMemsetAsync(ba.ticket, 0, sizeof(unsigned long long), s) != cudaSuccess) return DEINSUM_ERR_CUDA;
     if (launch_mttkrp_tc_batched(ba, b->grid, s)) return DEINSUM_ERR_CUDA;
     int64_t maxo = 1;
     for (auto &i : b->inst) maxo = std::max<int64_t>(maxo, i.g.I * i.g.R);

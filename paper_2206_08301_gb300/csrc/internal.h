@@ -108,14 +108,16 @@ struct MttkrpArgs {
 
 // Many MTTKRP instances in one persistent launch of the tensor-core kernel: per-instance
 // arguments (geometry, TMA descriptors of X, factor pointers, split factor tiles) live in
-// device memory; every CTA walks its own list of units, each unit = (instance, column,
-// first fiber group, end, offset of its 128 x R_pad partial block in `partial`).  The
-// kernel reads how an instance loads X (tensor map or row classes, the operand layout of
-// its mode) from its arguments, once per unit.
+// device memory; the units, each = (instance, column, first fiber group, end, offset of
+// its 128 x R_pad partial block in `partial`), form one list that the CTAs take in order
+// from the ticket counter (zero at launch).  The kernel reads how an instance loads X
+// (tensor map or row classes, the operand layout of its mode) from its arguments, once
+// per unit.
 struct BatchArgs {
     const MttkrpArgs *insts;
     const int64_t *units;       // 5 per unit
-    const int64_t *cta_begin;   // units of CTA c: cta_begin[c] .. cta_begin[c+1] - 1
+    int64_t n_units;
+    unsigned long long *ticket; // next unit to hand out
     float *partial;
     int *status;
     uint64_t wait_ns;           // limit of a pipeline wait (set by the launcher)

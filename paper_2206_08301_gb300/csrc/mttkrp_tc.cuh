@@ -52,11 +52,14 @@ template <int RP, bool THREE = false> struct TcCfg {
     // groups would otherwise hold the MMAs up behind the epilogue
     static constexpr int NACC = THREE ? 4 : 2;
     static constexpr int TMEM_COLS = NACC * ACC < 32 ? 32 : NACC * ACC;   // a power of two, >= 32
-    static constexpr int NBARS = 2 * RS + 3 * AS + 2 * NACC + 1 + 2 * WSLOTS;
+    // batched kernel: a ring of NQ unit tickets (the TMA thread takes each from the device
+    // counter and hands it to the other roles: qfull / qempty)
+    static constexpr int NQ = THREE ? 8 : 0;
+    static constexpr int NBARS = 2 * RS + 3 * AS + 2 * NACC + 1 + 2 * WSLOTS + 2 * NQ;
     static constexpr size_t SMEM = size_t(RS) * RAW_STAGE + size_t(AS) * ASTAGE_BYTES + WBUF_BYTES + 1024 + 512;
     static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB per-CTA limit");
     static_assert(RAW_BYTES <= RAW_STAGE, "a tensor-map box fits a raw stage");
-    static_assert(NBARS * 8 + 8 <= 512, "barrier area");
+    static_assert(NBARS * 8 + 8 + NQ * 8 <= 512, "barrier area (+ TMEM holder, abort flag, ticket ring)");
 };
 
 struct Iter {

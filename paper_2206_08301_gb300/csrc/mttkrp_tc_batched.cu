@@ -22,9 +22,12 @@ using namespace sm100;
 
 // ---------------------------------------------------------------------------
 // Batched form: one persistent launch over the work units of every instance.
-// Each CTA walks the unit list the host assigned to it (largest first over the
-// CTAs, then grouped by how the unit's instance loads X); every unit names its
-// instance, whose arguments sit in device memory.  Each role reads a unit's
+// The CTAs take units in order from one list (grouped by how the unit's instance
+// loads X, largest first within a group) through a device ticket counter: the TMA
+// thread takes each ticket and hands it to the CTA's other roles through a small
+// shared-memory ring, so a CTA takes its next unit only when its pipeline is ready
+// for one and all CTAs finish together.  Every unit names its instance, whose
+// arguments sit in device memory.  Each role reads a unit's
 // fields once and runs its chunks in code specialised for the instance's loads
 // (tensor map or row classes, K-major or MN-major operand) and, in the epilogue,
 // for its padded rank, so that all kinds of instance share one launch and one
@@ -77,7 +80,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
     int *status = bargs.status;
     const uint64_t wlim = bargs.wait_ns;
-    const int64_t ubeg = bargs.cta_begin[blockIdx.x], uend = bargs.cta_begin[blockIdx.x + 1];
+    int64_t *uring = reinterpret_cast<int64_t *>(tmem_holder + 2);   // NQ unit tickets
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t raw_s = smem_u32(raw_base), a_s = smem_u32(a_base);
@@ -96,10 +99,44 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     const uint32_t drain = smem_u32(bars + AB + 2 * C::NACC);
     auto wfull = [&](int s) { return smem_u32(bars + AB + 2 * C::NACC + 1 + s); };
     auto wempty = [&](int s) { return smem_u32(bars + AB + 2 * C::NACC + 1 + C::WSLOTS + s); };
+    constexpr int QB = AB + 2 * C::NACC + 1 + 2 * C::WSLOTS;   // the ticket ring's barriers
+    auto qfull = [&](int s) { return smem_u32(bars + QB + s); };
+    auto qempty = [&](int s) { return smem_u32(bars + QB + C::NQ + s); };
+    // readers of each ticket: the eight converter warps, the MMA thread, the four epilogue warps
+    constexpr uint32_t kQReaders = CONV_WARPS + 1 + EPI_WARPS;
     auto wslot_addr = [&](int s) { return smem_u32(wbuf) + uint32_t(s) * uint32_t(C::WSLOT_FLOATS) * 4u; };
     // unit u: its instance's arguments and (column, first fiber group, end, partial offset)
     auto unit_args = [&](int64_t u) -> const MttkrpArgs & { return bargs.insts[bargs.units[5 * u]]; };
     auto unit_field = [&](int64_t u, int f) { return bargs.units[5 * u + f]; };
+    // The q-th ticket of this CTA (q = 0, 1, ...): the TMA thread takes the next unit index
+    // from the device counter (-1 once the list is exhausted) and publishes it in ring slot
+    // q mod NQ; every other role reads it from there (a warp reads it with all its lanes,
+    // lane 0 releases the slot).  Every role walks the same tickets in the same order.
+    auto give_ticket = [&](int64_t q, int64_t &u) -> bool {
+        const int slot = int(q % C::NQ);
+        if (!mbar_wait(qempty(slot), uint32_t((q / C::NQ) & 1) ^ 1u, abort_flag, status, wlim)) return false;
+        const int64_t t = int64_t(atomicAdd(bargs.ticket, 1ull));
+        u = t < bargs.n_units ? t : -1;
+        uring[slot] = u;
+        mbar_arrive(qfull(slot));   // release: the slot's value is seen by whoever observes the phase
+        return true;
+    };
+    auto take_ticket_warp = [&](int64_t q, int64_t &u) -> bool {
+        const int slot = int(q % C::NQ);
+        if (!__all_sync(0xffffffffu, mbar_wait(qfull(slot), uint32_t((q / C::NQ) & 1), abort_flag, status, wlim)))
+            return false;
+        u = uring[slot];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(qempty(slot));
+        return true;
+    };
+    auto take_ticket_thread = [&](int64_t q, int64_t &u) -> bool {
+        const int slot = int(q % C::NQ);
+        if (!mbar_wait(qfull(slot), uint32_t((q / C::NQ) & 1), abort_flag, status, wlim)) return false;
+        u = uring[slot];
+        mbar_arrive(qempty(slot));
+        return true;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < RS; ++s) {
@@ -119,6 +156,10 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
         for (int s = 0; s < C::WSLOTS; ++s) {
             mbar_init(wfull(s), 1);
             mbar_init(wempty(s), EPI_WARPS);
+        }
+        for (int s = 0; s < C::NQ; ++s) {
+            mbar_init(qfull(s), 1);
+            mbar_init(qempty(s), kQReaders);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -206,7 +247,9 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             return true;
         };
         bool ok = true;
-        for (int64_t u = ubeg; ok && u < uend; ++u) {
+        int64_t u = 0;
+        for (int64_t q = 0; ok; ++q) {
+            if (!take_ticket_warp(q, u) || u < 0) break;
             const MttkrpArgs &a = unit_args(u);
             const int64_t col = unit_field(u, 1), f0 = unit_field(u, 2), f1 = unit_field(u, 3);
             switch (batch_kind(a)) {
@@ -280,7 +323,9 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 return true;
             };
             bool ok = true;
-            for (int64_t u = ubeg; ok && u < uend; ++u) {
+            int64_t u = 0;
+            for (int64_t q = 0; ok; ++q) {
+                if (!give_ticket(q, u) || u < 0) break;
                 const MttkrpArgs &a = unit_args(u);
                 const int64_t col = unit_field(u, 1), f0 = unit_field(u, 2), f1 = unit_field(u, 3);
                 switch (batch_kind(a)) {
@@ -343,7 +388,9 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 return true;
             };
             bool ok = true;
-            for (int64_t u = ubeg; ok && u < uend; ++u) {
+            int64_t u = 0;
+            for (int64_t q = 0; ok; ++q) {
+                if (!take_ticket_thread(q, u) || u < 0) break;
                 const MttkrpArgs &a = unit_args(u);
                 const int64_t f0 = unit_field(u, 2), f1 = unit_field(u, 3);
                 ok = a.g.kcase == 1 ? run(KindTag<1>{}, a, f0, f1) : run(KindTag<0>{}, a, f0, f1);
@@ -445,7 +492,9 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
             return true;
         };
         bool ok = true;
-        for (int64_t u = ubeg; ok && u < uend; ++u) {
+        int64_t u = 0;
+        for (int64_t q = 0; ok; ++q) {
+            if (!take_ticket_warp(q, u) || u < 0) break;
             const MttkrpArgs &a = unit_args(u);
             const int64_t col = unit_field(u, 1), f0 = unit_field(u, 2), f1 = unit_field(u, 3);
             const int64_t off = unit_field(u, 4);
