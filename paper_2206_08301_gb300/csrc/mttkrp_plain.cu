@@ -310,6 +310,43 @@ __global__ void mttkrp_reduce_kernel(const T *__restrict__ partial, const int64_
     out[idx] = s;
 }
 
+// The same sum for columns with many partial blocks (few output rows, long contracted
+// modes: e.g. mode 0 of an order-5 tensor, hundreds of units in one column): each block
+// takes 32 consecutive output elements; its eight warps each add one contiguous eighth of
+// the column's (unit, row group) terms in order, and thread 0 of each element's slot adds
+// the eight segment sums in order.  The order is fixed by the schedule alone, so results
+// stay bit-reproducible.
+template <typename T>
+__global__ void mttkrp_reduce_seg_kernel(const T *__restrict__ partial, const int64_t *__restrict__ col_begin,
+                                         T *__restrict__ out, int64_t I, int R, int RP, int64_t rows_per_col,
+                                         int64_t G, int narrow) {
+    __shared__ T seg[8][32];
+    const int e = threadIdx.x & 31, sg = threadIdx.x >> 5;
+    const int64_t idx = int64_t(blockIdx.x) * 32 + e;
+    T s = T(0);
+    if (idx < I * R) {
+        const int64_t row = idx / R;
+        const int r = int(idx - row * R);
+        const int64_t col = row / rows_per_col;
+        const int64_t i = row - col * rows_per_col;
+        const int64_t g = narrow ? G : 1;
+        const int64_t u0 = col_begin[col], nterm = (col_begin[col + 1] - u0) * g;
+        const int64_t t0 = nterm * sg / 8, t1 = nterm * (sg + 1) / 8;
+        for (int64_t t = t0; t < t1; ++t) {
+            const int64_t u = u0 + t / g, gi = t - (t / g) * g;
+            s += partial[(u * BM + (narrow ? gi * I + i : i)) * RP + r];
+        }
+    }
+    seg[sg][e] = s;
+    __syncthreads();
+    if (sg == 0 && idx < I * R) {
+        T tot = T(0);
+        #pragma unroll
+        for (int k = 0; k < 8; ++k) tot += seg[k][e];
+        out[idx] = tot;
+    }
+}
+
 // MTTKRP followed by a matrix product (Sec. II-A running example): per output
 // row, M[row, :] is summed from the unit partials in the same fixed order as
 // above into shared memory, then out[row, l] = sum_r M[row, r] C[r, l] (r in
@@ -356,10 +393,18 @@ int launch_reduce(const MttkrpArgs &a, const T *partial, const int64_t *col_begi
         return int(cudaGetLastError());
     }
     const int64_t n = a.g.I * a.g.R;
-    const int threads = 256;
-    const int64_t blocks = (n + threads - 1) / threads;
-    mttkrp_reduce_kernel<T><<<unsigned(blocks), threads, 0, static_cast<cudaStream_t>(stream)>>>(
-        partial, col_begin, static_cast<T *>(out), a.g.I, a.g.R, a.g.R_pad, a.g.rows_per_col, a.g.G, a.g.narrow);
+    // terms per output element: the units of a column times the row groups of a narrow tile
+    const int64_t cols = a.g.n_cols > 0 ? a.g.n_cols : 1;
+    const int64_t terms = (a.n_units + cols - 1) / cols * (a.g.narrow ? a.g.G : 1);
+    if (terms > 64) {
+        mttkrp_reduce_seg_kernel<T><<<unsigned((n + 31) / 32), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+            partial, col_begin, static_cast<T *>(out), a.g.I, a.g.R, a.g.R_pad, a.g.rows_per_col, a.g.G, a.g.narrow);
+    } else {
+        const int threads = 256;
+        const int64_t blocks = (n + threads - 1) / threads;
+        mttkrp_reduce_kernel<T><<<unsigned(blocks), threads, 0, static_cast<cudaStream_t>(stream)>>>(
+            partial, col_begin, static_cast<T *>(out), a.g.I, a.g.R, a.g.R_pad, a.g.rows_per_col, a.g.G, a.g.narrow);
+    }
     count_launch();
     return int(cudaGetLastError());
 }
