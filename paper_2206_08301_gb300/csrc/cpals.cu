@@ -52,6 +52,47 @@ __global__ void __launch_bounds__(128) tree_m0_kernel(const float *__restrict__ 
     if (threadIdx.x < R) M[i * R + threadIdx.x] = ((red[0][r] + red[1][r]) + red[2][r]) + red[3][r];
 }
 
+// The same for R a multiple of 4 (the common case), with 16-byte loads: thread (c, jg) of a
+// block of 256 holds rank columns 4 c .. 4 c + 3 (c < R / 4) and sums j = jg, jg + 32, ...
+// in two independent chains (j 32 apart); the 32 j groups are added in a fixed order.
+__global__ void __launch_bounds__(256) tree_m0_vec_kernel(const float *__restrict__ T, const float *__restrict__ U1,
+                                                          float *__restrict__ M, int64_t J, int R) {
+    const int64_t i = blockIdx.x;
+    const int c = threadIdx.x & 7, jg = threadIdx.x >> 3;
+    const int R4 = R >> 2;
+    __shared__ float4 red[32][8];
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+    if (c < R4) {
+        const float4 *Ti = reinterpret_cast<const float4 *>(T + i * J * R);
+        const float4 *U4 = reinterpret_cast<const float4 *>(U1);
+        int64_t j = jg;
+        for (; j + 32 < J; j += 64) {
+            const float4 t0 = Ti[j * R4 + c], u0 = U4[j * R4 + c];
+            const float4 t1 = Ti[(j + 32) * R4 + c], u1 = U4[(j + 32) * R4 + c];
+            a0.x = fmaf(t0.x, u0.x, a0.x); a0.y = fmaf(t0.y, u0.y, a0.y);
+            a0.z = fmaf(t0.z, u0.z, a0.z); a0.w = fmaf(t0.w, u0.w, a0.w);
+            a1.x = fmaf(t1.x, u1.x, a1.x); a1.y = fmaf(t1.y, u1.y, a1.y);
+            a1.z = fmaf(t1.z, u1.z, a1.z); a1.w = fmaf(t1.w, u1.w, a1.w);
+        }
+        for (; j < J; j += 32) {
+            const float4 t0 = Ti[j * R4 + c], u0 = U4[j * R4 + c];
+            a0.x = fmaf(t0.x, u0.x, a0.x); a0.y = fmaf(t0.y, u0.y, a0.y);
+            a0.z = fmaf(t0.z, u0.z, a0.z); a0.w = fmaf(t0.w, u0.w, a0.w);
+        }
+    }
+    red[jg][c] = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+    __syncthreads();
+    if (threadIdx.x < R) {
+        const int cc = threadIdx.x >> 2, q = threadIdx.x & 3;
+        float t = 0.f;
+        for (int k = 0; k < 32; ++k) {
+            const float4 v = red[k][cc];
+            t += q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+        }
+        M[i * R + threadIdx.x] = t;
+    }
+}
+
 // Dimension tree: M_1[j, r] = sum_i T[i, j, r] U_0[i, r].  Block (jb, is): four j, the
 // i of slice is (kTreeSplit slices); thread (j, r) runs over them in order into
 // part[is][j][r]; tree_m1_sum adds the slices in order.
@@ -81,31 +122,45 @@ bool tree_eligible(int order, const int64_t *dims, int R, deinsum_prec prec) {
            dims[0] < (int64_t(1) << 31) && dims[1] < (int64_t(1) << 31) && dims[2] < (int64_t(1) << 31);
 }
 
-// G = U^T U in FP64 (U: I x R float, row-major).  One block per row r1 of G;
-// thread (r2, slice) sums rows slice, slice + 4, ... of U[i, r1] U[i, r2].
-__global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ U, int64_t I, int R,
-                                                   double *__restrict__ G) {
+// G = U^T U in FP64 (U: I x R float, row-major).  One block per row r1 of G, 1024 threads:
+// thread (r2, slice) sums rows slice, slice + 16, ... of U[i, r1] U[i, r2] in four
+// independent FP32 chains (rows 16 apart), folded into an FP64 accumulator every 8 products
+// per chain (the FP64 pipe is narrow); the 16 slices are added in a fixed order.
+constexpr int kGramSlices = 16;
+__global__ void __launch_bounds__(1024) gram_kernel(const float *__restrict__ U, int64_t I, int R,
+                                                    double *__restrict__ G) {
     const int r1 = blockIdx.x;
     const int r2 = threadIdx.x & 63, sl = threadIdx.x >> 6;
-    __shared__ double red[4][64];
-    // FP32 partial sums of 8 products, accumulated in FP64 (the FP64 pipe is narrow)
+    __shared__ double red[kGramSlices][64];
     double acc = 0.0;
     if (r2 < R) {
-        float part = 0.f;
+        constexpr int64_t step = 4 * kGramSlices;
+        int64_t i = sl;
+        float p[4] = {0.f, 0.f, 0.f, 0.f};
         int cnt = 0;
-        for (int64_t i = sl; i < I; i += 4) {
-            part = fmaf(U[i * R + r1], U[i * R + r2], part);
+        for (; i + 3 * kGramSlices < I; i += step) {
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t row = (i + q * kGramSlices) * R;
+                p[q] = fmaf(U[row + r1], U[row + r2], p[q]);
+            }
             if (++cnt == 8) {
-                acc += double(part);
-                part = 0.f;
+                acc += (double(p[0]) + double(p[1])) + (double(p[2]) + double(p[3]));
+                p[0] = p[1] = p[2] = p[3] = 0.f;
                 cnt = 0;
             }
         }
-        acc += double(part);
+        for (; i < I; i += kGramSlices) p[0] = fmaf(U[i * R + r1], U[i * R + r2], p[0]);
+        acc += (double(p[0]) + double(p[1])) + (double(p[2]) + double(p[3]));
     }
     red[sl][r2] = acc;
     __syncthreads();
-    if (sl == 0 && r2 < R) G[r1 * R + r2] = (red[0][r2] + red[1][r2]) + (red[2][r2] + red[3][r2]);
+    if (sl == 0 && r2 < R) {
+        double t = 0.0;
+        #pragma unroll
+        for (int k = 0; k < kGramSlices; ++k) t += red[k][r2];
+        G[r1 * R + r2] = t;
+    }
 }
 
 // One block: V = Hadamard of the Grams of every mode except `mode`, its
@@ -621,7 +676,7 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
     sum_kernel<<<1, 256, 0, s>>>(h->partial, kSumBlocks, h->normx2);
     count_launch(2);
     for (int m = 0; m < h->order; ++m) {
-        gram_kernel<<<R, 256, 0, s>>>(factors[m], h->dims[m], R, h->grams + size_t(m) * R * R);
+        gram_kernel<<<R, 1024, 0, s>>>(factors[m], h->dims[m], R, h->grams + size_t(m) * R * R);
         count_launch();
     }
     if (cudaGetLastError() != cudaSuccess) return DEINSUM_ERR_CUDA;
@@ -660,7 +715,10 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
                 sa.U[2] = factors[2];
                 if (launch_split_inner_factor(sa, h->tb, stream) || launch_ttm_last_tc(ta, nsm, stream))
                     return DEINSUM_ERR_CUDA;
-                tree_m0_kernel<<<unsigned(h->dims[0]), 128, 0, s>>>(h->T, factors[1], h->M, h->dims[1], R);
+                if (R % 4 == 0 && (reinterpret_cast<uintptr_t>(factors[1]) & 15) == 0)
+                    tree_m0_vec_kernel<<<unsigned(h->dims[0]), 256, 0, s>>>(h->T, factors[1], h->M, h->dims[1], R);
+                else
+                    tree_m0_kernel<<<unsigned(h->dims[0]), 128, 0, s>>>(h->T, factors[1], h->M, h->dims[1], R);
                 count_launch();
             } else if (tree && n == 1) {
                 float *part = reinterpret_cast<float *>(h->tb + round_up(size_t((h->dims[2] + 63) / 64) * 8192, 1024));
@@ -683,7 +741,7 @@ deinsum_status deinsum_cpals_run(deinsum_cpals_t h, const float *X, float *const
             if (blocks > 1024) blocks = 1024;
             apply_kernel<<<blocks, 256, 0, s>>>(h->M, h->W, factors[n], I, R);
             normalize_kernel<<<R, 256, 0, s>>>(factors[n], I, R, lambda);
-            gram_kernel<<<R, 256, 0, s>>>(factors[n], I, R, h->grams + size_t(n) * R * R);
+            gram_kernel<<<R, 1024, 0, s>>>(factors[n], I, R, h->grams + size_t(n) * R * R);
             count_launch(4);
         }
         const int last = h->order - 1;
