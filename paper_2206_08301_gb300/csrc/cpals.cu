@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(256) inverse_kernel(const double *__restrict__
         floor_pivot = dmax > 0.0 ? dmax * 1e-300 : 1e-300;
     }
     __syncthreads();
+    __shared__ double rinv[kMaxR];   // 1 / L[k][k]: one FP64 division per column
     for (int k = 0; k < R; ++k) {
         if (threadIdx.x == 0) {
             double d = L[k][k];
@@ -197,10 +198,12 @@ __global__ void __launch_bounds__(256) inverse_kernel(const double *__restrict__
                 d = floor_pivot;
                 atomicOr(status, 2);
             }
-            L[k][k] = sqrt(d);
+            const double sd = sqrt(d);
+            L[k][k] = sd;
+            rinv[k] = 1.0 / sd;
         }
         __syncthreads();
-        for (int i = k + 1 + int(threadIdx.x); i < R; i += blockDim.x) L[i][k] /= L[k][k];
+        for (int i = k + 1 + int(threadIdx.x); i < R; i += blockDim.x) L[i][k] *= rinv[k];
         __syncthreads();
         const int rem = R - k - 1;
         for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(256) inverse_kernel(const double *__restrict__
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) Li[e / R][e % R] = (e / R == e % R) ? 1.0 : 0.0;
     for (int k = 0; k < R; ++k) {
         __syncthreads();
-        for (int j = threadIdx.x; j <= k; j += blockDim.x) Li[k][j] /= L[k][k];
+        for (int j = threadIdx.x; j <= k; j += blockDim.x) Li[k][j] *= rinv[k];
         __syncthreads();
         const int rows_below = R - k - 1;
         for (int e = threadIdx.x; e < rows_below * (k + 1); e += blockDim.x) {
