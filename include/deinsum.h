@@ -254,14 +254,16 @@ deinsum_status deinsum_kernel_time(deinsum_plan_t plan, double *total_ms, int64_
 /*
  * Batched MTTKRP: `n` instances (each an MTTKRP einsum with its own extents
  * and rank <= 64, float32) computed together.  With DEINSUM_PREC_SPLIT_BF16
- * they run in at most three persistent tensor-core launches (plus factor-split,
- * weight-table and reduction launches) replayed from a CUDA graph captured on
- * the first execute with a given set of pointers: one over the instances whose
- * rows are 16-byte aligned (by their extents), and one per operand layout over
- * the others (row-class tensor-map loads).  Every instance's rows are cut into work units of about
- * total / (SMs x unit_div) bytes of X, assigned to the CTAs of its launch
- * largest first.  With DEINSUM_PREC_PLAIN every instance runs as its own plain
- * launch.  Results are deterministic and within the split-BF16 tolerance of the
+ * they run in one persistent tensor-core launch (plus factor-split, weight-table
+ * and reduction launches) replayed from a CUDA graph captured on the first
+ * execute with a given set of pointers.  Every instance's rows are cut into work
+ * units of about total / (SMs x unit_div) bytes of X; the units form one list,
+ * grouped by how an instance loads X (tensor map when its rows are 16-byte
+ * aligned, row-class tensor maps otherwise; K-major or MN-major operand) and
+ * largest first within a group, which the CTAs take in order from a device
+ * ticket counter.  With DEINSUM_PREC_PLAIN every instance runs as its own plain
+ * launch.  Results are deterministic (each unit writes its own partial block and
+ * the reduction order is fixed) and within the split-BF16 tolerance of the
  * single-instance split path (which may regroup a short inner mode).
  */
 typedef struct deinsum_batch_s *deinsum_batch_t;
@@ -287,8 +289,8 @@ deinsum_status deinsum_execute_batched(deinsum_batch_t b, const void *const *con
 deinsum_status deinsum_batched_autotune(deinsum_batch_t b, const void *const *const *inputs,
                                         void *const *outputs, deinsum_stream_t stream, double *best_ms);
 
-/* Units, grid (the largest of the launches' grids), unit divisor and
- * algorithmic bytes (sum over the instances). */
+/* Units, grid (CTAs of the persistent launch), unit divisor and algorithmic
+ * bytes (sum over the instances). */
 deinsum_status deinsum_batched_info(deinsum_batch_t b, int64_t *n_units, int *grid, int *unit_div,
                                     double *alg_bytes);
 

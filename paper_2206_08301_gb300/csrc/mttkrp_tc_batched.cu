@@ -1,6 +1,6 @@
 // Batched split-BF16 MTTKRP on the tcgen05 tensor cores (sm_103a): one persistent
 // launch over the work units of many instances (see csrc/batched.cu for the host side:
-// instance tables, LPT schedule, graph capture, autotuning).  The pipeline is the one of
+// instance tables, the unit list, graph capture, autotuning).  The pipeline is the one of
 // the single-instance kernel (mttkrp_tc.cu): TMA ring of raw FP32 chunks, converter warps
 // splitting them into BF16 hi / lo operand tiles, one thread issuing tcgen05.mma, FP32
 // accumulators in TMEM, epilogue warps folding fiber groups with their Khatri-Rao weights.

@@ -1,4 +1,4 @@
-"""Batched MTTKRP: uneven instances in persistent launches, one per kind (graph-replayed).
+"""Batched MTTKRP: uneven instances in one persistent launch fed by a device ticket queue (graph-replayed).
 
 Each instance of the batch matches the FP64 oracle within the split-BF16 gate
 (relative Frobenius 1e-5, and element-wise within 1e-4 of the largest oracle
