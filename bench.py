@@ -24,7 +24,9 @@ timed region is bracketed by barriers and the max over ranks is reported
 from __future__ import annotations
 
 import argparse
+import contextlib
 import datetime
+import gc
 import hashlib
 import json
 import os
@@ -422,12 +424,12 @@ def run_paper(args):
         plan.set_kernel_timing(True)
         plan.kernel_time()
         e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-        with torch.cuda.stream(stream):
+        with host_gc_paused(), torch.cuda.stream(stream):
             e0.record(stream)
             for _ in range(steps):
                 plan(*ops, out=out, stream=stream)
             e1.record(stream)
-        stream.synchronize()
+            stream.synchronize()
         kms, kn = plan.kernel_time()
         plan.set_kernel_timing(False)
         return e0.elapsed_time(e1) / steps, kms / max(1, kn)
@@ -501,6 +503,21 @@ def run_paper(args):
 FP32_CORE_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
+@contextlib.contextmanager
+def host_gc_paused():
+    """Around a device-timed region: collect the host's garbage first and keep the collector
+    off, so that a collection pause of the Python host (tens of ms with large heaps) cannot
+    leave the queued GPU work idle inside the region.  The e2e region runs without it."""
+    was = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
+
+
 def _events_ms(stream, fn, reps, warm=3):
     import torch
     with torch.cuda.stream(stream):
@@ -508,12 +525,12 @@ def _events_ms(stream, fn, reps, warm=3):
             fn()
     stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
+    with host_gc_paused(), torch.cuda.stream(stream):
         e0.record(stream)
         for _ in range(reps):
             fn()
         e1.record(stream)
-    stream.synchronize()
+        stream.synchronize()
     return e0.elapsed_time(e1) / reps
 
 
@@ -814,10 +831,11 @@ def measure_cpals_sweep(clk, sweeps=4):
                 for S in (1, sweeps):
                     F = [u.clone() for u in init]
                     e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-                    e0.record(stream)
-                    lam, fits = cp.run(X, F, S, stream=stream)
-                    e1.record(stream)
-                    stream.synchronize()
+                    with host_gc_paused():
+                        e0.record(stream)
+                        lam, fits = cp.run(X, F, S, stream=stream)
+                        e1.record(stream)
+                        stream.synchronize()
                     t[S] = e0.elapsed_time(e1)
             per = (t[sweeps] - t[1]) / (sweeps - 1)
             res[tree] = (per, float(fits[-1]), cp.status())
@@ -974,12 +992,12 @@ def main():
     clocks.start()
     clocks.mark_start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
+    with host_gc_paused(), torch.cuda.stream(stream):
         ev0.record(stream)
         for _ in range(args.steps):
             step(stream)
         ev1.record(stream)
-    stream.synchronize()
+        stream.synchronize()
     torch.cuda.synchronize()
     clocks.mark_stop()
     if dist:

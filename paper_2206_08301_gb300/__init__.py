@@ -201,6 +201,24 @@ def _dev_ptr(t, name: str):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _dev_ptrs(ts, name: str) -> list:
+    """Device addresses (ints) of many tensors, checked as in _dev_ptr.  Builds no per-tensor
+    ctypes object: a batch call marshals thousands of pointers, and per-element objects made
+    the host's garbage collector pause for tens of ms every few dozen calls."""
+    import torch
+    try:
+        ptrs = [t.data_ptr() for t in ts if t.is_cuda and t.is_contiguous()]
+    except AttributeError:
+        ptrs = []
+    if len(ptrs) != len(ts):
+        for t in ts:
+            _dev_ptr(t, name)   # raises with the reason
+        raise TypeError(f"every {name} must be a contiguous CUDA torch.Tensor")
+    if not all(isinstance(t, torch.Tensor) for t in ts):
+        raise TypeError(f"{name} must be a CUDA torch.Tensor")
+    return ptrs
+
+
 class Plan:
     """A planned MTTKRP / TTMc contraction (``deinsum_plan``).
 
@@ -435,9 +453,17 @@ class Batch:
         self._h = h
 
     def _marshal(self, inputs, outputs):
-        self._ins = [(ctypes.c_void_p * len(ops))(*[_dev_ptr(t, "operand").value for t in ops]) for ops in inputs]
-        ip = (ctypes.c_void_p * self.n)(*[ctypes.cast(x, ctypes.c_void_p).value for x in self._ins])
-        op = (ctypes.c_void_p * self.n)(*[_dev_ptr(t, "output").value for t in outputs])
+        # every operand pointer in one flat array; instance i's table starts at its offset
+        if len(inputs) != self.n or len(outputs) != self.n:
+            raise ValueError(f"expected {self.n} instances")
+        flat = [t for ops in inputs for t in ops]
+        self._flat = (ctypes.c_void_p * max(1, len(flat)))(*_dev_ptrs(flat, "operand"))
+        base, off, starts = ctypes.addressof(self._flat), 0, []
+        for ops in inputs:
+            starts.append(base + 8 * off)
+            off += len(ops)
+        ip = (ctypes.c_void_p * self.n)(*starts)
+        op = (ctypes.c_void_p * self.n)(*_dev_ptrs(outputs, "output"))
         return ip, op
 
     def __call__(self, inputs, outputs, stream=None):

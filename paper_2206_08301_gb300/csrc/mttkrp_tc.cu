@@ -194,7 +194,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
                 const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_STAGE);
                 if (RC) {
                     if (MN) conv_read_rowcls_mn(g, a.X, it.col, it.o, it.kb, raw, pt, v);
-                    else conv_read_rowcls(g, a.X, it.col, it.tile, it.o, it.kb, raw, rowcls_thread(pt), v);
+                    else conv_read_rowcls_half(g, a.X, it.col, it.tile, it.o, it.kb, raw, pt, v);
                 } else if (MN && !OP && a.raw_pitch == BM) conv_read_smem_mn128(raw, pt, v);
                 else if (MN) conv_read_smem_mn(mp, a.raw_pitch, raw, pt, v);
                 else if (!g.narrow || g.G * g.I == BM) conv_read_smem_wide(raw, pt, v);   // all 128 rows
@@ -223,7 +223,8 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             }
             if (MN && RC) conv_store_mn_cls(pt, a_hi(as), a_lo(as), v);
             else if (MN) conv_store_mn(pt, a_hi(as), a_lo(as), v);
-            else conv_store(g, RC ? rowcls_thread(pt) : pt, a_hi(as), a_lo(as), v);
+            else if (RC) conv_store_rowcls_half(pt, a_hi(as), a_lo(as), v);
+            else conv_store(g, pt, a_hi(as), a_lo(as), v);
             // the proxy fence orders this thread's A stores before the tensor-core reads
             fence_proxy_async_smem();
             __syncwarp();
@@ -339,7 +340,8 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     } else {
         // ------------------------------------------------------------- epilogue
         const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
-        const int l = quad * 32 + lane;            // tile row of this thread
+        // tile row of this thread's TMEM lane (row-class K-major tiles are stored class-major)
+        const int l = (RC && !MN) ? rowcls_tile_row(quad * 32 + lane) : quad * 32 + lane;
         constexpr bool lane_weights = PW;          // per-row weights (the launcher's choice)
         const bool has_common = OP ? g.n_lmodes > 0 : g.n_outer > 0;   // a row common to the tile
         const int lg = g.narrow ? int(l / g.I) : 0;   // narrow: p offset of row l within its tile

@@ -22,16 +22,16 @@ using namespace sm100;
 
 constexpr int kFoldEvery = 64;  // fiber groups accumulated in registers before a flush
 
-// THREE: three split products into one accumulator of RP columns (X_hi U_hi + X_hi U_lo +
-// X_lo U_hi); otherwise two MMAs with N = 2 RP (X_hi and X_lo against [U_hi; U_lo]) into an
-// accumulator whose column r holds the U_hi products and column RP + r the U_lo products,
-// all four split products.  Three products halve the epilogue's TMEM reads, but one
-// accumulator takes 12 dependent MMAs per 64-k chunk against 8, which measured slower
-// wherever the MMAs keep pace with HBM (1024^3: 0.687 against 0.652 ms), so only the
-// batched kernel, whose short fiber groups make the epilogue weigh more, uses them.
-template <int RP, bool THREE = false> struct TcCfg {
+// Two MMAs per 16-k step with N = 2 RP (X_hi and X_lo against [U_hi; U_lo]) into an
+// accumulator whose column r holds the U_hi products and column RP + r the U_lo products:
+// all four split products, 8 MMAs per 64-k chunk.  Three products into one accumulator of
+// RP columns (X_hi U_hi + X_hi U_lo + X_lo U_hi) halve the epilogue's TMEM reads but take a
+// chain of 12 MMAs per chunk, which measured slower in both kernels (1024^3: 0.687 against
+// 0.652 ms; the 512-instance batch: 4.97 against 4.80 ms, aligned instances 10 % slower).
+// BATCHED: the persistent batched kernel's extra accumulators and ticket ring.
+template <int RP, bool BATCHED = false> struct TcCfg {
     static constexpr int N = 2 * RP;                       // rows of the split factor tile: hi, then lo
-    static constexpr int ACC = THREE ? RP : 2 * RP;        // MMA N and accumulator columns
+    static constexpr int ACC = 2 * RP;                     // MMA N and accumulator columns
     static constexpr int RS = RP <= 32 ? 4 : 3;            // raw X stages
     static constexpr int AS = 2;                           // operand stages
     static constexpr int MMA_WARP = CONV_WARPS + EPI_WARPS;
@@ -50,11 +50,12 @@ template <int RP, bool THREE = false> struct TcCfg {
     static constexpr int WBUF_BYTES = WSLOTS * WSLOT_FLOATS * 4;
     // TMEM accumulators in flight: two, or four for the batched kernel, whose short fiber
     // groups would otherwise hold the MMAs up behind the epilogue
-    static constexpr int NACC = THREE ? 4 : 2;
+    static constexpr int NACC = BATCHED ? 4 : 2;
     static constexpr int TMEM_COLS = NACC * ACC < 32 ? 32 : NACC * ACC;   // a power of two, >= 32
+    static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM allocation");
     // batched kernel: a ring of NQ unit tickets (the TMA thread takes each from the device
     // counter and hands it to the other roles: qfull / qempty)
-    static constexpr int NQ = THREE ? 8 : 0;
+    static constexpr int NQ = BATCHED ? 8 : 0;
     static constexpr int NBARS = 2 * RS + 3 * AS + 2 * NACC + 1 + 2 * WSLOTS + 2 * NQ;
     static constexpr size_t SMEM = size_t(RS) * RAW_STAGE + size_t(AS) * ASTAGE_BYTES + WBUF_BYTES + 1024 + 512;
     static_assert(SMEM <= 232448, "dynamic shared memory above the 227 KB per-CTA limit");

@@ -31,8 +31,9 @@ using namespace sm100;
 // fields once and runs its chunks in code specialised for the instance's loads
 // (tensor map or row classes, K-major or MN-major operand) and, in the epilogue,
 // for its padded rank, so that all kinds of instance share one launch and one
-// tail.  The MMAs take the three split products into one accumulator of R_pad
-// columns (N = R_pad, a runtime field of the instruction descriptor).
+// tail.  The MMAs take all four split products as in the single-instance kernel
+// (N = 2 R_pad, a runtime field of the instruction descriptor; the accumulator's
+// column r holds the U_hi products and column R_pad + r the U_lo products).
 // ---------------------------------------------------------------------------
 constexpr int RPB = 64;  // the batched kernel is shaped for the largest padded rank
 
@@ -206,7 +207,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                         if constexpr (K == BK_RC_MN) {
                             conv_read_rowcls_mn(g, X, col, o, kb, raw, pt, v);
                         } else if constexpr (K == BK_RC_K) {
-                            conv_read_rowcls(g, X, col, tile, o, kb, raw, rowcls_thread(pt), v);
+                            conv_read_rowcls_half(g, X, col, tile, o, kb, raw, pt, v);
                         } else if constexpr (K == BK_TMA_MN) {
                             if (pitch == BM) conv_read_smem_mn128(raw, pt, v);
                             else conv_read_smem_mn(mp, pitch, raw, pt, v);
@@ -238,7 +239,8 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                     }
                     if constexpr (K == BK_RC_MN) conv_store_mn_cls(pt, a_hi(as), a_lo(as), v);
                     else if constexpr (MN) conv_store_mn(pt, a_hi(as), a_lo(as), v);
-                    else conv_store(g, K == BK_RC_K ? rowcls_thread(pt) : pt, a_hi(as), a_lo(as), v);
+                    else if constexpr (K == BK_RC_K) conv_store_rowcls_half(pt, a_hi(as), a_lo(as), v);
+                    else conv_store(g, pt, a_hi(as), a_lo(as), v);
                     fence_proxy_async_smem();   // the A stores before the tensor-core reads
                     __syncwarp();
                     if (lane == 0) mbar_arrive(a_full(as));
@@ -352,8 +354,7 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 constexpr bool MN = decltype(mt)::value != 0;   // the last mode: MN-major A
                 const int n_kb = a.g.n_kb;
                 const int rp = a.g.R_pad;
-                const uint32_t idesc = idesc_bf16_f32(BM, rp) | (MN ? kIdescAMnMajor : 0u);
-                const uint32_t blo = uint32_t(rp * 128);   // U_lo rows of the split factor tile
+                const uint32_t idesc = idesc_bf16_f32(BM, 2 * rp) | (MN ? kIdescAMnMajor : 0u);
                 for (int64_t fg = f0; fg < f1; ++fg, ++fgi) {
                     const int b = int(fgi % C::NACC);
                     const uint32_t jb = uint32_t(fgi / C::NACC);
@@ -371,14 +372,12 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                                                : desc_kmajor_sw128(a_hi(s));
                         const uint64_t dl = MN ? desc_mnmajor_sw128(a_lo(s), kMnAtomStride, kMnKGroupStride)
                                                : desc_kmajor_sw128(a_lo(s));
-                        const uint64_t db = desc_kmajor_sw128(b_t(s));
-                        const uint64_t dbl = desc_kmajor_sw128(b_t(s) + blo);
+                        const uint64_t db = desc_kmajor_sw128(b_t(s));   // [U_hi; U_lo]: N = 2 R_pad rows
                         #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
                             const uint64_t adv = uint64_t(kk * 32) >> 4;
                             const uint64_t adv_a = MN ? uint64_t(kk * 2 * kMnKGroupStride) >> 4 : adv;
                             mma_bf16(dcol, dh + adv_a, db + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                            mma_bf16(dcol, dh + adv_a, dbl + adv, idesc, 1u);
                             mma_bf16(dcol, dl + adv_a, db + adv, idesc, 1u);
                         }
                         mma_commit(a_empty(s));
@@ -403,13 +402,15 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     } else {
         // ------------------------------------------------------------- epilogue
         const int quad = warp & 3;
-        const int l = quad * 32 + lane;
+        const int lane_row = quad * 32 + lane;   // this thread's TMEM lane (accumulator row)
         int64_t fgi = 0;
         auto run = [&](auto rt, const MttkrpArgs &a, int64_t col, int64_t f0, int64_t f1, int64_t part_off) -> bool {
             constexpr int RP = decltype(rt)::value;
             MttkrpGeom g;
             batch_geometry<false>(g, a.g);
             g.kcase = a.g.kcase;
+            // the tile row of this lane: K-major row-class tiles are stored class-major
+            const int l = batch_kind(a) == BK_RC_K ? rowcls_tile_row(lane_row) : lane_row;
             // per-row weights: narrow case-0 tiles of several p with L rows
             const bool lane_weights = g.kcase == 0 && g.narrow && g.n_lmodes > 0;
             const bool has_common = g.n_outer > 0;                 // a row common to the tile
@@ -454,9 +455,12 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
                 const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::ACC);
                 #pragma unroll
                 for (int c = 0; c < RP; c += 16) {
-                    uint32_t tv[16];
+                    uint32_t tv[16], tl[16];   // the U_hi and U_lo products of columns c .. c + 15
                     tmem_ld16(taddr + uint32_t(c), tv);
+                    tmem_ld16(taddr + uint32_t(RP + c), tl);
                     tmem_wait_ld();
+                    #pragma unroll
+                    for (int q = 0; q < 16; ++q) tv[q] = __float_as_uint(__uint_as_float(tv[q]) + __uint_as_float(tl[q]));
                     #pragma unroll
                     for (int q4 = 0; q4 < 4; ++q4) {
                         const int cc = c + 4 * q4;

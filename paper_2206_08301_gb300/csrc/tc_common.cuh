@@ -316,6 +316,77 @@ __device__ __forceinline__ void conv_read_rowcls(const MttkrpGeom &g, const void
         if (!row_valid(g, col, rowbase, rsub + 16 * j)) v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Case 0 from the four class boxes, one half row per thread, into a class-major A tile (the
+// batched kernel's layout).  A row a holds tile row l = 4 (a mod 32) + a / 32: the rows of
+// each residue l mod 4 form one 32-row block of A, a fixed permutation that the epilogue
+// undoes (rowcls_tile_row), whatever the tile.  Warp w takes the residue e = w mod 4, i.e.
+// class c = (rowbase + e) mod 4, whose box row b is tile row 4 b + e; lane b reads words
+// 32 h .. 32 h + 31 of box row b (h = w / 4), so v[i] = words 32 h + 4 i .. + 3 of that row.
+// A class's rows start at one word offset d within their 16-byte granule (the same for the
+// warp): nine aligned 16-byte reads per half row (eight for d = 0), and the 68-word box pitch
+// puts a warp's 32 rows on all banks.  Masking as in conv_read_rowcls.
+__device__ __forceinline__ int rowcls_tile_row(int a) { return 4 * (a & 31) + (a >> 5); }
+// Words D .. D + 31 from the 16-byte aligned address r on (nine aligned reads for D > 0).
+template <int D>
+__device__ __forceinline__ void half_row_read(uint32_t r, float4 (&v)[8]) {
+    if constexpr (D == 0) {
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = lds128(r + 16u * uint32_t(i));
+    } else {
+        float4 a0 = lds128(r);
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 a1 = lds128(r + 16u * uint32_t(i + 1));
+            if constexpr (D == 1) v[i] = make_float4(a0.y, a0.z, a0.w, a1.x);
+            else if constexpr (D == 2) v[i] = make_float4(a0.z, a0.w, a1.x, a1.y);
+            else v[i] = make_float4(a0.w, a1.x, a1.y, a1.z);
+            a0 = a1;
+        }
+    }
+}
+__device__ __forceinline__ void conv_read_rowcls_half(const MttkrpGeom &g, const void *X, int64_t col,
+                                                      int64_t tile, int64_t o, int kb, const float *raw, int pt,
+                                                      float4 (&v)[8]) {
+    const int w = pt >> 5, b = pt & 31;
+    const int e = w & 3, h = w >> 2;
+    const int64_t rowbase = tile_rowbase(g, col, tile);
+    const int cls = int(uint64_t(rowbase + e) & 3u);
+    const int64_t k0 = int64_t(kb) * BK;
+    const uint64_t w0 = word_index(X) + uint64_t(rowbase + e) * uint64_t(g.Q) + uint64_t(o * g.K_in + k0);
+    const int d = int(w0 & 3u);
+    const uint32_t r = smem_u32(raw) + uint32_t(((cls * kRcRows0 + b) * kRcPitch0 + 32 * h) * 4);
+    switch (d) {
+        case 0: half_row_read<0>(r, v); break;
+        case 1: half_row_read<1>(r, v); break;
+        case 2: half_row_read<2>(r, v); break;
+        default: half_row_read<3>(r, v); break;
+    }
+    if (!g.narrow || rowbase + BM <= g.P * g.I) return;
+    if (!row_valid(g, col, rowbase, 4 * b + e)) {
+        #pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+// Split and store conv_read_rowcls_half's half rows: A row 32 e + b (the warp's 32 consecutive
+// rows, all eight swizzle phases), k = 32 h .. 32 h + 31 = 16-byte chunks 4 h .. 4 h + 3 of the
+// 128-byte-swizzled K-major row: four wavefronts per 512-byte warp store, the least possible.
+__device__ __forceinline__ void conv_store_rowcls_half(int pt, uint32_t a_hi, uint32_t a_lo, const float4 (&v)[8]) {
+    const int w = pt >> 5;
+    const uint32_t arow = uint32_t(32 * (w & 3) + (pt & 31)), h = uint32_t(w >> 2);
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t off = sw128_offset(arow, 32u * h + 8u * uint32_t(j));
+        const float4 x0 = v[2 * j], x1 = v[2 * j + 1];
+        uint32_t hi[4], lo[4];
+        split2(x0.x, x0.y, hi[0], lo[0]);
+        split2(x0.z, x0.w, hi[1], lo[1]);
+        split2(x1.x, x1.y, hi[2], lo[2]);
+        split2(x1.z, x1.w, hi[3], lo[3]);
+        sts128(a_hi + off, hi[0], hi[1], hi[2], hi[3]);
+        sts128(a_lo + off, lo[0], lo[1], lo[2], lo[3]);
+    }
+}
+
 // Case 1 from the four class boxes.  Thread layout (warp w, lane): the warp holds the eight
 // k lines kl = r + 4 (8 h + j), j < 8, of one residue r = w mod 4 (h = w / 4), rows
 // m = 4 lane .. + 3 of each.  All of a warp's lines are members of one class, c = (L0 + r)
