@@ -417,14 +417,13 @@ def run_paper(args):
     stream = torch.cuda.Stream()
 
     def timed(plan, ops, out, steps):
-        with torch.cuda.stream(stream):
+        with host_gc_paused(), torch.cuda.stream(stream):
             for _ in range(3):
                 plan(*ops, out=out, stream=stream)
-        stream.synchronize()
-        plan.set_kernel_timing(True)
-        plan.kernel_time()
-        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-        with host_gc_paused(), torch.cuda.stream(stream):
+            stream.synchronize()
+            plan.set_kernel_timing(True)
+            plan.kernel_time()
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
             e0.record(stream)
             for _ in range(steps):
                 plan(*ops, out=out, stream=stream)
@@ -505,9 +504,11 @@ FP32_CORE_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x 
 
 @contextlib.contextmanager
 def host_gc_paused():
-    """Around a device-timed region: collect the host's garbage first and keep the collector
-    off, so that a collection pause of the Python host (tens of ms with large heaps) cannot
-    leave the queued GPU work idle inside the region.  The e2e region runs without it."""
+    """Around a device-timed region and its warm-up: collect the host's garbage first and keep
+    the collector off, so that a collection pause of the Python host (tens of ms with large
+    heaps) cannot leave the queued GPU work idle inside the region.  The collection runs before
+    the warm-up, not between it and the region: after an idle gap of that length the first
+    timed launches ran measurably slower.  The e2e region runs without it."""
     was = gc.isenabled()
     gc.collect()
     gc.disable()
@@ -520,12 +521,11 @@ def host_gc_paused():
 
 def _events_ms(stream, fn, reps, warm=3):
     import torch
-    with torch.cuda.stream(stream):
-        for _ in range(warm):
-            fn()
-    stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with host_gc_paused(), torch.cuda.stream(stream):
+        for _ in range(warm):
+            fn()
+        stream.synchronize()
         e0.record(stream)
         for _ in range(reps):
             fn()
@@ -536,17 +536,23 @@ def _events_ms(stream, fn, reps, warm=3):
 
 def _plan_timed(plan, ops, out, stream, reps, warm=3):
     """(ms per execute, average main-kernel ms) of a plan over `reps` executes."""
+    import torch
     fn = lambda: plan(*ops, out=out, stream=stream)  # noqa: E731
-    with torch_stream(stream):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with host_gc_paused(), torch_stream(stream):
         for _ in range(warm):
             fn()
-    stream.synchronize()
-    plan.set_kernel_timing(True)
-    plan.kernel_time()
-    ms = _events_ms(stream, fn, reps, warm=0)
+        stream.synchronize()
+        plan.set_kernel_timing(True)
+        plan.kernel_time()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
     kms, kn = plan.kernel_time()
     plan.set_kernel_timing(False)
-    return ms, kms / max(1, kn)
+    return e0.elapsed_time(e1) / reps, kms / max(1, kn)
 
 
 def torch_stream(stream):
@@ -740,9 +746,10 @@ def measure_c3_batched(clk, peak, n=512, reps=5):
     bsplit = dz.Batch(einsums, extents, "split_bf16")
     with torch.cuda.stream(stream):
         tune_ms = bsplit.autotune(ins, outs, stream=stream)
+    replay = bsplit.bind(ins, outs)   # pointers marshalled once: each call is one graph launch
     with clk.region("c3"):
         l0 = dz.kernel_launch_count()
-        t_batch = _events_ms(stream, lambda: bsplit(ins, outs, stream=stream), reps)
+        t_batch = _events_ms(stream, lambda: replay(stream=stream), reps)
         launches = (dz.kernel_launch_count() - l0) / (reps + 3)
     status = bsplit.status()
     info = bsplit.info()
@@ -764,7 +771,8 @@ def measure_c3_batched(clk, peak, n=512, reps=5):
     del ins, outs, facs, bsplit, bplain, plans
     torch.cuda.empty_cache()
     return {"workload": f"{n} order-3 MTTKRP instances, extents U{{32..384}}, R in {{8,16,32,64}}, mode U{{0,1,2}}, "
-                        "X uniform[-1,1) float32, one graph-replayed persistent split-BF16 batch",
+                        "X uniform[-1,1) float32, one graph-replayed persistent split-BF16 batch "
+                        "(Batch.bind: pointers marshalled once)",
             "metric": "GB/s", "value": gb / (t_batch * 1e-3), "unit": "GB/s", "ms_per_step": t_batch,
             "roofline": {"bound": "hbm", "kernel": "mttkrp_tc_batched_kernel (whole batch)",
                          "achieved": xb / (t_batch * 1e-3) / 1e9, "peak": peak,
@@ -825,17 +833,16 @@ def measure_cpals_sweep(clk, sweeps=4):
             cp = dz.CPALS(dims, R, "split_bf16")
             cp.set_dimension_tree(tree)
             t = {}
-            with torch.cuda.stream(stream):
+            with host_gc_paused(), torch.cuda.stream(stream):
                 F = [u.clone() for u in init]
                 cp.run(X, F, 1, stream=stream)
                 for S in (1, sweeps):
                     F = [u.clone() for u in init]
                     e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-                    with host_gc_paused():
-                        e0.record(stream)
-                        lam, fits = cp.run(X, F, S, stream=stream)
-                        e1.record(stream)
-                        stream.synchronize()
+                    e0.record(stream)
+                    lam, fits = cp.run(X, F, S, stream=stream)
+                    e1.record(stream)
+                    stream.synchronize()
                     t[S] = e0.elapsed_time(e1)
             per = (t[sweeps] - t[1]) / (sweeps - 1)
             res[tree] = (per, float(fits[-1]), cp.status())
@@ -977,22 +984,21 @@ def main():
         for mode in MODES:
             plans[mode](X, *[Ud[m] for m in range(3) if m != mode], out=outs[mode], stream=strm)
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step(stream)
-    stream.synchronize()
-    for p in plans.values():
-        p.set_kernel_timing(True)
-        p.kernel_time()
     clocks = ClockSampler(local)
-    launches0 = dz.kernel_launch_count()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    clocks.mark_start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with host_gc_paused(), torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(stream)
+        stream.synchronize()
+        for p in plans.values():
+            p.set_kernel_timing(True)
+            p.kernel_time()
+        launches0 = dz.kernel_launch_count()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.mark_start()
         ev0.record(stream)
         for _ in range(args.steps):
             step(stream)

@@ -437,6 +437,20 @@ class CPALS:
             pass
 
 
+class BoundBatch:
+    """A batch bound to fixed operand and output tensors (see ``Batch.bind``)."""
+
+    __slots__ = ("_batch", "_ip", "_op", "_flat", "_refs")
+
+    def __init__(self, batch, ip, op, flat, refs):
+        self._batch, self._ip, self._op, self._flat, self._refs = batch, ip, op, flat, refs
+
+    def __call__(self, stream=None):
+        _check(load().deinsum_execute_batched(self._batch._h, self._ip, self._op, _stream_ptr(stream)),
+               "deinsum_execute_batched")
+        return self._refs[1]
+
+
 class Batch:
     """Batched MTTKRP (``deinsum_plan_batched`` / ``deinsum_execute_batched`` / ...)."""
 
@@ -470,6 +484,15 @@ class Batch:
         ip, op = self._marshal(inputs, outputs)
         _check(load().deinsum_execute_batched(self._h, ip, op, _stream_ptr(stream)), "deinsum_execute_batched")
         return outputs
+
+    def bind(self, inputs, outputs) -> "BoundBatch":
+        """Marshal the operand and output pointers once and return a callable that replays
+        the batch on them: ``bound(stream=None)``.  Each replay then costs the host only the
+        C entry point (a pointer comparison and a graph launch) instead of re-checking every
+        tensor in Python (about 0.8 ms for 512 instances).  The bound object keeps the
+        tensors alive; they must not be resized or re-pointed while it is used."""
+        ip, op = self._marshal(inputs, outputs)
+        return BoundBatch(self, ip, op, self._flat, (list(inputs), list(outputs)))
 
     def autotune(self, inputs, outputs, stream=None) -> float:
         ip, op = self._marshal(inputs, outputs)
