@@ -283,7 +283,7 @@ deinsum_status deinsum_plan_batched(int n, const char *const *einsums, const int
 deinsum_status deinsum_execute_batched(deinsum_batch_t b, const void *const *const *inputs, void *const *outputs,
                                        deinsum_stream_t stream);
 
-/* Time the split-BF16 batch with unit_div in {1, 2, 4, 8, 16} on the device,
+/* Time the split-BF16 batch with unit_div in {1, 2, 4, 8, 16, 32, 64} on the device,
  * keep the fastest (and, if DEINSUM_AUTOTUNE_CACHE names a file, append it
  * there for later plans with the same signature).  Synchronous. */
 deinsum_status deinsum_batched_autotune(deinsum_batch_t b, const void *const *const *inputs,

@@ -14,12 +14,12 @@
 // within one kind's specialised loop for long stretches.  The granularity is picked by
 // an autotuner that times candidate schedules on the device and remembers the winner
 // per batch signature.
-// Device side: a batched split of the instances' inner factors, the batched
-// tensor-core kernel (mttkrp_tc_batched.cu), and a batched fixed-order reduction of
-// the unit partials into each instance's output.  With plain precision the
+// Device side (mttkrp_tc_batched.cu): one launch that splits every instance's inner factor
+// and fills its weight tables, the batched tensor-core kernel, and a fixed-order reduction
+// of the unit partials into each instance's output; the two around the kernel deal their
+// blocks out per instance in proportion to its work.  With plain precision the
 // batch runs as separate launches of the plain kernel (the baseline).
 #include <cuda_runtime.h>
-#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -36,71 +36,12 @@
 #include <vector>
 
 #include "internal.h"
-#include "sm100.cuh"
 
 namespace deinsum {
 namespace {
 
 constexpr int BM = DEINSUM_BM;
 constexpr int BK = DEINSUM_BK;
-
-struct SplitInst {
-    const float *U;
-    unsigned char *out;
-    int64_t K_in;
-    int R, RP, n_kb;
-};
-
-struct RedInst {
-    float *out;
-    int64_t I;
-    int R, RP;
-    int64_t rows_per_col, G;
-    int narrow;
-    int64_t col_table;  // first entry of this instance's column table in red_col
-};
-
-__global__ void batched_split_kernel(const SplitInst *__restrict__ si) {
-    const SplitInst s = si[blockIdx.y];
-    const int64_t total = int64_t(s.n_kb) * 2 * s.RP * BK;
-    for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
-         idx += int64_t(gridDim.x) * blockDim.x) {
-        const int k = int(idx % BK);
-        const int n = int((idx / BK) % (2 * s.RP));
-        const int64_t kb = idx / (int64_t(BK) * 2 * s.RP);
-        const int r = n % s.RP;
-        const int64_t kr = kb * BK + k;
-        const float v = (r < s.R && kr < s.K_in) ? s.U[kr * s.R + r] : 0.f;
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        const __nv_bfloat16 e = n < s.RP ? h : __float2bfloat16_rn(v - __bfloat162float(h));
-        *reinterpret_cast<__nv_bfloat16 *>(s.out + size_t(kb) * (2 * s.RP * BK * 2) +
-                                           sm100::sw128_offset(uint32_t(n), uint32_t(k))) = e;
-    }
-}
-
-// out_i[col*rows_per_col + r, c] = sum over the splits of the column, in order,
-// (and over the G row groups of narrow tiles) of the unit partials.
-__global__ void batched_reduce_kernel(const RedInst *__restrict__ ri, const int64_t *__restrict__ red_col,
-                                      const int64_t *__restrict__ red_off, const float *__restrict__ partial) {
-    const RedInst r = ri[blockIdx.y];
-    const int64_t n = r.I * r.R;
-    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t row = e / r.R;
-        const int c = int(e - row * r.R);
-        const int64_t col = row / r.rows_per_col;
-        const int64_t i = row - col * r.rows_per_col;
-        float s = 0.f;
-        for (int64_t k = red_col[r.col_table + col]; k < red_col[r.col_table + col + 1]; ++k) {
-            const float *p = partial + red_off[k];
-            if (r.narrow) {
-                for (int64_t g = 0; g < r.G; ++g) s += p[(g * r.I + i) * r.RP + c];
-            } else {
-                s += p[i * r.RP + c];
-            }
-        }
-        r.out[e] = s;
-    }
-}
 
 size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -162,12 +103,13 @@ struct deinsum_batch_s {
     std::vector<size_t> bsplit_off;
     std::vector<size_t> wtab_off;    // per instance: its weight tables (L, then O)
     size_t partial_floats = 0, bsplit_bytes = 0, wtab_bytes = 0;
-    int64_t max_wtab_floats = 0;
+    std::vector<int> prep_start;     // per instance: its blocks of the preparation launch (n + 1)
+    std::vector<int> red_start;      // per instance: its blocks of the reduction launch (n + 1)
     // device
     char *ws = nullptr;
     size_t ws_bytes = 0;
     size_t o_status = 0, o_insts = 0, o_split = 0, o_red = 0, o_units = 0, o_ticket = 0, o_redoff = 0, o_redcol = 0,
-           o_bsplit = 0, o_wtab = 0, o_partial = 0, o_end = 0;
+           o_pstart = 0, o_rstart = 0, o_bsplit = 0, o_wtab = 0, o_partial = 0, o_end = 0;
     char *staging = nullptr;  // pinned: insts + split table + reduce table
     size_t staging_bytes = 0;
     bool tables_uploaded = false;
@@ -210,7 +152,13 @@ void build_batch_schedule(deinsum_batch_s *b) {
     b->partial_floats = 0;
     b->bsplit_bytes = 0;
     b->wtab_bytes = 0;
-    b->max_wtab_floats = 0;
+    b->prep_start.assign(1, 0);
+    b->red_start.assign(1, 0);
+    // blocks of the launches around the tensor-core kernel, in proportion to each instance's
+    // work: about 8 split or weight entries and 2 output entries per thread
+    auto blocks = [](int64_t work, int64_t per_block) {
+        return int(std::min<int64_t>(256, std::max<int64_t>(1, (work + per_block - 1) / per_block)));
+    };
     for (int i = 0; i < b->n; ++i) {
         const MttkrpGeom &g = b->inst[size_t(i)].g;
         const int64_t max_units = g.n_cols * g.fg_per_col;
@@ -235,7 +183,9 @@ void build_batch_schedule(deinsum_batch_s *b) {
         const size_t wf = weight_table_floats_l(g) + weight_table_floats_o(g);
         b->wtab_off[size_t(i)] = b->wtab_bytes;
         b->wtab_bytes += up(wf * 4, 256);
-        b->max_wtab_floats = std::max<int64_t>(b->max_wtab_floats, int64_t(wf));
+        const int64_t split_elems = int64_t(g.n_kb) * 2 * g.R_pad * BK;
+        b->prep_start.push_back(b->prep_start.back() + blocks(split_elems + int64_t(wf), 256 * 8));
+        b->red_start.push_back(b->red_start.back() + blocks(g.I * int64_t(g.R), 256 * 2));
     }
     // one global list of units that the launch's CTAs take in order from a device ticket
     // counter: grouped by kind of instance (the kernel's specialised loops; a CTA then stays in
@@ -275,6 +225,8 @@ deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
     b->o_ticket = take(8, 256);
     b->o_redoff = take(b->red_off.size() * 8, 256);
     b->o_redcol = take(b->red_col.size() * 8, 256);
+    b->o_pstart = take(b->prep_start.size() * 4, 256);
+    b->o_rstart = take(b->red_start.size() * 4, 256);
     b->o_bsplit = take(b->bsplit_bytes, 1024);
     b->o_wtab = take(b->wtab_bytes, 256);
     b->o_partial = take(b->partial_floats * 4, 1024);
@@ -304,6 +256,8 @@ deinsum_status layout_and_upload(deinsum_batch_s *b, cudaStream_t s) {
     cudaMemcpyAsync(b->ws + b->o_units, b->units.data(), b->units.size() * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(b->ws + b->o_redoff, b->red_off.data(), b->red_off.size() * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(b->ws + b->o_redcol, b->red_col.data(), b->red_col.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->ws + b->o_pstart, b->prep_start.data(), b->prep_start.size() * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(b->ws + b->o_rstart, b->red_start.data(), b->red_start.size() * 4, cudaMemcpyHostToDevice, s);
     b->tables_uploaded = true;
     b->ptrs.clear();  // instance tables must be rebuilt for the new layout
     destroy_graph(b);
@@ -343,20 +297,10 @@ deinsum_status upload_instances(deinsum_batch_s *b, const void *const *const *in
     return cudaGetLastError() == cudaSuccess ? DEINSUM_OK : DEINSUM_ERR_CUDA;
 }
 
-int max_kb(const deinsum_batch_s *b) {
-    int m = 1;
-    for (auto &i : b->inst) m = std::max(m, i.g.n_kb);
-    return m;
-}
-
 deinsum_status launch_batch(deinsum_batch_s *b, cudaStream_t s) {
-    const int64_t maxtot = int64_t(max_kb(b)) * 2 * 64 * BK;
-    int gx = int(std::min<int64_t>(64, (maxtot + 255) / 256));
-    batched_split_kernel<<<dim3(unsigned(gx), unsigned(b->n)), 256, 0, s>>>(
-        reinterpret_cast<const SplitInst *>(b->ws + b->o_split));
-    count_launch();
-    if (launch_weight_tables_batched(reinterpret_cast<const MttkrpArgs *>(b->ws + b->o_insts), b->n,
-                                     b->max_wtab_floats, s))
+    if (launch_batched_prep(reinterpret_cast<const MttkrpArgs *>(b->ws + b->o_insts),
+                            reinterpret_cast<const SplitInst *>(b->ws + b->o_split),
+                            reinterpret_cast<const int *>(b->ws + b->o_pstart), b->n, b->prep_start.back(), s))
         return DEINSUM_ERR_CUDA;
     BatchArgs ba;
     ba.insts = reinterpret_cast<const MttkrpArgs *>(b->ws + b->o_insts);
@@ -367,13 +311,12 @@ deinsum_status launch_batch(deinsum_batch_s *b, cudaStream_t s) {
     ba.ticket = reinterpret_cast<unsigned long long *>(b->ws + b->o_ticket);
     if (cudaMemsetAsync(ba.ticket, 0, sizeof(unsigned long long), s) != cudaSuccess) return DEINSUM_ERR_CUDA;
     if (launch_mttkrp_tc_batched(ba, b->grid, s)) return DEINSUM_ERR_CUDA;
-    int64_t maxo = 1;
-    for (auto &i : b->inst) maxo = std::max<int64_t>(maxo, i.g.I * i.g.R);
-    int rx = int(std::min<int64_t>(64, (maxo + 255) / 256));
-    batched_reduce_kernel<<<dim3(unsigned(rx), unsigned(b->n)), 256, 0, s>>>(
-        reinterpret_cast<const RedInst *>(b->ws + b->o_red), reinterpret_cast<const int64_t *>(b->ws + b->o_redcol),
-        reinterpret_cast<const int64_t *>(b->ws + b->o_redoff), reinterpret_cast<const float *>(b->ws + b->o_partial));
-    count_launch();
+    if (launch_batched_reduce(reinterpret_cast<const RedInst *>(b->ws + b->o_red),
+                              reinterpret_cast<const int *>(b->ws + b->o_rstart), b->n, b->red_start.back(),
+                              reinterpret_cast<const int64_t *>(b->ws + b->o_redcol),
+                              reinterpret_cast<const int64_t *>(b->ws + b->o_redoff),
+                              reinterpret_cast<const float *>(b->ws + b->o_partial), s))
+        return DEINSUM_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? DEINSUM_OK : DEINSUM_ERR_CUDA;
 }
 
@@ -519,7 +462,7 @@ deinsum_status deinsum_batched_autotune(deinsum_batch_t b, const void *const *co
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int cand[] = {1, 2, 4, 8, 16};
+    const int cand[] = {1, 2, 4, 8, 16, 32, 64};
     int best = b->unit_div;
     double best_t = 1e30;
     for (int div : cand) {

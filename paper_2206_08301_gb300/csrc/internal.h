@@ -125,6 +125,34 @@ struct BatchArgs {
 int launch_mttkrp_tc_batched(const BatchArgs &b, int grid, void *stream);
 size_t mttkrp_tc_batched_smem_bytes();
 
+// The batched launches around the tensor-core kernel (mttkrp_tc_batched.cu).  Both run on a
+// 1-D grid whose blocks are dealt out per instance: instance i owns blocks
+// [start[i], start[i+1]) (start has n + 1 entries, every range non-empty), so that each
+// instance gets blocks in proportion to its work and no block idles.
+//   preparation: instance i's inner factor U (K_in x R) into n_kb split-BF16 tiles at `out`
+//     (128-byte-swizzled K-major, rows U_hi then U_lo, zero past R and K_in), and its weight
+//     tables (MttkrpArgs::Lw / Ow, as weight_tables_kernel);
+//   reduction: out[col * rows_per_col + r, c] = the column's unit partials added in unit order
+//     (narrow tiles: and over their G row groups).
+struct SplitInst {
+    const float *U;
+    unsigned char *out;
+    int64_t K_in;
+    int R, RP, n_kb;
+};
+struct RedInst {
+    float *out;
+    int64_t I;
+    int R, RP;
+    int64_t rows_per_col, G;
+    int narrow;
+    int64_t col_table;  // first entry of this instance's column table in red_col
+};
+int launch_batched_prep(const MttkrpArgs *insts, const SplitInst *splits, const int *start, int n, int n_blocks,
+                        void *stream);
+int launch_batched_reduce(const RedInst *red, const int *start, int n, int n_blocks, const int64_t *red_col,
+                          const int64_t *red_off, const float *partial, void *stream);
+
 // Fused last-two-mode stage of a TTMc keeping a mode n < N-2 (ttmc_tc.cu):
 //   T2[s, c, d] = sum_{k, l} X[s, k, l] U_{N-2}[k, c] U_{N-1}[l, d]
 // for every slab s (flat index over modes 0..N-3), k over I_{N-2}, l over
@@ -189,8 +217,6 @@ int launch_mttkrp_tc(const MttkrpArgs &a, int n_sm, void *stream);
 int launch_split_inner_factor(const MttkrpArgs &a, void *bsplit, void *stream);
 // Weight tables of the tensor-core kernel (a.Lw, a.Ow; sizes below).
 int launch_weight_tables(const MttkrpArgs &a, void *stream);
-// The same for n instances whose arguments are in device memory (max_floats: the largest L + O table).
-int launch_weight_tables_batched(const MttkrpArgs *insts, int n, int64_t max_floats, void *stream);
 // Floats of the two tables: P x R_pad (if n_lmodes > 0) and O x R_pad (if n_outer > 0).
 inline size_t weight_table_floats_l(const MttkrpGeom &g) { return g.n_lmodes > 0 ? size_t(g.P) * size_t(g.R_pad) : 0; }
 inline size_t weight_table_floats_o(const MttkrpGeom &g) { return g.n_outer > 0 ? size_t(g.O) * size_t(g.R_pad) : 0; }

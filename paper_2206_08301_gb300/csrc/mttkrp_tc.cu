@@ -42,62 +42,8 @@ namespace {
 
 using namespace sm100;
 
-// Product of the outer factors' entries at outer index o (row-major over the
-// outer modes), column c.
-__device__ __forceinline__ float outer_weight(const MttkrpArgs &a, int64_t o, int c) {
-    float v = 1.f;
-    for (int k = a.g.n_outer - 1; k >= 0; --k) {
-        const int64_t d = a.g.outer_dim[k];
-        const int64_t i = o % d;
-        o /= d;
-        v *= __ldg(static_cast<const float *>(a.U[a.g.outer_mode[k]]) + i * a.g.R + c);
-    }
-    return v;
-}
-
-// Product of the factors of modes 0..n-1 at p (row-major over those modes), column c.
-__device__ __forceinline__ float row_weight(const MttkrpArgs &a, int64_t p, int c) {
-    float v = 1.f;
-    for (int k = a.g.n_lmodes - 1; k >= 0; --k) {
-        const int64_t d = a.g.dims[k];
-        const int64_t i = p % d;
-        p /= d;
-        v *= __ldg(static_cast<const float *>(a.U[k]) + i * a.g.R + c);
-    }
-    return v;
-}
-
-// Weight tables (one pass before the tensor-core kernel, so that its epilogue
-// reads each fiber group's weights as whole rows, copied ahead by the TMA warp):
-//   Lw[p, c] = row_weight(p, c)    (n_lmodes > 0), p < P
-//   Ow[o, c] = outer_weight(o, c)  (n_outer > 0),  o < O
-// for c < R_pad, zero for c >= R (the products in the same order as above).
-__device__ __forceinline__ void weight_tables_body(const MttkrpArgs &a, int64_t t0, int64_t stride) {
-    const MttkrpGeom &g = a.g;
-    const int rp = g.R_pad;
-    const int64_t nl = g.n_lmodes > 0 ? g.P * rp : 0;
-    const int64_t no = g.n_outer > 0 ? g.O * rp : 0;
-    for (int64_t t = t0; t < nl + no; t += stride) {
-        if (t < nl) {
-            const int64_t p = t / rp;
-            const int c = int(t - p * rp);
-            a.Lw[t] = c < g.R ? row_weight(a, p, c) : 0.f;
-        } else {
-            const int64_t u = t - nl;
-            const int64_t o = u / rp;
-            const int c = int(u - o * rp);
-            a.Ow[u] = c < g.R ? outer_weight(a, o, c) : 0.f;
-        }
-    }
-}
-
 __global__ void weight_tables_kernel(const __grid_constant__ MttkrpArgs a) {
     weight_tables_body(a, int64_t(blockIdx.x) * blockDim.x + threadIdx.x, int64_t(gridDim.x) * blockDim.x);
-}
-
-__global__ void batched_weight_tables_kernel(const MttkrpArgs *__restrict__ insts) {
-    weight_tables_body(insts[blockIdx.y], int64_t(blockIdx.x) * blockDim.x + threadIdx.x,
-                       int64_t(gridDim.x) * blockDim.x);
 }
 
 // OP: outer indices packed into the tile; MN: MN-major A operand (the last mode);
@@ -546,15 +492,6 @@ int launch_weight_tables(const MttkrpArgs &a, void *stream) {
     int64_t blocks = (total + 255) / 256;
     if (blocks > 2048) blocks = 2048;
     weight_tables_kernel<<<unsigned(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(a);
-    count_launch();
-    return int(cudaGetLastError());
-}
-
-int launch_weight_tables_batched(const MttkrpArgs *insts, int n, int64_t max_floats, void *stream) {
-    if (max_floats == 0) return 0;
-    int64_t bx = (max_floats + 255) / 256;
-    if (bx > 64) bx = 64;
-    batched_weight_tables_kernel<<<dim3(unsigned(bx), unsigned(n)), 256, 0, static_cast<cudaStream_t>(stream)>>>(insts);
     count_launch();
     return int(cudaGetLastError());
 }

@@ -2,8 +2,8 @@
 // (mttkrp_tc.cu) and the batched kernel (mttkrp_tc_batched.cu): the tile configuration
 // (shared-memory rings, TMEM accumulators, barrier counts), the chunk iterator of a
 // CTA's units, the converters' per-thread global loads (rows that neither a tensor map
-// nor the row-class maps serve), and the weight-ring copy of a fiber group's
-// Khatri-Rao weights.
+// nor the row-class maps serve), the weight tables and the weight-ring copy of a fiber
+// group's Khatri-Rao weights.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -62,6 +62,55 @@ template <int RP, bool BATCHED = false> struct TcCfg {
     static_assert(RAW_BYTES <= RAW_STAGE, "a tensor-map box fits a raw stage");
     static_assert(NBARS * 8 + 8 + NQ * 8 <= 512, "barrier area (+ TMEM holder, abort flag, ticket ring)");
 };
+
+// Product of the outer factors' entries at outer index o (row-major over the
+// outer modes), column c.
+__device__ __forceinline__ float outer_weight(const MttkrpArgs &a, int64_t o, int c) {
+    float v = 1.f;
+    for (int k = a.g.n_outer - 1; k >= 0; --k) {
+        const int64_t d = a.g.outer_dim[k];
+        const int64_t i = o % d;
+        o /= d;
+        v *= __ldg(static_cast<const float *>(a.U[a.g.outer_mode[k]]) + i * a.g.R + c);
+    }
+    return v;
+}
+
+// Product of the factors of modes 0..n-1 at p (row-major over those modes), column c.
+__device__ __forceinline__ float row_weight(const MttkrpArgs &a, int64_t p, int c) {
+    float v = 1.f;
+    for (int k = a.g.n_lmodes - 1; k >= 0; --k) {
+        const int64_t d = a.g.dims[k];
+        const int64_t i = p % d;
+        p /= d;
+        v *= __ldg(static_cast<const float *>(a.U[k]) + i * a.g.R + c);
+    }
+    return v;
+}
+
+// Weight tables (one pass before the tensor-core kernel, so that its epilogue
+// reads each fiber group's weights as whole rows, copied ahead by the TMA warp):
+//   Lw[p, c] = row_weight(p, c)    (n_lmodes > 0), p < P
+//   Ow[o, c] = outer_weight(o, c)  (n_outer > 0),  o < O
+// for c < R_pad, zero for c >= R (the products in the same order as above).
+__device__ __forceinline__ void weight_tables_body(const MttkrpArgs &a, int64_t t0, int64_t stride) {
+    const MttkrpGeom &g = a.g;
+    const int rp = g.R_pad;
+    const int64_t nl = g.n_lmodes > 0 ? g.P * rp : 0;
+    const int64_t no = g.n_outer > 0 ? g.O * rp : 0;
+    for (int64_t t = t0; t < nl + no; t += stride) {
+        if (t < nl) {
+            const int64_t p = t / rp;
+            const int c = int(t - p * rp);
+            a.Lw[t] = c < g.R ? row_weight(a, p, c) : 0.f;
+        } else {
+            const int64_t u = t - nl;
+            const int64_t o = u / rp;
+            const int c = int(u - o * rp);
+            a.Ow[u] = c < g.R ? outer_weight(a, o, c) : 0.f;
+        }
+    }
+}
 
 struct Iter {
     int64_t u, col, fg, fg1, tile, o;

@@ -1,6 +1,7 @@
 // Batched split-BF16 MTTKRP on the tcgen05 tensor cores (sm_103a): one persistent
-// launch over the work units of many instances (see csrc/batched.cu for the host side:
-// instance tables, the unit list, graph capture, autotuning).  The pipeline is the one of
+// launch over the work units of many instances, with the launches around it (the factor
+// split and weight tables before, the fixed-order reduction after); csrc/batched.cu is the
+// host side (instance tables, the unit list, graph capture, autotuning).  The pipeline is the one of
 // the single-instance kernel (mttkrp_tc.cu): TMA ring of raw FP32 chunks, converter warps
 // splitting them into BF16 hi / lo operand tiles, one thread issuing tcgen05.mma, FP32
 // accumulators in TMEM, epilogue warps folding fiber groups with their Khatri-Rao weights.
@@ -517,7 +518,97 @@ mttkrp_tc_batched_kernel(const __grid_constant__ BatchArgs bargs) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// The launches around the tensor-core kernel.  Their grids are dealt out per instance
+// (instance i owns blocks [start[i], start[i+1])): block_instance finds a block's instance
+// by a binary search over start, done once per block.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int block_instance(const int *__restrict__ start, int n) {
+    __shared__ int inst;
+    if (threadIdx.x == 0) {
+        const int b = int(blockIdx.x);
+        int lo = 0, hi = n - 1;   // the last i with start[i] <= b
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        inst = lo;
+    }
+    __syncthreads();
+    return inst;
+}
+
+// Split factor tiles and weight tables of every instance, before the tensor-core kernel.
+__global__ void __launch_bounds__(256) batched_prep_kernel(const MttkrpArgs *__restrict__ insts,
+                                                           const SplitInst *__restrict__ si,
+                                                           const int *__restrict__ start, int n) {
+    const int i = block_instance(start, n);
+    const int64_t t0 = int64_t(int(blockIdx.x) - start[i]) * blockDim.x + threadIdx.x;
+    const int64_t stride = int64_t(start[i + 1] - start[i]) * blockDim.x;
+    const SplitInst s = si[i];
+    const int64_t total = int64_t(s.n_kb) * 2 * s.RP * BK;
+    for (int64_t idx = t0; idx < total; idx += stride) {
+        const int k = int(idx % BK);
+        const int nn = int((idx / BK) % (2 * s.RP));
+        const int64_t kb = idx / (int64_t(BK) * 2 * s.RP);
+        const int r = nn % s.RP;
+        const int64_t kr = kb * BK + k;
+        const float v = (r < s.R && kr < s.K_in) ? s.U[kr * s.R + r] : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 e = nn < s.RP ? h : __float2bfloat16_rn(v - __bfloat162float(h));
+        *reinterpret_cast<__nv_bfloat16 *>(s.out + size_t(kb) * (2 * s.RP * BK * 2) +
+                                           sw128_offset(uint32_t(nn), uint32_t(k))) = e;
+    }
+    weight_tables_body(insts[i], t0, stride);
+}
+
+// Each instance's output from its unit partials, in unit order (deterministic).
+__global__ void __launch_bounds__(256) batched_reduce_kernel(const RedInst *__restrict__ ri,
+                                                             const int *__restrict__ start, int n,
+                                                             const int64_t *__restrict__ red_col,
+                                                             const int64_t *__restrict__ red_off,
+                                                             const float *__restrict__ partial) {
+    const int i = block_instance(start, n);
+    const RedInst r = ri[i];
+    const int64_t stride = int64_t(start[i + 1] - start[i]) * blockDim.x;
+    const int64_t total = r.I * r.R;
+    for (int64_t e = int64_t(int(blockIdx.x) - start[i]) * blockDim.x + threadIdx.x; e < total; e += stride) {
+        const int64_t row = e / r.R;
+        const int c = int(e - row * r.R);
+        const int64_t col = row / r.rows_per_col;
+        const int64_t ii = row - col * r.rows_per_col;
+        const int64_t k0 = red_col[r.col_table + col], k1 = red_col[r.col_table + col + 1];
+        float acc = 0.f;
+        if (r.narrow) {
+            for (int64_t k = k0; k < k1; ++k) {
+                const float *p = partial + red_off[k] + ii * r.RP + c;
+                for (int64_t g = 0; g < r.G; ++g) acc += p[g * r.I * r.RP];
+            }
+        } else {
+            #pragma unroll 4
+            for (int64_t k = k0; k < k1; ++k) acc += partial[red_off[k] + ii * r.RP + c];
+        }
+        r.out[e] = acc;
+    }
+}
+
 }  // namespace
+
+int launch_batched_prep(const MttkrpArgs *insts, const SplitInst *splits, const int *start, int n, int n_blocks,
+                        void *stream) {
+    batched_prep_kernel<<<unsigned(n_blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(insts, splits, start, n);
+    count_launch();
+    return int(cudaGetLastError());
+}
+
+int launch_batched_reduce(const RedInst *red, const int *start, int n, int n_blocks, const int64_t *red_col,
+                          const int64_t *red_off, const float *partial, void *stream) {
+    batched_reduce_kernel<<<unsigned(n_blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(red, start, n, red_col,
+                                                                                           red_off, partial);
+    count_launch();
+    return int(cudaGetLastError());
+}
 
 size_t mttkrp_tc_batched_smem_bytes() { return TcCfg<RPB, true>::SMEM; }
 
