@@ -4,8 +4,10 @@ Gate: relative Frobenius error <= 1e-5 and element-wise <= 1e-4 of the largest
 oracle entry (the FP32-accurate tolerance of the TTMc contract).  Cases cover
 ragged k tiles (I_{N-2} not a multiple of 128), ragged l chunks (I_{N-1} not a
 multiple of 64), a k extent below one tile, ranks below the padded 32, orders
-3 to 5, every kept mode the fused path takes, and rows of X that are not 16-byte
-aligned (the row-class tensor maps).
+3 to 5, every kept mode the fused path takes, rows of X that are not 16-byte
+aligned (the row-class tensor maps), and order-5 chains with the kept mode before or
+between the two chain modes, ragged trailing extents and ranks that are not multiples
+of 8.
 """
 import numpy as np
 import pytest
@@ -44,6 +46,10 @@ CASES = [
     ((70, 64, 20), 0, (32, 13)),              # order 3, I_{N-2} = 64 exactly
     ((3, 5, 32, 8), 0, (2, 3, 4)),            # I_{N-2} = 32 exactly, one 8-wide l chunk
     ((4, 6, 60, 60, 60), 0, (24, 24, 24, 24)),  # the paper's order-5 TTMc shape, fewer slabs
+    # order-5 chains after the fused pair
+    ((9, 11, 40, 64, 36), 1, (13, 21, 24, 16)),  # kept mode 1 between the two chain modes
+    ((7, 30, 50, 60, 20), 0, (19, 11, 8, 5)),    # ranks 19 / 11, trailing extent 40
+    ((6, 50, 9, 64, 20), 0, (40, 7, 16, 8)),     # R_1 = 40
 ]
 
 
