@@ -48,9 +48,9 @@ template <int RP, bool BATCHED = false> struct TcCfg {
     static constexpr int WSLOTS = 4;
     static constexpr int WSLOT_FLOATS = (DEINSUM_GMAX + 1) * RP;
     static constexpr int WBUF_BYTES = WSLOTS * WSLOT_FLOATS * 4;
-    // TMEM accumulators in flight: two, or four for the batched kernel, whose short fiber
-    // groups would otherwise hold the MMAs up behind the epilogue
-    static constexpr int NACC = BATCHED ? 4 : 2;
+    // TMEM accumulators in flight: four, so that short fiber groups (one or two chunks) do not
+    // hold the MMAs up behind the epilogue
+    static constexpr int NACC = 4;
     static constexpr int TMEM_COLS = NACC * ACC < 32 ? 32 : NACC * ACC;   // a power of two, >= 32
     static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM allocation");
     // batched kernel: a ring of NQ unit tickets (the TMA thread takes each from the device
