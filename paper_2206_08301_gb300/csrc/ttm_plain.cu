@@ -180,9 +180,89 @@ ttm_strided_f32_kernel(const float *__restrict__ X, const float *__restrict__ U,
     }
 }
 
+// FP32 TTM with R <= 32 over a contiguous trailing extent B (a multiple of 4, X and Y 16-byte
+// aligned): each thread owns two consecutive b of one a and all RT >= R ranks (2 RT
+// accumulators) and reads its pair X[a, i, b .. b + 1] straight from global memory (a warp
+// reads 256 contiguous bytes), RPF rows ahead through a ring of registers; the rows of U come
+// from shared memory, 64 at a time, as warp-uniform 16-byte reads (broadcasts).  Every X value
+// feeds RT FMAs from registers; four CTAs per SM (at most 128 registers a thread).
+constexpr int RTHREADS = 128, RPF = 4, RUROWS = 64;
+
+template <int RT>
+__global__ void __launch_bounds__(RTHREADS, 4)
+ttm_rows_f32_kernel(const float *__restrict__ X, const float *__restrict__ U, float *__restrict__ Y, int64_t A,
+                    int64_t I, int64_t B, int R) {
+    __shared__ float4 us[RUROWS][RT / 4];
+    const int64_t B2 = B / 2;
+    const int64_t gid = int64_t(blockIdx.x) * RTHREADS + threadIdx.x;
+    const bool live = gid < A * B2;   // threads past the end still help stage U
+    const int64_t a = live ? gid / B2 : 0, b = live ? 2 * (gid - a * B2) : 0;
+    const float *xp = X + a * I * B + b;
+    auto ldx = [&](int64_t i) {
+        return (live && i < I) ? __ldg(reinterpret_cast<const float2 *>(xp + i * B)) : make_float2(0.f, 0.f);
+    };
+    float acc[RT][2];
+    #pragma unroll
+    for (int r = 0; r < RT; ++r) acc[r][0] = acc[r][1] = 0.f;
+    float2 xq[RPF];
+    #pragma unroll
+    for (int j = 0; j < RPF; ++j) xq[j] = ldx(j);
+    for (int64_t c0 = 0; c0 < I; c0 += RUROWS) {
+        __syncthreads();   // the previous chunk of U is no longer read
+        for (int e = threadIdx.x; e < RUROWS * RT; e += RTHREADS) {
+            const int k = e / RT, r = e - k * RT;
+            const int64_t i = c0 + k;
+            reinterpret_cast<float *>(us[k])[r] = (i < I && r < R) ? U[i * R + r] : 0.f;
+        }
+        __syncthreads();
+        const int64_t c1 = I - c0 < RUROWS ? I : c0 + RUROWS;
+        for (int64_t i0 = c0; i0 < c1; i0 += RPF) {   // RUROWS is a multiple of RPF
+            #pragma unroll
+            for (int j = 0; j < RPF; ++j) {
+                const int64_t i = i0 + j;
+                const float2 x = xq[j];
+                xq[j] = ldx(i + RPF);
+                const float4 *ur = us[i - c0];
+                #pragma unroll
+                for (int q = 0; q < RT / 4; ++q) {
+                    const float4 u = ur[q];
+                    acc[4 * q][0] = fmaf(u.x, x.x, acc[4 * q][0]);
+                    acc[4 * q][1] = fmaf(u.x, x.y, acc[4 * q][1]);
+                    acc[4 * q + 1][0] = fmaf(u.y, x.x, acc[4 * q + 1][0]);
+                    acc[4 * q + 1][1] = fmaf(u.y, x.y, acc[4 * q + 1][1]);
+                    acc[4 * q + 2][0] = fmaf(u.z, x.x, acc[4 * q + 2][0]);
+                    acc[4 * q + 2][1] = fmaf(u.z, x.y, acc[4 * q + 2][1]);
+                    acc[4 * q + 3][0] = fmaf(u.w, x.x, acc[4 * q + 3][0]);
+                    acc[4 * q + 3][1] = fmaf(u.w, x.y, acc[4 * q + 3][1]);
+                }
+            }
+        }
+    }
+    if (!live) return;
+    float *yp = Y + a * int64_t(R) * B + b;
+    #pragma unroll
+    for (int r = 0; r < RT; ++r)
+        if (r < R) *reinterpret_cast<float2 *>(yp + int64_t(r) * B) = make_float2(acc[r][0], acc[r][1]);
+}
+
 template <typename T>
 int launch_ttm(const T *X, const T *U, T *Y, int64_t Aext, int64_t Im, int64_t Bext, int64_t Rm, void *stream) {
     if constexpr (sizeof(T) == 4) {
+        if (Bext >= 64 && Bext % 4 == 0 && Rm <= 32 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+            (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
+            const int64_t threads = Aext * (Bext / 2);
+            const int64_t blocks = (threads + RTHREADS - 1) / RTHREADS;
+            if (blocks < 1 || blocks > 0x7FFFFFFFll) return int(cudaErrorInvalidValue);
+            const int rt = int((Rm + 7) / 8) * 8;
+            auto kern = rt == 8 ? ttm_rows_f32_kernel<8>
+                      : rt == 16 ? ttm_rows_f32_kernel<16>
+                      : rt == 24 ? ttm_rows_f32_kernel<24> : ttm_rows_f32_kernel<32>;
+            kern<<<unsigned(blocks), RTHREADS, 0, static_cast<cudaStream_t>(stream)>>>(
+                reinterpret_cast<const float *>(X), reinterpret_cast<const float *>(U), reinterpret_cast<float *>(Y),
+                Aext, Im, Bext, int(Rm));
+            count_launch();
+            return int(cudaGetLastError());
+        }
         if (Bext >= 64 && Bext % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
             (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
             const int64_t blocks = Aext * ((Bext + SB - 1) / SB) * ((Rm + SR - 1) / SR);
