@@ -1,0 +1,129 @@
+"""Seeded random-shape sweeps of the CUDA path against the FP64 oracle.
+
+The fixed parity cases pick shapes that hit known edges (ragged tiles, narrow rows, packed
+outer indices, unaligned rows); these sweeps draw shapes the cases did not think of: orders 2
+to 6, extents from 1 to a few hundred (log-uniform, X at most about 1.5 M elements so that the
+oracle finishes in well under a second), ranks 1 to 64, every mode, X starting 0 to 3 floats
+into its buffer (aligned rows, row classes, per-thread loads), in both precisions; random
+batches of uneven instances; random split-BF16 TTMc chains.  The shapes come from a fixed
+numpy generator seed, so a failure names a reproducible case.  Gates as in the parity tests:
+relative Frobenius 1e-5 and element-wise 1e-4 of the largest oracle entry.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_08301_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2206_08301_gb300 as dz  # noqa: E402
+
+
+def _gate(got, ref, what):
+    got = np.asarray(got, dtype=np.float64)
+    err = oracle.rel_error(got, ref)
+    worst = oracle.max_elem_error(got, ref)
+    assert err <= 1e-5, f"{what}: relative Frobenius error {err:.3e}"
+    assert worst <= 1e-4, f"{what}: max element error {worst:.3e} of max|ref|"
+
+
+def _extents(rng, order, max_elems):
+    """Log-uniform extents in [1, 400], shrunk (largest first) until their product fits."""
+    dims = [int(round(np.exp(rng.uniform(0.0, np.log(400.0))))) for _ in range(order)]
+    dims = [max(1, d) for d in dims]
+    while int(np.prod(dims)) > max_elems:
+        k = int(np.argmax(dims))
+        dims[k] = max(1, dims[k] * 2 // 3)
+    return tuple(dims)
+
+
+def _device_x(Xh, offset):
+    if offset:
+        buf = torch.empty(Xh.size + offset, device="cuda")
+        X = buf[offset:].view(Xh.shape)
+        X.copy_(torch.from_numpy(Xh))
+        return X
+    return torch.from_numpy(Xh).cuda()
+
+
+MTTKRP_DRAWS = 48
+
+
+@pytest.mark.parametrize("case", range(MTTKRP_DRAWS))
+def test_random_mttkrp_matches_oracle(case):
+    rng = np.random.default_rng(7000 + case)
+    order = int(rng.integers(2, 7))
+    dims = _extents(rng, order, 1_500_000)
+    R = int(rng.integers(1, 65))
+    offset = int(rng.integers(0, 4))
+    seed = 500 + case
+    Xh = inputs.tensor_uniform_f32(seed, dims)
+    Us = [inputs.factor_normal(seed, m, d, R).astype(np.float32) for m, d in enumerate(dims)]
+    X = _device_x(Xh, offset)
+    U = [torch.from_numpy(u).cuda() for u in Us]
+    for mode in range(order):
+        ref = oracle.mttkrp(Xh, Us, mode)
+        for prec in ("split_bf16", "plain"):
+            M = dz.mttkrp(X, U, mode, prec=prec)
+            torch.cuda.synchronize()
+            _gate(M.cpu().numpy(), ref, f"dims {dims} R {R} offset {offset} mode {mode} {prec}")
+
+
+BATCH_DRAWS = 6
+
+
+@pytest.mark.parametrize("case", range(BATCH_DRAWS))
+def test_random_batch_matches_oracle(case):
+    rng = np.random.default_rng(8000 + case)
+    n = int(rng.integers(5, 25))
+    einsums, extents, ins, outs, refs = [], [], [], [], []
+    for k in range(n):
+        order = int(rng.integers(3, 5))
+        dims = _extents(rng, order, 400_000)
+        R = int(rng.integers(1, 65))
+        mode = int(rng.integers(0, order))
+        offset = int(rng.integers(0, 4))
+        seed = 900 + 50 * case + k
+        Xh = inputs.tensor_uniform_f32(seed, dims)
+        Us = [inputs.factor_normal(seed, m, d, R).astype(np.float32) for m, d in enumerate(dims)]
+        einsums.append(dz.mttkrp_einsum(order, mode))
+        extents.append(list(dims) + [R])
+        ins.append([_device_x(Xh, offset)] + [torch.from_numpy(Us[m]).cuda() for m in range(order) if m != mode])
+        outs.append(torch.empty(dims[mode], R, device="cuda"))
+        refs.append((oracle.mttkrp(Xh, Us, mode), f"instance {k}: dims {dims} R {R} mode {mode} offset {offset}"))
+    b = dz.Batch(einsums, extents, "split_bf16")
+    b(ins, outs)
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    for out, (ref, what) in zip(outs, refs):
+        _gate(out.cpu().numpy(), ref, what)
+    b.close()
+
+
+TTMC_DRAWS = 20
+
+
+@pytest.mark.parametrize("case", range(TTMC_DRAWS))
+def test_random_ttmc_matches_oracle(case):
+    """Split-BF16 TTMc (fused last two modes, then the chain) and the plain chain: orders 3 to 5,
+    the kept mode below N-2, ranks of the last two modes up to 32, of the others up to 40."""
+    rng = np.random.default_rng(9000 + case)
+    order = int(rng.integers(3, 6))
+    dims = _extents(rng, order, 1_000_000)
+    keep = int(rng.integers(0, order - 2))
+    ranks = [int(rng.integers(1, 33)) if m >= order - 2 else int(rng.integers(1, 41)) for m in range(order)]
+    offset = int(rng.integers(0, 4))
+    seed = 1300 + case
+    Xh = inputs.tensor_uniform_f32(seed, dims)
+    Us = [None if m == keep else inputs.factor_normal(seed, m, d, ranks[m]).astype(np.float32)
+          for m, d in enumerate(dims)]
+    X = _device_x(Xh, offset)
+    U = [None if u is None else torch.from_numpy(u).cuda() for u in Us]
+    ref = oracle.ttmc(Xh, Us, keep)
+    for prec in ("split_bf16", "plain"):
+        Y = dz.ttmc(X, U, keep, prec=prec)
+        torch.cuda.synchronize()
+        assert Y.shape == ref.shape
+        _gate(Y.cpu().numpy(), ref, f"dims {dims} keep {keep} ranks {ranks} offset {offset} {prec}")
