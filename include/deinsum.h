@@ -283,9 +283,12 @@ deinsum_status deinsum_plan_batched(int n, const char *const *einsums, const int
 deinsum_status deinsum_execute_batched(deinsum_batch_t b, const void *const *const *inputs, void *const *outputs,
                                        deinsum_stream_t stream);
 
-/* Time the split-BF16 batch with unit_div in {1, 2, 4, 8, 16, 32, 64} on the device,
- * keep the fastest (and, if DEINSUM_AUTOTUNE_CACHE names a file, append it
- * there for later plans with the same signature).  Synchronous. */
+/* Time the split-BF16 batch on the device and keep the fastest schedule: first the unit
+ * size of the whole batch (units of about total / (SMs x unit_div) bytes of X, unit_div in
+ * {1, 2, 4, 8, 16, 32, 64}), then, for each kind of instance present (tensor-map or
+ * row-class loads, K-major or MN-major operand), twice or half as many units for that kind
+ * while that is faster.  If DEINSUM_AUTOTUNE_CACHE names a file the result is appended there
+ * for later batches with the same signature.  Synchronous. */
 deinsum_status deinsum_batched_autotune(deinsum_batch_t b, const void *const *const *inputs,
                                         void *const *outputs, deinsum_stream_t stream, double *best_ms);
 

@@ -54,8 +54,16 @@ struct Inst {
     int kind = 0;   // 0: tensor map (or per-thread loads); 1 / 2: row classes, case 0 / case 1
 };
 
+// Kinds of instance the schedule tunes separately: 2 * load kind (tensor map, row classes case 0,
+// row classes case 1) + operand layout (K-major, MN-major).
+constexpr int kKinds = 6;
+struct TuneEntry {
+    int div = 4;              // units of about total / (grid * div) bytes ...
+    int shift[kKinds] = {};   // ... times 2^shift[k] more of them for the instances of kind k
+};
+
 std::mutex g_tune_mutex;
-std::map<std::string, int> g_tune_cache;  // batch signature -> unit divisor
+std::map<std::string, TuneEntry> g_tune_cache;  // batch signature -> unit sizes
 bool g_tune_loaded = false;
 
 void load_tune_cache() {
@@ -66,18 +74,21 @@ void load_tune_cache() {
     FILE *f = std::fopen(path, "r");
     if (!f) return;
     char key[256];
-    int div = 0;
-    while (std::fscanf(f, "%255s %d", key, &div) == 2) g_tune_cache[key] = div;
+    TuneEntry e;
+    while (std::fscanf(f, "%255s %d %d %d %d %d %d %d", key, &e.div, &e.shift[0], &e.shift[1], &e.shift[2],
+                       &e.shift[3], &e.shift[4], &e.shift[5]) == 8)
+        g_tune_cache[key] = e;
     std::fclose(f);
 }
 
-void store_tune_cache(const std::string &key, int div) {
-    g_tune_cache[key] = div;
+void store_tune_cache(const std::string &key, const TuneEntry &e) {
+    g_tune_cache[key] = e;
     const char *path = std::getenv("DEINSUM_AUTOTUNE_CACHE");
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d\n", key.c_str(), div);
+    std::fprintf(f, "%s %d %d %d %d %d %d %d\n", key.c_str(), e.div, e.shift[0], e.shift[1], e.shift[2], e.shift[3],
+                 e.shift[4], e.shift[5]);
     std::fclose(f);
 }
 
@@ -93,7 +104,8 @@ struct deinsum_batch_s {
     std::vector<Inst> inst;
     double total_bytes = 0.0;
     std::string signature;
-    int unit_div = 4;   // units of about total / (grid * unit_div) bytes
+    int unit_div = 4;   // units of about total / (grid * unit_div) bytes ...
+    int kind_shift[kKinds] = {};   // ... times 2^kind_shift[k] more for instances of kind k (kind_key)
     int n_sm = 0, grid = 0;          // CTAs of the launch (one per SM, at most one per unit)
     // schedule (host)
     std::vector<int64_t> units;      // 5 per unit, in the order the CTAs take them
@@ -135,10 +147,12 @@ double unit_cost(const Inst &in, int64_t fgs) {
     return double(fgs) * (double(in.g.n_kb) * chunk + double(in.g.R_pad) / 128.0);
 }
 
-// Units of about total / (grid * unit_div) bytes of X, in the order the CTAs take them.
+int kind_key(const Inst &in) { return 2 * in.kind + in.g.kcase; }
+
+// Units of about total / (grid * unit_div * 2^kind_shift) bytes of X, in the order the CTAs
+// take them.
 void build_batch_schedule(deinsum_batch_s *b) {
-    const int64_t target_units = int64_t(b->n_sm) * b->unit_div;
-    const double unit_bytes = std::max(1.0, b->total_bytes / double(target_units));
+    const double target_units = double(b->n_sm) * double(b->unit_div);
     struct U {
         int64_t inst, col, f0, f1, off;
         double cost;
@@ -162,6 +176,8 @@ void build_batch_schedule(deinsum_batch_s *b) {
     for (int i = 0; i < b->n; ++i) {
         const MttkrpGeom &g = b->inst[size_t(i)].g;
         const int64_t max_units = g.n_cols * g.fg_per_col;
+        const double scale = std::ldexp(1.0, b->kind_shift[kind_key(b->inst[size_t(i)])]);
+        const double unit_bytes = std::max(1.0, b->total_bytes / (target_units * scale));
         int64_t want = int64_t(std::ceil(b->inst[size_t(i)].xbytes / unit_bytes));
         want = std::max<int64_t>(1, std::min(want, max_units));
         const int64_t per_col = std::min<int64_t>(g.fg_per_col, std::max<int64_t>(1, (want + g.n_cols - 1) / g.n_cols));
@@ -194,10 +210,7 @@ void build_batch_schedule(deinsum_batch_s *b) {
     b->units.clear();
     std::vector<size_t> order(all.size());
     for (size_t k = 0; k < all.size(); ++k) order[k] = k;
-    auto key = [&](size_t k) {   // kind of load, then operand layout
-        const Inst &in = b->inst[size_t(all[k].inst)];
-        return 2 * in.kind + in.g.kcase;
-    };
+    auto key = [&](size_t k) { return kind_key(b->inst[size_t(all[k].inst)]); };   // load, then layout
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
         if (key(x) != key(y)) return key(x) < key(y);
         return all[x].cost > all[y].cost;
@@ -404,7 +417,10 @@ deinsum_status deinsum_plan_batched(int n, const char *const *einsums, const int
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         load_tune_cache();
         auto it = g_tune_cache.find(b->signature);
-        if (it != g_tune_cache.end()) b->unit_div = it->second;
+        if (it != g_tune_cache.end()) {
+            b->unit_div = it->second.div;
+            for (int k = 0; k < kKinds; ++k) b->kind_shift[k] = it->second.shift[k];
+        }
     }
     *out = b;
     return DEINSUM_OK;
@@ -451,7 +467,9 @@ deinsum_status deinsum_execute_batched(deinsum_batch_t b, const void *const *con
         }
         return DEINSUM_OK;
     }
-    return cudaGraphLaunch(b->gexec, s) == cudaSuccess ? DEINSUM_OK : DEINSUM_ERR_CUDA;
+    if (cudaGraphLaunch(b->gexec, s) != cudaSuccess) return DEINSUM_ERR_CUDA;
+    count_launch(3);   // the graph's kernels: preparation, tensor-core kernel, reduction
+    return DEINSUM_OK;
 }
 
 deinsum_status deinsum_batched_autotune(deinsum_batch_t b, const void *const *const *inputs, void *const *outputs,
@@ -462,14 +480,10 @@ deinsum_status deinsum_batched_autotune(deinsum_batch_t b, const void *const *co
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int cand[] = {1, 2, 4, 8, 16, 32, 64};
-    int best = b->unit_div;
-    double best_t = 1e30;
-    for (int div : cand) {
-        b->unit_div = div;
+    // ms per execute of the current schedule (two untimed, three timed; < 0 on an error)
+    auto time_it = [&]() -> double {
         b->tables_uploaded = false;
-        deinsum_status st = ensure_ready(b, inputs, outputs, s);
-        if (st != DEINSUM_OK) return st;
+        if (ensure_ready(b, inputs, outputs, s) != DEINSUM_OK) return -1.0;
         for (int r = 0; r < 2; ++r) launch_batch(b, s);
         cudaEventRecord(e0, s);
         for (int r = 0; r < 3; ++r) launch_batch(b, s);
@@ -477,18 +491,56 @@ deinsum_status deinsum_batched_autotune(deinsum_batch_t b, const void *const *co
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms / 3.0 < best_t) {
-            best_t = ms / 3.0;
+        return ms / 3.0;
+    };
+    auto fail = [&]() {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return DEINSUM_ERR_CUDA;
+    };
+    // the unit size of the whole batch, then one pass over the kinds of instance present,
+    // halving or doubling each kind's unit count while that is faster
+    for (int k = 0; k < kKinds; ++k) b->kind_shift[k] = 0;
+    const int cand[] = {1, 2, 4, 8, 16, 32, 64};
+    int best = b->unit_div;
+    double best_t = 1e30;
+    for (int div : cand) {
+        b->unit_div = div;
+        const double t = time_it();
+        if (t < 0) return fail();
+        if (t < best_t) {
+            best_t = t;
             best = div;
+        }
+    }
+    b->unit_div = best;
+    bool present[kKinds] = {};
+    for (const Inst &in : b->inst) present[kind_key(in)] = true;
+    for (int k = 0; k < kKinds; ++k) {
+        if (!present[k]) continue;
+        for (int step : {1, -1}) {
+            while (std::abs(b->kind_shift[k] + step) <= 3) {
+                b->kind_shift[k] += step;
+                const double t = time_it();
+                if (t < 0) return fail();
+                if (t < best_t) {
+                    best_t = t;
+                } else {
+                    b->kind_shift[k] -= step;
+                    break;
+                }
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->unit_div = best;
     b->tables_uploaded = false;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        store_tune_cache(b->signature, best);
+        TuneEntry e;
+        e.div = b->unit_div;
+        for (int k = 0; k < kKinds; ++k) e.shift[k] = b->kind_shift[k];
+        store_tune_cache(b->signature, e);
     }
     if (best_ms) *best_ms = best_t;
     return ensure_ready(b, inputs, outputs, s);
