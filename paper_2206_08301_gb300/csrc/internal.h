@@ -104,6 +104,7 @@ struct MttkrpArgs {
     double *partial64;                 // n_units x 128 x R_pad (F64 path)
     int *status;                       // device status word
     uint64_t wait_ns;                  // limit of a pipeline wait (set by the launcher)
+    float *ttm_out;                    // launch_ttm_tc only: Y (see there)
 };
 
 // Many MTTKRP instances in one persistent launch of the tensor-core kernel: per-instance
@@ -214,6 +215,13 @@ constexpr int kTtmcTc2MaxKt = 2;   // k tiles the tensor-core stage 2 keeps resi
 int launch_mttkrp_plain_f32(const MttkrpArgs &a, int n_sm, void *stream);
 int launch_mttkrp_plain_f64(const MttkrpArgs &a, int n_sm, void *stream);
 int launch_mttkrp_tc(const MttkrpArgs &a, int n_sm, void *stream);
+// One TTM of a chain on the tensor cores, Y[a, r, b] = sum_i X[a, i, b] U[i, r] (split BF16,
+// FP32 accumulation), with X seen as the order-3 tensor (A, I, B) whose last mode b is the
+// row of the MTTKRP view (geometry of mttkrp_prepare_oneoff(3, {A, I, B}, 2, R, X, a, false),
+// X through its tensor map): every fiber group (128 rows b, one outer index a) is one output
+// tile, written to a.ttm_out (A x R x B, FP32) instead of being folded with weights.  Needs
+// a.U[1] = U, its split tiles in a.Bsplit (launch_split_inner_factor) and a unit table.
+int launch_ttm_tc(const MttkrpArgs &a, int n_sm, void *stream);
 int launch_split_inner_factor(const MttkrpArgs &a, void *bsplit, void *stream);
 // Weight tables of the tensor-core kernel (a.Lw, a.Ow; sizes below).
 int launch_weight_tables(const MttkrpArgs &a, void *stream);

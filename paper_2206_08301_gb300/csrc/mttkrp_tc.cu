@@ -54,9 +54,12 @@ __global__ void weight_tables_kernel(const __grid_constant__ MttkrpArgs a) {
 // to a multiple of four (14 -> 16), and 16 x 32 x 128 is the SM's 65,536; a 144-register
 // build of this 448-thread kernel fails to launch.  The rank-64 instances with per-row
 // weights (64 accumulators and a float4 weight row per thread in the epilogue) spill there.
-template <int RP, bool OP, bool MN, bool PW, bool RC>
+// TTM: one TTM of a chain (launch_ttm_tc): no weights; every fiber group's result is an
+// output tile of its own, written to a.ttm_out.
+template <int RP, bool OP, bool MN, bool PW, bool RC, bool TTM = false>
 __global__ void __maxnreg__(128)
 mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
+    static_assert(!TTM || (MN && !OP && !PW && !RC), "the TTM form takes the last-mode view through a tensor map");
     static_assert(!OP || PW, "packed outer indices weight every row group");
     static_assert(!(OP && RC), "row classes are not used with packed outer indices");
     using C = TcCfg<RP>;
@@ -191,7 +194,7 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             uint32_t r_used = 0, r_par = 0, w_used = 0, w_par = 0;
             int64_t fgi = 0;
             for (int64_t chunk = 0; !it.done; ++chunk) {
-                if (it.kb == it.kb_lo) {
+                if (!TTM && it.kb == it.kb_lo) {
                     const int ws = int(fgi % C::WSLOTS);
                     const uint32_t wj = uint32_t(fgi / C::WSLOTS);
                     if (!mbar_wait(wempty(ws), (wj & 1u) ^ 1u, abort_flag, a.status, wlim)) break;
@@ -283,6 +286,41 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             mbar_drain(drain, 0, a.status);
         }
         __syncwarp();
+    } else if constexpr (TTM) {
+        // ------------------------------------------------------- TTM write-out
+        // every fiber group (a column of 128 rows b, outer index o = a) is one output tile:
+        // Y[o, r, b] = T[b, r], the U_hi and U_lo columns added; rows past I_n are not written
+        const int quad = warp & 3;
+        const int l = quad * 32 + lane;
+        float *Y = a.ttm_out;
+        Iter it;
+        it.init(a);
+        int64_t fgi = 0;
+        while (!it.done) {
+            const int b = int(fgi % C::NACC);
+            const uint32_t jb = uint32_t(fgi / C::NACC);
+            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), jb & 1u, abort_flag, a.status, wlim))) break;
+            tc_fence_after();
+            const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + uint32_t(b * C::ACC);
+            const int64_t row = it.col * BM + l;
+            const bool rv = row < g.I;
+            float *yr = Y + it.o * int64_t(g.R) * g.I + row;
+            #pragma unroll
+            for (int c = 0; c < RP; c += 16) {
+                uint32_t t[16], tl[16];
+                tmem_ld16(taddr + uint32_t(c), t);
+                tmem_ld16(taddr + uint32_t(RP + c), tl);
+                tmem_wait_ld();
+                #pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (rv && c + q < g.R) yr[int64_t(c + q) * g.I] = __uint_as_float(t[q]) + __uint_as_float(tl[q]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce(b));
+            ++fgi;
+            it.next_fg(a);
+        }
     } else {
         // ------------------------------------------------------------- epilogue
         const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
@@ -427,17 +465,17 @@ __global__ void split_inner_factor_kernel(const float *__restrict__ U, const flo
     }
 }
 
-template <int RP, bool OP, bool MN, bool PW, bool RC = false>
+template <int RP, bool OP, bool MN, bool PW, bool RC = false, bool TTM = false>
 int launch_tc_rp_op(const MttkrpArgs &a, int n_sm, void *stream) {
     using C = TcCfg<RP>;
-    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_kernel<RP, OP, MN, PW, RC>,
+    cudaError_t e = cudaFuncSetAttribute(mttkrp_tc_kernel<RP, OP, MN, PW, RC, TTM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
     if (e != cudaSuccess) return int(e);
     int64_t grid = a.n_units < n_sm ? a.n_units : n_sm;
     if (grid < 1) grid = 1;
     MttkrpArgs ka = a;
     ka.wait_ns = wait_limit_ns();
-    mttkrp_tc_kernel<RP, OP, MN, PW, RC><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(ka);
+    mttkrp_tc_kernel<RP, OP, MN, PW, RC, TTM><<<unsigned(grid), C::THREADS, C::SMEM, static_cast<cudaStream_t>(stream)>>>(ka);
     count_launch();
     return int(cudaGetLastError());
 }
@@ -494,6 +532,16 @@ int launch_weight_tables(const MttkrpArgs &a, void *stream) {
     weight_tables_kernel<<<unsigned(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(a);
     count_launch();
     return int(cudaGetLastError());
+}
+
+int launch_ttm_tc(const MttkrpArgs &a, int n_sm, void *stream) {
+    if (!a.ttm_out || !a.use_tma || a.g.kcase != 1 || a.g.opack || a.g.kseg != 1) return int(cudaErrorInvalidValue);
+    switch (a.g.R_pad) {
+        case 16: return launch_tc_rp_op<16, false, true, false, false, true>(a, n_sm, stream);
+        case 32: return launch_tc_rp_op<32, false, true, false, false, true>(a, n_sm, stream);
+        case 64: return launch_tc_rp_op<64, false, true, false, false, true>(a, n_sm, stream);
+    }
+    return int(cudaErrorInvalidValue);
 }
 
 int launch_mttkrp_tc(const MttkrpArgs &a, int n_sm, void *stream) {

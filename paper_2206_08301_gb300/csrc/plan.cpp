@@ -90,6 +90,17 @@ struct deinsum_plan_s {
     float *d_wtab = nullptr;   // weight tables of the tensor-core kernel (L, then O)
     int *d_status = nullptr;
     void *d_ttm[2] = {nullptr, nullptr};
+    // fused TTMc: the chain's TTMs that run on the tensor cores (launch_ttm_tc), each with its
+    // row view (A, I, B) and a unit table of its own (the tables back to back, 3 int64 a unit)
+    struct TtmStage {
+        int tc = 0;
+        int64_t unit_off = 0, n_units = 0;
+    };
+    std::vector<TtmStage> ttm_stages;
+    std::vector<int64_t> ttm_units;
+    size_t ttm_bsplit_bytes = 0;
+    int64_t *d_ttm_units = nullptr;
+    void *d_ttm_bsplit = nullptr;
     float *d_t2 = nullptr;
     void *d_tbsplit = nullptr;
     float *d_u2pad = nullptr;
@@ -320,8 +331,67 @@ deinsum_status cuda_status(cudaError_t e) {
 
 struct WsLayout {
     size_t status = 0, units = 0, cols = 0, partial = 0, bsplit = 0, wtab = 0, ttm0 = 0, ttm1 = 0, t2 = 0, tb = 0, u2 = 0,
-           total = 0;
+           tunits = 0, tbs = 0, total = 0;
 };
+
+// Row view of one TTM of a fused TTMc chain, Y[a, r, b] = sum_i X[a, i, b] U[i, r], as the
+// last-mode MTTKRP view of the order-3 tensor (A, I, B) (no packing, no k segments: the
+// geometry mttkrp_prepare_oneoff gives with allow_opack = false).
+MttkrpGeom ttm_stage_geometry(int64_t A, int64_t I, int64_t B, int R) {
+    deinsum_plan_s tmp;
+    tmp.kind = DEINSUM_KIND_MTTKRP;
+    tmp.no_opack = true;
+    tmp.order = 3;
+    tmp.mode = 2;
+    tmp.dtype = DEINSUM_F32;
+    tmp.prec = DEINSUM_PREC_SPLIT_BF16;
+    const int64_t d[3] = {A, I, B};
+    for (int m = 0; m < 3; ++m) {
+        tmp.dims[m] = d[m];
+        tmp.ranks[m] = m == 2 ? d[m] : R;
+    }
+    build_mttkrp_geometry(&tmp);
+    return tmp.geom;
+}
+
+// The chain's TTMs after the fused pair: which run on the tensor cores (the trailing extent B
+// a multiple of 4 for the tensor map of rows b, R <= 64; the first two at most: each split-BF16
+// stage adds about 1e-6 to the relative error, 4.9e-6 -> 6.1e-6 at 256^4 with one and
+// 5.4e-6 -> 7.4e-6 at 60^5 with two, and the later, smaller stages stay in FP32 so that the
+// chain keeps the 1e-5 gate at any order), and their unit tables for `target` persistent CTAs.
+void build_ttm_stages(deinsum_plan_s *pl, int64_t target) {
+    const int N = pl->order;
+    pl->ttm_stages.assign(pl->ttm_rest.size(), deinsum_plan_s::TtmStage{});
+    pl->ttm_units.clear();
+    pl->ttm_bsplit_bytes = 0;
+    int64_t cur[DEINSUM_MAX_ORDER];
+    for (int m = 0; m < N; ++m) cur[m] = (m >= N - 2) ? pl->ranks[m] : pl->dims[m];
+    for (size_t s = 0; s < pl->ttm_rest.size(); ++s) {
+        const int m = pl->ttm_rest[s];
+        int64_t A = 1, B = 1;
+        for (int k = 0; k < m; ++k) A *= cur[k];
+        for (int k = m + 1; k < N; ++k) B *= cur[k];
+        const int R = int(pl->ranks[m]);
+        if (s < 2 && B % 4 == 0 && R <= 64) {
+            const MttkrpGeom g = ttm_stage_geometry(A, cur[m], B, R);
+            if (g.kcase == 1 && !g.opack && g.kseg == 1) {
+                deinsum_plan_s::TtmStage &st = pl->ttm_stages[s];
+                st.tc = 1;
+                st.unit_off = int64_t(pl->ttm_units.size() / 3);
+                const int64_t per_col = balanced_units_per_col(g.n_cols, g.fg_per_col, target, 8 * target);
+                for (int64_t c = 0; c < g.n_cols; ++c)
+                    for (int64_t u = 0; u < per_col; ++u) {
+                        const int64_t f0 = g.fg_per_col * u / per_col, f1 = g.fg_per_col * (u + 1) / per_col;
+                        if (f1 > f0) pl->ttm_units.insert(pl->ttm_units.end(), {c, f0, f1});
+                    }
+                st.n_units = int64_t(pl->ttm_units.size() / 3) - st.unit_off;
+                pl->ttm_bsplit_bytes =
+                    std::max(pl->ttm_bsplit_bytes, size_t(g.n_kb) * 2 * size_t(g.R_pad) * DEINSUM_BK * 2);
+            }
+        }
+        cur[m] = R;
+    }
+}
 
 // Fix the device (the current one), the schedule (one unit per resident CTA:
 // the tensor-core kernel keeps one CTA per SM, the plain kernel as many as its
@@ -341,6 +411,8 @@ deinsum_status plan_layout(deinsum_plan_s *pl, WsLayout &L) {
             if (pl->prec == DEINSUM_PREC_PLAIN)
                 per_sm = mttkrp_plain_ctas_per_sm(pl->dtype == DEINSUM_F64 ? 1 : 0, pl->geom.R_pad);
             build_schedule(pl, int64_t(nsm) * per_sm);
+        } else if (pl->ttmc_fused) {
+            build_ttm_stages(pl, nsm);
         }
     }
     size_t off = 0;
@@ -371,6 +443,10 @@ deinsum_status plan_layout(deinsum_plan_s *pl, WsLayout &L) {
         off = align_up(off + size_t(pl->t_nkb) * 2 * 32 * DEINSUM_BK * 2, 1024);
         L.u2 = off;   // U_{N-2} padded to n_kt*128 rows x 32
         off = align_up(off + size_t(pl->t_nkt) * DEINSUM_BM * 32 * sizeof(float), 256);
+        L.tunits = off;   // the chain's tensor-core TTMs: unit tables, split factor tiles
+        off = align_up(off + pl->ttm_units.size() * sizeof(int64_t), 1024);
+        L.tbs = off;
+        off = align_up(off + pl->ttm_bsplit_bytes, 256);
     } else {
         L.ttm0 = off;
         off = align_up(off + size_t(pl->ttm_buf_elems) * elem_size(pl->dtype), 256);
@@ -409,6 +485,13 @@ deinsum_status attach_workspace(deinsum_plan_s *pl, char *ws, const WsLayout &L,
             pl->d_t2 = reinterpret_cast<float *>(pl->ws + L.t2);
             pl->d_tbsplit = pl->ws + L.tb;
             pl->d_u2pad = reinterpret_cast<float *>(pl->ws + L.u2);
+            pl->d_ttm_units = reinterpret_cast<int64_t *>(pl->ws + L.tunits);
+            pl->d_ttm_bsplit = pl->ws + L.tbs;
+            if (!pl->ttm_units.empty()) {
+                e = cudaMemcpyAsync(pl->d_ttm_units, pl->ttm_units.data(), pl->ttm_units.size() * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, stream);
+                if (e != cudaSuccess) return cuda_status(e);
+            }
         }
     }
     return DEINSUM_OK;
@@ -853,6 +936,27 @@ deinsum_status execute_ttmc_fused(deinsum_plan_s *pl, const void *const *inputs,
         for (int k = 0; k < m; ++k) A *= cur[k];
         for (int k = m + 1; k < N; ++k) B *= cur[k];
         void *dst = (s + 1 == pl->ttm_rest.size()) ? output : pl->d_ttm[s % 2];
+        if (s < pl->ttm_stages.size() && pl->ttm_stages[s].tc) {
+            // on the tensor cores (its own input is a 16-byte aligned workspace buffer)
+            MttkrpArgs a;
+            std::memset(static_cast<void *>(&a), 0, sizeof(a));
+            const int64_t d3[3] = {A, cur[m], B};
+            mttkrp_prepare_oneoff(3, d3, 2, int(pl->ranks[m]), src, &a, false);
+            if (a.use_tma) {
+                a.X = src;
+                a.U[1] = U[m];
+                a.Bsplit = pl->d_ttm_bsplit;
+                a.units = pl->d_ttm_units + 3 * pl->ttm_stages[s].unit_off;
+                a.n_units = pl->ttm_stages[s].n_units;
+                a.status = pl->d_status;
+                a.ttm_out = static_cast<float *>(dst);
+                err = launch_split_inner_factor(a, pl->d_ttm_bsplit, stream);
+                if (!err) err = launch_ttm_tc(a, pl->n_sm, stream);
+                cur[m] = pl->ranks[m];
+                src = dst;
+                continue;
+            }
+        }
         err = launch_ttm_plain_f32(static_cast<const float *>(src), static_cast<const float *>(U[m]),
                                    static_cast<float *>(dst), A, cur[m], B, pl->ranks[m], stream);
         cur[m] = pl->ranks[m];

@@ -7,7 +7,7 @@ multiple of 64), a k extent below one tile, ranks below the padded 32, orders
 3 to 5, every kept mode the fused path takes, rows of X that are not 16-byte
 aligned (the row-class tensor maps), and order-5 chains with the kept mode before or
 between the two chain modes, ragged trailing extents and ranks that are not multiples
-of 8.
+of 8, and order-6 chains (two chain TTMs on the tensor cores, the third in FP32).
 """
 import numpy as np
 import pytest
@@ -50,6 +50,9 @@ CASES = [
     ((9, 11, 40, 64, 36), 1, (13, 21, 24, 16)),  # kept mode 1 between the two chain modes
     ((7, 30, 50, 60, 20), 0, (19, 11, 8, 5)),    # ranks 19 / 11, trailing extent 40
     ((6, 50, 9, 64, 20), 0, (40, 7, 16, 8)),     # R_1 = 40
+    # order 6: three chain stages, the first two on the tensor cores, the last in FP32
+    ((5, 6, 7, 8, 60, 36), 0, (4, 5, 6, 24, 16)),
+    ((6, 5, 30, 7, 40, 44), 1, (3, 9, 5, 20, 12)),
 ]
 
 
