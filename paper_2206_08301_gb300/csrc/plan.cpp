@@ -378,7 +378,19 @@ void build_ttm_stages(deinsum_plan_s *pl, int64_t target) {
                 deinsum_plan_s::TtmStage &st = pl->ttm_stages[s];
                 st.tc = 1;
                 st.unit_off = int64_t(pl->ttm_units.size() / 3);
-                const int64_t per_col = balanced_units_per_col(g.n_cols, g.fg_per_col, target, 8 * target);
+                // a TTM unit writes its own output tiles (no partial sums to reduce), so units can
+                // be fine: the split with the best balance over whole waves, up to 64 per CTA
+                const double mean = double(g.n_cols) * double(g.fg_per_col) / double(target);
+                int64_t per_col = 1;
+                double best_eff = 0.0;
+                for (int64_t p = 1; p <= g.fg_per_col && g.n_cols * p <= 64 * target; ++p) {
+                    const int64_t waves = (g.n_cols * p + target - 1) / target;
+                    const double e = mean / double(waves * ((g.fg_per_col + p - 1) / p));
+                    if (e > best_eff + 0.005) {
+                        best_eff = e;
+                        per_col = p;
+                    }
+                }
                 for (int64_t c = 0; c < g.n_cols; ++c)
                     for (int64_t u = 0; u < per_col; ++u) {
                         const int64_t f0 = g.fg_per_col * u / per_col, f1 = g.fg_per_col * (u + 1) / per_col;
