@@ -50,6 +50,10 @@ CASES = [
     ((9, 11, 40, 64, 36), 1, (13, 21, 24, 16)),  # kept mode 1 between the two chain modes
     ((7, 30, 50, 60, 20), 0, (19, 11, 8, 5)),    # ranks 19 / 11, trailing extent 40
     ((6, 50, 9, 64, 20), 0, (40, 7, 16, 8)),     # R_1 = 40
+    # chain TTMs on the tensor cores at their edges: a trailing extent of one 128-row column
+    # then rank 64 (R_pad 64); a trailing extent of 8 (an 8-row box)
+    ((3, 70, 5, 64, 36), 0, (64, 3, 16, 8)),
+    ((5, 7, 2, 8, 12), 0, (3, 2, 1, 4)),
     # order 6: three chain stages, the first two on the tensor cores, the last in FP32
     ((5, 6, 7, 8, 60, 36), 0, (4, 5, 6, 24, 16)),
     ((6, 5, 30, 7, 40, 44), 1, (3, 9, 5, 20, 12)),
