@@ -1,4 +1,4 @@
-"""Pins of the oracle's error metric: every parity verdict goes through it.
+"""Pins of the oracle's error metric: every parity check goes through it.
 
 ``oracle.frobenius`` (the C routine ``oracle_frobenius``), ``oracle.rel_error``
 and ``oracle.max_elem_error`` decide whether a GPU result passes, so each is
