@@ -117,6 +117,9 @@ ROWCLASS_CASES = [
     ((50, 300, 133), 0, (17, 31), 3),           # order 3, I_{N-2} = 300: CUDA-core stage 2
     ((6, 7, 8, 90, 45), 0, (3, 5, 32, 7), 2),   # order 5, two chain stages after the fused pair
     ((4, 6, 60, 60, 61), 0, (24, 24, 24, 24), 0),   # the paper's order-5 shape with an odd last mode
+    ((7, 64, 66), 0, (9, 20), 0),               # slabs of exactly 64 rows
+    ((3, 65, 70), 0, (9, 20), 1),               # 65-row slabs, X one float into its buffer
+    ((5, 3, 5, 9), 0, (2, 3, 7), 2),            # 3-row slabs, 9-word rows
 ]
 
 
