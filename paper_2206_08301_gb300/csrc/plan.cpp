@@ -41,6 +41,8 @@ uint64_t wait_limit_ns() {
     const uint64_t v = g_wait_limit_ns.load(std::memory_order_relaxed);
     return v ? v : 2000000000ull;
 }
+// The row-class maps of encode_x_rowclass_maps with case-0 boxes of `rows` rows.
+static bool encode_rowclass_maps_rows(const MttkrpGeom &g, const void *X, CUtensorMap *maps, int rows);
 }  // namespace deinsum
 
 struct deinsum_plan_s {
@@ -895,17 +897,19 @@ deinsum_status execute_ttmc_fused(deinsum_plan_s *pl, const void *const *inputs,
         t.sg = pl->t_sg;
     } else {
         // rows not 16-byte aligned (I_{N-1} not a multiple of 4, or X itself): the four
-        // row-class maps of the one-slab-per-tile view, cached per X pointer
-        ttm_last_geometry(N, pl->t_S, pl->dims[N - 2], pl->dims[N - 1], int(pl->ranks[N - 1]), &t.g, 1);
+        // row-class maps, cached per X pointer; slabs of at most 64 (32) rows packed two
+        // (four) to a tile as in the aligned kernel, with class boxes of 32 / sg rows
+        const int sg = pl->t_nkt <= kTtmcTc2MaxKt ? ttmc_slab_group(pl->dims[N - 2]) : 1;
+        ttm_last_geometry(N, pl->t_S, pl->dims[N - 2], pl->dims[N - 1], int(pl->ranks[N - 1]), &t.g, sg);
         if (pl->xrow_ptr != inputs[0]) {
             pl->xrow_ptr = inputs[0];
-            pl->xrow_ok = encode_x_rowclass_maps(t.g, inputs[0], pl->xrow) ? 1 : 0;
+            pl->xrow_ok = encode_rowclass_maps_rows(t.g, inputs[0], pl->xrow, DEINSUM_BM / 4 / sg) ? 1 : 0;
         }
         if (!pl->xrow_ok) return DEINSUM_ERR_ALIGN;
         for (int c = 0; c < 4; ++c) t.xrow[c] = pl->xrow[c];
         t.X = inputs[0];
         t.row_classes = 1;
-        t.sg = 1;
+        t.sg = sg;
     }
     // split tiles of U_{N-1} (the same layout as the MTTKRP inner factor)
     MttkrpArgs sa;
@@ -1022,7 +1026,8 @@ bool rowclass_supported(const MttkrpGeom &g) {
     return !g.opack && n >= 4 && len + 3 < lim && n < 4 * lim;
 }
 
-bool encode_x_rowclass_maps(const MttkrpGeom &g, const void *X, CUtensorMap *maps) {
+// The same maps with case-0 boxes of `rows` rows (32, or 32 / SG for slabs packed SG to a tile).
+static bool encode_rowclass_maps_rows(const MttkrpGeom &g, const void *X, CUtensorMap *maps, int rows) {
     auto enc = tensor_map_encoder();
     if (!enc || !rowclass_supported(g) || (reinterpret_cast<uintptr_t>(X) & 3) != 0) return false;
     const int64_t len = g.kcase == 0 ? g.Q : g.I;
@@ -1035,7 +1040,7 @@ bool encode_x_rowclass_maps(const MttkrpGeom &g, const void *X, CUtensorMap *map
         cuuint64_t dims[2] = {cuuint64_t(len + d), cuuint64_t((n - c + 3) / 4)};
         cuuint64_t strides[1] = {cuuint64_t(4 * len) * 4};
         cuuint32_t box[2] = {g.kcase == 0 ? cuuint32_t(DEINSUM_BK + 4) : cuuint32_t(DEINSUM_BM + 4),
-                             g.kcase == 0 ? cuuint32_t(DEINSUM_BM / 4) : cuuint32_t(DEINSUM_BK / 4)};
+                             g.kcase == 0 ? cuuint32_t(rows) : cuuint32_t(DEINSUM_BK / 4)};
         cuuint32_t estr[2] = {1, 1};
         if (enc(&maps[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1043,6 +1048,10 @@ bool encode_x_rowclass_maps(const MttkrpGeom &g, const void *X, CUtensorMap *map
             return false;
     }
     return true;
+}
+
+bool encode_x_rowclass_maps(const MttkrpGeom &g, const void *X, CUtensorMap *maps) {
+    return encode_rowclass_maps_rows(g, X, maps, DEINSUM_BM / 4);
 }
 
 // Converter view of one raw chunk (128 k rows x 64 l) of the last-mode TTM kernels:

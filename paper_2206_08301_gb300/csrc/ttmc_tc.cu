@@ -120,11 +120,79 @@ __device__ __forceinline__ float4 *t1_slot(float *t1s, int r, int x) {
     return reinterpret_cast<float4 *>(t1s + r * TtmcCfg<>::RP) + (x ^ (r & 7));
 }
 
+// Row classes with SG > 1 packed slabs (I_{N-2} <= 128 / SG): slab g of the group fills tile
+// rows g KP .. g KP + KP - 1 (KP = 128 / SG), rows past I_{N-2} in it being the next slab's
+// rows (finite values against the zero rows of U_{N-2}) or zero past X.  The class boxes hold
+// KP / 4 rows each (the maps are encoded so): for class c, slab g's box goes to rows
+// g KP / 4 .. of the class's 32-row region, so tile row l of any slab sits at region row
+// l / 4, as with one slab per tile, and only the class and word offset change per slab.
+template <int SG>
+__device__ __forceinline__ void rc_load_packed(const TtmcArgs &a, int64_t grp, int kb, uint32_t dst, uint32_t bar) {
+    constexpr int KP = BM / SG;
+    mbar_arrive_expect_tx(bar, kRcRawBytes);   // 4 classes x SG boxes of KP / 4 rows
+    const uint64_t xw = word_index(a.X);
+    const int64_t x0 = int64_t(kb) * BK;
+    #pragma unroll
+    for (int g = 0; g < SG; ++g) {
+        const int64_t rowbase = (grp * SG + g) * a.g.I;
+        #pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t rc = rowbase + ((c - rowbase) & 3);          // slab's first row of class c
+            const int64_t x = int64_t((xw + uint64_t(c) * uint64_t(a.g.Q)) & 3u) + x0;
+            tma_load_2d(dst + uint32_t((c * kRcRows0 + g * (KP / 4)) * kRcPitch0 * 4), &a.xrow[c],
+                        int(x & ~int64_t(3)), int((rc - c) >> 2), bar);
+        }
+    }
+}
+// JN rows of one class run (4 words each, box rows 4 apart) starting at word d of address r.
+template <int JN>
+__device__ __forceinline__ void rc_read_run(uint32_t r, int d, float4 *v) {
+    constexpr uint32_t JS = 4u * kRcPitch0 * 4u;
+    switch (d) {
+        case 0:
+            #pragma unroll
+            for (int j = 0; j < JN; ++j) v[j] = lds128(r + JS * j);
+            break;
+        case 1:
+            #pragma unroll
+            for (int j = 0; j < JN; ++j) v[j] = lds_words(r + JS * j, 1);
+            break;
+        case 2:
+            #pragma unroll
+            for (int j = 0; j < JN; ++j) v[j] = lds_words(r + JS * j, 2);
+            break;
+        default:
+            #pragma unroll
+            for (int j = 0; j < JN; ++j) v[j] = lds_words(r + JS * j, 3);
+            break;
+    }
+}
+// The converter's rows rsub + 16 j (rowcls_thread layout) of a packed group: j in
+// [g 8 / SG, (g + 1) 8 / SG) belongs to slab g, of class (slab start + rsub) mod 4.
+template <int SG>
+__device__ __forceinline__ void rc_read_packed(const TtmcArgs &a, int64_t grp, int kb, const float *raw, int pt,
+                                               float4 (&v)[8]) {
+    constexpr int JG = 8 / SG;
+    const int k4 = pt & 15, rsub = pt >> 4;
+    const uint64_t xw = word_index(a.X);
+    const uint64_t x0 = uint64_t(kb) * BK;
+    #pragma unroll
+    for (int g = 0; g < SG; ++g) {
+        const uint64_t row = uint64_t((grp * SG + g) * a.g.I + rsub);
+        const int d = int((xw + row * uint64_t(a.g.Q) + x0) & 3u);
+        const int c = int(row & 3u);
+        const uint32_t r = smem_u32(raw) +
+                           uint32_t(((c * kRcRows0 + (rsub >> 2) + 4 * g * JG) * kRcPitch0 + 4 * k4) * 4);
+        rc_read_run<JG>(r, d, v + g * JG);
+    }
+}
+
 // STORE: the epilogue writes the T1 tiles to HBM (a.T2 as S x I_{N-2} x R_{N-1}:
 // the TTM over the last mode alone) instead of running stage 2.  SG: slabs per
 // tile (a.sg).  TC2: stage 2 on the tensor cores (a.tc2), else on CUDA cores.
-// RC: X through the row-class maps a.xrow (rows of I_{N-1} words not 16-byte aligned;
-// one slab per tile, the tile's rows s I_{N-2} + 128 kt + l as in the MTTKRP case-0 view).
+// RC: X through the row-class maps a.xrow (rows of I_{N-1} words not 16-byte aligned; with
+// SG = 1 the tile's rows s I_{N-2} + 128 kt + l as in the MTTKRP case-0 view, with SG > 1
+// the packed slabs of rc_load_packed).
 template <bool STORE, int SG, bool TC2, bool RC>
 __global__ void __launch_bounds__(TtmcCfg<RC, TC2>::THREADS, 1)
 ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
@@ -132,7 +200,6 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     constexpr int RS = C::RS, AS = C::AS, RP = C::RP;
     static_assert(!STORE || (SG == 1 && !TC2), "the last-mode TTM keeps one slab per tile");
     static_assert(TC2 || SG == 1, "packed slabs take the tensor-core stage 2");
-    static_assert(!RC || SG == 1, "row classes keep one slab per tile");
     // Packed short slabs (one 64-wide l chunk per tile at most once the tile is full, so the
     // T1 feed runs per chunk): stage 1 takes three split products (X_hi U_hi + X_hi U_lo +
     // X_lo U_hi) into RP accumulator columns, halving the feed's TMEM reads; the other
@@ -240,7 +307,8 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             const uint32_t rj = uint32_t(chunk / RS);
             if (!__all_sync(0xffffffffu, mbar_wait(raw_full(rs), rj & 1u, abort_flag, status, wlim))) break;
             const float *raw = reinterpret_cast<const float *>(raw_base + size_t(rs) * C::RAW_STAGE);
-            if constexpr (RC) conv_read_rowcls(a.g, a.X, it.kt, it.s, 0, it.kb, raw, rowcls_thread(pt), v);
+            if constexpr (RC && SG > 1) rc_read_packed<SG>(a, it.s, it.kb, raw, rowcls_thread(pt), v);
+            else if constexpr (RC) conv_read_rowcls(a.g, a.X, it.kt, it.s, 0, it.kb, raw, rowcls_thread(pt), v);
             else if (!a.g.narrow) conv_read_smem_wide(raw, pt, v);
             else conv_read_smem_t<false>(a.g, BM, raw, pt, v);
             // hand the raw stage back to the TMA warp before the split, so that its next
@@ -281,7 +349,9 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 const int rs = int(chunk % RS);
                 const uint32_t rj = uint32_t(chunk / RS);
                 if (!mbar_wait(raw_empty(rs), (rj & 1u) ^ 1u, abort_flag, status, wlim)) break;
-                if constexpr (RC) {
+                if constexpr (RC && SG > 1) {
+                    rc_load_packed<SG>(a, it.s, it.kb, raw_addr(rs), raw_full(rs));
+                } else if constexpr (RC) {
                     rowcls_load(a.g, a.X, a.xrow, it.kt, it.s, 0, it.kb, raw_addr(rs), raw_full(rs));
                 } else {
                     mbar_arrive_expect_tx(raw_full(rs), a.box_bytes);
@@ -749,9 +819,11 @@ int launch_ttmc_variant(const TtmcArgs &a, int n_sm, void *stream) {
 
 int launch_ttmc_fused(const TtmcArgs &a, int n_sm, void *stream) {
     if (a.row_classes) {
-        if (a.sg != 1) return int(cudaErrorInvalidValue);
+        if (a.sg != 1 && (!a.tc2 || a.sg != ttmc_slab_group(a.g.I))) return int(cudaErrorInvalidValue);
         if (a.tc2) {
             if (a.n_kt > kTtmcTc2MaxKt) return int(cudaErrorInvalidValue);
+            if (a.sg == 4) return launch_ttmc_variant<false, 4, true, true>(a, n_sm, stream);
+            if (a.sg == 2) return launch_ttmc_variant<false, 2, true, true>(a, n_sm, stream);
             return launch_ttmc_variant<false, 1, true, true>(a, n_sm, stream);
         }
         return launch_ttmc_variant<false, 1, false, true>(a, n_sm, stream);

@@ -113,13 +113,16 @@ ROWCLASS_CASES = [
     # (dims, keep, ranks, X offset in floats)
     ((8, 9, 130, 66), 0, (5, 16, 12), 0),       # I_{N-1} = 66: rows 8 bytes off, two l chunks
     ((8, 9, 130, 64), 0, (5, 16, 12), 1),       # aligned shape, X one float into its buffer
-    ((31, 7, 60, 61), 0, (5, 24, 24), 0),       # short slabs (I_{N-2} = 60) one per tile
+    ((31, 7, 60, 61), 0, (5, 24, 24), 0),       # short slabs (I_{N-2} = 60) two to a tile
     ((50, 300, 133), 0, (17, 31), 3),           # order 3, I_{N-2} = 300: CUDA-core stage 2
     ((6, 7, 8, 90, 45), 0, (3, 5, 32, 7), 2),   # order 5, two chain stages after the fused pair
     ((4, 6, 60, 60, 61), 0, (24, 24, 24, 24), 0),   # the paper's order-5 shape with an odd last mode
     ((7, 64, 66), 0, (9, 20), 0),               # slabs of exactly 64 rows
     ((3, 65, 70), 0, (9, 20), 1),               # 65-row slabs, X one float into its buffer
     ((5, 3, 5, 9), 0, (2, 3, 7), 2),            # 3-row slabs, 9-word rows
+    ((7, 32, 30), 0, (5, 17), 1),               # four 32-row slabs a tile, the last group of three
+    ((9, 33, 50), 0, (4, 9), 3),                # two 33-row slabs a tile, the last group of one
+    ((5, 20, 150), 0, (3, 20), 2),              # four 20-row slabs a tile, three l chunks
 ]
 
 
