@@ -17,21 +17,24 @@
 //     TMEM accumulator (rows c on TMEM lanes 96 + c), and another warp reads D2 once
 //     the slab is complete and writes T2.  Slabs with I_{N-2} <= 64 (<= 32) share a tile two
 //     (four) at a time, 128 / SG rows apart, each contracted over its own rows, so
-//     that short slabs still fill the tensor-core tile.  The stage-2 issue never
-//     blocks the stage-1 issue: separate threads, separate commits.
+//     that short slabs still fill the tensor-core tile; there the operands swap (T1 the
+//     MN-major A operand with rows (slab, d), U_{N-2} the B operand), so that 8 (4) MMAs
+//     of M = 64 (128) serve the whole tile, and four warps of their own write T2 out.
+//     The stage-2 issue never blocks the stage-1 issue: separate threads, separate commits.
 //   stage 2 (CUDA cores, FP32, I_{N-2} > 256): each epilogue warp moves the 32 T1
 //     rows of its TMEM lane quadrant to shared memory and adds U_{N-2}^T T1 over
 //     them into its own partial block of T2; at the end of a slab the four
 //     partials are added in warp order.  The factor rows of a k tile sit in one
 //     of two shared-memory slots, copied one tile ahead by the epilogue itself.
 // T1 never reaches HBM; T2 (R_{N-2} R_{N-1} / (I_{N-2} I_{N-1}) of X) is written
-// once, and the remaining modes are contracted by the plain TTM chain.  Each
+// once, and the remaining modes are contracted by the TTM chain.  Each
 // CTA owns a contiguous range of slabs, so every T2 block is produced by one
 // CTA in a fixed order (deterministic, no reduction pass).
 //
 // Warp roles: 0-7 converters, 8-11 epilogue (stage 2), 12 TMEM + stage-1 MMA
 // issue, 13 TMA; with the tensor-core stage 2 also 14 (stage-2 MMA issue) and 15
-// (T2 write-out from TMEM lanes 96-127).  Every wait is bounded (mbar_wait); the epilogue warps meet only
+// (T2 write-out from TMEM lanes 96-127); with packed slabs 12-15 write T2 out (one TMEM
+// lane quadrant each) and 16, 17, 18 take the MMA, TMA and stage-2 issue roles.  Every wait is bounded (mbar_wait); the epilogue warps meet only
 // through mbarriers (tensor-core stage 2: b2full / b2free for the T1 operand,
 // d2full / d2free for the TMEM accumulators; CUDA-core stage 2: ufree for the U
 // slots, t1full / t1free for the partial blocks), so a time-out anywhere ends
@@ -53,16 +56,20 @@ namespace {
 // TC2: stage 2 on the tensor cores, with two more warps: 14 issues the stage-2 MMAs and 15
 // reads the finished slabs' T2 out of TMEM (a 448-thread block is checked as 16 warps for
 // its registers anyway, so they cost no registers).
-template <bool RC = false, bool TC2 = false> struct TtmcCfg {
+// PACK (packed slabs, SG > 1): warps 12-15 write T2 out, one TMEM lane quadrant each, and
+// the MMA, TMA and stage-2 issue roles move to warps 16-18 (608 threads, at most 104
+// registers a thread).
+template <bool RC = false, bool TC2 = false, bool PACK = false> struct TtmcCfg {
     static constexpr int RP = 32;                          // padded R_{N-1} and R_{N-2}
     static constexpr int N = 2 * RP;                       // rows of the split factor tile (hi, then lo)
     static constexpr int RS = RC ? 2 : 3;                  // raw X stages
     static constexpr int AS = 2;                           // operand stages
-    static constexpr int MMA_WARP = CONV_WARPS + EPI_WARPS;
+    static constexpr int OUT_WARP = CONV_WARPS + EPI_WARPS;  // PACK: first of the four T2 writers
+    static constexpr int MMA_WARP = CONV_WARPS + EPI_WARPS + (PACK ? 4 : 0);
     static constexpr int TMA_WARP = MMA_WARP + 1;
     static constexpr int S2_WARP = TMA_WARP + 1;            // TC2: stage-2 issue (lane 0)
-    static constexpr int T2_WARP = TMA_WARP + 2;            // TC2: T2 writer (TMEM lanes 96-127)
-    static constexpr int WARPS = TC2 ? TMA_WARP + 3 : TMA_WARP + 1;
+    static constexpr int T2_WARP = TMA_WARP + 2;            // TC2 without PACK: T2 writer (TMEM lanes 96-127)
+    static constexpr int WARPS = PACK ? S2_WARP + 1 : (TC2 ? TMA_WARP + 3 : TMA_WARP + 1);
     static constexpr int THREADS = WARPS * 32;
     static constexpr int RAW_BYTES = BM * BK * 4;           // one box of the tensor map
     static constexpr int RAW_STAGE = RC ? kRcRawBytes : RAW_BYTES;
@@ -194,9 +201,9 @@ __device__ __forceinline__ void rc_read_packed(const TtmcArgs &a, int64_t grp, i
 // SG = 1 the tile's rows s I_{N-2} + 128 kt + l as in the MTTKRP case-0 view, with SG > 1
 // the packed slabs of rc_load_packed).
 template <bool STORE, int SG, bool TC2, bool RC>
-__global__ void __launch_bounds__(TtmcCfg<RC, TC2>::THREADS, 1)
+__global__ void __launch_bounds__(TtmcCfg<RC, TC2, (SG > 1)>::THREADS, 1)
 ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
-    using C = TtmcCfg<RC, TC2>;
+    using C = TtmcCfg<RC, TC2, (SG > 1)>;
     constexpr int RS = C::RS, AS = C::AS, RP = C::RP;
     static_assert(!STORE || (SG == 1 && !TC2), "the last-mode TTM keeps one slab per tile");
     static_assert(TC2 || SG == 1, "packed slabs take the tensor-core stage 2");
@@ -278,7 +285,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         }
         for (int j = 0; j < C::D2_SLOTS; ++j) {
             mbar_init(d2full(j), 1);
-            mbar_init(d2free(j), 1);
+            mbar_init(d2free(j), SG > 1 ? 4 : 1);   // packed slabs: the four T2 writers
         }
         mbar_init(drain2, 1);
         *abort_flag = 0;
@@ -478,14 +485,123 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         // n = (p, d)), k over the slab's rows of the tile.  Its commits track only its own MMAs.
         // Warp 15 (write-out): TMEM lanes 96-127 = c of each finished slab's D2 slot -> T2.
         // The three meet only through mbarriers (b2full / b2free, d2full / d2free).
+        // Packed slabs (SG > 1) swap the operands, so that one group of MMAs serves the whole
+        // tile: the feed writes T1 as an MN-major A tile with rows m = (g, d) (32 g + d) and
+        // k index kk = (p, k) (KP p + k, k the row within slab g); B is the split U_{N-2}
+        // block, K-major, rows (q, c) (32 q + c), the same 64 k for both p; so
+        //   D2[tile][(g, d), (q, c)] = sum_{p, k} T1_p[g KP + k, d] U_q[k, c],
+        // and T2[g, c, d] = D2[(g, d), c] + D2[(g, d), 32 + c].  SG = 4: M = 128 (row m on
+        // TMEM lane m), K = 64, 4 MMAs; SG = 2: M = 64 (rows 16 i .. 16 i + 15 on lanes
+        // 32 i .. 32 i + 15), K = 128, 8 MMAs -- against 16 MMAs of M = 128 with A = U
+        // (8 of whose 128 rows in 32 are used).  Warps 12-15 write T2 out, each from its own
+        // TMEM lane quadrant, up to four tiles (the D2 slots) behind the feed: stores issued
+        // by the feed warps themselves held the feed back (0.69 against 0.90 ms at 60^5).
         TIter it;
         it.init(ngroups);
         const int64_t nfg = (it.s1 - it.s) * a.n_kt;
         const bool vec = (a.R3 & 3) == 0;
         constexpr uint32_t kD2Lanes = 96u << 16;   // TMEM lane offset of the D2 rows c
+        constexpr int KP = BM / SG;                // tile rows of one slab
+        constexpr int M2 = SG == 2 ? 64 : BM;      // packed slabs: rows (g, d) of the A tile
+        // packed slabs: the U_{N-2} region's second half (unused with one k tile) holds 2 KB of
+        // scratch per T2 writer, through which it turns its values into rows of d for 16-byte
+        // stores
+        constexpr int kScratchBytes = 2048;
+        float *scratch = reinterpret_cast<float *>(region + 8192);
+        auto issue_packed = [&](int64_t t, int bi) -> bool {
+            constexpr uint32_t idesc2 = idesc_bf16_f32(M2, 2 * RP) | kIdescAMnMajor;
+            const int slot = int(t % C::D2_SLOTS);
+            if (!mbar_wait(b2full(bi), uint32_t((t / nb2) & 1), abort_flag, status, wlim)) return false;
+            if (t == 0 && !mbar_wait(u2full, 0u, abort_flag, status, wlim)) return false;
+            // the tile that last used the slot has been written out
+            if (!mbar_wait(d2free(slot), uint32_t((t / C::D2_SLOTS) & 1) ^ 1u, abort_flag, status, wlim)) return false;
+            tc_fence_after();
+            const uint32_t dcol = tmem + uint32_t(C::NACC * C::N + slot * 2 * RP);
+            const uint64_t bdesc = desc_kmajor_sw128(u2s_addr);   // U_{N-2} block: rows (q, c), 64 k
+            #pragma unroll
+            for (int ks = 0; ks < 2 * KP / 16; ++ks) {
+                const uint64_t adesc =
+                    SG == 2 ? desc_mnmajor_sw128(b2_addr(bi) + uint32_t(ks * 2048), 1024u, 1024u)
+                            : desc_mnmajor_sw128(b2_addr(bi) + uint32_t(ks * 2 * kMnKGroupStride), kMnAtomStride,
+                                                 kMnKGroupStride);
+                const uint64_t adv = uint64_t((ks % (KP / 16)) * 32) >> 4;   // k = 16 ks mod KP
+                mma_bf16(dcol, adesc, bdesc + adv, idesc2, ks > 0 ? 1u : 0u);
+            }
+            mma_commit(d2full(slot));
+            mma_commit(b2free(bi));
+            return true;
+        };
+        // Packed slabs: the T2 writer of TMEM quadrant qd writes tile t's T2 rows (g, d) held
+        // in its lanes (SG = 4: g = qd, d = lane; SG = 2: g = qd / 2, d = 16 (qd mod 2) + lane
+        // for lanes below 16), every c.  With R_{N-1} a multiple of 4 (and T2 16-byte aligned)
+        // the lanes put their values in the warp's scratch as rows c of W d values (SG = 2:
+        // W = 16, all 32 rows at once; SG = 4: W = 32, 16 rows at a time) and read them back
+        // as 16-byte words, W / 4 lanes to a row; otherwise each lane stores its own values
+        // (4-byte words, rows c R_{N-1} floats apart).
+        auto write_packed = [&](int64_t t, int qd) -> bool {
+            const int slot = int(t % C::D2_SLOTS);
+            if (!__all_sync(0xffffffffu, mbar_wait(d2full(slot), uint32_t((t / C::D2_SLOTS) & 1), abort_flag, status,
+                                                   wlim)))
+                return false;
+            tc_fence_after();
+            const uint32_t d2 = tmem + (uint32_t(qd * 32) << 16) + uint32_t(C::NACC * C::N + slot * 2 * RP);
+            uint32_t vh[2][16], vl[2][16];   // columns (hi part, c) and (lo part, c)
+            tmem_ld16(d2, vh[0]);
+            tmem_ld16(d2 + 16, vh[1]);
+            tmem_ld16(d2 + RP, vl[0]);
+            tmem_ld16(d2 + RP + 16, vl[1]);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(d2free(slot));
+            constexpr int W = SG == 2 ? 16 : 32;           // d values per warp
+            const int g = SG == 4 ? qd : (qd >> 1);
+            const int d0 = SG == 4 ? 0 : 16 * (qd & 1);    // the warp's first d
+            const int64_t sl = (it.s + t) * SG + g;
+            if (sl >= a.S || d0 >= a.R3) return true;       // (warp-uniform)
+            float *blk = a.T2 + sl * a.R2 * a.R3;
+            if ((a.R3 & 3) == 0 && (reinterpret_cast<uintptr_t>(a.T2) & 15) == 0) {
+                float *sc = scratch + qd * (kScratchBytes / 4);
+                constexpr int RPASS = kScratchBytes / 4 / W;   // rows c per pass (32 or 16)
+                constexpr int LPR = W / 4;                     // lanes per row
+                constexpr int RPI = 32 / LPR;                  // rows per 16-byte read
+                const int q = lane % LPR, rr = lane / LPR;
+                const bool qok = d0 + 4 * q < a.R3;
+                #pragma unroll
+                for (int c0 = 0; c0 < RP; c0 += RPASS) {
+                    if (c0 >= a.R2) break;
+                    if (lane < W) {
+                        #pragma unroll
+                        for (int c = 0; c < RPASS; ++c)
+                            sc[c * W + lane] = __uint_as_float(vh[(c0 + c) >> 4][(c0 + c) & 15]) +
+                                               __uint_as_float(vl[(c0 + c) >> 4][(c0 + c) & 15]);
+                    }
+                    __syncwarp();
+                    #pragma unroll
+                    for (int r0 = 0; r0 < RPASS; r0 += RPI) {
+                        const int c = c0 + r0 + rr;
+                        if (c < a.R2 && qok) {
+                            const float4 v4 = *reinterpret_cast<const float4 *>(sc + (r0 + rr) * W + 4 * q);
+                            *reinterpret_cast<float4 *>(blk + int64_t(c) * a.R3 + d0 + 4 * q) = v4;
+                        }
+                    }
+                    __syncwarp();   // the rows are read before the next pass overwrites them
+                }
+            } else {
+                const int d = d0 + lane;
+                if (lane < W && d < a.R3) {
+                    #pragma unroll
+                    for (int c = 0; c < RP; ++c)
+                        if (c < a.R2)
+                            blk[int64_t(c) * a.R3 + d] =
+                                __uint_as_float(vh[c >> 4][c & 15]) + __uint_as_float(vl[c >> 4][c & 15]);
+                }
+            }
+            return true;
+        };
         auto issue_stage2 = [&](int64_t t, int bi) -> bool {
+            if constexpr (SG > 1) return issue_packed(t, bi);
             constexpr uint32_t idesc2 = idesc_bf16_f32(BM, 2 * RP) | kIdescBMnMajor;
-            constexpr int KP = BM / SG;            // tile rows of one slab
             const int tk = int(t % a.n_kt);
             const int64_t tg = t / a.n_kt;         // slab group within the CTA
             if (!mbar_wait(b2full(bi), uint32_t((t / nb2) & 1), abort_flag, status, wlim)) return false;
@@ -503,8 +619,8 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 for (int ks = 0; ks < KP / 16; ++ks) {
                     const int ku = 16 * ks;                       // k within the tile's k range
                     const int h = ku >> 6, st = (ku & 63) >> 4;   // 64-k half, 16-k step in it
-                    const uint32_t ahi = u2s_addr + uint32_t(((tk * 2 + 0) * 2 + h) * 4096) - 12288u;
-                    const uint32_t alo = u2s_addr + uint32_t(((tk * 2 + 1) * 2 + h) * 4096) - 12288u;
+                    const uint32_t ahi = u2s_addr + uint32_t(((tk * 2 + h) * 2 + 0) * 4096) - 12288u;
+                    const uint32_t alo = u2s_addr + uint32_t(((tk * 2 + h) * 2 + 1) * 4096) - 12288u;
                     const uint64_t adv = uint64_t(st * 32) >> 4;
                     const uint64_t db =
                         desc_mnmajor_sw128(b2_addr(bi) + uint32_t(((g * KP + ku) >> 3) * 1024), 1024u, 1024u);
@@ -561,8 +677,11 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         if (warp == C::S2_WARP) {
             if (lane == 0 && nfg > 0) {
                 // the split U_{N-2} tiles stay for the whole kernel
-                mbar_arrive_expect_tx(u2full, uint32_t(a.n_kt) * 16384u);
-                bulk_g2s(u2s_addr, a.U2split, uint32_t(a.n_kt) * 16384u, u2full);
+                // (packed slabs: only the first 8 KB, rows (q, c) for k < 64; the rest of the
+                // region is the feed warps' T2 scratch)
+                const uint32_t u2bytes = SG > 1 ? 8192u : uint32_t(a.n_kt) * 16384u;
+                mbar_arrive_expect_tx(u2full, u2bytes);
+                bulk_g2s(u2s_addr, a.U2split, u2bytes, u2full);
                 for (int64_t fgi = 0; fgi < nfg; ++fgi)
                     if (!issue_stage2(fgi, int(fgi % nb2))) break;
                 // the U_{N-2} copy has landed and every stage-2 MMA has completed before exit
@@ -573,8 +692,15 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             }
             __syncwarp();
         } else if (warp == C::T2_WARP) {
-            for (int64_t pg = it.s; pg < it.s1; ++pg)
-                if (!write_t2(pg)) break;
+            if constexpr (SG == 1) {
+                for (int64_t pg = it.s; pg < it.s1; ++pg)
+                    if (!write_t2(pg)) break;
+            }
+        } else if (SG > 1 && warp >= C::OUT_WARP && warp < C::OUT_WARP + 4) {
+            // packed slabs: the T2 writers, one TMEM lane quadrant each (warp mod 4), as far
+            // as four tiles behind the feed (the D2 slots)
+            for (int64_t t = 0; t < nfg; ++t)
+                if (!write_packed(t, warp & 3)) break;
         } else {
             const int quad = warp & 3;
             const int row = quad * 32 + lane;
@@ -608,12 +734,25 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 }
                 tc_fence_before();
                 const uint32_t b2 = b2_addr(bi);
-                #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
-                    sts128(b2 + sw128_mn64_offset(uint32_t(8 * ch), uint32_t(row)), ph[4 * ch], ph[4 * ch + 1],
-                           ph[4 * ch + 2], ph[4 * ch + 3]);
-                    sts128(b2 + sw128_mn64_offset(uint32_t(RP + 8 * ch), uint32_t(row)), pl[4 * ch], pl[4 * ch + 1],
-                           pl[4 * ch + 2], pl[4 * ch + 3]);
+                if constexpr (SG > 1) {
+                    // A tile element (m, kk) = (32 g + d, KP p + k) for tile row g KP + k
+                    const uint32_t m0 = uint32_t(row / KP) * 32u, k = uint32_t(row % KP);
+                    #pragma unroll
+                    for (int ch = 0; ch < 4; ++ch) {
+                        const uint32_t m = m0 + uint32_t(8 * ch);
+                        const uint32_t oh = SG == 2 ? sw128_mn64_offset(m, k) : sw128_mn_offset(m, k);
+                        const uint32_t ol = SG == 2 ? sw128_mn64_offset(m, KP + k) : sw128_mn_offset(m, KP + k);
+                        sts128(b2 + oh, ph[4 * ch], ph[4 * ch + 1], ph[4 * ch + 2], ph[4 * ch + 3]);
+                        sts128(b2 + ol, pl[4 * ch], pl[4 * ch + 1], pl[4 * ch + 2], pl[4 * ch + 3]);
+                    }
+                } else {
+                    #pragma unroll
+                    for (int ch = 0; ch < 4; ++ch) {
+                        sts128(b2 + sw128_mn64_offset(uint32_t(8 * ch), uint32_t(row)), ph[4 * ch], ph[4 * ch + 1],
+                               ph[4 * ch + 2], ph[4 * ch + 3]);
+                        sts128(b2 + sw128_mn64_offset(uint32_t(RP + 8 * ch), uint32_t(row)), pl[4 * ch],
+                               pl[4 * ch + 1], pl[4 * ch + 2], pl[4 * ch + 3]);
+                    }
                 }
                 fence_proxy_async_smem();   // the B2 stores before the tensor-core reads
                 __syncwarp();
@@ -802,7 +941,7 @@ __global__ void pad_factor_kernel(const float *__restrict__ U, int64_t rows, int
 namespace {
 template <bool STORE, int SG, bool TC2, bool RC = false>
 int launch_ttmc_variant(const TtmcArgs &a, int n_sm, void *stream) {
-    using C = TtmcCfg<RC, TC2>;
+    using C = TtmcCfg<RC, TC2, (SG > 1)>;
     cudaError_t e = cudaFuncSetAttribute(ttmc_fused_kernel<STORE, SG, TC2, RC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::SMEM));
     if (e != cudaSuccess) return int(e);
@@ -844,7 +983,7 @@ int launch_ttm_last_tc(const TtmcArgs &a, int n_sm, void *stream) {
 }
 
 namespace {
-// U (rows x R) -> split BF16 blocks ((kt * 2 + p) * 2 + h) * 4096: 32 rows c x 64 k,
+// U (rows x R) -> split BF16 blocks ((kt * 2 + h) * 2 + p) * 4096: 32 rows c x 64 k,
 // K-major 128-byte swizzle; hi = bf16(u), lo = bf16(u - hi); zero beyond rows x R.
 __global__ void u2_split_kernel(const float *__restrict__ U, int64_t rows, int R, unsigned char *__restrict__ out,
                                 int64_t total) {
@@ -859,7 +998,7 @@ __global__ void u2_split_kernel(const float *__restrict__ U, int64_t rows, int R
         const float v = (c < R && k < rows) ? U[k * R + c] : 0.f;
         const __nv_bfloat16 hb = __float2bfloat16_rn(v);
         const __nv_bfloat16 e = p == 0 ? hb : __float2bfloat16_rn(v - __bfloat162float(hb));
-        *reinterpret_cast<__nv_bfloat16 *>(out + size_t(((kt * 2 + p) * 2 + h) * 4096) +
+        *reinterpret_cast<__nv_bfloat16 *>(out + size_t(((kt * 2 + h) * 2 + p) * 4096) +
                                            sw128_offset(uint32_t(c), uint32_t(kq))) = e;
     }
 }

@@ -39,13 +39,17 @@ CASES = [
     ((6, 7, 8, 90, 44), 0, (3, 5, 32, 7)),    # order 5, two more chain stages
     ((6, 7, 8, 90, 44), 2, (4, 6, 9, 32)),    # order 5, kept mode in the middle
     # short slabs share a tile: I_{N-2} <= 64 two per tile, <= 32 four per tile; the slab
-    # counts leave a partial last group, and R_{N-1} = 10 takes the scalar stores of T2
+    # counts leave a partial last group; T2 blocks of up to 8 KB a tile (sizes a multiple
+    # of 16 bytes) go out as one bulk store each, other ones from the feed warps
     ((31, 7, 60, 60), 0, (5, 24, 24)),        # two slabs per tile, S = 217
     ((9, 13, 28, 36), 0, (6, 30, 10)),        # four slabs per tile, S = 117
     ((5, 40, 33, 64), 1, (7, 32, 32)),        # two per tile, kept mode 1
     ((70, 64, 20), 0, (32, 13)),              # order 3, I_{N-2} = 64 exactly
     ((3, 5, 32, 8), 0, (2, 3, 4)),            # I_{N-2} = 32 exactly, one 8-wide l chunk
     ((4, 6, 60, 60, 60), 0, (24, 24, 24, 24)),  # the paper's order-5 TTMc shape, fewer slabs
+    ((9, 20, 40), 0, (24, 24)),               # four per tile, 9 KB of T2 a tile: the feed warps' own 16-byte stores
+    ((7, 50, 44), 0, (5, 7)),                 # two per tile, R_{N-1} = 7: the feed warps' 4-byte stores
+    ((7, 50, 44), 0, (5, 6)),                 # bulk stores, the last group's 30 floats copied by words
     # order-5 chains after the fused pair
     ((9, 11, 40, 64, 36), 1, (13, 21, 24, 16)),  # kept mode 1 between the two chain modes
     ((7, 30, 50, 60, 20), 0, (19, 11, 8, 5)),    # ranks 19 / 11, trailing extent 40
