@@ -207,12 +207,10 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     constexpr int RS = C::RS, AS = C::AS, RP = C::RP;
     static_assert(!STORE || (SG == 1 && !TC2), "the last-mode TTM keeps one slab per tile");
     static_assert(TC2 || SG == 1, "packed slabs take the tensor-core stage 2");
-    // Packed short slabs (one 64-wide l chunk per tile at most once the tile is full, so the
-    // T1 feed runs per chunk): stage 1 takes three split products (X_hi U_hi + X_hi U_lo +
-    // X_lo U_hi) into RP accumulator columns, halving the feed's TMEM reads; the other
-    // variants keep two MMAs of N = 2 RP (four products), whose 8 dependent MMAs per chunk
-    // keep pace with long slabs where 12 did not.
-    constexpr bool S1THREE = TC2 && SG > 1;
+    // Stage 1 takes two MMAs of N = 2 RP per 16 k (X_hi [U_hi U_lo], X_lo [U_hi U_lo]: four
+    // split products, hi and lo columns added by the feed).  A three-product form for packed
+    // slabs (12 MMAs of N = RP a chunk, half the feed's TMEM reads) measured no faster once
+    // their T2 writes left the feed warps (60^5: 0.688 against 0.684 ms).
     constexpr uint32_t kTmemCols = TC2 ? C::TMEM_COLS_TC2 : C::TMEM_COLS;
     const int64_t ngroups = (a.S + SG - 1) / SG;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -377,7 +375,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
     } else if (warp == C::MMA_WARP) {
         // -------------------------------------------------------------- MMA issue
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(BM, S1THREE ? RP : C::N);
+            constexpr uint32_t idesc = idesc_bf16_f32(BM, C::N);
             TIter it;
             it.init(ngroups);
             const int64_t nfg = (it.s1 - it.s) * a.n_kt;
@@ -401,12 +399,10 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                     const uint64_t dh = desc_kmajor_sw128(a_hi(s));
                     const uint64_t dl = desc_kmajor_sw128(a_lo(s));
                     const uint64_t db = desc_kmajor_sw128(b_t(s));
-                    const uint64_t dbl = desc_kmajor_sw128(b_t(s) + uint32_t(RP * 128));   // U_lo rows
                     #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint64_t adv = uint64_t(kk * 32) >> 4;  // 32 bytes per K=16 step
                         mma_bf16(dcol, dh + adv, db + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                        if constexpr (S1THREE) mma_bf16(dcol, dh + adv, dbl + adv, idesc, 1u);
                         mma_bf16(dcol, dl + adv, db + adv, idesc, 1u);
                     }
                     mma_commit(a_empty(s));
@@ -720,15 +716,12 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
                 for (int c0 = 0; c0 < RP; c0 += 16) {
                     uint32_t hi[16], lo[16];
                     tmem_ld16(taddr + uint32_t(c0), hi);
-                    if constexpr (!S1THREE) tmem_ld16(taddr + uint32_t(RP + c0), lo);
+                    tmem_ld16(taddr + uint32_t(RP + c0), lo);
                     tmem_wait_ld();
                     #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        float x0 = __uint_as_float(hi[2 * q]), x1 = __uint_as_float(hi[2 * q + 1]);
-                        if constexpr (!S1THREE) {
-                            x0 += __uint_as_float(lo[2 * q]);
-                            x1 += __uint_as_float(lo[2 * q + 1]);
-                        }
+                        const float x0 = __uint_as_float(hi[2 * q]) + __uint_as_float(lo[2 * q]);
+                        const float x1 = __uint_as_float(hi[2 * q + 1]) + __uint_as_float(lo[2 * q + 1]);
                         split2(x0, x1, ph[c0 / 2 + q], pl[c0 / 2 + q]);
                     }
                 }
