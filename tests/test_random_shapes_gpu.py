@@ -5,7 +5,8 @@ outer indices, unaligned rows); these sweeps draw shapes the cases did not think
 to 6, extents from 1 to a few hundred (log-uniform, X at most about 1.5 M elements so that the
 oracle finishes in well under a second), ranks 1 to 64, every mode, X starting 0 to 3 floats
 into its buffer (aligned rows, row classes, per-thread loads), in both precisions; random
-batches of uneven instances; random split-BF16 TTMc chains.  The shapes come from a fixed
+batches of uneven instances; random split-BF16 TTMc chains, and TTMc with short slabs
+packed two or four to a tile.  The shapes come from a fixed
 numpy generator seed, so a failure names a reproducible case.  Gates as in the parity tests:
 relative Frobenius 1e-5 and element-wise 1e-4 of the largest oracle entry.
 """
@@ -127,3 +128,34 @@ def test_random_ttmc_matches_oracle(case):
         torch.cuda.synchronize()
         assert Y.shape == ref.shape
         _gate(Y.cpu().numpy(), ref, f"dims {dims} keep {keep} ranks {ranks} offset {offset} {prec}")
+
+
+PACKED_DRAWS = 24
+
+
+@pytest.mark.parametrize("case", range(PACKED_DRAWS))
+def test_random_packed_ttmc_matches_oracle(case):
+    """Split-BF16 TTMc with short slabs (I_{N-2} <= 64: two or four to a tile), orders 3 to 5,
+    I_{N-1} from 1 to 149 (aligned rows and row classes), X 0 to 3 floats into its buffer,
+    R_{N-2}, R_{N-1} from 1 to 32 (T2 blocks through every store path of the writer warps)."""
+    rng = np.random.default_rng(77000 + case)
+    order = int(rng.integers(3, 6))
+    K = int(rng.integers(1, 65))
+    L = int(rng.integers(1, 150))
+    lead = [int(rng.integers(1, 12)) for _ in range(order - 2)]
+    dims = tuple(lead + [K, L])
+    keep = int(rng.integers(0, order - 2))
+    ranks = [int(rng.integers(1, 33)) if m >= order - 2 else int(rng.integers(1, 20)) for m in range(order)]
+    offset = int(rng.integers(0, 4))
+    if int(np.prod(dims[:-1])) < 4 and (L % 4 or offset):
+        pytest.skip("fewer than 4 rows without 16-byte aligned rows: refused by the split plan")
+    seed = 5000 + case
+    Xh = inputs.tensor_uniform_f32(seed, dims)
+    Us = [None if m == keep else inputs.factor_normal(seed, m, d, ranks[m]).astype(np.float32)
+          for m, d in enumerate(dims)]
+    X = _device_x(Xh, offset)
+    U = [None if u is None else torch.from_numpy(u).cuda() for u in Us]
+    ref = oracle.ttmc(Xh, Us, keep)
+    Y = dz.ttmc(X, U, keep, prec="split_bf16")
+    torch.cuda.synchronize()
+    _gate(Y.cpu().numpy(), ref, f"dims {dims} keep {keep} ranks {ranks} offset {offset}")
