@@ -289,10 +289,18 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
     } else if constexpr (TTM) {
         // ------------------------------------------------------- TTM write-out
         // every fiber group (a column of 128 rows b, outer index o = a) is one output tile:
-        // Y[o, r, b] = T[b, r], the U_hi and U_lo columns added; rows past I_n are not written
+        // Y[o, r, b] = T[b, r], the U_hi and U_lo columns added; rows past I_n are not written.
+        // With I_n a multiple of 4 (and Y 16-byte aligned) each warp turns its 32 rows into
+        // 16-byte words along b through 4 KB of scratch in the (unused) weight ring: PWC
+        // columns r at a time, 8 lanes to a column; otherwise each lane stores its own row.
         const int quad = warp & 3;
         const int l = quad * 32 + lane;
         float *Y = a.ttm_out;
+        constexpr int PWC = (C::WBUF_BYTES / 512) >= 16 ? 16 : 8;   // columns per scratch pass
+        static_assert(C::WBUF_BYTES >= 4 * 32 * PWC * 4, "TTM write-out scratch");
+        float *sc = wbuf + quad * 32 * PWC;
+        const bool vec = (g.I & 3) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+        const int q4 = lane & 7, rr = lane >> 3;   // the 16-byte word this lane stores: b 4 q4, column rr + 4 i
         Iter it;
         it.init(a);
         int64_t fgi = 0;
@@ -305,15 +313,37 @@ mttkrp_tc_kernel(const __grid_constant__ MttkrpArgs a) {
             const int64_t row = it.col * BM + l;
             const bool rv = row < g.I;
             float *yr = Y + it.o * int64_t(g.R) * g.I + row;
+            const int64_t b0 = it.col * BM + quad * 32;           // the warp's first row
+            float *yw = Y + it.o * int64_t(g.R) * g.I + b0 + 4 * q4;
+            const bool wv = b0 + 4 * q4 < g.I;                     // (all four rows, I_n % 4 == 0)
             #pragma unroll
             for (int c = 0; c < RP; c += 16) {
                 uint32_t t[16], tl[16];
                 tmem_ld16(taddr + uint32_t(c), t);
                 tmem_ld16(taddr + uint32_t(RP + c), tl);
                 tmem_wait_ld();
-                #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (rv && c + q < g.R) yr[int64_t(c + q) * g.I] = __uint_as_float(t[q]) + __uint_as_float(tl[q]);
+                if (vec) {
+                    #pragma unroll
+                    for (int h = 0; h < 16; h += PWC) {
+                        if (c + h >= g.R) break;
+                        #pragma unroll
+                        for (int q = 0; q < PWC; ++q)
+                            sc[q * 32 + lane] = __uint_as_float(t[h + q]) + __uint_as_float(tl[h + q]);
+                        __syncwarp();
+                        #pragma unroll
+                        for (int i = 0; i < PWC / 4; ++i) {
+                            const int r = c + h + rr + 4 * i;
+                            if (wv && r < g.R)
+                                *reinterpret_cast<float4 *>(yw + int64_t(r) * g.I) =
+                                    *reinterpret_cast<const float4 *>(sc + (rr + 4 * i) * 32 + 4 * q4);
+                        }
+                        __syncwarp();   // read before the next pass overwrites the scratch
+                    }
+                } else {
+                    #pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (rv && c + q < g.R) yr[int64_t(c + q) * g.I] = __uint_as_float(t[q]) + __uint_as_float(tl[q]);
+                }
             }
             tc_fence_before();
             __syncwarp();
