@@ -178,11 +178,38 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """C/C++ source as the compiler reads it: comments removed (string and character
+    literals kept whole), each line stripped, blank lines dropped."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        ch = text[i]
+        if ch in "\"'":
+            j = i + 1
+            while j < n and text[j] != ch:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(ch)
+            i += 1
+    return "\n".join(line.strip() for line in "".join(out).splitlines() if line.strip())
+
+
 def _kernel_source_hash(source="mttkrp_tc.cu"):
+    """Hash of the code (not the comments) of the files a main kernel is compiled from: a
+    committed traffic record stays current across edits of comments only."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES.get(source, (source,)):
-        with open(os.path.join(ROOT, "paper_2206_08301_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2206_08301_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

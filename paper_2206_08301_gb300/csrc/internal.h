@@ -158,18 +158,20 @@ int launch_batched_reduce(const RedInst *red, const int *start, int n, int n_blo
 //   T2[s, c, d] = sum_{k, l} X[s, k, l] U_{N-2}[k, c] U_{N-1}[l, d]
 // for every slab s (flat index over modes 0..N-3), k over I_{N-2}, l over
 // I_{N-1}.  The contraction over l runs on the tensor cores (split BF16, 128 k
-// at a time), the one over k on CUDA cores in FP32; T1 = X U_{N-1} stays on chip.
+// at a time), the one over k on the tensor cores as well while I_{N-2} <= 256 (tc2),
+// else on CUDA cores in FP32; T1 = X U_{N-1} stays on chip.
 // Short slabs share a 128-row tile: sg = 2 (I_{N-2} <= 64) or 4 (<= 32) slabs at a
-// row pitch of 128 / sg, the rows past I_{N-2} zero-filled by the TMA.
+// row pitch of 128 / sg, the rows past I_{N-2} zero-filled by the TMA (the next slab's
+// rows, or zero past X, with row classes).
 struct TtmcArgs {
     CUtensorMap xmap;     // 3-D {I_{N-1}, I_{N-2}, S}, box {64, min(I_{N-2}, 128), 1}; sg > 1: {64, 128/sg, sg}
     // rows of X (I_{N-1} words) not 16-byte aligned: the four row-class maps of the case-0 view
-    // g (encode_x_rowclass_maps), X's address, and sg = 1
+    // g, X's address; sg = 1 (boxes of 32 rows), or sg = 2 / 4 with tc2 (boxes of 32 / sg rows)
     CUtensorMap xrow[4];
     const void *X;
     int row_classes;
     uint32_t box_bytes;
-    MttkrpGeom g;         // converter view of a chunk: case 0, I = I_{N-2}, narrow = I < 128 (sg = 1), G = 1
+    MttkrpGeom g;         // converter view of a chunk: case 0, I = I_{N-2}, narrow = I < 128 and sg = 1, G = 1
     const void *Bsplit;   // split-BF16 tiles of U_{N-1} (R_pad 32, n_kb tiles)
     const float *U2pad;   // CUDA-core stage 2: U_{N-2} as n_kt*128 rows x 32 FP32, zero beyond I_{N-2} x R_{N-2}
     const void *U2split;  // tensor-core stage 2 (tc2): split BF16 tiles of U_{N-2} (launch_ttmc_u2_split)

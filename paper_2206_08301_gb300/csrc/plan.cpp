@@ -632,7 +632,7 @@ void plan_ttmc_chain(deinsum_plan_s *pl) {
 // the other contracted modes follow in the same greedy order on
 // T2 = [I_0 .. I_{N-3}, R_{N-2}, R_{N-1}].  Offered when the kept mode is
 // below N-2 and R_{N-2}, R_{N-1} <= 32; rows of X (I_{N-1} words) that are not
-// 16-byte aligned take the row-class tensor maps (one slab per tile).
+// 16-byte aligned take the row-class tensor maps (short slabs packed as with the tensor map).
 // Merge the inner mode of a tensor-core MTTKRP with its neighbour when the inner mode is
 // short (at most two 64-wide chunks, so that every fiber group would be one or two chunks
 // and the epilogue and its handshakes would run per 32 KB of X) and the merged view still
@@ -667,7 +667,8 @@ deinsum_status plan_ttmc_fused(deinsum_plan_s *pl) {
     int64_t S = 1;
     for (int m = 0; m < N - 2; ++m) S *= pl->dims[m];
     if (S >= lim || pl->dims[N - 2] >= lim || pl->dims[N - 1] >= lim) return DEINSUM_ERR_UNSUPPORTED;
-    // rows of I_{N-1} words that are not 16-byte aligned take the row-class maps, one slab per tile
+    // rows of I_{N-1} words that are not 16-byte aligned take the row-class maps (their slabs
+    // packed at execution, as the aligned ones are here)
     const bool rows16 = pl->dims[N - 1] % 4 == 0;
     if (!rows16) {
         MttkrpGeom g1;

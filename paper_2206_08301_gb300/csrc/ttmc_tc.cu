@@ -488,8 +488,8 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
         //   D2[tile][(g, d), (q, c)] = sum_{p, k} T1_p[g KP + k, d] U_q[k, c],
         // and T2[g, c, d] = D2[(g, d), c] + D2[(g, d), 32 + c].  SG = 4: M = 128 (row m on
         // TMEM lane m), K = 64, 4 MMAs; SG = 2: M = 64 (rows 16 i .. 16 i + 15 on lanes
-        // 32 i .. 32 i + 15), K = 128, 8 MMAs -- against 16 MMAs of M = 128 with A = U
-        // (8 of whose 128 rows in 32 are used).  Warps 12-15 write T2 out, each from its own
+        // 32 i .. 32 i + 15), K = 128, 8 MMAs -- against 16 MMAs of M = 128 with A = the
+        // U_{N-2} window, of whose 128 rows R_{N-2} <= 32 are used.  Warps 12-15 write T2 out, each from its own
         // TMEM lane quadrant, up to four tiles (the D2 slots) behind the feed: stores issued
         // by the feed warps themselves held the feed back (0.69 against 0.90 ms at 60^5).
         TIter it;
@@ -596,7 +596,7 @@ ttmc_fused_kernel(const __grid_constant__ TtmcArgs a) {
             return true;
         };
         auto issue_stage2 = [&](int64_t t, int bi) -> bool {
-            if constexpr (SG > 1) return issue_packed(t, bi);
+            if constexpr (SG > 1) return issue_packed(t, bi);   // (the rest: one slab per tile)
             constexpr uint32_t idesc2 = idesc_bf16_f32(BM, 2 * RP) | kIdescBMnMajor;
             const int tk = int(t % a.n_kt);
             const int64_t tg = t / a.n_kt;         // slab group within the CTA
