@@ -743,6 +743,51 @@ def measure_c2b_ttmc(clk, peak, reps=3):
             "clocks_region": "c2b"}
 
 
+def measure_ttmc_o5(clk, peak, reps=5):
+    """The paper's TTMc-O5-M0 (Table V): X 60^5 FP32 uniform[-1,1), U 60 x 24 N(0,1), mode 0
+    kept, split-BF16 (fused last two modes, then the chain's two TTMs on the tensor cores)
+    against the plain FP32 chain of TTMs."""
+    import torch
+    import oracle
+    import paper_2206_08301_gb300 as dz
+    from paper_2206_08301_gb300 import inputs
+    seed, n, R, N = 1301, 60, 24, 5
+    dims = (n,) * N
+    spec = dz.ttmc_einsum(N, 0)
+    X = dz.gen_uniform(seed, inputs.STREAM_X, dims)
+    Us = [inputs.factor_normal(seed, m, n, R).astype(np.float32) for m in range(N)]
+    Ud = [torch.from_numpy(u).cuda() for u in Us]
+    out = torch.empty(n, R, R, R, R, device="cuda")
+    stream = torch.cuda.Stream()
+    plans = {p: dz.Plan(spec, list(dims) + [R] * (N - 1), "float32", p) for p in ("split_bf16", "plain")}
+    with clk.region("ttmc_o5"):
+        l0 = dz.kernel_launch_count()
+        ms, kms = _plan_timed(plans["split_bf16"], [X] + Ud[1:], out, stream, reps)
+        launches = (dz.kernel_launch_count() - l0) / (reps + 3)
+        status = plans["split_bf16"].last_device_status()
+        rows = inputs.sample_rows(seed, n, 2, tag=0)
+        got = out[torch.from_numpy(rows).cuda()].cpu().numpy()
+        ms_plain, _ = _plan_timed(plans["plain"], [X] + Ud[1:], out, stream, 1, warm=1)
+    del X
+    torch.cuda.empty_cache()
+    slabs = np.stack([inputs.uniform_slab(seed, dims, 0, int(r)).ravel() for r in rows])
+    ref = oracle.ttmc_rows(dims, 0, slabs, Us)
+    ab = plans["split_bf16"].info()["alg_bytes"]
+    kbytes = 4.0 * n ** N + 4.0 * n ** (N - 2) * R * R   # X once + T2 written once
+    return {"workload": "TTMc-O5-M0 ijklm,jb,kc,ld,me->ibcde, X 60^5 FP32 uniform[-1,1), U 60x24 N(0,1), "
+                        "split-BF16 (fused last two modes, chain TTMs on the tensor cores) vs plain FP32 chain",
+            "metric": "GB/s", "value": ab / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms,
+            "alg_frac": ab / (ms * 1e-3) / 1e9 / peak,
+            "roofline": {"bound": "hbm", "kernel": "ttmc_fused_kernel", "kernel_ms": kms,
+                         "bytes_per_launch": kbytes, "achieved": kbytes / (kms * 1e-3) / 1e9, "peak": peak,
+                         "frac": kbytes / (kms * 1e-3) / 1e9 / peak,
+                         "traffic": _traffic_per_launch("ttmc_split_bf16_packed", "ttmc_tc.cu")},
+            "plain_chain_ms": ms_plain, "speedup_vs_plain_chain": ms_plain / ms, "launches_per_step": launches,
+            "rel_err": oracle.rel_error(got, ref), "max_elem_err": oracle.max_elem_error(got, ref),
+            "sample": "2 kept-mode slices (2 x 24^4 outputs)", "device_status": status,
+            "clocks_region": "ttmc_o5"}
+
+
 def measure_c3_batched(clk, peak, n=512, reps=5):
     """512 uneven order-3 MTTKRP instances (extents U{32..384}, R in {8,16,32,64}, mode
     U{0,1,2}, X uniform[-1,1) float32): the graph-replayed persistent split-BF16 launches
@@ -1120,6 +1165,7 @@ def main():
         for key, fn, kw in (("c0_mttkrp_64cubed_fp64", measure_c0_fp64, {}),
                             ("c2a_mttkrp_64pow5_r24_modes_0_2", measure_c2a_order5, {"peak": peak}),
                             ("c2b_ttmc_256pow4_r32", measure_c2b_ttmc, {"peak": peak}),
+                            ("ttmc_o5_m0_60pow5_r24", measure_ttmc_o5, {"peak": peak}),
                             ("c3_batched_512_instances", measure_c3_batched, {"peak": peak}),
                             ("c4_cpals_serving", measure_c4_serving, {}),
                             ("cpals_sweep_1024cubed_r32", measure_cpals_sweep, {})):
