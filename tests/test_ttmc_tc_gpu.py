@@ -4,8 +4,10 @@ Gate: relative Frobenius error <= 1e-5 and element-wise <= 1e-4 of the largest
 oracle entry (the FP32-accurate tolerance of the TTMc contract).  Cases cover
 ragged k tiles (I_{N-2} not a multiple of 128), ragged l chunks (I_{N-1} not a
 multiple of 64), a k extent below one tile, ranks below the padded 32, orders
-3 to 5, every kept mode the fused path takes, rows of X that are not 16-byte
-aligned (the row-class tensor maps), and order-5 chains with the kept mode before or
+3 to 5, every kept mode the fused path takes, short slabs packed two or four to a
+tile (partial last groups, every store path of the T2 writer warps), rows of X that
+are not 16-byte aligned (the row-class tensor maps, one slab per tile or packed), and
+order-5 chains with the kept mode before or
 between the two chain modes, ragged trailing extents and ranks that are not multiples
 of 8, and order-6 chains (two chain TTMs on the tensor cores, the third in FP32).
 """
