@@ -129,9 +129,15 @@ typedef struct {
  *              final reduction, so the I_n x R MTTKRP result never reaches HBM.
  *              Anything else returns DEINSUM_ERR_UNSUPPORTED (paper Sec. III-A
  *              semantics: repeated letters are summed, output letters kept).
- *              TTMc with SPLIT_BF16 is the fused kernel of the last two modes:
- *              it needs the kept mode below N-2, R_{N-2}, R_{N-1} <= 32 and
- *              I_{N-1} a multiple of 4 (else DEINSUM_ERR_UNSUPPORTED).
+ *              TTMc with SPLIT_BF16 is the fused kernel of the last two modes,
+ *              then the chain over the others: it needs the kept mode below N-2
+ *              and R_{N-2}, R_{N-1} <= 32 (else DEINSUM_ERR_UNSUPPORTED).  Rows
+ *              of I_{N-1} words that are not 16-byte aligned (I_{N-1} not a
+ *              multiple of 4, or X offset from a 16-byte boundary) take the
+ *              row-class maps; those need at least 4 rows in all
+ *              (I_0 ... I_{N-2}) and extents within 32-bit coordinates (else
+ *              DEINSUM_ERR_UNSUPPORTED at plan time for I_{N-1} mod 4 != 0,
+ *              DEINSUM_ERR_ALIGN at execute time for an offset X).
  *   extents    one positive extent per distinct letter, in order of first
  *              appearance in `einsum` (host array of n_extents values).
  *   dtype      tensor element type.
